@@ -1,0 +1,346 @@
+/*
+ * spinsys_oracle.c -- plain, slow, FP64 CPU oracle of the stochastic Heun-LLG step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call this
+ * file; only tests, the smoke check and the benchmark's CPU-baseline leg use it.  It
+ * shares no code, header, table or constant generator with the CUDA path.
+ *
+ * What it computes (Evans et al., "Atomistic spin model simulations of magnetic
+ * nanomaterials", arXiv:1310.6143):
+ *   - Hamiltonian H = H_exc + H_ani + H_app                       (Eq. spinhamiltonian)
+ *       H_exc = -sum_{i!=j} J_ij S_i.S_j, each bond counted once   (Eq. HJij, reading below)
+ *       H_ani = -k_u sum_i (S_i.e)^2                              (uniaxial anisotropy eq.)
+ *       H_app = -sum_i mu_s S_i.H_app                             (applied-field eq.)
+ *     plus an optional per-site Neel surface tensor term -S_i^T K_i S_i (not in the
+ *     paper; a project extension for surface anisotropy, folded into the anisotropy
+ *     energy).
+ *   - Effective field H_eff = -(1/mu_s) dH/dS_i                    (Eq. Heff)
+ *   - Langevin thermal field Gamma(t) sqrt(2 lambda kB T/(gamma mu_s dt))  (thermal-field eq.)
+ *   - LLG right-hand side -gamma/(1+lambda^2)[S x H + lambda S x (S x H)]  (Eq. LLG)
+ *   - Heun predictor / corrector with renormalisation after both passes and the thermal
+ *     field held fixed between them; predictor over all spins before any corrector
+ *     (Section "Time Integration of the LLG Equation").
+ *
+ * Readings of the paper that this file takes (the paper is silent or ambiguous):
+ *   R1  H_exc counts each bond once: the field is (1/mu_s) sum_j J_ij S_j and the energy
+ *       is -1/2 sum_i sum_j J_ij S_i.S_j over the (symmetric) neighbour list.
+ *   R2  Constants are the paper's Table I values (gamma = 1.76e11, kB = 1.3807e-23).
+ *   R3  Noise variance 2 lambda kB T/(gamma mu_s dt) carries no (1+lambda^2) factor.
+ *   R4  The thermal field for step n is drawn once, at temperature T(t_n), t_n = n dt,
+ *       and used unchanged by predictor and corrector.
+ *   R5  The corrector starts from the un-normalised sum S + dt/2 (dS + dS') and is then
+ *       renormalised; dS' is evaluated at the renormalised predictor spin S'.
+ *   R6  Random numbers: the paper's Mersenne Twister + Ziggurat is replaced by a
+ *       counter-based Philox4x32-10 generator (Salmon, Moraes, Dror and Shaw, SC'11)
+ *       followed by the Box-Muller transform (Box and Muller, 1958).  One Philox call per
+ *       (spin, step): counter (i, n, system, 0), key (seed low word, seed high word);
+ *       u_k = (w_k + 1/2) 2^-32;  gx = sqrt(-2 ln u0) cos(2 pi u1),
+ *       gy = sqrt(-2 ln u0) sin(2 pi u1),  gz = sqrt(-2 ln u2) cos(2 pi u3).
+ *       Initial random spins use counter (i, 0xFFFFFFFF, system, 1) and normalise the
+ *       same three Gaussians.
+ *   R7  Magnetisation is sum_i mu_s,i S_i (and sum_i mu_s,i); the per-step record holds
+ *       the state at the start of the step, S(t_n).
+ *
+ * Layout: spins and vectors are array-of-structures, 3 doubles per site (x, y, z).
+ * Neel tensors are 6 doubles per site in the order xx, yy, zz, xy, xz, yz.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no fused multiply-add, so
+ * every product and sum is rounded as written).  The spin loops may run on several
+ * threads; every site is computed independently and every sum over sites runs serially
+ * in site order, so the result does not depend on the thread count.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_KB 1.3807e-23      /* Boltzmann constant, J/K (Table I) */
+#define ORC_GAMMA 1.76e11      /* gyromagnetic ratio, 1/(T s) (Table I) */
+#define ORC_PI 3.14159265358979323846
+
+typedef struct {
+    int64_t n;                /* number of spins                                  */
+    const int64_t *row_ptr;   /* [n+1] CSR row offsets                             */
+    const int32_t *col;       /* [nnz] neighbour indices                           */
+    const double *J;          /* [nnz] exchange constants, J/link                  */
+    const double *mu_s;       /* [n] atomic moments, J/T                           */
+    const double *k_u;        /* [n] uniaxial anisotropy, J/atom                   */
+    const double *easy_axis;  /* [3n] unit easy axes                               */
+    const double *K_neel;     /* [6n] Neel tensors (xx,yy,zz,xy,xz,yz) or NULL     */
+    double alpha;             /* Gilbert damping lambda                            */
+    double dt;                /* time step, s                                      */
+    double gamma;             /* gyromagnetic ratio, 1/(T s)                       */
+    double H_app[3];          /* applied field, T                                  */
+    uint64_t seed;            /* Philox key                                        */
+    uint32_t sys;             /* system id (third counter word)                    */
+} orc_system;
+
+static int g_threads = 1;
+
+void orc_set_threads(int t) { g_threads = t < 1 ? 1 : t; }
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplications   */
+/* with the published multipliers, the key bumped by the published Weyl increments     */
+/* between rounds.                                                                      */
+/* ---------------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static double orc_uniform(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
+
+/* Three standard Gaussians from one Philox block (reading R6). */
+static void orc_box_muller3(const uint32_t w[4], double g[3]) {
+    double u0 = orc_uniform(w[0]), u1 = orc_uniform(w[1]);
+    double u2 = orc_uniform(w[2]), u3 = orc_uniform(w[3]);
+    double r1 = sqrt(-2.0 * log(u0));
+    double r2 = sqrt(-2.0 * log(u2));
+    double phi1 = 2.0 * ORC_PI * u1;
+    double phi2 = 2.0 * ORC_PI * u3;
+    g[0] = r1 * cos(phi1);
+    g[1] = r1 * sin(phi1);
+    g[2] = r2 * cos(phi2);
+}
+
+void orc_thermal_gaussians(uint64_t seed, uint32_t sys, uint32_t spin, uint32_t step, double g[3]) {
+    uint32_t ctr[4] = {spin, step, sys, 0u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    orc_box_muller3(w, g);
+}
+
+/* Random-on-sphere initial state: normalised Gaussian triple from the reserved stream. */
+void orc_init_sphere(uint64_t seed, uint32_t sys, int64_t n, double *S) {
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t ctr[4] = {(uint32_t)i, 0xFFFFFFFFu, sys, 1u};
+        uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+        uint32_t w[4];
+        double g[3];
+        orc_philox4x32_10(ctr, key, w);
+        orc_box_muller3(w, g);
+        double len = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        S[3 * i + 0] = g[0] / len;
+        S[3 * i + 1] = g[1] / len;
+        S[3 * i + 2] = g[2] / len;
+    }
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Deterministic field of one site, Eq. Heff applied to the Hamiltonian terms.         */
+/* hex receives the raw exchange sum sum_j J_ij S_j (J), H the field in tesla.         */
+/* Terms are added in the order: exchange, anisotropy, applied, Neel.                  */
+/* ---------------------------------------------------------------------------------- */
+static void orc_site_field(const orc_system *s, const double *S, int64_t i, double hex[3], double H[3]) {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t k = s->row_ptr[i]; k < s->row_ptr[i + 1]; ++k) {
+        int64_t j = s->col[k];
+        sx += s->J[k] * S[3 * j + 0];
+        sy += s->J[k] * S[3 * j + 1];
+        sz += s->J[k] * S[3 * j + 2];
+    }
+    hex[0] = sx; hex[1] = sy; hex[2] = sz;
+    double mu = s->mu_s[i];
+    /* exchange: -(1/mu) d/dS_i of -sum_{bonds} J S_i.S_j */
+    H[0] = sx / mu;
+    H[1] = sy / mu;
+    H[2] = sz / mu;
+    /* uniaxial anisotropy: -(1/mu) d/dS of -k_u (S.e)^2 = (2 k_u/mu)(S.e) e */
+    const double *e = s->easy_axis + 3 * i;
+    double sdote = S[3 * i + 0] * e[0] + S[3 * i + 1] * e[1] + S[3 * i + 2] * e[2];
+    double a = 2.0 * s->k_u[i] / mu * sdote;
+    H[0] += a * e[0];
+    H[1] += a * e[1];
+    H[2] += a * e[2];
+    /* applied field: -(1/mu) d/dS of -mu S.H_app = H_app */
+    H[0] += s->H_app[0];
+    H[1] += s->H_app[1];
+    H[2] += s->H_app[2];
+    /* Neel tensor: -(1/mu) d/dS of -S^T K S = (2/mu) K S */
+    if (s->K_neel) {
+        const double *K = s->K_neel + 6 * i;
+        double x = S[3 * i + 0], y = S[3 * i + 1], z = S[3 * i + 2];
+        double kx = K[0] * x + K[3] * y + K[4] * z;
+        double ky = K[3] * x + K[1] * y + K[5] * z;
+        double kz = K[4] * x + K[5] * y + K[2] * z;
+        H[0] += 2.0 / mu * kx;
+        H[1] += 2.0 / mu * ky;
+        H[2] += 2.0 / mu * kz;
+    }
+}
+
+/* Deterministic fields of all sites (tesla), AoS [3n]; exposed for tests. */
+void orc_fields(const orc_system *s, const double *S, double *H) {
+    for (int64_t i = 0; i < s->n; ++i) {
+        double hex[3];
+        orc_site_field(s, S, i, hex, H + 3 * i);
+    }
+}
+
+/* Magnetisation and energy of a state (reading R7, energy per R1):
+ * out = {sum mu Sx, sum mu Sy, sum mu Sz, sum mu, E_exc, E_ani, E_app, E_total} (J/T, J). */
+void orc_moment_energy(const orc_system *s, const double *S, double out[8]) {
+    double m0 = 0, m1 = 0, m2 = 0, msum = 0, eex = 0, ean = 0, eap = 0;
+    for (int64_t i = 0; i < s->n; ++i) {
+        double hex[3], H[3];
+        orc_site_field(s, S, i, hex, H);
+        const double *Si = S + 3 * i;
+        double mu = s->mu_s[i];
+        m0 += mu * Si[0];
+        m1 += mu * Si[1];
+        m2 += mu * Si[2];
+        msum += mu;
+        eex += -0.5 * (Si[0] * hex[0] + Si[1] * hex[1] + Si[2] * hex[2]);
+        const double *e = s->easy_axis + 3 * i;
+        double sdote = Si[0] * e[0] + Si[1] * e[1] + Si[2] * e[2];
+        double ea = -s->k_u[i] * sdote * sdote;
+        if (s->K_neel) {
+            const double *K = s->K_neel + 6 * i;
+            double x = Si[0], y = Si[1], z = Si[2];
+            double q = K[0] * x * x + K[1] * y * y + K[2] * z * z
+                     + 2.0 * (K[3] * x * y + K[4] * x * z + K[5] * y * z);
+            ea += -q;
+        }
+        ean += ea;
+        eap += -mu * (Si[0] * s->H_app[0] + Si[1] * s->H_app[1] + Si[2] * s->H_app[2]);
+    }
+    out[0] = m0; out[1] = m1; out[2] = m2; out[3] = msum;
+    out[4] = eex; out[5] = ean; out[6] = eap; out[7] = eex + ean + eap;
+}
+
+/* LLG right-hand side, Eq. LLG. */
+static void orc_llg(double gamma, double lambda, const double S[3], const double H[3], double dS[3]) {
+    double c0 = S[1] * H[2] - S[2] * H[1];
+    double c1 = S[2] * H[0] - S[0] * H[2];
+    double c2 = S[0] * H[1] - S[1] * H[0];
+    double d0 = S[1] * c2 - S[2] * c1;
+    double d1 = S[2] * c0 - S[0] * c2;
+    double d2 = S[0] * c1 - S[1] * c0;
+    double pre = -gamma / (1.0 + lambda * lambda);
+    dS[0] = pre * (c0 + lambda * d0);
+    dS[1] = pre * (c1 + lambda * d1);
+    dS[2] = pre * (c2 + lambda * d2);
+}
+
+static void orc_normalise(double v[3]) {
+    double len = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] = v[0] / len;
+    v[1] = v[1] / len;
+    v[2] = v[2] / len;
+}
+
+/*
+ * Advance nsteps Heun steps from step index step0.  S [3n] is updated in place.
+ * T[k] is the temperature of step step0+k (K).  If rec is not NULL it receives
+ * 8 doubles per step: orc_moment_energy of the state at the start of that step.
+ * Returns 0, or -1 if memory could not be allocated.
+ */
+int orc_heun_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, const double *T, double *rec) {
+    int64_t n = s->n;
+    double *Hth = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *dS = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *Sp = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    if (!Hth || !dS || !Sp) {
+        free(Hth); free(dS); free(Sp);
+        return -1;
+    }
+    double gamma = s->gamma > 0.0 ? s->gamma : ORC_GAMMA;
+    double lambda = s->alpha;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        uint32_t step = (uint32_t)(step0 + k);
+        double Tn = T[k];
+        if (rec) orc_moment_energy(s, S, rec + 8 * k);
+        /* thermal field, drawn once per step (R4) */
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+        for (int64_t i = 0; i < n; ++i) {
+            double g[3];
+            orc_thermal_gaussians(s->seed, s->sys, (uint32_t)i, step, g);
+            double sigma = sqrt(2.0 * lambda * ORC_KB * Tn / (gamma * s->mu_s[i] * s->dt));
+            Hth[3 * i + 0] = sigma * g[0];
+            Hth[3 * i + 1] = sigma * g[1];
+            Hth[3 * i + 2] = sigma * g[2];
+        }
+        /* predictor on every spin */
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+        for (int64_t i = 0; i < n; ++i) {
+            double hex[3], H[3];
+            orc_site_field(s, S, i, hex, H);
+            H[0] += Hth[3 * i + 0];
+            H[1] += Hth[3 * i + 1];
+            H[2] += Hth[3 * i + 2];
+            orc_llg(gamma, lambda, S + 3 * i, H, dS + 3 * i);
+            double v[3];
+            v[0] = S[3 * i + 0] + dS[3 * i + 0] * s->dt;
+            v[1] = S[3 * i + 1] + dS[3 * i + 1] * s->dt;
+            v[2] = S[3 * i + 2] + dS[3 * i + 2] * s->dt;
+            orc_normalise(v);
+            Sp[3 * i + 0] = v[0];
+            Sp[3 * i + 1] = v[1];
+            Sp[3 * i + 2] = v[2];
+        }
+        /* corrector on every spin, field re-evaluated at S' with the same thermal field */
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+        for (int64_t i = 0; i < n; ++i) {
+            double hex[3], H[3], dSp[3];
+            orc_site_field(s, Sp, i, hex, H);
+            H[0] += Hth[3 * i + 0];
+            H[1] += Hth[3 * i + 1];
+            H[2] += Hth[3 * i + 2];
+            orc_llg(gamma, lambda, Sp + 3 * i, H, dSp);
+            double v[3];
+            v[0] = S[3 * i + 0] + 0.5 * (dS[3 * i + 0] + dSp[0]) * s->dt;
+            v[1] = S[3 * i + 1] + 0.5 * (dS[3 * i + 1] + dSp[1]) * s->dt;
+            v[2] = S[3 * i + 2] + 0.5 * (dS[3 * i + 2] + dSp[2]) * s->dt;
+            orc_normalise(v);
+            /* S_i is only read by site i in this pass, so it can be overwritten here */
+            S[3 * i + 0] = v[0];
+            S[3 * i + 1] = v[1];
+            S[3 * i + 2] = v[2];
+        }
+    }
+    free(Hth); free(dS); free(Sp);
+    return 0;
+}
+
+/* Bulk helpers for statistical tests: Philox blocks of counters (c0+k, c1, c2, c3), and
+ * the thermal Gaussians of spins 0..n-1 at one step, both in the definitions above. */
+void orc_philox_bulk(const uint32_t ctr0[4], const uint32_t key[2], int64_t count, uint32_t *out) {
+    for (int64_t k = 0; k < count; ++k) {
+        uint32_t c[4] = {ctr0[0] + (uint32_t)k, ctr0[1], ctr0[2], ctr0[3]};
+        orc_philox4x32_10(c, key, out + 4 * k);
+    }
+}
+
+void orc_gaussians_bulk(uint64_t seed, uint32_t sys, uint32_t step, int64_t n, double *g) {
+    for (int64_t i = 0; i < n; ++i) orc_thermal_gaussians(seed, sys, (uint32_t)i, step, g + 3 * i);
+}

@@ -1,0 +1,345 @@
+"""Seeded synthetic spin systems: lattice generation and CSR neighbour lists.
+
+This module builds the *inputs* of the Heun-LLG step -- site positions, per-site moments
+and anisotropies, and the exchange neighbour list in CSR form -- following the system
+generation scheme of arXiv:1310.6143 (Appendix B: replicate a unit cell, cut the shape,
+assign materials, build the nearest-neighbour interaction list from per-cell offsets).
+It contains no part of the integrator, field or reduction arithmetic, and is used by
+both the CUDA path and the CPU oracle's tests.
+
+Conventions
+-----------
+* SI units: moments in J/T, energies in J, fields in T, lengths in m.
+* CSR rows list every neighbour j of site i (both directions of every bond), no self
+  bonds; ``row_ptr`` is int64, ``col`` int32, ``J`` float64.
+* Simple-cubic index ``i = z + nz * (x + nx * y)`` (z fastest): for a thin film the
+  short axis is contiguous, so the six neighbours of a site are within +-nz*nx sites.
+* FCC: four sites per cubic cell at (0,0,0), (1/2,1/2,0), (1/2,0,1/2), (0,1/2,1/2);
+  index ``i = b + 4 * (cz + nz * (cx + nx * cy))``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MU_B = 9.2740e-24  # Bohr magneton, J/T (Table I of the paper)
+KB = 1.3807e-23    # Boltzmann constant, J/K (Table I)
+
+
+@dataclass
+class SpinLattice:
+    """A spin system as plain arrays (the argument set of ``spin_system_create``)."""
+
+    row_ptr: np.ndarray            # int64 [n+1]
+    col: np.ndarray                # int32 [nnz]
+    J: np.ndarray                  # float64 [nnz], J/link
+    mu_s: np.ndarray               # float64 [n], J/T
+    k_u: np.ndarray                # float64 [n], J/atom
+    easy_axis: np.ndarray          # float64 [n, 3]
+    K_neel: np.ndarray | None = None   # float64 [n, 6] (xx, yy, zz, xy, xz, yz) or None
+    pos: np.ndarray | None = None      # float64 [n, 3], m
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.row_ptr.size - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.size)
+
+
+def _csr_from_targets(targets: np.ndarray, jvals: np.ndarray | float):
+    """targets: (n, z) int64 neighbour ids, -1 where absent; rows keep column order."""
+    valid = targets >= 0
+    counts = valid.sum(axis=1)
+    row_ptr = np.zeros(targets.shape[0] + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    col = targets[valid].astype(np.int32)
+    if np.isscalar(jvals):
+        J = np.full(col.size, float(jvals))
+    else:
+        J = np.asarray(jvals, dtype=np.float64)[valid]
+    return row_ptr, col, J
+
+
+def _homogeneous(n, mu_s, k_u, easy_axis):
+    ax = np.asarray(easy_axis, dtype=np.float64)
+    ax = ax / np.linalg.norm(ax)
+    return (np.full(n, float(mu_s)), np.full(n, float(k_u)), np.ascontiguousarray(np.broadcast_to(ax, (n, 3))))
+
+
+def simple_cubic(nx: int, ny: int, nz: int, periodic=(True, True, True), J=6.0e-21,
+                 mu_s=1.5 * MU_B, k_u=1.0e-24, easy_axis=(0.0, 0.0, 1.0), a=3.0e-10,
+                 with_pos: bool = False) -> SpinLattice:
+    """Simple-cubic lattice with nearest-neighbour exchange (z = 6 in the bulk).
+
+    Each row lists neighbours in the order -z, +z, -x, +x, -y, +y (absent ones skipped at
+    free surfaces).  A periodic axis needs at least 3 sites, so that no bond is a self
+    bond or a duplicate.
+    """
+    for L, p in zip((nx, ny, nz), periodic):
+        if L < 1 or (p and L < 3):
+            raise ValueError("each axis needs >= 1 site, periodic axes >= 3 sites")
+    n = nx * ny * nz
+    idx = np.arange(n, dtype=np.int64)
+    z = idx % nz
+    x = (idx // nz) % nx
+    y = idx // (nz * nx)
+
+    def site(xx, yy, zz):
+        return zz + nz * (xx + nx * yy)
+
+    targets = np.full((n, 6), -1, dtype=np.int64)
+    for d, (axis, step) in enumerate((("z", -1), ("z", 1), ("x", -1), ("x", 1), ("y", -1), ("y", 1))):
+        L, p = {"x": (nx, periodic[0]), "y": (ny, periodic[1]), "z": (nz, periodic[2])}[axis]
+        coord = {"x": x, "y": y, "z": z}[axis]
+        c2 = coord + step
+        ok = (c2 >= 0) & (c2 < L)
+        if p:
+            c2 = c2 % L
+            ok = np.ones(n, dtype=bool)
+        xx = c2 if axis == "x" else x
+        yy = c2 if axis == "y" else y
+        zz = c2 if axis == "z" else z
+        t = site(xx % nx, yy % ny, zz % nz)
+        targets[:, d] = np.where(ok, t, -1)
+    row_ptr, col, Jv = _csr_from_targets(targets, J)
+    mu, ku, ax = _homogeneous(n, mu_s, k_u, easy_axis)
+    pos = np.stack([x, y, z], axis=1).astype(np.float64) * a if with_pos else None
+    return SpinLattice(row_ptr, col, Jv, mu, ku, ax, None, pos,
+                       meta={"kind": "sc", "dims": (nx, ny, nz), "periodic": tuple(periodic), "a": a})
+
+
+_FCC_BASIS = np.array([[0, 0, 0], [1, 1, 0], [1, 0, 1], [0, 1, 1]], dtype=np.int64)  # doubled units
+_FCC_NN = np.array([[sx, sy, 0] for sx in (-1, 1) for sy in (-1, 1)]
+                   + [[sx, 0, sz] for sx in (-1, 1) for sz in (-1, 1)]
+                   + [[0, sy, sz] for sy in (-1, 1) for sz in (-1, 1)], dtype=np.int64)
+
+
+def _fcc_sites(nx, ny, nz):
+    """Doubled integer coordinates of all fcc sites in nx*ny*nz cells, in index order."""
+    ncell = nx * ny * nz
+    c = np.arange(ncell, dtype=np.int64)
+    cz = c % nz
+    cx = (c // nz) % nx
+    cy = c // (nz * nx)
+    cell = np.stack([cx, cy, cz], axis=1) * 2
+    X = (cell[:, None, :] + _FCC_BASIS[None, :, :]).reshape(-1, 3)
+    return X
+
+
+def _fcc_index(X, nx, ny, nz):
+    """Inverse of _fcc_sites for doubled coordinates already wrapped into the box."""
+    cx, cy, cz = X[:, 0] // 2, X[:, 1] // 2, X[:, 2] // 2
+    px, py, pz = X[:, 0] % 2, X[:, 1] % 2, X[:, 2] % 2
+    b = np.where((px == 0) & (py == 0), 0, np.where(pz == 0, 1, np.where(py == 0, 2, 3)))
+    return b + 4 * (cz + nz * (cx + nx * cy))
+
+
+def fcc(nx: int, ny: int, nz: int, periodic=(True, True, True), J=11.2e-21, mu_s=1.72 * MU_B,
+        k_u=6.69e-24, easy_axis=(0.0, 0.0, 1.0), a=3.524e-10, with_pos: bool = False) -> SpinLattice:
+    """Face-centred-cubic lattice of nx*ny*nz cubic cells, 12 nearest neighbours at a/sqrt(2)."""
+    for L, p in zip((nx, ny, nz), periodic):
+        if L < 1 or (p and L < 2):
+            raise ValueError("fcc: each axis needs >= 1 cell, periodic axes >= 2 cells")
+    X = _fcc_sites(nx, ny, nz)
+    n = X.shape[0]
+    dims = np.array([2 * nx, 2 * ny, 2 * nz])
+    targets = np.full((n, 12), -1, dtype=np.int64)
+    for d in range(12):
+        Y = X + _FCC_NN[d]
+        ok = np.ones(n, dtype=bool)
+        for ax in range(3):
+            if periodic[ax]:
+                Y[:, ax] %= dims[ax]
+            else:
+                ok &= (Y[:, ax] >= 0) & (Y[:, ax] < dims[ax])
+        Yc = np.where(ok[:, None], Y, 0)
+        targets[:, d] = np.where(ok, _fcc_index(Yc, nx, ny, nz), -1)
+    row_ptr, col, Jv = _csr_from_targets(targets, J)
+    mu, ku, ax_ = _homogeneous(n, mu_s, k_u, easy_axis)
+    pos = X.astype(np.float64) * (a / 2) if with_pos else None
+    return SpinLattice(row_ptr, col, Jv, mu, ku, ax_, None, pos,
+                       meta={"kind": "fcc", "cells": (nx, ny, nz), "periodic": tuple(periodic), "a": a})
+
+
+def film(nx=1024, ny=1024, nz=16, J=6.0e-21, mu_s=1.5 * MU_B, k_u=1.0e-24) -> SpinLattice:
+    """Thin simple-cubic film, periodic in-plane, free surfaces in z."""
+    lat = simple_cubic(nx, ny, nz, periodic=(True, True, False), J=J, mu_s=mu_s, k_u=k_u)
+    lat.meta["kind"] = "film"
+    return lat
+
+
+def neel_tensors(pos: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, k_s: float,
+                 mask: np.ndarray) -> np.ndarray:
+    """Neel pair surface-anisotropy tensors K_i = (k_s/2) sum_j e_ij e_ij^T on masked sites.
+
+    e_ij is the unit bond vector to neighbour j.  The energy of site i is -S_i^T K_i S_i.
+    Returns (n, 6) in the order xx, yy, zz, xy, xz, yz (zero rows where mask is False).
+    """
+    n = row_ptr.size - 1
+    rows = np.repeat(np.arange(n), np.diff(row_ptr))
+    d = pos[col] - pos[rows]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    comps = np.stack([d[:, 0] * d[:, 0], d[:, 1] * d[:, 1], d[:, 2] * d[:, 2],
+                      d[:, 0] * d[:, 1], d[:, 0] * d[:, 2], d[:, 1] * d[:, 2]], axis=1)
+    K = np.zeros((n, 6))
+    np.add.at(K, rows, comps)
+    K *= 0.5 * k_s
+    K[~mask] = 0.0
+    return K
+
+
+def core_shell_sphere(diameter=20e-9, a=3.524e-10, r_core=8e-9, J_core=11.2e-21, J_shell=-5.0e-21,
+                      J_int=2.0e-21, mu_s=1.72 * MU_B, k_s=5.0e-23, z_full=12) -> SpinLattice:
+    """FCC sphere cut from a crystal: ferromagnetic core, antiferromagnetic shell.
+
+    Bonds are core-core J_core, shell-shell J_shell and core-shell J_int.  Sites with
+    fewer than ``z_full`` neighbours (the surface) carry a Neel pair anisotropy tensor of
+    strength k_s.  No uniaxial anisotropy (k_u = 0, easy axis +z).
+    """
+    R = diameter / 2
+    cells = int(np.ceil(diameter / a)) + 1
+    X = _fcc_sites(cells, cells, cells)
+    centre = np.full(3, cells * a / 2)
+    P = X.astype(np.float64) * (a / 2) - centre
+    keep = np.einsum("ij,ij->i", P, P) <= R * R
+    new_id = np.full(X.shape[0], -1, dtype=np.int64)
+    new_id[keep] = np.arange(int(keep.sum()))
+    Xk = X[keep]
+    Pk = P[keep]
+    n = Xk.shape[0]
+    dims = np.array([2 * cells] * 3)
+    core = np.einsum("ij,ij->i", Pk, Pk) < r_core * r_core
+    targets = np.full((n, 12), -1, dtype=np.int64)
+    jv = np.zeros((n, 12))
+    for d in range(12):
+        Y = Xk + _FCC_NN[d]
+        ok = np.all((Y >= 0) & (Y < dims), axis=1)
+        Yc = np.where(ok[:, None], Y, 0)
+        t = new_id[_fcc_index(Yc, cells, cells, cells)]
+        t = np.where(ok, t, -1)
+        targets[:, d] = t
+        tc = np.where(t >= 0, core[np.maximum(t, 0)], False)
+        jv[:, d] = np.where(core & tc, J_core, np.where(~core & ~tc, J_shell, J_int))
+    row_ptr, col, Jv = _csr_from_targets(targets, jv)
+    mu, ku, ax = _homogeneous(n, mu_s, 0.0, (0, 0, 1))
+    coord = np.diff(row_ptr)
+    K = neel_tensors(Pk, row_ptr, col, k_s, coord < z_full)
+    return SpinLattice(row_ptr, col, Jv, mu, ku, ax, K, Pk,
+                       meta={"kind": "core_shell", "diameter": diameter, "r_core": r_core,
+                             "n_core": int(core.sum()), "n_surface": int((coord < z_full).sum())})
+
+
+def _grain_shape(rng, target_columns, n_nbr=7):
+    """Columns (x, y) of one Voronoi-like cell: the points nearer the origin than any of
+    n_nbr seeded neighbour seeds, with the seed distance scaled so the cell holds
+    about target_columns lattice columns."""
+    ang = (np.linspace(0, 2 * np.pi, n_nbr, endpoint=False) + rng.uniform(-0.3, 0.3, n_nbr)
+           + rng.uniform(0, 2 * np.pi))
+    rad = rng.uniform(0.8, 1.2, n_nbr)
+    q = np.stack([np.cos(ang) * rad, np.sin(ang) * rad], axis=1)
+
+    def columns(D):
+        ext = int(np.ceil(D * 1.3)) + 2
+        g = np.arange(-ext, ext + 1)
+        gx, gy = np.meshgrid(g, g, indexing="ij")
+        p = np.stack([gx.ravel(), gy.ravel()], axis=1).astype(np.float64)
+        qq = q * D
+        inside = np.all(p @ qq.T < 0.5 * np.einsum("ij,ij->i", qq, qq)[None, :], axis=1)
+        return p[inside].astype(np.int64)
+
+    lo, hi = 1.0, 2.0
+    while columns(hi).shape[0] < target_columns:
+        hi *= 2
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        if columns(mid).shape[0] < target_columns:
+            lo = mid
+        else:
+            hi = mid
+    return columns(hi)
+
+
+def grain(columns: np.ndarray, layers: int, J=6.0e-21, mu_s=1.5 * MU_B, k_u=1.0e-23,
+          easy_axis=(0, 0, 1)) -> SpinLattice:
+    """A columnar grain: the given (x, y) columns extruded over ``layers`` simple-cubic
+    layers, free surfaces everywhere, sites ordered by column then layer."""
+    cols = columns - columns.min(axis=0)
+    W = int(cols[:, 0].max()) + 1
+    H = int(cols[:, 1].max()) + 1
+    order = np.lexsort((cols[:, 0], cols[:, 1]))
+    cols = cols[order]
+    ncol = cols.shape[0]
+    colid = np.full((W + 2, H + 2), -1, dtype=np.int64)
+    colid[cols[:, 0] + 1, cols[:, 1] + 1] = np.arange(ncol)
+    n = ncol * layers
+    idx = np.arange(n)
+    z = idx % layers
+    c = idx // layers
+    cx, cy = cols[c, 0] + 1, cols[c, 1] + 1
+    targets = np.full((n, 6), -1, dtype=np.int64)
+    targets[:, 0] = np.where(z > 0, idx - 1, -1)
+    targets[:, 1] = np.where(z < layers - 1, idx + 1, -1)
+    for d, (dx, dy) in enumerate(((-1, 0), (1, 0), (0, -1), (0, 1))):
+        nb = colid[cx + dx, cy + dy]
+        targets[:, 2 + d] = np.where(nb >= 0, nb * layers + z, -1)
+    row_ptr, col, Jv = _csr_from_targets(targets, J)
+    mu, ku, ax = _homogeneous(n, mu_s, k_u, easy_axis)
+    return SpinLattice(row_ptr, col, Jv, mu, ku, ax, None, None,
+                       meta={"kind": "grain", "columns": ncol, "layers": layers})
+
+
+def grain_ensemble(count=256, n_min=2000, n_max=40000, layers=10, seed=12345, J=6.0e-21,
+                   mu_s=1.5 * MU_B, ku_mean=1.0e-23, ku_lnsigma=0.3, cap_deg=5.0, T_max=800.0):
+    """Independent columnar Voronoi-like grains (the granular-medium picture of Appendix B).
+
+    Grain sizes are uniform in [n_min, n_max] spins; k_u is log-normal with arithmetic mean
+    ku_mean and log-sigma ku_lnsigma; easy axes are uniform on the spherical cap within
+    cap_deg of +z; temperatures are uniform in [0, T_max].  Returns (grains, temperatures).
+    """
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(n_min, n_max + 1, size=count)
+    mu_ln = np.log(ku_mean) - 0.5 * ku_lnsigma ** 2
+    kus = np.exp(rng.normal(mu_ln, ku_lnsigma, size=count))
+    cos_cap = np.cos(np.deg2rad(cap_deg))
+    ct = rng.uniform(cos_cap, 1.0, size=count)
+    ph = rng.uniform(0, 2 * np.pi, size=count)
+    st = np.sqrt(1 - ct * ct)
+    axes = np.stack([st * np.cos(ph), st * np.sin(ph), ct], axis=1)
+    temps = rng.uniform(0.0, T_max, size=count)
+    grains = []
+    for g in range(count):
+        cols = _grain_shape(rng, max(1, int(round(sizes[g] / layers))))
+        gr = grain(cols, layers, J=J, mu_s=mu_s, k_u=float(kus[g]), easy_axis=axes[g])
+        gr.meta.update({"grain": g, "T": float(temps[g])})
+        grains.append(gr)
+    return grains, temps
+
+
+def single_spin(mu_s=1.5 * MU_B, k_u=0.0, easy_axis=(0, 0, 1)) -> SpinLattice:
+    """One isolated spin (empty neighbour list)."""
+    mu, ku, ax = _homogeneous(1, mu_s, k_u, easy_axis)
+    return SpinLattice(np.zeros(2, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0), mu, ku, ax,
+                       meta={"kind": "single"})
+
+
+def dimer(J=6.0e-21, mu_s=1.5 * MU_B, k_u=0.0) -> SpinLattice:
+    """Two spins joined by one bond."""
+    mu, ku, ax = _homogeneous(2, mu_s, k_u, (0, 0, 1))
+    return SpinLattice(np.array([0, 1, 2], dtype=np.int64), np.array([1, 0], dtype=np.int32),
+                       np.array([J, J]), mu, ku, ax, meta={"kind": "dimer"})
+
+
+def uniform_state(n: int, direction=(0.0, 0.0, 1.0)) -> np.ndarray:
+    d = np.asarray(direction, dtype=np.float64)
+    return np.ascontiguousarray(np.broadcast_to(d / np.linalg.norm(d), (n, 3)))
+
+
+def random_state(n: int, seed: int) -> np.ndarray:
+    """Seeded random unit vectors (numpy generator; input data, not the method's stream)."""
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
