@@ -1,0 +1,241 @@
+/*
+ * spinsys.h -- C ABI of the GB300 stochastic Heun-LLG spin-dynamics library
+ * (libspinsys.so).  Plain C types only: host pointers, sizes and opaque handles.
+ *
+ * The library integrates the stochastic Landau-Lifshitz-Gilbert equation of an atomistic
+ * classical Heisenberg spin model (Evans et al., "Atomistic spin model simulations of
+ * magnetic nanomaterials", arXiv:1310.6143):
+ *
+ *   Hamiltonian     H = -sum_{bonds} J_ij S_i.S_j - sum_i k_u (S_i.e_i)^2
+ *                       - sum_i mu_s S_i.H_app [- sum_i S_i^T K_i S_i]
+ *                   (Eq. spinhamiltonian, Eq. HJij, the uniaxial and applied-field terms;
+ *                   each bond of the symmetric neighbour list counted once; the Neel
+ *                   surface tensor K_i is an optional extension)
+ *   effective field H_eff = -(1/mu_s) dH/dS_i + H_th                    (Eqs. Heff, Heffth)
+ *   thermal field   H_th = Gamma sqrt(2 lambda kB T / (gamma mu_s dt))   (Langevin dynamics)
+ *   equation        dS/dt = -gamma/(1+lambda^2) [S x H + lambda S x (S x H)]     (Eq. LLG)
+ *   integrator      Heun predictor-corrector, |S| renormalised after both passes, the
+ *                   thermal field held fixed between them, predictor over all spins
+ *                   before any corrector (Section "Time Integration of the LLG Equation").
+ *
+ * The paper's Mersenne Twister + Ziggurat generator is replaced by Philox4x32-10
+ * (Salmon et al., SC'11) with counter (spin index within its system, step, system id, 0)
+ * and key (seed low word, seed high word), followed by an FP64 Box-Muller transform:
+ * u_k = (w_k + 1/2) 2^-32, gx = sqrt(-2 ln u0) cos(2 pi u1), gy = sqrt(-2 ln u0)
+ * sin(2 pi u1), gz = sqrt(-2 ln u2) cos(2 pi u3).  Steps are counted modulo 2^32 in the
+ * counter.  Constants are those of Table I: gamma = 1.76e11 1/(T s), kB = 1.3807e-23 J/K.
+ *
+ * Units: SI throughout -- moments J/T, energies J, fields T, temperatures K, time s.
+ * Layouts: vectors are array-of-structures on the host (x, y, z per site); Neel tensors
+ * are 6 doubles per site (xx, yy, zz, xy, xz, yz).  On the device spins are stored as
+ * structure-of-arrays in the working precision.
+ *
+ * Ownership: every host array passed in is caller-owned and copied during the call.
+ * Device memory is owned by the handle and released by spin_system_destroy.  Device
+ * pointers returned by get_spins_device stay valid until the next call that changes the
+ * state (llg_heun_step, set_spins) or spin_system_destroy.
+ *
+ * Errors: every call returns an ss_status and never aborts the process.  A message for
+ * the last failure of a handle is available from ss_last_error.  After a CUDA error the
+ * handle answers SS_ERR_STATE to every call but spin_system_destroy.  Calls on one handle
+ * must not run concurrently from several host threads.
+ *
+ * Streams: all device work of a handle is issued on its stream (a private non-blocking
+ * stream unless spin_system_set_stream names another).  Calls that return host data
+ * synchronise that stream; llg_heun_step and the set_* calls are asynchronous.
+ */
+#ifndef SPINSYS_H
+#define SPINSYS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ss_system ss_system; /* opaque, library-owned */
+
+typedef enum {
+    SS_OK = 0,
+    SS_ERR_INVALID_ARG = 1, /* a pointer, size or value is out of range          */
+    SS_ERR_CUDA = 2,        /* a CUDA runtime call failed                         */
+    SS_ERR_OOM = 3,         /* device or host allocation failed                   */
+    SS_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out                 */
+    SS_ERR_NONFINITE = 5,   /* a spin became NaN or infinite                      */
+    SS_ERR_STATE = 6,       /* the handle is unusable after an earlier failure    */
+    SS_ERR_UNSUPPORTED = 7  /* a valid request this build cannot serve            */
+} ss_status;
+
+typedef enum {
+    SS_FP64 = 0,      /* every step in FP64                                          */
+    SS_FP32_MIXED = 1 /* FP32 storage, field and LLG arithmetic; FP64 Philox-to-Gaussian
+                         transform and FP64 moment/energy sums                        */
+} ss_precision;
+
+/* ss_params.flags */
+#define SS_FLAG_CHECK_SYMMETRY 1u /* reject a neighbour list with J_ij != J_ji      */
+#define SS_FLAG_INIT_RANDOM 2u    /* start from random unit spins drawn from the
+                                     reserved Philox stream (counter (i, 0xFFFFFFFF,
+                                     system, 1)); S0 is then ignored                 */
+
+typedef struct {
+    int64_t n;                /* spins, 1 <= n < 2^31                                  */
+    const double *pos;        /* [3n] positions (m) or NULL; validated, not used by the
+                                 step (no long-range term is computed)                */
+    const double *mu_s;       /* [n] atomic moments, J/T, > 0                          */
+    const double *k_u;        /* [n] uniaxial anisotropy, J/atom                       */
+    const double *easy_axis;  /* [3n] easy axes (normalised on copy) or NULL for +z    */
+    const int64_t *row_ptr;   /* [n+1] CSR offsets, row_ptr[0] = 0, non-decreasing,
+                                 nnz = row_ptr[n] < 2^31                               */
+    const int32_t *col;       /* [nnz] neighbour indices in [0, n), no self bonds      */
+    const double *J;          /* [nnz] exchange, J/link; the list holds both j->i and
+                                 i->j of each bond (symmetric)                        */
+    const double *K_neel;     /* [6n] Neel surface tensors or NULL                     */
+    const double *S0;         /* [3n] initial spins or NULL (+z); normalised on copy
+                                 unless already of unit length within 1e-6 (FP32-mixed)
+                                 or 1e-14 (FP64), so stored states round-trip bitwise */
+    double alpha;             /* Gilbert damping lambda, >= 0                          */
+    double dt;                /* time step, s, > 0                                     */
+    double gamma;             /* gyromagnetic ratio 1/(T s); 0 selects 1.76e11         */
+    double H_app[3];          /* initial applied field, T                              */
+    double T;                 /* initial temperature, K, >= 0                          */
+    uint64_t seed;            /* Philox key                                            */
+    uint32_t sys_id;          /* third Philox counter word of this system              */
+    ss_precision precision;   /* must be equal for all systems of a batch              */
+    uint32_t flags;           /* SS_FLAG_*                                             */
+} ss_params;
+
+/* Execution modes of llg_heun_step (spin_system_set_exec). */
+typedef enum {
+    SS_EXEC_AUTO = 0,      /* graphs for long runs, direct launches for short ones  */
+    SS_EXEC_KERNELS = 1,   /* one predictor and one corrector launch per step       */
+    SS_EXEC_GRAPH = 2,     /* CUDA graphs of captured step launches                 */
+    SS_EXEC_PERSISTENT = 3 /* one cooperative launch runs many steps, with a bounded
+                              grid barrier between the Heun passes                  */
+} ss_exec;
+
+typedef struct {
+    int64_t n;            /* total spins                                              */
+    int64_t nnz;          /* total neighbour entries                                  */
+    int32_t num_systems;  /* systems in the handle (1 unless batched)                 */
+    int32_t num_materials;/* distinct (system, mu_s, k_u, axis, Neel) combinations    */
+    int32_t precision;    /* ss_precision                                             */
+    int32_t exec;         /* ss_exec currently selected                               */
+    int32_t block;        /* threads per block of the step kernels                    */
+    int32_t tile;         /* spins per tile (one tile never spans two systems)        */
+    int64_t num_tiles;
+    int64_t step;         /* index of the next step                                   */
+    int64_t record_capacity; /* steps kept in the per-step record ring               */
+    int64_t device_bytes; /* device memory held by the handle                         */
+} ss_info;
+
+/* Create one system.  Validates and copies every array (SS_ERR_INVALID_ARG on bad
+ * input: n out of range, non-monotone row_ptr, column out of range, self bond,
+ * non-positive mu_s or dt, negative alpha or T, non-finite values, or an asymmetric
+ * list when SS_FLAG_CHECK_SYMMETRY is set). */
+ss_status spin_system_create(const ss_params *p, ss_system **out);
+
+/* Create one handle holding `count` independent systems (statistical parallelism,
+ * Appendix C): each system keeps its own neighbour list, moments, anisotropy, field,
+ * temperature, seed and system id, and is advanced exactly as if it were alone.  All
+ * systems share one step counter and one precision. */
+ss_status spin_batch_create(const ss_params *systems, int32_t count, ss_system **out);
+
+/* Release all device and host memory of the handle (NULL is accepted). */
+ss_status spin_system_destroy(ss_system *h);
+
+/* Issue all further work of the handle on this cudaStream_t (NULL = the library's own
+ * stream).  The handle synchronises its previous stream first. */
+ss_status spin_system_set_stream(ss_system *h, void *cuda_stream);
+
+/* Applied field (T) of system `sys`, or of every system when sys < 0. */
+ss_status set_field(ss_system *h, int32_t sys, const double H_app[3]);
+
+/* Temperature (K) of every system; removes any temperature schedule. */
+ss_status set_temperature(ss_system *h, double T);
+
+/* Temperatures of systems 0..count-1 (count = number of systems). */
+ss_status set_temperature_batch(ss_system *h, const double *T, int32_t count);
+
+/* Temperature schedule shared by all systems: step k uses T_per_step[k - step0] for
+ * step0 <= k < step0 + nsteps, T_per_step[0] before and T_per_step[nsteps-1] after.
+ * The temperature of a step is taken at its start, t_n = n dt. */
+ss_status set_temperature_schedule(ss_system *h, const double *T_per_step, int64_t nsteps, int64_t step0);
+
+/* Advance every system by n >= 0 Heun steps (asynchronous).  Each step records the
+ * moment and energy of the state at its start into the per-step record ring. */
+ss_status llg_heun_step(ss_system *h, int64_t n);
+
+/* Copy all spins (concatenated over systems) to out3n [3n], AoS, FP64 (synchronous). */
+ss_status get_spins(ss_system *h, double *out3n);
+
+/* Device pointers of the x, y, z spin arrays (SoA, float or double as the precision). */
+ss_status get_spins_device(ss_system *h, const void **sx, const void **sy, const void **sz);
+
+/* Magnetisation of the current state of system `sys`: out = (mx, my, mz, |m|) with
+ * m = sum_i mu_s,i S_i / sum_i mu_s,i (FP64 sums; synchronous). */
+ss_status get_magnetisation(ss_system *h, int32_t sys, double out[4]);
+
+/* Energy of the current state of system `sys` (J, FP64 sums, thermal field excluded):
+ * out = (total, exchange, anisotropy incl. Neel, applied-field). */
+ss_status get_energy(ss_system *h, int32_t sys, double out[4]);
+
+/* Per-step record of steps first_step .. first_step+count-1 (all still in the ring):
+ * out[(k * num_systems + s) * 8 + c] with c = (sum mu Sx, sum mu Sy, sum mu Sz,
+ * sum mu, E_exchange, E_anisotropy, E_applied, E_total) of the state at the start of
+ * step first_step+k.  Synchronous. */
+ss_status get_record(ss_system *h, int64_t first_step, int64_t count, double *out);
+
+/* Overwrite all spins from in3n [3n] AoS (normalised on copy as S0 is). */
+ss_status set_spins(ss_system *h, const double *in3n);
+
+/* Set the index of the next step (selects the Philox counter and schedule entry). */
+ss_status set_step(ss_system *h, int64_t step);
+ss_status get_step(ss_system *h, int64_t *step);
+
+/* Select how llg_heun_step launches its work (see ss_exec). */
+ss_status spin_system_set_exec(ss_system *h, ss_exec mode);
+
+/* Threads per block (64..1024, multiple of 32) and spins per tile (a multiple of the
+ * block size, at most 16 blocks' worth) of the step kernels; rebuilds the tile list. */
+ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
+
+/* Time the candidate (exec, block, tile) choices on this handle over `trial_steps`
+ * steps each, keep the fastest, and write it to *out_info.  The spins and the step
+ * counter are restored afterwards, so the trajectory is unchanged. */
+ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_info);
+
+ss_status spin_system_info(ss_system *h, ss_info *out);
+
+/* Advance `nsteps` steps with one predictor and one corrector launch each, timing every
+ * launch with CUDA events on the handle's stream.  out_ms receives the mean duration of
+ * (predictor, corrector) launches and the mean wall time of one step, in milliseconds.
+ * The steps are real steps: the state and the step counter advance. */
+ss_status spin_system_time_kernels(ss_system *h, int32_t nsteps, double out_ms[3]);
+
+/* Test hook for the bounded grid barrier: when nonzero, the next persistent launches
+ * wait for `extra` blocks that do not exist and give up after `timeout_ns`; the step then
+ * fails with SS_ERR_TIMEOUT and the handle stays usable. */
+ss_status spin_system_set_barrier_test(ss_system *h, int32_t extra, int64_t timeout_ns);
+
+/* Wait for the handle's queued work and report any device-side failure (non-finite
+ * spin, barrier timeout) raised since the last check; the flag is then cleared. */
+ss_status spin_system_sync(ss_system *h);
+
+/* Diagnostics (synchronous, default device, no handle).  ss_debug_philox writes the
+ * Philox4x32-10 blocks of counters (ctr0[0]+k, ctr0[1], ctr0[2], ctr0[3]), k < count,
+ * to out[4*count].  ss_debug_gaussians writes the thermal Gaussian triples of spins
+ * 0..n-1 at one (seed, system id, step) to out[3n]; mode 0 uses the step kernels'
+ * table-driven FP64 transform, mode 1 CUDA's own log/sqrt/sincospi. */
+ss_status ss_debug_philox(const uint32_t ctr0[4], const uint32_t key[2], int64_t count, uint32_t *out);
+ss_status ss_debug_gaussians(uint64_t seed, uint32_t sys_id, uint32_t step, int64_t n, int32_t mode, double *out);
+
+/* Human-readable message of the last failure on this handle ("" if none). */
+const char *ss_last_error(ss_system *h);
+const char *ss_status_string(ss_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPINSYS_H */

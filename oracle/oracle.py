@@ -55,6 +55,7 @@ class _CSys(ctypes.Structure):
         ("H_app", ctypes.c_double * 3),
         ("seed", ctypes.c_uint64),
         ("sys", ctypes.c_uint32),
+        ("ids", ctypes.c_void_p),
     ]
 
 
@@ -102,6 +103,7 @@ class OracleSystem:
     H_app: tuple = (0.0, 0.0, 0.0)
     seed: int = 1
     sys_id: int = 0
+    ids: np.ndarray | None = None
     _keep: list = field(default_factory=list, repr=False)
 
     def __post_init__(self):
@@ -115,6 +117,8 @@ class OracleSystem:
             np.broadcast_to(np.asarray(self.easy_axis, dtype=np.float64), (n, 3)))
         if self.K_neel is not None:
             self.K_neel = np.ascontiguousarray(self.K_neel, dtype=np.float64).reshape(n, 6)
+        if self.ids is not None:
+            self.ids = np.ascontiguousarray(self.ids, dtype=np.uint32).reshape(n)
 
     @property
     def n(self) -> int:
@@ -137,6 +141,7 @@ class OracleSystem:
             c.H_app[k] = float(self.H_app[k])
         c.seed = int(self.seed) & 0xFFFFFFFFFFFFFFFF
         c.sys = int(self.sys_id) & 0xFFFFFFFF
+        c.ids = _ptr(self.ids)
         return c
 
 

@@ -76,6 +76,8 @@ typedef struct {
     double H_app[3];          /* applied field, T                                  */
     uint64_t seed;            /* Philox key                                        */
     uint32_t sys;             /* system id (third counter word)                    */
+    const uint32_t *ids;      /* [n] Philox spin word of each site, or NULL (= i); lets a
+                                 test run a cut-out neighbourhood of a large system     */
 } orc_system;
 
 static int g_threads = 1;
@@ -284,7 +286,7 @@ int orc_heun_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, 
 #pragma omp parallel for schedule(static) num_threads(g_threads)
         for (int64_t i = 0; i < n; ++i) {
             double g[3];
-            orc_thermal_gaussians(s->seed, s->sys, (uint32_t)i, step, g);
+            orc_thermal_gaussians(s->seed, s->sys, s->ids ? s->ids[i] : (uint32_t)i, step, g);
             double sigma = sqrt(2.0 * lambda * ORC_KB * Tn / (gamma * s->mu_s[i] * s->dt));
             Hth[3 * i + 0] = sigma * g[0];
             Hth[3 * i + 1] = sigma * g[1];

@@ -1,0 +1,1187 @@
+// Host implementation of the C ABI declared in include/spinsys.h.
+//
+// A handle owns the device image of one or more spin systems (concatenated), the working
+// buffers of the Heun step, a per-step record ring and the launch state (stream, tile
+// list, captured graph).  Everything that touches spins runs in the CUDA kernels of
+// ss_kernels_f32.cu / ss_kernels_f64.cu; this file validates, converts and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/spinsys.h"
+#include "ss_internal.h"
+
+using namespace ss;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Host-side description of one system after validation.
+struct HostSys {
+    const ss_params *p;
+    int64_t offset;
+    int64_t nnz_offset;
+};
+
+// Material key: compared bitwise.
+struct MatKey {
+    int32_t sys;
+    int32_t has_neel;
+    double v[11];  // mu, ku, e[3], K[6]
+    bool operator==(const MatKey &o) const {
+        return sys == o.sys && has_neel == o.has_neel && std::memcmp(v, o.v, sizeof(v)) == 0;
+    }
+};
+
+struct MatKeyHash {
+    size_t operator()(const MatKey &k) const {
+        uint64_t h = 1469598103934665603ull ^ (uint64_t)(uint32_t)k.sys;
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(k.v);
+        for (size_t i = 0; i < sizeof(k.v); ++i) h = (h ^ b[i]) * 1099511628211ull;
+        return (size_t)h;
+    }
+};
+
+}  // namespace
+
+struct ss_system {
+    int precision = SS_FP64;
+    int64_t n = 0, nnz = 0;
+    int32_t nsys = 0, nmat = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    int device = 0, sm_count = 0;
+    int block = 256, tile = 256;
+    int64_t ntiles = 0;
+    int exec = SS_EXEC_AUTO;
+    int64_t step = 0;
+    bool bad = false;
+    std::string err;
+    std::vector<DevBuf> bufs;
+    size_t device_bytes = 0;
+
+    // device arrays
+    int32_t *row_ptr = nullptr, *col = nullptr, *mat = nullptr, *sys_tiles = nullptr;
+    void *J = nullptr, *mats = nullptr;
+    void *state[12] = {};  // sx sy sz px py pz qx qy qz hx hy hz
+    SysDesc *sys = nullptr;
+    TileDesc *tiles = nullptr;
+    double *partials = nullptr, *rec = nullptr, *cur = nullptr, *sched = nullptr;
+    int64_t rec_cap = 0, sched_len = 0, sched_step0 = 0, sched_cap = 0;
+    unsigned long long *ctl = nullptr;  // [0] step, [1] err|ticket, [2] barrier count|gen
+    double2 *tab = nullptr;             // log | ln2 | trig
+
+    std::vector<SysDesc> hsys;
+    std::vector<int64_t> sys_offset, sys_n;
+
+    // launch state
+    int nfin = 1;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    bool graph_failed = false;
+    unsigned int bar_extra = 0;
+    long long bar_timeout_ns = 2000000000ll;
+    long long persist_chunk = 4096;
+};
+
+namespace {
+
+ss_status fail(ss_system *h, ss_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) {
+        h->err = buf;
+    } else {
+        g_create_error = buf;
+    }
+    return s;
+}
+
+ss_status cuda_fail(ss_system *h, cudaError_t e, const char *what) {
+    if (h) h->bad = true;
+    return fail(h, e == cudaErrorMemoryAllocation ? SS_ERR_OOM : SS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SS_CUDA(h, call)                                      \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+cudaError_t dalloc(ss_system *h, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return e;
+    h->bufs.push_back({*p, bytes});
+    h->device_bytes += bytes;
+    return cudaSuccess;
+}
+
+void dfree(ss_system *h, void *p) {
+    for (size_t i = 0; i < h->bufs.size(); ++i) {
+        if (h->bufs[i].p == p) {
+            cudaFree(p);
+            h->device_bytes -= h->bufs[i].bytes;
+            h->bufs.erase(h->bufs.begin() + (long)i);
+            return;
+        }
+    }
+}
+
+size_t real_size(const ss_system *h) { return h->precision == SS_FP32_MIXED ? 4 : 8; }
+
+// Unit vector of v.  A vector already of unit length within `tol` is kept as given, so
+// that spins read with get_spins and written back with set_spins round-trip bitwise.
+void unit_in(const double *v, double out[3], double tol) {
+    const double len = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (std::fabs(len - 1.0) <= tol) {
+        out[0] = v[0];
+        out[1] = v[1];
+        out[2] = v[2];
+    } else {
+        out[0] = v[0] / len;
+        out[1] = v[1] / len;
+        out[2] = v[2] / len;
+    }
+}
+
+double unit_tol(int precision) { return precision == SS_FP32_MIXED ? 1e-6 : 1e-14; }
+
+bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+ss_status validate(const ss_params *p, int idx) {
+    if (!p) return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: params is NULL", idx);
+    if (p->n < 1 || p->n >= (int64_t(1) << 31))
+        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: n = %lld out of range [1, 2^31)", idx, (long long)p->n);
+    if (!p->row_ptr || !p->mu_s || !p->k_u)
+        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: row_ptr, mu_s and k_u are required", idx);
+    if (p->precision != SS_FP64 && p->precision != SS_FP32_MIXED)
+        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: unknown precision %d", idx, (int)p->precision);
+    const int64_t n = p->n;
+    if (p->row_ptr[0] != 0) return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: row_ptr[0] != 0", idx);
+    for (int64_t i = 0; i < n; ++i)
+        if (p->row_ptr[i + 1] < p->row_ptr[i])
+            return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: row_ptr decreases at row %lld", idx, (long long)i);
+    const int64_t nnz = p->row_ptr[n];
+    if (nnz >= (int64_t(1) << 31)) return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: nnz >= 2^31", idx);
+    if (nnz > 0 && (!p->col || !p->J))
+        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: col and J are required when nnz > 0", idx);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) {
+            const int32_t j = p->col[k];
+            if (j < 0 || j >= n)
+                return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: col[%lld] = %d out of range", idx, (long long)k, j);
+            if (j == i) return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: self bond at row %lld", idx, (long long)i);
+            if (!std::isfinite(p->J[k]))
+                return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: J[%lld] not finite", idx, (long long)k);
+        }
+        if (!(p->mu_s[i] > 0.0) || !std::isfinite(p->mu_s[i]))
+            return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: mu_s[%lld] must be finite and > 0", idx, (long long)i);
+        if (!std::isfinite(p->k_u[i]))
+            return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: k_u[%lld] not finite", idx, (long long)i);
+        if (p->easy_axis) {
+            const double *e = p->easy_axis + 3 * i;
+            if (!finite3(e) || e[0] * e[0] + e[1] * e[1] + e[2] * e[2] == 0.0)
+                return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: easy_axis[%lld] invalid", idx, (long long)i);
+        }
+        if (p->K_neel)
+            for (int c = 0; c < 6; ++c)
+                if (!std::isfinite(p->K_neel[6 * i + c]))
+                    return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: K_neel[%lld] not finite", idx, (long long)i);
+        if (p->S0 && !(p->flags & SS_FLAG_INIT_RANDOM)) {
+            const double *s = p->S0 + 3 * i;
+            if (!finite3(s) || s[0] * s[0] + s[1] * s[1] + s[2] * s[2] == 0.0)
+                return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: S0[%lld] invalid", idx, (long long)i);
+        }
+        if (p->pos && !finite3(p->pos + 3 * i))
+            return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: pos[%lld] not finite", idx, (long long)i);
+    }
+    if (!(p->alpha >= 0.0) || !std::isfinite(p->alpha))
+        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: alpha must be finite and >= 0", idx);
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt))
+        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: dt must be finite and > 0", idx);
+    if (!(p->gamma >= 0.0) || !std::isfinite(p->gamma))
+        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: gamma must be finite and >= 0", idx);
+    if (!(p->T >= 0.0) || !std::isfinite(p->T))
+        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: T must be finite and >= 0", idx);
+    if (!finite3(p->H_app)) return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: H_app not finite", idx);
+    if (p->flags & SS_FLAG_CHECK_SYMMETRY) {
+        std::unordered_map<uint64_t, double> bonds;
+        bonds.reserve((size_t)nnz);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k)
+                bonds[((uint64_t)i << 32) | (uint32_t)p->col[k]] += p->J[k];
+        for (const auto &b : bonds) {
+            const uint64_t rev = ((b.first & 0xffffffffull) << 32) | (b.first >> 32);
+            auto it = bonds.find(rev);
+            if (it == bonds.end() || it->second != b.second)
+                return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: neighbour list not symmetric at (%llu, %llu)",
+                            idx, (unsigned long long)(b.first >> 32), (unsigned long long)(b.first & 0xffffffffull));
+        }
+    }
+    return SS_OK;
+}
+
+// Function tables of the table-driven FP64 Box-Muller transform, evaluated in long double.
+void build_tables(std::vector<double2> &t) {
+    t.resize(kLogTab + kLn2Tab + kTrigTab);
+    for (int i = 0; i < kLogTab; ++i) {
+        const long double c = (long double)(192 + i) / 256.0L;
+        const double inv = (double)(1.0L / c);
+        t[i] = make_double2(inv, (double)(-2.0L * logl((long double)inv)));
+    }
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    for (int i = 0; i < kLn2Tab; ++i) {
+        const long double v = 2.0L * (long double)i * ln2;
+        const double hi = (double)v;
+        t[kLogTab + i] = make_double2(hi, (double)(v - (long double)hi));
+    }
+    const long double twopi = 6.283185307179586476925286766559005768L;
+    for (int j = 0; j < kTrigTab; ++j) {
+        const long double a = twopi * (long double)j / (long double)kTrigTab;
+        t[kLogTab + kLn2Tab + j] = make_double2((double)sinl(a), (double)cosl(a));
+    }
+}
+
+template <typename R>
+KArgs<R> make_args(const ss_system *h) {
+    KArgs<R> a{};
+    a.n = h->n;
+    a.row_ptr = h->row_ptr;
+    a.col = h->col;
+    a.J = static_cast<const R *>(h->J);
+    a.mat = h->mat;
+    a.mats = static_cast<const MatDesc<R> *>(h->mats);
+    a.sys = h->sys;
+    a.tiles = h->tiles;
+    a.ntiles = h->ntiles;
+    a.sys_tiles = h->sys_tiles;
+    a.nsys = h->nsys;
+    R **s = reinterpret_cast<R **>(const_cast<void **>(h->state));
+    a.sx = s[0]; a.sy = s[1]; a.sz = s[2];
+    a.px = s[3]; a.py = s[4]; a.pz = s[5];
+    a.qx = s[6]; a.qy = s[7]; a.qz = s[8];
+    a.hx = s[9]; a.hy = s[10]; a.hz = s[11];
+    a.partials = h->partials;
+    a.rec = h->rec;
+    a.rec_cap = h->rec_cap;
+    a.cur = h->cur;
+    a.step = h->ctl;
+    a.sqrtT_sched = h->sched;
+    a.sched_len = h->sched_len;
+    a.sched_step0 = h->sched_step0;
+    a.err = reinterpret_cast<unsigned int *>(h->ctl + 1);
+    a.ticket = reinterpret_cast<unsigned int *>(h->ctl + 1) + 1;
+    a.bar_count = reinterpret_cast<unsigned int *>(h->ctl + 2);
+    a.bar_gen = reinterpret_cast<unsigned int *>(h->ctl + 2) + 1;
+    a.tab_log = h->tab;
+    a.tab_ln2 = h->tab + kLogTab;
+    a.tab_trig = h->tab + kLogTab + kLn2Tab;
+    a.bar_extra = h->bar_extra;
+    a.bar_timeout_ns = h->bar_timeout_ns;
+    return a;
+}
+
+void drop_graph(ss_system *h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_steps = 0;
+}
+
+int step_grid(const ss_system *h) {
+    const int per_sm = h->precision == SS_FP32_MIXED ? step_blocks_per_sm<float>(h->block)
+                                                     : step_blocks_per_sm<double>(h->block);
+    const int64_t g = (int64_t)h->sm_count * std::max(per_sm, 1);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(h->ntiles, g));
+}
+
+int corrector_grid(const ss_system *h) {
+    const int64_t g = (int64_t)h->sm_count * (2048 / h->block);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(h->ntiles, g));
+}
+
+int persistent_grid(const ss_system *h) {
+    const int per_sm = h->precision == SS_FP32_MIXED ? persistent_blocks_per_sm<float>(h->block)
+                                                     : persistent_blocks_per_sm<double>(h->block);
+    const int64_t g = (int64_t)h->sm_count * per_sm;
+    return (int)std::max<int64_t>(0, std::min<int64_t>(h->ntiles, g));
+}
+
+template <typename R>
+cudaError_t enqueue_steps_kernels(ss_system *h, int64_t n) {
+    const KArgs<R> a = make_args<R>(h);
+    const int gp = step_grid(h), gc = corrector_grid(h);
+    for (int64_t k = 0; k < n; ++k) {
+        cudaError_t e = launch_predictor<R>(a, h->block, gp, h->stream);
+        if (e != cudaSuccess) return e;
+        e = launch_corrector<R>(a, h->block, gc, h->nfin, h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t enqueue_persistent(ss_system *h, int64_t n) {
+    const KArgs<R> a = make_args<R>(h);
+    const int grid = persistent_grid(h);
+    if (grid < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const int nfin = std::min(h->nsys, grid);
+    while (n > 0) {
+        const long long k = std::min<long long>(n, h->persist_chunk);
+        cudaError_t e = cudaMemsetAsync(h->ctl + 2, 0, sizeof(unsigned long long), h->stream);
+        if (e != cudaSuccess) return e;
+        e = launch_persistent<R>(a, h->block, grid, nfin, k, h->stream);
+        if (e != cudaSuccess) return e;
+        n -= k;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_kernels(ss_system *h, int64_t n) {
+    return h->precision == SS_FP32_MIXED ? enqueue_steps_kernels<float>(h, n) : enqueue_steps_kernels<double>(h, n);
+}
+
+cudaError_t enqueue_persist(ss_system *h, int64_t n) {
+    return h->precision == SS_FP32_MIXED ? enqueue_persistent<float>(h, n) : enqueue_persistent<double>(h, n);
+}
+
+int graph_len(const ss_system *h) {
+    // enough steps per graph that the launch cost is amortised, few enough that capture
+    // stays cheap
+    return h->n >= (int64_t(1) << 22) ? 8 : 64;
+}
+
+cudaError_t ensure_graph(ss_system *h) {
+    if (h->graph) return cudaSuccess;
+    const int g = graph_len(h);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t ek = enqueue_kernels(h, g);
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (ek != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return ek;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return e;
+    }
+    h->graph_steps = g;
+    return cudaSuccess;
+}
+
+ss_status check_device_flags(ss_system *h) {
+    unsigned long long ctl[3];
+    SS_CUDA(h, cudaMemcpyAsync(ctl, h->ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->stream));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    const unsigned int err = (unsigned int)(ctl[1] & 0xffffffffull);
+    h->step = (int64_t)ctl[0];
+    if (err) {
+        const unsigned long long zero[3] = {ctl[0], 0ull, 0ull};
+        SS_CUDA(h, cudaMemcpyAsync(h->ctl, zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream));
+        SS_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (err & kErrTimeout)
+            return fail(h, SS_ERR_TIMEOUT, "grid barrier of the persistent kernel timed out; step counter at %lld",
+                        (long long)h->step);
+        return fail(h, SS_ERR_NONFINITE, "a spin became non-finite (NaN/inf or zero length)");
+    }
+    return SS_OK;
+}
+
+ss_status build_tiles(ss_system *h) {
+    std::vector<TileDesc> tiles;
+    std::vector<int32_t> st(h->nsys + 1);
+    for (int s = 0; s < h->nsys; ++s) {
+        st[s] = (int32_t)tiles.size();
+        for (int64_t b = 0; b < h->sys_n[s]; b += h->tile) {
+            TileDesc t;
+            t.start = h->sys_offset[s] + b;
+            t.count = (int32_t)std::min<int64_t>(h->tile, h->sys_n[s] - b);
+            t.sys = s;
+            tiles.push_back(t);
+        }
+    }
+    st[h->nsys] = (int32_t)tiles.size();
+    if (h->tiles) dfree(h, h->tiles);
+    if (h->sys_tiles) dfree(h, h->sys_tiles);
+    if (h->partials) dfree(h, h->partials);
+    h->tiles = nullptr;
+    h->sys_tiles = nullptr;
+    h->partials = nullptr;
+    h->ntiles = (int64_t)tiles.size();
+    SS_CUDA(h, dalloc(h, (void **)&h->tiles, tiles.size() * sizeof(TileDesc)));
+    SS_CUDA(h, dalloc(h, (void **)&h->sys_tiles, st.size() * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, (void **)&h->partials, tiles.size() * kPartComps * sizeof(double)));
+    SS_CUDA(h, cudaMemcpyAsync(h->tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice,
+                               h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->sys_tiles, st.data(), st.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               h->stream));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->nfin = std::max(1, std::min(h->nsys, 64));
+    drop_graph(h);
+    return SS_OK;
+}
+
+template <typename R>
+void fill_material(MatDesc<R> &m, const MatKey &k, const ss_params *p) {
+    const double mu = k.v[0], ku = k.v[1];
+    const double gamma = p->gamma > 0.0 ? p->gamma : kGammaDefault;
+    const double lam = p->alpha;
+    std::memset(&m, 0, sizeof(m));
+    m.inv_mu = (R)(1.0 / mu);
+    m.ani = (R)(2.0 * ku / mu);
+    for (int c = 0; c < 3; ++c) m.e[c] = (R)k.v[2 + c];
+    for (int c = 0; c < 6; ++c) {
+        m.kf[c] = (R)(2.0 / mu * k.v[5 + c]);
+        m.K[c] = (R)k.v[5 + c];
+    }
+    m.gp = (R)(gamma / (1.0 + lam * lam));
+    m.lambda = (R)lam;
+    m.dt = (R)p->dt;
+    m.sig = (R)std::sqrt(2.0 * lam * kBoltzmann / (gamma * mu * p->dt));
+    m.mu = (R)mu;
+    m.ku = (R)ku;
+    m.sys = k.sys;
+    m.has_neel = k.has_neel;
+}
+
+template <typename R>
+ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
+    const int64_t n = h->n, nnz = h->nnz;
+    // CSR with global indices
+    std::vector<int32_t> rp((size_t)n + 1), col((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<R> J((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<int32_t> mat((size_t)n);
+    std::vector<MatDesc<R>> mats;
+    std::unordered_map<MatKey, int32_t, MatKeyHash> mat_id;
+    for (int s = 0; s < h->nsys; ++s) {
+        const ss_params *p = hs[s].p;
+        const int64_t off = hs[s].offset, noff = hs[s].nnz_offset;
+        for (int64_t i = 0; i < p->n; ++i) rp[off + i] = (int32_t)(noff + p->row_ptr[i]);
+        for (int64_t k = 0; k < p->row_ptr[p->n]; ++k) {
+            col[noff + k] = (int32_t)(off + p->col[k]);
+            J[noff + k] = (R)p->J[k];
+        }
+        MatKey last{};
+        int32_t last_id = -1;
+        for (int64_t i = 0; i < p->n; ++i) {
+            MatKey key{};
+            key.sys = s;
+            key.v[0] = p->mu_s[i];
+            key.v[1] = p->k_u[i];
+            double e[3] = {0.0, 0.0, 1.0};
+            if (p->easy_axis) {
+                const double *a = p->easy_axis + 3 * i;
+                const double len = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+                e[0] = a[0] / len;
+                e[1] = a[1] / len;
+                e[2] = a[2] / len;
+            }
+            for (int c = 0; c < 3; ++c) key.v[2 + c] = e[c];
+            if (p->K_neel) {
+                bool any = false;
+                for (int c = 0; c < 6; ++c) {
+                    key.v[5 + c] = p->K_neel[6 * i + c];
+                    any = any || key.v[5 + c] != 0.0;
+                }
+                key.has_neel = any ? 1 : 0;
+            }
+            int32_t id;
+            if (last_id >= 0 && key == last) {
+                id = last_id;
+            } else {
+                auto it = mat_id.find(key);
+                if (it == mat_id.end()) {
+                    id = (int32_t)mats.size();
+                    mat_id.emplace(key, id);
+                    MatDesc<R> m;
+                    fill_material(m, key, p);
+                    mats.push_back(m);
+                } else {
+                    id = it->second;
+                }
+                last = key;
+                last_id = id;
+            }
+            mat[off + i] = id;
+        }
+    }
+    rp[n] = (int32_t)nnz;
+    h->nmat = (int32_t)mats.size();
+    const size_t rs = sizeof(R);
+    SS_CUDA(h, dalloc(h, (void **)&h->row_ptr, rp.size() * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, (void **)&h->col, col.size() * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, &h->J, J.size() * rs));
+    SS_CUDA(h, dalloc(h, (void **)&h->mat, mat.size() * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, &h->mats, mats.size() * sizeof(MatDesc<R>)));
+    SS_CUDA(h, cudaMemcpyAsync(h->row_ptr, rp.data(), rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->col, col.data(), col.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->J, J.data(), J.size() * rs, cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->mat, mat.data(), mat.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->mats, mats.data(), mats.size() * sizeof(MatDesc<R>), cudaMemcpyHostToDevice,
+                               h->stream));
+    for (int b = 0; b < 12; ++b) SS_CUDA(h, dalloc(h, &h->state[b], (size_t)n * rs));
+    // initial spins
+    std::vector<R> s0((size_t)n), s1((size_t)n), s2((size_t)n);
+    for (int s = 0; s < h->nsys; ++s) {
+        const ss_params *p = hs[s].p;
+        const int64_t off = hs[s].offset;
+        for (int64_t i = 0; i < p->n; ++i) {
+            double v[3] = {0.0, 0.0, 1.0};
+            if (p->S0 && !(p->flags & SS_FLAG_INIT_RANDOM)) unit_in(p->S0 + 3 * i, v, unit_tol(h->precision));
+            s0[off + i] = (R)v[0];
+            s1[off + i] = (R)v[1];
+            s2[off + i] = (R)v[2];
+        }
+    }
+    SS_CUDA(h, cudaMemcpyAsync(h->state[0], s0.data(), (size_t)n * rs, cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->state[1], s1.data(), (size_t)n * rs, cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->state[2], s2.data(), (size_t)n * rs, cudaMemcpyHostToDevice, h->stream));
+    for (int b = 3; b < 12; ++b) SS_CUDA(h, cudaMemsetAsync(h->state[b], 0, (size_t)n * rs, h->stream));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SS_OK;
+}
+
+template <typename R>
+ss_status init_random(ss_system *h, const std::vector<HostSys> &hs) {
+    // random start for the systems that asked for it: draw for all, then restore the others
+    bool any = false;
+    for (const auto &x : hs) any = any || (x.p->flags & SS_FLAG_INIT_RANDOM);
+    if (!any) return SS_OK;
+    const size_t rs = sizeof(R);
+    const int64_t n = h->n;
+    std::vector<R> keep(3 * (size_t)n);
+    for (int c = 0; c < 3; ++c)
+        SS_CUDA(h, cudaMemcpyAsync(keep.data() + c * n, h->state[c], (size_t)n * rs, cudaMemcpyDeviceToHost, h->stream));
+    SS_CUDA(h, launch_init_sphere<R>(make_args<R>(h), h->stream));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (const auto &x : hs) {
+        if (x.p->flags & SS_FLAG_INIT_RANDOM) continue;
+        for (int c = 0; c < 3; ++c)
+            SS_CUDA(h, cudaMemcpyAsync((char *)h->state[c] + x.offset * rs, keep.data() + c * n + x.offset,
+                                       (size_t)x.p->n * rs, cudaMemcpyHostToDevice, h->stream));
+    }
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SS_OK;
+}
+
+ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) {
+    if (!out) return fail(nullptr, SS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!systems || count < 1) return fail(nullptr, SS_ERR_INVALID_ARG, "need at least one system");
+    std::vector<HostSys> hs((size_t)count);
+    int64_t n = 0, nnz = 0;
+    for (int s = 0; s < count; ++s) {
+        ss_status st = validate(systems + s, s);
+        if (st != SS_OK) return st;
+        if (systems[s].precision != systems[0].precision)
+            return fail(nullptr, SS_ERR_INVALID_ARG, "all systems of a batch must share one precision");
+        hs[s].p = systems + s;
+        hs[s].offset = n;
+        hs[s].nnz_offset = nnz;
+        n += systems[s].n;
+        nnz += systems[s].row_ptr[systems[s].n];
+    }
+    if (n >= (int64_t(1) << 31) || nnz >= (int64_t(1) << 31))
+        return fail(nullptr, SS_ERR_INVALID_ARG, "total spins and total neighbour entries must be < 2^31");
+
+    ss_system *h = new (std::nothrow) ss_system();
+    if (!h) return fail(nullptr, SS_ERR_OOM, "host allocation failed");
+    h->precision = systems[0].precision;
+    h->n = n;
+    h->nnz = nnz;
+    h->nsys = count;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        ss_status st = fail(nullptr, e == cudaErrorNoDevice ? SS_ERR_UNSUPPORTED : SS_ERR_CUDA, "CUDA: %s",
+                            cudaGetErrorString(e));
+        delete h;
+        return st;
+    }
+    h->stream = h->own_stream;
+    for (int s = 0; s < count; ++s) {
+        h->sys_offset.push_back(hs[s].offset);
+        h->sys_n.push_back(systems[s].n);
+    }
+    // system table
+    h->hsys.resize((size_t)count);
+    for (int s = 0; s < count; ++s) {
+        const ss_params *p = systems + s;
+        SysDesc &d = h->hsys[s];
+        std::memset(&d, 0, sizeof(d));
+        d.offset = hs[s].offset;
+        d.n = p->n;
+        d.key0 = (uint32_t)(p->seed & 0xffffffffull);
+        d.key1 = (uint32_t)(p->seed >> 32);
+        d.ctr2 = p->sys_id;
+        for (int c = 0; c < 3; ++c) d.H[c] = p->H_app[c];
+        d.sqrtT = std::sqrt(p->T);
+        double ms = 0.0;
+        for (int64_t i = 0; i < p->n; ++i) ms += p->mu_s[i];
+        d.msum = ms;
+    }
+    auto cleanup = [&](ss_status st) {
+        std::string msg = h->err;
+        spin_system_destroy(h);
+        g_create_error = msg;
+        return st;
+    };
+    ss_status st;
+    if ((e = dalloc(h, (void **)&h->sys, (size_t)count * sizeof(SysDesc))) != cudaSuccess)
+        return cleanup(cuda_fail(h, e, "cudaMalloc"));
+    if ((e = cudaMemcpyAsync(h->sys, h->hsys.data(), (size_t)count * sizeof(SysDesc), cudaMemcpyHostToDevice,
+                             h->stream)) != cudaSuccess)
+        return cleanup(cuda_fail(h, e, "cudaMemcpyAsync"));
+    // control words, tables, record ring, current measurement
+    if ((e = dalloc(h, (void **)&h->ctl, 4 * sizeof(unsigned long long))) != cudaSuccess)
+        return cleanup(cuda_fail(h, e, "cudaMalloc"));
+    if ((e = cudaMemsetAsync(h->ctl, 0, 4 * sizeof(unsigned long long), h->stream)) != cudaSuccess)
+        return cleanup(cuda_fail(h, e, "cudaMemsetAsync"));
+    std::vector<double2> tab;
+    build_tables(tab);
+    if ((e = dalloc(h, (void **)&h->tab, tab.size() * sizeof(double2))) != cudaSuccess)
+        return cleanup(cuda_fail(h, e, "cudaMalloc"));
+    if ((e = cudaMemcpyAsync(h->tab, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream)) !=
+        cudaSuccess)
+        return cleanup(cuda_fail(h, e, "cudaMemcpyAsync"));
+    h->rec_cap = std::max<int64_t>(16, std::min<int64_t>(4096, (int64_t(1) << 22) / ((int64_t)count * kRecComps)));
+    if ((e = dalloc(h, (void **)&h->rec, (size_t)h->rec_cap * count * kRecComps * sizeof(double))) != cudaSuccess)
+        return cleanup(cuda_fail(h, e, "cudaMalloc"));
+    if ((e = cudaMemsetAsync(h->rec, 0, (size_t)h->rec_cap * count * kRecComps * sizeof(double), h->stream)) !=
+        cudaSuccess)
+        return cleanup(cuda_fail(h, e, "cudaMemsetAsync"));
+    if ((e = dalloc(h, (void **)&h->cur, (size_t)count * kRecComps * sizeof(double))) != cudaSuccess)
+        return cleanup(cuda_fail(h, e, "cudaMalloc"));
+    st = h->precision == SS_FP32_MIXED ? upload_system<float>(h, hs) : upload_system<double>(h, hs);
+    if (st != SS_OK) return cleanup(st);
+    st = build_tiles(h);
+    if (st != SS_OK) return cleanup(st);
+    st = h->precision == SS_FP32_MIXED ? init_random<float>(h, hs) : init_random<double>(h, hs);
+    if (st != SS_OK) return cleanup(st);
+    *out = h;
+    return SS_OK;
+}
+
+ss_status usable(ss_system *h) {
+    if (!h) return fail(nullptr, SS_ERR_INVALID_ARG, "handle is NULL");
+    if (h->bad) return fail(h, SS_ERR_STATE, "handle unusable after an earlier CUDA error: %s", h->err.c_str());
+    return SS_OK;
+}
+
+template <typename R>
+ss_status measure(ss_system *h) {
+    const KArgs<R> a = make_args<R>(h);
+    SS_CUDA(h, launch_measure<R>(a, h->block, step_grid(h), h->stream));
+    SS_CUDA(h, launch_finalize(h->sys, h->sys_tiles, h->nsys, h->partials, h->cur, h->stream));
+    return SS_OK;
+}
+
+ss_status current_record(ss_system *h, int32_t sys, double rec[kRecComps]) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (sys < 0 || sys >= h->nsys) return fail(h, SS_ERR_INVALID_ARG, "system %d out of range", sys);
+    st = h->precision == SS_FP32_MIXED ? measure<float>(h) : measure<double>(h);
+    if (st != SS_OK) return st;
+    SS_CUDA(h, cudaMemcpyAsync(rec, h->cur + (int64_t)sys * kRecComps, kRecComps * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
+    return check_device_flags(h);
+}
+
+template <typename R>
+ss_status time_kernels_impl(ss_system *h, int32_t nsteps, double out_ms[3]) {
+    const KArgs<R> a = make_args<R>(h);
+    const int gp = step_grid(h), gc = corrector_grid(h);
+    std::vector<cudaEvent_t> ev(2 * (size_t)nsteps + 1);
+    for (auto &e : ev) SS_CUDA(h, cudaEventCreate(&e));
+    SS_CUDA(h, cudaEventRecord(ev[0], h->stream));
+    for (int32_t k = 0; k < nsteps; ++k) {
+        SS_CUDA(h, launch_predictor<R>(a, h->block, gp, h->stream));
+        SS_CUDA(h, cudaEventRecord(ev[2 * k + 1], h->stream));
+        SS_CUDA(h, launch_corrector<R>(a, h->block, gc, h->nfin, h->stream));
+        SS_CUDA(h, cudaEventRecord(ev[2 * k + 2], h->stream));
+    }
+    SS_CUDA(h, cudaEventSynchronize(ev.back()));
+    double tp = 0.0, tc = 0.0;
+    for (int32_t k = 0; k < nsteps; ++k) {
+        float a1 = 0.f, a2 = 0.f;
+        cudaEventElapsedTime(&a1, ev[2 * k], ev[2 * k + 1]);
+        cudaEventElapsedTime(&a2, ev[2 * k + 1], ev[2 * k + 2]);
+        tp += a1;
+        tc += a2;
+    }
+    float all = 0.f;
+    cudaEventElapsedTime(&all, ev[0], ev.back());
+    for (auto &e : ev) cudaEventDestroy(e);
+    h->step += nsteps;
+    out_ms[0] = tp / nsteps;
+    out_ms[1] = tc / nsteps;
+    out_ms[2] = all / nsteps;
+    return check_device_flags(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+ss_status spin_system_create(const ss_params *p, ss_system **out) { return create_impl(p, 1, out); }
+
+ss_status spin_batch_create(const ss_params *systems, int32_t count, ss_system **out) {
+    return create_impl(systems, count, out);
+}
+
+ss_status spin_system_destroy(ss_system *h) {
+    if (!h) return SS_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    for (auto &b : h->bufs) cudaFree(b.p);
+    h->bufs.clear();
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+    return SS_OK;
+}
+
+ss_status spin_system_set_stream(ss_system *h, void *cuda_stream) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->own_stream;
+    return SS_OK;
+}
+
+ss_status set_field(ss_system *h, int32_t sys, const double H_app[3]) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!H_app || !finite3(H_app)) return fail(h, SS_ERR_INVALID_ARG, "H_app must be 3 finite values");
+    if (sys >= h->nsys) return fail(h, SS_ERR_INVALID_ARG, "system %d out of range", sys);
+    for (int s = 0; s < h->nsys; ++s) {
+        if (sys >= 0 && s != sys) continue;
+        for (int c = 0; c < 3; ++c) h->hsys[s].H[c] = H_app[c];
+        SS_CUDA(h, cudaMemcpyAsync(&h->sys[s].H[0], &h->hsys[s].H[0], 3 * sizeof(double), cudaMemcpyHostToDevice,
+                                   h->stream));
+    }
+    return SS_OK;
+}
+
+static ss_status upload_sqrtT(ss_system *h) {
+    for (int s = 0; s < h->nsys; ++s)
+        SS_CUDA(h, cudaMemcpyAsync(&h->sys[s].sqrtT, &h->hsys[s].sqrtT, sizeof(double), cudaMemcpyHostToDevice,
+                                   h->stream));
+    return SS_OK;
+}
+
+static ss_status clear_schedule(ss_system *h) {
+    if (h->sched_len != 0) {
+        h->sched_len = 0;
+        drop_graph(h);
+    }
+    return SS_OK;
+}
+
+ss_status set_temperature(ss_system *h, double T) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!(T >= 0.0) || !std::isfinite(T)) return fail(h, SS_ERR_INVALID_ARG, "T must be finite and >= 0");
+    for (auto &d : h->hsys) d.sqrtT = std::sqrt(T);
+    clear_schedule(h);
+    return upload_sqrtT(h);
+}
+
+ss_status set_temperature_batch(ss_system *h, const double *T, int32_t count) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!T || count != h->nsys) return fail(h, SS_ERR_INVALID_ARG, "need one temperature per system (%d)", h->nsys);
+    for (int s = 0; s < count; ++s)
+        if (!(T[s] >= 0.0) || !std::isfinite(T[s])) return fail(h, SS_ERR_INVALID_ARG, "T[%d] invalid", s);
+    for (int s = 0; s < count; ++s) h->hsys[s].sqrtT = std::sqrt(T[s]);
+    clear_schedule(h);
+    return upload_sqrtT(h);
+}
+
+ss_status set_temperature_schedule(ss_system *h, const double *T_per_step, int64_t nsteps, int64_t step0) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!T_per_step || nsteps < 1) return fail(h, SS_ERR_INVALID_ARG, "schedule needs at least one entry");
+    std::vector<double> r((size_t)nsteps);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        if (!(T_per_step[k] >= 0.0) || !std::isfinite(T_per_step[k]))
+            return fail(h, SS_ERR_INVALID_ARG, "T_per_step[%lld] invalid", (long long)k);
+        r[k] = std::sqrt(T_per_step[k]);
+    }
+    if (nsteps > h->sched_cap) {
+        SS_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (h->sched) dfree(h, h->sched);
+        h->sched = nullptr;
+        h->sched_cap = 0;
+        SS_CUDA(h, dalloc(h, (void **)&h->sched, (size_t)nsteps * sizeof(double)));
+        h->sched_cap = nsteps;
+    }
+    SS_CUDA(h, cudaMemcpyAsync(h->sched, r.data(), (size_t)nsteps * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->sched_len != nsteps || h->sched_step0 != step0) drop_graph(h);
+    h->sched_len = nsteps;
+    h->sched_step0 = step0;
+    return SS_OK;
+}
+
+ss_status llg_heun_step(ss_system *h, int64_t n) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (n < 0) return fail(h, SS_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return SS_OK;
+    cudaError_t e = cudaSuccess;
+    int mode = h->exec;
+    if (mode == SS_EXEC_AUTO) mode = n >= graph_len(h) ? SS_EXEC_GRAPH : SS_EXEC_KERNELS;
+    if (mode == SS_EXEC_GRAPH && !h->graph_failed) {
+        e = ensure_graph(h);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->graph_failed = true;
+            mode = SS_EXEC_KERNELS;
+        }
+    } else if (mode == SS_EXEC_GRAPH) {
+        mode = SS_EXEC_KERNELS;
+    }
+    if (mode == SS_EXEC_GRAPH) {
+        int64_t left = n;
+        while (left >= h->graph_steps) {
+            e = cudaGraphLaunch(h->graph, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+            left -= h->graph_steps;
+        }
+        e = enqueue_kernels(h, left);
+    } else if (mode == SS_EXEC_PERSISTENT) {
+        e = enqueue_persist(h, n);
+        if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+            cudaGetLastError();
+            return fail(h, SS_ERR_UNSUPPORTED, "persistent launch not possible: %s", cudaGetErrorString(e));
+        }
+    } else {
+        e = enqueue_kernels(h, n);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+    h->step += n;
+    return SS_OK;
+}
+
+ss_status spin_system_sync(ss_system *h) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    return check_device_flags(h);
+}
+
+ss_status get_spins(ss_system *h, double *out3n) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!out3n) return fail(h, SS_ERR_INVALID_ARG, "out3n is NULL");
+    const int64_t n = h->n;
+    if (h->precision == SS_FP32_MIXED) {
+        std::vector<float> b(3 * (size_t)n);
+        for (int c = 0; c < 3; ++c)
+            SS_CUDA(h, cudaMemcpyAsync(b.data() + c * n, h->state[c], n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        st = check_device_flags(h);
+        for (int64_t i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) out3n[3 * i + c] = (double)b[c * n + i];
+    } else {
+        std::vector<double> b(3 * (size_t)n);
+        for (int c = 0; c < 3; ++c)
+            SS_CUDA(h, cudaMemcpyAsync(b.data() + c * n, h->state[c], n * sizeof(double), cudaMemcpyDeviceToHost,
+                                       h->stream));
+        st = check_device_flags(h);
+        for (int64_t i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) out3n[3 * i + c] = b[c * n + i];
+    }
+    return st;
+}
+
+ss_status get_spins_device(ss_system *h, const void **sx, const void **sy, const void **sz) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!sx || !sy || !sz) return fail(h, SS_ERR_INVALID_ARG, "NULL output pointer");
+    *sx = h->state[0];
+    *sy = h->state[1];
+    *sz = h->state[2];
+    return SS_OK;
+}
+
+ss_status get_magnetisation(ss_system *h, int32_t sys, double out[4]) {
+    if (!out) return fail(h, SS_ERR_INVALID_ARG, "out is NULL");
+    double r[kRecComps];
+    ss_status st = current_record(h, sys, r);
+    if (st != SS_OK) return st;
+    for (int c = 0; c < 3; ++c) out[c] = r[c] / r[3];
+    out[3] = std::sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+    return SS_OK;
+}
+
+ss_status get_energy(ss_system *h, int32_t sys, double out[4]) {
+    if (!out) return fail(h, SS_ERR_INVALID_ARG, "out is NULL");
+    double r[kRecComps];
+    ss_status st = current_record(h, sys, r);
+    if (st != SS_OK) return st;
+    out[0] = r[7];
+    out[1] = r[4];
+    out[2] = r[5];
+    out[3] = r[6];
+    return SS_OK;
+}
+
+ss_status get_record(ss_system *h, int64_t first_step, int64_t count, double *out) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (count < 0 || (count > 0 && !out)) return fail(h, SS_ERR_INVALID_ARG, "bad count or NULL out");
+    st = check_device_flags(h);
+    if (st != SS_OK) return st;
+    if (first_step < 0 || first_step + count > h->step || first_step < h->step - h->rec_cap)
+        return fail(h, SS_ERR_INVALID_ARG, "steps [%lld, %lld) not in the record ring [%lld, %lld)",
+                    (long long)first_step, (long long)(first_step + count),
+                    (long long)std::max<int64_t>(0, h->step - h->rec_cap), (long long)h->step);
+    const size_t per = (size_t)h->nsys * kRecComps;
+    int64_t k = 0;
+    while (k < count) {
+        const int64_t slot = (first_step + k) % h->rec_cap;
+        const int64_t run = std::min<int64_t>(count - k, h->rec_cap - slot);
+        SS_CUDA(h, cudaMemcpyAsync(out + k * per, h->rec + slot * per, (size_t)run * per * sizeof(double),
+                                   cudaMemcpyDeviceToHost, h->stream));
+        k += run;
+    }
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SS_OK;
+}
+
+ss_status set_spins(ss_system *h, const double *in3n) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!in3n) return fail(h, SS_ERR_INVALID_ARG, "in3n is NULL");
+    const int64_t n = h->n;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *v = in3n + 3 * i;
+        if (!finite3(v) || v[0] * v[0] + v[1] * v[1] + v[2] * v[2] == 0.0)
+            return fail(h, SS_ERR_INVALID_ARG, "spin %lld invalid", (long long)i);
+    }
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->precision == SS_FP32_MIXED) {
+        std::vector<float> b(3 * (size_t)n);
+        for (int64_t i = 0; i < n; ++i) {
+            double u[3];
+            unit_in(in3n + 3 * i, u, unit_tol(h->precision));
+            for (int c = 0; c < 3; ++c) b[c * n + i] = (float)u[c];
+        }
+        for (int c = 0; c < 3; ++c)
+            SS_CUDA(h, cudaMemcpyAsync(h->state[c], b.data() + c * n, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    } else {
+        std::vector<double> b(3 * (size_t)n);
+        for (int64_t i = 0; i < n; ++i) {
+            double u[3];
+            unit_in(in3n + 3 * i, u, unit_tol(h->precision));
+            for (int c = 0; c < 3; ++c) b[c * n + i] = u[c];
+        }
+        for (int c = 0; c < 3; ++c)
+            SS_CUDA(h, cudaMemcpyAsync(h->state[c], b.data() + c * n, n * sizeof(double), cudaMemcpyHostToDevice,
+                                       h->stream));
+        SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    return SS_OK;
+}
+
+ss_status set_step(ss_system *h, int64_t step) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (step < 0) return fail(h, SS_ERR_INVALID_ARG, "step must be >= 0");
+    const unsigned long long v = (unsigned long long)step;
+    SS_CUDA(h, cudaMemcpyAsync(h->ctl, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->step = step;
+    return SS_OK;
+}
+
+ss_status get_step(ss_system *h, int64_t *step) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!step) return fail(h, SS_ERR_INVALID_ARG, "step is NULL");
+    st = check_device_flags(h);
+    *step = h->step;
+    return st;
+}
+
+ss_status spin_system_set_exec(ss_system *h, ss_exec mode) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (mode < SS_EXEC_AUTO || mode > SS_EXEC_PERSISTENT) return fail(h, SS_ERR_INVALID_ARG, "unknown exec mode");
+    if (mode == SS_EXEC_PERSISTENT && persistent_grid(h) < 1)
+        return fail(h, SS_ERR_UNSUPPORTED, "persistent kernel cannot be made co-resident with block %d", h->block);
+    h->exec = mode;
+    return SS_OK;
+}
+
+ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (block != 128 && block != 256 && block != 512)
+        return fail(h, SS_ERR_INVALID_ARG, "block must be 128, 256 or 512");
+    if (tile < block || tile % block != 0 || tile > 16 * block)
+        return fail(h, SS_ERR_INVALID_ARG, "tile must be a multiple of block, at most 16 blocks");
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->block = block;
+    h->tile = tile;
+    return build_tiles(h);
+}
+
+ss_status spin_system_info(ss_system *h, ss_info *o) {
+    if (!h || !o) return fail(h, SS_ERR_INVALID_ARG, "NULL argument");
+    o->n = h->n;
+    o->nnz = h->nnz;
+    o->num_systems = h->nsys;
+    o->num_materials = h->nmat;
+    o->precision = h->precision;
+    o->exec = h->exec;
+    o->block = h->block;
+    o->tile = h->tile;
+    o->num_tiles = h->ntiles;
+    o->step = h->step;
+    o->record_capacity = h->rec_cap;
+    o->device_bytes = (int64_t)h->device_bytes;
+    return SS_OK;
+}
+
+ss_status spin_system_time_kernels(ss_system *h, int32_t nsteps, double out_ms[3]) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (nsteps < 1 || !out_ms) return fail(h, SS_ERR_INVALID_ARG, "nsteps >= 1 and out_ms needed");
+    return h->precision == SS_FP32_MIXED ? time_kernels_impl<float>(h, nsteps, out_ms)
+                                         : time_kernels_impl<double>(h, nsteps, out_ms);
+}
+
+ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_info) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (trial_steps < 1) return fail(h, SS_ERR_INVALID_ARG, "trial_steps must be >= 1");
+    st = check_device_flags(h);
+    if (st != SS_OK) return st;
+    const size_t rs = real_size(h);
+    const int64_t n = h->n;
+    const int64_t step0 = h->step;
+    void *save = nullptr;
+    SS_CUDA(h, dalloc(h, &save, 3 * (size_t)n * rs));
+    for (int c = 0; c < 3; ++c)
+        SS_CUDA(h, cudaMemcpyAsync((char *)save + c * n * rs, h->state[c], n * rs, cudaMemcpyDeviceToDevice, h->stream));
+    struct Cand { int exec, block, tile; };
+    std::vector<Cand> cands;
+    for (int b : {128, 256, 512})
+        for (int m : {1, 2, 4}) {
+            cands.push_back({SS_EXEC_GRAPH, b, b * m});
+            cands.push_back({SS_EXEC_PERSISTENT, b, b * m});
+        }
+    cudaEvent_t e0, e1;
+    SS_CUDA(h, cudaEventCreate(&e0));
+    SS_CUDA(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand bestc{h->exec, h->block, h->tile};
+    for (const Cand &c : cands) {
+        if (spin_system_set_launch(h, c.block, c.tile) != SS_OK) continue;
+        if (spin_system_set_exec(h, (ss_exec)c.exec) != SS_OK) continue;
+        if (llg_heun_step(h, std::min(trial_steps, 4)) != SS_OK) { h->bad = false; continue; }
+        cudaEventRecord(e0, h->stream);
+        if (llg_heun_step(h, trial_steps) != SS_OK) { h->bad = false; continue; }
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
+        if (check_device_flags(h) != SS_OK) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bestc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st = spin_system_set_launch(h, bestc.block, bestc.tile);
+    if (st == SS_OK) st = spin_system_set_exec(h, (ss_exec)bestc.exec);
+    for (int c = 0; c < 3; ++c)
+        SS_CUDA(h, cudaMemcpyAsync(h->state[c], (char *)save + c * n * rs, n * rs, cudaMemcpyDeviceToDevice, h->stream));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    dfree(h, save);
+    if (st == SS_OK) st = set_step(h, step0);
+    if (st == SS_OK && out_info) st = spin_system_info(h, out_info);
+    return st;
+}
+
+ss_status spin_system_set_barrier_test(ss_system *h, int32_t extra, int64_t timeout_ns) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (extra < 0 || timeout_ns < 1000) return fail(h, SS_ERR_INVALID_ARG, "extra >= 0 and timeout_ns >= 1000 needed");
+    h->bar_extra = (unsigned int)extra;
+    h->bar_timeout_ns = extra ? timeout_ns : 2000000000ll;
+    if (!extra && timeout_ns != 2000000000ll) h->bar_timeout_ns = timeout_ns;
+    drop_graph(h);
+    return SS_OK;
+}
+
+ss_status ss_debug_philox(const uint32_t ctr0[4], const uint32_t key[2], int64_t count, uint32_t *out) {
+    if (!ctr0 || !key || !out || count < 0) return fail(nullptr, SS_ERR_INVALID_ARG, "bad arguments");
+    uint32_t *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, (size_t)std::max<int64_t>(count, 1) * 16);
+    if (e == cudaSuccess) e = launch_debug_philox(ctr0, key, count, d, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, (size_t)count * 16, cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    return e == cudaSuccess ? SS_OK : fail(nullptr, SS_ERR_CUDA, "%s", cudaGetErrorString(e));
+}
+
+ss_status ss_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, int64_t n, int32_t mode, double *out) {
+    if (!out || n < 0 || (mode != 0 && mode != 1)) return fail(nullptr, SS_ERR_INVALID_ARG, "bad arguments");
+    std::vector<double2> tab;
+    build_tables(tab);
+    double2 *dt = nullptr;
+    double *d = nullptr;
+    cudaError_t e = cudaMalloc(&dt, tab.size() * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&d, (size_t)std::max<int64_t>(n, 1) * 3 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(dt, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_debug_gaussians(seed, sys, step, n, mode, dt, dt + kLogTab, dt + kLogTab + kLn2Tab, d, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (dt) cudaFree(dt);
+    return e == cudaSuccess ? SS_OK : fail(nullptr, SS_ERR_CUDA, "%s", cudaGetErrorString(e));
+}
+
+const char *ss_last_error(ss_system *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+const char *ss_status_string(ss_status s) {
+    switch (s) {
+        case SS_OK: return "ok";
+        case SS_ERR_INVALID_ARG: return "invalid argument";
+        case SS_ERR_CUDA: return "CUDA error";
+        case SS_ERR_OOM: return "out of memory";
+        case SS_ERR_TIMEOUT: return "device wait timed out";
+        case SS_ERR_NONFINITE: return "non-finite spin";
+        case SS_ERR_STATE: return "handle unusable";
+        case SS_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// Precision-independent kernels: the per-system finalisation of on-demand measurements
+// and the diagnostic Philox / Gaussian kernels used by the tests.
+#include "ss_kernels.cuh"
+
+namespace ss {
+
+cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
+                            double *dst, cudaStream_t s) {
+    const int grid = nsys < 1024 ? nsys : 1024;
+    k_finalize<256><<<grid > 0 ? grid : 1, 256, 0, s>>>(sys, sys_tiles, nsys, partials, dst);
+    return cudaGetLastError();
+}
+
+__global__ void k_debug_philox(uint4 ctr0, uint2 key, long long count, uint32_t *out) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+         k += (long long)gridDim.x * blockDim.x) {
+        const Philox4 w = philox4x32_10(ctr0.x + (uint32_t)k, ctr0.y, ctr0.z, ctr0.w, key.x, key.y);
+        out[4 * k + 0] = w.w0;
+        out[4 * k + 1] = w.w1;
+        out[4 * k + 2] = w.w2;
+        out[4 * k + 3] = w.w3;
+    }
+}
+
+cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long long count, uint32_t *out,
+                                cudaStream_t s) {
+    const uint4 c = make_uint4(ctr0[0], ctr0[1], ctr0[2], ctr0[3]);
+    const uint2 k = make_uint2(key[0], key[1]);
+    k_debug_philox<<<256, 256, 0, s>>>(c, k, count, out);
+    return cudaGetLastError();
+}
+
+// mode 0: the step kernels' table-driven transform; mode 1: CUDA's log/sqrt/sincospi.
+__global__ void k_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
+                                  const double2 *tab_log, const double2 *tab_ln2, const double2 *tab_trig,
+                                  double *out) {
+    __shared__ SmemTables tab;
+    for (int i = threadIdx.x; i < kLogTab; i += blockDim.x) tab.log_[i] = tab_log[i];
+    for (int i = threadIdx.x; i < kLn2Tab; i += blockDim.x) tab.ln2[i] = tab_ln2[i];
+    for (int i = threadIdx.x; i < kTrigTab; i += blockDim.x) tab.trig[i] = tab_trig[i];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const Philox4 w = philox4x32_10((uint32_t)i, step, sys, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+        double g0, g1, g2;
+        if (mode == 0) {
+            box_muller3(w, tab.log_, tab.ln2, tab.trig, g0, g1, g2);
+        } else {
+            box_muller3_libm(w, g0, g1, g2);
+        }
+        out[3 * i + 0] = g0;
+        out[3 * i + 1] = g1;
+        out[3 * i + 2] = g2;
+    }
+}
+
+cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
+                                   const double2 *tab_log, const double2 *tab_ln2, const double2 *tab_trig,
+                                   double *out, cudaStream_t s) {
+    k_debug_gaussians<<<256, 256, 0, s>>>(seed, sys, step, n, mode, tab_log, tab_ln2, tab_trig, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ss

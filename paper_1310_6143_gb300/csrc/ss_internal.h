@@ -1,0 +1,117 @@
+// Internal structures shared by the host API (ss_api.cu) and the step kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ss {
+
+// Table I of the paper.
+constexpr double kBoltzmann = 1.3807e-23;   // J/K
+constexpr double kGammaDefault = 1.76e11;   // 1/(T s)
+
+// Sizes of the Box-Muller function tables held in shared memory.
+constexpr int kLogTab = 193;   // centres c_t = (192 + t)/256, t = 0..192, covering [0.75, 1.5]
+constexpr int kLn2Tab = 34;    // 2 n ln 2, n = 0..33, as (hi, lo)
+constexpr int kTrigTab = 512;  // (sin, cos) of 2 pi j / 512
+constexpr int kRecComps = 8;   // record: sum mu S (3), sum mu, E_exc, E_ani, E_app, E_total
+constexpr int kPartComps = 8;  // tile partials: sum mu S (3), E_exc, E_ani, E_app, 0, 0
+
+// One system of a handle (several when batched).  Lives in device memory; the field and
+// temperature entries are rewritten by set_field / set_temperature between launches.
+struct SysDesc {
+    int64_t offset;      // first spin of the system in the concatenated arrays
+    int64_t n;           // spins
+    uint32_t key0, key1; // Philox key = (seed low word, seed high word)
+    uint32_t ctr2;       // third counter word (system id)
+    uint32_t pad;
+    double H[3];         // applied field, T
+    double sqrtT;        // square root of the temperature, sqrt(K)
+    double msum;         // sum of mu_s over the system, J/T
+};
+
+// One material: a distinct (system, mu_s, k_u, easy axis, Neel tensor) combination.
+// Per-spin arrays are replaced by a material index per spin; identical sites share an
+// entry, so a homogeneous lattice reads one broadcast entry.
+template <typename R>
+struct MatDesc {
+    R inv_mu;     // 1 / mu_s                                      (1/(J/T))
+    R ani;        // 2 k_u / mu_s                                  (T)
+    R e[3];       // easy axis
+    R kf[6];      // (2 / mu_s) K, field tensor of the Neel term    (T)
+    R gp;         // gamma / (1 + lambda^2)
+    R lambda;     // damping
+    R dt;         // time step
+    R sig;        // sqrt(2 lambda kB / (gamma mu_s dt)); sigma = sig * sqrt(T)
+    R mu;         // mu_s
+    R ku;         // k_u
+    R K[6];       // Neel tensor (energy)
+    int32_t sys;
+    int32_t has_neel;
+};
+
+// A contiguous range of spins of one system, processed by one block per pass.
+struct TileDesc {
+    int64_t start;
+    int32_t count;
+    int32_t sys;
+};
+
+// Everything a step kernel reads or writes.  Passed by value.
+template <typename R>
+struct KArgs {
+    int64_t n;
+    const int32_t *row_ptr;   // [n+1]
+    const int32_t *col;       // [nnz]
+    const R *J;               // [nnz]
+    const int32_t *mat;       // [n] material index
+    const MatDesc<R> *mats;
+    const SysDesc *sys;
+    const TileDesc *tiles;
+    int64_t ntiles;
+    const int32_t *sys_tiles; // [nsys+1] tile range of each system
+    int32_t nsys;
+    R *sx, *sy, *sz;          // S (state)
+    R *px, *py, *pz;          // S' (predictor, renormalised)
+    R *qx, *qy, *qz;          // S + dt/2 dS (predictor half step)
+    R *hx, *hy, *hz;          // thermal field of the current step
+    double *partials;         // [ntiles * kPartComps]
+    double *rec;              // ring [rec_cap][nsys][kRecComps]
+    int64_t rec_cap;
+    double *cur;              // [nsys][kRecComps] on-demand measurement
+    unsigned long long *step; // index of the next step
+    const double *sqrtT_sched;
+    int64_t sched_len;
+    int64_t sched_step0;
+    unsigned int *err;        // bit 0: non-finite spin, bit 1: barrier timeout
+    unsigned int *ticket;     // completion counter of the corrector launch
+    const double2 *tab_log;   // (1/c_t, 2 ln c_t) rounded from 1/c_t
+    const double2 *tab_ln2;   // (hi, lo) of 2 n ln 2
+    const double2 *tab_trig;  // (sin, cos) of 2 pi j / 512
+    unsigned int *bar_count;  // grid barrier of the persistent kernel
+    unsigned int *bar_gen;
+    unsigned int bar_extra;   // test hook: phantom blocks the barrier waits for
+    long long bar_timeout_ns;
+};
+
+constexpr unsigned int kErrNonFinite = 1u;
+constexpr unsigned int kErrTimeout = 2u;
+
+// Launchers (ss_kernels_f32.cu / ss_kernels_f64.cu).
+template <typename R> cudaError_t launch_predictor(const KArgs<R> &a, int block, int grid, cudaStream_t s);
+template <typename R> cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s);
+template <typename R> cudaError_t launch_measure(const KArgs<R> &a, int block, int grid, cudaStream_t s);
+template <typename R> cudaError_t launch_init_sphere(const KArgs<R> &a, cudaStream_t s);
+template <typename R> cudaError_t launch_persistent(const KArgs<R> &a, int block, int grid, int nfin,
+                                                    long long nsteps, cudaStream_t s);
+template <typename R> int persistent_blocks_per_sm(int block);
+template <typename R> int step_blocks_per_sm(int block);
+cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
+                            double *dst, cudaStream_t s);
+cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long long count, uint32_t *out,
+                                cudaStream_t s);
+cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
+                                   const double2 *tab_log, const double2 *tab_ln2, const double2 *tab_trig,
+                                   double *out, cudaStream_t s);
+
+}  // namespace ss

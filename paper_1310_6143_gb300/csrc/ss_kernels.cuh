@@ -1,0 +1,478 @@
+// Step kernels of the stochastic Heun-LLG integrator (templated on the working type R).
+//
+// One step (Section "Time Integration of the LLG Equation" of arXiv:1310.6143):
+//   predictor pass, every spin i:
+//     H_i  = (1/mu) sum_j J_ij S_j + (2 k_u/mu)(S_i.e) e + H_app [+ (2/mu) K S_i] + H_th,i
+//            (Eq. Heff applied to the Hamiltonian; H_th,i from Philox + Box-Muller, drawn
+//            once per step at T(t_n) and stored for the corrector)
+//     dS_i = -gamma/(1+lambda^2) [S_i x H_i + lambda S_i x (S_i x H_i)]       (Eq. LLG)
+//     S'_i = normalise(S_i + dt dS_i),  Q_i = S_i + dt/2 dS_i
+//     + FP64 partial sums of sum mu S, E_exc, E_ani, E_app of the state S(t_n)
+//   -- every predictor finishes before any corrector starts (kernel boundary, or a grid
+//      barrier in the persistent kernel) --
+//   corrector pass, every spin i:
+//     H'_i from S' with the same H_th,i; dS'_i = LLG(S'_i, H'_i)
+//     S_i <- normalise(Q_i + dt/2 dS'_i)   (= S_i + dt/2 (dS_i + dS'_i), then renormalised)
+//
+// Data layout: spins as structure-of-arrays (three arrays per vector); the neighbour list
+// in CSR (int32 offsets and columns, J in the working type); one material index per spin.
+// Work is split into tiles (contiguous spins of one system); each tile yields one FP64
+// partial of the reductions, summed per system in a fixed order, so the record is
+// bitwise reproducible.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <stdint.h>
+
+#include "ss_internal.h"
+#include "ss_math.cuh"
+
+namespace ss {
+
+// Loads of data written earlier in the same launch must bypass the non-coherent L1
+// (the persistent kernel); everything else may use the read-only path.
+template <bool Coherent, typename T>
+__device__ __forceinline__ T ld(const T *p) {
+    if constexpr (Coherent) {
+        return __ldcg(p);
+    } else {
+        return __ldg(p);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R rsqrt_r(R x);
+template <>
+__device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
+
+// Shared-memory copies of the Box-Muller function tables.
+struct SmemTables {
+    double2 log_[kLogTab];
+    double2 ln2[kLn2Tab];
+    double2 trig[kTrigTab];
+};
+
+template <typename R>
+__device__ __forceinline__ void stage_tables(const KArgs<R> &a, SmemTables &t) {
+    for (int i = threadIdx.x; i < kLogTab; i += blockDim.x) t.log_[i] = a.tab_log[i];
+    for (int i = threadIdx.x; i < kLn2Tab; i += blockDim.x) t.ln2[i] = a.tab_ln2[i];
+    for (int i = threadIdx.x; i < kTrigTab; i += blockDim.x) t.trig[i] = a.tab_trig[i];
+}
+
+// sum_j J_ij X_j over row i (CSR order, one FMA per term and component).
+template <typename R, bool Coherent>
+__device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int64_t i,
+                                             R &e0, R &e1, R &e2) {
+    const int32_t b = __ldg(a.row_ptr + i);
+    const int32_t e = __ldg(a.row_ptr + i + 1);
+    R x = 0, y = 0, z = 0;
+    for (int32_t k = b; k < e; ++k) {
+        const int32_t j = __ldg(a.col + k);
+        const R Jk = __ldg(a.J + k);
+        x = fma(Jk, ld<Coherent>(X + j), x);
+        y = fma(Jk, ld<Coherent>(Y + j), y);
+        z = fma(Jk, ld<Coherent>(Z + j), z);
+    }
+    e0 = x;
+    e1 = y;
+    e2 = z;
+}
+
+// Deterministic field (tesla) from the exchange sum, in the order exchange, anisotropy,
+// applied field, Neel.
+template <typename R>
+__device__ __forceinline__ void det_field(const MatDesc<R> &m, const SysDesc &sd, R s0, R s1, R s2, R e0, R e1, R e2,
+                                          R &H0, R &H1, R &H2) {
+    const R im = m.inv_mu;
+    H0 = e0 * im;
+    H1 = e1 * im;
+    H2 = e2 * im;
+    const R sde = s0 * m.e[0] + s1 * m.e[1] + s2 * m.e[2];
+    const R an = m.ani * sde;
+    H0 = fma(an, m.e[0], H0);
+    H1 = fma(an, m.e[1], H1);
+    H2 = fma(an, m.e[2], H2);
+    H0 += (R)sd.H[0];
+    H1 += (R)sd.H[1];
+    H2 += (R)sd.H[2];
+    if (m.has_neel) {
+        H0 += m.kf[0] * s0 + m.kf[3] * s1 + m.kf[4] * s2;
+        H1 += m.kf[3] * s0 + m.kf[1] * s1 + m.kf[5] * s2;
+        H2 += m.kf[4] * s0 + m.kf[5] * s1 + m.kf[2] * s2;
+    }
+}
+
+// dS = -gamma/(1+lambda^2) [S x H + lambda S x (S x H)]  (Eq. LLG)
+template <typename R>
+__device__ __forceinline__ void llg_rhs(R gp, R lam, R s0, R s1, R s2, R H0, R H1, R H2, R &d0, R &d1, R &d2) {
+    const R c0 = s1 * H2 - s2 * H1;
+    const R c1 = s2 * H0 - s0 * H2;
+    const R c2 = s0 * H1 - s1 * H0;
+    const R x0 = s1 * c2 - s2 * c1;
+    const R x1 = s2 * c0 - s0 * c2;
+    const R x2 = s0 * c1 - s1 * c0;
+    d0 = -gp * fma(lam, x0, c0);
+    d1 = -gp * fma(lam, x1, c1);
+    d2 = -gp * fma(lam, x2, c2);
+}
+
+// Per-spin contributions to the reductions of the state S: mu S (3), E_exc, E_ani, E_app.
+template <typename R>
+__device__ __forceinline__ void spin_terms(const MatDesc<R> &m, const SysDesc &sd, R s0, R s1, R s2, R e0, R e1,
+                                           R e2, double v[6]) {
+    const R mu = m.mu;
+    v[0] = (double)(mu * s0);
+    v[1] = (double)(mu * s1);
+    v[2] = (double)(mu * s2);
+    v[3] = (double)((R)-0.5 * (s0 * e0 + s1 * e1 + s2 * e2));
+    const R sde = s0 * m.e[0] + s1 * m.e[1] + s2 * m.e[2];
+    R ea = -m.ku * sde * sde;
+    if (m.has_neel) {
+        ea -= m.K[0] * s0 * s0 + m.K[1] * s1 * s1 + m.K[2] * s2 * s2
+            + (R)2 * (m.K[3] * s0 * s1 + m.K[4] * s0 * s2 + m.K[5] * s1 * s2);
+    }
+    v[4] = (double)ea;
+    v[5] = (double)(-mu * (s0 * (R)sd.H[0] + s1 * (R)sd.H[1] + s2 * (R)sd.H[2]));
+}
+
+// Sum of eight FP64 values over a warp by a transposing butterfly: 9 additions per lane
+// instead of 40.  Afterwards lane L holds component ((L>>4)&1)*4 + ((L>>3)&1)*2 + ((L>>2)&1).
+__device__ __forceinline__ double warp_sum8(const double v[8]) {
+    const int lane = threadIdx.x & 31;
+    double w4[4], w2[2];
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double send = u16 ? v[k] : v[k + 4];
+        const double keep = u16 ? v[k + 4] : v[k];
+        w4[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double send = u8 ? w4[k] : w4[k + 2];
+        const double keep = u8 ? w4[k + 2] : w4[k];
+        w2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    double x;
+    {
+        const double send = u4 ? w2[0] : w2[1];
+        const double keep = u4 ? w2[1] : w2[0];
+        x = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    return x;
+}
+
+__device__ __forceinline__ int warp_sum8_component(int lane) {
+    return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
+// Block sum of eight FP64 values in a fixed order; the result is valid in thread 0..7
+// (component = thread index) after the call.  red must hold (BS/32)*8 doubles.
+template <int BS>
+__device__ __forceinline__ double block_sum8(const double v[8], double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double x = warp_sum8(v);
+    if ((lane & 3) == 0) red[warp * 8 + warp_sum8_component(lane)] = x;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 8) {
+#pragma unroll 4
+        for (int w = 0; w < BS / 32; ++w) r += red[w * 8 + threadIdx.x];
+    }
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double sqrtT_of_step(const double *sched, int64_t len, int64_t step0, uint64_t step,
+                                                double sqrtT_sys) {
+    if (len <= 0) return sqrtT_sys;
+    int64_t k = (int64_t)step - step0;
+    k = k < 0 ? 0 : (k >= len ? len - 1 : k);
+    return sched[k];
+}
+
+// Predictor over one tile.  Writes S', Q and H_th; returns the tile's partial sums
+// (valid in threads 0..7).
+template <typename R, int BS, bool Coherent>
+__device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
+                                                 const SmemTables &tab, double *red) {
+    const SysDesc &sd = a.sys[td.sys];
+    const double sqrtT = sqrtT_of_step(a.sqrtT_sched, a.sched_len, a.sched_step0, step, sd.sqrtT);
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    bool first = true;
+    for (int k = threadIdx.x; k < td.count; k += BS) {
+        const int64_t i = td.start + k;
+        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+        const R s0 = ld<Coherent>(a.sx + i), s1 = ld<Coherent>(a.sy + i), s2 = ld<Coherent>(a.sz + i);
+        R e0, e1, e2;
+        exchange_sum<R, Coherent>(a, a.sx, a.sy, a.sz, i, e0, e1, e2);
+        R H0, H1, H2;
+        det_field(m, sd, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+        R t0 = 0, t1 = 0, t2 = 0;
+        if (sqrtT > 0.0) {
+            const Philox4 w = philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
+            double g0, g1, g2;
+            box_muller3(w, tab.log_, tab.ln2, tab.trig, g0, g1, g2);
+            const R sig = m.sig * (R)sqrtT;
+            t0 = sig * (R)g0;
+            t1 = sig * (R)g1;
+            t2 = sig * (R)g2;
+        }
+        a.hx[i] = t0;
+        a.hy[i] = t1;
+        a.hz[i] = t2;
+        H0 += t0;
+        H1 += t1;
+        H2 += t2;
+        R d0, d1, d2;
+        llg_rhs(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, d0, d1, d2);
+        const R dt = m.dt;
+        const R v0 = fma(dt, d0, s0), v1 = fma(dt, d1, s1), v2 = fma(dt, d2, s2);
+        const R inv = rsqrt_r(v0 * v0 + v1 * v1 + v2 * v2);
+        a.px[i] = v0 * inv;
+        a.py[i] = v1 * inv;
+        a.pz[i] = v2 * inv;
+        const R hdt = (R)0.5 * dt;
+        a.qx[i] = fma(hdt, d0, s0);
+        a.qy[i] = fma(hdt, d1, s1);
+        a.qz[i] = fma(hdt, d2, s2);
+        double v[6];
+        spin_terms(m, sd, s0, s1, s2, e0, e1, e2, v);
+        if (first) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[c] = v[c];
+            first = false;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[c] += v[c];
+        }
+    }
+    return block_sum8<BS>(acc, red);
+}
+
+template <typename R, int BS, bool Coherent>
+__device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc &td) {
+    const SysDesc &sd = a.sys[td.sys];
+    for (int k = threadIdx.x; k < td.count; k += BS) {
+        const int64_t i = td.start + k;
+        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+        const R s0 = ld<Coherent>(a.px + i), s1 = ld<Coherent>(a.py + i), s2 = ld<Coherent>(a.pz + i);
+        R e0, e1, e2;
+        exchange_sum<R, Coherent>(a, a.px, a.py, a.pz, i, e0, e1, e2);
+        R H0, H1, H2;
+        det_field(m, sd, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+        H0 += ld<Coherent>(a.hx + i);
+        H1 += ld<Coherent>(a.hy + i);
+        H2 += ld<Coherent>(a.hz + i);
+        R d0, d1, d2;
+        llg_rhs(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, d0, d1, d2);
+        const R hdt = (R)0.5 * m.dt;
+        const R v0 = fma(hdt, d0, ld<Coherent>(a.qx + i));
+        const R v1 = fma(hdt, d1, ld<Coherent>(a.qy + i));
+        const R v2 = fma(hdt, d2, ld<Coherent>(a.qz + i));
+        const R inv = rsqrt_r(v0 * v0 + v1 * v1 + v2 * v2);
+        if (!(inv < (R)3.0e38)) atomicOr(a.err, kErrNonFinite);  // NaN, inf or zero length
+        a.sx[i] = v0 * inv;
+        a.sy[i] = v1 * inv;
+        a.sz[i] = v2 * inv;
+    }
+}
+
+// Sum the tile partials of system s in tile order and write one record (8 doubles).
+template <int BS, bool Coherent>
+__device__ __forceinline__ void finalize_system(const SysDesc *sys, const int32_t *sys_tiles, const double *partials,
+                                                int s, double *dst, double *red) {
+    const int32_t t0 = sys_tiles[s], t1 = sys_tiles[s + 1];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int32_t t = t0 + threadIdx.x; t < t1; t += BS) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += ld<Coherent>(partials + (int64_t)t * kPartComps + c);
+    }
+    const double r = block_sum8<BS>(acc, red);
+    // threads 0..7 hold components; place them into the record layout
+    __shared__ double comp[8];
+    if (threadIdx.x < 8) comp[threadIdx.x] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        dst[0] = comp[0];
+        dst[1] = comp[1];
+        dst[2] = comp[2];
+        dst[3] = sys[s].msum;
+        dst[4] = comp[3];
+        dst[5] = comp[4];
+        dst[6] = comp[5];
+        dst[7] = (comp[3] + comp[4]) + comp[5];
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------------------------------
+// Kernels
+// ----------------------------------------------------------------------------------
+
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_predictor(const KArgs<R> a) {
+    __shared__ SmemTables tab;
+    __shared__ double red[(BS / 32) * 8];
+    stage_tables(a, tab);
+    __syncthreads();
+    const uint64_t step = *a.step;
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const TileDesc td = a.tiles[t];
+        const double r = predictor_tile<R, BS, false>(a, td, step, tab, red);
+        if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
+    }
+}
+
+// Blocks [0, nfin) sum the predictor's tile partials into the record ring; the rest run
+// the corrector over the tiles.  The last block to finish advances the step counter.
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_corrector(const KArgs<R> a, int nfin) {
+    __shared__ double red[(BS / 32) * 8];
+    const uint64_t step = *a.step;
+    if ((int)blockIdx.x < nfin) {
+        for (int s = blockIdx.x; s < a.nsys; s += nfin) {
+            double *dst = a.rec + ((int64_t)(step % (uint64_t)a.rec_cap) * a.nsys + s) * kRecComps;
+            finalize_system<BS, false>(a.sys, a.sys_tiles, a.partials, s, dst, red);
+        }
+    } else {
+        const int64_t nb = gridDim.x - nfin;
+        for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb) corrector_tile<R, BS, false>(a, a.tiles[t]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int done = atomicAdd(a.ticket, 1u);
+        if (done == gridDim.x - 1) {
+            *a.ticket = 0u;
+            *a.step = step + 1ull;
+            __threadfence();
+        }
+    }
+}
+
+// Tile partials of the current state (no integration): the on-demand measurement.
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_measure(const KArgs<R> a) {
+    __shared__ double red[(BS / 32) * 8];
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const TileDesc td = a.tiles[t];
+        const SysDesc &sd = a.sys[td.sys];
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = threadIdx.x; k < td.count; k += BS) {
+            const int64_t i = td.start + k;
+            const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+            const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
+            R e0, e1, e2;
+            exchange_sum<R, false>(a, a.sx, a.sy, a.sz, i, e0, e1, e2);
+            double v[6];
+            spin_terms(m, sd, s0, s1, s2, e0, e1, e2, v);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[c] += v[c];
+        }
+        const double r = block_sum8<BS>(acc, red);
+        if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
+    }
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) k_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys,
+                                                 const double *partials, double *dst) {
+    __shared__ double red[(BS / 32) * 8];
+    for (int s = blockIdx.x; s < nsys; s += gridDim.x)
+        finalize_system<BS, false>(sys, sys_tiles, partials, s, dst + (int64_t)s * kRecComps, red);
+}
+
+// Random unit spins from the reserved stream: counter (i, 0xFFFFFFFF, system, 1).
+template <typename R>
+__global__ void k_init_sphere(const KArgs<R> a) {
+    __shared__ SmemTables tab;
+    stage_tables(a, tab);
+    __syncthreads();
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const TileDesc td = a.tiles[t];
+        const SysDesc &sd = a.sys[td.sys];
+        for (int k = threadIdx.x; k < td.count; k += blockDim.x) {
+            const int64_t i = td.start + k;
+            const Philox4 w = philox4x32_10((uint32_t)(i - sd.offset), 0xFFFFFFFFu, sd.ctr2, 1u, sd.key0, sd.key1);
+            double g0, g1, g2;
+            box_muller3(w, tab.log_, tab.ln2, tab.trig, g0, g1, g2);
+            const double inv = 1.0 / sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+            a.sx[i] = (R)(g0 * inv);
+            a.sy[i] = (R)(g1 * inv);
+            a.sz[i] = (R)(g2 * inv);
+        }
+    }
+}
+
+// Bounded grid barrier: waits at most bar_timeout_ns (globaltimer) and then reports a
+// timeout instead of hanging.  Returns false on timeout (uniform within the block).
+__device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int *gen, unsigned int expected,
+                                             long long timeout_ns, unsigned int *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *vgen = gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(count, 1u);
+        if (arrived == expected - 1u) {
+            *count = 0u;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            unsigned long long t0;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            while (*vgen == g) {
+                unsigned long long t1;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+                if ((long long)(t1 - t0) > timeout_ns) {
+                    atomicOr(err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Many steps in one cooperative launch: predictor phase, barrier, corrector phase (with
+// the record of the step summed by blocks [0, nfin)), barrier.
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, long long nsteps) {
+    __shared__ SmemTables tab;
+    __shared__ double red[(BS / 32) * 8];
+    stage_tables(a, tab);
+    __syncthreads();
+    const uint64_t step0 = __ldcg(a.step);
+    const unsigned int expected = gridDim.x + a.bar_extra;
+    for (long long k = 0; k < nsteps; ++k) {
+        const uint64_t step = step0 + (uint64_t)k;
+        for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+            const TileDesc td = a.tiles[t];
+            const double r = predictor_tile<R, BS, true>(a, td, step, tab, red);
+            if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
+        }
+        if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
+        if ((int)blockIdx.x < nfin) {
+            for (int s = blockIdx.x; s < a.nsys; s += nfin) {
+                double *dst = a.rec + ((int64_t)(step % (uint64_t)a.rec_cap) * a.nsys + s) * kRecComps;
+                finalize_system<BS, true>(a.sys, a.sys_tiles, a.partials, s, dst, red);
+            }
+        }
+        for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) corrector_tile<R, BS, true>(a, a.tiles[t]);
+        if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.step = step0 + (uint64_t)nsteps;
+}
+
+}  // namespace ss

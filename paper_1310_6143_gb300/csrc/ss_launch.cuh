@@ -1,0 +1,85 @@
+// Host launchers of the step kernels for one working type; included by
+// ss_kernels_f32.cu and ss_kernels_f64.cu (one translation unit per precision).
+#pragma once
+
+#include "ss_kernels.cuh"
+
+namespace ss {
+
+#define SS_BLOCK_SWITCH(block, ...)                      \
+    switch (block) {                                     \
+        case 128: { constexpr int BS = 128; __VA_ARGS__; } break; \
+        case 256: { constexpr int BS = 256; __VA_ARGS__; } break; \
+        case 512: { constexpr int BS = 512; __VA_ARGS__; } break; \
+        default: return cudaErrorInvalidValue;           \
+    }
+
+template <typename R>
+cudaError_t launch_predictor(const KArgs<R> &a, int block, int grid, cudaStream_t s) {
+    SS_BLOCK_SWITCH(block, k_predictor<R, BS><<<grid, BS, 0, s>>>(a));
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s) {
+    SS_BLOCK_SWITCH(block, k_corrector<R, BS><<<grid + nfin, BS, 0, s>>>(a, nfin));
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_measure(const KArgs<R> &a, int block, int grid, cudaStream_t s) {
+    SS_BLOCK_SWITCH(block, k_measure<R, BS><<<grid, BS, 0, s>>>(a));
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_init_sphere(const KArgs<R> &a, cudaStream_t s) {
+    const int64_t g = a.ntiles < 4096 ? a.ntiles : 4096;
+    k_init_sphere<R><<<(int)(g > 0 ? g : 1), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R>
+int persistent_blocks_per_sm(int block) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (block) {
+        case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, 128>, 128, 0); break;
+        case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, 256>, 256, 0); break;
+        case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, 512>, 512, 0); break;
+        default: break;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
+template <typename R>
+int step_blocks_per_sm(int block) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (block) {
+        case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_predictor<R, 128>, 128, 0); break;
+        case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_predictor<R, 256>, 256, 0); break;
+        case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_predictor<R, 512>, 512, 0); break;
+        default: break;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
+template <typename R>
+cudaError_t launch_persistent(const KArgs<R> &a, int block, int grid, int nfin, long long nsteps, cudaStream_t s) {
+    KArgs<R> args = a;
+    void *params[] = {(void *)&args, (void *)&nfin, (void *)&nsteps};
+    SS_BLOCK_SWITCH(block, return cudaLaunchCooperativeKernel((const void *)k_persistent<R, BS>, dim3(grid),
+                                                              dim3(BS), params, 0, s));
+    return cudaSuccess;
+}
+
+template cudaError_t launch_predictor<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
+template cudaError_t launch_corrector<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
+template cudaError_t launch_measure<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
+template cudaError_t launch_init_sphere<SS_REAL>(const KArgs<SS_REAL> &, cudaStream_t);
+template cudaError_t launch_persistent<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, long long, cudaStream_t);
+template int persistent_blocks_per_sm<SS_REAL>(int);
+template int step_blocks_per_sm<SS_REAL>(int);
+
+}  // namespace ss

@@ -1,0 +1,245 @@
+"""User-facing Python front end of libspinsys (argument marshalling only).
+
+``SpinSystem`` owns one C handle (one system, or a batch of independent systems) and
+forwards every call to the C ABI of ``include/spinsys.h``.  Arrays come from
+``paper_1310_6143_gb300.lattice`` (or any source of the same shapes).  PyTorch is only
+used, when asked, for the CUDA stream handle and zero-copy device views of the spins.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import numpy as np
+
+from . import _binding as B
+from .lattice import SpinLattice
+
+_PREC = {"fp64": B.SS_FP64, "fp32": B.SS_FP32_MIXED, "fp32_mixed": B.SS_FP32_MIXED}
+_EXEC = {"auto": B.SS_EXEC_AUTO, "kernels": B.SS_EXEC_KERNELS, "graph": B.SS_EXEC_GRAPH,
+         "persistent": B.SS_EXEC_PERSISTENT}
+
+
+def _per_system(v, count, name):
+    if isinstance(v, (list, tuple, np.ndarray)) and np.ndim(v) >= 1 and not (
+            name == "H" and np.ndim(v) == 1 and len(v) == 3 and count != 3):
+        if name == "H" and np.ndim(v) == 1:
+            return [tuple(v)] * count
+        if len(v) != count:
+            raise ValueError(f"{name}: need one value per system ({count})")
+        return list(v)
+    return [v] * count
+
+
+class _DeviceArray:
+    """Minimal __cuda_array_interface__ carrier for zero-copy torch views."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+class SpinSystem:
+    """One handle of the GB300 Heun-LLG library.
+
+    ``lattices`` is a SpinLattice or a sequence of them (a batch of independent systems).
+    ``alpha``, ``dt``, ``T``, ``H``, ``seed``, ``sys_id`` and ``S0`` may be given per
+    system as sequences.  ``precision`` is "fp64" or "fp32" (FP32 storage and field/LLG
+    arithmetic with FP64 thermal transform and FP64 reductions).
+    """
+
+    def __init__(self, lattices: SpinLattice | Sequence[SpinLattice], *, alpha=0.1, dt=1e-16, T=0.0,
+                 H=(0.0, 0.0, 0.0), seed=1, sys_id=None, precision="fp64", S0=None, init_random=False,
+                 gamma=0.0, check_symmetry=False, stream=None):
+        self._lib = B.load()
+        self._h = ctypes.c_void_p()
+        lats = [lattices] if isinstance(lattices, SpinLattice) else list(lattices)
+        count = len(lats)
+        if count < 1:
+            raise ValueError("need at least one lattice")
+        alphas = _per_system(alpha, count, "alpha")
+        dts = _per_system(dt, count, "dt")
+        Ts = _per_system(T, count, "T")
+        Hs = _per_system(H, count, "H")
+        seeds = _per_system(seed, count, "seed")
+        ids = list(range(count)) if sys_id is None else _per_system(sys_id, count, "sys_id")
+        S0s = [None] * count if S0 is None else (S0 if count > 1 else [S0])
+        if precision not in _PREC:
+            raise ValueError(f"precision must be one of {sorted(_PREC)}")
+        keep = []
+        params = (B.SSParams * count)()
+        for s, lat in enumerate(lats):
+            arrs = {
+                "row_ptr": np.ascontiguousarray(lat.row_ptr, dtype=np.int64),
+                "col": np.ascontiguousarray(lat.col, dtype=np.int32),
+                "J": np.ascontiguousarray(lat.J, dtype=np.float64),
+                "mu_s": np.ascontiguousarray(lat.mu_s, dtype=np.float64),
+                "k_u": np.ascontiguousarray(lat.k_u, dtype=np.float64),
+                "easy_axis": np.ascontiguousarray(lat.easy_axis, dtype=np.float64),
+                "K_neel": None if lat.K_neel is None else np.ascontiguousarray(lat.K_neel, dtype=np.float64),
+                "pos": None if lat.pos is None else np.ascontiguousarray(lat.pos, dtype=np.float64),
+                "S0": None if S0s[s] is None else np.ascontiguousarray(S0s[s], dtype=np.float64),
+            }
+            keep.append(arrs)
+            p = params[s]
+            p.n = lat.n
+            for k, a in arrs.items():
+                setattr(p, k, None if a is None else a.ctypes.data)
+            p.alpha = float(alphas[s])
+            p.dt = float(dts[s])
+            p.gamma = float(gamma)
+            for c in range(3):
+                p.H_app[c] = float(Hs[s][c])
+            p.T = float(Ts[s])
+            p.seed = int(seeds[s]) & 0xFFFFFFFFFFFFFFFF
+            p.sys_id = int(ids[s]) & 0xFFFFFFFF
+            p.precision = _PREC[precision]
+            p.flags = (B.SS_FLAG_CHECK_SYMMETRY if check_symmetry else 0) | (B.SS_FLAG_INIT_RANDOM if init_random else 0)
+        if count == 1:
+            st = self._lib.spin_system_create(ctypes.byref(params[0]), ctypes.byref(self._h))
+        else:
+            st = self._lib.spin_batch_create(params, count, ctypes.byref(self._h))
+        B.check(st, None)
+        self.n = int(sum(l.n for l in lats))
+        self.num_systems = count
+        self.sizes = [l.n for l in lats]
+        self.offsets = list(np.cumsum([0] + self.sizes[:-1]))
+        self.precision = precision
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- lifetime ---------------------------------------------------------------------
+    def close(self):
+        if self._h:
+            self._lib.spin_system_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st):
+        B.check(st, self._h)
+
+    # -- configuration ----------------------------------------------------------------
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (own stream)."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(self._lib.spin_system_set_stream(self._h, ctypes.c_void_p(raw) if raw else None))
+
+    def set_field(self, H, sys: int = -1):
+        arr = np.ascontiguousarray(H, dtype=np.float64).reshape(3)
+        self._check(self._lib.set_field(self._h, int(sys), B.ptr(arr)))
+
+    def set_temperature(self, T):
+        if np.ndim(T) == 0:
+            self._check(self._lib.set_temperature(self._h, float(T)))
+        else:
+            arr = np.ascontiguousarray(T, dtype=np.float64)
+            self._check(self._lib.set_temperature_batch(self._h, B.ptr(arr), int(arr.size)))
+
+    def set_temperature_schedule(self, T_per_step, step0: int = 0):
+        arr = np.ascontiguousarray(T_per_step, dtype=np.float64)
+        self._check(self._lib.set_temperature_schedule(self._h, B.ptr(arr), int(arr.size), int(step0)))
+
+    def set_exec(self, mode: str):
+        self._check(self._lib.spin_system_set_exec(self._h, _EXEC[mode]))
+
+    def set_launch(self, block: int, tile: int):
+        self._check(self._lib.spin_system_set_launch(self._h, int(block), int(tile)))
+
+    def autotune(self, trial_steps: int = 20) -> dict:
+        info = B.SSInfo()
+        self._check(self._lib.spin_system_autotune(self._h, int(trial_steps), ctypes.byref(info)))
+        return info.as_dict()
+
+    def info(self) -> dict:
+        info = B.SSInfo()
+        self._check(self._lib.spin_system_info(self._h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def time_kernels(self, nsteps: int) -> dict:
+        """Real steps with CUDA events around every launch: mean predictor / corrector
+        launch time and mean step time, in ms."""
+        out = np.zeros(3)
+        self._check(self._lib.spin_system_time_kernels(self._h, int(nsteps), B.ptr(out)))
+        return {"predictor_ms": out[0], "corrector_ms": out[1], "step_ms": out[2]}
+
+    def set_barrier_test(self, extra: int, timeout_ns: int):
+        self._check(self._lib.spin_system_set_barrier_test(self._h, int(extra), int(timeout_ns)))
+
+    # -- stepping and state -----------------------------------------------------------
+    def step(self, n: int = 1):
+        self._check(self._lib.llg_heun_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._lib.spin_system_sync(self._h))
+
+    @property
+    def step_index(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self._lib.get_step(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    @step_index.setter
+    def step_index(self, step: int):
+        self._check(self._lib.set_step(self._h, int(step)))
+
+    def spins(self, out: np.ndarray | None = None) -> np.ndarray:
+        out = np.empty((self.n, 3)) if out is None else out
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 3 * self.n
+        self._check(self._lib.get_spins(self._h, B.ptr(out)))
+        return out
+
+    def set_spins(self, S: np.ndarray):
+        arr = np.ascontiguousarray(S, dtype=np.float64).reshape(self.n, 3)
+        self._check(self._lib.set_spins(self._h, B.ptr(arr)))
+
+    def spins_device(self):
+        """Zero-copy torch views (x, y, z) of the device spins, valid until the next step."""
+        import torch
+
+        px, py, pz = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        self._check(self._lib.get_spins_device(self._h, ctypes.byref(px), ctypes.byref(py), ctypes.byref(pz)))
+        ts = "<f4" if self.precision != "fp64" else "<f8"
+        return tuple(torch.as_tensor(_DeviceArray(p.value, self.n, ts), device="cuda") for p in (px, py, pz))
+
+    def magnetisation(self, sys: int = 0) -> np.ndarray:
+        out = np.zeros(4)
+        self._check(self._lib.get_magnetisation(self._h, int(sys), B.ptr(out)))
+        return out
+
+    def energy(self, sys: int = 0) -> np.ndarray:
+        out = np.zeros(4)
+        self._check(self._lib.get_energy(self._h, int(sys), B.ptr(out)))
+        return out
+
+    def record(self, first_step: int, count: int) -> np.ndarray:
+        """(count, num_systems, 8): sum mu S (3), sum mu, E_exc, E_ani, E_app, E_total."""
+        out = np.zeros((count, self.num_systems, 8))
+        self._check(self._lib.get_record(self._h, int(first_step), int(count), B.ptr(out)))
+        return out
+
+
+def debug_philox(ctr0, key, count: int) -> np.ndarray:
+    lib = B.load()
+    c = np.ascontiguousarray(ctr0, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros((count, 4), dtype=np.uint32)
+    B.check(lib.ss_debug_philox(B.ptr(c), B.ptr(k), int(count), B.ptr(out)))
+    return out
+
+
+def debug_gaussians(seed: int, sys_id: int, step: int, n: int, mode: int = 0) -> np.ndarray:
+    lib = B.load()
+    out = np.zeros((n, 3))
+    B.check(lib.ss_debug_gaussians(int(seed) & 0xFFFFFFFFFFFFFFFF, int(sys_id), int(step), int(n), int(mode),
+                                   B.ptr(out)))
+    return out
