@@ -124,7 +124,7 @@ __device__ __forceinline__ TurnSplit split_turn(uint32_t w) {
     const int32_t rho = (int32_t)(int64_t)(t - (q << 24));
     TurnSplit s;
     s.j = (uint32_t)q & 511u;
-    s.d = int_to_double(rho) * 7.3145904285217165e-10;  // 2 pi / 2^33
+    s.d = int_to_double(rho) * (6.283185307179586 / 8589934592.0);  // 2 pi / 2^33 (exact scaling)
     return s;
 }
 

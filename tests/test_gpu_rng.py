@@ -30,8 +30,9 @@ def test_gaussians_match_oracle(ss):
         ref = O.gaussians_bulk(seed, sys_id, step, n)
         err = np.abs(g - ref)
         assert err.max() <= 4e-15 * max(1.0, np.abs(ref).max()), err.max()
-        # relative to each value, away from the zeros of sin/cos
-        big = np.abs(ref) > 1e-3
+        # relative to each value, away from the zeros of sin/cos (where the absolute error
+        # of a few ulp of 1 dominates)
+        big = np.abs(ref) > 0.05
         assert (err[big] / np.abs(ref[big])).max() < 5e-14
 
 
