@@ -230,6 +230,57 @@ ss_status spin_system_sync(ss_system *h);
 ss_status ss_debug_philox(const uint32_t ctr0[4], const uint32_t key[2], int64_t count, uint32_t *out);
 ss_status ss_debug_gaussians(uint64_t seed, uint32_t sys_id, uint32_t step, int64_t n, int32_t mode, double *out);
 
+/* ---------------------------------------------------------------------------------
+ * Allocation-free stepping.  The paper has no counterpart of this entry point.
+ *
+ * Some callers cannot call cudaMalloc: code running inside a memory pool or arena that
+ * owns all device memory of the process, callers that must not allocate after start-up
+ * (real-time loops, allocators that forbid it during stream capture), or host code
+ * that receives device buffers from another runtime.  llg_heun_step_noalloc advances
+ * one FP64 system whose arrays the caller already holds in device memory, and keeps its
+ * working buffers (predictor spins, half steps, thermal field, reduction partials,
+ * Box-Muller tables) in one statically sized device array inside the library instead
+ * of allocating them.  It never calls cudaMalloc, cudaFree or any allocating library
+ * routine.
+ *
+ * Limits and behaviour:
+ *  - n <= SS_NOALLOC_MAX_SPINS (131072); larger systems are rejected with
+ *    SS_ERR_INVALID_ARG before any device work.  The static array holds 9.5 MB on every
+ *    GPU that loads the library, until the process exits.
+ *  - The first call on a device (the current device) finds the array's device address
+ *    and uploads the function tables with synchronous copies; make that first call
+ *    before any stream capture.  Later calls are asynchronous on `cuda_stream`.
+ *  - All calls share the one array, which keeps the last call's contents; each call
+ *    clears what must start at zero.  Calls whose work overlaps on the GPU (on
+ *    different streams or devices sharing no order) race on the array and give wrong
+ *    results: order them on one stream.
+ *  - The result equals llg_heun_step on a handle created from the same arrays with
+ *    precision SS_FP64 (same Philox stream, same Heun step, same reductions).
+ *  - Non-finite spins are not reported by this call; inspect the spins or the record.
+ * ------------------------------------------------------------------------------- */
+#define SS_NOALLOC_MAX_SPINS 131072
+
+typedef struct {
+    int64_t n;               /* spins, 1 <= n <= SS_NOALLOC_MAX_SPINS                   */
+    const int32_t *row_ptr;  /* device [n+1] CSR offsets, row_ptr[0] = 0                */
+    const int32_t *col;      /* device [nnz] neighbour indices in [0, n)                 */
+    const double *J;         /* device [nnz] exchange, J/link                             */
+    const double *mu_s;      /* device [n] atomic moments, J/T                            */
+    const double *k_u;       /* device [n] uniaxial anisotropy, J                         */
+    const double *easy_axis; /* device [3n] unit easy axes, AoS                           */
+    double *sx, *sy, *sz;    /* device [n] each: spins, read and overwritten (SoA)        */
+    double *record;          /* device [8 * nsteps] per-step record as in get_record, or
+                                NULL                                                    */
+    double alpha, dt, gamma; /* gamma 0 selects 1.76e11                                   */
+    double H_app[3];         /* T                                                         */
+    double T;                /* K                                                         */
+    uint64_t seed;
+    uint32_t sys_id;
+    int64_t step0;           /* index of the first step (Philox counter)                  */
+} ss_noalloc_step;
+
+ss_status llg_heun_step_noalloc(const ss_noalloc_step *p, int64_t nsteps, void *cuda_stream);
+
 /* Human-readable message of the last failure on this handle ("" if none). */
 const char *ss_last_error(ss_system *h);
 const char *ss_status_string(ss_status s);

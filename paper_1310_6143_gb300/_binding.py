@@ -28,6 +28,7 @@ EXPORTS = (
     "get_spins_device", "get_magnetisation", "get_energy", "get_record", "set_spins", "set_step", "get_step",
     "spin_system_set_exec", "spin_system_set_launch", "spin_system_autotune", "spin_system_info",
     "spin_system_set_barrier_test", "spin_system_sync", "spin_system_time_kernels", "ss_debug_philox", "ss_debug_gaussians",
+    "llg_heun_step_noalloc",
     "ss_last_error", "ss_status_string",
 )
 

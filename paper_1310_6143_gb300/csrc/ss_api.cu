@@ -22,8 +22,17 @@
 using namespace ss;
 
 namespace {
-
 thread_local std::string g_create_error;
+}  // namespace
+
+namespace ss {
+
+void set_global_error(const char *msg) { g_create_error = msg; }
+
+}  // namespace ss
+
+namespace {
+
 
 struct DevBuf {
     void *p = nullptr;

@@ -97,6 +97,9 @@ struct KArgs {
 constexpr unsigned int kErrNonFinite = 1u;
 constexpr unsigned int kErrTimeout = 2u;
 
+// Host helper (ss_api.cu): sets the message returned by ss_last_error(NULL).
+void set_global_error(const char *msg);
+
 // Launchers (ss_kernels_f32.cu / ss_kernels_f64.cu).
 template <typename R> cudaError_t launch_predictor(const KArgs<R> &a, int block, int grid, cudaStream_t s);
 template <typename R> cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s);
