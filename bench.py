@@ -9,7 +9,7 @@ energy reductions.  The state (~0.8 GB of working arrays) is far larger than L2,
 flush is needed between steps.
 
 Also reported: the same film in plain FP64, and the 256-grain batched ensemble in one
-persistent launch (FP32-mixed).  The CPU oracle (FP64, all host cores) is timed on a
+handle (FP32-mixed, launch shape picked by the autotuner).  The CPU oracle (FP64, all host cores) is timed on a
 bounded sample of the film for the CPU baseline.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under torchrun each
@@ -41,14 +41,24 @@ def pulse_T(nsteps, dt=1e-16, base=300.0, peak=1200.0, t0=1e-12, fwhm=100e-15):
     return base + (peak - base) * np.exp(-((t - t0) ** 2) / (2 * s * s))
 
 
-def film_bytes_per_spin(real_bytes, nnz_per_spin):
-    """Bytes each Heun pass must move per spin in this design:
-    predictor: read S, row offsets, columns + J, material index; write S', Q, H_th.
-    corrector: read S', Q, H_th, row offsets, columns + J, material index; write S."""
-    csr = 4 + nnz_per_spin * (4 + real_bytes)
-    pred = 3 * real_bytes + csr + 4 + 9 * real_bytes
-    corr = 9 * real_bytes + csr + 4 + 3 * real_bytes
-    return pred, corr
+# Algorithmic HBM bytes per spin-step of the two-pass Heun step with the CSR as stored
+# (read S, write S' and the half step, read them back, write S: 18 words; the CSR read
+# once per pass): 18 p + 2 (z (4 + p) + 4).  For the film (mean z = 5.875) this is 174 B
+# in FP32 and 293 B in FP64.
+def step_bytes_per_spin(real_bytes, nnz_per_spin):
+    return 18 * real_bytes + 2 * (nnz_per_spin * (4 + real_bytes) + 4)
+
+
+# FP64 pipe instructions per spin of one k_predictor launch of the FP32-mixed film in the
+# default launch shape (block 256, 4 spins per thread, back half of the Gaussians drawn
+# ahead by the corrector), from ncu (profiles/k_predictor_film1024x1024x16_fp32.md):
+# 9.81 DADD + 8.00 DMUL + 13.50 DFMA.  Each FP64 instruction takes one FMA slot of the
+# pipe (2 slots per cycle per SM), so it counts as 2 flop-equivalents, the convention of
+# the chip's FP64 rating.  DRAM traffic of that launch: 1.259 GB read + 0.579 GB written.
+PRED_FP64_INST_PER_SPIN = 9.81 + 8.00 + 13.50
+PRED_DRAM_BYTES = 1.259e9 + 0.579e9
+SMS = 152
+FP64_SLOTS_PER_SM_CYCLE = 2
 
 
 class Clocks:
@@ -237,6 +247,7 @@ def main():
             # end to end through the public API: per step the temperature goes host->device,
             # the step runs, and the step's moment/energy record comes back device->host
             e2e_steps = max(5, min(steps, 50))
+            s.set_exec("kernels")
             t0 = time.perf_counter()
             first = s.step_index
             for k in range(e2e_steps):
@@ -250,8 +261,11 @@ def main():
 
     ms32, kt32, e2e32, clk32, mag32, info32 = timed_run("fp32", args.steps, args.warmup, 5)
     value = world * lat.n * args.steps / (ms32 * 1e-3)
-    pred_b, corr_b = film_bytes_per_spin(4, nnz_per)
-    achieved = pred_b * lat.n / (kt32["predictor_ms"] * 1e-3) / 1e9
+    sm_ghz = (clk32.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))) / 1e3
+    fp64_peak = SMS * FP64_SLOTS_PER_SM_CYCLE * 2 * sm_ghz / 1e3  # TFLOP/s (FMA-slot flops)
+    achieved = 2 * PRED_FP64_INST_PER_SPIN * lat.n / (kt32["predictor_ms"] * 1e-3) / 1e12
+    step_b = step_bytes_per_spin(4, nnz_per)
+    hbm_achieved = step_b * lat.n / (ms32 / args.steps * 1e-3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -261,9 +275,13 @@ def main():
                    "precision": "fp32-mixed (FP64 Box-Muller and reductions)", "spins": lat.n, "nnz": lat.nnz,
                    "exec": "cuda graph", "block": info32["block"], "tile": info32["tile"],
                    "l2": "state 0.8 GB >> 126 MB L2, no flush needed", "replicas": world},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_predictor",
-                     "algorithmic_bytes_per_spin": pred_b, "peak_source": peak_src},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": PRED_DRAM_BYTES, "kernel": "k_predictor",
+                     "pipe": "fp64", "per_unit": f"{PRED_FP64_INST_PER_SPIN:.2f} FP64 instructions per spin, "
+                                                 "2 flop-equivalents each",
+                     "peak_source": f"152 SMs x 2 FP64 slots/cycle x 2 x {sm_ghz:.3f} GHz (measured clock)"},
+        "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                         "per_unit": f"{step_b:.1f} B per spin-step (whole step)", "peak_source": peak_src},
         "kernels_ms": kt32, "clocks": clk32,
         "e2e": {"value": world * lat.n / e2e32, "unit": "spin-steps/s", "h2d_bytes_per_step": 8,
                 "d2h_bytes_per_step": 64},
@@ -273,11 +291,30 @@ def main():
     if not args.no_extras:
         k64 = max(20, args.steps // 4)
         ms64, kt64, _, clk64, _, _ = timed_run("fp64", k64, args.warmup, 5)
-        pb64, _ = film_bytes_per_spin(8, nnz_per)
         out["fp64"] = {"value": world * lat.n * k64 / (ms64 * 1e-3), "unit": "spin-steps/s", "steps": k64,
                        "kernels_ms": kt64, "clocks": clk64,
-                       "predictor_GBps": pb64 * lat.n / (kt64["predictor_ms"] * 1e-3) / 1e9}
-        out["gpu_launches"] += 2 * k64
+                       "hbm_frac": step_bytes_per_spin(8, nnz_per) * lat.n / (ms64 / k64 * 1e-3) / 1e9 / hbm_peak}
+        # the batched form: 256 independent columnar grains (2,000-40,000 spins each, T
+        # uniform in 0-800 K) in one handle, launch shape chosen by the autotuner
+        grains, temps = L.grain_ensemble(count=256, seed=12345)
+        ng = sum(g.n for g in grains)
+        with SpinSystem(grains, alpha=0.1, dt=1e-16, T=list(temps), seed=[4000 + k for k in range(256)],
+                        sys_id=list(range(256)), precision="fp32", stream=stream) as b:
+            tuned = b.autotune(10)
+            b.step(args.warmup)
+            b.sync()
+            kb = max(50, args.steps // 2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(kb)
+            e1.record(stream)
+            e1.synchronize()
+            b.sync()
+            msb = e0.elapsed_time(e1)
+        out["batched"] = {"value": world * ng * kb / (msb * 1e-3), "unit": "spin-steps/s", "steps": kb,
+                          "systems": 256, "spins": ng, "ms_per_step": msb / kb,
+                          "exec": {0: "auto", 1: "kernels", 2: "graph", 3: "persistent"}[tuned["exec"]],
+                          "block": tuned["block"], "tile": tuned["tile"]}
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(lat, T)
     if rank == 0:

@@ -87,9 +87,14 @@ struct ss_system {
     int32_t *row_ptr = nullptr, *col = nullptr, *mat = nullptr, *sys_tiles = nullptr;
     void *J = nullptr, *mats = nullptr;
     void *state[12] = {};  // sx sy sz px py pz qx qy qz hx hy hz
+    void *ahead[3] = {};   // Gaussians drawn ahead by the corrector (FP32-mixed only)
+    int pre_slot = 1 << 30;
+    bool zero_T = true;    // some temperature in force could be zero (the corrector then
+                           // skips drawing those spins ahead)
     SysDesc *sys = nullptr;
     TileDesc *tiles = nullptr;
     double *partials = nullptr, *rec = nullptr, *cur = nullptr, *sched = nullptr;
+    float *sched_f = nullptr;
     int64_t rec_cap = 0, sched_len = 0, sched_step0 = 0, sched_cap = 0;
     unsigned long long *ctl = nullptr;  // [0] step, [1] err|ticket, [2] barrier count|gen
     double2 *tab = nullptr;             // log | ln2 | trig
@@ -253,7 +258,7 @@ ss_status validate(const ss_params *p, int idx) {
 void build_tables(std::vector<double2> &t) {
     t.resize(kLogTab + kLn2Tab + kTrigTab);
     for (int i = 0; i < kLogTab; ++i) {
-        const long double c = (long double)(192 + i) / 256.0L;
+        const long double c = (long double)(kLogFirst + i) / (long double)kLogScale;
         const double inv = (double)(1.0L / c);
         t[i] = make_double2(inv, (double)(-2.0L * logl((long double)inv)));
     }
@@ -289,12 +294,18 @@ KArgs<R> make_args(const ss_system *h) {
     a.px = s[3]; a.py = s[4]; a.pz = s[5];
     a.qx = s[6]; a.qy = s[7]; a.qz = s[8];
     a.hx = s[9]; a.hy = s[10]; a.hz = s[11];
+    a.gx = static_cast<R *>(h->ahead[0]);
+    a.gy = static_cast<R *>(h->ahead[1]);
+    a.gz = static_cast<R *>(h->ahead[2]);
+    a.g_step = h->ahead[0] ? h->ctl + 3 : nullptr;
+    a.pre_slot = h->pre_slot;
     a.partials = h->partials;
     a.rec = h->rec;
     a.rec_cap = h->rec_cap;
     a.cur = h->cur;
     a.step = h->ctl;
     a.sqrtT_sched = h->sched;
+    a.sqrtT_sched_f = h->sched_f;
     a.sched_len = h->sched_len;
     a.sched_step0 = h->sched_step0;
     a.err = reinterpret_cast<unsigned int *>(h->ctl + 1);
@@ -307,6 +318,14 @@ KArgs<R> make_args(const ss_system *h) {
     a.bar_extra = h->bar_extra;
     a.bar_timeout_ns = h->bar_timeout_ns;
     return a;
+}
+
+// Forget Gaussians drawn ahead: needed when the tile shape changes (the drawn slots depend
+// on it) and when a temperature that could have been zero becomes non-zero (the corrector
+// draws only where the next temperature is non-zero).  Gaussians do not depend on spins,
+// on the temperature's value or on the step counter itself.
+cudaError_t invalidate_ahead(ss_system *h) {
+    return cudaMemsetAsync(h->ctl + 3, 0xFF, sizeof(unsigned long long), h->stream);
 }
 
 void drop_graph(ss_system *h) {
@@ -449,6 +468,9 @@ ss_status build_tiles(ss_system *h) {
                                h->stream));
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
     h->nfin = std::max(1, std::min(h->nsys, 64));
+    const int slots = h->tile / h->block;
+    h->pre_slot = slots >= 2 ? slots - slots / 2 : 1 << 30;  // the corrector draws the back half ahead
+    SS_CUDA(h, invalidate_ahead(h));
     drop_graph(h);
     return SS_OK;
 }
@@ -552,6 +574,8 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     SS_CUDA(h, cudaMemcpyAsync(h->mats, mats.data(), mats.size() * sizeof(MatDesc<R>), cudaMemcpyHostToDevice,
                                h->stream));
     for (int b = 0; b < 12; ++b) SS_CUDA(h, dalloc(h, &h->state[b], (size_t)n * rs));
+    if (h->precision == SS_FP32_MIXED)
+        for (int b = 0; b < 3; ++b) SS_CUDA(h, dalloc(h, &h->ahead[b], (size_t)n * rs));
     // initial spins
     std::vector<R> s0((size_t)n), s1((size_t)n), s2((size_t)n);
     for (int s = 0; s < h->nsys; ++s) {
@@ -647,8 +671,12 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         d.key0 = (uint32_t)(p->seed & 0xffffffffull);
         d.key1 = (uint32_t)(p->seed >> 32);
         d.ctr2 = p->sys_id;
-        for (int c = 0; c < 3; ++c) d.H[c] = p->H_app[c];
+        for (int c = 0; c < 3; ++c) {
+            d.H[c] = p->H_app[c];
+            d.Hf[c] = (float)p->H_app[c];
+        }
         d.sqrtT = std::sqrt(p->T);
+        d.sqrtTf = (float)d.sqrtT;
         double ms = 0.0;
         for (int64_t i = 0; i < p->n; ++i) ms += p->mu_s[i];
         d.msum = ms;
@@ -687,6 +715,8 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         return cleanup(cuda_fail(h, e, "cudaMalloc"));
     st = h->precision == SS_FP32_MIXED ? upload_system<float>(h, hs) : upload_system<double>(h, hs);
     if (st != SS_OK) return cleanup(st);
+    // four spins per thread once the grid is many waves deep, one for small systems
+    h->tile = n >= (int64_t(1) << 20) ? 4 * h->block : h->block;
     st = build_tiles(h);
     if (st != SS_OK) return cleanup(st);
     st = h->precision == SS_FP32_MIXED ? init_random<float>(h, hs) : init_random<double>(h, hs);
@@ -788,17 +818,24 @@ ss_status set_field(ss_system *h, int32_t sys, const double H_app[3]) {
     if (sys >= h->nsys) return fail(h, SS_ERR_INVALID_ARG, "system %d out of range", sys);
     for (int s = 0; s < h->nsys; ++s) {
         if (sys >= 0 && s != sys) continue;
-        for (int c = 0; c < 3; ++c) h->hsys[s].H[c] = H_app[c];
-        SS_CUDA(h, cudaMemcpyAsync(&h->sys[s].H[0], &h->hsys[s].H[0], 3 * sizeof(double), cudaMemcpyHostToDevice,
-                                   h->stream));
+        for (int c = 0; c < 3; ++c) {
+            h->hsys[s].H[c] = H_app[c];
+            h->hsys[s].Hf[c] = (float)H_app[c];
+        }
+        SS_CUDA(h, cudaMemcpyAsync(&h->sys[s], &h->hsys[s], sizeof(SysDesc), cudaMemcpyHostToDevice, h->stream));
     }
     return SS_OK;
 }
 
 static ss_status upload_sqrtT(ss_system *h) {
-    for (int s = 0; s < h->nsys; ++s)
-        SS_CUDA(h, cudaMemcpyAsync(&h->sys[s].sqrtT, &h->hsys[s].sqrtT, sizeof(double), cudaMemcpyHostToDevice,
-                                   h->stream));
+    if (h->zero_T) SS_CUDA(h, invalidate_ahead(h));
+    h->zero_T = false;
+    for (auto &d : h->hsys) {
+        d.sqrtTf = (float)d.sqrtT;
+        h->zero_T = h->zero_T || d.sqrtT == 0.0;
+    }
+    SS_CUDA(h, cudaMemcpyAsync(h->sys, h->hsys.data(), h->hsys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice,
+                               h->stream));
     return SS_OK;
 }
 
@@ -835,21 +872,31 @@ ss_status set_temperature_schedule(ss_system *h, const double *T_per_step, int64
     if (st != SS_OK) return st;
     if (!T_per_step || nsteps < 1) return fail(h, SS_ERR_INVALID_ARG, "schedule needs at least one entry");
     std::vector<double> r((size_t)nsteps);
+    std::vector<float> rf((size_t)nsteps);
     for (int64_t k = 0; k < nsteps; ++k) {
         if (!(T_per_step[k] >= 0.0) || !std::isfinite(T_per_step[k]))
             return fail(h, SS_ERR_INVALID_ARG, "T_per_step[%lld] invalid", (long long)k);
         r[k] = std::sqrt(T_per_step[k]);
+        rf[k] = (float)r[k];
     }
     if (nsteps > h->sched_cap) {
         SS_CUDA(h, cudaStreamSynchronize(h->stream));
         if (h->sched) dfree(h, h->sched);
+        if (h->sched_f) dfree(h, h->sched_f);
         h->sched = nullptr;
+        h->sched_f = nullptr;
         h->sched_cap = 0;
         SS_CUDA(h, dalloc(h, (void **)&h->sched, (size_t)nsteps * sizeof(double)));
+        SS_CUDA(h, dalloc(h, (void **)&h->sched_f, (size_t)nsteps * sizeof(float)));
         h->sched_cap = nsteps;
+        drop_graph(h);
     }
     SS_CUDA(h, cudaMemcpyAsync(h->sched, r.data(), (size_t)nsteps * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->sched_f, rf.data(), (size_t)nsteps * sizeof(float), cudaMemcpyHostToDevice,
+                               h->stream));
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->zero_T) SS_CUDA(h, invalidate_ahead(h));
+    h->zero_T = std::any_of(r.begin(), r.end(), [](double v) { return v == 0.0; });
     if (h->sched_len != nsteps || h->sched_step0 != step0) drop_graph(h);
     h->sched_len = nsteps;
     h->sched_step0 = step0;

@@ -11,7 +11,9 @@ constexpr double kBoltzmann = 1.3807e-23;   // J/K
 constexpr double kGammaDefault = 1.76e11;   // 1/(T s)
 
 // Sizes of the Box-Muller function tables held in shared memory.
-constexpr int kLogTab = 193;   // centres c_t = (192 + t)/256, t = 0..192, covering [0.75, 1.5]
+constexpr int kLogTab = 769;   // centres c_t = (kLogFirst + t)/kLogScale, t = 0..768: [0.75, 1.5]
+constexpr int kLogFirst = 768;
+constexpr int kLogScale = 1024;
 constexpr int kLn2Tab = 34;    // 2 n ln 2, n = 0..33, as (hi, lo)
 constexpr int kTrigTab = 512;  // (sin, cos) of 2 pi j / 512
 constexpr int kRecComps = 8;   // record: sum mu S (3), sum mu, E_exc, E_ani, E_app, E_total
@@ -28,6 +30,8 @@ struct SysDesc {
     double H[3];         // applied field, T
     double sqrtT;        // square root of the temperature, sqrt(K)
     double msum;         // sum of mu_s over the system, J/T
+    float Hf[3];         // H rounded to float (FP32-mixed field arithmetic)
+    float sqrtTf;        // sqrtT rounded to float
 };
 
 // One material: a distinct (system, mu_s, k_u, easy axis, Neel tensor) combination.
@@ -75,12 +79,17 @@ struct KArgs {
     R *px, *py, *pz;          // S' (predictor, renormalised)
     R *qx, *qy, *qz;          // S + dt/2 dS (predictor half step)
     R *hx, *hy, *hz;          // thermal field of the current step
+    R *gx, *gy, *gz;          // Gaussians of the next step drawn by the corrector (FP32-mixed)
+    unsigned long long *g_step; // step whose Gaussians gx..gz hold (tile slots >= pre_slot)
+    int pre_slot;             // first tile slot (spin k of a tile: slot k / block) whose
+                              // Gaussians the corrector draws ahead; >= slots: none
     double *partials;         // [ntiles * kPartComps]
     double *rec;              // ring [rec_cap][nsys][kRecComps]
     int64_t rec_cap;
     double *cur;              // [nsys][kRecComps] on-demand measurement
     unsigned long long *step; // index of the next step
     const double *sqrtT_sched;
+    const float *sqrtT_sched_f;  // the schedule rounded to float
     int64_t sched_len;
     int64_t sched_step0;
     unsigned int *err;        // bit 0: non-finite spin, bit 1: barrier timeout

@@ -40,6 +40,18 @@ __device__ __forceinline__ T ld(const T *p) {
     }
 }
 
+// Working-type views of the system's double-precision parameters and of FP64 results:
+// the FP32-mixed form reads float copies prepared on the host and converts with integer
+// bit operations, so that the narrow FP64 pipe only runs the Box-Muller transform and the
+// reduction sums.
+__device__ __forceinline__ float sys_H(const SysDesc &sd, int c, float) { return sd.Hf[c]; }
+__device__ __forceinline__ double sys_H(const SysDesc &sd, int c, double) { return sd.H[c]; }
+__device__ __forceinline__ double widen(float v) { return f2d_bits(v); }
+__device__ __forceinline__ double widen(double v) { return v; }
+template <typename R> __device__ __forceinline__ R narrow(double v);
+template <> __device__ __forceinline__ float narrow<float>(double v) { return d2f_bits(v); }
+template <> __device__ __forceinline__ double narrow<double>(double v) { return v; }
+
 template <typename R>
 __device__ __forceinline__ R rsqrt_r(R x);
 template <>
@@ -94,9 +106,9 @@ __device__ __forceinline__ void det_field(const MatDesc<R> &m, const SysDesc &sd
     H0 = fma(an, m.e[0], H0);
     H1 = fma(an, m.e[1], H1);
     H2 = fma(an, m.e[2], H2);
-    H0 += (R)sd.H[0];
-    H1 += (R)sd.H[1];
-    H2 += (R)sd.H[2];
+    H0 += sys_H(sd, 0, R());
+    H1 += sys_H(sd, 1, R());
+    H2 += sys_H(sd, 2, R());
     if (m.has_neel) {
         H0 += m.kf[0] * s0 + m.kf[3] * s1 + m.kf[4] * s2;
         H1 += m.kf[3] * s0 + m.kf[1] * s1 + m.kf[5] * s2;
@@ -123,18 +135,18 @@ template <typename R>
 __device__ __forceinline__ void spin_terms(const MatDesc<R> &m, const SysDesc &sd, R s0, R s1, R s2, R e0, R e1,
                                            R e2, double v[6]) {
     const R mu = m.mu;
-    v[0] = (double)(mu * s0);
-    v[1] = (double)(mu * s1);
-    v[2] = (double)(mu * s2);
-    v[3] = (double)((R)-0.5 * (s0 * e0 + s1 * e1 + s2 * e2));
+    v[0] = widen(mu * s0);
+    v[1] = widen(mu * s1);
+    v[2] = widen(mu * s2);
+    v[3] = widen((R)-0.5 * (s0 * e0 + s1 * e1 + s2 * e2));
     const R sde = s0 * m.e[0] + s1 * m.e[1] + s2 * m.e[2];
     R ea = -m.ku * sde * sde;
     if (m.has_neel) {
         ea -= m.K[0] * s0 * s0 + m.K[1] * s1 * s1 + m.K[2] * s2 * s2
             + (R)2 * (m.K[3] * s0 * s1 + m.K[4] * s0 * s2 + m.K[5] * s1 * s2);
     }
-    v[4] = (double)ea;
-    v[5] = (double)(-mu * (s0 * (R)sd.H[0] + s1 * (R)sd.H[1] + s2 * (R)sd.H[2]));
+    v[4] = widen(ea);
+    v[5] = widen(-mu * (s0 * sys_H(sd, 0, R()) + s1 * sys_H(sd, 1, R()) + s2 * sys_H(sd, 2, R())));
 }
 
 // Sum of eight FP64 values over a warp by a transposing butterfly: 9 additions per lane
@@ -187,24 +199,27 @@ __device__ __forceinline__ double block_sum8(const double v[8], double *red) {
     return r;
 }
 
-__device__ __forceinline__ double sqrtT_of_step(const double *sched, int64_t len, int64_t step0, uint64_t step,
-                                                double sqrtT_sys) {
-    if (len <= 0) return sqrtT_sys;
-    int64_t k = (int64_t)step - step0;
-    k = k < 0 ? 0 : (k >= len ? len - 1 : k);
-    return sched[k];
+// sqrt(T) of a step in the working type: the schedule entry when a schedule is set.
+template <typename R>
+__device__ __forceinline__ R sqrtT_of_step(const KArgs<R> &a, uint64_t step, const SysDesc &sd) {
+    const bool f32 = sizeof(R) == 4;
+    if (a.sched_len <= 0) return f32 ? (R)sd.sqrtTf : (R)sd.sqrtT;
+    int64_t k = (int64_t)step - a.sched_step0;
+    k = k < 0 ? 0 : (k >= a.sched_len ? a.sched_len - 1 : k);
+    return f32 ? (R)a.sqrtT_sched_f[k] : (R)a.sqrtT_sched[k];
 }
 
 // Predictor over one tile.  Writes S', Q and H_th; returns the tile's partial sums
 // (valid in threads 0..7).
 template <typename R, int BS, bool Coherent>
 __device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
-                                                 const SmemTables &tab, double *red) {
+                                                 const SmemTables &tab, double *red, int pre_slot) {
     const SysDesc &sd = a.sys[td.sys];
-    const double sqrtT = sqrtT_of_step(a.sqrtT_sched, a.sched_len, a.sched_step0, step, sd.sqrtT);
+    const R sqrtT = sqrtT_of_step(a, step, sd);
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     bool first = true;
-    for (int k = threadIdx.x; k < td.count; k += BS) {
+    int slot = 0;
+    for (int k = threadIdx.x; k < td.count; k += BS, ++slot) {
         const int64_t i = td.start + k;
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = ld<Coherent>(a.sx + i), s1 = ld<Coherent>(a.sy + i), s2 = ld<Coherent>(a.sz + i);
@@ -213,14 +228,21 @@ __device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDe
         R H0, H1, H2;
         det_field(m, sd, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         R t0 = 0, t1 = 0, t2 = 0;
-        if (sqrtT > 0.0) {
-            const Philox4 w = philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
-            double g0, g1, g2;
-            box_muller3(w, tab.log_, tab.ln2, tab.trig, g0, g1, g2);
-            const R sig = m.sig * (R)sqrtT;
-            t0 = sig * (R)g0;
-            t1 = sig * (R)g1;
-            t2 = sig * (R)g2;
+        if (sqrtT > (R)0) {
+            const R sig = m.sig * sqrtT;
+            if (slot >= pre_slot) {  // drawn ahead by the previous corrector
+                t0 = sig * ld<Coherent>(a.gx + i);
+                t1 = sig * ld<Coherent>(a.gy + i);
+                t2 = sig * ld<Coherent>(a.gz + i);
+            } else {
+                const Philox4 w =
+                    philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
+                double g0, g1, g2;
+                box_muller3(w, tab.log_, tab.ln2, tab.trig, g0, g1, g2);
+                t0 = sig * narrow<R>(g0);
+                t1 = sig * narrow<R>(g1);
+                t2 = sig * narrow<R>(g2);
+            }
         }
         a.hx[i] = t0;
         a.hy[i] = t1;
@@ -255,9 +277,14 @@ __device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDe
 }
 
 template <typename R, int BS, bool Coherent>
-__device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc &td) {
+__device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
+                                               const SmemTables *tab) {
     const SysDesc &sd = a.sys[td.sys];
-    for (int k = threadIdx.x; k < td.count; k += BS) {
+    // Gaussians of step + 1 for the slots the next predictor will not draw (FP32-mixed):
+    // this puts FP64 transform work next to the corrector's memory traffic.
+    const R sqrtT_next = tab ? sqrtT_of_step(a, step + 1, sd) : (R)0;
+    int slot = 0;
+    for (int k = threadIdx.x; k < td.count; k += BS, ++slot) {
         const int64_t i = td.start + k;
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = ld<Coherent>(a.px + i), s1 = ld<Coherent>(a.py + i), s2 = ld<Coherent>(a.pz + i);
@@ -279,6 +306,15 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
         a.sx[i] = v0 * inv;
         a.sy[i] = v1 * inv;
         a.sz[i] = v2 * inv;
+        if (slot >= a.pre_slot && sqrtT_next > (R)0) {
+            const Philox4 w =
+                philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)(step + 1), sd.ctr2, 0u, sd.key0, sd.key1);
+            double g0, g1, g2;
+            box_muller3(w, tab->log_, tab->ln2, tab->trig, g0, g1, g2);
+            a.gx[i] = narrow<R>(g0);
+            a.gy[i] = narrow<R>(g1);
+            a.gz[i] = narrow<R>(g2);
+        }
     }
 }
 
@@ -321,16 +357,18 @@ __global__ void __launch_bounds__(BS) k_predictor(const KArgs<R> a) {
     stage_tables(a, tab);
     __syncthreads();
     const uint64_t step = *a.step;
+    // Gaussians drawn ahead are valid only if the previous corrector ran for this step.
+    const int pre_slot = (a.g_step != nullptr && *a.g_step == step) ? a.pre_slot : 1 << 30;
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDesc td = a.tiles[t];
-        const double r = predictor_tile<R, BS, false>(a, td, step, tab, red);
+        const double r = predictor_tile<R, BS, false>(a, td, step, tab, red, pre_slot);
         if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
     }
 }
 
 // Blocks [0, nfin) sum the predictor's tile partials into the record ring; the rest run
 // the corrector over the tiles.  The last block to finish advances the step counter.
-template <typename R, int BS>
+template <typename R, int BS, bool DrawAhead>
 __global__ void __launch_bounds__(BS) k_corrector(const KArgs<R> a, int nfin) {
     __shared__ double red[(BS / 32) * 8];
     const uint64_t step = *a.step;
@@ -339,9 +377,16 @@ __global__ void __launch_bounds__(BS) k_corrector(const KArgs<R> a, int nfin) {
             double *dst = a.rec + ((int64_t)(step % (uint64_t)a.rec_cap) * a.nsys + s) * kRecComps;
             finalize_system<BS, false>(a.sys, a.sys_tiles, a.partials, s, dst, red);
         }
+    } else if constexpr (DrawAhead) {
+        __shared__ SmemTables tab;
+        stage_tables(a, tab);
+        __syncthreads();
+        const int64_t nb = gridDim.x - nfin;
+        for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb) corrector_tile<R, BS, false>(a, a.tiles[t], step, &tab);
     } else {
         const int64_t nb = gridDim.x - nfin;
-        for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb) corrector_tile<R, BS, false>(a, a.tiles[t]);
+        for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb)
+            corrector_tile<R, BS, false>(a, a.tiles[t], step, nullptr);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -349,6 +394,7 @@ __global__ void __launch_bounds__(BS) k_corrector(const KArgs<R> a, int nfin) {
         const unsigned int done = atomicAdd(a.ticket, 1u);
         if (done == gridDim.x - 1) {
             *a.ticket = 0u;
+            if (DrawAhead) *a.g_step = step + 1ull;
             *a.step = step + 1ull;
             __threadfence();
         }
@@ -459,7 +505,7 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
         const uint64_t step = step0 + (uint64_t)k;
         for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
             const TileDesc td = a.tiles[t];
-            const double r = predictor_tile<R, BS, true>(a, td, step, tab, red);
+            const double r = predictor_tile<R, BS, true>(a, td, step, tab, red, 1 << 30);
             if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
         }
         if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
@@ -469,7 +515,8 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
                 finalize_system<BS, true>(a.sys, a.sys_tiles, a.partials, s, dst, red);
             }
         }
-        for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) corrector_tile<R, BS, true>(a, a.tiles[t]);
+        for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x)
+            corrector_tile<R, BS, true>(a, a.tiles[t], step, nullptr);
         if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.step = step0 + (uint64_t)nsteps;

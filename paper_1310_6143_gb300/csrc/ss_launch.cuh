@@ -22,7 +22,11 @@ cudaError_t launch_predictor(const KArgs<R> &a, int block, int grid, cudaStream_
 
 template <typename R>
 cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s) {
-    SS_BLOCK_SWITCH(block, k_corrector<R, BS><<<grid + nfin, BS, 0, s>>>(a, nfin));
+    if (a.g_step != nullptr) {
+        SS_BLOCK_SWITCH(block, k_corrector<R, BS, true><<<grid + nfin, BS, 0, s>>>(a, nfin));
+    } else {
+        SS_BLOCK_SWITCH(block, k_corrector<R, BS, false><<<grid + nfin, BS, 0, s>>>(a, nfin));
+    }
     return cudaGetLastError();
 }
 

@@ -13,22 +13,25 @@
 //   * -2 ln u by Tang's table-driven method (P. T. P. Tang, "Table-driven implementation
 //     of the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16, 1990):
 //     u = 2^-n f with f in [0.75, 1.5) taken exactly from the integer 2w+1; f is reduced
-//     against the nearest table centre c = k/256 through r = f (1/c) - 1 (one FMA, so
+//     against the nearest table centre c = k/1024 through r = f (1/c) - 1 (one FMA, so
 //     the table's rounded 1/c defines the split exactly), and
-//     -2 ln u = 2 n ln 2 - 2 ln c - 2 log1p(r), with log1p(r) the Taylor series to r^6
-//     (|r| < 2^-8.4, truncation below 2^-60 relative).  Near u = 1 (n = 0, c = 1) the
-//     result is -2 log1p(r) with r exact, so it keeps full relative accuracy.
-//   * sqrt by two coupled Newton (Goldschmidt) iterations from the single-precision
-//     reciprocal square root, each squaring the relative error (2^-21 -> 2^-42 -> 2^-84).
+//     -2 ln u = 2 n ln 2 - 2 ln c - 2 log1p(r), with log1p(r) the Taylor series to r^5
+//     (|r| < 1.31e-3; the dropped r^6/3 term is below 1.7e-18 in absolute value, which
+//     is below 2^-53 of the result except within 1.3e-3 of u = 1, where the result is
+//     small and its square root carries an absolute error below 2e-17).
+//   * sqrt from a reciprocal square root refined to about 2^-45 in single precision with
+//     error-free float products, then one coupled Newton (Goldschmidt) step in FP64.
 //   * sin/cos of 2 pi t / 2^33 (t = 2w+1, an exact binary angle) by the nearest of 512
 //     table angles a and the remainder d = 2 pi rho / 2^33, |d| <= pi/512:
-//     sin(a+d) = sin a + (sin a (cos d - 1) + cos a sin d), and likewise for cos, with
-//     sin d, cos d - 1 from their Taylor series (errors below 2^-56).
+//     sin(a+d) = cos a sin d + sin a cos d, cos(a+d) = cos a cos d - sin a sin d, with
+//     sin d and cos d from their Taylor series (truncation below 2^-56).
 // All results are within a few units in the last place of the correctly rounded values;
 // the tests compare them with CUDA's own log, sqrt and sincospi and with the CPU oracle.
 #pragma once
 
 #include <stdint.h>
+
+#include "ss_internal.h"
 
 namespace ss {
 
@@ -58,6 +61,28 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
     return Philox4{c0, c1, c2, c3};
 }
 
+// Exact float -> double from the bits (no FP64 instruction).  Subnormal floats become
+// signed zero; infinities and NaN keep their class.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    const uint32_t E = e == 0xFFu ? 0x7FFu : e + 896u;
+    const uint32_t hi = (b & 0x80000000u) | (e ? (E << 20) | ((b & 0x7FFFFFu) >> 3) : 0u);
+    const uint32_t lo = e ? b << 29 : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// double -> float rounded to nearest-even, from the bits, for finite non-zero x with
+// 2^-126 <= |x| < 2^127 (no FP64 instruction).
+__device__ __forceinline__ float d2f_bits(double x) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const uint32_t e = (uint32_t)((b >> 52) & 0x7FFu) - 896u;
+    const uint64_t m = b & 0x000FFFFFFFFFFFFFull;
+    const uint64_t mr = (m + 0x0FFFFFFFull + ((m >> 29) & 1ull)) >> 29;  // may carry into the exponent
+    return __uint_as_float(sign | ((e << 23) + (uint32_t)mr));
+}
+
 // -2 ln((w + 1/2) 2^-32).  tab_log[t] = (1/c_t rounded, -2 ln(that rounded value)),
 // tab_ln2[n] = 2 n ln 2 as (hi, lo).
 __device__ __forceinline__ double neg2log_u(uint32_t w, const double2 *tab_log, const double2 *tab_ln2) {
@@ -69,47 +94,55 @@ __device__ __forceinline__ double neg2log_u(uint32_t w, const double2 *tab_log, 
     const int n = 33 - k - (big ? 1 : 0);            // u = 2^-n f'
     const uint64_t ebits = big ? (1022ull << 52) : (1023ull << 52);
     const double fp = __longlong_as_double((long long)(ebits | frac));    // f' in [0.75, 1.5)
-    // nearest centre c = j/256: j = round(256 f')
-    const uint32_t j = big ? (uint32_t)(128u + (uint32_t)((frac + (1ull << 44)) >> 45))
-                           : (uint32_t)(256u + (uint32_t)((frac + (1ull << 43)) >> 44));
-    const double2 tl = tab_log[j - 192u];
+    // nearest centre c = j/1024: j = round(1024 f')
+    const uint32_t j = big ? (uint32_t)(512u + (uint32_t)((frac + (1ull << 42)) >> 43))
+                           : (uint32_t)(1024u + (uint32_t)((frac + (1ull << 41)) >> 42));
+    const double2 tl = tab_log[j - (uint32_t)kLogFirst];
     const double2 tn = tab_ln2[n];
     const double r = fma(fp, tl.x, -1.0);            // f'/c - 1 up to one rounding
     const double r2 = r * r;
-    // 2 log1p(r) = 2r - r^2 + (2/3) r^3 - (1/2) r^4 + (2/5) r^5 - (1/3) r^6
-    double t = fma(r, -1.0 / 3.0, 0.4);
-    t = fma(r, t, -0.5);
+    // 2 log1p(r) = 2r - r^2 + (2/3) r^3 - (1/2) r^4 + (2/5) r^5 = 2r + r^2 t
+    double t = fma(r, 0.4, -0.5);
     t = fma(r, t, 2.0 / 3.0);
     t = fma(r, t, -1.0);
-    const double p2 = fma(r2, t, r + r);
-    const double a = tn.x - tl.y;                    // 2 n ln2 - 2 ln c (leading part)
-    return a + (tn.y - p2);
+    const double b = fma(-2.0, r, fma(-r2, t, tn.y));  // lo part of 2 n ln 2 - 2 log1p(r)
+    return (tn.x - tl.y) + b;                          // + 2 n ln 2 - 2 ln c (leading part)
 }
 
-// sqrt(x) for 1e-30 < x < 1e30.
+// sqrt(x) for 2^-100 < x < 2^100.  The reciprocal square root is first refined in
+// single precision carried as a float pair: x = xh + xl (both taken from the bits of x),
+// y0 = rsqrtf(xh), r = 1 - x y0^2 evaluated with error-free products, and
+// y = y0 (1 + r/2 + 3r^2/8) ~ 1/sqrt(x) to about 2^-45.  One FP64 Goldschmidt step then
+// gives sqrt(x) to about one ulp: four FP64 instructions in all.
 __device__ __forceinline__ double sqrt_pos(double x) {
-    // single-precision seed from the high word (exponent rebiased, mantissa truncated)
-    const int hi = __double2hiint(x);
-    const int fe = ((hi >> 20) & 0x7FF) - 1023 + 127;
-    const float xf = __int_as_float((fe << 23) | ((hi & 0xFFFFF) << 3));
-    const float yf = rsqrtf(xf);
-    const int yb = __float_as_int(yf);
-    const int ye = ((yb >> 23) & 0xFF) - 127 + 1023;
-    const double y = __hiloint2double((ye << 20) | ((yb & 0x7FFFFF) >> 3), (yb & 7) << 29);
-    // Goldschmidt: s -> sqrt(x), h -> 1/(2 sqrt(x))
-    double s = x * y;
-    double h = __hiloint2double(((ye - 1) << 20) | ((yb & 0x7FFFFF) >> 3), (yb & 7) << 29);  // y/2
-    double e = fma(-s, h, 0.5);
-    s = fma(s, e, s);
-    h = fma(h, e, h);
-    e = fma(-s, h, 0.5);
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    const float xh = __uint_as_float(((uint32_t)(E - 896) << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
+    const float scale = __uint_as_float((uint32_t)(E - 1075 + 127) << 23);  // 2^(E - 1075)
+    const float xl = __int2float_rn((int)(b & 0x1FFFFFFFu)) * scale;          // x - xh to 2^-48 x
+    const float y0 = rsqrtf(xh);
+    const float p = y0 * y0;
+    const float q = fmaf(y0, y0, -p);        // y0^2 = p + q exactly
+    const float P = xh * p;
+    const float Pe = fmaf(xh, p, -P);        // xh p = P + Pe exactly
+    const float r = ((1.0f - P) - Pe) - fmaf(xh, q, xl * p);
+    const float yl = y0 * (r * fmaf(0.375f, r, 0.5f));
+    const double y = f2d_bits(y0) + f2d_bits(yl);
+    const double s = x * y;
+    const uint64_t yb = (uint64_t)__double_as_longlong(y);
+    const double h = __longlong_as_double((long long)(yb - (1ull << 52)));  // y / 2
+    const double e = fma(-s, h, 0.5);
     return fma(s, e, s);
 }
 
-// Exact int32 -> double through the 2^52 + 2^31 bias (one FP64 add).
+// Exact int32 -> double for v != 0, assembled from the integer bits (no FP64 instruction).
 __device__ __forceinline__ double int_to_double(int32_t v) {
-    const double biased = __hiloint2double(0x43300000, (int)((uint32_t)v ^ 0x80000000u));
-    return biased - 4503601774854144.0;  // 2^52 + 2^31
+    const uint32_t sign = (uint32_t)v & 0x80000000u;
+    const uint32_t a = v < 0 ? (uint32_t)(-v) : (uint32_t)v;
+    const int k = 31 - __clz(a);                                   // a in [2^k, 2^(k+1))
+    const uint64_t m = ((uint64_t)a << (52 - k)) & 0x000FFFFFFFFFFFFFull;
+    const uint64_t bits = ((uint64_t)sign << 32) | ((uint64_t)(1023 + k) << 52) | m;
+    return __longlong_as_double((long long)bits);
 }
 
 // Reduction of the binary angle 2 pi (2w+1) / 2^33 to a table angle and a remainder.
@@ -121,7 +154,7 @@ struct TurnSplit {
 __device__ __forceinline__ TurnSplit split_turn(uint32_t w) {
     const uint64_t t = 2ull * w + 1ull;
     const uint64_t q = (t + (1ull << 23)) >> 24;     // nearest multiple of 2^24
-    const int32_t rho = (int32_t)(int64_t)(t - (q << 24));
+    const int32_t rho = (int32_t)(int64_t)(t - (q << 24));  // odd, so never zero
     TurnSplit s;
     s.j = (uint32_t)q & 511u;
     s.d = int_to_double(rho) * (6.283185307179586 / 8589934592.0);  // 2 pi / 2^33 (exact scaling)
@@ -133,10 +166,10 @@ __device__ __forceinline__ void sincos_turn(uint32_t w, const double2 *tab_trig,
     const double d = ts.d;
     const double d2 = d * d;
     const double sd = fma(d2 * d, fma(d2, 1.0 / 120.0, -1.0 / 6.0), d);  // sin d
-    const double cm1 = d2 * fma(d2, 1.0 / 24.0, -0.5);                     // cos d - 1
+    const double cd = fma(d2, fma(d2, 1.0 / 24.0, -0.5), 1.0);             // cos d
     const double2 sc = tab_trig[ts.j];
-    sv = sc.x + fma(sc.y, sd, sc.x * cm1);
-    cv = sc.y + fma(-sc.x, sd, sc.y * cm1);
+    sv = fma(sc.y, sd, sc.x * cd);
+    cv = fma(-sc.x, sd, sc.y * cd);
 }
 
 __device__ __forceinline__ double cos_turn(uint32_t w, const double2 *tab_trig) {
@@ -144,10 +177,11 @@ __device__ __forceinline__ double cos_turn(uint32_t w, const double2 *tab_trig) 
     const double d = ts.d;
     const double d2 = d * d;
     const double sd = fma(d2 * d, fma(d2, 1.0 / 120.0, -1.0 / 6.0), d);
-    const double cm1 = d2 * fma(d2, 1.0 / 24.0, -0.5);
+    const double cd = fma(d2, fma(d2, 1.0 / 24.0, -0.5), 1.0);
     const double2 sc = tab_trig[ts.j];
-    return sc.y + fma(-sc.x, sd, sc.y * cm1);
+    return fma(-sc.x, sd, sc.y * cd);
 }
+
 
 // Three standard Gaussians of one Philox block (project transform, see the file header).
 __device__ __forceinline__ void box_muller3(const Philox4 &w, const double2 *tab_log, const double2 *tab_ln2,

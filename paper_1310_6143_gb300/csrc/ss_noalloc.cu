@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kNaBlock) k_na_corrector(const NaArgs a) {
 // Box-Muller function tables, as the handle-based path builds them.
 void na_fill_tables(double2 *t) {
     for (int i = 0; i < kLogTab; ++i) {
-        const long double c = (long double)(192 + i) / 256.0L;
+        const long double c = (long double)(kLogFirst + i) / (long double)kLogScale;
         const double inv = (double)(1.0L / c);
         t[i] = make_double2(inv, (double)(-2.0L * logl((long double)inv)));
     }
