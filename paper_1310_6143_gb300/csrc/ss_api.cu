@@ -106,10 +106,13 @@ struct ss_system {
     int nfin = 1;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
+    cudaGraphExec_t pgraph = nullptr;  // captured persistent launch (barrier reset + kernel)
+    long long pgraph_steps = 0;
+    bool pgraph_failed = false;
     bool graph_failed = false;
     unsigned int bar_extra = 0;
     long long bar_timeout_ns = 2000000000ll;
-    long long persist_chunk = 4096;
+    long long persist_chunk = 64;  // steps per persistent launch
 };
 
 namespace {
@@ -332,6 +335,9 @@ void drop_graph(ss_system *h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     h->graph_steps = 0;
+    if (h->pgraph) cudaGraphExecDestroy(h->pgraph);
+    h->pgraph = nullptr;
+    h->pgraph_steps = 0;
 }
 
 int step_grid(const ss_system *h) {
@@ -391,6 +397,38 @@ cudaError_t enqueue_persist(ss_system *h, int64_t n) {
     return h->precision == SS_FP32_MIXED ? enqueue_persistent<float>(h, n) : enqueue_persistent<double>(h, n);
 }
 
+// The persistent launch of `persist_chunk` steps (barrier reset + cooperative kernel),
+// captured once into a CUDA graph and replayed.  Returns an error if capture is refused;
+// the caller then launches directly.
+cudaError_t persistent_graph_run(ss_system *h, int64_t &n) {
+    const long long k = h->persist_chunk;
+    if (n < k) return cudaSuccess;
+    if (!h->pgraph) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaError_t ek = enqueue_persist(h, k);
+        e = cudaStreamEndCapture(h->stream, &g);
+        if (ek != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return ek != cudaSuccess ? ek : e;
+        }
+        e = cudaGraphInstantiate(&h->pgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->pgraph = nullptr;
+            return e;
+        }
+        h->pgraph_steps = k;
+    }
+    while (n >= h->pgraph_steps) {
+        cudaError_t e = cudaGraphLaunch(h->pgraph, h->stream);
+        if (e != cudaSuccess) return e;
+        n -= h->pgraph_steps;
+    }
+    return cudaSuccess;
+}
+
 int graph_len(const ss_system *h) {
     // enough steps per graph that the launch cost is amortised, few enough that capture
     // stays cheap
@@ -430,9 +468,12 @@ ss_status check_device_flags(ss_system *h) {
         const unsigned long long zero[3] = {ctl[0], 0ull, 0ull};
         SS_CUDA(h, cudaMemcpyAsync(h->ctl, zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream));
         SS_CUDA(h, cudaStreamSynchronize(h->stream));
-        if (err & kErrTimeout)
+        if (err & kErrTimeout) {
+            SS_CUDA(h, invalidate_ahead(h));  // an aborted launch may have drawn part of a step
+            SS_CUDA(h, cudaStreamSynchronize(h->stream));
             return fail(h, SS_ERR_TIMEOUT, "grid barrier of the persistent kernel timed out; step counter at %lld",
                         (long long)h->step);
+        }
         return fail(h, SS_ERR_NONFINITE, "a spin became non-finite (NaN/inf or zero length)");
     }
     return SS_OK;
@@ -930,7 +971,17 @@ ss_status llg_heun_step(ss_system *h, int64_t n) {
         }
         e = enqueue_kernels(h, left);
     } else if (mode == SS_EXEC_PERSISTENT) {
-        e = enqueue_persist(h, n);
+        int64_t left = n;
+        if (!h->pgraph_failed) {
+            e = persistent_graph_run(h, left);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                h->pgraph_failed = true;  // capture refused: launch directly from now on
+                left = n;
+                e = cudaSuccess;
+            }
+        }
+        if (e == cudaSuccess && left > 0) e = enqueue_persist(h, left);
         if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
             cudaGetLastError();
             return fail(h, SS_ERR_UNSUPPORTED, "persistent launch not possible: %s", cudaGetErrorString(e));

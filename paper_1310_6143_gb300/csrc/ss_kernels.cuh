@@ -57,7 +57,14 @@ __device__ __forceinline__ R rsqrt_r(R x);
 template <>
 __device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
 template <>
-__device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
+__device__ __forceinline__ double rsqrt_r<double>(double x) {
+    // |v|^2 of a renormalised spin plus a small step: well inside the range of rsqrt_pos
+    return rsqrt_pos(x);
+}
+
+// True when the reciprocal length of a renormalised spin is NaN or infinite.
+__device__ __forceinline__ bool bad_inv(float v) { return !(v < 3.0e38f); }
+__device__ __forceinline__ bool bad_inv(double v) { return ((__double2hiint(v) >> 20) & 0x7FF) == 0x7FF; }
 
 // Shared-memory copies of the Box-Muller function tables.
 struct SmemTables {
@@ -302,7 +309,7 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
         const R v1 = fma(hdt, d1, ld<Coherent>(a.qy + i));
         const R v2 = fma(hdt, d2, ld<Coherent>(a.qz + i));
         const R inv = rsqrt_r(v0 * v0 + v1 * v1 + v2 * v2);
-        if (!(inv < (R)3.0e38)) atomicOr(a.err, kErrNonFinite);  // NaN, inf or zero length
+        if (bad_inv(inv)) atomicOr(a.err, kErrNonFinite);  // NaN or infinite length
         a.sx[i] = v0 * inv;
         a.sy[i] = v1 * inv;
         a.sz[i] = v2 * inv;
@@ -492,7 +499,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int *
 }
 
 // Many steps in one cooperative launch: predictor phase, barrier, corrector phase (with
-// the record of the step summed by blocks [0, nfin)), barrier.
+// the record of the step summed by blocks [0, nfin), and in the FP32-mixed form the back
+// half of the next step's Gaussians drawn ahead), barrier.
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, long long nsteps) {
     __shared__ SmemTables tab;
@@ -500,12 +508,15 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
     stage_tables(a, tab);
     __syncthreads();
     const uint64_t step0 = __ldcg(a.step);
+    const bool ahead = a.g_step != nullptr;
+    const int pre_first = (ahead && __ldcg(a.g_step) == step0) ? a.pre_slot : 1 << 30;
     const unsigned int expected = gridDim.x + a.bar_extra;
     for (long long k = 0; k < nsteps; ++k) {
         const uint64_t step = step0 + (uint64_t)k;
+        const int pre_slot = k == 0 ? pre_first : (ahead ? a.pre_slot : 1 << 30);
         for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
             const TileDesc td = a.tiles[t];
-            const double r = predictor_tile<R, BS, true>(a, td, step, tab, red, 1 << 30);
+            const double r = predictor_tile<R, BS, true>(a, td, step, tab, red, pre_slot);
             if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
         }
         if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
@@ -516,10 +527,13 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
             }
         }
         for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x)
-            corrector_tile<R, BS, true>(a, a.tiles[t], step, nullptr);
+            corrector_tile<R, BS, true>(a, a.tiles[t], step, ahead ? &tab : nullptr);
         if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.step = step0 + (uint64_t)nsteps;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (ahead) *a.g_step = step0 + (uint64_t)nsteps;
+        *a.step = step0 + (uint64_t)nsteps;
+    }
 }
 
 }  // namespace ss

@@ -20,7 +20,8 @@
 //     is below 2^-53 of the result except within 1.3e-3 of u = 1, where the result is
 //     small and its square root carries an absolute error below 2e-17).
 //   * sqrt from a reciprocal square root refined to about 2^-45 in single precision with
-//     error-free float products, then one coupled Newton (Goldschmidt) step in FP64.
+//     error-free float products, then one coupled Newton (Goldschmidt) step in FP64 (the
+//     same seed serves the FP64 form's renormalisation, rsqrt_pos).
 //   * sin/cos of 2 pi t / 2^33 (t = 2w+1, an exact binary angle) by the nearest of 512
 //     table angles a and the remainder d = 2 pi rho / 2^33, |d| <= pi/512:
 //     sin(a+d) = cos a sin d + sin a cos d, cos(a+d) = cos a cos d - sin a sin d, with
@@ -109,12 +110,11 @@ __device__ __forceinline__ double neg2log_u(uint32_t w, const double2 *tab_log, 
     return (tn.x - tl.y) + b;                          // + 2 n ln 2 - 2 ln c (leading part)
 }
 
-// sqrt(x) for 2^-100 < x < 2^100.  The reciprocal square root is first refined in
-// single precision carried as a float pair: x = xh + xl (both taken from the bits of x),
-// y0 = rsqrtf(xh), r = 1 - x y0^2 evaluated with error-free products, and
-// y = y0 (1 + r/2 + 3r^2/8) ~ 1/sqrt(x) to about 2^-45.  One FP64 Goldschmidt step then
-// gives sqrt(x) to about one ulp: four FP64 instructions in all.
-__device__ __forceinline__ double sqrt_pos(double x) {
+// 1/sqrt(x) for 2^-100 < x < 2^100, refined in single precision carried as a float pair:
+// x = xh + xl (both taken from the bits of x), y0 = rsqrtf(xh), r = 1 - x y0^2 evaluated
+// with error-free products, y = y0 (1 + r/2 + 3r^2/8) ~ 1/sqrt(x) to about 2^-45.
+// Returned as a double (one FP64 add).
+__device__ __forceinline__ double rsqrt_seed(double x) {
     const uint64_t b = (uint64_t)__double_as_longlong(x);
     const int E = (int)((b >> 52) & 0x7FF);
     const float xh = __uint_as_float(((uint32_t)(E - 896) << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
@@ -127,12 +127,28 @@ __device__ __forceinline__ double sqrt_pos(double x) {
     const float Pe = fmaf(xh, p, -P);        // xh p = P + Pe exactly
     const float r = ((1.0f - P) - Pe) - fmaf(xh, q, xl * p);
     const float yl = y0 * (r * fmaf(0.375f, r, 0.5f));
-    const double y = f2d_bits(y0) + f2d_bits(yl);
+    return f2d_bits(y0) + f2d_bits(yl);
+}
+
+__device__ __forceinline__ double half_of(double y) {  // y / 2 for normal y, from the bits
+    return __longlong_as_double(__double_as_longlong(y) - (1ll << 52));
+}
+
+// sqrt(x), 2^-100 < x < 2^100: one FP64 Goldschmidt step from the refined seed -- four
+// FP64 instructions, about one ulp.
+__device__ __forceinline__ double sqrt_pos(double x) {
+    const double y = rsqrt_seed(x);
     const double s = x * y;
-    const uint64_t yb = (uint64_t)__double_as_longlong(y);
-    const double h = __longlong_as_double((long long)(yb - (1ull << 52)));  // y / 2
-    const double e = fma(-s, h, 0.5);
+    const double e = fma(-s, half_of(y), 0.5);
     return fma(s, e, s);
+}
+
+// 1/sqrt(x), 2^-100 < x < 2^100: one FP64 Newton step from the refined seed -- four FP64
+// instructions, about one ulp.
+__device__ __forceinline__ double rsqrt_pos(double x) {
+    const double y = rsqrt_seed(x);
+    const double e = fma(-(x * y), y, 1.0);
+    return fma(half_of(y), e, y);
 }
 
 // Exact int32 -> double for v != 0, assembled from the integer bits (no FP64 instruction).
