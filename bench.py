@@ -49,14 +49,20 @@ def step_bytes_per_spin(real_bytes, nnz_per_spin):
     return 18 * real_bytes + 2 * (nnz_per_spin * (4 + real_bytes) + 4)
 
 
-# FP64 pipe instructions per spin of one k_predictor launch of the FP32-mixed film in the
-# default launch shape (block 256, 4 spins per thread, back half of the Gaussians drawn
-# ahead by the corrector), from ncu (profiles/k_predictor_film1024x1024x16_fp32.md):
-# 9.81 DADD + 8.00 DMUL + 13.50 DFMA.  Each FP64 instruction takes one FMA slot of the
-# pipe (2 slots per cycle per SM), so it counts as 2 flop-equivalents, the convention of
-# the chip's FP64 rating.  DRAM traffic of that launch: 1.259 GB read + 0.579 GB written.
-PRED_FP64_INST_PER_SPIN = 9.81 + 8.00 + 13.50
-PRED_DRAM_BYTES = 1.259e9 + 0.579e9
+# FP64 pipe instructions per spin and DRAM bytes per launch of each step kernel on the
+# film in the default launch shape (block 512, 8 spins per thread, 3/4 of the Gaussians
+# drawn ahead by the corrector), from ncu (profiles/k_predictor_film1024x1024x16_fp32.md,
+# profiles/k_corrector_film1024x1024x16_fp32.md).  Each FP64 instruction (DADD, DMUL or
+# DFMA) takes one FMA slot of the pipe (2 slots per cycle per SM), so it counts as 2
+# flop-equivalents, the convention of the chip's FP64 rating.
+KERNEL_FP64_INST_PER_SPIN = {
+    "fp32": {"k_predictor": 7.91 + 1.25 + 4.50, "k_corrector": 4.50 + 3.75 + 13.50},
+    "fp64": {"k_predictor": None, "k_corrector": None},
+}
+KERNEL_DRAM_BYTES = {
+    "fp32": {"k_predictor": 1.286e9 + 0.578e9, "k_corrector": 1.545e9 + 0.337e9},
+    "fp64": {"k_predictor": None, "k_corrector": None},
+}
 SMS = 152
 FP64_SLOTS_PER_SM_CYCLE = 2
 
@@ -193,6 +199,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU legs")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="precision of the headline film run (fp32 = FP32-mixed)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -259,26 +267,31 @@ def main():
             info = s.info()
         return ms, kt, e2e_s / e2e_steps, ck.summary(local), mag, info
 
-    ms32, kt32, e2e32, clk32, mag32, info32 = timed_run("fp32", args.steps, args.warmup, 5)
+    ms32, kt32, e2e32, clk32, mag32, info32 = timed_run(args.precision, args.steps, args.warmup, 5)
     value = world * lat.n * args.steps / (ms32 * 1e-3)
     sm_ghz = (clk32.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))) / 1e3
     fp64_peak = SMS * FP64_SLOTS_PER_SM_CYCLE * 2 * sm_ghz / 1e3  # TFLOP/s (FMA-slot flops)
-    achieved = 2 * PRED_FP64_INST_PER_SPIN * lat.n / (kt32["predictor_ms"] * 1e-3) / 1e12
-    step_b = step_bytes_per_spin(4, nnz_per)
+    # the dominant kernel of the step, by live CUDA-event time
+    dom = "k_predictor" if kt32["predictor_ms"] >= kt32["corrector_ms"] else "k_corrector"
+    dom_ms = kt32["predictor_ms"] if dom == "k_predictor" else kt32["corrector_ms"]
+    inst = KERNEL_FP64_INST_PER_SPIN[args.precision][dom]
+    achieved = 2 * inst * lat.n / (dom_ms * 1e-3) / 1e12 if inst else None
+    step_b = step_bytes_per_spin(4 if args.precision == "fp32" else 8, nnz_per)
     hbm_achieved = step_b * lat.n / (ms32 / args.steps * 1e-3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": "film 1024x1024x16 sc (16,777,216 spins), in-plane periodic, J 6.0e-21, "
                                "k_u 1.0e-24 || z, alpha 0.02, dt 1e-16 s, T pulse 300->1200 K (100 fs FWHM)",
-                   "precision": "fp32-mixed (FP64 Box-Muller and reductions)", "spins": lat.n, "nnz": lat.nnz,
+                   "precision": "fp32-mixed (FP64 Box-Muller and reductions)" if args.precision == "fp32" else "fp64",
+                   "spins": lat.n, "nnz": lat.nnz,
                    "exec": "cuda graph", "block": info32["block"], "tile": info32["tile"],
                    "l2": "state 0.8 GB >> 126 MB L2, no flush needed", "replicas": world},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": PRED_DRAM_BYTES, "kernel": "k_predictor",
-                     "pipe": "fp64", "per_unit": f"{PRED_FP64_INST_PER_SPIN:.2f} FP64 instructions per spin, "
-                                                 "2 flop-equivalents each",
+                     "frac": achieved / fp64_peak if achieved else None,
+                     "traffic": KERNEL_DRAM_BYTES[args.precision][dom], "kernel": dom, "kernel_ms": dom_ms,
+                     "pipe": "fp64", "per_unit": f"{inst} FP64 instructions per spin, 2 flop-equivalents each",
                      "peak_source": f"152 SMs x 2 FP64 slots/cycle x 2 x {sm_ghz:.3f} GHz (measured clock)"},
         "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                          "per_unit": f"{step_b:.1f} B per spin-step (whole step)", "peak_source": peak_src},

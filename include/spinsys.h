@@ -127,6 +127,9 @@ typedef struct {
     int64_t step;         /* index of the next step                                   */
     int64_t record_capacity; /* steps kept in the per-step record ring               */
     int64_t device_bytes; /* device memory held by the handle                         */
+    int32_t draw_ahead;   /* quarters of each tile's spins whose next-step Gaussians the
+                             corrector draws (FP32-mixed form; see spin_system_set_draw_ahead) */
+    int32_t pad;
 } ss_info;
 
 /* Create one system.  Validates and copies every array (SS_ERR_INVALID_ARG on bad
@@ -200,7 +203,13 @@ ss_status spin_system_set_exec(ss_system *h, ss_exec mode);
  * block size, at most 16 blocks' worth) of the step kernels; rebuilds the tile list. */
 ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
 
-/* Time the candidate (exec, block, tile) choices on this handle over `trial_steps`
+/* FP32-mixed form: the corrector of step n draws the thermal Gaussians of step n+1 for
+ * `quarters`/4 of each tile's spins (rounded down to whole blocks), so that their FP64
+ * transform overlaps the corrector's memory traffic; the predictor draws the rest.
+ * 0..4; the default is 3.  Results do not depend on it (the same Gaussians are drawn). */
+ss_status spin_system_set_draw_ahead(ss_system *h, int32_t quarters);
+
+/* Time the candidate (exec, block, tile, draw-ahead) choices on this handle over `trial_steps`
  * steps each, keep the fastest, and write it to *out_info.  The spins and the step
  * counter are restored afterwards, so the trajectory is unchanged. */
 ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_info);

@@ -28,7 +28,7 @@ EXPORTS = (
     "get_spins_device", "get_magnetisation", "get_energy", "get_record", "set_spins", "set_step", "get_step",
     "spin_system_set_exec", "spin_system_set_launch", "spin_system_autotune", "spin_system_info",
     "spin_system_set_barrier_test", "spin_system_sync", "spin_system_time_kernels", "ss_debug_philox", "ss_debug_gaussians",
-    "llg_heun_step_noalloc",
+    "llg_heun_step_noalloc", "spin_system_set_draw_ahead",
     "ss_last_error", "ss_status_string",
 )
 
@@ -77,6 +77,8 @@ class SSInfo(ctypes.Structure):
         ("step", ctypes.c_int64),
         ("record_capacity", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64),
+        ("draw_ahead", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -118,6 +120,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "get_step": [P, P],
         "spin_system_set_exec": [P, ctypes.c_int],
         "spin_system_set_launch": [P, I32, I32],
+        "spin_system_set_draw_ahead": [P, I32],
         "spin_system_autotune": [P, I32, P],
         "spin_system_info": [P, P],
         "spin_system_set_barrier_test": [P, I32, I64],

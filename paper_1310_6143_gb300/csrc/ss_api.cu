@@ -89,6 +89,7 @@ struct ss_system {
     void *state[12] = {};  // sx sy sz px py pz qx qy qz hx hy hz
     void *ahead[3] = {};   // Gaussians drawn ahead by the corrector (FP32-mixed only)
     int pre_slot = 1 << 30;
+    int ahead_q = 3;       // quarters of each tile drawn ahead by the corrector
     bool zero_T = true;    // some temperature in force could be zero (the corrector then
                            // skips drawing those spins ahead)
     SysDesc *sys = nullptr;
@@ -273,7 +274,7 @@ void build_tables(std::vector<double2> &t) {
     }
     const long double twopi = 6.283185307179586476925286766559005768L;
     for (int j = 0; j < kTrigTab; ++j) {
-        const long double a = twopi * (long double)j / (long double)kTrigTab;
+        const long double a = twopi * (long double)j / 4096.0L;  // first octant of 4096 points
         t[kLogTab + kLn2Tab + j] = make_double2((double)sinl(a), (double)cosl(a));
     }
 }
@@ -510,7 +511,8 @@ ss_status build_tiles(ss_system *h) {
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
     h->nfin = std::max(1, std::min(h->nsys, 64));
     const int slots = h->tile / h->block;
-    h->pre_slot = slots >= 2 ? slots - slots / 2 : 1 << 30;  // the corrector draws the back half ahead
+    const int ahead = (h->ahead_q * slots) / 4;                // slots the corrector draws ahead
+    h->pre_slot = ahead >= 1 ? slots - ahead : 1 << 30;
     SS_CUDA(h, invalidate_ahead(h));
     drop_graph(h);
     return SS_OK;
@@ -756,8 +758,15 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         return cleanup(cuda_fail(h, e, "cudaMalloc"));
     st = h->precision == SS_FP32_MIXED ? upload_system<float>(h, hs) : upload_system<double>(h, hs);
     if (st != SS_OK) return cleanup(st);
-    // four spins per thread once the grid is many waves deep, one for small systems
-    h->tile = n >= (int64_t(1) << 20) ? 4 * h->block : h->block;
+    // Launch shape: 512-thread blocks for large systems; spins per thread (a power of two,
+    // at most 8) chosen so that there are about eight tiles per resident block.
+    h->block = n >= (int64_t(1) << 22) ? 512 : 256;
+    {
+        int64_t spt = n / ((int64_t)std::max(h->sm_count, 1) * 8 * h->block);
+        int slots = 1;
+        while (slots < 8 && 2 * slots <= spt) slots *= 2;
+        h->tile = slots * h->block;
+    }
     st = build_tiles(h);
     if (st != SS_OK) return cleanup(st);
     st = h->precision == SS_FP32_MIXED ? init_random<float>(h, hs) : init_random<double>(h, hs);
@@ -1158,6 +1167,15 @@ ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile) {
     return build_tiles(h);
 }
 
+ss_status spin_system_set_draw_ahead(ss_system *h, int32_t quarters) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (quarters < 0 || quarters > 4) return fail(h, SS_ERR_INVALID_ARG, "quarters must be 0..4");
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->ahead_q = quarters;
+    return build_tiles(h);
+}
+
 ss_status spin_system_info(ss_system *h, ss_info *o) {
     if (!h || !o) return fail(h, SS_ERR_INVALID_ARG, "NULL argument");
     o->n = h->n;
@@ -1172,6 +1190,8 @@ ss_status spin_system_info(ss_system *h, ss_info *o) {
     o->step = h->step;
     o->record_capacity = h->rec_cap;
     o->device_bytes = (int64_t)h->device_bytes;
+    o->draw_ahead = h->ahead_q;
+    o->pad = 0;
     return SS_OK;
 }
 
@@ -1196,19 +1216,23 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     SS_CUDA(h, dalloc(h, &save, 3 * (size_t)n * rs));
     for (int c = 0; c < 3; ++c)
         SS_CUDA(h, cudaMemcpyAsync((char *)save + c * n * rs, h->state[c], n * rs, cudaMemcpyDeviceToDevice, h->stream));
-    struct Cand { int exec, block, tile; };
+    struct Cand { int exec, block, tile, ahead; };
     std::vector<Cand> cands;
-    for (int b : {128, 256, 512})
-        for (int m : {1, 2, 4}) {
-            cands.push_back({SS_EXEC_GRAPH, b, b * m});
-            cands.push_back({SS_EXEC_PERSISTENT, b, b * m});
-        }
+    const bool mixed = h->precision == SS_FP32_MIXED;
+    for (int b : {256, 512})
+        for (int m : {1, 2, 4, 8})
+            for (int q : {2, 3}) {
+                if (!mixed && q != 3) continue;  // no draw-ahead in the FP64 form
+                cands.push_back({SS_EXEC_GRAPH, b, b * m, q});
+                cands.push_back({SS_EXEC_PERSISTENT, b, b * m, q});
+            }
     cudaEvent_t e0, e1;
     SS_CUDA(h, cudaEventCreate(&e0));
     SS_CUDA(h, cudaEventCreate(&e1));
     float best = 1e30f;
-    Cand bestc{h->exec, h->block, h->tile};
+    Cand bestc{h->exec, h->block, h->tile, h->ahead_q};
     for (const Cand &c : cands) {
+        h->ahead_q = c.ahead;
         if (spin_system_set_launch(h, c.block, c.tile) != SS_OK) continue;
         if (spin_system_set_exec(h, (ss_exec)c.exec) != SS_OK) continue;
         if (llg_heun_step(h, std::min(trial_steps, 4)) != SS_OK) { h->bad = false; continue; }
@@ -1226,6 +1250,7 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    h->ahead_q = bestc.ahead;
     st = spin_system_set_launch(h, bestc.block, bestc.tile);
     if (st == SS_OK) st = spin_system_set_exec(h, (ss_exec)bestc.exec);
     for (int c = 0; c < 3; ++c)

@@ -11,11 +11,11 @@ constexpr double kBoltzmann = 1.3807e-23;   // J/K
 constexpr double kGammaDefault = 1.76e11;   // 1/(T s)
 
 // Sizes of the Box-Muller function tables held in shared memory.
-constexpr int kLogTab = 769;   // centres c_t = (kLogFirst + t)/kLogScale, t = 0..768: [0.75, 1.5]
-constexpr int kLogFirst = 768;
-constexpr int kLogScale = 1024;
+constexpr int kLogTab = 1537;  // centres c_t = (kLogFirst + t)/kLogScale, t = 0..1536: [0.75, 1.5]
+constexpr int kLogFirst = 1536;
+constexpr int kLogScale = 2048;
 constexpr int kLn2Tab = 34;    // 2 n ln 2, n = 0..33, as (hi, lo)
-constexpr int kTrigTab = 512;  // (sin, cos) of 2 pi j / 512
+constexpr int kTrigTab = 513;  // (sin, cos) of pi m / 2048, m = 0..512: one octant of a 4096-point circle
 constexpr int kRecComps = 8;   // record: sum mu S (3), sum mu, E_exc, E_ani, E_app, E_total
 constexpr int kPartComps = 8;  // tile partials: sum mu S (3), E_exc, E_ani, E_app, 0, 0
 

@@ -13,19 +13,23 @@
 //   * -2 ln u by Tang's table-driven method (P. T. P. Tang, "Table-driven implementation
 //     of the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16, 1990):
 //     u = 2^-n f with f in [0.75, 1.5) taken exactly from the integer 2w+1; f is reduced
-//     against the nearest table centre c = k/1024 through r = f (1/c) - 1 (one FMA, so
+//     against the nearest table centre c = k/2048 through r = f (1/c) - 1 (one FMA, so
 //     the table's rounded 1/c defines the split exactly), and
-//     -2 ln u = 2 n ln 2 - 2 ln c - 2 log1p(r), with log1p(r) the Taylor series to r^5
-//     (|r| < 1.31e-3; the dropped r^6/3 term is below 1.7e-18 in absolute value, which
-//     is below 2^-53 of the result except within 1.3e-3 of u = 1, where the result is
-//     small and its square root carries an absolute error below 2e-17).
+//     -2 ln u = 2 n ln 2 - 2 ln c - 2r + r^2 - r^3 (2/3 - r/2 + 2r^2/5) (Taylor series of
+//     2 log1p(r), |r| < 6.6e-4).  The r^3 tail is below 1.9e-10, so single precision
+//     evaluates it to an absolute 2e-17; the leading terms stay in FP64.  Near u = 1
+//     (n = 0, c = 1, r exact) the result keeps its relative accuracy.
 //   * sqrt from a reciprocal square root refined to about 2^-45 in single precision with
 //     error-free float products, then one coupled Newton (Goldschmidt) step in FP64 (the
 //     same seed serves the FP64 form's renormalisation, rsqrt_pos).
-//   * sin/cos of 2 pi t / 2^33 (t = 2w+1, an exact binary angle) by the nearest of 512
-//     table angles a and the remainder d = 2 pi rho / 2^33, |d| <= pi/512:
-//     sin(a+d) = cos a sin d + sin a cos d, cos(a+d) = cos a cos d - sin a sin d, with
-//     sin d and cos d from their Taylor series (truncation below 2^-56).
+//   * sin/cos of 2 pi t / 2^33 (t = 2w+1, an exact binary angle) by the nearest of 4096
+//     angles a (tabulated for one octant, the rest by exact symmetries) and the remainder
+//     d = 2 pi rho / 2^33, |d| <= pi/4096: sin(a+d) = cos a sin d + sin a cos d,
+//     cos(a+d) = cos a cos d - sin a sin d, with sin d = d - d^3/6 and
+//     cos d = (1 - d^2/2) + d^4/24 (dropped terms below 2.2e-18).  d is carried as a pair
+//     of floats (rho is exact in single precision); only the products of the table values
+//     with the leading parts of sin d and cos d run in FP64, the rest in single precision
+//     (those parts are below 1e-10, so within 1e-17 absolute).
 // All results are within a few units in the last place of the correctly rounded values;
 // the tests compare them with CUDA's own log, sqrt and sincospi and with the CPU oracle.
 #pragma once
@@ -84,8 +88,15 @@ __device__ __forceinline__ float d2f_bits(double x) {
     return __uint_as_float(sign | ((e << 23) + (uint32_t)mr));
 }
 
+// double -> float rounded to nearest for |x| < 2^127; values below 2^-126 in magnitude
+// (including zero) give zero (no FP64 instruction).
+__device__ __forceinline__ float d2f_small(double x) {
+    const uint32_t ex = (uint32_t)(__double2hiint(x) >> 20) & 0x7FFu;
+    return ex >= 897u ? d2f_bits(x) : 0.0f;
+}
+
 // -2 ln((w + 1/2) 2^-32).  tab_log[t] = (1/c_t rounded, -2 ln(that rounded value)),
-// tab_ln2[n] = 2 n ln 2 as (hi, lo).
+// tab_ln2[n] = 2 n ln 2 as (hi, lo).  Five FP64 instructions.
 __device__ __forceinline__ double neg2log_u(uint32_t w, const double2 *tab_log, const double2 *tab_ln2) {
     const uint64_t m = 2ull * w + 1ull;              // u = m 2^-33, m odd, < 2^33
     const int lz = __clzll((long long)m);
@@ -95,19 +106,17 @@ __device__ __forceinline__ double neg2log_u(uint32_t w, const double2 *tab_log, 
     const int n = 33 - k - (big ? 1 : 0);            // u = 2^-n f'
     const uint64_t ebits = big ? (1022ull << 52) : (1023ull << 52);
     const double fp = __longlong_as_double((long long)(ebits | frac));    // f' in [0.75, 1.5)
-    // nearest centre c = j/1024: j = round(1024 f')
-    const uint32_t j = big ? (uint32_t)(512u + (uint32_t)((frac + (1ull << 42)) >> 43))
-                           : (uint32_t)(1024u + (uint32_t)((frac + (1ull << 41)) >> 42));
+    // nearest centre c = j/2048: j = round(2048 f')
+    const uint32_t j = big ? (uint32_t)(1024u + (uint32_t)((frac + (1ull << 41)) >> 42))
+                           : (uint32_t)(2048u + (uint32_t)((frac + (1ull << 40)) >> 41));
     const double2 tl = tab_log[j - (uint32_t)kLogFirst];
     const double2 tn = tab_ln2[n];
     const double r = fma(fp, tl.x, -1.0);            // f'/c - 1 up to one rounding
-    const double r2 = r * r;
-    // 2 log1p(r) = 2r - r^2 + (2/3) r^3 - (1/2) r^4 + (2/5) r^5 = 2r + r^2 t
-    double t = fma(r, 0.4, -0.5);
-    t = fma(r, t, 2.0 / 3.0);
-    t = fma(r, t, -1.0);
-    const double b = fma(-2.0, r, fma(-r2, t, tn.y));  // lo part of 2 n ln 2 - 2 log1p(r)
-    return (tn.x - tl.y) + b;                          // + 2 n ln 2 - 2 ln c (leading part)
+    const float rf = d2f_small(r);
+    const float tail = ((rf * rf) * rf) * fmaf(rf, fmaf(rf, 0.4f, -0.5f), 2.0f / 3.0f);
+    const double c = f2d_bits(d2f_small(tn.y) - tail);   // lo part of 2 n ln 2, minus the tail
+    const double b = fma(-2.0, r, fma(r, r, c));         // -2r + r^2 + c
+    return (tn.x - tl.y) + b;                            // + 2 n ln 2 - 2 ln c (leading part)
 }
 
 // 1/sqrt(x) for 2^-100 < x < 2^100, refined in single precision carried as a float pair:
@@ -161,43 +170,74 @@ __device__ __forceinline__ double int_to_double(int32_t v) {
     return __longlong_as_double((long long)bits);
 }
 
-// Reduction of the binary angle 2 pi (2w+1) / 2^33 to a table angle and a remainder.
+// Reduction of the binary angle 2 pi (2w+1) / 2^33 to the nearest of 4096 table angles
+// (index j) and a remainder d = 2 pi rho / 2^33, |rho| < 2^20 (odd).  rho is exact in
+// single precision, so d is formed as a float pair dh + dl (about 2^-48 relative) and
+// sin d = dh + sdl, cos d = (1 - p/2) + T with p = dh^2 rounded and sdl, T small floats.
 struct TurnSplit {
-    uint32_t j;   // table index, angle 2 pi j / 512
-    double d;     // remainder angle, |d| <= pi/512
+    uint32_t j;   // angle 2 pi j / 4096
+    float dh;     // leading part of d (exact as a double)
+    float sdl;    // sin d - dh
+    float p;      // dh^2 rounded to float
+    float T;      // cos d - (1 - p/2)
 };
 
 __device__ __forceinline__ TurnSplit split_turn(uint32_t w) {
+    constexpr double C = 6.283185307179586 / 8589934592.0;  // 2 pi / 2^33 (exact scaling)
+    constexpr float Ch = (float)C;
+    constexpr float Cl = (float)(C - (double)Ch);
     const uint64_t t = 2ull * w + 1ull;
-    const uint64_t q = (t + (1ull << 23)) >> 24;     // nearest multiple of 2^24
-    const int32_t rho = (int32_t)(int64_t)(t - (q << 24));  // odd, so never zero
+    const uint64_t q = (t + (1ull << 20)) >> 21;            // nearest multiple of 2^21
+    const float rho = __int2float_rn((int)(int64_t)(t - (q << 21)));
     TurnSplit s;
-    s.j = (uint32_t)q & 511u;
-    s.d = int_to_double(rho) * (6.283185307179586 / 8589934592.0);  // 2 pi / 2^33 (exact scaling)
+    s.j = (uint32_t)q & 4095u;
+    s.dh = rho * Ch;
+    const float dl = fmaf(rho, Ch, -s.dh) + rho * Cl;        // d = dh + dl
+    s.p = s.dh * s.dh;
+    const float d2l = fmaf(s.dh, s.dh, -s.p) + 2.0f * (s.dh * dl);  // d^2 = p + d2l
+    s.sdl = dl - (s.p * s.dh) * (1.0f / 6.0f);               // sin d = d - d^3/6
+    s.T = (s.p * s.p) * (1.0f / 24.0f) - 0.5f * d2l;         // cos d = 1 - d^2/2 + d^4/24
     return s;
 }
 
+// (sin, cos) of 2 pi j / 4096 from the first-octant table (pi m / 2048, m = 0..512):
+// reflect within the octant, swap sine and cosine, flip signs.
+__device__ __forceinline__ void octant_lookup(uint32_t j, const double2 *tab_trig, double &sa, double &ca) {
+    const uint32_t o = j >> 9, m = j & 511u;
+    const double2 v = tab_trig[(o & 1u) ? 512u - m : m];
+    const bool swap = ((o + 1u) >> 1) & 1u;
+    const double s = swap ? v.y : v.x;
+    const double c = swap ? v.x : v.y;
+    const long long sbit = (long long)((o & 4u) != 0) << 63;
+    const long long cbit = (long long)(((o + 2u) & 4u) != 0) << 63;
+    sa = __longlong_as_double(__double_as_longlong(s) ^ sbit);
+    ca = __longlong_as_double(__double_as_longlong(c) ^ cbit);
+}
+
+// sin(a + d) = cos a sin d + sin a cos d, cos(a + d) = cos a cos d - sin a sin d: the
+// FP64 parts are cos a dh, sin a (1 - p/2) and their cosine counterparts; the products of
+// the table values with the small float parts are formed in single precision (below
+// 1e-10 in size, so within 1e-17 absolute).  Five FP64 instructions for both outputs.
 __device__ __forceinline__ void sincos_turn(uint32_t w, const double2 *tab_trig, double &sv, double &cv) {
     const TurnSplit ts = split_turn(w);
-    const double d = ts.d;
-    const double d2 = d * d;
-    const double sd = fma(d2 * d, fma(d2, 1.0 / 120.0, -1.0 / 6.0), d);  // sin d
-    const double cd = fma(d2, fma(d2, 1.0 / 24.0, -0.5), 1.0);             // cos d
-    const double2 sc = tab_trig[ts.j];
-    sv = fma(sc.y, sd, sc.x * cd);
-    cv = fma(-sc.x, sd, sc.y * cd);
+    double sa, ca;
+    octant_lookup(ts.j, tab_trig, sa, ca);
+    const float saf = d2f_small(sa), caf = d2f_small(ca);
+    const double cd = fma(f2d_bits(ts.p), -0.5, 1.0);
+    const double dh = f2d_bits(ts.dh);
+    sv = fma(ca, dh, fma(sa, cd, f2d_bits(saf * ts.T + caf * ts.sdl)));
+    cv = fma(-sa, dh, fma(ca, cd, f2d_bits(caf * ts.T - saf * ts.sdl)));
 }
 
+// cos(a + d) alone: three FP64 instructions.
 __device__ __forceinline__ double cos_turn(uint32_t w, const double2 *tab_trig) {
     const TurnSplit ts = split_turn(w);
-    const double d = ts.d;
-    const double d2 = d * d;
-    const double sd = fma(d2 * d, fma(d2, 1.0 / 120.0, -1.0 / 6.0), d);
-    const double cd = fma(d2, fma(d2, 1.0 / 24.0, -0.5), 1.0);
-    const double2 sc = tab_trig[ts.j];
-    return fma(-sc.x, sd, sc.y * cd);
+    double sa, ca;
+    octant_lookup(ts.j, tab_trig, sa, ca);
+    const float saf = d2f_small(sa), caf = d2f_small(ca);
+    const double cd = fma(f2d_bits(ts.p), -0.5, 1.0);
+    return fma(-sa, f2d_bits(ts.dh), fma(ca, cd, f2d_bits(caf * ts.T - saf * ts.sdl)));
 }
-
 
 // Three standard Gaussians of one Philox block (project transform, see the file header).
 __device__ __forceinline__ void box_muller3(const Philox4 &w, const double2 *tab_log, const double2 *tab_ln2,

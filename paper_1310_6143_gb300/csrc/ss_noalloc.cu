@@ -208,7 +208,7 @@ void na_fill_tables(double2 *t) {
     }
     const long double twopi = 6.283185307179586476925286766559005768L;
     for (int j = 0; j < kTrigTab; ++j) {
-        const long double a = twopi * (long double)j / (long double)kTrigTab;
+        const long double a = twopi * (long double)j / 4096.0L;  // first octant of 4096 points
         t[kLogTab + kLn2Tab + j] = make_double2((double)sinl(a), (double)cosl(a));
     }
 }

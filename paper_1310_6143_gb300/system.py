@@ -155,6 +155,9 @@ class SpinSystem:
     def set_launch(self, block: int, tile: int):
         self._check(self._lib.spin_system_set_launch(self._h, int(block), int(tile)))
 
+    def set_draw_ahead(self, quarters: int):
+        self._check(self._lib.spin_system_set_draw_ahead(self._h, int(quarters)))
+
     def autotune(self, trial_steps: int = 20) -> dict:
         info = B.SSInfo()
         self._check(self._lib.spin_system_autotune(self._h, int(trial_steps), ctypes.byref(info)))
