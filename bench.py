@@ -277,6 +277,10 @@ def main():
     inst = KERNEL_FP64_INST_PER_SPIN[args.precision][dom]
     achieved = 2 * inst * lat.n / (dom_ms * 1e-3) / 1e12 if inst else None
     step_b = step_bytes_per_spin(4 if args.precision == "fp32" else 8, nnz_per)
+    from paper_1310_6143_gb300.system import debug_fp64_rate
+
+    fp64_meas = {f"{name}_inst_per_sm_cycle": debug_fp64_rate(m) / SMS / (sm_ghz * 1e9)
+                 for m, name in ((0, "dfma_shared_operands"), (1, "dfma_distinct_operands"), (2, "dadd"))}
     hbm_achieved = step_b * lat.n / (ms32 / args.steps * 1e-3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
@@ -292,7 +296,8 @@ def main():
                      "frac": achieved / fp64_peak if achieved else None,
                      "traffic": KERNEL_DRAM_BYTES[args.precision][dom], "kernel": dom, "kernel_ms": dom_ms,
                      "pipe": "fp64", "per_unit": f"{inst} FP64 instructions per spin, 2 flop-equivalents each",
-                     "peak_source": f"152 SMs x 2 FP64 slots/cycle x 2 x {sm_ghz:.3f} GHz (measured clock)"},
+                     "peak_source": f"152 SMs x 2 FP64 slots/cycle x 2 x {sm_ghz:.3f} GHz (measured clock)",
+                     "measured_fp64_rate": fp64_meas},
         "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                          "per_unit": f"{step_b:.1f} B per spin-step (whole step)", "peak_source": peak_src},
         "kernels_ms": kt32, "clocks": clk32,

@@ -239,6 +239,13 @@ ss_status spin_system_sync(ss_system *h);
 ss_status ss_debug_philox(const uint32_t ctr0[4], const uint32_t key[2], int64_t count, uint32_t *out);
 ss_status ss_debug_gaussians(uint64_t seed, uint32_t sys_id, uint32_t step, int64_t n, int32_t mode, double *out);
 
+/* Measured FP64 instruction throughput of the current device (instructions per second)
+ * from a probe kernel of eight independent chains per thread: mode 0 DFMA with shared
+ * multiplier and addend, mode 1 DFMA with three distinct register operands, mode 2 DADD.
+ * The step kernels are bound by this pipe; the benchmark reports it beside the nominal
+ * rate.  Synchronous; allocates and frees a small device buffer. */
+ss_status ss_debug_fp64_rate(int32_t mode, double *inst_per_s);
+
 /* ---------------------------------------------------------------------------------
  * Allocation-free stepping.  The paper has no counterpart of this entry point.
  *

@@ -63,7 +63,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # SPINSYS_ORACLE_LIB names a prebuilt oracle library to use instead (the mutation
+            # test loads deliberately broken copies this way, in child processes)
+            lib = ctypes.CDLL(os.environ.get("SPINSYS_ORACLE_LIB") or build())
             P = ctypes.c_void_p
             lib.orc_philox4x32_10.argtypes = [P, P, P]
             lib.orc_thermal_gaussians.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,

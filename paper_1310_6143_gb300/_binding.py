@@ -28,7 +28,7 @@ EXPORTS = (
     "get_spins_device", "get_magnetisation", "get_energy", "get_record", "set_spins", "set_step", "get_step",
     "spin_system_set_exec", "spin_system_set_launch", "spin_system_autotune", "spin_system_info",
     "spin_system_set_barrier_test", "spin_system_sync", "spin_system_time_kernels", "ss_debug_philox", "ss_debug_gaussians",
-    "llg_heun_step_noalloc", "spin_system_set_draw_ahead",
+    "llg_heun_step_noalloc", "spin_system_set_draw_ahead", "ss_debug_fp64_rate",
     "ss_last_error", "ss_status_string",
 )
 
@@ -128,6 +128,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "spin_system_time_kernels": [P, I32, P],
         "ss_debug_philox": [P, P, I64, P],
         "ss_debug_gaussians": [U64, U32, U32, I64, I32, P],
+        "ss_debug_fp64_rate": [I32, P],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)

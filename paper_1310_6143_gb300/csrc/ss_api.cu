@@ -1300,6 +1300,12 @@ ss_status ss_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, int64_t
     return e == cudaSuccess ? SS_OK : fail(nullptr, SS_ERR_CUDA, "%s", cudaGetErrorString(e));
 }
 
+ss_status ss_debug_fp64_rate(int32_t mode, double *inst_per_s) {
+    if (!inst_per_s || mode < 0 || mode > 2) return fail(nullptr, SS_ERR_INVALID_ARG, "bad arguments");
+    const cudaError_t e = fp64_rate(mode, inst_per_s);
+    return e == cudaSuccess ? SS_OK : fail(nullptr, SS_ERR_CUDA, "%s", cudaGetErrorString(e));
+}
+
 const char *ss_last_error(ss_system *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 const char *ss_status_string(ss_status s) {

@@ -60,4 +60,58 @@ cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, l
     return cudaGetLastError();
 }
 
+// FP64 instruction throughput probe: eight independent chains per thread.  mode 0: DFMA
+// with the multiplier and addend shared by all chains; mode 1: DFMA with three distinct
+// register operands (the pattern of general code); mode 2: DADD.
+template <int MODE>
+__global__ void k_fp64_rate(double *out, int iters, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (MODE == 0) x[k] = fma(x[k], a, b);
+            else if (MODE == 1) x[k] = fma(x[k], x[(k + 1) & 7], (k & 1) ? a : b);
+            else x[k] = x[k] + ((k & 1) ? a : b);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// FP64 instructions per second of the probe (grid: 4 blocks of 256 threads per SM).
+cudaError_t fp64_rate(int mode, double *inst_per_s) {
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    if (e != cudaSuccess) return e;
+    const int block = 256, grid = 4 * sms, iters = 4096, reps = 5;
+    double *out = nullptr;
+    e = cudaMalloc(&out, sizeof(double) * (size_t)grid * block);
+    if (e != cudaSuccess) return e;
+    auto launch = [&]() {
+        if (mode == 0) k_fp64_rate<0><<<grid, block>>>(out, iters, 0.999, 1e-3);
+        else if (mode == 1) k_fp64_rate<1><<<grid, block>>>(out, iters, 0.999, 1e-3);
+        else k_fp64_rate<2><<<grid, block>>>(out, iters, 0.999, 1e-3);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    launch();
+    cudaEventRecord(e0);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e == cudaSuccess) *inst_per_s = (double)reps * grid * block * iters * 8.0 / (ms * 1e-3);
+    return e;
+}
+
 }  // namespace ss

@@ -122,6 +122,7 @@ cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int ns
                             double *dst, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long long count, uint32_t *out,
                                 cudaStream_t s);
+cudaError_t fp64_rate(int mode, double *inst_per_s);
 cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
                                    const double2 *tab_log, const double2 *tab_ln2, const double2 *tab_trig,
                                    double *out, cudaStream_t s);

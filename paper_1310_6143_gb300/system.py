@@ -246,3 +246,11 @@ def debug_gaussians(seed: int, sys_id: int, step: int, n: int, mode: int = 0) ->
     B.check(lib.ss_debug_gaussians(int(seed) & 0xFFFFFFFFFFFFFFFF, int(sys_id), int(step), int(n), int(mode),
                                    B.ptr(out)))
     return out
+
+
+def debug_fp64_rate(mode: int = 1) -> float:
+    """Measured FP64 instructions per second of the current device (see spinsys.h)."""
+    lib = B.load()
+    out = ctypes.c_double()
+    B.check(lib.ss_debug_fp64_rate(int(mode), ctypes.byref(out)))
+    return out.value

@@ -1,0 +1,155 @@
+"""Quick pins run against one (possibly mutated) oracle library in a child process.
+
+Prints one line per pin, 'PASS name' or 'FAIL name'.  Used by test_oracle_mutants.py.
+"""
+import math
+import sys
+
+import numpy as np
+
+import oracle as O
+from paper_1310_6143_gb300 import lattice as L
+
+GAMMA, KB, MU = 1.76e11, 1.3807e-23, 1.5 * 9.2740e-24
+
+
+def pin_field_gradient():
+    rng = np.random.default_rng(3)
+    n = 6
+    A = np.zeros((n, n))
+    for i in range(n):
+        for j in range(i + 1, n):
+            if rng.random() < 0.6:
+                A[i, j] = A[j, i] = rng.normal(0, 5e-21)
+    rp, col, J = [0], [], []
+    for i in range(n):
+        nz = np.nonzero(A[i])[0]
+        col += list(nz); J += list(A[i, nz]); rp.append(len(col))
+    mu = rng.uniform(1, 3, n) * 9.274e-24
+    ku = rng.normal(0, 2e-23, n)
+    ax = rng.normal(size=(n, 3)); ax /= np.linalg.norm(ax, axis=1, keepdims=True)
+    H = rng.normal(0, 3, 3)
+    K = np.zeros((n, 6))
+    for i in range(0, n, 2):
+        M = rng.normal(0, 1e-23, (3, 3))
+        M = M + M.T
+        K[i] = [M[0, 0], M[1, 1], M[2, 2], M[0, 1], M[0, 2], M[1, 2]]
+    s = O.OracleSystem(np.array(rp), np.array(col), np.array(J), mu, ku, ax, K, H_app=tuple(H))
+    S = L.random_state(n, 4)
+
+    def energy(S):
+        e = 0.0
+        for i in range(n):
+            for j in range(i + 1, n):
+                e -= A[i, j] * S[i] @ S[j]
+        for i in range(n):
+            Mi = np.array([[K[i, 0], K[i, 3], K[i, 4]], [K[i, 3], K[i, 1], K[i, 5]], [K[i, 4], K[i, 5], K[i, 2]]])
+            e -= S[i] @ Mi @ S[i]
+        return e - np.sum(ku * np.einsum("ij,ij->i", S, ax) ** 2) - np.sum(mu * (S @ H))
+    me = O.moment_energy(s, S)
+    if abs(me[7] - energy(S)) > 1e-12 * abs(energy(S)):
+        return False
+    F = O.fields(s, S)
+    h = 1e-6
+    for i in range(n):
+        for c in range(3):
+            Sp, Sm = S.copy(), S.copy()
+            Sp[i, c] += h; Sm[i, c] -= h
+            ref = -(energy(Sp) - energy(Sm)) / (2 * h) / mu[i]
+            if abs(F[i, c] - ref) > 1e-7 * max(1.0, np.abs(F[i]).max()):
+                return False
+    return True
+
+
+def pin_single_spin_analytic():
+    lat = L.single_spin()
+    lam, H, dt = 0.1, 10.0, 1e-15
+    s = O.OracleSystem(lat.row_ptr, lat.col, lat.J, lat.mu_s, 0.0, lat.easy_axis, alpha=lam, dt=dt, H_app=(0, 0, H))
+    S = np.array([[1.0, 0, 0]])
+    err = 0.0
+    for k in range(60):
+        S, _ = O.heun_run(s, S, 500, 0.0, step0=k * 500)
+        t = (k + 1) * 500 * dt
+        a, w = lam * GAMMA * H / (1 + lam ** 2) * t, GAMMA * H / (1 + lam ** 2) * t
+        ref = np.array([math.cos(w) / math.cosh(a), math.sin(w) / math.cosh(a), math.tanh(a)])
+        err = max(err, np.abs(S[0] - ref).max())
+    return err < 1e-6
+
+
+def pin_unit_length():
+    lat = L.simple_cubic(4, 4, 4)
+    s = O.OracleSystem(lat.row_ptr, lat.col, lat.J, lat.mu_s, lat.k_u, lat.easy_axis, alpha=0.1, dt=1e-16)
+    S = L.random_state(lat.n, 2)
+    for k in range(5):
+        S, _ = O.heun_run(s, S, 1, 500.0, step0=k)
+        if np.abs(np.linalg.norm(S, axis=1) - 1).max() > 1e-15:
+            return False
+    return True
+
+
+def pin_gaussians():
+    g = O.gaussians_bulk(9, 1, 3, 100_000)
+    if np.abs(g.mean(0)).max() > 0.02 or np.abs(g.var(0) - 1).max() > 0.02:
+        return False
+    return np.abs(np.corrcoef(g.T) - np.eye(3)).max() < 0.015
+
+
+def pin_philox_against_torch():
+    import os
+    import subprocess
+    import tempfile
+
+    import torch
+
+    inc = os.path.join(os.path.dirname(torch.__file__), "include")
+    d = tempfile.mkdtemp()
+    src = os.path.join(d, "p.cpp")
+    open(src, "w").write("#include <ATen/core/PhiloxRNGEngine.h>\n#include <cstdio>\nint main(){ at::philox_engine "
+                         "e(0x0123456789abcdefULL, 7ULL, (5ULL<<32)|3ULL); for(int i=0;i<4;i++) printf(\"%u \", e());"
+                         " return 0; }\n")
+    subprocess.run(["g++", "-std=c++17", "-O1", f"-I{inc}", "-o", os.path.join(d, "p"), src], check=True)
+    out = [int(v) for v in subprocess.run([os.path.join(d, "p")], capture_output=True, text=True).stdout.split()]
+    return list(O.philox4x32_10([3, 5, 7, 0], [0x89ABCDEF, 0x01234567])) == out
+
+
+def pin_boltzmann():
+    ku, kappa, lam = 1e-22, 3.0, 1.0
+    T = ku / (kappa * KB)
+    dt = 0.0025 * MU / (2 * lam * KB * T * GAMMA)
+    n = 64
+    s = O.OracleSystem(np.zeros(n + 1, dtype=np.int64), np.zeros(0, np.int32), np.zeros(0), np.full(n, MU),
+                       np.full(n, ku), (0, 0, 1), alpha=lam, dt=dt, seed=5)
+    S, _ = O.heun_run(s, np.tile([0, 0, 1.0], (n, 1)), 3000, T)
+    c2 = []
+    for k in range(100):
+        S, _ = O.heun_run(s, S, 400, T, step0=3000 + k * 400)
+        c2.append(S[:, 2] ** 2)
+    m2 = np.concatenate(c2).mean()
+    from scipy import integrate
+    Z = integrate.quad(lambda x: np.exp(kappa * x * x), 0, 1)[0]
+    ref = integrate.quad(lambda x: x * x * np.exp(kappa * x * x), 0, 1)[0] / Z
+    return abs(m2 - ref) < 0.02
+
+
+def pin_curie():
+    lat = L.simple_cubic(6, 6, 6, J=6e-21, k_u=0.0)
+    ms = {}
+    for T in (312.5, 937.5):
+        s = O.OracleSystem(lat.row_ptr, lat.col, lat.J, lat.mu_s, 0.0, lat.easy_axis, alpha=1.0, dt=1e-17, seed=7)
+        S, _ = O.heun_run(s, L.uniform_state(lat.n), 2500, T)
+        S, rec = O.heun_run(s, S, 2500, T, step0=2500, record=True)
+        ms[T] = (np.linalg.norm(rec[:, :3], axis=1) / rec[:, 3]).mean()
+    return 0.6 < ms[312.5] < 0.92 and ms[937.5] < 0.3
+
+
+PINS = [pin_field_gradient, pin_single_spin_analytic, pin_unit_length, pin_gaussians, pin_philox_against_torch,
+        pin_boltzmann, pin_curie]
+
+if __name__ == "__main__":
+    for p in PINS:
+        try:
+            ok = bool(p())
+        except Exception:
+            ok = False
+        print(("PASS " if ok else "FAIL ") + p.__name__, flush=True)
+    sys.exit(0)

@@ -1,0 +1,72 @@
+"""Mutation check of the oracle's pins: plausible mistakes planted in copies of the
+oracle source (compiled on the CPU, loaded in child processes) must each fail at least
+one pin, while the unmodified oracle passes all of them."""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "spinsys_oracle.c")
+
+# (name, original text, mistaken text)
+MUTANTS = [
+    ("anisotropy field without factor 2", "double a = 2.0 * s->k_u[i] / mu * sdote;",
+     "double a = s->k_u[i] / mu * sdote;"),
+    ("exchange bonds counted twice in the field", "    H[0] = sx / mu;\n    H[1] = sy / mu;\n    H[2] = sz / mu;",
+     "    H[0] = 2.0 * sx / mu;\n    H[1] = 2.0 * sy / mu;\n    H[2] = 2.0 * sz / mu;"),
+    ("applied field with the wrong sign", "    H[0] += s->H_app[0];\n    H[1] += s->H_app[1];\n    H[2] += s->H_app[2];",
+     "    H[0] -= s->H_app[0];\n    H[1] -= s->H_app[1];\n    H[2] -= s->H_app[2];"),
+    ("Neel field without factor 2", "        H[0] += 2.0 / mu * kx;", "        H[0] += 1.0 / mu * kx;"),
+    ("damping term with the wrong sign", "    dS[0] = pre * (c0 + lambda * d0);\n    dS[1] = pre * (c1 + lambda * d1);\n"
+     "    dS[2] = pre * (c2 + lambda * d2);", "    dS[0] = pre * (c0 - lambda * d0);\n    dS[1] = pre * (c1 - lambda * d1);\n"
+     "    dS[2] = pre * (c2 - lambda * d2);"),
+    ("LLG prefactor without 1/(1+lambda^2)", "double pre = -gamma / (1.0 + lambda * lambda);", "double pre = -gamma;"),
+    ("transposed cross product", "    double c0 = S[1] * H[2] - S[2] * H[1];", "    double c0 = S[2] * H[1] - S[1] * H[2];"),
+    ("noise variance with a (1+lambda^2) factor",
+     "double sigma = sqrt(2.0 * lambda * ORC_KB * Tn / (gamma * s->mu_s[i] * s->dt));",
+     "double sigma = sqrt(2.0 * lambda * ORC_KB * Tn * (1.0 + lambda * lambda) / (gamma * s->mu_s[i] * s->dt));"),
+    ("corrector started from the predicted spin", "            v[0] = S[3 * i + 0] + 0.5 * (dS[3 * i + 0] + dSp[0]) * s->dt;",
+     "            v[0] = Sp[3 * i + 0] + 0.5 * (dS[3 * i + 0] + dSp[0]) * s->dt;"),
+    ("corrector without renormalisation", "            orc_normalise(v);\n            /* S_i is only read",
+     "            /* S_i is only read"),
+    ("exchange energy without the factor 1/2", "eex += -0.5 * (Si[0] * hex[0]", "eex += -1.0 * (Si[0] * hex[0]"),
+    ("third Gaussian reusing the first angle", "    g[2] = r2 * cos(phi2);", "    g[2] = r2 * cos(phi1);"),
+    ("Philox key not advanced", "            k0 += 0x9E3779B9u;", ""),
+    ("Philox multipliers swapped", "uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;",
+     "uint64_t p0 = (uint64_t)0xCD9E8D57u * (uint64_t)x0;"),
+]
+
+
+def _build(name, text, tmp):
+    path = os.path.join(tmp, f"lib_{abs(hash(name))}.so")
+    csrc = path.replace(".so", ".c")
+    open(csrc, "w").write(text)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC", "-std=c11",
+                    "-o", path, csrc, "-lm"], check=True)
+    return path
+
+
+def _run(lib):
+    env = dict(os.environ, SPINSYS_ORACLE_LIB=lib, PYTHONPATH=ROOT, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "_mutant_pins.py")], capture_output=True,
+                         text=True, env=env, timeout=600).stdout
+    return [line.split()[1] for line in out.splitlines() if line.startswith("FAIL")], out
+
+
+@pytest.mark.filterwarnings("ignore")
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    base = open(SRC).read()
+    jobs = {"(unmodified)": base}
+    for name, a, b in MUTANTS:
+        assert base.count(a) == 1, f"mutant text not found once: {name}"
+        jobs[name] = base.replace(a, b)
+    libs = {name: _build(name, text, str(tmp_path)) for name, text in jobs.items()}
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = dict(zip(libs, ex.map(_run, libs.values())))
+    failed, out = results.pop("(unmodified)")
+    assert failed == [], out
+    survivors = [name for name, (f, _) in results.items() if not f]
+    assert survivors == [], f"mistakes no pin detects: {survivors}"
