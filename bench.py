@@ -56,14 +56,15 @@ def step_bytes_per_spin(real_bytes, nnz_per_spin):
 # DFMA) takes one FMA slot of the pipe (2 slots per cycle per SM), so it counts as 2
 # flop-equivalents, the convention of the chip's FP64 rating.
 KERNEL_FP64_INST_PER_SPIN = {
-    "fp32": {"k_predictor": 7.91 + 1.25 + 4.50, "k_corrector": 4.50 + 3.75 + 13.50},
+    "fp32": {"k_predictor": 7.03 + 1.25 + 4.50, "k_corrector": 4.50 + 3.75 + 13.50},
     "fp64": {"k_predictor": None, "k_corrector": None},
 }
 KERNEL_DRAM_BYTES = {
-    "fp32": {"k_predictor": 1.286e9 + 0.578e9, "k_corrector": 1.545e9 + 0.337e9},
+    "fp32": {"k_predictor": 1.286e9 + 0.578e9, "k_corrector": 1.545e9 + 0.337e9},  # per launch
     "fp64": {"k_predictor": None, "k_corrector": None},
 }
 SMS = 152
+EXEC_NAMES = {0: "auto", 1: "kernels", 2: "graph", 3: "persistent", 4: "system_blocks"}
 FP64_SLOTS_PER_SM_CYCLE = 2
 
 
@@ -168,6 +169,53 @@ def cpu_baseline(lat, T, seconds=15.0):
                       f"record), {one:.1f} s"}
 
 
+def time_workload(lats, kw, precision, steps, stream, warmup=5, autotune=True):
+    """spin-steps/s of `steps` Heun steps on one handle (CUDA events on its stream)."""
+    import torch
+
+    from paper_1310_6143_gb300.system import SpinSystem
+
+    n = sum(l.n for l in (lats if isinstance(lats, list) else [lats]))
+    with SpinSystem(lats, precision=precision, stream=stream, **kw) as s:
+        info = s.autotune(8) if autotune else s.info()
+        s.step(warmup)
+        s.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        s.sync()
+        ms = e0.elapsed_time(e1)
+    return {"value": n * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps,
+            "exec": EXEC_NAMES[info["exec"]], "block": info["block"],
+            "tile": info["tile"]}
+
+
+def workload_table(stream, rank):
+    """The five workload shapes of the method's benchmark set, FP32-mixed and FP64."""
+    from paper_1310_6143_gb300 import lattice as L
+
+    rows = {}
+    sc = L.simple_cubic(10, 10, 10, J=6.0e-21, k_u=1.0e-24)
+    rows["sc10_fp64"] = dict(spins=sc.n, **time_workload(sc, dict(alpha=0.1, dt=1e-16, T=300.0, seed=1 + rank),
+                                                          "fp64", 2000, stream))
+    fcc = L.fcc(64, 64, 64, J=11.2e-21, k_u=6.69e-24)
+    kw = dict(alpha=0.05, dt=1e-16, T=1000.0, seed=2 + rank, init_random=True)
+    for prec, k in (("fp32", 200), ("fp64", 50)):
+        rows[f"fcc64_{prec}"] = dict(spins=fcc.n, **time_workload(fcc, kw, prec, k, stream))
+    # a temperature sweep as one batch: 1,024 independent 10^3 lattices from 0 to 1,023 K
+    sweep = [sc] * 1024
+    rows["sc10_x1024_sweep_fp32"] = dict(spins=sc.n * 1024, systems=1024, **time_workload(
+        sweep, dict(alpha=0.1, dt=1e-16, T=[float(t) for t in range(1024)], seed=1 + rank,
+                    sys_id=list(range(1024))), "fp32", 500, stream))
+    cs = L.core_shell_sphere()
+    kw = dict(alpha=0.1, dt=1e-16, T=10.0, H=(1.0, 0.0, 0.0), seed=3 + rank)
+    for prec, k in (("fp32", 400), ("fp64", 100)):
+        rows[f"core_shell_{prec}"] = dict(spins=cs.n, **time_workload(cs, kw, prec, k, stream))
+    return rows
+
+
 def run_reference(args):
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
@@ -199,6 +247,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU legs")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch shape for the film (for profiling runs)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the headline film run (fp32 = FP32-mixed)")
     args = ap.parse_args()
@@ -234,7 +284,7 @@ def main():
         with SpinSystem(lat, alpha=0.02, dt=1e-16, T=300.0, seed=seed + rank, sys_id=rank, precision=precision,
                         stream=stream) as s:
             s.set_temperature_schedule(T)
-            s.set_exec("graph")
+            info = s.info() if args.no_autotune else s.autotune(6)
             s.step(warmup)
             s.sync()
             torch.cuda.synchronize()
@@ -264,7 +314,6 @@ def main():
                 s.record(first + k, 1)
             e2e_s = time.perf_counter() - t0
             mag = s.magnetisation()
-            info = s.info()
         return ms, kt, e2e_s / e2e_steps, ck.summary(local), mag, info
 
     ms32, kt32, e2e32, clk32, mag32, info32 = timed_run(args.precision, args.steps, args.warmup, 5)
@@ -279,8 +328,9 @@ def main():
     step_b = step_bytes_per_spin(4 if args.precision == "fp32" else 8, nnz_per)
     from paper_1310_6143_gb300.system import debug_fp64_rate
 
-    fp64_meas = {f"{name}_inst_per_sm_cycle": debug_fp64_rate(m) / SMS / (sm_ghz * 1e9)
-                 for m, name in ((0, "dfma_shared_operands"), (1, "dfma_distinct_operands"), (2, "dadd"))}
+    fp64_meas = None if args.no_extras else {
+        f"{name}_inst_per_sm_cycle": debug_fp64_rate(m) / SMS / (sm_ghz * 1e9)
+        for m, name in ((0, "dfma_shared_operands"), (1, "dfma_distinct_operands"), (2, "dadd"))}
     hbm_achieved = step_b * lat.n / (ms32 / args.steps * 1e-3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
@@ -290,7 +340,9 @@ def main():
                                "k_u 1.0e-24 || z, alpha 0.02, dt 1e-16 s, T pulse 300->1200 K (100 fs FWHM)",
                    "precision": "fp32-mixed (FP64 Box-Muller and reductions)" if args.precision == "fp32" else "fp64",
                    "spins": lat.n, "nnz": lat.nnz,
-                   "exec": "cuda graph", "block": info32["block"], "tile": info32["tile"],
+                   "exec": EXEC_NAMES[info32["exec"]],
+                   "block": info32["block"], "tile": info32["tile"], "draw_ahead_eighths": info32["draw_ahead"],
+                   "launch_shape": "chosen by spin_system_autotune on the handle",
                    "l2": "state 0.8 GB >> 126 MB L2, no flush needed", "replicas": world},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp64_peak if achieved else None,
@@ -303,7 +355,9 @@ def main():
         "kernels_ms": kt32, "clocks": clk32,
         "e2e": {"value": world * lat.n / e2e32, "unit": "spin-steps/s", "h2d_bytes_per_step": 8,
                 "d2h_bytes_per_step": 64},
-        "gpu_launches": 2 * args.steps,
+        # step kernels launched in the timed region: a predictor and a corrector per step, or
+        # one cooperative launch per 64 steps in the persistent form
+        "gpu_launches": (-(-args.steps // 64)) if info32["exec"] == 3 else 2 * args.steps,
         "final_m": [float(x) for x in mag32],
     }
     if not args.no_extras:
@@ -331,8 +385,9 @@ def main():
             msb = e0.elapsed_time(e1)
         out["batched"] = {"value": world * ng * kb / (msb * 1e-3), "unit": "spin-steps/s", "steps": kb,
                           "systems": 256, "spins": ng, "ms_per_step": msb / kb,
-                          "exec": {0: "auto", 1: "kernels", 2: "graph", 3: "persistent"}[tuned["exec"]],
+                          "exec": EXEC_NAMES[tuned["exec"]],
                           "block": tuned["block"], "tile": tuned["tile"]}
+        out["workloads"] = workload_table(stream, rank)
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(lat, T)
     if rank == 0:

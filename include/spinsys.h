@@ -110,8 +110,10 @@ typedef enum {
     SS_EXEC_AUTO = 0,      /* graphs for long runs, direct launches for short ones  */
     SS_EXEC_KERNELS = 1,   /* one predictor and one corrector launch per step       */
     SS_EXEC_GRAPH = 2,     /* CUDA graphs of captured step launches                 */
-    SS_EXEC_PERSISTENT = 3 /* one cooperative launch runs many steps, with a bounded
+    SS_EXEC_PERSISTENT = 3, /* one cooperative launch runs many steps, with a bounded
                               grid barrier between the Heun passes                  */
+    SS_EXEC_SYSTEM_BLOCKS = 4 /* one thread block advances whole systems for many steps
+                              with block barriers only (batches of small systems)   */
 } ss_exec;
 
 typedef struct {
@@ -127,7 +129,7 @@ typedef struct {
     int64_t step;         /* index of the next step                                   */
     int64_t record_capacity; /* steps kept in the per-step record ring               */
     int64_t device_bytes; /* device memory held by the handle                         */
-    int32_t draw_ahead;   /* quarters of each tile's spins whose next-step Gaussians the
+    int32_t draw_ahead;   /* eighths of each tile's spins whose next-step Gaussians the
                              corrector draws (FP32-mixed form; see spin_system_set_draw_ahead) */
     int32_t pad;
 } ss_info;
@@ -204,10 +206,10 @@ ss_status spin_system_set_exec(ss_system *h, ss_exec mode);
 ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
 
 /* FP32-mixed form: the corrector of step n draws the thermal Gaussians of step n+1 for
- * `quarters`/4 of each tile's spins (rounded down to whole blocks), so that their FP64
+ * `eighths`/8 of each tile's spins (rounded down to whole blocks), so that their FP64
  * transform overlaps the corrector's memory traffic; the predictor draws the rest.
- * 0..4; the default is 3.  Results do not depend on it (the same Gaussians are drawn). */
-ss_status spin_system_set_draw_ahead(ss_system *h, int32_t quarters);
+ * 0..8; the default is 6.  Results do not depend on it (the same Gaussians are drawn). */
+ss_status spin_system_set_draw_ahead(ss_system *h, int32_t eighths);
 
 /* Time the candidate (exec, block, tile, draw-ahead) choices on this handle over `trial_steps`
  * steps each, keep the fastest, and write it to *out_info.  The spins and the step

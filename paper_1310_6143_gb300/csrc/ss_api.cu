@@ -89,7 +89,7 @@ struct ss_system {
     void *state[12] = {};  // sx sy sz px py pz qx qy qz hx hy hz
     void *ahead[3] = {};   // Gaussians drawn ahead by the corrector (FP32-mixed only)
     int pre_slot = 1 << 30;
-    int ahead_q = 3;       // quarters of each tile drawn ahead by the corrector
+    int ahead_q = 6;       // eighths of each tile drawn ahead by the corrector
     bool zero_T = true;    // some temperature in force could be zero (the corrector then
                            // skips drawing those spins ahead)
     SysDesc *sys = nullptr;
@@ -394,6 +394,24 @@ cudaError_t enqueue_kernels(ss_system *h, int64_t n) {
     return h->precision == SS_FP32_MIXED ? enqueue_steps_kernels<float>(h, n) : enqueue_steps_kernels<double>(h, n);
 }
 
+template <typename R>
+cudaError_t enqueue_system_blocks(ss_system *h, int64_t n) {
+    const KArgs<R> a = make_args<R>(h);
+    const int per_sm = std::max(1, step_blocks_per_sm<R>(h->block));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->nsys, (int64_t)h->sm_count * per_sm));
+    while (n > 0) {
+        const long long k = std::min<long long>(n, 1ll << 20);
+        const cudaError_t e = launch_system_blocks<R>(a, h->block, grid, k, h->stream);
+        if (e != cudaSuccess) return e;
+        n -= k;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_sysblocks(ss_system *h, int64_t n) {
+    return h->precision == SS_FP32_MIXED ? enqueue_system_blocks<float>(h, n) : enqueue_system_blocks<double>(h, n);
+}
+
 cudaError_t enqueue_persist(ss_system *h, int64_t n) {
     return h->precision == SS_FP32_MIXED ? enqueue_persistent<float>(h, n) : enqueue_persistent<double>(h, n);
 }
@@ -511,7 +529,7 @@ ss_status build_tiles(ss_system *h) {
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
     h->nfin = std::max(1, std::min(h->nsys, 64));
     const int slots = h->tile / h->block;
-    const int ahead = (h->ahead_q * slots) / 4;                // slots the corrector draws ahead
+    const int ahead = (h->ahead_q * slots) / 8;                // slots the corrector draws ahead
     h->pre_slot = ahead >= 1 ? slots - ahead : 1 << 30;
     SS_CUDA(h, invalidate_ahead(h));
     drop_graph(h);
@@ -554,10 +572,12 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
         const ss_params *p = hs[s].p;
         const int64_t off = hs[s].offset, noff = hs[s].nnz_offset;
         for (int64_t i = 0; i < p->n; ++i) rp[off + i] = (int32_t)(noff + p->row_ptr[i]);
-        for (int64_t k = 0; k < p->row_ptr[p->n]; ++k) {
-            col[noff + k] = (int32_t)(off + p->col[k]);
-            J[noff + k] = (R)p->J[k];
-        }
+        // J stored divided by the row's moment: the exchange sum then is the field (tesla)
+        for (int64_t i = 0; i < p->n; ++i)
+            for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) {
+                col[noff + k] = (int32_t)(off + p->col[k]);
+                J[noff + k] = (R)(p->J[k] / p->mu_s[i]);
+            }
         MatKey last{};
         int32_t last_id = -1;
         for (int64_t i = 0; i < p->n; ++i) {
@@ -979,6 +999,8 @@ ss_status llg_heun_step(ss_system *h, int64_t n) {
             left -= h->graph_steps;
         }
         e = enqueue_kernels(h, left);
+    } else if (mode == SS_EXEC_SYSTEM_BLOCKS) {
+        e = enqueue_sysblocks(h, n);
     } else if (mode == SS_EXEC_PERSISTENT) {
         int64_t left = n;
         if (!h->pgraph_failed) {
@@ -1147,7 +1169,7 @@ ss_status get_step(ss_system *h, int64_t *step) {
 ss_status spin_system_set_exec(ss_system *h, ss_exec mode) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
-    if (mode < SS_EXEC_AUTO || mode > SS_EXEC_PERSISTENT) return fail(h, SS_ERR_INVALID_ARG, "unknown exec mode");
+    if (mode < SS_EXEC_AUTO || mode > SS_EXEC_SYSTEM_BLOCKS) return fail(h, SS_ERR_INVALID_ARG, "unknown exec mode");
     if (mode == SS_EXEC_PERSISTENT && persistent_grid(h) < 1)
         return fail(h, SS_ERR_UNSUPPORTED, "persistent kernel cannot be made co-resident with block %d", h->block);
     h->exec = mode;
@@ -1167,12 +1189,12 @@ ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile) {
     return build_tiles(h);
 }
 
-ss_status spin_system_set_draw_ahead(ss_system *h, int32_t quarters) {
+ss_status spin_system_set_draw_ahead(ss_system *h, int32_t eighths) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
-    if (quarters < 0 || quarters > 4) return fail(h, SS_ERR_INVALID_ARG, "quarters must be 0..4");
+    if (eighths < 0 || eighths > 8) return fail(h, SS_ERR_INVALID_ARG, "eighths must be 0..8");
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
-    h->ahead_q = quarters;
+    h->ahead_q = eighths;
     return build_tiles(h);
 }
 
@@ -1221,11 +1243,16 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     const bool mixed = h->precision == SS_FP32_MIXED;
     for (int b : {256, 512})
         for (int m : {1, 2, 4, 8})
-            for (int q : {2, 3}) {
-                if (!mixed && q != 3) continue;  // no draw-ahead in the FP64 form
+            for (int q : {4, 5, 6}) {
+                if (!mixed && q != 6) continue;  // no draw-ahead in the FP64 form
                 cands.push_back({SS_EXEC_GRAPH, b, b * m, q});
                 cands.push_back({SS_EXEC_PERSISTENT, b, b * m, q});
             }
+    // whole systems per block pays when every system fits a few blocks' worth of threads
+    int64_t biggest = 0;
+    for (int64_t v : h->sys_n) biggest = std::max(biggest, v);
+    if (biggest <= 16384)
+        for (int b : {128, 256, 512}) cands.push_back({SS_EXEC_SYSTEM_BLOCKS, b, b, h->ahead_q});
     cudaEvent_t e0, e1;
     SS_CUDA(h, cudaEventCreate(&e0));
     SS_CUDA(h, cudaEventCreate(&e1));

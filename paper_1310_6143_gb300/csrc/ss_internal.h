@@ -17,7 +17,7 @@ constexpr int kLogScale = 2048;
 constexpr int kLn2Tab = 34;    // 2 n ln 2, n = 0..33, as (hi, lo)
 constexpr int kTrigTab = 513;  // (sin, cos) of pi m / 2048, m = 0..512: one octant of a 4096-point circle
 constexpr int kRecComps = 8;   // record: sum mu S (3), sum mu, E_exc, E_ani, E_app, E_total
-constexpr int kPartComps = 8;  // tile partials: sum mu S (3), E_exc, E_ani, E_app, 0, 0
+constexpr int kPartComps = 8;  // tile partials: sum mu S (3), sum -mu S.h/2, E_ani, 0, 0, 0
 
 // One system of a handle (several when batched).  Lives in device memory; the field and
 // temperature entries are rewritten by set_field / set_temperature between launches.
@@ -67,7 +67,7 @@ struct KArgs {
     int64_t n;
     const int32_t *row_ptr;   // [n+1]
     const int32_t *col;       // [nnz]
-    const R *J;               // [nnz]
+    const R *J;               // [nnz] J_ij / mu_s,i (the exchange field per unit spin, T)
     const int32_t *mat;       // [n] material index
     const MatDesc<R> *mats;
     const SysDesc *sys;
@@ -116,6 +116,8 @@ template <typename R> cudaError_t launch_measure(const KArgs<R> &a, int block, i
 template <typename R> cudaError_t launch_init_sphere(const KArgs<R> &a, cudaStream_t s);
 template <typename R> cudaError_t launch_persistent(const KArgs<R> &a, int block, int grid, int nfin,
                                                     long long nsteps, cudaStream_t s);
+template <typename R> cudaError_t launch_system_blocks(const KArgs<R> &a, int block, int grid, long long nsteps,
+                                                       cudaStream_t s);
 template <typename R> int persistent_blocks_per_sm(int block);
 template <typename R> int step_blocks_per_sm(int block);
 cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,

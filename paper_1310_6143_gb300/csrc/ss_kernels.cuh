@@ -80,13 +80,14 @@ __device__ __forceinline__ void stage_tables(const KArgs<R> &a, SmemTables &t) {
     for (int i = threadIdx.x; i < kTrigTab; i += blockDim.x) t.trig[i] = a.tab_trig[i];
 }
 
-// sum_j J_ij X_j over row i (CSR order, one FMA per term and component).
+// H_app + sum_j (J_ij / mu_s,i) X_j over row i (CSR order, one FMA per term and
+// component): the exchange plus applied field, in tesla.
 template <typename R, bool Coherent>
-__device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int64_t i,
-                                             R &e0, R &e1, R &e2) {
+__device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &sd, const R *X, const R *Y,
+                                             const R *Z, int64_t i, R &e0, R &e1, R &e2) {
     const int32_t b = __ldg(a.row_ptr + i);
     const int32_t e = __ldg(a.row_ptr + i + 1);
-    R x = 0, y = 0, z = 0;
+    R x = sys_H(sd, 0, R()), y = sys_H(sd, 1, R()), z = sys_H(sd, 2, R());
     for (int32_t k = b; k < e; ++k) {
         const int32_t j = __ldg(a.col + k);
         const R Jk = __ldg(a.J + k);
@@ -99,28 +100,22 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const R *X, cons
     e2 = z;
 }
 
-// Deterministic field (tesla) from the exchange sum, in the order exchange, anisotropy,
-// applied field, Neel.
+// Deterministic field (tesla): the exchange + applied field h from exchange_sum, then
+// the anisotropy and Neel terms.  Returns S.e for the anisotropy energy.
 template <typename R>
-__device__ __forceinline__ void det_field(const MatDesc<R> &m, const SysDesc &sd, R s0, R s1, R s2, R e0, R e1, R e2,
-                                          R &H0, R &H1, R &H2) {
-    const R im = m.inv_mu;
-    H0 = e0 * im;
-    H1 = e1 * im;
-    H2 = e2 * im;
+__device__ __forceinline__ R det_field(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R &H0, R &H1,
+                                       R &H2) {
     const R sde = s0 * m.e[0] + s1 * m.e[1] + s2 * m.e[2];
     const R an = m.ani * sde;
-    H0 = fma(an, m.e[0], H0);
-    H1 = fma(an, m.e[1], H1);
-    H2 = fma(an, m.e[2], H2);
-    H0 += sys_H(sd, 0, R());
-    H1 += sys_H(sd, 1, R());
-    H2 += sys_H(sd, 2, R());
+    H0 = fma(an, m.e[0], e0);
+    H1 = fma(an, m.e[1], e1);
+    H2 = fma(an, m.e[2], e2);
     if (m.has_neel) {
         H0 += m.kf[0] * s0 + m.kf[3] * s1 + m.kf[4] * s2;
         H1 += m.kf[3] * s0 + m.kf[1] * s1 + m.kf[5] * s2;
         H2 += m.kf[4] * s0 + m.kf[5] * s1 + m.kf[2] * s2;
     }
+    return sde;
 }
 
 // dS = -gamma/(1+lambda^2) [S x H + lambda S x (S x H)]  (Eq. LLG)
@@ -137,23 +132,24 @@ __device__ __forceinline__ void llg_rhs(R gp, R lam, R s0, R s1, R s2, R H0, R H
     d2 = -gp * fma(lam, x2, c2);
 }
 
-// Per-spin contributions to the reductions of the state S: mu S (3), E_exc, E_ani, E_app.
+// Per-spin contributions to the reductions of the state S: mu S (3), -mu S.h/2 with h the
+// exchange + applied field, and the anisotropy energy.  The applied-field energy is
+// -H.M (H is uniform within a system) and the exchange energy sum(-mu S.h/2) + H.M/2;
+// both are formed from the FP64 sums when a system's record is finalised.
 template <typename R>
-__device__ __forceinline__ void spin_terms(const MatDesc<R> &m, const SysDesc &sd, R s0, R s1, R s2, R e0, R e1,
-                                           R e2, double v[6]) {
+__device__ __forceinline__ void spin_terms(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R sde,
+                                           double v[5]) {
     const R mu = m.mu;
     v[0] = widen(mu * s0);
     v[1] = widen(mu * s1);
     v[2] = widen(mu * s2);
-    v[3] = widen((R)-0.5 * (s0 * e0 + s1 * e1 + s2 * e2));
-    const R sde = s0 * m.e[0] + s1 * m.e[1] + s2 * m.e[2];
+    v[3] = widen((R)-0.5 * mu * (s0 * e0 + s1 * e1 + s2 * e2));
     R ea = -m.ku * sde * sde;
     if (m.has_neel) {
         ea -= m.K[0] * s0 * s0 + m.K[1] * s1 * s1 + m.K[2] * s2 * s2
             + (R)2 * (m.K[3] * s0 * s1 + m.K[4] * s0 * s2 + m.K[5] * s1 * s2);
     }
     v[4] = widen(ea);
-    v[5] = widen(-mu * (s0 * sys_H(sd, 0, R()) + s1 * sys_H(sd, 1, R()) + s2 * sys_H(sd, 2, R())));
 }
 
 // Sum of eight FP64 values over a warp by a transposing butterfly: 9 additions per lane
@@ -231,9 +227,9 @@ __device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDe
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = ld<Coherent>(a.sx + i), s1 = ld<Coherent>(a.sy + i), s2 = ld<Coherent>(a.sz + i);
         R e0, e1, e2;
-        exchange_sum<R, Coherent>(a, a.sx, a.sy, a.sz, i, e0, e1, e2);
+        exchange_sum<R, Coherent>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
         R H0, H1, H2;
-        det_field(m, sd, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+        const R sde = det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         R t0 = 0, t1 = 0, t2 = 0;
         if (sqrtT > (R)0) {
             const R sig = m.sig * sqrtT;
@@ -269,15 +265,15 @@ __device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDe
         a.qx[i] = fma(hdt, d0, s0);
         a.qy[i] = fma(hdt, d1, s1);
         a.qz[i] = fma(hdt, d2, s2);
-        double v[6];
-        spin_terms(m, sd, s0, s1, s2, e0, e1, e2, v);
+        double v[5];
+        spin_terms(m, s0, s1, s2, e0, e1, e2, sde, v);
         if (first) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) acc[c] = v[c];
+            for (int c = 0; c < 5; ++c) acc[c] = v[c];
             first = false;
         } else {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) acc[c] += v[c];
+            for (int c = 0; c < 5; ++c) acc[c] += v[c];
         }
     }
     return block_sum8<BS>(acc, red);
@@ -296,9 +292,9 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = ld<Coherent>(a.px + i), s1 = ld<Coherent>(a.py + i), s2 = ld<Coherent>(a.pz + i);
         R e0, e1, e2;
-        exchange_sum<R, Coherent>(a, a.px, a.py, a.pz, i, e0, e1, e2);
+        exchange_sum<R, Coherent>(a, sd, a.px, a.py, a.pz, i, e0, e1, e2);
         R H0, H1, H2;
-        det_field(m, sd, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+        det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         H0 += ld<Coherent>(a.hx + i);
         H1 += ld<Coherent>(a.hy + i);
         H2 += ld<Coherent>(a.hz + i);
@@ -325,6 +321,30 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
     }
 }
 
+// One record (8 doubles) from the block sums of the per-spin terms (valid in threads 0..7
+// on entry): sum mu S (3), sum mu, E_exc = sum(-mu S.h/2) + H.M/2, E_ani, E_app = -H.M,
+// E_total.  Called by every thread of the block.
+__device__ __forceinline__ void write_record(const SysDesc &sd, double r, double *dst) {
+    __shared__ double comp[8];
+    if (threadIdx.x < 8) comp[threadIdx.x] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double *H = sd.H;
+        const double hm = (H[0] * comp[0] + H[1] * comp[1]) + H[2] * comp[2];  // H.M
+        const double e_app = -hm;
+        const double e_exc = comp[3] + 0.5 * hm;
+        dst[0] = comp[0];
+        dst[1] = comp[1];
+        dst[2] = comp[2];
+        dst[3] = sd.msum;
+        dst[4] = e_exc;
+        dst[5] = comp[4];
+        dst[6] = e_app;
+        dst[7] = (e_exc + comp[4]) + e_app;
+    }
+    __syncthreads();
+}
+
 // Sum the tile partials of system s in tile order and write one record (8 doubles).
 template <int BS, bool Coherent>
 __device__ __forceinline__ void finalize_system(const SysDesc *sys, const int32_t *sys_tiles, const double *partials,
@@ -333,24 +353,10 @@ __device__ __forceinline__ void finalize_system(const SysDesc *sys, const int32_
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int32_t t = t0 + threadIdx.x; t < t1; t += BS) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] += ld<Coherent>(partials + (int64_t)t * kPartComps + c);
+        for (int c = 0; c < 5; ++c) acc[c] += ld<Coherent>(partials + (int64_t)t * kPartComps + c);
     }
     const double r = block_sum8<BS>(acc, red);
-    // threads 0..7 hold components; place them into the record layout
-    __shared__ double comp[8];
-    if (threadIdx.x < 8) comp[threadIdx.x] = r;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        dst[0] = comp[0];
-        dst[1] = comp[1];
-        dst[2] = comp[2];
-        dst[3] = sys[s].msum;
-        dst[4] = comp[3];
-        dst[5] = comp[4];
-        dst[6] = comp[5];
-        dst[7] = (comp[3] + comp[4]) + comp[5];
-    }
-    __syncthreads();
+    write_record(sys[s], r, dst);
 }
 
 // ----------------------------------------------------------------------------------
@@ -421,11 +427,13 @@ __global__ void __launch_bounds__(BS) k_measure(const KArgs<R> a) {
             const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
             const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
             R e0, e1, e2;
-            exchange_sum<R, false>(a, a.sx, a.sy, a.sz, i, e0, e1, e2);
-            double v[6];
-            spin_terms(m, sd, s0, s1, s2, e0, e1, e2, v);
+            exchange_sum<R, false>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
+            R H0, H1, H2;
+            const R sde = det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+            double v[5];
+            spin_terms(m, s0, s1, s2, e0, e1, e2, sde, v);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) acc[c] += v[c];
+            for (int c = 0; c < 5; ++c) acc[c] += v[c];
         }
         const double r = block_sum8<BS>(acc, red);
         if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
@@ -533,6 +541,43 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (ahead) *a.g_step = step0 + (uint64_t)nsteps;
         *a.step = step0 + (uint64_t)nsteps;
+    }
+}
+
+// Whole systems per block: block b advances systems b, b + gridDim.x, ... for nsteps steps
+// each, with block barriers between the Heun passes and no grid-wide synchronisation (the
+// systems are independent).  Every spin a block reads was written by the same block, after
+// a block barrier; loads bypass the non-coherent L1.  Each step's record is summed in the
+// block directly.  The last block to finish advances the step counter.
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long long nsteps) {
+    __shared__ SmemTables tab;
+    __shared__ double red[(BS / 32) * 8];
+    stage_tables(a, tab);
+    __syncthreads();
+    const uint64_t step0 = __ldcg(a.step);
+    for (int s = blockIdx.x; s < a.nsys; s += gridDim.x) {
+        const SysDesc &sd = a.sys[s];
+        TileDesc whole;
+        whole.start = sd.offset;
+        whole.count = (int32_t)sd.n;
+        whole.sys = s;
+        for (long long k = 0; k < nsteps; ++k) {
+            const uint64_t step = step0 + (uint64_t)k;
+            const double r = predictor_tile<R, BS, true>(a, whole, step, tab, red, 1 << 30);
+            write_record(sd, r, a.rec + ((int64_t)(step % (uint64_t)a.rec_cap) * a.nsys + s) * kRecComps);
+            corrector_tile<R, BS, true>(a, whole, step, nullptr);
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int done = atomicAdd(a.ticket, 1u);
+        if (done == gridDim.x - 1) {
+            *a.ticket = 0u;
+            *a.step = step0 + (uint64_t)nsteps;
+            __threadfence();
+        }
     }
 }
 

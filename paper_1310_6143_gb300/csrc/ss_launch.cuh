@@ -78,6 +78,13 @@ cudaError_t launch_persistent(const KArgs<R> &a, int block, int grid, int nfin, 
     return cudaSuccess;
 }
 
+template <typename R>
+cudaError_t launch_system_blocks(const KArgs<R> &a, int block, int grid, long long nsteps, cudaStream_t s) {
+    SS_BLOCK_SWITCH(block, k_system_blocks<R, BS><<<grid, BS, 0, s>>>(a, nsteps));
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_system_blocks<SS_REAL>(const KArgs<SS_REAL> &, int, int, long long, cudaStream_t);
 template cudaError_t launch_predictor<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_corrector<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
 template cudaError_t launch_measure<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);

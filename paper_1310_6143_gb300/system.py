@@ -17,7 +17,7 @@ from .lattice import SpinLattice
 
 _PREC = {"fp64": B.SS_FP64, "fp32": B.SS_FP32_MIXED, "fp32_mixed": B.SS_FP32_MIXED}
 _EXEC = {"auto": B.SS_EXEC_AUTO, "kernels": B.SS_EXEC_KERNELS, "graph": B.SS_EXEC_GRAPH,
-         "persistent": B.SS_EXEC_PERSISTENT}
+         "persistent": B.SS_EXEC_PERSISTENT, "system_blocks": B.SS_EXEC_SYSTEM_BLOCKS}
 
 
 def _per_system(v, count, name):
@@ -155,8 +155,8 @@ class SpinSystem:
     def set_launch(self, block: int, tile: int):
         self._check(self._lib.spin_system_set_launch(self._h, int(block), int(tile)))
 
-    def set_draw_ahead(self, quarters: int):
-        self._check(self._lib.spin_system_set_draw_ahead(self._h, int(quarters)))
+    def set_draw_ahead(self, eighths: int):
+        self._check(self._lib.spin_system_set_draw_ahead(self._h, int(eighths)))
 
     def autotune(self, trial_steps: int = 20) -> dict:
         info = B.SSInfo()

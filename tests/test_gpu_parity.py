@@ -91,7 +91,7 @@ def test_all_terms_ragged_tiles(SS, precision, tol, steps):
 def test_exec_modes_bitwise_identical(SS):
     lat = L.simple_cubic(9, 7, 5)
     out = {}
-    for mode in ("kernels", "graph", "persistent"):
+    for mode in ("kernels", "graph", "persistent", "system_blocks"):
         with SS(lat, alpha=0.1, dt=1e-16, T=400.0, seed=3, precision="fp64") as s:
             s.set_launch(128, 256)
             s.set_exec(mode)
@@ -100,6 +100,38 @@ def test_exec_modes_bitwise_identical(SS):
     for mode in ("graph", "persistent"):
         np.testing.assert_array_equal(out[mode][0], out["kernels"][0])
         np.testing.assert_array_equal(out[mode][1], out["kernels"][1])
+    # whole systems per block: same spins; the record sums in another order
+    np.testing.assert_array_equal(out["system_blocks"][0], out["kernels"][0])
+    np.testing.assert_allclose(out["system_blocks"][1], out["kernels"][1], rtol=1e-13,
+                               atol=1e-13 * np.abs(out["kernels"][1]).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_many_small_systems_one_block_each(SS, precision):
+    """A temperature sweep of 300 small lattices (sizes 27..729, ragged against the block)
+    advanced with one thread block per system equals the per-step launches, and its
+    systems match the oracle."""
+    lats = [L.simple_cubic(3 + k % 7, 3 + (k // 7) % 5, 3 + k % 3) for k in range(300)]
+    kw = dict(alpha=0.1, dt=1e-16, T=[float(3 * k) for k in range(300)], seed=[7 + k for k in range(300)],
+              sys_id=list(range(300)))
+    res = {}
+    for mode in ("kernels", "system_blocks"):
+        with SS(lats, precision=precision, **kw) as s:
+            s.set_launch(128, 128)
+            s.set_exec(mode)
+            s.step(37)
+            res[mode] = (s.spins(), s.record(0, 37), s.step_index)
+    np.testing.assert_array_equal(res["system_blocks"][0], res["kernels"][0])
+    assert res["system_blocks"][2] == 37
+    np.testing.assert_allclose(res["system_blocks"][1], res["kernels"][1], rtol=1e-12,
+                               atol=1e-12 * np.abs(res["kernels"][1]).max())
+    if precision == "fp64":
+        off = 0
+        for k in (0, 151, 299):
+            off = sum(l.n for l in lats[:k])
+            S_ref, _ = O.heun_run(oracle_system(lats[k], seed=7 + k, sys_id=k), L.uniform_state(lats[k].n), 37,
+                                  3.0 * k)
+            assert np.abs(res["system_blocks"][0][off:off + lats[k].n] - S_ref).max() <= TOL64
 
 
 def test_launch_shapes_agree(SS):
