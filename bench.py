@@ -49,21 +49,30 @@ def step_bytes_per_spin(real_bytes, nnz_per_spin):
     return 18 * real_bytes + 2 * (nnz_per_spin * (4 + real_bytes) + 4)
 
 
-# FP64 pipe instructions per spin and DRAM bytes per launch of each step kernel on the
-# film in the default launch shape (block 512, 8 spins per thread, 3/4 of the Gaussians
-# drawn ahead by the corrector), from ncu (profiles/k_predictor_film1024x1024x16_fp32.md,
+# FP64 pipe instructions per spin of the FP32-mixed step kernels.  One thermal draw (the
+# table-driven FP64 Box-Muller) costs 29 FP64 instructions; the corrector draws a fraction
+# f of them for the next step, the predictor the rest.  The FP64 moment/energy sums cost
+# 5 DADD per spin accumulated per thread over `spt` spins plus a 9-add warp butterfly.
+# For the default film shape (block 512, 8 spins per thread, f = 6/8) this gives 12.8 and
+# 21.75, the values ncu counts (profiles/k_predictor_film1024x1024x16_fp32.md,
 # profiles/k_corrector_film1024x1024x16_fp32.md).  Each FP64 instruction (DADD, DMUL or
 # DFMA) takes one FMA slot of the pipe (2 slots per cycle per SM), so it counts as 2
 # flop-equivalents, the convention of the chip's FP64 rating.
-KERNEL_FP64_INST_PER_SPIN = {
-    "fp32": {"k_predictor": 7.03 + 1.25 + 4.50, "k_corrector": 4.50 + 3.75 + 13.50},
-    "fp64": {"k_predictor": None, "k_corrector": None},
-}
-KERNEL_DRAM_BYTES = {
-    "fp32": {"k_predictor": 1.286e9 + 0.578e9, "k_corrector": 1.545e9 + 0.337e9},  # per launch
-    "fp64": {"k_predictor": None, "k_corrector": None},
-}
+FP64_PER_DRAW = 29.0
+
+
+def fp64_inst_per_spin(kernel, block, tile, draw_ahead_eighths):
+    spt = tile // block
+    f = ((draw_ahead_eighths * spt) // 8) / spt
+    if kernel == "k_corrector":
+        return FP64_PER_DRAW * f
+    return FP64_PER_DRAW * (1 - f) + 5.0 * (spt - 1) / spt + 9.0 / spt
+
+
+# DRAM bytes per launch of the default film shape, from the same ncu captures.
+KERNEL_DRAM_BYTES = {"k_predictor": 1.286e9 + 0.578e9, "k_corrector": 1.545e9 + 0.337e9}
 SMS = 152
+NO_AUTOTUNE = False
 EXEC_NAMES = {0: "auto", 1: "kernels", 2: "graph", 3: "persistent", 4: "system_blocks"}
 FP64_SLOTS_PER_SM_CYCLE = 2
 
@@ -170,6 +179,7 @@ def cpu_baseline(lat, T, seconds=15.0):
 
 
 def time_workload(lats, kw, precision, steps, stream, warmup=5, autotune=True):
+    autotune = autotune and not NO_AUTOTUNE
     """spin-steps/s of `steps` Heun steps on one handle (CUDA events on its stream)."""
     import torch
 
@@ -247,8 +257,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU legs")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the library's default launch shape for the film (for profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true", help="no autotuning in the batched and workload legs")
+    ap.add_argument("--autotune-film", action="store_true",
+                    help="autotune the film's launch shape too (default: the library's default shape, "
+                         "whose ncu counters are in profiles/)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the headline film run (fp32 = FP32-mixed)")
     args = ap.parse_args()
@@ -257,6 +269,8 @@ def main():
         return
     if args.warmup < 3:
         args.warmup = 3
+    global NO_AUTOTUNE
+    NO_AUTOTUNE = args.no_autotune
 
     world, rank, local = dist_init()
     import torch
@@ -284,7 +298,7 @@ def main():
         with SpinSystem(lat, alpha=0.02, dt=1e-16, T=300.0, seed=seed + rank, sys_id=rank, precision=precision,
                         stream=stream) as s:
             s.set_temperature_schedule(T)
-            info = s.info() if args.no_autotune else s.autotune(6)
+            info = s.autotune(6) if args.autotune_film else s.info()
             s.step(warmup)
             s.sync()
             torch.cuda.synchronize()
@@ -323,8 +337,10 @@ def main():
     # the dominant kernel of the step, by live CUDA-event time
     dom = "k_predictor" if kt32["predictor_ms"] >= kt32["corrector_ms"] else "k_corrector"
     dom_ms = kt32["predictor_ms"] if dom == "k_predictor" else kt32["corrector_ms"]
-    inst = KERNEL_FP64_INST_PER_SPIN[args.precision][dom]
+    inst = fp64_inst_per_spin(dom, info32["block"], info32["tile"], info32["draw_ahead"]) \
+        if args.precision == "fp32" else None
     achieved = 2 * inst * lat.n / (dom_ms * 1e-3) / 1e12 if inst else None
+    default_shape = (info32["block"], info32["tile"], info32["draw_ahead"]) == (512, 4096, 6)
     step_b = step_bytes_per_spin(4 if args.precision == "fp32" else 8, nnz_per)
     from paper_1310_6143_gb300.system import debug_fp64_rate
 
@@ -340,14 +356,16 @@ def main():
                                "k_u 1.0e-24 || z, alpha 0.02, dt 1e-16 s, T pulse 300->1200 K (100 fs FWHM)",
                    "precision": "fp32-mixed (FP64 Box-Muller and reductions)" if args.precision == "fp32" else "fp64",
                    "spins": lat.n, "nnz": lat.nnz,
-                   "exec": EXEC_NAMES[info32["exec"]],
+                   "exec": EXEC_NAMES[info32["exec"]] if info32["exec"] else "auto (captured graphs of step launches)",
                    "block": info32["block"], "tile": info32["tile"], "draw_ahead_eighths": info32["draw_ahead"],
-                   "launch_shape": "chosen by spin_system_autotune on the handle",
+                   "launch_shape": "spin_system_autotune" if args.autotune_film else "library default",
                    "l2": "state 0.8 GB >> 126 MB L2, no flush needed", "replicas": world},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp64_peak if achieved else None,
-                     "traffic": KERNEL_DRAM_BYTES[args.precision][dom], "kernel": dom, "kernel_ms": dom_ms,
-                     "pipe": "fp64", "per_unit": f"{inst} FP64 instructions per spin, 2 flop-equivalents each",
+                     "traffic": KERNEL_DRAM_BYTES[dom] if (default_shape and args.precision == "fp32") else None,
+                     "kernel": dom, "kernel_ms": dom_ms,
+                     "pipe": "fp64", "per_unit": f"{inst:.2f} FP64 instructions per spin, 2 flop-equivalents each"
+                     if inst else None,
                      "peak_source": f"152 SMs x 2 FP64 slots/cycle x 2 x {sm_ghz:.3f} GHz (measured clock)",
                      "measured_fp64_rate": fp64_meas},
         "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
@@ -372,7 +390,7 @@ def main():
         ng = sum(g.n for g in grains)
         with SpinSystem(grains, alpha=0.1, dt=1e-16, T=list(temps), seed=[4000 + k for k in range(256)],
                         sys_id=list(range(256)), precision="fp32", stream=stream) as b:
-            tuned = b.autotune(10)
+            tuned = b.info() if args.no_autotune else b.autotune(10)
             b.step(args.warmup)
             b.sync()
             kb = max(50, args.steps // 2)
