@@ -303,6 +303,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.gz = static_cast<R *>(h->ahead[2]);
     a.g_step = h->ahead[0] ? h->ctl + 3 : nullptr;
     a.pre_slot = h->pre_slot;
+    a.slots = std::max(1, h->tile / h->block);
     a.partials = h->partials;
     a.rec = h->rec;
     a.rec_cap = h->rec_cap;

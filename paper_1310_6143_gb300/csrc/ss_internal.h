@@ -81,8 +81,10 @@ struct KArgs {
     R *hx, *hy, *hz;          // thermal field of the current step
     R *gx, *gy, *gz;          // Gaussians of the next step drawn by the corrector (FP32-mixed)
     unsigned long long *g_step; // step whose Gaussians gx..gz hold (tile slots >= pre_slot)
-    int pre_slot;             // first tile slot (spin k of a tile: slot k / block) whose
-                              // Gaussians the corrector draws ahead; >= slots: none
+    int pre_slot;             // Gaussians of a tile slot (spin k of a tile: slot k / block) are
+                              // drawn ahead by the corrector when its rotated index
+                              // (slot + warp) mod slots is >= pre_slot; >= slots: none
+    int slots;                // tile / block
     double *partials;         // [ntiles * kPartComps]
     double *rec;              // ring [rec_cap][nsys][kRecComps]
     int64_t rec_cap;

@@ -221,8 +221,10 @@ __device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDe
     const R sqrtT = sqrtT_of_step(a, step, sd);
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     bool first = true;
-    int slot = 0;
-    for (int k = threadIdx.x; k < td.count; k += BS, ++slot) {
+    // The slot index is rotated by the warp index, so that the warps of a block reach their
+    // FP64-heavy slots (the Gaussians not drawn ahead) at different times.
+    int rot = (threadIdx.x >> 5) % a.slots;
+    for (int k = threadIdx.x; k < td.count; k += BS, rot = rot + 1 == a.slots ? 0 : rot + 1) {
         const int64_t i = td.start + k;
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = ld<Coherent>(a.sx + i), s1 = ld<Coherent>(a.sy + i), s2 = ld<Coherent>(a.sz + i);
@@ -233,7 +235,7 @@ __device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDe
         R t0 = 0, t1 = 0, t2 = 0;
         if (sqrtT > (R)0) {
             const R sig = m.sig * sqrtT;
-            if (slot >= pre_slot) {  // drawn ahead by the previous corrector
+            if (rot >= pre_slot) {  // drawn ahead by the previous corrector
                 t0 = sig * ld<Coherent>(a.gx + i);
                 t1 = sig * ld<Coherent>(a.gy + i);
                 t2 = sig * ld<Coherent>(a.gz + i);
@@ -286,8 +288,8 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
     // Gaussians of step + 1 for the slots the next predictor will not draw (FP32-mixed):
     // this puts FP64 transform work next to the corrector's memory traffic.
     const R sqrtT_next = tab ? sqrtT_of_step(a, step + 1, sd) : (R)0;
-    int slot = 0;
-    for (int k = threadIdx.x; k < td.count; k += BS, ++slot) {
+    int rot = (threadIdx.x >> 5) % a.slots;  // the predictor's rotated slot index
+    for (int k = threadIdx.x; k < td.count; k += BS, rot = rot + 1 == a.slots ? 0 : rot + 1) {
         const int64_t i = td.start + k;
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = ld<Coherent>(a.px + i), s1 = ld<Coherent>(a.py + i), s2 = ld<Coherent>(a.pz + i);
@@ -309,7 +311,7 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
         a.sx[i] = v0 * inv;
         a.sy[i] = v1 * inv;
         a.sz[i] = v2 * inv;
-        if (slot >= a.pre_slot && sqrtT_next > (R)0) {
+        if (rot >= a.pre_slot && sqrtT_next > (R)0) {
             const Philox4 w =
                 philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)(step + 1), sd.ctr2, 0u, sd.key0, sd.key1);
             double g0, g1, g2;
