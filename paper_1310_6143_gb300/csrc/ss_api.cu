@@ -98,7 +98,7 @@ struct ss_system {
     float *sched_f = nullptr;
     int64_t rec_cap = 0, sched_len = 0, sched_step0 = 0, sched_cap = 0;
     unsigned long long *ctl = nullptr;  // [0] step, [1] err|ticket, [2] barrier count|gen
-    double2 *tab = nullptr;             // log | ln2 | trig
+    double2 *tab = nullptr;             // Box-Muller tables (build_bm_tables)
 
     std::vector<SysDesc> hsys;
     std::vector<int64_t> sys_offset, sys_n;
@@ -258,25 +258,10 @@ ss_status validate(const ss_params *p, int idx) {
     return SS_OK;
 }
 
-// Function tables of the table-driven FP64 Box-Muller transform, evaluated in long double.
+// Function tables of the table-driven FP64 Box-Muller transform.
 void build_tables(std::vector<double2> &t) {
-    t.resize(kLogTab + kLn2Tab + kTrigTab);
-    for (int i = 0; i < kLogTab; ++i) {
-        const long double c = (long double)(kLogFirst + i) / (long double)kLogScale;
-        const double inv = (double)(1.0L / c);
-        t[i] = make_double2(inv, (double)(-2.0L * logl((long double)inv)));
-    }
-    const long double ln2 = 0.693147180559945309417232121458176568L;
-    for (int i = 0; i < kLn2Tab; ++i) {
-        const long double v = 2.0L * (long double)i * ln2;
-        const double hi = (double)v;
-        t[kLogTab + i] = make_double2(hi, (double)(v - (long double)hi));
-    }
-    const long double twopi = 6.283185307179586476925286766559005768L;
-    for (int j = 0; j < kTrigTab; ++j) {
-        const long double a = twopi * (long double)j / 4096.0L;  // first octant of 4096 points
-        t[kLogTab + kLn2Tab + j] = make_double2((double)sinl(a), (double)cosl(a));
-    }
+    t.resize(kTabCount);
+    build_bm_tables(t.data());
 }
 
 template <typename R>
@@ -317,9 +302,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.ticket = reinterpret_cast<unsigned int *>(h->ctl + 1) + 1;
     a.bar_count = reinterpret_cast<unsigned int *>(h->ctl + 2);
     a.bar_gen = reinterpret_cast<unsigned int *>(h->ctl + 2) + 1;
-    a.tab_log = h->tab;
-    a.tab_ln2 = h->tab + kLogTab;
-    a.tab_trig = h->tab + kLogTab + kLn2Tab;
+    a.tab = h->tab;
     a.bar_extra = h->bar_extra;
     a.bar_timeout_ns = h->bar_timeout_ns;
     return a;
@@ -349,8 +332,12 @@ int step_grid(const ss_system *h) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(h->ntiles, g));
 }
 
+// One wave of resident corrector blocks (the finalisation blocks come on top).
 int corrector_grid(const ss_system *h) {
-    const int64_t g = (int64_t)h->sm_count * (2048 / h->block);
+    const bool ahead = h->ahead[0] != nullptr;
+    const int per_sm = h->precision == SS_FP32_MIXED ? corrector_blocks_per_sm<float>(h->block, ahead)
+                                                     : corrector_blocks_per_sm<double>(h->block, ahead);
+    const int64_t g = (int64_t)h->sm_count * std::max(per_sm, 1);
     return (int)std::max<int64_t>(1, std::min<int64_t>(h->ntiles, g));
 }
 
@@ -1321,7 +1308,7 @@ ss_status ss_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, int64_t
     if (e == cudaSuccess) e = cudaMalloc(&d, (size_t)std::max<int64_t>(n, 1) * 3 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(dt, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = launch_debug_gaussians(seed, sys, step, n, mode, dt, dt + kLogTab, dt + kLogTab + kLn2Tab, d, nullptr);
+        e = launch_debug_gaussians(seed, sys, step, n, mode, dt, d, nullptr);
     if (e == cudaSuccess) e = cudaMemcpy(out, d, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost);
     if (d) cudaFree(d);
     if (dt) cudaFree(dt);

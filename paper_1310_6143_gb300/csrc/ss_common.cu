@@ -1,5 +1,8 @@
 // Precision-independent kernels: the per-system finalisation of on-demand measurements
 // and the diagnostic Philox / Gaussian kernels used by the tests.
+#include <cmath>
+#include <cstring>
+
 #include "ss_kernels.cuh"
 
 namespace ss {
@@ -32,18 +35,15 @@ cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long 
 
 // mode 0: the step kernels' table-driven transform; mode 1: CUDA's log/sqrt/sincospi.
 __global__ void k_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
-                                  const double2 *tab_log, const double2 *tab_ln2, const double2 *tab_trig,
-                                  double *out) {
+                                  const double2 *tabs, double *out) {
     __shared__ SmemTables tab;
-    for (int i = threadIdx.x; i < kLogTab; i += blockDim.x) tab.log_[i] = tab_log[i];
-    for (int i = threadIdx.x; i < kLn2Tab; i += blockDim.x) tab.ln2[i] = tab_ln2[i];
-    for (int i = threadIdx.x; i < kTrigTab; i += blockDim.x) tab.trig[i] = tab_trig[i];
+    stage_bm_tables(tabs, tab);
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const Philox4 w = philox4x32_10((uint32_t)i, step, sys, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
         double g0, g1, g2;
         if (mode == 0) {
-            box_muller3(w, tab.log_, tab.ln2, tab.trig, g0, g1, g2);
+            box_muller3(w, tab, g0, g1, g2);
         } else {
             box_muller3_libm(w, g0, g1, g2);
         }
@@ -54,10 +54,41 @@ __global__ void k_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, lo
 }
 
 cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
-                                   const double2 *tab_log, const double2 *tab_ln2, const double2 *tab_trig,
-                                   double *out, cudaStream_t s) {
-    k_debug_gaussians<<<256, 256, 0, s>>>(seed, sys, step, n, mode, tab_log, tab_ln2, tab_trig, out);
+                                   const double2 *tab, double *out, cudaStream_t s) {
+    k_debug_gaussians<<<256, 256, 0, s>>>(seed, sys, step, n, mode, tab, out);
     return cudaGetLastError();
+}
+
+// Box-Muller tables (layout in SmemTables), evaluated in long double.  The log and ln 2
+// constants are split as 2^-45 M + remainder with M an integer stored in the bits of a
+// double slot; the remainders of the log table are floats packed after the trig table.
+void build_bm_tables(double2 *t) {
+    const long double q = 35184372088832.0L;  // 2^45
+    float *lolog = reinterpret_cast<float *>(t + kLogTab + kLn2Tab + kTrigTab);
+    for (int i = 0; i < 4 * kLogLo; ++i) lolog[i] = 0.0f;
+    for (int i = 0; i < kLogTab; ++i) {
+        const long double c = (long double)(kLogFirst + i) / (long double)kLogScale;
+        const double inv = (double)(1.0L / c);
+        const long double T = -2.0L * logl((long double)inv);
+        const long long M = llroundl(T * q);
+        double mbits;
+        std::memcpy(&mbits, &M, sizeof(mbits));
+        t[i] = make_double2(inv, mbits);
+        lolog[i] = (float)(T - (long double)M / q);
+    }
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    for (int i = 0; i < kLn2Tab; ++i) {
+        const long double v = 2.0L * (long double)i * ln2;
+        const long long N = llroundl(v * q);
+        double nbits;
+        std::memcpy(&nbits, &N, sizeof(nbits));
+        t[kLogTab + i] = make_double2(nbits, (double)(v - (long double)N / q));
+    }
+    const long double twopi = 6.283185307179586476925286766559005768L;
+    for (int j = 0; j < kTrigTab; ++j) {
+        const long double a = twopi * (long double)j / 4096.0L;  // first octant of 4096 points
+        t[kLogTab + kLn2Tab + j] = make_double2((double)sinl(a), (double)cosl(a));
+    }
 }
 
 // FP64 instruction throughput probe: eight independent chains per thread.  mode 0: DFMA

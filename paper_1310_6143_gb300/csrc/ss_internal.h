@@ -14,8 +14,11 @@ constexpr double kGammaDefault = 1.76e11;   // 1/(T s)
 constexpr int kLogTab = 1537;  // centres c_t = (kLogFirst + t)/kLogScale, t = 0..1536: [0.75, 1.5]
 constexpr int kLogFirst = 1536;
 constexpr int kLogScale = 2048;
-constexpr int kLn2Tab = 34;    // 2 n ln 2, n = 0..33, as (hi, lo)
+constexpr int kLn2Tab = 34;    // 2 n ln 2, n = 0..33, as a multiple of 2^-45 and a remainder
 constexpr int kTrigTab = 513;  // (sin, cos) of pi m / 2048, m = 0..512: one octant of a 4096-point circle
+constexpr int kLogLo = (kLogTab + 3) / 4;  // double2 slots holding the kLogTab float remainders
+// One table buffer of double2: log | ln2 | trig | log remainders (floats, packed four per slot).
+constexpr int kTabCount = kLogTab + kLn2Tab + kTrigTab + kLogLo;
 constexpr int kRecComps = 8;   // record: sum mu S (3), sum mu, E_exc, E_ani, E_app, E_total
 constexpr int kPartComps = 8;  // tile partials: sum mu S (3), sum -mu S.h/2, E_ani, 0, 0, 0
 
@@ -96,9 +99,7 @@ struct KArgs {
     int64_t sched_step0;
     unsigned int *err;        // bit 0: non-finite spin, bit 1: barrier timeout
     unsigned int *ticket;     // completion counter of the corrector launch
-    const double2 *tab_log;   // (1/c_t, 2 ln c_t) rounded from 1/c_t
-    const double2 *tab_ln2;   // (hi, lo) of 2 n ln 2
-    const double2 *tab_trig;  // (sin, cos) of 2 pi j / 512
+    const double2 *tab;       // Box-Muller tables, kTabCount entries (build_bm_tables)
     unsigned int *bar_count;  // grid barrier of the persistent kernel
     unsigned int *bar_gen;
     unsigned int bar_extra;   // test hook: phantom blocks the barrier waits for
@@ -122,13 +123,16 @@ template <typename R> cudaError_t launch_system_blocks(const KArgs<R> &a, int bl
                                                        cudaStream_t s);
 template <typename R> int persistent_blocks_per_sm(int block);
 template <typename R> int step_blocks_per_sm(int block);
+template <typename R> int corrector_blocks_per_sm(int block, bool draw_ahead);
 cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
                             double *dst, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long long count, uint32_t *out,
                                 cudaStream_t s);
 cudaError_t fp64_rate(int mode, double *inst_per_s);
 cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
-                                   const double2 *tab_log, const double2 *tab_ln2, const double2 *tab_trig,
-                                   double *out, cudaStream_t s);
+                                   const double2 *tab, double *out, cudaStream_t s);
+
+// Host (ss_common.cu): fills the kTabCount entries of the Box-Muller tables.
+void build_bm_tables(double2 *t);
 
 }  // namespace ss

@@ -66,18 +66,9 @@ __device__ __forceinline__ double rsqrt_r<double>(double x) {
 __device__ __forceinline__ bool bad_inv(float v) { return !(v < 3.0e38f); }
 __device__ __forceinline__ bool bad_inv(double v) { return ((__double2hiint(v) >> 20) & 0x7FF) == 0x7FF; }
 
-// Shared-memory copies of the Box-Muller function tables.
-struct SmemTables {
-    double2 log_[kLogTab];
-    double2 ln2[kLn2Tab];
-    double2 trig[kTrigTab];
-};
-
 template <typename R>
 __device__ __forceinline__ void stage_tables(const KArgs<R> &a, SmemTables &t) {
-    for (int i = threadIdx.x; i < kLogTab; i += blockDim.x) t.log_[i] = a.tab_log[i];
-    for (int i = threadIdx.x; i < kLn2Tab; i += blockDim.x) t.ln2[i] = a.tab_ln2[i];
-    for (int i = threadIdx.x; i < kTrigTab; i += blockDim.x) t.trig[i] = a.tab_trig[i];
+    stage_bm_tables(a.tab, t);
 }
 
 // H_app + sum_j (J_ij / mu_s,i) X_j over row i (CSR order, one FMA per term and
@@ -243,7 +234,7 @@ __device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDe
                 const Philox4 w =
                     philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
                 double g0, g1, g2;
-                box_muller3(w, tab.log_, tab.ln2, tab.trig, g0, g1, g2);
+                box_muller3(w, tab, g0, g1, g2);
                 t0 = sig * narrow<R>(g0);
                 t1 = sig * narrow<R>(g1);
                 t2 = sig * narrow<R>(g2);
@@ -315,7 +306,7 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
             const Philox4 w =
                 philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)(step + 1), sd.ctr2, 0u, sd.key0, sd.key1);
             double g0, g1, g2;
-            box_muller3(w, tab->log_, tab->ln2, tab->trig, g0, g1, g2);
+            box_muller3(w, *tab, g0, g1, g2);
             a.gx[i] = narrow<R>(g0);
             a.gy[i] = narrow<R>(g1);
             a.gz[i] = narrow<R>(g2);
@@ -463,7 +454,7 @@ __global__ void k_init_sphere(const KArgs<R> a) {
             const int64_t i = td.start + k;
             const Philox4 w = philox4x32_10((uint32_t)(i - sd.offset), 0xFFFFFFFFu, sd.ctr2, 1u, sd.key0, sd.key1);
             double g0, g1, g2;
-            box_muller3(w, tab.log_, tab.ln2, tab.trig, g0, g1, g2);
+            box_muller3(w, tab, g0, g1, g2);
             const double inv = 1.0 / sqrt(g0 * g0 + g1 * g1 + g2 * g2);
             a.sx[i] = (R)(g0 * inv);
             a.sy[i] = (R)(g1 * inv);

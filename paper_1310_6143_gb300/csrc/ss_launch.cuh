@@ -69,6 +69,29 @@ int step_blocks_per_sm(int block) {
     return e == cudaSuccess ? nb : 0;
 }
 
+// Resident blocks per SM of the corrector variant the handle launches.
+template <typename R>
+int corrector_blocks_per_sm(int block, bool draw_ahead) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (block) {
+        case 128:
+            e = draw_ahead ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 128, true>, 128, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 128, false>, 128, 0);
+            break;
+        case 256:
+            e = draw_ahead ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 256, true>, 256, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 256, false>, 256, 0);
+            break;
+        case 512:
+            e = draw_ahead ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 512, true>, 512, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 512, false>, 512, 0);
+            break;
+        default: break;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
 template <typename R>
 cudaError_t launch_persistent(const KArgs<R> &a, int block, int grid, int nfin, long long nsteps, cudaStream_t s) {
     KArgs<R> args = a;
@@ -92,5 +115,6 @@ template cudaError_t launch_init_sphere<SS_REAL>(const KArgs<SS_REAL> &, cudaStr
 template cudaError_t launch_persistent<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, long long, cudaStream_t);
 template int persistent_blocks_per_sm<SS_REAL>(int);
 template int step_blocks_per_sm<SS_REAL>(int);
+template int corrector_blocks_per_sm<SS_REAL>(int, bool);
 
 }  // namespace ss

@@ -17,11 +17,15 @@
 //     the table's rounded 1/c defines the split exactly), and
 //     -2 ln u = 2 n ln 2 - 2 ln c - 2r + r^2 - r^3 (2/3 - r/2 + 2r^2/5) (Taylor series of
 //     2 log1p(r), |r| < 6.6e-4).  The r^3 tail is below 1.9e-10, so single precision
-//     evaluates it to an absolute 2e-17; the leading terms stay in FP64.  Near u = 1
-//     (n = 0, c = 1, r exact) the result keeps its relative accuracy.
-//   * sqrt from a reciprocal square root refined to about 2^-45 in single precision with
-//     error-free float products, then one coupled Newton (Goldschmidt) step in FP64 (the
-//     same seed serves the FP64 form's renormalisation, rsqrt_pos).
+//     evaluates it to an absolute 2e-17; the leading terms stay in FP64.  The tables hold
+//     2 n ln 2 and -2 ln c as integer multiples of 2^-45 plus small remainders, so the sum
+//     of the two leading constants is an exact integer difference whose double is built
+//     from its bits (no FP64 instruction); the remainders join the single-precision tail.
+//     Near u = 1 (n = 0, c = 1, r exact) the result keeps its relative accuracy.
+//   * sqrt(x): 1/sqrt(x) refined to about 2^-45 in single precision with error-free float
+//     products, s = sqrt(x) from it as a float pair, then one Newton step in FP64,
+//     sqrt(x) = s + (x - s^2) / (2s), the residual from one FMA (the same seed serves the
+//     FP64 form's renormalisation, rsqrt_pos).
 //   * sin/cos of 2 pi t / 2^33 (t = 2w+1, an exact binary angle) by the nearest of 4096
 //     angles a (tabulated for one octant, the rest by exact symmetries) and the remainder
 //     d = 2 pi rho / 2^33, |d| <= pi/4096: sin(a+d) = cos a sin d + sin a cos d,
@@ -29,7 +33,8 @@
 //     cos d = (1 - d^2/2) + d^4/24 (dropped terms below 2.2e-18).  d is carried as a pair
 //     of floats (rho is exact in single precision); only the products of the table values
 //     with the leading parts of sin d and cos d run in FP64, the rest in single precision
-//     (those parts are below 1e-10, so within 1e-17 absolute).
+//     (those parts are below 1e-10, so within 1e-17 absolute).  1 - p/2 (p = d^2 rounded
+//     to float) is exact in double for p >= 2^-29 and is built from the bits of p.
 // All results are within a few units in the last place of the correctly rounded values;
 // the tests compare them with CUDA's own log, sqrt and sincospi and with the CPU oracle.
 #pragma once
@@ -43,6 +48,27 @@ namespace ss {
 struct Philox4 {
     uint32_t w0, w1, w2, w3;
 };
+
+// Shared-memory copy of the Box-Muller tables (build_bm_tables):
+//   log_[t] = (1/c_t rounded to double, M_t as int64 bits), M_t = round(2^45 T_t) with
+//             T_t = -2 ln(that rounded 1/c_t) = 2 ln c_t up to the rounding of 1/c_t;
+//   lolog[t] = T_t - 2^-45 M_t (|.| <= 2^-46);
+//   ln2[n] = (N_n as int64 bits, 2 n ln 2 - 2^-45 N_n), N_n = round(2^45 2 n ln 2);
+//   trig[m] = (sin, cos) of pi m / 2048.
+struct SmemTables {
+    double2 log_[kLogTab];
+    double2 ln2[kLn2Tab];
+    double2 trig[kTrigTab];
+    float lolog[kLogTab];
+};
+
+__device__ __forceinline__ void stage_bm_tables(const double2 *tab, SmemTables &t) {
+    for (int i = threadIdx.x; i < kLogTab; i += blockDim.x) t.log_[i] = tab[i];
+    for (int i = threadIdx.x; i < kLn2Tab; i += blockDim.x) t.ln2[i] = tab[kLogTab + i];
+    for (int i = threadIdx.x; i < kTrigTab; i += blockDim.x) t.trig[i] = tab[kLogTab + kLn2Tab + i];
+    const float *lo = reinterpret_cast<const float *>(tab + kLogTab + kLn2Tab + kTrigTab);
+    for (int i = threadIdx.x; i < kLogTab; i += blockDim.x) t.lolog[i] = lo[i];
+}
 
 __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                                  uint32_t k0, uint32_t k1) {
@@ -95,9 +121,16 @@ __device__ __forceinline__ float d2f_small(double x) {
     return ex >= 897u ? d2f_bits(x) : 0.0f;
 }
 
-// -2 ln((w + 1/2) 2^-32).  tab_log[t] = (1/c_t rounded, -2 ln(that rounded value)),
-// tab_ln2[n] = 2 n ln 2 as (hi, lo).  Five FP64 instructions.
-__device__ __forceinline__ double neg2log_u(uint32_t w, const double2 *tab_log, const double2 *tab_ln2) {
+// m 2^-45 as a double for 0 <= m < 2^53 (exact), assembled from the integer bits.
+__device__ __forceinline__ double fixed45_to_double(uint64_t m) {
+    const int lz = __clzll((long long)m);                        // m in [2^(63-lz), 2^(64-lz))
+    const uint64_t mn = m << ((lz - 11) & 63);                   // leading one at bit 52
+    const uint64_t bits = ((uint64_t)(1023 + 18 - 1 - lz) << 52) + mn;  // exponent 18 - lz
+    return m ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+// -2 ln((w + 1/2) 2^-32) from the tables of SmemTables.  Four FP64 instructions.
+__device__ __forceinline__ double neg2log_u(uint32_t w, const SmemTables &tab) {
     const uint64_t m = 2ull * w + 1ull;              // u = m 2^-33, m odd, < 2^33
     const int lz = __clzll((long long)m);
     const int k = 63 - lz;                           // m in [2^k, 2^(k+1)), k <= 32
@@ -109,21 +142,28 @@ __device__ __forceinline__ double neg2log_u(uint32_t w, const double2 *tab_log, 
     // nearest centre c = j/2048: j = round(2048 f')
     const uint32_t j = big ? (uint32_t)(1024u + (uint32_t)((frac + (1ull << 41)) >> 42))
                            : (uint32_t)(2048u + (uint32_t)((frac + (1ull << 40)) >> 41));
-    const double2 tl = tab_log[j - (uint32_t)kLogFirst];
-    const double2 tn = tab_ln2[n];
+    const double2 tl = tab.log_[j - (uint32_t)kLogFirst];
+    const double2 tn = tab.ln2[n];
     const double r = fma(fp, tl.x, -1.0);            // f'/c - 1 up to one rounding
     const float rf = d2f_small(r);
     const float tail = ((rf * rf) * rf) * fmaf(rf, fmaf(rf, 0.4f, -0.5f), 2.0f / 3.0f);
-    const double c = f2d_bits(d2f_small(tn.y) - tail);   // lo part of 2 n ln 2, minus the tail
+    // 2 n ln 2 - T = 2^-45 (N - M) + (remainders); N - M >= 0 (the result is positive
+    // for n >= 1, and c <= 1 for n = 0) and < 2^51
+    const uint64_t nm = (uint64_t)__double_as_longlong(tn.x) - (uint64_t)__double_as_longlong(tl.y);
+    const float lo = d2f_small(tn.y) - tab.lolog[j - (uint32_t)kLogFirst];
+    const double c = f2d_bits(lo - tail);                // remainders minus the tail
     const double b = fma(-2.0, r, fma(r, r, c));         // -2r + r^2 + c
-    return (tn.x - tl.y) + b;                            // + 2 n ln 2 - 2 ln c (leading part)
+    return fixed45_to_double(nm) + b;
 }
 
 // 1/sqrt(x) for 2^-100 < x < 2^100, refined in single precision carried as a float pair:
 // x = xh + xl (both taken from the bits of x), y0 = rsqrtf(xh), r = 1 - x y0^2 evaluated
-// with error-free products, y = y0 (1 + r/2 + 3r^2/8) ~ 1/sqrt(x) to about 2^-45.
-// Returned as a double (one FP64 add).
-__device__ __forceinline__ double rsqrt_seed(double x) {
+// with error-free products, y = y0 + yl = y0 (1 + r/2 + 3r^2/8) ~ 1/sqrt(x) to about 2^-45.
+struct RsqrtPair {
+    float xh, xl, y0, yl;
+};
+
+__device__ __forceinline__ RsqrtPair rsqrt_pair(double x) {
     const uint64_t b = (uint64_t)__double_as_longlong(x);
     const int E = (int)((b >> 52) & 0x7FF);
     const float xh = __uint_as_float(((uint32_t)(E - 896) << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
@@ -136,20 +176,31 @@ __device__ __forceinline__ double rsqrt_seed(double x) {
     const float Pe = fmaf(xh, p, -P);        // xh p = P + Pe exactly
     const float r = ((1.0f - P) - Pe) - fmaf(xh, q, xl * p);
     const float yl = y0 * (r * fmaf(0.375f, r, 0.5f));
-    return f2d_bits(y0) + f2d_bits(yl);
+    return RsqrtPair{xh, xl, y0, yl};
+}
+
+// The refined 1/sqrt(x) as a double (one FP64 add).
+__device__ __forceinline__ double rsqrt_seed(double x) {
+    const RsqrtPair p = rsqrt_pair(x);
+    return f2d_bits(p.y0) + f2d_bits(p.yl);
 }
 
 __device__ __forceinline__ double half_of(double y) {  // y / 2 for normal y, from the bits
     return __longlong_as_double(__double_as_longlong(y) - (1ll << 52));
 }
 
-// sqrt(x), 2^-100 < x < 2^100: one FP64 Goldschmidt step from the refined seed -- four
-// FP64 instructions, about one ulp.
+// sqrt(x), 2^-100 < x < 2^100: s = x (y0 + yl) as a float pair (xh y0 = S + Se exactly,
+// the cross terms in single precision; about 2^-44), then one Newton step in FP64,
+// sqrt(x) = s + (x - s^2) y0/2, the residual x - s^2 from one FMA -- three FP64
+// instructions, within half an ulp but for the last rounding.
 __device__ __forceinline__ double sqrt_pos(double x) {
-    const double y = rsqrt_seed(x);
-    const double s = x * y;
-    const double e = fma(-s, half_of(y), 0.5);
-    return fma(s, e, s);
+    const RsqrtPair p = rsqrt_pair(x);
+    const float S = p.xh * p.y0;
+    const float Se = fmaf(p.xh, p.y0, -S);
+    const float sl = Se + fmaf(p.xh, p.yl, p.xl * p.y0);
+    const double s = f2d_bits(S) + f2d_bits(sl);
+    const double e = fma(-s, s, x);
+    return fma(e, f2d_bits(0.5f * p.y0), s);
 }
 
 // 1/sqrt(x), 2^-100 < x < 2^100: one FP64 Newton step from the refined seed -- four FP64
@@ -200,6 +251,17 @@ __device__ __forceinline__ TurnSplit split_turn(uint32_t w) {
     return s;
 }
 
+// 1 - p/2 for 0 <= p < 2^-20 from the bits of p: 2^53 (1 - p/2) = 2^53 - P 2^(e+29) for
+// p = P 2^(e-23) (P the 24-bit significand), exact for e >= -29, rounded to nearest below.
+__device__ __forceinline__ double one_minus_half(float p) {
+    const uint32_t pb = __float_as_uint(p);
+    const int sh = (int)(pb >> 23) - 127 + 29;                 // e + 29 <= 8
+    const uint32_t P = pb ? ((pb & 0x7FFFFFu) | 0x800000u) : 0u;
+    const int k = -sh;                                         // right shift when > 0
+    const uint32_t v = sh >= 0 ? P << sh : (k < 32 ? (P + (1u << (k - 1))) >> k : 0u);
+    return __longlong_as_double((long long)(0x3FF0000000000000ull - (uint64_t)v));
+}
+
 // (sin, cos) of 2 pi j / 4096 from the first-octant table (pi m / 2048, m = 0..512):
 // reflect within the octant, swap sine and cosine, flip signs.
 __device__ __forceinline__ void octant_lookup(uint32_t j, const double2 *tab_trig, double &sa, double &ca) {
@@ -217,36 +279,37 @@ __device__ __forceinline__ void octant_lookup(uint32_t j, const double2 *tab_tri
 // sin(a + d) = cos a sin d + sin a cos d, cos(a + d) = cos a cos d - sin a sin d: the
 // FP64 parts are cos a dh, sin a (1 - p/2) and their cosine counterparts; the products of
 // the table values with the small float parts are formed in single precision (below
-// 1e-10 in size, so within 1e-17 absolute).  Five FP64 instructions for both outputs.
+// 1e-10 in size, so within 1e-17 absolute).  Four FP64 instructions for both outputs.
 __device__ __forceinline__ void sincos_turn(uint32_t w, const double2 *tab_trig, double &sv, double &cv) {
     const TurnSplit ts = split_turn(w);
     double sa, ca;
     octant_lookup(ts.j, tab_trig, sa, ca);
     const float saf = d2f_small(sa), caf = d2f_small(ca);
-    const double cd = fma(f2d_bits(ts.p), -0.5, 1.0);
+    const double cd = one_minus_half(ts.p);
     const double dh = f2d_bits(ts.dh);
     sv = fma(ca, dh, fma(sa, cd, f2d_bits(saf * ts.T + caf * ts.sdl)));
     cv = fma(-sa, dh, fma(ca, cd, f2d_bits(caf * ts.T - saf * ts.sdl)));
 }
 
-// cos(a + d) alone: three FP64 instructions.
+// cos(a + d) alone: two FP64 instructions.
 __device__ __forceinline__ double cos_turn(uint32_t w, const double2 *tab_trig) {
     const TurnSplit ts = split_turn(w);
     double sa, ca;
     octant_lookup(ts.j, tab_trig, sa, ca);
     const float saf = d2f_small(sa), caf = d2f_small(ca);
-    const double cd = fma(f2d_bits(ts.p), -0.5, 1.0);
+    const double cd = one_minus_half(ts.p);
     return fma(-sa, f2d_bits(ts.dh), fma(ca, cd, f2d_bits(caf * ts.T - saf * ts.sdl)));
 }
 
-// Three standard Gaussians of one Philox block (project transform, see the file header).
-__device__ __forceinline__ void box_muller3(const Philox4 &w, const double2 *tab_log, const double2 *tab_ln2,
-                                            const double2 *tab_trig, double &gx, double &gy, double &gz) {
-    const double r1 = sqrt_pos(neg2log_u(w.w0, tab_log, tab_ln2));
-    const double r2 = sqrt_pos(neg2log_u(w.w2, tab_log, tab_ln2));
+// Three standard Gaussians of one Philox block (project transform, see the file header):
+// 23 FP64 instructions.
+__device__ __forceinline__ void box_muller3(const Philox4 &w, const SmemTables &tab, double &gx, double &gy,
+                                            double &gz) {
+    const double r1 = sqrt_pos(neg2log_u(w.w0, tab));
+    const double r2 = sqrt_pos(neg2log_u(w.w2, tab));
     double s1, c1;
-    sincos_turn(w.w1, tab_trig, s1, c1);
-    const double c2 = cos_turn(w.w3, tab_trig);
+    sincos_turn(w.w1, tab.trig, s1, c1);
+    const double c2 = cos_turn(w.w3, tab.trig);
     gx = r1 * c1;
     gy = r1 * s1;
     gz = r2 * c2;

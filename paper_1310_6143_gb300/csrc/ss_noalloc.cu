@@ -27,7 +27,7 @@ namespace {
 constexpr int64_t kNaMax = SS_NOALLOC_MAX_SPINS;
 constexpr int kNaBlock = 256;
 constexpr int64_t kNaTiles = (kNaMax + kNaBlock - 1) / kNaBlock;
-constexpr size_t kNaTabCount = (size_t)kLogTab + kLn2Tab + kTrigTab;
+constexpr size_t kNaTabCount = (size_t)kTabCount;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Layout of the static array (byte offsets, each 256-byte aligned).
@@ -97,9 +97,7 @@ __device__ __forceinline__ void na_field(const NaArgs &a, int64_t i, const doubl
 __global__ void __launch_bounds__(kNaBlock) k_na_predictor(const NaArgs a) {
     __shared__ SmemTables tab;
     __shared__ double red[(kNaBlock / 32) * 8];
-    for (int i = threadIdx.x; i < kLogTab; i += kNaBlock) tab.log_[i] = a.tab[i];
-    for (int i = threadIdx.x; i < kLn2Tab; i += kNaBlock) tab.ln2[i] = a.tab[kLogTab + i];
-    for (int i = threadIdx.x; i < kTrigTab; i += kNaBlock) tab.trig[i] = a.tab[kLogTab + kLn2Tab + i];
+    stage_bm_tables(a.tab, tab);
     __syncthreads();
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int64_t i = (int64_t)blockIdx.x * kNaBlock + threadIdx.x;
@@ -112,7 +110,7 @@ __global__ void __launch_bounds__(kNaBlock) k_na_predictor(const NaArgs a) {
         if (a.sqrtT > 0.0) {
             const Philox4 w = philox4x32_10((uint32_t)i, a.step, a.ctr2, 0u, a.key0, a.key1);
             double g0, g1, g2;
-            box_muller3(w, tab.log_, tab.ln2, tab.trig, g0, g1, g2);
+            box_muller3(w, tab, g0, g1, g2);
             const double sig = sqrt(a.sig_num / (a.gamma * mu * a.dt)) * a.sqrtT;
             t0 = sig * g0;
             t1 = sig * g1;
@@ -193,26 +191,6 @@ __global__ void __launch_bounds__(kNaBlock) k_na_corrector(const NaArgs a) {
     a.sz[i] = v2 * inv;
 }
 
-// Box-Muller function tables, as the handle-based path builds them.
-void na_fill_tables(double2 *t) {
-    for (int i = 0; i < kLogTab; ++i) {
-        const long double c = (long double)(kLogFirst + i) / (long double)kLogScale;
-        const double inv = (double)(1.0L / c);
-        t[i] = make_double2(inv, (double)(-2.0L * logl((long double)inv)));
-    }
-    const long double ln2 = 0.693147180559945309417232121458176568L;
-    for (int i = 0; i < kLn2Tab; ++i) {
-        const long double v = 2.0L * (long double)i * ln2;
-        const double hi = (double)v;
-        t[kLogTab + i] = make_double2(hi, (double)(v - (long double)hi));
-    }
-    const long double twopi = 6.283185307179586476925286766559005768L;
-    for (int j = 0; j < kTrigTab; ++j) {
-        const long double a = twopi * (long double)j / 4096.0L;  // first octant of 4096 points
-        t[kLogTab + kLn2Tab + j] = make_double2((double)sinl(a), (double)cosl(a));
-    }
-}
-
 ss_status na_error(ss_status s, const char *msg) {
     set_global_error(msg);
     return s;
@@ -231,7 +209,7 @@ ss_status na_base(unsigned char **out) {
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return na_error(SS_ERR_CUDA, "cudaGetSymbolAddress(g_noalloc_scratch) failed");
         static double2 tab[kNaTabCount];
-        na_fill_tables(tab);
+        build_bm_tables(tab);
         e = cudaMemcpy((unsigned char *)p + kNaTabOff, tab, sizeof(tab), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return na_error(SS_ERR_CUDA, cudaGetErrorString(e));
         g_na_base[dev] = (unsigned char *)p;
