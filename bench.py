@@ -50,15 +50,15 @@ def step_bytes_per_spin(real_bytes, nnz_per_spin):
 
 
 # FP64 pipe instructions per spin of the FP32-mixed step kernels.  One thermal draw (the
-# table-driven FP64 Box-Muller) costs 29 FP64 instructions; the corrector draws a fraction
+# table-driven FP64 Box-Muller) costs 23 FP64 instructions; the corrector draws a fraction
 # f of them for the next step, the predictor the rest.  The FP64 moment/energy sums cost
 # 5 DADD per spin accumulated per thread over `spt` spins plus a 9-add warp butterfly.
-# For the default film shape (block 512, 8 spins per thread, f = 6/8) this gives 12.8 and
-# 21.75, the values ncu counts (profiles/k_predictor_film1024x1024x16_fp32.md,
+# For the default film shape (block 512, 8 spins per thread, f = 5/8) this gives 14.125
+# and 14.375, the values ncu counts (profiles/k_predictor_film1024x1024x16_fp32.md,
 # profiles/k_corrector_film1024x1024x16_fp32.md).  Each FP64 instruction (DADD, DMUL or
 # DFMA) takes one FMA slot of the pipe (2 slots per cycle per SM), so it counts as 2
 # flop-equivalents, the convention of the chip's FP64 rating.
-FP64_PER_DRAW = 29.0
+FP64_PER_DRAW = 23.0
 
 
 def fp64_inst_per_spin(kernel, block, tile, draw_ahead_eighths):
@@ -69,8 +69,10 @@ def fp64_inst_per_spin(kernel, block, tile, draw_ahead_eighths):
     return FP64_PER_DRAW * (1 - f) + 5.0 * (spt - 1) / spt + 9.0 / spt
 
 
-# DRAM bytes per launch of the default film shape, from the same ncu captures.
-KERNEL_DRAM_BYTES = {"k_predictor": 1.286e9 + 0.578e9, "k_corrector": 1.545e9 + 0.337e9}
+# DRAM bytes per launch of the default film shape (block, tile, draw-ahead eighths), from
+# the same ncu captures.
+DEFAULT_FILM_SHAPE = (512, 4096, 5)
+KERNEL_DRAM_BYTES = {"k_predictor": 1.257e9 + 0.577e9, "k_corrector": 1.539e9 + 0.314e9}
 SMS = 152
 NO_AUTOTUNE = False
 EXEC_NAMES = {0: "auto", 1: "kernels", 2: "graph", 3: "persistent", 4: "system_blocks"}
@@ -340,7 +342,7 @@ def main():
     inst = fp64_inst_per_spin(dom, info32["block"], info32["tile"], info32["draw_ahead"]) \
         if args.precision == "fp32" else None
     achieved = 2 * inst * lat.n / (dom_ms * 1e-3) / 1e12 if inst else None
-    default_shape = (info32["block"], info32["tile"], info32["draw_ahead"]) == (512, 4096, 6)
+    default_shape = (info32["block"], info32["tile"], info32["draw_ahead"]) == DEFAULT_FILM_SHAPE
     step_b = step_bytes_per_spin(4 if args.precision == "fp32" else 8, nnz_per)
     from paper_1310_6143_gb300.system import debug_fp64_rate
 
