@@ -61,19 +61,22 @@ cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, l
 
 // Box-Muller tables (layout in SmemTables), evaluated in long double.  The log and ln 2
 // constants are split as 2^-45 M + remainder with M an integer stored in the bits of a
-// double slot; the remainders of the log table are floats packed after the trig table.
+// double slot (so is the 21-bit reciprocal C); the remainders of the log table are floats
+// packed after the trig table.
 void build_bm_tables(double2 *t) {
     const long double q = 35184372088832.0L;  // 2^45
     float *lolog = reinterpret_cast<float *>(t + kLogTab + kLn2Tab + kTrigTab);
     for (int i = 0; i < 4 * kLogLo; ++i) lolog[i] = 0.0f;
     for (int i = 0; i < kLogTab; ++i) {
-        const long double c = (long double)(kLogFirst + i) / (long double)kLogScale;
-        const double inv = (double)(1.0L / c);
-        const long double T = -2.0L * logl((long double)inv);
+        // 1/c = kLogScale / j rounded to 21 bits: C 2^-20, C = round(2^20 kLogScale / j)
+        const long long j = kLogFirst + i;
+        const long long C = ((2ll << 20) * kLogScale / j + 1) / 2;
+        const long double T = -2.0L * logl((long double)C / 1048576.0L);
         const long long M = llroundl(T * q);
-        double mbits;
+        double cbits, mbits;
+        std::memcpy(&cbits, &C, sizeof(cbits));
         std::memcpy(&mbits, &M, sizeof(mbits));
-        t[i] = make_double2(inv, mbits);
+        t[i] = make_double2(cbits, mbits);
         lolog[i] = (float)(T - (long double)M / q);
     }
     const long double ln2 = 0.693147180559945309417232121458176568L;

@@ -13,8 +13,10 @@
 //   * -2 ln u by Tang's table-driven method (P. T. P. Tang, "Table-driven implementation
 //     of the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16, 1990):
 //     u = 2^-n f with f in [0.75, 1.5) taken exactly from the integer 2w+1; f is reduced
-//     against the nearest table centre c = k/2048 through r = f (1/c) - 1 (one FMA, so
-//     the table's rounded 1/c defines the split exactly), and
+//     against the nearest table centre c = k/2048 through r = f (1/c) - 1, where the
+//     table's 1/c is rounded to 21 bits so that the product of the integers behind f and
+//     1/c is exact in 64-bit integer arithmetic (r is then exact, and its double is
+//     assembled from the bits), and
 //     -2 ln u = 2 n ln 2 - 2 ln c - 2r + r^2 - r^3 (2/3 - r/2 + 2r^2/5) (Taylor series of
 //     2 log1p(r), |r| < 6.6e-4).  The r^3 tail is below 1.9e-10, so single precision
 //     evaluates it to an absolute 2e-17; the leading terms stay in FP64.  The tables hold
@@ -23,9 +25,9 @@
 //     from its bits (no FP64 instruction); the remainders join the single-precision tail.
 //     Near u = 1 (n = 0, c = 1, r exact) the result keeps its relative accuracy.
 //   * sqrt(x): 1/sqrt(x) refined to about 2^-45 in single precision with error-free float
-//     products, s = sqrt(x) from it as a float pair, then one Newton step in FP64,
-//     sqrt(x) = s + (x - s^2) / (2s), the residual from one FMA (the same seed serves the
-//     FP64 form's renormalisation, rsqrt_pos).
+//     products, s = sqrt(x) from it as a float pair whose double is assembled from the
+//     bits, then one Newton step in FP64, sqrt(x) = s + (x - s^2) / (2s), the residual
+//     from one FMA (the same seed serves the FP64 form's renormalisation, rsqrt_pos).
 //   * sin/cos of 2 pi t / 2^33 (t = 2w+1, an exact binary angle) by the nearest of 4096
 //     angles a (tabulated for one octant, the rest by exact symmetries) and the remainder
 //     d = 2 pi rho / 2^33, |d| <= pi/4096: sin(a+d) = cos a sin d + sin a cos d,
@@ -50,8 +52,8 @@ struct Philox4 {
 };
 
 // Shared-memory copy of the Box-Muller tables (build_bm_tables):
-//   log_[t] = (1/c_t rounded to double, M_t as int64 bits), M_t = round(2^45 T_t) with
-//             T_t = -2 ln(that rounded 1/c_t) = 2 ln c_t up to the rounding of 1/c_t;
+//   log_[t] = (C_t, M_t, both as int64 bits), C_t = round(2^20 / c_t) (1/c_t rounded to
+//             21 bits: 2^-20 C_t), M_t = round(2^45 T_t), T_t = -2 ln(2^-20 C_t);
 //   lolog[t] = T_t - 2^-45 M_t (|.| <= 2^-46);
 //   ln2[n] = (N_n as int64 bits, 2 n ln 2 - 2^-45 N_n), N_n = round(2^45 2 n ln 2);
 //   trig[m] = (sin, cos) of pi m / 2048.
@@ -121,15 +123,18 @@ __device__ __forceinline__ float d2f_small(double x) {
     return ex >= 897u ? d2f_bits(x) : 0.0f;
 }
 
-// m 2^-45 as a double for 0 <= m < 2^53 (exact), assembled from the integer bits.
-__device__ __forceinline__ double fixed45_to_double(uint64_t m) {
-    const int lz = __clzll((long long)m);                        // m in [2^(63-lz), 2^(64-lz))
-    const uint64_t mn = m << ((lz - 11) & 63);                   // leading one at bit 52
-    const uint64_t bits = ((uint64_t)(1023 + 18 - 1 - lz) << 52) + mn;  // exponent 18 - lz
-    return m ? __longlong_as_double((long long)bits) : 0.0;
+// v 2^-q as a double for |v| < 2^53 and 0 <= q <= 60 (exact), assembled from the integer
+// bits.
+__device__ __forceinline__ double fixed_to_double(int64_t v, int q) {
+    const uint64_t sign = (uint64_t)v & 0x8000000000000000ull;
+    const uint64_t a = v < 0 ? (uint64_t)(-v) : (uint64_t)v;
+    const int lz = __clzll((long long)a);                        // a in [2^(63-lz), 2^(64-lz))
+    const uint64_t mn = a << ((lz - 11) & 63);                   // leading one at bit 52
+    const uint64_t bits = sign | (((uint64_t)(1023 + 63 - lz - q - 1) << 52) + mn);
+    return a ? __longlong_as_double((long long)bits) : 0.0;
 }
 
-// -2 ln((w + 1/2) 2^-32) from the tables of SmemTables.  Four FP64 instructions.
+// -2 ln((w + 1/2) 2^-32) from the tables of SmemTables.  Three FP64 instructions.
 __device__ __forceinline__ double neg2log_u(uint32_t w, const SmemTables &tab) {
     const uint64_t m = 2ull * w + 1ull;              // u = m 2^-33, m odd, < 2^33
     const int lz = __clzll((long long)m);
@@ -137,14 +142,17 @@ __device__ __forceinline__ double neg2log_u(uint32_t w, const SmemTables &tab) {
     const uint64_t frac = (m << (52 - k)) & 0x000FFFFFFFFFFFFFull;  // f = 1.frac in [1, 2)
     const bool big = frac >= (1ull << 51);           // f >= 1.5: use f/2 and k + 1
     const int n = 33 - k - (big ? 1 : 0);            // u = 2^-n f'
-    const uint64_t ebits = big ? (1022ull << 52) : (1023ull << 52);
-    const double fp = __longlong_as_double((long long)(ebits | frac));    // f' in [0.75, 1.5)
+    const int K = k + (big ? 1 : 0);                 // f' = m 2^-K in [0.75, 1.5)
     // nearest centre c = j/2048: j = round(2048 f')
     const uint32_t j = big ? (uint32_t)(1024u + (uint32_t)((frac + (1ull << 41)) >> 42))
                            : (uint32_t)(2048u + (uint32_t)((frac + (1ull << 40)) >> 41));
     const double2 tl = tab.log_[j - (uint32_t)kLogFirst];
     const double2 tn = tab.ln2[n];
-    const double r = fma(fp, tl.x, -1.0);            // f'/c - 1 up to one rounding
+    // r = f' 2^-20 C - 1 = (m C - 2^(K+20)) 2^-(K+20): m < 2^33 and C < 2^21, so the
+    // integer product is exact; |r| < 3.3e-4
+    const uint64_t C = (uint64_t)__double_as_longlong(tl.x);
+    const int64_t Dr = (int64_t)(m * C) - (int64_t)(1ull << (K + 20));
+    const double r = fixed_to_double(Dr, K + 20);
     const float rf = d2f_small(r);
     const float tail = ((rf * rf) * rf) * fmaf(rf, fmaf(rf, 0.4f, -0.5f), 2.0f / 3.0f);
     // 2 n ln 2 - T = 2^-45 (N - M) + (remainders); N - M >= 0 (the result is positive
@@ -153,7 +161,7 @@ __device__ __forceinline__ double neg2log_u(uint32_t w, const SmemTables &tab) {
     const float lo = d2f_small(tn.y) - tab.lolog[j - (uint32_t)kLogFirst];
     const double c = f2d_bits(lo - tail);                // remainders minus the tail
     const double b = fma(-2.0, r, fma(r, r, c));         // -2r + r^2 + c
-    return fixed45_to_double(nm) + b;
+    return fixed_to_double((int64_t)nm, 45) + b;
 }
 
 // 1/sqrt(x) for 2^-100 < x < 2^100, refined in single precision carried as a float pair:
@@ -189,18 +197,29 @@ __device__ __forceinline__ double half_of(double y) {  // y / 2 for normal y, fr
     return __longlong_as_double(__double_as_longlong(y) - (1ll << 52));
 }
 
-// sqrt(x), 2^-100 < x < 2^100: s = x (y0 + yl) as a float pair (xh y0 = S + Se exactly,
-// the cross terms in single precision; about 2^-44), then one Newton step in FP64,
-// sqrt(x) = s + (x - s^2) y0/2, the residual x - s^2 from one FMA -- three FP64
-// instructions, within half an ulp but for the last rounding.
+// sqrt(x), 2^-100 < x < 2^100: s = x (y0 + yl) as a float pair S + sl (xh y0 = S + Se
+// exactly, the cross terms in single precision; about 2^-44), then one Newton step in
+// FP64, sqrt(x) = s + (x - s^2) h with h = (y0 + yl)/2 rounded to float, the residual
+// x - s^2 from one FMA -- two FP64 instructions, within half an ulp but for the last
+// rounding.  The double s is S + sl placed on the double grid of S from the bits (bits
+// of sl below that grid are dropped; just below a power of two the grid is twice as
+// fine): a start within about 2^-44, where the step needs 2^-30.
 __device__ __forceinline__ double sqrt_pos(double x) {
     const RsqrtPair p = rsqrt_pair(x);
     const float S = p.xh * p.y0;
     const float Se = fmaf(p.xh, p.y0, -S);
     const float sl = Se + fmaf(p.xh, p.yl, p.xl * p.y0);
-    const double s = f2d_bits(S) + f2d_bits(sl);
+    const uint64_t Sb = (uint64_t)__double_as_longlong(f2d_bits(S));
+    const uint32_t lb = __float_as_uint(sl);
+    const int el = (int)((lb >> 23) & 0xFFu);
+    const int sh = (el - 150) - ((int)(Sb >> 52) - 1075);     // sl = M 2^(el-150), grid 2^(eS-1075)
+    const uint32_t M = (lb & 0x7FFFFFu) | 0x800000u;
+    int64_t delta = sh >= 0 ? (int64_t)((uint64_t)M << (sh & 31)) : (sh > -32 ? (int64_t)(M >> (-sh)) : 0);
+    delta = el == 0 ? 0 : ((lb >> 31) ? -delta : delta);
+    if ((Sb & 0x000FFFFFFFFFFFFFull) == 0 && delta < 0) delta *= 2;
+    const double s = __longlong_as_double((long long)(Sb + (uint64_t)delta));
     const double e = fma(-s, s, x);
-    return fma(e, f2d_bits(0.5f * p.y0), s);
+    return fma(e, f2d_bits(0.5f * (p.y0 + p.yl)), s);
 }
 
 // 1/sqrt(x), 2^-100 < x < 2^100: one FP64 Newton step from the refined seed -- four FP64
@@ -302,7 +321,7 @@ __device__ __forceinline__ double cos_turn(uint32_t w, const double2 *tab_trig) 
 }
 
 // Three standard Gaussians of one Philox block (project transform, see the file header):
-// 23 FP64 instructions.
+// 19 FP64 instructions.
 __device__ __forceinline__ void box_muller3(const Philox4 &w, const SmemTables &tab, double &gx, double &gy,
                                             double &gz) {
     const double r1 = sqrt_pos(neg2log_u(w.w0, tab));
