@@ -203,14 +203,41 @@ __device__ __forceinline__ R sqrtT_of_step(const KArgs<R> &a, uint64_t step, con
     return f32 ? (R)a.sqrtT_sched_f[k] : (R)a.sqrtT_sched[k];
 }
 
-// Predictor over one tile.  Writes S', Q and H_th; returns the tile's partial sums
-// (valid in threads 0..7).
+// Tiles whose per-warp partial sums a block keeps in shared memory between two barriers.
+constexpr int kTileChunk = 8;
+
+// The warp's sums of eight per-thread values go to red[(q * warps + warp) * 8 + component]
+// (tile slot q of the block's current chunk).
+template <int BS>
+__device__ __forceinline__ void warp_partials(const double v[8], double *red, int q) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double x = warp_sum8(v);
+    if ((lane & 3) == 0) red[(q * (BS / 32) + warp) * 8 + warp_sum8_component(lane)] = x;
+}
+
+// After a barrier: the partial of chunk slot q is the sum of its warps' entries in warp
+// order (the order of block_sum8), written for tile t0 + q * stride.
+template <int BS>
+__device__ __forceinline__ void flush_partials(const double *red, int nq, double *partials, int64_t t0,
+                                               int64_t stride) {
+    if ((int)threadIdx.x < nq * 8) {
+        const int q = threadIdx.x >> 3, c = threadIdx.x & 7;
+        double r = 0.0;
+#pragma unroll 4
+        for (int w = 0; w < BS / 32; ++w) r += red[(q * (BS / 32) + w) * 8 + c];
+        partials[(t0 + q * stride) * kPartComps + c] = r;
+    }
+}
+
+// Predictor over one tile.  Writes S', Q and H_th; acc receives this thread's sums of the
+// per-spin reduction terms.
 template <typename R, int BS, bool Coherent>
-__device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
-                                                 const SmemTables &tab, double *red, int pre_slot) {
+__device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
+                                               const SmemTables &tab, int pre_slot, double (&acc)[8]) {
     const SysDesc &sd = a.sys[td.sys];
     const R sqrtT = sqrtT_of_step(a, step, sd);
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = 0.0;
     bool first = true;
     // The slot index is rotated by the warp index, so that the warps of a block reach their
     // FP64-heavy slots (the Gaussians not drawn ahead) at different times.
@@ -269,7 +296,6 @@ __device__ __forceinline__ double predictor_tile(const KArgs<R> &a, const TileDe
             for (int c = 0; c < 5; ++c) acc[c] += v[c];
         }
     }
-    return block_sum8<BS>(acc, red);
 }
 
 template <typename R, int BS, bool Coherent>
@@ -356,20 +382,37 @@ __device__ __forceinline__ void finalize_system(const SysDesc *sys, const int32_
 // Kernels
 // ----------------------------------------------------------------------------------
 
+// Predictor passes over the block's tiles t = blockIdx.x + j gridDim.x, in chunks of
+// kTileChunk tiles whose partials are summed after one barrier.
+template <typename R, int BS, bool Coherent>
+__device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step, const SmemTables &tab,
+                                               int pre_slot, double *red) {
+    const int64_t stride = gridDim.x;
+    for (int64_t t0 = blockIdx.x; t0 < a.ntiles; t0 += (int64_t)kTileChunk * stride) {
+        int nq = 0;
+        for (; nq < kTileChunk; ++nq) {
+            const int64_t t = t0 + nq * stride;
+            if (t >= a.ntiles) break;
+            double acc[8];
+            predictor_tile<R, BS, Coherent>(a, a.tiles[t], step, tab, pre_slot, acc);
+            warp_partials<BS>(acc, red, nq);
+        }
+        __syncthreads();
+        flush_partials<BS>(red, nq, a.partials, t0, stride);
+        __syncthreads();
+    }
+}
+
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_predictor(const KArgs<R> a) {
     __shared__ SmemTables tab;
-    __shared__ double red[(BS / 32) * 8];
+    __shared__ double red[kTileChunk * (BS / 32) * 8];
     stage_tables(a, tab);
     __syncthreads();
     const uint64_t step = *a.step;
     // Gaussians drawn ahead are valid only if the previous corrector ran for this step.
     const int pre_slot = (a.g_step != nullptr && *a.g_step == step) ? a.pre_slot : 1 << 30;
-    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-        const TileDesc td = a.tiles[t];
-        const double r = predictor_tile<R, BS, false>(a, td, step, tab, red, pre_slot);
-        if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
-    }
+    predictor_pass<R, BS, false>(a, step, tab, pre_slot, red);
 }
 
 // Blocks [0, nfin) sum the predictor's tile partials into the record ring; the rest run
@@ -414,7 +457,7 @@ __global__ void __launch_bounds__(BS) k_measure(const KArgs<R> a) {
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDesc td = a.tiles[t];
         const SysDesc &sd = a.sys[td.sys];
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // summed in the order of the step kernels
         for (int k = threadIdx.x; k < td.count; k += BS) {
             const int64_t i = td.start + k;
             const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
@@ -505,7 +548,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int *
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, long long nsteps) {
     __shared__ SmemTables tab;
-    __shared__ double red[(BS / 32) * 8];
+    __shared__ double red[kTileChunk * (BS / 32) * 8];
     stage_tables(a, tab);
     __syncthreads();
     const uint64_t step0 = __ldcg(a.step);
@@ -515,11 +558,7 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
     for (long long k = 0; k < nsteps; ++k) {
         const uint64_t step = step0 + (uint64_t)k;
         const int pre_slot = k == 0 ? pre_first : (ahead ? a.pre_slot : 1 << 30);
-        for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-            const TileDesc td = a.tiles[t];
-            const double r = predictor_tile<R, BS, true>(a, td, step, tab, red, pre_slot);
-            if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
-        }
+        predictor_pass<R, BS, true>(a, step, tab, pre_slot, red);
         if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
         if ((int)blockIdx.x < nfin) {
             for (int s = blockIdx.x; s < a.nsys; s += nfin) {
@@ -557,7 +596,9 @@ __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long lon
         whole.sys = s;
         for (long long k = 0; k < nsteps; ++k) {
             const uint64_t step = step0 + (uint64_t)k;
-            const double r = predictor_tile<R, BS, true>(a, whole, step, tab, red, 1 << 30);
+            double acc[8];
+            predictor_tile<R, BS, true>(a, whole, step, tab, 1 << 30, acc);
+            const double r = block_sum8<BS>(acc, red);
             write_record(sd, r, a.rec + ((int64_t)(step % (uint64_t)a.rec_cap) * a.nsys + s) * kRecComps);
             corrector_tile<R, BS, true>(a, whole, step, nullptr);
             __syncthreads();
