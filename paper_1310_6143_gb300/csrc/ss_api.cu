@@ -90,6 +90,8 @@ struct ss_system {
     void *ahead[3] = {};   // Gaussians drawn ahead by the corrector (FP32-mixed only)
     int pre_slot = 1 << 30;
     int ahead_q = 6;       // eighths of each tile drawn ahead by the corrector
+    bool J_uniform = false;  // every bond has the same J_ij / mu_s,i (J_value)
+    double J_value = 0.0;
     bool zero_T = true;    // some temperature in force could be zero (the corrector then
                            // skips drawing those spins ahead)
     SysDesc *sys = nullptr;
@@ -271,6 +273,8 @@ KArgs<R> make_args(const ss_system *h) {
     a.row_ptr = h->row_ptr;
     a.col = h->col;
     a.J = static_cast<const R *>(h->J);
+    a.J_value = (R)h->J_value;
+    a.J_uniform = h->J_uniform ? 1 : 0;
     a.mat = h->mat;
     a.mats = static_cast<const MatDesc<R> *>(h->mats);
     a.sys = h->sys;
@@ -612,6 +616,10 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     }
     rp[n] = (int32_t)nnz;
     h->nmat = (int32_t)mats.size();
+    // Homogeneous exchange (one J_ij / mu_s,i for every bond): the kernels skip the J loads.
+    h->J_uniform = nnz > 0;
+    for (int64_t k = 1; k < nnz && h->J_uniform; ++k) h->J_uniform = std::memcmp(&J[k], &J[0], sizeof(R)) == 0;
+    h->J_value = nnz > 0 ? (double)J[0] : 0.0;
     const size_t rs = sizeof(R);
     SS_CUDA(h, dalloc(h, (void **)&h->row_ptr, rp.size() * sizeof(int32_t)));
     SS_CUDA(h, dalloc(h, (void **)&h->col, col.size() * sizeof(int32_t)));

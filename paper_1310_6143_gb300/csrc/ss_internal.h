@@ -71,6 +71,8 @@ struct KArgs {
     const int32_t *row_ptr;   // [n+1]
     const int32_t *col;       // [nnz]
     const R *J;               // [nnz] J_ij / mu_s,i (the exchange field per unit spin, T)
+    R J_value;                // the common value when every entry of J is the same
+    int J_uniform;            // 1: J is not read, every bond has J_value
     const int32_t *mat;       // [n] material index
     const MatDesc<R> *mats;
     const SysDesc *sys;

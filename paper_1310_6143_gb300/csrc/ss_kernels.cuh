@@ -81,7 +81,7 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
     R x = sys_H(sd, 0, R()), y = sys_H(sd, 1, R()), z = sys_H(sd, 2, R());
     for (int32_t k = b; k < e; ++k) {
         const int32_t j = __ldg(a.col + k);
-        const R Jk = __ldg(a.J + k);
+        const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + k);
         x = fma(Jk, ld<Coherent>(X + j), x);
         y = fma(Jk, ld<Coherent>(Y + j), y);
         z = fma(Jk, ld<Coherent>(Z + j), z);
