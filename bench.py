@@ -49,16 +49,25 @@ def step_bytes_per_spin(real_bytes, nnz_per_spin):
     return 18 * real_bytes + 2 * (nnz_per_spin * (4 + real_bytes) + 4)
 
 
+# Bytes the implemented layout moves per spin-step: S, S', the half step Q and the stored
+# thermal field (24 words), the Gaussians drawn ahead (written and read back for a fraction
+# f of the spins), the CSR columns and row offsets once per pass, J once per pass unless
+# every bond has the same J_ij/mu_s,i, and the material index once per pass.
+def layout_bytes_per_spin(real_bytes, nnz_per_spin, f_ahead, j_uniform):
+    return (24 * real_bytes + 6 * real_bytes * f_ahead + 2 * (nnz_per_spin * 4 + 4)
+            + (0 if j_uniform else 2 * nnz_per_spin * real_bytes) + 8)
+
+
 # FP64 pipe instructions per spin of the FP32-mixed step kernels.  One thermal draw (the
-# table-driven FP64 Box-Muller) costs 23 FP64 instructions; the corrector draws a fraction
+# table-driven FP64 Box-Muller) costs 19 FP64 instructions; the corrector draws a fraction
 # f of them for the next step, the predictor the rest.  The FP64 moment/energy sums cost
 # 5 DADD per spin accumulated per thread over `spt` spins plus a 9-add warp butterfly.
-# For the default film shape (block 512, 8 spins per thread, f = 5/8) this gives 14.125
-# and 14.375, the values ncu counts (profiles/k_predictor_film1024x1024x16_fp32.md,
+# For the default film shape (block 512, 8 spins per thread, f = 4/8) this gives 15.0
+# and 9.5, the values ncu counts (profiles/k_predictor_film1024x1024x16_fp32.md,
 # profiles/k_corrector_film1024x1024x16_fp32.md).  Each FP64 instruction (DADD, DMUL or
 # DFMA) takes one FMA slot of the pipe (2 slots per cycle per SM), so it counts as 2
 # flop-equivalents, the convention of the chip's FP64 rating.
-FP64_PER_DRAW = 23.0
+FP64_PER_DRAW = 19.0
 
 
 def fp64_inst_per_spin(kernel, block, tile, draw_ahead_eighths):
@@ -71,8 +80,8 @@ def fp64_inst_per_spin(kernel, block, tile, draw_ahead_eighths):
 
 # DRAM bytes per launch of the default film shape (block, tile, draw-ahead eighths), from
 # the same ncu captures.
-DEFAULT_FILM_SHAPE = (512, 4096, 5)
-KERNEL_DRAM_BYTES = {"k_predictor": 1.257e9 + 0.577e9, "k_corrector": 1.539e9 + 0.314e9}
+DEFAULT_FILM_SHAPE = (512, 4096, 4)
+KERNEL_DRAM_BYTES = {"k_predictor": 0.842e9 + 0.568e9, "k_corrector": 1.150e9 + 0.286e9}
 SMS = 152
 NO_AUTOTUNE = False
 EXEC_NAMES = {0: "auto", 1: "kernels", 2: "graph", 3: "persistent", 4: "system_blocks"}
@@ -350,6 +359,11 @@ def main():
         f"{name}_inst_per_sm_cycle": debug_fp64_rate(m) / SMS / (sm_ghz * 1e9)
         for m, name in ((0, "dfma_shared_operands"), (1, "dfma_distinct_operands"), (2, "dadd"))}
     hbm_achieved = step_b * lat.n / (ms32 / args.steps * 1e-3) / 1e9
+    spt = info32["tile"] // info32["block"]
+    f_ahead = ((info32["draw_ahead"] * spt) // 8) / spt if args.precision == "fp32" else 0.0
+    j_rows = lat.J / np.repeat(lat.mu_s, np.diff(lat.row_ptr))
+    lay_b = layout_bytes_per_spin(4 if args.precision == "fp32" else 8, nnz_per, f_ahead,
+                                  bool(np.all(j_rows == j_rows[0])))
     out = {
         "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -371,6 +385,8 @@ def main():
                      "peak_source": f"152 SMs x 2 FP64 slots/cycle x 2 x {sm_ghz:.3f} GHz (measured clock)",
                      "measured_fp64_rate": fp64_meas},
         "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                         "layout_bytes_per_spin_step": lay_b,
+                         "layout_frac": lay_b * lat.n / (ms32 / args.steps * 1e-3) / 1e9 / hbm_peak,
                          "per_unit": f"{step_b:.1f} B per spin-step (whole step)", "peak_source": peak_src},
         "kernels_ms": kt32, "clocks": clk32,
         "e2e": {"value": world * lat.n / e2e32, "unit": "spin-steps/s", "h2d_bytes_per_step": 8,

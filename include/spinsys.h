@@ -208,7 +208,7 @@ ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
 /* FP32-mixed form: the corrector of step n draws the thermal Gaussians of step n+1 for
  * `eighths`/8 of each tile's spins (rounded down to whole blocks), so that their FP64
  * transform overlaps the corrector's memory traffic; the predictor draws the rest.
- * 0..8; the default is 5 when the default tile gives each thread 8 spins, else 6.
+ * 0..8; the default is 4 when the default tile gives each thread 8 spins, else 6.
  * Results do not depend on it (the same Gaussians are drawn). */
 ss_status spin_system_set_draw_ahead(ss_system *h, int32_t eighths);
 

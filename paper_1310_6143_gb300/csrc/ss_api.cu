@@ -782,7 +782,7 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         int slots = 1;
         while (slots < 8 && 2 * slots <= spt) slots *= 2;
         h->tile = slots * h->block;
-        h->ahead_q = slots >= 8 ? 5 : 6;  // the faster split on GB300 for each case
+        h->ahead_q = slots >= 8 ? 4 : 6;  // the faster split on GB300 for each case
     }
     st = build_tiles(h);
     if (st != SS_OK) return cleanup(st);
