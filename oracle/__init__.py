@@ -1,4 +1,5 @@
-"""FP64 CPU oracle of the stochastic Heun-LLG step (test infrastructure only).
+"""FP64 CPU oracle of the stochastic Heun-LLG step and of the Hinzke-Nowak Monte Carlo
+step (test infrastructure only).
 
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this package.  The product package never imports it, and the oracle shares
@@ -18,4 +19,7 @@ from .oracle import (  # noqa: F401
     heun_run,
     set_threads,
     max_threads,
+    colour_greedy,
+    mc_sigma_g,
+    mc_run,
 )

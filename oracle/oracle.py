@@ -80,6 +80,13 @@ def _load():
             lib.orc_philox_bulk.argtypes = [P, P, ctypes.c_int64, P]
             lib.orc_gaussians_bulk.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                                ctypes.c_int64, P]
+            lib.orc_colour_greedy.argtypes = [ctypes.POINTER(_CSys), P]
+            lib.orc_colour_greedy.restype = ctypes.c_int
+            lib.orc_mc_sigma_g.argtypes = [ctypes.c_double]
+            lib.orc_mc_sigma_g.restype = ctypes.c_double
+            lib.orc_mc_run.argtypes = [ctypes.POINTER(_CSys), P, ctypes.c_int64, ctypes.c_int64, P, P,
+                                       ctypes.c_int32, P, P]
+            lib.orc_mc_run.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -223,3 +230,37 @@ def heun_run(system: OracleSystem, S: np.ndarray, nsteps: int, T, step0: int = 0
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
     return S, rec
+
+
+def colour_greedy(system: OracleSystem):
+    """Greedy colouring of the neighbour graph in site order -> (colour[n] int32, ncolours)."""
+    colour = np.zeros(system.n, dtype=np.int32)
+    c = system._c()
+    nc = _load().orc_colour_greedy(ctypes.byref(c), _ptr(colour))
+    if nc < 0:
+        raise MemoryError("oracle: allocation failed")
+    return colour, int(nc)
+
+
+def mc_sigma_g(T: float) -> float:
+    """Width of the Gaussian trial cone at temperature T (Eq. MCgaussianSigma)."""
+    return float(_load().orc_mc_sigma_g(float(T)))
+
+
+def mc_run(system: OracleSystem, S: np.ndarray, nsteps: int, T, step0: int = 0, record: bool = False):
+    """Advance ``nsteps`` Hinzke-Nowak Monte Carlo steps; returns (S_new, rec or None, accepted).
+
+    ``T`` is a scalar temperature (K) or an array of ``nsteps`` temperatures; ``accepted``
+    holds the accepted trial moves of each step (one trial per spin per step).
+    """
+    S = np.array(S, dtype=np.float64, copy=True).reshape(system.n, 3)
+    Tarr = np.ascontiguousarray(np.broadcast_to(np.asarray(T, dtype=np.float64), (nsteps,)))
+    colour, nc = colour_greedy(system)
+    rec = np.zeros((nsteps, 8)) if record else None
+    acc = np.zeros(nsteps, dtype=np.int64)
+    c = system._c()
+    rc = _load().orc_mc_run(ctypes.byref(c), _ptr(S), int(step0), int(nsteps), _ptr(Tarr), _ptr(colour), nc,
+                            _ptr(rec), _ptr(acc))
+    if rc != 0:
+        raise MemoryError("oracle: allocation failed")
+    return S, rec, acc

@@ -41,6 +41,27 @@
  *   R7  Magnetisation is sum_i mu_s,i S_i (and sum_i mu_s,i); the per-step record holds
  *       the state at the start of the step, S(t_n).
  *
+ * Monte Carlo (Section "Monte Carlo Methods": the Metropolis criterion, Eq. AMCP, with
+ * the Hinzke-Nowak trial moves: spin flip, Gaussian move Eq. MCgaussian with the cone
+ * width Eq. MCgaussianSigma, random move Eq. MCrandom), readings:
+ *   M1  One Monte Carlo step gives every spin exactly one trial move, colour class by
+ *       colour class of a proper colouring of the neighbour graph (no two neighbours share
+ *       a colour), colours in increasing order, the spins of one colour in site order (they
+ *       do not interact, so their order does not change the result).  The colouring is
+ *       greedy in site order: each site takes the smallest colour no earlier neighbour
+ *       holds.  (The paper picks N random sites per step; every single-spin Metropolis
+ *       update keeps the Boltzmann distribution invariant either way.)
+ *   M2  Random numbers per (spin i, Monte Carlo step n): Philox block A with counter
+ *       (i, n, system, 2) gives the Gaussian triple Gamma by the Box-Muller transform of R6;
+ *       block B with counter (i, n, system, 3) gives the move type from its first word w0,
+ *       floor(3 w0 / 2^32) (0 spin flip, 1 Gaussian, 2 random), and the acceptance uniform
+ *       u = (w1 + 1/2) 2^-32 from its second word.
+ *   M3  A move is accepted when dE <= -kB T ln u, i.e. u <= exp(-dE/(kB T)) (Eq. AMCP);
+ *       energy-lowering moves are always accepted; at T = 0 exactly the moves with dE <= 0.
+ *   M4  The energy change is that of site i's terms of the Hamiltonian: exchange with its
+ *       neighbours, its anisotropy, its applied-field term and its Neel term.
+ *   M5  The record of Monte Carlo step n holds the state at the start of the step.
+ *
  * Layout: spins and vectors are array-of-structures, 3 doubles per site (x, y, z).
  * Neel tensors are 6 doubles per site in the order xx, yy, zz, xy, xz, yz.
  *
@@ -60,6 +81,7 @@
 #define ORC_KB 1.3807e-23      /* Boltzmann constant, J/K (Table I) */
 #define ORC_GAMMA 1.76e11      /* gyromagnetic ratio, 1/(T s) (Table I) */
 #define ORC_PI 3.14159265358979323846
+#define ORC_MUB 9.2740e-24     /* Bohr magneton, J/T (Table I) */
 
 typedef struct {
     int64_t n;                /* number of spins                                  */
@@ -345,4 +367,163 @@ void orc_philox_bulk(const uint32_t ctr0[4], const uint32_t key[2], int64_t coun
 
 void orc_gaussians_bulk(uint64_t seed, uint32_t sys, uint32_t step, int64_t n, double *g) {
     for (int64_t i = 0; i < n; ++i) orc_thermal_gaussians(seed, sys, (uint32_t)i, step, g + 3 * i);
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Monte Carlo (Section "Monte Carlo Methods"), readings M1-M5 in the file header.     */
+/* ---------------------------------------------------------------------------------- */
+
+/* Greedy colouring in site order (M1).  colour[i] receives the colour of site i; the
+ * return value is the number of colours, or -1 if memory could not be allocated. */
+int orc_colour_greedy(const orc_system *s, int32_t *colour) {
+    int64_t n = s->n;
+    int32_t ncol = 0;
+    int32_t cap = 64;
+    int64_t *seen = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    if (!seen) return -1;
+    for (int32_t c = 0; c < cap; ++c) seen[c] = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        /* mark the colours of the neighbours coloured before i */
+        for (int64_t k = s->row_ptr[i]; k < s->row_ptr[i + 1]; ++k) {
+            int64_t j = s->col[k];
+            if (j < i) {
+                int32_t c = colour[j];
+                if (c >= cap) {
+                    int32_t ncap = 2 * c + 2;
+                    int64_t *m = (int64_t *)realloc(seen, sizeof(int64_t) * (size_t)ncap);
+                    if (!m) {
+                        free(seen);
+                        return -1;
+                    }
+                    seen = m;
+                    for (int32_t q = cap; q < ncap; ++q) seen[q] = -1;
+                    cap = ncap;
+                }
+                seen[c] = i;
+            }
+        }
+        int32_t c = 0;
+        while (c < cap && seen[c] == i) ++c;
+        if (c == cap) {
+            int32_t ncap = 2 * cap;
+            int64_t *m = (int64_t *)realloc(seen, sizeof(int64_t) * (size_t)ncap);
+            if (!m) {
+                free(seen);
+                return -1;
+            }
+            seen = m;
+            for (int32_t q = cap; q < ncap; ++q) seen[q] = -1;
+            cap = ncap;
+        }
+        colour[i] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(seen);
+    return ncol;
+}
+
+/* Width of the Gaussian trial cone, Eq. MCgaussianSigma. */
+double orc_mc_sigma_g(double T) { return 2.0 / 25.0 * pow(ORC_KB * T / ORC_MUB, 0.2); }
+
+/* Energy of site i's terms of the Hamiltonian with its spin set to X (M4):
+ * -sum_j J_ij X.S_j - k_u (X.e)^2 - mu_s X.H_app - X^T K X. */
+static double orc_site_energy(const orc_system *s, const double *S, int64_t i, const double X[3]) {
+    double hx = 0.0, hy = 0.0, hz = 0.0;
+    for (int64_t k = s->row_ptr[i]; k < s->row_ptr[i + 1]; ++k) {
+        int64_t j = s->col[k];
+        hx += s->J[k] * S[3 * j + 0];
+        hy += s->J[k] * S[3 * j + 1];
+        hz += s->J[k] * S[3 * j + 2];
+    }
+    double e = -(X[0] * hx + X[1] * hy + X[2] * hz);
+    const double *a = s->easy_axis + 3 * i;
+    double xe = X[0] * a[0] + X[1] * a[1] + X[2] * a[2];
+    e += -s->k_u[i] * xe * xe;
+    e += -s->mu_s[i] * (X[0] * s->H_app[0] + X[1] * s->H_app[1] + X[2] * s->H_app[2]);
+    if (s->K_neel) {
+        const double *K = s->K_neel + 6 * i;
+        double q = K[0] * X[0] * X[0] + K[1] * X[1] * X[1] + K[2] * X[2] * X[2]
+                 + 2.0 * (K[3] * X[0] * X[1] + K[4] * X[0] * X[2] + K[5] * X[1] * X[2]);
+        e += -q;
+    }
+    return e;
+}
+
+/* One Hinzke-Nowak trial move of site i at Monte Carlo step n and temperature T
+ * (Eqs. AMCP, MCgaussian, MCrandom; readings M2-M4).  Returns 1 if accepted. */
+static int orc_mc_trial(const orc_system *s, double *S, int64_t i, uint32_t n, double T, double sigma_g) {
+    uint32_t spin = s->ids ? s->ids[i] : (uint32_t)i;
+    uint32_t key[2] = {(uint32_t)(s->seed & 0xFFFFFFFFu), (uint32_t)(s->seed >> 32)};
+    uint32_t ca[4] = {spin, n, s->sys, 2u}, cb[4] = {spin, n, s->sys, 3u};
+    uint32_t wa[4], wb[4];
+    orc_philox4x32_10(ca, key, wa);
+    orc_philox4x32_10(cb, key, wb);
+    double g[3];
+    orc_box_muller3(wa, g);
+    int move = (int)(((uint64_t)wb[0] * 3u) >> 32);
+    double u = orc_uniform(wb[1]);
+    const double *Si = S + 3 * i;
+    double Sn[3];
+    if (move == 0) {            /* spin flip */
+        Sn[0] = -Si[0];
+        Sn[1] = -Si[1];
+        Sn[2] = -Si[2];
+    } else if (move == 1) {     /* Gaussian move, Eq. MCgaussian */
+        Sn[0] = Si[0] + sigma_g * g[0];
+        Sn[1] = Si[1] + sigma_g * g[1];
+        Sn[2] = Si[2] + sigma_g * g[2];
+        orc_normalise(Sn);
+    } else {                    /* random move, Eq. MCrandom */
+        Sn[0] = g[0];
+        Sn[1] = g[1];
+        Sn[2] = g[2];
+        orc_normalise(Sn);
+    }
+    double dE = orc_site_energy(s, S, i, Sn) - orc_site_energy(s, S, i, Si);
+    int accept = T > 0.0 ? (dE <= -ORC_KB * T * log(u)) : (dE <= 0.0);
+    if (accept) {
+        S[3 * i + 0] = Sn[0];
+        S[3 * i + 1] = Sn[1];
+        S[3 * i + 2] = Sn[2];
+    }
+    return accept;
+}
+
+/*
+ * Advance nsteps Monte Carlo steps from step index step0 (M1-M5).  colour[i] and ncol
+ * come from orc_colour_greedy.  T[k] is the temperature of step step0+k (K).  If rec is
+ * not NULL it receives orc_moment_energy of the state at the start of each step; if
+ * accepted is not NULL it receives the accepted trial moves of each step.  Returns 0, or
+ * -1 if memory could not be allocated.
+ */
+int orc_mc_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, const double *T,
+               const int32_t *colour, int32_t ncol, double *rec, int64_t *accepted) {
+    int64_t n = s->n;
+    /* the sites of each colour, in site order */
+    int64_t *start = (int64_t *)calloc((size_t)ncol + 1, sizeof(int64_t));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *fill = (int64_t *)calloc((size_t)ncol + 1, sizeof(int64_t));
+    if (!start || !order || !fill) {
+        free(start); free(order); free(fill);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i) start[colour[i] + 1]++;
+    for (int32_t c = 0; c < ncol; ++c) start[c + 1] += start[c];
+    for (int64_t i = 0; i < n; ++i) order[start[colour[i]] + fill[colour[i]]++] = i;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        uint32_t step = (uint32_t)(step0 + k);
+        double Tn = T[k];
+        double sg = orc_mc_sigma_g(Tn);
+        if (rec) orc_moment_energy(s, S, rec + 8 * k);
+        int64_t acc = 0;
+        for (int32_t c = 0; c < ncol; ++c) {
+            /* sites of one colour have no bonds between them: each trial reads only spins of
+               other colours, so the loop may run on several threads */
+#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(+ : acc)
+            for (int64_t q = start[c]; q < start[c + 1]; ++q) acc += orc_mc_trial(s, S, order[q], step, Tn, sg);
+        }
+        if (accepted) accepted[k] = acc;
+    }
+    free(start); free(order); free(fill);
+    return 0;
 }

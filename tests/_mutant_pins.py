@@ -142,8 +142,100 @@ def pin_curie():
     return 0.6 < ms[312.5] < 0.92 and ms[937.5] < 0.3
 
 
+def _free(n, k_u=0.0):
+    return np.zeros(n + 1, dtype=np.int64), np.zeros(0, np.int32), np.zeros(0), np.full(n, MU), np.full(n, k_u)
+
+
+def _mc_average(s, S, T, equil, blocks, per, f):
+    S, _, _ = O.mc_run(s, S, equil, T)
+    vals, step = [], equil
+    for _ in range(blocks):
+        S, _, _ = O.mc_run(s, S, per, T, step0=step)
+        step += per
+        vals.append(f(S))
+    return np.concatenate(vals).mean()
+
+
+def _langevin(x):
+    return 1.0 / math.tanh(x) - 1.0 / x
+
+
+def pin_mc_boltzmann():
+    """Eq. boltz with Monte Carlo: <cos^2> of free spins with anisotropy, k_u/(kB T) = 3."""
+    n, T, kappa = 2000, 50.0, 3.0
+    rp, col, J, mu, ku = _free(n, kappa * KB * T)
+    s = O.OracleSystem(rp, col, J, mu, ku, (0, 0, 1), seed=3)
+    m2 = _mc_average(s, L.uniform_state(n), T, 60, 15, 5, lambda S: S[:, 2] ** 2)
+    from scipy import integrate
+    Z = integrate.quad(lambda x: np.exp(kappa * x * x), 0, 1)[0]
+    return abs(m2 - integrate.quad(lambda x: x * x * np.exp(kappa * x * x), 0, 1)[0] / Z) < 0.015
+
+
+def pin_mc_langevin():
+    n, T, x = 2000, 100.0, 2.0
+    rp, col, J, mu, ku = _free(n)
+    H = x * KB * T / MU
+    s = O.OracleSystem(rp, col, J, mu, ku, (0, 0, 1), H_app=(0.0, 0.0, H), seed=8)
+    return abs(_mc_average(s, L.random_state(n, 2), T, 40, 15, 4, lambda S: S[:, 2]) - _langevin(x)) < 0.015
+
+
+def pin_mc_dimer():
+    npairs, T, K = 1500, 100.0, 1.5
+    n = 2 * npairs
+    s = O.OracleSystem(np.arange(n + 1, dtype=np.int64), (np.arange(n) ^ 1).astype(np.int32), np.full(n, K * KB * T),
+                       np.full(n, MU), np.zeros(n), (0, 0, 1), seed=13)
+    got = _mc_average(s, L.random_state(n, 4), T, 40, 15, 4, lambda S: np.einsum("ij,ij->i", S[0::2], S[1::2]))
+    return abs(got - _langevin(K)) < 0.02
+
+
+def pin_mc_moves():
+    """One step of free spins (all moves accepted): a third flips, unit lengths, the
+    Gaussian moves inside a cone of a few sigma_g (Eq. MCgaussianSigma), the rest uniform."""
+    n, T = 12000, 10.0
+    rp, col, J, mu, ku = _free(n)
+    s = O.OracleSystem(rp, col, J, mu, ku, (0, 0, 1), seed=21)
+    S0 = L.random_state(n, 5)
+    S1, _, acc = O.mc_run(s, S0, 1, T)
+    if acc[0] != n or np.abs(np.linalg.norm(S1, axis=1) - 1).max() > 1e-14:
+        return False
+    dot = np.einsum("ij,ij->i", S0, S1)
+    flip = np.all(S1 == -S0, axis=1)
+    sg = 0.08 * (KB * T / 9.2740e-24) ** 0.2
+    near = (~flip) & (dot > math.cos(5 * sg))
+    c = math.cos(5 * sg)
+    far = dot[~(flip | near)]
+    third = n / 3
+    return (abs(flip.sum() - third) < 5 * math.sqrt(n * 2 / 9)
+            and abs(near.sum() - third * (1 + (1 - c) / 2)) < 5 * math.sqrt(n * 2 / 9) + 10
+            and abs(far.mean() - (c - 1) / 2) < 0.03 and 0.5 * sg ** 2 < (1 - dot[near]).mean() < 1.5 * sg ** 2)
+
+
+def pin_mc_sigma():
+    return abs(O.mc_sigma_g(320.0) / O.mc_sigma_g(10.0) - 2.0) < 1e-12
+
+
+def pin_mc_zero_T():
+    """T = 0: no step raises the energy; the record holds the state before each step."""
+    lat = L.simple_cubic(6, 6, 6, J=6e-21, k_u=1e-23)
+    s = O.OracleSystem(lat.row_ptr, lat.col, lat.J, lat.mu_s, lat.k_u, lat.easy_axis, H_app=(0, 0.3, 0.5), seed=2)
+    S0 = L.random_state(lat.n, 7)
+    _, rec, _ = O.mc_run(s, S0, 5, 0.0, record=True)
+    return np.all(np.diff(rec[:, 7]) <= 1e-30) and np.allclose(rec[0], O.moment_energy(s, S0), rtol=0, atol=0)
+
+
+def pin_colouring():
+    for lat in (L.simple_cubic(5, 5, 5), L.fcc(3, 3, 3)):
+        s = O.OracleSystem(lat.row_ptr, lat.col, lat.J, lat.mu_s, lat.k_u, lat.easy_axis)
+        colour, nc = O.colour_greedy(s)
+        rows = np.repeat(np.arange(lat.n), np.diff(lat.row_ptr))
+        if np.any(colour[rows] == colour[lat.col]) or colour.max() != nc - 1:
+            return False
+    return True
+
+
 PINS = [pin_field_gradient, pin_single_spin_analytic, pin_unit_length, pin_gaussians, pin_philox_against_torch,
-        pin_boltzmann, pin_curie]
+        pin_boltzmann, pin_curie, pin_mc_boltzmann, pin_mc_langevin, pin_mc_dimer, pin_mc_moves, pin_mc_sigma,
+        pin_mc_zero_T, pin_colouring]
 
 if __name__ == "__main__":
     for p in PINS:

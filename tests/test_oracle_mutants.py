@@ -37,6 +37,22 @@ MUTANTS = [
     ("Philox key not advanced", "            k0 += 0x9E3779B9u;", ""),
     ("Philox multipliers swapped", "uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;",
      "uint64_t p0 = (uint64_t)0xCD9E8D57u * (uint64_t)x0;"),
+    # Monte Carlo
+    ("Metropolis test with the wrong sign", "(dE <= -ORC_KB * T * log(u))", "(dE <= ORC_KB * T * log(u))"),
+    ("Metropolis test without kB", "(dE <= -ORC_KB * T * log(u))", "(dE <= -T * log(u))"),
+    ("exchange counted twice in the energy change", "    double e = -(X[0] * hx + X[1] * hy + X[2] * hz);",
+     "    double e = -2.0 * (X[0] * hx + X[1] * hy + X[2] * hz);"),
+    ("anisotropy energy with the wrong sign", "    e += -s->k_u[i] * xe * xe;", "    e += s->k_u[i] * xe * xe;"),
+    ("applied-field energy without the moment",
+     "    e += -s->mu_s[i] * (X[0] * s->H_app[0] + X[1] * s->H_app[1] + X[2] * s->H_app[2]);",
+     "    e += -(X[0] * s->H_app[0] + X[1] * s->H_app[1] + X[2] * s->H_app[2]);"),
+    ("Gaussian move not renormalised", "        Sn[2] = Si[2] + sigma_g * g[2];\n        orc_normalise(Sn);",
+     "        Sn[2] = Si[2] + sigma_g * g[2];"),
+    ("every move a Gaussian move", "    int move = (int)(((uint64_t)wb[0] * 3u) >> 32);", "    int move = 1;"),
+    ("cone width with exponent 1/4", "pow(ORC_KB * T / ORC_MUB, 0.2)", "pow(ORC_KB * T / ORC_MUB, 0.25)"),
+    ("colouring ignores the neighbours", "        while (c < cap && seen[c] == i) ++c;", "        c = 0;"),
+    ("record taken after the step", "        if (rec) orc_moment_energy(s, S, rec + 8 * k);\n        int64_t acc = 0;",
+     "        int64_t acc = 0;"),
 ]
 
 
