@@ -58,6 +58,8 @@
  *       u = (w1 + 1/2) 2^-32 from its second word.
  *   M3  A move is accepted when dE <= -kB T ln u, i.e. u <= exp(-dE/(kB T)) (Eq. AMCP);
  *       energy-lowering moves are always accepted; at T = 0 exactly the moves with dE <= 0.
+ *       At T = 0 the cone width is 0 and the Gaussian move leaves the spin exactly as it is
+ *       (dE = 0, counted as accepted) rather than renormalising it.
  *   M4  The energy change is that of site i's terms of the Hamiltonian: exchange with its
  *       neighbours, its anisotropy, its applied-field term and its Neel term.
  *   M5  The record of Monte Carlo step n holds the state at the start of the step.
@@ -468,6 +470,10 @@ static int orc_mc_trial(const orc_system *s, double *S, int64_t i, uint32_t n, d
         Sn[0] = -Si[0];
         Sn[1] = -Si[1];
         Sn[2] = -Si[2];
+    } else if (move == 1 && sigma_g == 0.0) {  /* T = 0: a cone of width 0 (M3) */
+        Sn[0] = Si[0];
+        Sn[1] = Si[1];
+        Sn[2] = Si[2];
     } else if (move == 1) {     /* Gaussian move, Eq. MCgaussian */
         Sn[0] = Si[0] + sigma_g * g[0];
         Sn[1] = Si[1] + sigma_g * g[1];
