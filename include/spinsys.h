@@ -171,6 +171,27 @@ ss_status set_temperature_schedule(ss_system *h, const double *T_per_step, int64
  * moment and energy of the state at its start into the per-step record ring. */
 ss_status llg_heun_step(ss_system *h, int64_t n);
 
+/* Advance every system by n >= 0 Monte Carlo steps (asynchronous; Section "Monte Carlo
+ * Methods": the Metropolis criterion Eq. AMCP with the Hinzke-Nowak mixture of spin-flip,
+ * Gaussian (Eq. MCgaussian, cone width Eq. MCgaussianSigma) and random (Eq. MCrandom)
+ * trial moves).  One Monte Carlo step gives every spin exactly one trial move, colour
+ * class by colour class of a greedy colouring of the neighbour graph (in site order: each
+ * site takes the smallest colour no lower-indexed neighbour holds), so that spins updated
+ * together share no bond.  Per (spin i, step n) the trial uses Philox blocks
+ * (i, n, system id, 2) for the Gaussian triple and (i, n, system id, 3) for the move type
+ * floor(3 w0 / 2^32) (0 flip, 1 Gaussian, 2 random) and the acceptance uniform
+ * u = (w1 + 1/2) 2^-32; a move is accepted when dE <= -kB T ln u (at T = 0 when dE <= 0),
+ * dE being the change of the spin's Hamiltonian terms.  Temperatures, the schedule, the
+ * step counter and the per-step record ring are shared with llg_heun_step: each Monte
+ * Carlo step advances the counter by one and records the moment and energy of the state
+ * at its start.  The first call builds the colouring (a copy of the neighbour list to the
+ * host, one int32 per spin of device memory).  SS_ERR_INVALID_ARG for n < 0. */
+ss_status mc_step(ss_system *h, int64_t n);
+
+/* Monte Carlo acceptance of system `sys` since the handle was created: out[0] accepted
+ * trial moves, out[1] attempted trial moves (synchronous). */
+ss_status get_mc_stats(ss_system *h, int32_t sys, int64_t out[2]);
+
 /* Copy all spins (concatenated over systems) to out3n [3n], AoS, FP64 (synchronous). */
 ss_status get_spins(ss_system *h, double *out3n);
 

@@ -104,6 +104,18 @@ struct ss_system {
 
     std::vector<SysDesc> hsys;
     std::vector<int64_t> sys_offset, sys_n;
+    std::vector<double> Tsys;     // temperature of each system when no schedule is set, K
+    std::vector<double> sched_T;  // the schedule's temperatures, K
+
+    // Monte Carlo state (built on the first mc_step)
+    int32_t *mc_order = nullptr;             // spins sorted by colour, then index
+    std::vector<int64_t> mc_cstart;          // colour class c is mc_order[mc_cstart[c] .. mc_cstart[c+1])
+    double2 *mc_par = nullptr;               // per system (-kB T, sigma_g)
+    double2 *mc_sched = nullptr;             // per schedule step (-kB T_k, sigma_g(T_k))
+    int64_t mc_sched_cap = 0;
+    bool mc_par_dirty = true;
+    unsigned long long *mc_acc = nullptr;    // accepted trial moves per system (device)
+    std::vector<int64_t> mc_tried;           // trial moves per system (host count)
 
     // launch state
     int nfin = 1;
@@ -736,6 +748,7 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         }
         d.sqrtT = std::sqrt(p->T);
         d.sqrtTf = (float)d.sqrtT;
+        h->Tsys.push_back(p->T);
         double ms = 0.0;
         for (int64_t i = 0; i < p->n; ++i) ms += p->mu_s[i];
         d.msum = ms;
@@ -849,6 +862,122 @@ ss_status time_kernels_impl(ss_system *h, int32_t nsteps, double out_ms[3]) {
     return check_device_flags(h);
 }
 
+// ----------------------------------------------------------------------------------
+// Monte Carlo (Section "Monte Carlo Methods")
+// ----------------------------------------------------------------------------------
+
+// Colour classes of the neighbour graph, built on the first Monte Carlo call: greedy in
+// site order (each site takes the smallest colour that no lower-indexed neighbour holds);
+// systems share no bonds, so over the concatenated batch this is each system's own
+// colouring.  The spins are listed by colour, in index order within a colour.
+ss_status mc_prepare(ss_system *h) {
+    if (h->mc_order) return SS_OK;
+    const int64_t n = h->n;
+    std::vector<int32_t> rp((size_t)n + 1), col((size_t)std::max<int64_t>(h->nnz, 1));
+    SS_CUDA(h, cudaMemcpyAsync(rp.data(), h->row_ptr, rp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               h->stream));
+    if (h->nnz > 0)
+        SS_CUDA(h, cudaMemcpyAsync(col.data(), h->col, (size_t)h->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                   h->stream));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    std::vector<int32_t> colour((size_t)n, 0);
+    std::vector<int64_t> taken;  // taken[c] == i: a lower-indexed neighbour of i holds colour c
+    int32_t ncol = n > 0 ? 1 : 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int64_t j = col[k];
+            if (j >= i) continue;
+            const int32_t cj = colour[j];
+            if (cj >= (int32_t)taken.size()) taken.resize((size_t)cj + 1, -1);
+            taken[cj] = i;
+        }
+        int32_t c = 0;
+        while (c < (int32_t)taken.size() && taken[c] == i) ++c;
+        colour[i] = c;
+        ncol = std::max(ncol, c + 1);
+    }
+    h->mc_cstart.assign((size_t)ncol + 1, 0);
+    for (int64_t i = 0; i < n; ++i) h->mc_cstart[colour[i] + 1]++;
+    for (int32_t c = 0; c < ncol; ++c) h->mc_cstart[c + 1] += h->mc_cstart[c];
+    std::vector<int32_t> order((size_t)std::max<int64_t>(n, 1));
+    std::vector<int64_t> fill(h->mc_cstart.begin(), h->mc_cstart.end() - 1);
+    for (int64_t i = 0; i < n; ++i) order[fill[colour[i]]++] = (int32_t)i;
+    int32_t *dorder = nullptr;
+    SS_CUDA(h, dalloc(h, (void **)&dorder, order.size() * sizeof(int32_t)));
+    SS_CUDA(h, cudaMemcpyAsync(dorder, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               h->stream));
+    SS_CUDA(h, dalloc(h, (void **)&h->mc_acc, (size_t)h->nsys * sizeof(unsigned long long)));
+    SS_CUDA(h, cudaMemsetAsync(h->mc_acc, 0, (size_t)h->nsys * sizeof(unsigned long long), h->stream));
+    SS_CUDA(h, dalloc(h, (void **)&h->mc_par, (size_t)h->nsys * sizeof(double2)));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->mc_order = dorder;
+    h->mc_tried.assign((size_t)h->nsys, 0);
+    h->mc_par_dirty = true;
+    return SS_OK;
+}
+
+// (-kB T, sigma_g) with the cone width of Eq. MCgaussianSigma, sigma_g = (2/25)(kB T/muB)^(1/5).
+double2 mc_params(double T) {
+    return make_double2(-kBoltzmann * T, 2.0 / 25.0 * std::pow(kBoltzmann * T / kBohrMagneton, 0.2));
+}
+
+ss_status mc_upload_params(ss_system *h) {
+    if (!h->mc_par_dirty) return SS_OK;
+    std::vector<double2> ps((size_t)h->nsys);
+    for (int s = 0; s < h->nsys; ++s) ps[s] = mc_params(h->Tsys[s]);
+    SS_CUDA(h, cudaMemcpyAsync(h->mc_par, ps.data(), ps.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                               h->stream));
+    if (h->sched_len > 0) {
+        if (h->sched_len > h->mc_sched_cap) {
+            SS_CUDA(h, cudaStreamSynchronize(h->stream));
+            if (h->mc_sched) dfree(h, h->mc_sched);
+            h->mc_sched = nullptr;
+            h->mc_sched_cap = 0;
+            SS_CUDA(h, dalloc(h, (void **)&h->mc_sched, (size_t)h->sched_len * sizeof(double2)));
+            h->mc_sched_cap = h->sched_len;
+        }
+        std::vector<double2> pk((size_t)h->sched_len);
+        for (int64_t k = 0; k < h->sched_len; ++k) pk[k] = mc_params(h->sched_T[k]);
+        SS_CUDA(h, cudaMemcpyAsync(h->mc_sched, pk.data(), pk.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                                   h->stream));
+    }
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->mc_par_dirty = false;
+    return SS_OK;
+}
+
+// Per Monte Carlo step: the record of the state at the start of the step (measure and
+// finalise into the ring), one launch per colour class, then the step counter advances.
+template <typename R>
+cudaError_t enqueue_mc(ss_system *h, int64_t nsteps) {
+    const KArgs<R> a = make_args<R>(h);
+    McArgs m{};
+    m.order = h->mc_order;
+    m.par_sys = h->mc_par;
+    m.par_sched = h->mc_sched;
+    m.acc = h->mc_acc;
+    const int block = 256;
+    const int64_t resident = (int64_t)h->sm_count * std::max(1, mc_blocks_per_sm<R>(block));
+    const int gmeas = step_grid(h);
+    const int ncol = (int)h->mc_cstart.size() - 1;
+    cudaError_t e = cudaSuccess;
+    for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        const int64_t step = h->step + k;
+        double *dst = h->rec + (step % h->rec_cap) * (int64_t)h->nsys * kRecComps;
+        e = launch_measure<R>(a, h->block, gmeas, h->stream);
+        if (e == cudaSuccess) e = launch_finalize(h->sys, h->sys_tiles, h->nsys, h->partials, dst, h->stream);
+        for (int c = 0; c < ncol && e == cudaSuccess; ++c) {
+            m.c0 = h->mc_cstart[c];
+            m.c1 = h->mc_cstart[c + 1];
+            const int64_t need = (m.c1 - m.c0 + block - 1) / block;
+            const int grid = (int)std::max<int64_t>(1, std::min(need, resident));
+            e = launch_mc_colour<R>(a, m, block, grid, h->stream);
+        }
+        if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
+    }
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -919,6 +1048,8 @@ ss_status set_temperature(ss_system *h, double T) {
     if (st != SS_OK) return st;
     if (!(T >= 0.0) || !std::isfinite(T)) return fail(h, SS_ERR_INVALID_ARG, "T must be finite and >= 0");
     for (auto &d : h->hsys) d.sqrtT = std::sqrt(T);
+    for (auto &t : h->Tsys) t = T;
+    h->mc_par_dirty = true;
     clear_schedule(h);
     return upload_sqrtT(h);
 }
@@ -930,6 +1061,8 @@ ss_status set_temperature_batch(ss_system *h, const double *T, int32_t count) {
     for (int s = 0; s < count; ++s)
         if (!(T[s] >= 0.0) || !std::isfinite(T[s])) return fail(h, SS_ERR_INVALID_ARG, "T[%d] invalid", s);
     for (int s = 0; s < count; ++s) h->hsys[s].sqrtT = std::sqrt(T[s]);
+    for (int s = 0; s < count; ++s) h->Tsys[s] = T[s];
+    h->mc_par_dirty = true;
     clear_schedule(h);
     return upload_sqrtT(h);
 }
@@ -967,6 +1100,8 @@ ss_status set_temperature_schedule(ss_system *h, const double *T_per_step, int64
     if (h->sched_len != nsteps || h->sched_step0 != step0) drop_graph(h);
     h->sched_len = nsteps;
     h->sched_step0 = step0;
+    h->sched_T.assign(T_per_step, T_per_step + nsteps);
+    h->mc_par_dirty = true;
     return SS_OK;
 }
 
@@ -1020,6 +1155,37 @@ ss_status llg_heun_step(ss_system *h, int64_t n) {
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     h->step += n;
     return SS_OK;
+}
+
+ss_status mc_step(ss_system *h, int64_t nsteps) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (nsteps < 0) return fail(h, SS_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return SS_OK;
+    st = mc_prepare(h);
+    if (st != SS_OK) return st;
+    st = mc_upload_params(h);
+    if (st != SS_OK) return st;
+    const cudaError_t e = h->precision == SS_FP32_MIXED ? enqueue_mc<float>(h, nsteps) : enqueue_mc<double>(h, nsteps);
+    if (e != cudaSuccess) return cuda_fail(h, e, "Monte Carlo launch");
+    h->step += nsteps;
+    for (int s = 0; s < h->nsys; ++s) h->mc_tried[s] += h->sys_n[s] * nsteps;
+    return SS_OK;
+}
+
+ss_status get_mc_stats(ss_system *h, int32_t sys, int64_t out[2]) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!out) return fail(h, SS_ERR_INVALID_ARG, "out is NULL");
+    if (sys < 0 || sys >= h->nsys) return fail(h, SS_ERR_INVALID_ARG, "system %d out of range", sys);
+    out[0] = out[1] = 0;
+    if (!h->mc_acc) return check_device_flags(h);
+    unsigned long long acc = 0;
+    SS_CUDA(h, cudaMemcpyAsync(&acc, h->mc_acc + sys, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+    st = check_device_flags(h);
+    out[0] = (int64_t)acc;
+    out[1] = h->mc_tried[sys];
+    return st;
 }
 
 ss_status spin_system_sync(ss_system *h) {

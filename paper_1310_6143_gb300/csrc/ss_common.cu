@@ -7,6 +7,13 @@
 
 namespace ss {
 
+__global__ void k_advance_step(unsigned long long *step) { *step += 1ull; }
+
+cudaError_t launch_advance_step(unsigned long long *step, cudaStream_t s) {
+    k_advance_step<<<1, 1, 0, s>>>(step);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
                             double *dst, cudaStream_t s) {
     const int grid = nsys < 1024 ? nsys : 1024;

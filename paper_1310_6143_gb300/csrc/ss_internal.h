@@ -9,6 +9,7 @@ namespace ss {
 // Table I of the paper.
 constexpr double kBoltzmann = 1.3807e-23;   // J/K
 constexpr double kGammaDefault = 1.76e11;   // 1/(T s)
+constexpr double kBohrMagneton = 9.2740e-24;  // J/T
 
 // Sizes of the Box-Muller function tables held in shared memory.
 constexpr int kLogTab = 1537;  // centres c_t = (kLogFirst + t)/kLogScale, t = 0..1536: [0.75, 1.5]
@@ -108,6 +109,16 @@ struct KArgs {
     long long bar_timeout_ns;
 };
 
+// Monte Carlo colour pass (Section "Monte Carlo Methods"): the spins order[c0..c1) of one
+// colour class, each given one Hinzke-Nowak trial move.
+struct McArgs {
+    const int32_t *order;     // spins sorted by colour, then index
+    int64_t c0, c1;           // range of this colour class in order
+    const double2 *par_sys;   // per system (-kB T, sigma_g) when no schedule is set
+    const double2 *par_sched; // per schedule step (-kB T_k, sigma_g(T_k))
+    unsigned long long *acc;  // accepted trial moves per system
+};
+
 constexpr unsigned int kErrNonFinite = 1u;
 constexpr unsigned int kErrTimeout = 2u;
 
@@ -126,6 +137,10 @@ template <typename R> cudaError_t launch_system_blocks(const KArgs<R> &a, int bl
 template <typename R> int persistent_blocks_per_sm(int block);
 template <typename R> int step_blocks_per_sm(int block);
 template <typename R> int corrector_blocks_per_sm(int block, bool draw_ahead);
+template <typename R> cudaError_t launch_mc_colour(const KArgs<R> &a, const McArgs &m, int block, int grid,
+                                                   cudaStream_t s);
+template <typename R> int mc_blocks_per_sm(int block);
+cudaError_t launch_advance_step(unsigned long long *step, cudaStream_t s);
 cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
                             double *dst, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long long count, uint32_t *out,

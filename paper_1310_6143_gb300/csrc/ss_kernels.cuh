@@ -615,4 +615,105 @@ __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long lon
     }
 }
 
+// ----------------------------------------------------------------------------------
+// Monte Carlo (Section "Monte Carlo Methods")
+// ----------------------------------------------------------------------------------
+
+// One Hinzke-Nowak trial move (spin flip, Gaussian move Eq. MCgaussian, random move
+// Eq. MCrandom, picked with equal odds) for every spin of one colour class, accepted by
+// the Metropolis criterion Eq. AMCP as dE <= -kB T ln u.  Per (spin i, step n): Philox
+// block (i, n, system, 2) gives the Gaussian triple, block (i, n, system, 3) the move type
+// (from the first word, floor(3 w0 / 2^32)) and the acceptance uniform (second word).
+// Spins of one colour share no bond, so each trial reads only spins of other colours.
+// dE is the change of site i's Hamiltonian terms: exchange and applied field through the
+// field h = H_app + sum_j (J_ij / mu_s,i) S_j, then anisotropy and the Neel term.
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs m) {
+    __shared__ SmemTables tab;
+    stage_tables(a, tab);
+    __syncthreads();
+    const uint64_t step = *a.step;
+    for (int64_t k = m.c0 + (int64_t)blockIdx.x * BS + threadIdx.x; k < m.c1; k += (int64_t)gridDim.x * BS) {
+        const int64_t i = __ldg(m.order + k);
+        const MatDesc<R> &mt = a.mats[__ldg(a.mat + i)];
+        const SysDesc &sd = a.sys[mt.sys];
+        double2 par;
+        if (a.sched_len > 0) {
+            int64_t q = (int64_t)step - a.sched_step0;
+            q = q < 0 ? 0 : (q >= a.sched_len ? a.sched_len - 1 : q);
+            par = m.par_sched[q];
+        } else {
+            par = m.par_sys[mt.sys];
+        }
+        const uint32_t spin = (uint32_t)(i - sd.offset);
+        const Philox4 wa = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 2u, sd.key0, sd.key1);
+        const Philox4 wb = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 3u, sd.key0, sd.key1);
+        const int move = (int)(((uint64_t)wb.w0 * 3u) >> 32);
+        const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
+        R n0, n1, n2;
+        if (move == 0) {  // spin flip
+            n0 = -s0;
+            n1 = -s1;
+            n2 = -s2;
+        } else if (move == 1 && par.y == 0.0) {  // T = 0: a Gaussian cone of width 0
+            n0 = s0;
+            n1 = s1;
+            n2 = s2;
+        } else {
+            double g0, g1, g2;
+            box_muller3(wa, tab, g0, g1, g2);
+            if (move == 1) {  // Gaussian move: S + sigma_g Gamma, normalised
+                const double sg = par.y;
+                if constexpr (sizeof(R) == 8) {
+                    n0 = fma(sg, g0, (double)s0);
+                    n1 = fma(sg, g1, (double)s1);
+                    n2 = fma(sg, g2, (double)s2);
+                } else {
+                    const float sgf = narrow<float>(sg);
+                    n0 = fmaf(sgf, narrow<float>(g0), (float)s0);
+                    n1 = fmaf(sgf, narrow<float>(g1), (float)s1);
+                    n2 = fmaf(sgf, narrow<float>(g2), (float)s2);
+                }
+            } else {  // random move: Gamma normalised
+                n0 = narrow<R>(g0);
+                n1 = narrow<R>(g1);
+                n2 = narrow<R>(g2);
+            }
+            const R inv = rsqrt_r(n0 * n0 + n1 * n1 + n2 * n2);
+            n0 *= inv;
+            n1 *= inv;
+            n2 *= inv;
+        }
+        R h0, h1, h2;
+        exchange_sum<R, false>(a, sd, a.sx, a.sy, a.sz, i, h0, h1, h2);
+        // quadratic terms as (n - s).(A (n + s)): exactly zero when the spin is unchanged or
+        // flipped, whatever the contraction of products into FMAs
+        const R d0 = n0 - s0, d1 = n1 - s1, d2 = n2 - s2;
+        const R p0 = n0 + s0, p1 = n1 + s1, p2 = n2 + s2;
+        const R de = d0 * mt.e[0] + d1 * mt.e[1] + d2 * mt.e[2];
+        const R pe = p0 * mt.e[0] + p1 * mt.e[1] + p2 * mt.e[2];
+        R dE = -mt.mu * (d0 * h0 + d1 * h1 + d2 * h2) - mt.ku * (de * pe);
+        if (mt.has_neel) {
+            const R k0 = mt.K[0] * p0 + mt.K[3] * p1 + mt.K[4] * p2;
+            const R k1 = mt.K[3] * p0 + mt.K[1] * p1 + mt.K[5] * p2;
+            const R k2 = mt.K[4] * p0 + mt.K[5] * p1 + mt.K[2] * p2;
+            dE -= d0 * k0 + d1 * k1 + d2 * k2;
+        }
+        // accept when dE <= -kB T ln u = (-kB T)(-1/2)(-2 ln u); at T = 0 when dE <= 0
+        const double dEd = widen(dE);
+        const bool accept = par.x < 0.0 ? dEd <= par.x * (-0.5 * neg2log_u(wb.w1, tab)) : dEd <= 0.0;
+        if (accept) {
+            a.sx[i] = n0;
+            a.sy[i] = n1;
+            a.sz[i] = n2;
+        }
+        // accepted moves per system, one atomic per (warp, system)
+        const unsigned act = __activemask();
+        const unsigned same = __match_any_sync(act, mt.sys);
+        const unsigned yes = __ballot_sync(act, accept);
+        if ((int)(threadIdx.x & 31) == __ffs(same) - 1)
+            atomicAdd(m.acc + mt.sys, (unsigned long long)__popc(yes & same));
+    }
+}
+
 }  // namespace ss

@@ -93,6 +93,25 @@ int corrector_blocks_per_sm(int block, bool draw_ahead) {
 }
 
 template <typename R>
+cudaError_t launch_mc_colour(const KArgs<R> &a, const McArgs &m, int block, int grid, cudaStream_t s) {
+    SS_BLOCK_SWITCH(block, k_mc_colour<R, BS><<<grid, BS, 0, s>>>(a, m));
+    return cudaGetLastError();
+}
+
+template <typename R>
+int mc_blocks_per_sm(int block) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (block) {
+        case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc_colour<R, 128>, 128, 0); break;
+        case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc_colour<R, 256>, 256, 0); break;
+        case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc_colour<R, 512>, 512, 0); break;
+        default: break;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
+template <typename R>
 cudaError_t launch_persistent(const KArgs<R> &a, int block, int grid, int nfin, long long nsteps, cudaStream_t s) {
     KArgs<R> args = a;
     void *params[] = {(void *)&args, (void *)&nfin, (void *)&nsteps};
@@ -116,5 +135,7 @@ template cudaError_t launch_persistent<SS_REAL>(const KArgs<SS_REAL> &, int, int
 template int persistent_blocks_per_sm<SS_REAL>(int);
 template int step_blocks_per_sm<SS_REAL>(int);
 template int corrector_blocks_per_sm<SS_REAL>(int, bool);
+template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
+template int mc_blocks_per_sm<SS_REAL>(int);
 
 }  // namespace ss

@@ -182,6 +182,16 @@ class SpinSystem:
     def step(self, n: int = 1):
         self._check(self._lib.llg_heun_step(self._h, int(n)))
 
+    def mc_step(self, n: int = 1):
+        """n Hinzke-Nowak Monte Carlo steps (one trial move per spin each)."""
+        self._check(self._lib.mc_step(self._h, int(n)))
+
+    def mc_stats(self, sys: int = 0):
+        """(accepted, attempted) Monte Carlo trial moves of system `sys` so far."""
+        out = (ctypes.c_int64 * 2)()
+        self._check(self._lib.get_mc_stats(self._h, int(sys), out))
+        return int(out[0]), int(out[1])
+
     def sync(self):
         self._check(self._lib.spin_system_sync(self._h))
 
