@@ -237,6 +237,42 @@ def workload_table(stream, rank):
     return rows
 
 
+def time_mc(lat, kw, precision, steps, stream, warmup=3):
+    """Hinzke-Nowak Monte Carlo steps (one trial move per spin each, with the per-step
+    moment/energy record), timed with CUDA events on the handle's stream."""
+    import torch
+    from paper_1310_6143_gb300.system import SpinSystem
+
+    with SpinSystem(lat, precision=precision, stream=stream, **kw) as s:
+        s.mc_step(warmup)
+        s.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.mc_step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        s.sync()
+        ms = e0.elapsed_time(e1)
+        acc, tried = s.mc_stats(0)
+    return {"value": lat.n * steps / (ms * 1e-3), "unit": "spin trial moves/s", "steps": steps,
+            "ms_per_step": ms / steps, "acceptance": acc / tried}
+
+
+def mc_table(stream, rank, film_steps=100):
+    """Monte Carlo legs: the film (16.8 M spins, two colours) and the paper's Fig. MCLLG
+    system (simple cubic 28^3, J = 6.0e-21 J/link, periodic) at 300 K."""
+    from paper_1310_6143_gb300 import lattice as L
+
+    rows = {}
+    film = L.film(1024, 1024, 16)
+    for prec, k in (("fp32", film_steps), ("fp64", max(10, film_steps // 4))):
+        rows[f"film_{prec}"] = dict(spins=film.n, **time_mc(film, dict(T=300.0, seed=7 + rank), prec, k, stream))
+    sc28 = L.simple_cubic(28, 28, 28, J=6.0e-21, k_u=0.0)
+    for prec in ("fp32", "fp64"):
+        rows[f"sc28_{prec}"] = dict(spins=sc28.n, **time_mc(sc28, dict(T=300.0, seed=31 + rank), prec, 1000, stream))
+    return rows
+
+
 def run_reference(args):
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
@@ -268,6 +304,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU legs")
+    ap.add_argument("--mc-only", action="store_true",
+                    help="run only a short Monte Carlo leg on the film (for profiling) and print it")
     ap.add_argument("--no-autotune", action="store_true", help="no autotuning in the batched and workload legs")
     ap.add_argument("--autotune-film", action="store_true",
                     help="autotune the film's launch shape too (default: the library's default shape, "
@@ -304,6 +342,12 @@ def main():
     T = pulse_T(total_steps + 16)
     stream = torch.cuda.Stream()
     res = {}
+    if args.mc_only:
+        film = dict(spins=lat.n, **time_mc(lat, dict(T=300.0, seed=7 + rank), args.precision, args.steps, stream,
+                                           warmup=args.warmup))
+        if rank == 0:
+            print(json.dumps({"mc_film": film, "precision": args.precision}))
+        return
 
     def timed_run(precision, steps, warmup, seed):
         with SpinSystem(lat, alpha=0.02, dt=1e-16, T=300.0, seed=seed + rank, sys_id=rank, precision=precision,
@@ -424,6 +468,7 @@ def main():
                           "exec": EXEC_NAMES[tuned["exec"]],
                           "block": tuned["block"], "tile": tuned["tile"]}
         out["workloads"] = workload_table(stream, rank)
+        out["mc"] = mc_table(stream, rank)
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(lat, T)
     if rank == 0:
