@@ -1,5 +1,5 @@
-"""FP64 CPU oracle of the stochastic Heun-LLG step and of the Hinzke-Nowak Monte Carlo
-step (test infrastructure only).
+"""FP64 CPU oracle of the stochastic Heun-LLG step (with the optional macrocell
+demagnetising field) and of the Hinzke-Nowak Monte Carlo step (test infrastructure only).
 
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this package.  The product package never imports it, and the oracle shares
@@ -22,4 +22,6 @@ from .oracle import (  # noqa: F401
     colour_greedy,
     mc_sigma_g,
     mc_run,
+    macrocells,
+    demag_fields,
 )

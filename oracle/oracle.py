@@ -56,6 +56,10 @@ class _CSys(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("sys", ctypes.c_uint32),
         ("ids", ctypes.c_void_p),
+        ("pos", ctypes.c_void_p),
+        ("demag_cell", ctypes.c_double),
+        ("demag_vatom", ctypes.c_double),
+        ("demag_every", ctypes.c_int64),
     ]
 
 
@@ -87,6 +91,10 @@ def _load():
             lib.orc_mc_run.argtypes = [ctypes.POINTER(_CSys), P, ctypes.c_int64, ctypes.c_int64, P, P,
                                        ctypes.c_int32, P, P]
             lib.orc_mc_run.restype = ctypes.c_int
+            lib.orc_macrocells.argtypes = [ctypes.POINTER(_CSys), P]
+            lib.orc_macrocells.restype = ctypes.c_int64
+            lib.orc_demag_fields.argtypes = [ctypes.POINTER(_CSys), P, P, P]
+            lib.orc_demag_fields.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -113,6 +121,10 @@ class OracleSystem:
     seed: int = 1
     sys_id: int = 0
     ids: np.ndarray | None = None
+    pos: np.ndarray | None = None       # (n, 3) atomic positions, m (demagnetising field)
+    demag_cell: float = 0.0             # macrocell edge, m; 0: no demagnetising field
+    demag_vatom: float = 0.0            # volume per atom, m^3
+    demag_every: int = 1                # steps between demagnetising-field updates
     _keep: list = field(default_factory=list, repr=False)
 
     def __post_init__(self):
@@ -128,6 +140,8 @@ class OracleSystem:
             self.K_neel = np.ascontiguousarray(self.K_neel, dtype=np.float64).reshape(n, 6)
         if self.ids is not None:
             self.ids = np.ascontiguousarray(self.ids, dtype=np.uint32).reshape(n)
+        if self.pos is not None:
+            self.pos = np.ascontiguousarray(self.pos, dtype=np.float64).reshape(n, 3)
 
     @property
     def n(self) -> int:
@@ -151,6 +165,10 @@ class OracleSystem:
         c.seed = int(self.seed) & 0xFFFFFFFFFFFFFFFF
         c.sys = int(self.sys_id) & 0xFFFFFFFF
         c.ids = _ptr(self.ids)
+        c.pos = _ptr(self.pos)
+        c.demag_cell = float(self.demag_cell)
+        c.demag_vatom = float(self.demag_vatom)
+        c.demag_every = int(self.demag_every)
         return c
 
 
@@ -264,3 +282,25 @@ def mc_run(system: OracleSystem, S: np.ndarray, nsteps: int, T, step0: int = 0, 
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
     return S, rec, acc
+
+
+def macrocells(system: OracleSystem):
+    """Macrocell of every atom (needs ``pos`` and ``demag_cell``) -> (cell[n] int64, ncell)."""
+    cell = np.zeros(system.n, dtype=np.int64)
+    c = system._c()
+    nc = _load().orc_macrocells(ctypes.byref(c), _ptr(cell))
+    if nc < 0:
+        raise MemoryError("oracle: allocation failed")
+    return cell, int(nc)
+
+
+def demag_fields(system: OracleSystem, S: np.ndarray):
+    """Macrocell demagnetising field of the state S -> (per atom (n, 3), per macrocell (ncell, 3)), T."""
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(system.n, 3)
+    _, nc = macrocells(system)
+    Hd = np.zeros((system.n, 3))
+    Hmc = np.zeros((max(nc, 1), 3))
+    c = system._c()
+    if _load().orc_demag_fields(ctypes.byref(c), _ptr(S), _ptr(Hd), _ptr(Hmc)) < 0:
+        raise MemoryError("oracle: allocation failed")
+    return Hd, Hmc[:nc]

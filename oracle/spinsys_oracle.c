@@ -64,6 +64,25 @@
  *       neighbours, its anisotropy, its applied-field term and its Neel term.
  *   M5  The record of Monte Carlo step n holds the state at the start of the step.
  *
+ * Demagnetising field (Section "Demagnetising fields": Eqs. macrocellpos, mc_volume, demag,
+ * demag-fast), readings:
+ *   D1  Macrocells are cubes of edge `demag_cell` on a grid anchored at the smallest atomic
+ *       coordinate of the system on each axis; an atom belongs to the cube holding its
+ *       position; empty cubes are not macrocells.  Macrocells are numbered in the order of
+ *       their grid index (x fastest, then y, then z).
+ *   D2  Position of a macrocell: the moment-weighted centre of mass (Eq. macrocellpos);
+ *       moment: sum_i mu_s,i S_i; volume: n_atoms * V_atom (Eq. mc_volume), with V_atom =
+ *       V_uc / n_uc given per system (`demag_vatom`).
+ *   D3  H_p = mu0/(4 pi) sum_{q != p} [3 (m_q . r) r - m_q] / |r_pq|^3 - (mu0/3) m_p / V_p with
+ *       r the unit vector from p to q (Eq. demag); Eq. demag-fast is the same sum with the
+ *       dipole tensors precomputed (its printed diagonal "-1/3" and the missing 1/r^3 on its
+ *       off-diagonal entries are read as garbled: the self term is the separate -mu0/3 m/V).
+ *       mu0 = 4 pi 1e-7 T m/A.  H_p acts on every atom of macrocell p as an added field.
+ *   D4  The field is recomputed from the state at the start of step n when n is a multiple
+ *       of `demag_every` and at the first step of each call, and held fixed in between; both
+ *       Heun passes of a step use the same field.
+ *   D5  The recorded energies exclude the demagnetising energy.
+ *
  * Layout: spins and vectors are array-of-structures, 3 doubles per site (x, y, z).
  * Neel tensors are 6 doubles per site in the order xx, yy, zz, xy, xz, yz.
  *
@@ -84,6 +103,7 @@
 #define ORC_GAMMA 1.76e11      /* gyromagnetic ratio, 1/(T s) (Table I) */
 #define ORC_PI 3.14159265358979323846
 #define ORC_MUB 9.2740e-24     /* Bohr magneton, J/T (Table I) */
+#define ORC_MU0 (4.0e-7 * ORC_PI) /* vacuum permeability, T m/A (reading D3) */
 
 typedef struct {
     int64_t n;                /* number of spins                                  */
@@ -102,6 +122,10 @@ typedef struct {
     uint32_t sys;             /* system id (third counter word)                    */
     const uint32_t *ids;      /* [n] Philox spin word of each site, or NULL (= i); lets a
                                  test run a cut-out neighbourhood of a large system     */
+    const double *pos;        /* [3n] atomic positions, m (needed by the demag field)   */
+    double demag_cell;        /* macrocell edge, m; <= 0: no demagnetising field        */
+    double demag_vatom;       /* volume per atom V_uc / n_uc, m^3                       */
+    int64_t demag_every;      /* steps between updates of the demagnetising field       */
 } orc_system;
 
 static int g_threads = 1;
@@ -285,6 +309,102 @@ static void orc_normalise(double v[3]) {
     v[2] = v[2] / len;
 }
 
+/* ---------------------------------------------------------------------------------- */
+/* Macrocell demagnetising field, readings D1-D5 in the file header.                   */
+/* ---------------------------------------------------------------------------------- */
+
+/* Macrocell of every atom (D1): cell[i] in 0..ncell-1.  Returns ncell, or -1 if memory
+ * could not be allocated. */
+int64_t orc_macrocells(const orc_system *s, int64_t *cell) {
+    int64_t n = s->n;
+    if (n == 0) return 0;
+    double lo[3] = {s->pos[0], s->pos[1], s->pos[2]}, hi[3] = {s->pos[0], s->pos[1], s->pos[2]};
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (s->pos[3 * i + a] < lo[a]) lo[a] = s->pos[3 * i + a];
+            if (s->pos[3 * i + a] > hi[a]) hi[a] = s->pos[3 * i + a];
+        }
+    int64_t dim[3];
+    for (int a = 0; a < 3; ++a) dim[a] = (int64_t)floor((hi[a] - lo[a]) / s->demag_cell) + 1;
+    int64_t ngrid = dim[0] * dim[1] * dim[2];
+    int64_t *id = (int64_t *)malloc(sizeof(int64_t) * (size_t)ngrid);
+    if (!id) return -1;
+    for (int64_t g = 0; g < ngrid; ++g) id[g] = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c[3];
+        for (int a = 0; a < 3; ++a) c[a] = (int64_t)floor((s->pos[3 * i + a] - lo[a]) / s->demag_cell);
+        cell[i] = c[0] + dim[0] * (c[1] + dim[1] * c[2]);
+        id[cell[i]] = 0;
+    }
+    int64_t ncell = 0;
+    for (int64_t g = 0; g < ngrid; ++g)
+        if (id[g] == 0) id[g] = ncell++;
+    for (int64_t i = 0; i < n; ++i) cell[i] = id[cell[i]];
+    free(id);
+    return ncell;
+}
+
+/* Demagnetising field of every atom (tesla, AoS [3n]) for the state S (D2, D3).  If
+ * Hmc is not NULL it receives the field of each macrocell [3 ncell].  Returns ncell, or -1
+ * if memory could not be allocated. */
+int64_t orc_demag_fields(const orc_system *s, const double *S, double *Hd, double *Hmc) {
+    int64_t n = s->n;
+    int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!cell) return -1;
+    int64_t nc = orc_macrocells(s, cell);
+    if (nc < 0) {
+        free(cell);
+        return -1;
+    }
+    double *m = (double *)calloc((size_t)(3 * nc + 1), sizeof(double));
+    double *p = (double *)calloc((size_t)(3 * nc + 1), sizeof(double));
+    double *w = (double *)calloc((size_t)(nc + 1), sizeof(double));
+    double *na = (double *)calloc((size_t)(nc + 1), sizeof(double));
+    double *H = (double *)calloc((size_t)(3 * nc + 1), sizeof(double));
+    if (!m || !p || !w || !na || !H) {
+        free(cell); free(m); free(p); free(w); free(na); free(H);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c = cell[i];
+        double mu = s->mu_s[i];
+        for (int a = 0; a < 3; ++a) {
+            m[3 * c + a] += mu * S[3 * i + a];
+            p[3 * c + a] += mu * s->pos[3 * i + a];
+        }
+        w[c] += mu;
+        na[c] += 1.0;
+    }
+    for (int64_t c = 0; c < nc; ++c)
+        for (int a = 0; a < 3; ++a) p[3 * c + a] = p[3 * c + a] / w[c];
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+    for (int64_t a = 0; a < nc; ++a) {
+        double hx = 0.0, hy = 0.0, hz = 0.0;
+        for (int64_t b = 0; b < nc; ++b) {
+            if (b == a) continue;
+            double rx = p[3 * b + 0] - p[3 * a + 0];
+            double ry = p[3 * b + 1] - p[3 * a + 1];
+            double rz = p[3 * b + 2] - p[3 * a + 2];
+            double r = sqrt(rx * rx + ry * ry + rz * rz);
+            double ux = rx / r, uy = ry / r, uz = rz / r;
+            double mdotu = m[3 * b + 0] * ux + m[3 * b + 1] * uy + m[3 * b + 2] * uz;
+            double r3 = r * r * r;
+            hx += (3.0 * mdotu * ux - m[3 * b + 0]) / r3;
+            hy += (3.0 * mdotu * uy - m[3 * b + 1]) / r3;
+            hz += (3.0 * mdotu * uz - m[3 * b + 2]) / r3;
+        }
+        double V = na[a] * s->demag_vatom;
+        H[3 * a + 0] = ORC_MU0 / (4.0 * ORC_PI) * hx - ORC_MU0 / 3.0 * m[3 * a + 0] / V;
+        H[3 * a + 1] = ORC_MU0 / (4.0 * ORC_PI) * hy - ORC_MU0 / 3.0 * m[3 * a + 1] / V;
+        H[3 * a + 2] = ORC_MU0 / (4.0 * ORC_PI) * hz - ORC_MU0 / 3.0 * m[3 * a + 2] / V;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) Hd[3 * i + a] = H[3 * cell[i] + a];
+    if (Hmc) memcpy(Hmc, H, sizeof(double) * 3 * (size_t)nc);
+    free(cell); free(m); free(p); free(w); free(na); free(H);
+    return nc;
+}
+
 /*
  * Advance nsteps Heun steps from step index step0.  S [3n] is updated in place.
  * T[k] is the temperature of step step0+k (K).  If rec is not NULL it receives
@@ -296,8 +416,10 @@ int orc_heun_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, 
     double *Hth = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double *dS = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double *Sp = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-    if (!Hth || !dS || !Sp) {
-        free(Hth); free(dS); free(Sp);
+    int demag = s->demag_cell > 0.0;
+    double *Hd = demag ? (double *)calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double)) : NULL;
+    if (!Hth || !dS || !Sp || (demag && !Hd)) {
+        free(Hth); free(dS); free(Sp); free(Hd);
         return -1;
     }
     double gamma = s->gamma > 0.0 ? s->gamma : ORC_GAMMA;
@@ -306,6 +428,13 @@ int orc_heun_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, 
         uint32_t step = (uint32_t)(step0 + k);
         double Tn = T[k];
         if (rec) orc_moment_energy(s, S, rec + 8 * k);
+        /* demagnetising field from the state at the start of the step (D4) */
+        if (demag && (k == 0 || (step0 + k) % (s->demag_every > 0 ? s->demag_every : 1) == 0)) {
+            if (orc_demag_fields(s, S, Hd, NULL) < 0) {
+                free(Hth); free(dS); free(Sp); free(Hd);
+                return -1;
+            }
+        }
         /* thermal field, drawn once per step (R4) */
 #pragma omp parallel for schedule(static) num_threads(g_threads)
         for (int64_t i = 0; i < n; ++i) {
@@ -321,6 +450,11 @@ int orc_heun_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, 
         for (int64_t i = 0; i < n; ++i) {
             double hex[3], H[3];
             orc_site_field(s, S, i, hex, H);
+            if (demag) {
+                H[0] += Hd[3 * i + 0];
+                H[1] += Hd[3 * i + 1];
+                H[2] += Hd[3 * i + 2];
+            }
             H[0] += Hth[3 * i + 0];
             H[1] += Hth[3 * i + 1];
             H[2] += Hth[3 * i + 2];
@@ -339,6 +473,11 @@ int orc_heun_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, 
         for (int64_t i = 0; i < n; ++i) {
             double hex[3], H[3], dSp[3];
             orc_site_field(s, Sp, i, hex, H);
+            if (demag) {
+                H[0] += Hd[3 * i + 0];
+                H[1] += Hd[3 * i + 1];
+                H[2] += Hd[3 * i + 2];
+            }
             H[0] += Hth[3 * i + 0];
             H[1] += Hth[3 * i + 1];
             H[2] += Hth[3 * i + 2];
@@ -354,7 +493,7 @@ int orc_heun_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, 
             S[3 * i + 2] = v[2];
         }
     }
-    free(Hth); free(dS); free(Sp);
+    free(Hth); free(dS); free(Sp); free(Hd);
     return 0;
 }
 

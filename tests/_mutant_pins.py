@@ -233,9 +233,50 @@ def pin_colouring():
     return True
 
 
+def pin_demag():
+    """Macrocell demagnetising field: self term of one cell, axis / broadside ratio of two
+    dipoles, the moment-weighted cell centre, and the update interval."""
+    mu0, a, vat, muB = 4e-7 * math.pi, 3e-10, (3e-10) ** 3, 9.2740e-24
+
+    def pts(pos, mu, cell):
+        n = len(pos)
+        return O.OracleSystem(np.zeros(n + 1, dtype=np.int64), np.zeros(0, np.int32), np.zeros(0),
+                              np.broadcast_to(np.asarray(mu, dtype=float), (n,)), np.zeros(n), (0, 0, 1),
+                              pos=np.asarray(pos, dtype=float), demag_cell=cell, demag_vatom=vat)
+
+    g = np.stack(np.meshgrid(*[np.arange(3)] * 3, indexing="ij"), -1).reshape(-1, 3) * a
+    S = L.random_state(len(g), 3)
+    _, Hmc = O.demag_fields(pts(g, 2 * muB, 10 * a), S)
+    if not np.allclose(Hmc[0], -mu0 / 3 * 2 * muB * S.sum(0) / (len(g) * vat), rtol=1e-12, atol=0):
+        return False
+    two = [[0, 0, 0], [0, 0, 5e-9]]
+    s2 = pts(two, 1.5 * muB, a)
+    self_ = -mu0 / 3 * 1.5 * muB / vat
+    ax = O.demag_fields(s2, np.array([[0, 0, 1.0], [0, 0, 1.0]]))[0][0, 2] - self_
+    br = O.demag_fields(s2, np.array([[1.0, 0, 0], [1.0, 0, 0]]))[0][0, 0] - self_
+    if abs(ax / br + 2.0) > 1e-8:
+        return False
+    # a cell of a tiny and a large moment acts from (almost) the large one's position
+    mixed = pts([[0, 0, 0], [0.9 * a, 0, 0], [0.45 * a, 0, 6e-9]], [1e-6 * muB, 2 * muB, muB], 2 * a)
+    alone = pts([[0.9 * a, 0, 0], [0.45 * a, 0, 6e-9]], [2 * muB, muB], 2 * a)
+    up = lambda n: np.tile([0, 0, 1.0], (n, 1))  # noqa: E731
+    hm = O.demag_fields(mixed, up(3))[0][2]
+    ha = O.demag_fields(alone, up(2))[0][1]
+    if abs(hm[2] - ha[2]) > 1e-5 * abs(ha[2]) or abs(hm[0] - ha[0]) > 1e-5 * abs(ha[0]):
+        return False
+    lat = L.simple_cubic(6, 6, 2, periodic=(False, False, False), J=6e-21, k_u=0.0, with_pos=True)
+    mk = lambda every: O.OracleSystem(lat.row_ptr, lat.col, lat.J, lat.mu_s, lat.k_u, lat.easy_axis,  # noqa: E731
+                                      alpha=0.5, dt=1e-15, seed=5, pos=lat.pos, demag_cell=6e-10,
+                                      demag_vatom=(3e-10) ** 3, demag_every=every)
+    S0 = L.random_state(lat.n, 1)
+    r5, _ = O.heun_run(mk(5), S0, 10, 50.0)
+    r1, _ = O.heun_run(mk(1), S0, 10, 50.0)
+    return np.abs(r5 - r1).max() > 1e-9
+
+
 PINS = [pin_field_gradient, pin_single_spin_analytic, pin_unit_length, pin_gaussians, pin_philox_against_torch,
         pin_boltzmann, pin_curie, pin_mc_boltzmann, pin_mc_langevin, pin_mc_dimer, pin_mc_moves, pin_mc_sigma,
-        pin_mc_zero_T, pin_colouring]
+        pin_mc_zero_T, pin_colouring, pin_demag]
 
 if __name__ == "__main__":
     for p in PINS:

@@ -53,6 +53,17 @@ MUTANTS = [
     ("colouring ignores the neighbours", "        while (c < cap && seen[c] == i) ++c;", "        c = 0;"),
     ("record taken after the step", "        if (rec) orc_moment_energy(s, S, rec + 8 * k);\n        int64_t acc = 0;",
      "        int64_t acc = 0;"),
+    # demagnetising field
+    ("self term without the factor 1/3", "- ORC_MU0 / 3.0 * m[3 * a + 0] / V;", "- ORC_MU0 * m[3 * a + 0] / V;"),
+    ("dipole term with 2 (m.r)r", "            hz += (3.0 * mdotu * uz - m[3 * b + 2]) / r3;",
+     "            hz += (2.0 * mdotu * uz - m[3 * b + 2]) / r3;"),
+    ("cell centre not weighted by the moment",
+     "            p[3 * c + a] += mu * s->pos[3 * i + a];\n        }\n        w[c] += mu;",
+     "            p[3 * c + a] += s->pos[3 * i + a];\n        }\n        w[c] += 1.0;"),
+    ("cell volume from the cube edge", "        double V = na[a] * s->demag_vatom;",
+     "        double V = s->demag_cell * s->demag_cell * s->demag_cell;"),
+    ("demagnetising field updated every step",
+     "(k == 0 || (step0 + k) % (s->demag_every > 0 ? s->demag_every : 1) == 0)", "(1)"),
 ]
 
 
