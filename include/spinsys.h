@@ -80,8 +80,8 @@ typedef enum {
 
 typedef struct {
     int64_t n;                /* spins, 1 <= n < 2^31                                  */
-    const double *pos;        /* [3n] positions (m) or NULL; validated, not used by the
-                                 step (no long-range term is computed)                */
+    const double *pos;        /* [3n] positions (m) or NULL; validated; kept (with mu_s)
+                                 when every system has them, for set_demag              */
     const double *mu_s;       /* [n] atomic moments, J/T, > 0                          */
     const double *k_u;        /* [n] uniaxial anisotropy, J/atom                       */
     const double *easy_axis;  /* [3n] easy axes (normalised on copy) or NULL for +z    */
@@ -187,6 +187,25 @@ ss_status llg_heun_step(ss_system *h, int64_t n);
  * at its start.  The first call builds the colouring (a copy of the neighbour list to the
  * host, one int32 per spin of device memory).  SS_ERR_INVALID_ARG for n < 0. */
 ss_status mc_step(ss_system *h, int64_t n);
+
+/* Macrocell demagnetising field (Section "Demagnetising fields"; Eqs. macrocellpos,
+ * mc_volume, demag).  Needs the atomic positions (ss_params.pos) of every system.  Each
+ * system is divided into cubic macrocells of edge `cell_size` (m) on a grid anchored at its
+ * smallest coordinate on each axis; occupied cubes are the macrocells.  A macrocell sits at
+ * the moment-weighted mean position of its atoms, has the moment sum_i mu_s,i S_i and the
+ * volume n_atoms * atom_volume (atom_volume = V_uc / n_uc, m^3).  Its field is
+ * mu0/(4 pi) sum over the other macrocells of the same system of [3 (m.u) u - m] / r^3 minus
+ * the self term mu0/3 m_p / V_p (FP64), and it is added to the field of every atom in the
+ * cell.  The field is recomputed from the state at the start of every step whose index is a
+ * multiple of `every` (and at the first step after set_demag, set_spins or set_step) and held
+ * in between; llg_heun_step uses it (mc_step does not); the recorded energies exclude it.
+ * cell_size <= 0 switches the field off.  SS_ERR_INVALID_ARG without positions or for
+ * atom_volume <= 0 or every < 1.  The all-pairs sum costs O(macrocells^2) per update. */
+ss_status set_demag(ss_system *h, double cell_size, double atom_volume, int32_t every);
+
+/* The demagnetising field in force for the next step, per atom (AoS [3n], tesla); computed
+ * from the current state first if it is due (synchronous). */
+ss_status get_demag_field(ss_system *h, double *out3n);
 
 /* Monte Carlo acceptance of system `sys` since the handle was created: out[0] accepted
  * trial moves, out[1] attempted trial moves (synchronous). */

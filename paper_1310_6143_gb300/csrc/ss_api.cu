@@ -117,6 +117,17 @@ struct ss_system {
     unsigned long long *mc_acc = nullptr;    // accepted trial moves per system (device)
     std::vector<int64_t> mc_tried;           // trial moves per system (host count)
 
+    // Macrocell demagnetising field (set_demag)
+    std::vector<double> hpos, hmu;           // positions [3n] and moments [n] when given at create
+    bool demag_on = false, demag_stale = true;
+    double demag_cell = 0.0, demag_vatom = 0.0;
+    int64_t demag_every = 1, ncell = 0;
+    std::vector<int32_t> hcell_of;           // macrocell of each spin (host copy)
+    int32_t *d_cell_of = nullptr, *d_cell_start = nullptr, *d_cell_spins = nullptr, *d_cell_first = nullptr,
+            *d_cell_end = nullptr;
+    double *d_cpos = nullptr, *d_cvol = nullptr, *d_cm = nullptr, *d_cH = nullptr;
+    void *d_hd[3] = {};
+
     // launch state
     int nfin = 1;
     cudaGraphExec_t graph = nullptr;
@@ -287,6 +298,11 @@ KArgs<R> make_args(const ss_system *h) {
     a.J = static_cast<const R *>(h->J);
     a.J_value = (R)h->J_value;
     a.J_uniform = h->J_uniform ? 1 : 0;
+    a.demag = h->demag_on ? 1 : 0;
+    a.mc_of = h->d_cell_of;
+    a.hdx = static_cast<const R *>(h->d_hd[0]);
+    a.hdy = static_cast<const R *>(h->d_hd[1]);
+    a.hdz = static_cast<const R *>(h->d_hd[2]);
     a.mat = h->mat;
     a.mats = static_cast<const MatDesc<R> *>(h->mats);
     a.sys = h->sys;
@@ -727,9 +743,17 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         return st;
     }
     h->stream = h->own_stream;
+    bool all_pos = true;
     for (int s = 0; s < count; ++s) {
         h->sys_offset.push_back(hs[s].offset);
         h->sys_n.push_back(systems[s].n);
+        all_pos = all_pos && systems[s].pos != nullptr;
+    }
+    if (all_pos) {  // kept for the macrocell demagnetising field
+        for (int s = 0; s < count; ++s) {
+            h->hpos.insert(h->hpos.end(), systems[s].pos, systems[s].pos + 3 * systems[s].n);
+            h->hmu.insert(h->hmu.end(), systems[s].mu_s, systems[s].mu_s + systems[s].n);
+        }
     }
     // system table
     h->hsys.resize((size_t)count);
@@ -860,6 +884,129 @@ ss_status time_kernels_impl(ss_system *h, int32_t nsteps, double out_ms[3]) {
     out_ms[1] = tc / nsteps;
     out_ms[2] = all / nsteps;
     return check_device_flags(h);
+}
+
+// ----------------------------------------------------------------------------------
+// Macrocell demagnetising field (Section "Demagnetising fields")
+// ----------------------------------------------------------------------------------
+
+void demag_free(ss_system *h) {
+    void *bufs[] = {h->d_cell_of, h->d_cell_start, h->d_cell_spins, h->d_cell_first, h->d_cell_end, h->d_cpos,
+                    h->d_cvol, h->d_cm, h->d_cH, h->d_hd[0], h->d_hd[1], h->d_hd[2]};
+    for (void *b : bufs)
+        if (b) dfree(h, b);
+    h->d_cell_of = h->d_cell_start = h->d_cell_spins = h->d_cell_first = h->d_cell_end = nullptr;
+    h->d_cpos = h->d_cvol = h->d_cm = h->d_cH = nullptr;
+    h->d_hd[0] = h->d_hd[1] = h->d_hd[2] = nullptr;
+    h->ncell = 0;
+    h->hcell_of.clear();
+}
+
+// Macrocells of every system: cubes of edge `cell` on a grid anchored at the system's
+// smallest coordinate on each axis, numbered by grid index (x fastest) among the occupied
+// cubes, systems one after another.  Centre: the moment-weighted mean position; volume:
+// n_atoms * vatom.
+ss_status demag_build(ss_system *h, double cell, double vatom) {
+    const int64_t n = h->n;
+    std::vector<int32_t> cell_of((size_t)n);
+    std::vector<int32_t> first, end;
+    std::vector<double> cpos, cw, cvol;
+    int64_t ncell = 0;
+    for (int s = 0; s < h->nsys; ++s) {
+        const int64_t off = h->sys_offset[s], ns = h->sys_n[s];
+        if (ns == 0) continue;
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) lo[a] = hi[a] = h->hpos[3 * off + a];
+        for (int64_t i = off; i < off + ns; ++i)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], h->hpos[3 * i + a]);
+                hi[a] = std::max(hi[a], h->hpos[3 * i + a]);
+            }
+        int64_t dim[3];
+        for (int a = 0; a < 3; ++a) dim[a] = (int64_t)std::floor((hi[a] - lo[a]) / cell) + 1;
+        std::vector<int64_t> g((size_t)ns);
+        for (int64_t k = 0; k < ns; ++k) {
+            int64_t c[3];
+            for (int a = 0; a < 3; ++a) c[a] = (int64_t)std::floor((h->hpos[3 * (off + k) + a] - lo[a]) / cell);
+            g[k] = c[0] + dim[0] * (c[1] + dim[1] * c[2]);
+        }
+        std::vector<int64_t> occupied(g);
+        std::sort(occupied.begin(), occupied.end());
+        occupied.erase(std::unique(occupied.begin(), occupied.end()), occupied.end());
+        const int64_t c0 = ncell;
+        ncell += (int64_t)occupied.size();
+        cpos.resize(3 * (size_t)ncell, 0.0);
+        cw.resize((size_t)ncell, 0.0);
+        cvol.resize((size_t)ncell, 0.0);
+        for (int64_t k = 0; k < ns; ++k) {
+            const int64_t c = c0 + (std::lower_bound(occupied.begin(), occupied.end(), g[k]) - occupied.begin());
+            cell_of[off + k] = (int32_t)c;
+            const double mu = h->hmu[off + k];
+            for (int a = 0; a < 3; ++a) cpos[3 * c + a] += mu * h->hpos[3 * (off + k) + a];
+            cw[c] += mu;
+            cvol[c] += 1.0;
+        }
+        for (int64_t c = c0; c < ncell; ++c) {
+            for (int a = 0; a < 3; ++a) cpos[3 * c + a] = cpos[3 * c + a] / cw[c];
+            cvol[c] = cvol[c] * vatom;
+            first.push_back((int32_t)c0);
+            end.push_back((int32_t)ncell);
+        }
+    }
+    if (ncell >= (int64_t(1) << 31)) return fail(h, SS_ERR_INVALID_ARG, "too many macrocells");
+    std::vector<int32_t> start((size_t)ncell + 1, 0), spins((size_t)std::max<int64_t>(n, 1));
+    for (int64_t i = 0; i < n; ++i) start[cell_of[i] + 1]++;
+    for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+    std::vector<int32_t> fill(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < n; ++i) spins[fill[cell_of[i]]++] = (int32_t)i;
+    demag_free(h);
+    const size_t rs = real_size(h), nc = (size_t)std::max<int64_t>(ncell, 1);
+    SS_CUDA(h, dalloc(h, (void **)&h->d_cell_of, cell_of.size() * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, (void **)&h->d_cell_start, start.size() * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, (void **)&h->d_cell_spins, spins.size() * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, (void **)&h->d_cell_first, nc * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, (void **)&h->d_cell_end, nc * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, (void **)&h->d_cpos, 3 * nc * sizeof(double)));
+    SS_CUDA(h, dalloc(h, (void **)&h->d_cvol, nc * sizeof(double)));
+    SS_CUDA(h, dalloc(h, (void **)&h->d_cm, 3 * nc * sizeof(double)));
+    SS_CUDA(h, dalloc(h, (void **)&h->d_cH, 3 * nc * sizeof(double)));
+    for (int c = 0; c < 3; ++c) SS_CUDA(h, dalloc(h, &h->d_hd[c], nc * rs));
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream) : cudaSuccess;
+    };
+    SS_CUDA(h, up(h->d_cell_of, cell_of.data(), cell_of.size() * sizeof(int32_t)));
+    SS_CUDA(h, up(h->d_cell_start, start.data(), start.size() * sizeof(int32_t)));
+    SS_CUDA(h, up(h->d_cell_spins, spins.data(), (size_t)n * sizeof(int32_t)));
+    SS_CUDA(h, up(h->d_cell_first, first.data(), first.size() * sizeof(int32_t)));
+    SS_CUDA(h, up(h->d_cell_end, end.data(), end.size() * sizeof(int32_t)));
+    SS_CUDA(h, up(h->d_cpos, cpos.data(), cpos.size() * sizeof(double)));
+    SS_CUDA(h, up(h->d_cvol, cvol.data(), cvol.size() * sizeof(double)));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->ncell = ncell;
+    h->hcell_of.swap(cell_of);
+    return SS_OK;
+}
+
+template <typename R>
+cudaError_t enqueue_demag_update(ss_system *h) {
+    const KArgs<R> a = make_args<R>(h);
+    DemagArgs d{};
+    d.ncell = h->ncell;
+    d.cell_start = h->d_cell_start;
+    d.cell_spins = h->d_cell_spins;
+    d.cell_first = h->d_cell_first;
+    d.cell_end = h->d_cell_end;
+    d.pos = h->d_cpos;
+    d.vol = h->d_cvol;
+    d.m = h->d_cm;
+    d.H = h->d_cH;
+    return launch_demag<R>(a, d, h->stream);
+}
+
+cudaError_t demag_update(ss_system *h) {
+    cudaError_t e = h->precision == SS_FP32_MIXED ? enqueue_demag_update<float>(h) : enqueue_demag_update<double>(h);
+    if (e == cudaSuccess) h->demag_stale = false;
+    return e;
 }
 
 // ----------------------------------------------------------------------------------
@@ -1105,11 +1252,31 @@ ss_status set_temperature_schedule(ss_system *h, const double *T_per_step, int64
     return SS_OK;
 }
 
+static ss_status advance_steps(ss_system *h, int64_t n);
+
 ss_status llg_heun_step(ss_system *h, int64_t n) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
     if (n < 0) return fail(h, SS_ERR_INVALID_ARG, "n must be >= 0");
     if (n == 0) return SS_OK;
+    if (!h->demag_on) return advance_steps(h, n);
+    // demagnetising field: recomputed at multiples of the interval (and when stale), held in
+    // between; the steps between two updates run as one chunk
+    while (n > 0) {
+        const int64_t r = h->step % h->demag_every;
+        if (r == 0 || h->demag_stale) {
+            const cudaError_t e = demag_update(h);
+            if (e != cudaSuccess) return cuda_fail(h, e, "demagnetising field");
+        }
+        const int64_t chunk = std::min<int64_t>(n, h->demag_every - r);
+        st = advance_steps(h, chunk);
+        if (st != SS_OK) return st;
+        n -= chunk;
+    }
+    return SS_OK;
+}
+
+static ss_status advance_steps(ss_system *h, int64_t n) {
     cudaError_t e = cudaSuccess;
     int mode = h->exec;
     if (mode == SS_EXEC_AUTO) mode = n >= graph_len(h) ? SS_EXEC_GRAPH : SS_EXEC_KERNELS;
@@ -1154,6 +1321,51 @@ ss_status llg_heun_step(ss_system *h, int64_t n) {
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     h->step += n;
+    return SS_OK;
+}
+
+ss_status set_demag(ss_system *h, double cell_size, double atom_volume, int32_t every) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!std::isfinite(cell_size)) return fail(h, SS_ERR_INVALID_ARG, "cell_size must be finite");
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    drop_graph(h);  // captured launches hold the previous arguments
+    if (cell_size <= 0.0) {
+        h->demag_on = false;
+        demag_free(h);
+        return SS_OK;
+    }
+    if (h->hpos.empty()) return fail(h, SS_ERR_INVALID_ARG, "the demagnetising field needs atomic positions (pos)");
+    if (!(atom_volume > 0.0) || !std::isfinite(atom_volume))
+        return fail(h, SS_ERR_INVALID_ARG, "atom_volume must be finite and > 0");
+    if (every < 1) return fail(h, SS_ERR_INVALID_ARG, "every must be >= 1");
+    h->demag_on = false;
+    st = demag_build(h, cell_size, atom_volume);
+    if (st != SS_OK) return st;
+    h->demag_cell = cell_size;
+    h->demag_vatom = atom_volume;
+    h->demag_every = every;
+    h->demag_on = true;
+    h->demag_stale = true;
+    return SS_OK;
+}
+
+ss_status get_demag_field(ss_system *h, double *out3n) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (!out3n) return fail(h, SS_ERR_INVALID_ARG, "out3n is NULL");
+    if (!h->demag_on) return fail(h, SS_ERR_INVALID_ARG, "the demagnetising field is not enabled (set_demag)");
+    if (h->demag_stale) {
+        const cudaError_t e = demag_update(h);
+        if (e != cudaSuccess) return cuda_fail(h, e, "demagnetising field");
+    }
+    std::vector<double> H(3 * (size_t)std::max<int64_t>(h->ncell, 1));
+    SS_CUDA(h, cudaMemcpyAsync(H.data(), h->d_cH, 3 * (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+    st = check_device_flags(h);
+    if (st != SS_OK) return st;
+    for (int64_t i = 0; i < h->n; ++i)
+        for (int c = 0; c < 3; ++c) out3n[3 * i + c] = H[3 * (size_t)h->hcell_of[i] + c];
     return SS_OK;
 }
 
@@ -1306,6 +1518,7 @@ ss_status set_spins(ss_system *h, const double *in3n) {
                                        h->stream));
         SS_CUDA(h, cudaStreamSynchronize(h->stream));
     }
+    h->demag_stale = true;  // the held demagnetising field belongs to the previous state
     return SS_OK;
 }
 
@@ -1317,6 +1530,7 @@ ss_status set_step(ss_system *h, int64_t step) {
     SS_CUDA(h, cudaMemcpyAsync(h->ctl, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
     h->step = step;
+    h->demag_stale = true;
     return SS_OK;
 }
 

@@ -10,6 +10,7 @@ namespace ss {
 constexpr double kBoltzmann = 1.3807e-23;   // J/K
 constexpr double kGammaDefault = 1.76e11;   // 1/(T s)
 constexpr double kBohrMagneton = 9.2740e-24;  // J/T
+constexpr double kMu0 = 4.0e-7 * 3.14159265358979323846;  // vacuum permeability, T m/A
 
 // Sizes of the Box-Muller function tables held in shared memory.
 constexpr int kLogTab = 1537;  // centres c_t = (kLogFirst + t)/kLogScale, t = 0..1536: [0.75, 1.5]
@@ -74,6 +75,9 @@ struct KArgs {
     const R *J;               // [nnz] J_ij / mu_s,i (the exchange field per unit spin, T)
     R J_value;                // the common value when every entry of J is the same
     int J_uniform;            // 1: J is not read, every bond has J_value
+    const int32_t *mc_of;     // [n] macrocell of each spin (demagnetising field)
+    const R *hdx, *hdy, *hdz; // [ncell] demagnetising field of each macrocell (T)
+    int demag;                // 1: add the macrocell field to every spin's field
     const int32_t *mat;       // [n] material index
     const MatDesc<R> *mats;
     const SysDesc *sys;
@@ -119,6 +123,19 @@ struct McArgs {
     unsigned long long *acc;  // accepted trial moves per system
 };
 
+// Macrocell demagnetising field (Section "Demagnetising fields").
+struct DemagArgs {
+    int64_t ncell;
+    const int32_t *cell_start;  // [ncell+1] spins of cell c: cell_spins[cell_start[c] .. cell_start[c+1])
+    const int32_t *cell_spins;  // spins sorted by cell, then index
+    const int32_t *cell_first;  // [ncell] first macrocell of the cell's system
+    const int32_t *cell_end;    // [ncell] one past the last macrocell of the cell's system
+    const double *pos;          // [3 ncell] moment-weighted centre of each cell, m
+    const double *vol;          // [ncell] effective volume n_atoms V_atom, m^3
+    double *m;                  // [3 ncell] moment of each cell, J/T
+    double *H;                  // [3 ncell] field of each cell, T
+};
+
 constexpr unsigned int kErrNonFinite = 1u;
 constexpr unsigned int kErrTimeout = 2u;
 
@@ -141,6 +158,7 @@ template <typename R> cudaError_t launch_mc_colour(const KArgs<R> &a, const McAr
                                                    cudaStream_t s);
 template <typename R> int mc_blocks_per_sm(int block);
 cudaError_t launch_advance_step(unsigned long long *step, cudaStream_t s);
+template <typename R> cudaError_t launch_demag(const KArgs<R> &a, const DemagArgs &d, cudaStream_t s);
 cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
                             double *dst, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long long count, uint32_t *out,

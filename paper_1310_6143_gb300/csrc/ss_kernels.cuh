@@ -109,6 +109,16 @@ __device__ __forceinline__ R det_field(const MatDesc<R> &m, R s0, R s1, R s2, R 
     return sde;
 }
 
+// The macrocell demagnetising field of spin i's cell, added to its field (Eq. demag; the
+// field is held between updates, so it is read like a parameter).
+template <typename R>
+__device__ __forceinline__ void add_demag(const KArgs<R> &a, int64_t i, R &H0, R &H1, R &H2) {
+    const int32_t c = __ldg(a.mc_of + i);
+    H0 += __ldg(a.hdx + c);
+    H1 += __ldg(a.hdy + c);
+    H2 += __ldg(a.hdz + c);
+}
+
 // dS = -gamma/(1+lambda^2) [S x H + lambda S x (S x H)]  (Eq. LLG)
 template <typename R>
 __device__ __forceinline__ void llg_rhs(R gp, R lam, R s0, R s1, R s2, R H0, R H1, R H2, R &d0, R &d1, R &d2) {
@@ -250,6 +260,7 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
         exchange_sum<R, Coherent>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
         R H0, H1, H2;
         const R sde = det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+        if (a.demag) add_demag(a, i, H0, H1, H2);
         R t0 = 0, t1 = 0, t2 = 0;
         if (sqrtT > (R)0) {
             const R sig = m.sig * sqrtT;
@@ -314,6 +325,7 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
         exchange_sum<R, Coherent>(a, sd, a.px, a.py, a.pz, i, e0, e1, e2);
         R H0, H1, H2;
         det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+        if (a.demag) add_demag(a, i, H0, H1, H2);
         H0 += ld<Coherent>(a.hx + i);
         H1 += ld<Coherent>(a.hy + i);
         H2 += ld<Coherent>(a.hz + i);
@@ -613,6 +625,74 @@ __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long lon
             __threadfence();
         }
     }
+}
+
+// ----------------------------------------------------------------------------------
+// Macrocell demagnetising field (Section "Demagnetising fields")
+// ----------------------------------------------------------------------------------
+
+// Moment of every macrocell, m_c = sum_i mu_s,i S_i over its spins (the moment equation):
+// one warp per cell, FP64, summed in a fixed order (lane-strided, then a fixed butterfly).
+template <typename R>
+__global__ void k_demag_moments(const KArgs<R> a, const DemagArgs d) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = warp; c < d.ncell; c += nwarps) {
+        double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+        for (int32_t k = d.cell_start[c] + lane; k < d.cell_start[c + 1]; k += 32) {
+            const int32_t i = d.cell_spins[k];
+            const double mu = widen(a.mats[a.mat[i]].mu);
+            m0 += mu * widen(a.sx[i]);
+            m1 += mu * widen(a.sy[i]);
+            m2 += mu * widen(a.sz[i]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            m0 += __shfl_xor_sync(0xffffffffu, m0, o);
+            m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+            m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+        }
+        if (lane == 0) {
+            d.m[3 * c + 0] = m0;
+            d.m[3 * c + 1] = m1;
+            d.m[3 * c + 2] = m2;
+        }
+    }
+}
+
+// Field of every macrocell p (Eq. demag): mu0/(4 pi) sum over the other cells q of the same
+// system of [3 (m_q . u) u - m_q] / r^3, u the unit vector from p to q, minus the self term
+// mu0/3 m_p / V_p; FP64, q in increasing order.  Also writes the working-type copy the step
+// kernels read.
+template <typename R>
+__global__ void k_demag_field(const KArgs<R> a, const DemagArgs d) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= d.ncell) return;
+    const double px = d.pos[3 * p], py = d.pos[3 * p + 1], pz = d.pos[3 * p + 2];
+    double hx = 0.0, hy = 0.0, hz = 0.0;
+    for (int32_t q = d.cell_first[p]; q < d.cell_end[p]; ++q) {
+        if (q == p) continue;
+        const double rx = d.pos[3 * q] - px, ry = d.pos[3 * q + 1] - py, rz = d.pos[3 * q + 2] - pz;
+        const double rinv = rsqrt_pos(rx * rx + ry * ry + rz * rz);
+        const double ux = rx * rinv, uy = ry * rinv, uz = rz * rinv;
+        const double mx = d.m[3 * q], my = d.m[3 * q + 1], mz = d.m[3 * q + 2];
+        const double mu3 = 3.0 * (mx * ux + my * uy + mz * uz);
+        const double r3inv = rinv * rinv * rinv;
+        hx += (mu3 * ux - mx) * r3inv;
+        hy += (mu3 * uy - my) * r3inv;
+        hz += (mu3 * uz - mz) * r3inv;
+    }
+    const double c1 = kMu0 / (4.0 * 3.14159265358979323846), c2 = kMu0 / 3.0 / d.vol[p];
+    const double H0 = c1 * hx - c2 * d.m[3 * p], H1 = c1 * hy - c2 * d.m[3 * p + 1];
+    const double H2 = c1 * hz - c2 * d.m[3 * p + 2];
+    d.H[3 * p] = H0;
+    d.H[3 * p + 1] = H1;
+    d.H[3 * p + 2] = H2;
+    R *hx_ = const_cast<R *>(a.hdx), *hy_ = const_cast<R *>(a.hdy), *hz_ = const_cast<R *>(a.hdz);
+    hx_[p] = narrow<R>(H0);
+    hy_[p] = narrow<R>(H1);
+    hz_[p] = narrow<R>(H2);
 }
 
 // ----------------------------------------------------------------------------------

@@ -99,6 +99,17 @@ cudaError_t launch_mc_colour(const KArgs<R> &a, const McArgs &m, int block, int 
 }
 
 template <typename R>
+cudaError_t launch_demag(const KArgs<R> &a, const DemagArgs &d, cudaStream_t s) {
+    if (d.ncell <= 0) return cudaSuccess;
+    const int64_t wblocks = (d.ncell * 32 + 255) / 256;
+    k_demag_moments<R><<<(int)(wblocks < 4096 ? wblocks : 4096), 256, 0, s>>>(a, d);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_demag_field<R><<<(int)((d.ncell + 127) / 128), 128, 0, s>>>(a, d);
+    return cudaGetLastError();
+}
+
+template <typename R>
 int mc_blocks_per_sm(int block) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
@@ -137,5 +148,6 @@ template int step_blocks_per_sm<SS_REAL>(int);
 template int corrector_blocks_per_sm<SS_REAL>(int, bool);
 template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
 template int mc_blocks_per_sm<SS_REAL>(int);
+template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
 
 }  // namespace ss

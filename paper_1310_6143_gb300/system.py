@@ -182,6 +182,18 @@ class SpinSystem:
     def step(self, n: int = 1):
         self._check(self._lib.llg_heun_step(self._h, int(n)))
 
+    def set_demag(self, cell_size: float, atom_volume: float, every: int = 1):
+        """Macrocell demagnetising field: cubic cells of edge cell_size (m), volume per atom
+        atom_volume (m^3), recomputed every `every` steps; cell_size <= 0 switches it off.
+        Needs the lattices' positions."""
+        self._check(self._lib.set_demag(self._h, float(cell_size), float(atom_volume), int(every)))
+
+    def demag_field(self) -> np.ndarray:
+        """The demagnetising field in force, per atom, (n, 3) tesla."""
+        out = np.zeros((self.n, 3))
+        self._check(self._lib.get_demag_field(self._h, B.ptr(out)))
+        return out
+
     def mc_step(self, n: int = 1):
         """n Hinzke-Nowak Monte Carlo steps (one trial move per spin each)."""
         self._check(self._lib.mc_step(self._h, int(n)))
