@@ -273,6 +273,46 @@ def mc_table(stream, rank, film_steps=100):
     return rows
 
 
+def demag_table(stream, rank):
+    """Macrocell demagnetising field on the paper's ellipsoid: cost of one field update
+    (cell-pair interactions per second) and Heun-LLG throughput with the paper's update
+    every 100 steps."""
+    import torch
+    from paper_1310_6143_gb300.system import SpinSystem
+
+    from paper_1310_6143_gb300 import lattice as L
+
+    lat = L.prolate_ellipsoid()
+    vatom, cell = lat.meta["atom_volume"], 2 * lat.meta["a"]
+    grid = np.floor((lat.pos - lat.pos.min(axis=0)) / cell).astype(np.int64)
+    nc = int(np.unique(grid[:, 0] + 4096 * (grid[:, 1] + 4096 * grid[:, 2])).size)
+    rows = {}
+    for prec in ("fp32", "fp64"):
+        res = {}
+        for every in (0, 1, 100):
+            with SpinSystem(lat, alpha=0.1, dt=1e-16, T=300.0, seed=9 + rank, precision=prec,
+                            stream=stream) as s:
+                s.set_exec("kernels")
+                if every:
+                    s.set_demag(cell, vatom, every)
+                s.step(5)
+                s.sync()
+                k = 400
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.step(k)
+                e1.record(stream)
+                e1.synchronize()
+                s.sync()
+                res[every] = e0.elapsed_time(e1) / k
+        upd = max(res[1] - res[0], 1e-9)
+        rows[f"ellipsoid_{prec}"] = {"spins": lat.n, "macrocells": nc, "update_ms": upd,
+                                     "cell_pairs_per_s": nc * (nc - 1) / (upd * 1e-3),
+                                     "ms_per_step_no_demag": res[0], "ms_per_step_every_100": res[100],
+                                     "value": lat.n / (res[100] * 1e-3), "unit": "spin-steps/s (update every 100)"}
+    return rows
+
+
 def run_reference(args):
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
@@ -304,6 +344,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU legs")
+    ap.add_argument("--demag-only", action="store_true",
+                    help="run only the demagnetising-field leg on the paper's ellipsoid and print it")
     ap.add_argument("--mc-only", action="store_true",
                     help="run only a short Monte Carlo leg on the film (for profiling) and print it")
     ap.add_argument("--no-autotune", action="store_true", help="no autotuning in the batched and workload legs")
@@ -342,6 +384,10 @@ def main():
     T = pulse_T(total_steps + 16)
     stream = torch.cuda.Stream()
     res = {}
+    if args.demag_only:
+        if rank == 0:
+            print(json.dumps({"demag": demag_table(stream, rank)}))
+        return
     if args.mc_only:
         film = dict(spins=lat.n, **time_mc(lat, dict(T=300.0, seed=7 + rank), args.precision, args.steps, stream,
                                            warmup=args.warmup))
@@ -469,6 +515,7 @@ def main():
                           "block": tuned["block"], "tile": tuned["tile"]}
         out["workloads"] = workload_table(stream, rank)
         out["mc"] = mc_table(stream, rank)
+        out["demag"] = demag_table(stream, rank)
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(lat, T)
     if rank == 0:

@@ -49,6 +49,8 @@ __device__ __forceinline__ double sys_H(const SysDesc &sd, int c, double) { retu
 __device__ __forceinline__ double widen(float v) { return f2d_bits(v); }
 __device__ __forceinline__ double widen(double v) { return v; }
 template <typename R> __device__ __forceinline__ R narrow(double v);
+// double -> working type for any finite value (the hardware conversion; off the hot path)
+template <typename R> __device__ __forceinline__ R narrow_any(double v) { return (R)v; }
 template <> __device__ __forceinline__ float narrow<float>(double v) { return d2f_bits(v); }
 template <> __device__ __forceinline__ double narrow<double>(double v) { return v; }
 
@@ -663,36 +665,50 @@ __global__ void k_demag_moments(const KArgs<R> a, const DemagArgs d) {
 
 // Field of every macrocell p (Eq. demag): mu0/(4 pi) sum over the other cells q of the same
 // system of [3 (m_q . u) u - m_q] / r^3, u the unit vector from p to q, minus the self term
-// mu0/3 m_p / V_p; FP64, q in increasing order.  Also writes the working-type copy the step
-// kernels read.
+// mu0/3 m_p / V_p.  One warp per cell: lane-strided over q, the lane sums in FP64 combined by
+// a fixed butterfly.  The separations are formed in FP64; the rest of a pair's arithmetic runs
+// in the working type.  Also writes the working-type copy the step kernels read.
 template <typename R>
 __global__ void k_demag_field(const KArgs<R> a, const DemagArgs d) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= d.ncell) return;
-    const double px = d.pos[3 * p], py = d.pos[3 * p + 1], pz = d.pos[3 * p + 2];
-    double hx = 0.0, hy = 0.0, hz = 0.0;
-    for (int32_t q = d.cell_first[p]; q < d.cell_end[p]; ++q) {
-        if (q == p) continue;
-        const double rx = d.pos[3 * q] - px, ry = d.pos[3 * q + 1] - py, rz = d.pos[3 * q + 2] - pz;
-        const double rinv = rsqrt_pos(rx * rx + ry * ry + rz * rz);
-        const double ux = rx * rinv, uy = ry * rinv, uz = rz * rinv;
-        const double mx = d.m[3 * q], my = d.m[3 * q + 1], mz = d.m[3 * q + 2];
-        const double mu3 = 3.0 * (mx * ux + my * uy + mz * uz);
-        const double r3inv = rinv * rinv * rinv;
-        hx += (mu3 * ux - mx) * r3inv;
-        hy += (mu3 * uy - my) * r3inv;
-        hz += (mu3 * uz - mz) * r3inv;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p < d.ncell; p += nwarps) {
+        const double px = d.pos[3 * p], py = d.pos[3 * p + 1], pz = d.pos[3 * p + 2];
+        double hx = 0.0, hy = 0.0, hz = 0.0;
+        for (int32_t q = d.cell_first[p] + lane; q < d.cell_end[p]; q += 32) {
+            if (q == p) continue;
+            const R rx = narrow_any<R>(d.pos[3 * q] - px), ry = narrow_any<R>(d.pos[3 * q + 1] - py);
+            const R rz = narrow_any<R>(d.pos[3 * q + 2] - pz);
+            const R rinv = rsqrt_r(rx * rx + ry * ry + rz * rz);
+            const R ux = rx * rinv, uy = ry * rinv, uz = rz * rinv;
+            const R mx = narrow_any<R>(d.m[3 * q]), my = narrow_any<R>(d.m[3 * q + 1]);
+            const R mz = narrow_any<R>(d.m[3 * q + 2]);
+            const R mu3 = (R)3 * (mx * ux + my * uy + mz * uz);
+            const R r3inv = rinv * rinv * rinv;
+            hx += widen((mu3 * ux - mx) * r3inv);
+            hy += widen((mu3 * uy - my) * r3inv);
+            hz += widen((mu3 * uz - mz) * r3inv);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            hx += __shfl_xor_sync(0xffffffffu, hx, o);
+            hy += __shfl_xor_sync(0xffffffffu, hy, o);
+            hz += __shfl_xor_sync(0xffffffffu, hz, o);
+        }
+        if (lane == 0) {
+            const double c1 = kMu0 / (4.0 * 3.14159265358979323846), c2 = kMu0 / 3.0 / d.vol[p];
+            const double H0 = c1 * hx - c2 * d.m[3 * p], H1 = c1 * hy - c2 * d.m[3 * p + 1];
+            const double H2 = c1 * hz - c2 * d.m[3 * p + 2];
+            d.H[3 * p] = H0;
+            d.H[3 * p + 1] = H1;
+            d.H[3 * p + 2] = H2;
+            R *hx_ = const_cast<R *>(a.hdx), *hy_ = const_cast<R *>(a.hdy), *hz_ = const_cast<R *>(a.hdz);
+            hx_[p] = narrow_any<R>(H0);
+            hy_[p] = narrow_any<R>(H1);
+            hz_[p] = narrow_any<R>(H2);
+        }
     }
-    const double c1 = kMu0 / (4.0 * 3.14159265358979323846), c2 = kMu0 / 3.0 / d.vol[p];
-    const double H0 = c1 * hx - c2 * d.m[3 * p], H1 = c1 * hy - c2 * d.m[3 * p + 1];
-    const double H2 = c1 * hz - c2 * d.m[3 * p + 2];
-    d.H[3 * p] = H0;
-    d.H[3 * p + 1] = H1;
-    d.H[3 * p + 2] = H2;
-    R *hx_ = const_cast<R *>(a.hdx), *hy_ = const_cast<R *>(a.hdy), *hz_ = const_cast<R *>(a.hdz);
-    hx_[p] = narrow<R>(H0);
-    hy_[p] = narrow<R>(H1);
-    hz_[p] = narrow<R>(H2);
 }
 
 // ----------------------------------------------------------------------------------

@@ -105,7 +105,7 @@ cudaError_t launch_demag(const KArgs<R> &a, const DemagArgs &d, cudaStream_t s) 
     k_demag_moments<R><<<(int)(wblocks < 4096 ? wblocks : 4096), 256, 0, s>>>(a, d);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_demag_field<R><<<(int)((d.ncell + 127) / 128), 128, 0, s>>>(a, d);
+    k_demag_field<R><<<(int)(wblocks < 4096 ? wblocks : 4096), 256, 0, s>>>(a, d);
     return cudaGetLastError();
 }
 

@@ -192,6 +192,39 @@ def neel_tensors(pos: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, k_s: flo
     return K
 
 
+def subset(lat: SpinLattice, sites: np.ndarray) -> SpinLattice:
+    """The lattice induced on `sites` (sorted site ids): their per-site arrays and the bonds
+    between them, renumbered 0..len(sites)-1 in the given order."""
+    sites = np.asarray(sites, dtype=np.int64)
+    new_id = np.full(lat.n, -1, dtype=np.int64)
+    new_id[sites] = np.arange(sites.size)
+    rows = np.repeat(np.arange(lat.n), np.diff(lat.row_ptr))
+    keep = (new_id[rows] >= 0) & (new_id[lat.col] >= 0)
+    r, c, j = new_id[rows[keep]], new_id[lat.col[keep]], lat.J[keep]
+    order = np.lexsort((np.arange(r.size), r))  # rows in order, bonds in their CSR order
+    row_ptr = np.zeros(sites.size + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=sites.size), out=row_ptr[1:])
+    return SpinLattice(row_ptr, c[order].astype(np.int32), j[order], lat.mu_s[sites], lat.k_u[sites],
+                       lat.easy_axis[sites], None if lat.K_neel is None else lat.K_neel[sites],
+                       None if lat.pos is None else lat.pos[sites], meta=dict(lat.meta, subset=True))
+
+
+def prolate_ellipsoid(diameter=10e-9, height=20e-9, a=3.54e-10, mu_s=1.5 * MU_B, H_a=1.0, J=11.2e-21) -> SpinLattice:
+    """The demagnetising-field test particle of the paper's prolate-ellipsoid section: an fcc
+    crystal (lattice constant a, moment mu_s, uniaxial anisotropy field H_a = 2 k_u / mu_s along
+    the long axis z) cut to an ellipsoid `diameter` across and `height` long, with positions.
+    The paper gives no exchange constant for it; J is the fcc value used elsewhere here."""
+    nxy = int(np.ceil(diameter / a)) + 1
+    nz = int(np.ceil(height / a)) + 1
+    big = fcc(nxy, nxy, nz, periodic=(False, False, False), J=J, mu_s=mu_s, k_u=0.5 * mu_s * H_a, a=a,
+              with_pos=True)
+    c = big.pos - np.array([nxy, nxy, nz]) * a / 2
+    keep = (c[:, 0] / (diameter / 2)) ** 2 + (c[:, 1] / (diameter / 2)) ** 2 + (c[:, 2] / (height / 2)) ** 2 <= 1.0
+    lat = subset(big, np.nonzero(keep)[0])
+    lat.meta.update(kind="prolate_ellipsoid", atom_volume=a ** 3 / 4, a=a)
+    return lat
+
+
 def core_shell_sphere(diameter=20e-9, a=3.524e-10, r_core=8e-9, J_core=11.2e-21, J_shell=-5.0e-21,
                       J_int=2.0e-21, mu_s=1.72 * MU_B, k_s=5.0e-23, z_full=12) -> SpinLattice:
     """FCC sphere cut from a crystal: ferromagnetic core, antiferromagnetic shell.
