@@ -60,6 +60,8 @@ class _CSys(ctypes.Structure):
         ("demag_cell", ctypes.c_double),
         ("demag_vatom", ctypes.c_double),
         ("demag_every", ctypes.c_int64),
+        ("Jt", ctypes.c_void_p),
+        ("k_c", ctypes.c_void_p),
     ]
 
 
@@ -125,6 +127,8 @@ class OracleSystem:
     demag_cell: float = 0.0             # macrocell edge, m; 0: no demagnetising field
     demag_vatom: float = 0.0            # volume per atom, m^3
     demag_every: int = 1                # steps between demagnetising-field updates
+    J_tensor: np.ndarray | None = None  # (nnz, 3, 3) exchange tensors, or None (scalar J)
+    k_c: np.ndarray | float | None = None  # cubic anisotropy, J/atom
     _keep: list = field(default_factory=list, repr=False)
 
     def __post_init__(self):
@@ -142,6 +146,10 @@ class OracleSystem:
             self.ids = np.ascontiguousarray(self.ids, dtype=np.uint32).reshape(n)
         if self.pos is not None:
             self.pos = np.ascontiguousarray(self.pos, dtype=np.float64).reshape(n, 3)
+        if self.J_tensor is not None:
+            self.J_tensor = np.ascontiguousarray(self.J_tensor, dtype=np.float64).reshape(-1, 3, 3)
+        if self.k_c is not None:
+            self.k_c = np.ascontiguousarray(np.broadcast_to(np.asarray(self.k_c, dtype=np.float64), (n,)))
 
     @property
     def n(self) -> int:
@@ -169,6 +177,8 @@ class OracleSystem:
         c.demag_cell = float(self.demag_cell)
         c.demag_vatom = float(self.demag_vatom)
         c.demag_every = int(self.demag_every)
+        c.Jt = _ptr(self.J_tensor)
+        c.k_c = _ptr(self.k_c)
         return c
 
 

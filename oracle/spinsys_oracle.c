@@ -11,6 +11,8 @@
  *       H_exc = -sum_{i!=j} J_ij S_i.S_j, each bond counted once   (Eq. HJij, reading below)
  *       H_ani = -k_u sum_i (S_i.e)^2                              (uniaxial anisotropy eq.)
  *       H_app = -sum_i mu_s S_i.H_app                             (applied-field eq.)
+ *       H_ani also takes the cubic term (k_c/2) sum_i (Sx^4+Sy^4+Sz^4) (cubic-anisotropy eq.)
+ *       and H_exc the tensorial form of Eq. HJijSMS when tensors are given (T1, T2);
  *     plus an optional per-site Neel surface tensor term -S_i^T K_i S_i (not in the
  *     paper; a project extension for surface anisotropy, folded into the anisotropy
  *     energy).
@@ -83,6 +85,17 @@
  *       Heun passes of a step use the same field.
  *   D5  The recorded energies exclude the demagnetising energy.
  *
+ * Tensorial exchange (Eqs. HJijM, HJijSMS) and cubic anisotropy (the cubic-anisotropy
+ * equation), readings:
+ *   T1  A bond k of row i (i -> j = col[k]) may carry a 3x3 exchange tensor J_k, stored row
+ *       by row (Jxx Jxy Jxz Jyx Jyy Jyz Jzx Jzy Jzz).  The field on i is (1/mu_s,i) sum_k J_k S_j
+ *       and the energy -1/2 sum_i S_i . sum_k J_k S_j (each bond once, as R1); the field is
+ *       the gradient of that energy when the reverse bond carries the transpose.  A scalar J
+ *       is the tensor J times the identity.
+ *   T2  The cubic anisotropy energy is +(k_c/2)(Sx^4 + Sy^4 + Sz^4) per atom as printed (the
+ *       sign of k_c picks the easy axes) in the lattice frame, with the field
+ *       -(2 k_c/mu_s)(Sx^3, Sy^3, Sz^3); it is part of the anisotropy energy.
+ *
  * Layout: spins and vectors are array-of-structures, 3 doubles per site (x, y, z).
  * Neel tensors are 6 doubles per site in the order xx, yy, zz, xy, xz, yz.
  *
@@ -126,6 +139,8 @@ typedef struct {
     double demag_cell;        /* macrocell edge, m; <= 0: no demagnetising field        */
     double demag_vatom;       /* volume per atom V_uc / n_uc, m^3                       */
     int64_t demag_every;      /* steps between updates of the demagnetising field       */
+    const double *Jt;         /* [9 nnz] exchange tensors (T1) or NULL (scalar J)       */
+    const double *k_c;        /* [n] cubic anisotropy, J/atom (T2), or NULL             */
 } orc_system;
 
 static int g_threads = 1;
@@ -211,14 +226,29 @@ void orc_init_sphere(uint64_t seed, uint32_t sys, int64_t n, double *S) {
 /* hex receives the raw exchange sum sum_j J_ij S_j (J), H the field in tesla.         */
 /* Terms are added in the order: exchange, anisotropy, applied, Neel.                  */
 /* ---------------------------------------------------------------------------------- */
-static void orc_site_field(const orc_system *s, const double *S, int64_t i, double hex[3], double H[3]) {
+/* sum_k J_k S_j over row i: scalar J (R1) or exchange tensors (T1). */
+static void orc_exchange_sum(const orc_system *s, const double *S, int64_t i, double h[3]) {
     double sx = 0.0, sy = 0.0, sz = 0.0;
     for (int64_t k = s->row_ptr[i]; k < s->row_ptr[i + 1]; ++k) {
         int64_t j = s->col[k];
-        sx += s->J[k] * S[3 * j + 0];
-        sy += s->J[k] * S[3 * j + 1];
-        sz += s->J[k] * S[3 * j + 2];
+        if (s->Jt) {
+            const double *t = s->Jt + 9 * k;
+            sx += t[0] * S[3 * j + 0] + t[1] * S[3 * j + 1] + t[2] * S[3 * j + 2];
+            sy += t[3] * S[3 * j + 0] + t[4] * S[3 * j + 1] + t[5] * S[3 * j + 2];
+            sz += t[6] * S[3 * j + 0] + t[7] * S[3 * j + 1] + t[8] * S[3 * j + 2];
+        } else {
+            sx += s->J[k] * S[3 * j + 0];
+            sy += s->J[k] * S[3 * j + 1];
+            sz += s->J[k] * S[3 * j + 2];
+        }
     }
+    h[0] = sx; h[1] = sy; h[2] = sz;
+}
+
+static void orc_site_field(const orc_system *s, const double *S, int64_t i, double hex[3], double H[3]) {
+    double hs[3];
+    orc_exchange_sum(s, S, i, hs);
+    double sx = hs[0], sy = hs[1], sz = hs[2];
     hex[0] = sx; hex[1] = sy; hex[2] = sz;
     double mu = s->mu_s[i];
     /* exchange: -(1/mu) d/dS_i of -sum_{bonds} J S_i.S_j */
@@ -232,6 +262,14 @@ static void orc_site_field(const orc_system *s, const double *S, int64_t i, doub
     H[0] += a * e[0];
     H[1] += a * e[1];
     H[2] += a * e[2];
+    /* cubic anisotropy (T2): -(1/mu) d/dS of (k_c/2)(Sx^4+Sy^4+Sz^4) = -(2 k_c/mu) S^3 */
+    if (s->k_c) {
+        double c = -2.0 * s->k_c[i] / mu;
+        double x = S[3 * i + 0], y = S[3 * i + 1], z = S[3 * i + 2];
+        H[0] += c * x * x * x;
+        H[1] += c * y * y * y;
+        H[2] += c * z * z * z;
+    }
     /* applied field: -(1/mu) d/dS of -mu S.H_app = H_app */
     H[0] += s->H_app[0];
     H[1] += s->H_app[1];
@@ -274,6 +312,10 @@ void orc_moment_energy(const orc_system *s, const double *S, double out[8]) {
         const double *e = s->easy_axis + 3 * i;
         double sdote = Si[0] * e[0] + Si[1] * e[1] + Si[2] * e[2];
         double ea = -s->k_u[i] * sdote * sdote;
+        if (s->k_c) {
+            double x2 = Si[0] * Si[0], y2 = Si[1] * Si[1], z2 = Si[2] * Si[2];
+            ea += 0.5 * s->k_c[i] * (x2 * x2 + y2 * y2 + z2 * z2);
+        }
         if (s->K_neel) {
             const double *K = s->K_neel + 6 * i;
             double x = Si[0], y = Si[1], z = Si[2];
@@ -569,17 +611,17 @@ double orc_mc_sigma_g(double T) { return 2.0 / 25.0 * pow(ORC_KB * T / ORC_MUB, 
 /* Energy of site i's terms of the Hamiltonian with its spin set to X (M4):
  * -sum_j J_ij X.S_j - k_u (X.e)^2 - mu_s X.H_app - X^T K X. */
 static double orc_site_energy(const orc_system *s, const double *S, int64_t i, const double X[3]) {
-    double hx = 0.0, hy = 0.0, hz = 0.0;
-    for (int64_t k = s->row_ptr[i]; k < s->row_ptr[i + 1]; ++k) {
-        int64_t j = s->col[k];
-        hx += s->J[k] * S[3 * j + 0];
-        hy += s->J[k] * S[3 * j + 1];
-        hz += s->J[k] * S[3 * j + 2];
-    }
+    double h[3];
+    orc_exchange_sum(s, S, i, h);
+    double hx = h[0], hy = h[1], hz = h[2];
     double e = -(X[0] * hx + X[1] * hy + X[2] * hz);
     const double *a = s->easy_axis + 3 * i;
     double xe = X[0] * a[0] + X[1] * a[1] + X[2] * a[2];
     e += -s->k_u[i] * xe * xe;
+    if (s->k_c) {
+        double x2 = X[0] * X[0], y2 = X[1] * X[1], z2 = X[2] * X[2];
+        e += 0.5 * s->k_c[i] * (x2 * x2 + y2 * y2 + z2 * z2);
+    }
     e += -s->mu_s[i] * (X[0] * s->H_app[0] + X[1] * s->H_app[1] + X[2] * s->H_app[2]);
     if (s->K_neel) {
         const double *K = s->K_neel + 6 * i;

@@ -274,9 +274,66 @@ def pin_demag():
     return np.abs(r5 - r1).max() > 1e-9
 
 
+def _skew(d):
+    return np.array([[0.0, -d[2], d[1]], [d[2], 0.0, -d[0]], [-d[1], d[0], 0.0]])
+
+
+def pin_tensor_cubic():
+    """Tensorial exchange and cubic anisotropy: field = -(1/mu) grad E on a random 2x2x2
+    system (energy from the printed expressions), and the DM dimer's chirality."""
+    lat = L.simple_cubic(2, 2, 2, periodic=(False, False, False))
+    rng = np.random.default_rng(2)
+    rows = np.repeat(np.arange(lat.n), np.diff(lat.row_ptr))
+    where = {(int(i), int(j)): k for k, (i, j) in enumerate(zip(rows, lat.col))}
+    Jt = np.zeros((lat.nnz, 3, 3))
+    for k, (i, j) in enumerate(zip(rows, lat.col)):
+        if i < j:
+            B = rng.normal(size=(3, 3)) * 1e-21
+            A = 6e-21 * np.eye(3) + 0.5 * (B + B.T) + _skew(rng.normal(size=3) * 2e-21)
+            Jt[k], Jt[where[(int(j), int(i))]] = A, A.T
+    kc = rng.uniform(-2e-23, 2e-23, lat.n)
+    s = O.OracleSystem(lat.row_ptr, lat.col, np.zeros(lat.nnz), np.full(lat.n, MU), 0.0, (0, 0, 1), J_tensor=Jt,
+                       k_c=kc)
+
+    def energy(S):
+        e = sum(-S[i] @ Jt[k] @ S[j] for k, (i, j) in enumerate(zip(rows, lat.col)) if i < j)
+        return e + np.sum(0.5 * kc * (S ** 4).sum(1))
+
+    S = L.random_state(lat.n, 4)
+    Hf = O.fields(s, S)
+    if abs(O.moment_energy(s, S)[7] - energy(S)) > 1e-12 * abs(energy(S)):
+        return False
+    for i in range(lat.n):
+        for c in range(3):
+            Sp, Sm = S.copy(), S.copy()
+            Sp[i, c] += 1e-6
+            Sm[i, c] -= 1e-6
+            if abs(Hf[i, c] + (energy(Sp) - energy(Sm)) / 2e-6 / MU) > 1e-7 * max(1.0, np.abs(Hf[i]).max()):
+                return False
+    J, D = 5e-21, np.array([1.0, -2.0, 2.0]) * 1e-21
+    A = J * np.eye(3) + _skew(D)
+    d = O.OracleSystem(np.array([0, 1, 2]), np.array([1, 0], dtype=np.int32), np.zeros(2), np.full(2, 2 * MU / 1.5),
+                       0.0, (0, 0, 1), J_tensor=np.stack([A, A.T]), alpha=1.0, dt=1e-16, seed=4)
+    Sd, _ = O.heun_run(d, L.random_state(2, 6), 30000, 0.0)
+    return np.cross(Sd[0], Sd[1]) @ D / np.linalg.norm(D) < -0.45
+
+
+def pin_mc_cubic():
+    n, T, K = 2000, 40.0, 4.0
+    s = O.OracleSystem(np.zeros(n + 1, dtype=np.int64), np.zeros(0, np.int32), np.zeros(0), np.full(n, MU), 0.0,
+                       (0, 0, 1), k_c=K * KB * T, seed=12)
+    got = _mc_average(s, L.random_state(n, 1), T, 60, 15, 4, lambda S: (S ** 4).sum(1))
+    from scipy import integrate
+    f = lambda th, ph: np.sin(th) ** 4 * (np.cos(ph) ** 4 + np.sin(ph) ** 4) + np.cos(th) ** 4  # noqa: E731
+    w = lambda th, ph: np.exp(-0.5 * K * f(th, ph)) * np.sin(th)  # noqa: E731
+    Z = integrate.dblquad(w, 0, 2 * np.pi, 0, np.pi)[0]
+    ref = integrate.dblquad(lambda th, ph: f(th, ph) * w(th, ph), 0, 2 * np.pi, 0, np.pi)[0] / Z
+    return abs(got - ref) < 0.006
+
+
 PINS = [pin_field_gradient, pin_single_spin_analytic, pin_unit_length, pin_gaussians, pin_philox_against_torch,
         pin_boltzmann, pin_curie, pin_mc_boltzmann, pin_mc_langevin, pin_mc_dimer, pin_mc_moves, pin_mc_sigma,
-        pin_mc_zero_T, pin_colouring, pin_demag]
+        pin_mc_zero_T, pin_colouring, pin_demag, pin_tensor_cubic, pin_mc_cubic]
 
 if __name__ == "__main__":
     for p in PINS:

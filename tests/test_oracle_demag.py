@@ -72,7 +72,7 @@ def test_point_dipoles_axis_broadside_ratio_scaling_and_reciprocity():
     H, _ = O.demag_fields(s, S)
     m = S * (np.array([1.5, 2.5]) * MU_B)[:, None]
     self_ = -MU0 / 3 * m / vat
-    assert m[0] @ (H[0] - self_[0]) == pytest.approx(m[1] @ (H[1] - self_[1]), rel=1e-9)
+    assert m[0] @ (H[0] - self_[0]) == pytest.approx(m[1] @ (H[1] - self_[1]), rel=1e-9, abs=0)
 
 
 def test_uniform_sphere_has_demagnetising_factor_one_third():

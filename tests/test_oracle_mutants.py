@@ -64,6 +64,21 @@ MUTANTS = [
      "        double V = s->demag_cell * s->demag_cell * s->demag_cell;"),
     ("demagnetising field updated every step",
      "(k == 0 || (step0 + k) % (s->demag_every > 0 ? s->demag_every : 1) == 0)", "(1)"),
+    # tensorial exchange and cubic anisotropy
+    ("exchange tensors applied transposed",
+     "            sx += t[0] * S[3 * j + 0] + t[1] * S[3 * j + 1] + t[2] * S[3 * j + 2];\n"
+     "            sy += t[3] * S[3 * j + 0] + t[4] * S[3 * j + 1] + t[5] * S[3 * j + 2];\n"
+     "            sz += t[6] * S[3 * j + 0] + t[7] * S[3 * j + 1] + t[8] * S[3 * j + 2];",
+     "            sx += t[0] * S[3 * j + 0] + t[3] * S[3 * j + 1] + t[6] * S[3 * j + 2];\n"
+     "            sy += t[1] * S[3 * j + 0] + t[4] * S[3 * j + 1] + t[7] * S[3 * j + 2];\n"
+     "            sz += t[2] * S[3 * j + 0] + t[5] * S[3 * j + 1] + t[8] * S[3 * j + 2];"),
+    ("one tensor row transposed", "            sx += t[0] * S[3 * j + 0] + t[1] * S[3 * j + 1] + t[2] * S[3 * j + 2];",
+     "            sx += t[0] * S[3 * j + 0] + t[3] * S[3 * j + 1] + t[6] * S[3 * j + 2];"),
+    ("cubic field without factor 2", "        double c = -2.0 * s->k_c[i] / mu;", "        double c = -1.0 * s->k_c[i] / mu;"),
+    ("cubic energy with the wrong sign", "            ea += 0.5 * s->k_c[i] * (x2 * x2 + y2 * y2 + z2 * z2);",
+     "            ea -= 0.5 * s->k_c[i] * (x2 * x2 + y2 * y2 + z2 * z2);"),
+    ("cubic term missing from the Monte Carlo energy", "        e += 0.5 * s->k_c[i] * (x2 * x2 + y2 * y2 + z2 * z2);",
+     "        e += 0.0;"),
 ]
 
 
