@@ -103,6 +103,17 @@ typedef struct {
     uint32_t sys_id;          /* third Philox counter word of this system              */
     ss_precision precision;   /* must be equal for all systems of a batch              */
     uint32_t flags;           /* SS_FLAG_*                                             */
+    const double *J_tensor;   /* [9 nnz] exchange tensors (Eqs. HJijM, HJijSMS) or NULL:
+                                 bond k (row i -> j = col[k]) carries J_k row by row
+                                 (Jxx Jxy Jxz Jyx Jyy Jyz Jzx Jzy Jzz); the field on i is
+                                 (1/mu_s,i) sum_k J_k S_j, the energy -1/2 sum_i S_i.(...)
+                                 (each bond once); the reverse bond should carry the
+                                 transpose (checked with SS_FLAG_CHECK_SYMMETRY).  When
+                                 given, J may be NULL and is not used; systems of a batch
+                                 without tensors use J times the identity             */
+    const double *k_c;        /* [n] cubic anisotropy, J/atom, or NULL: energy
+                                 +(k_c/2)(Sx^4+Sy^4+Sz^4) per atom (cubic-anisotropy eq.),
+                                 field -(2 k_c/mu_s)(Sx^3, Sy^3, Sz^3)                 */
 } ss_params;
 
 /* Execution modes of llg_heun_step (spin_system_set_exec). */

@@ -61,6 +61,8 @@ class SSParams(ctypes.Structure):
         ("sys_id", ctypes.c_uint32),
         ("precision", ctypes.c_int),
         ("flags", ctypes.c_uint32),
+        ("J_tensor", ctypes.c_void_p),
+        ("k_c", ctypes.c_void_p),
     ]
 
 

@@ -50,7 +50,7 @@ struct HostSys {
 struct MatKey {
     int32_t sys;
     int32_t has_neel;
-    double v[11];  // mu, ku, e[3], K[6]
+    double v[12];  // mu, ku, e[3], K[6], k_c
     bool operator==(const MatKey &o) const {
         return sys == o.sys && has_neel == o.has_neel && std::memcmp(v, o.v, sizeof(v)) == 0;
     }
@@ -91,6 +91,8 @@ struct ss_system {
     int pre_slot = 1 << 30;
     int ahead_q = 6;       // eighths of each tile drawn ahead by the corrector
     bool J_uniform = false;  // every bond has the same J_ij / mu_s,i (J_value)
+    bool J_tensor = false;   // bonds carry exchange tensors (Jt)
+    void *Jt = nullptr;
     double J_value = 0.0;
     bool zero_T = true;    // some temperature in force could be zero (the corrector then
                            // skips drawing those spins ahead)
@@ -225,21 +227,29 @@ ss_status validate(const ss_params *p, int idx) {
             return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: row_ptr decreases at row %lld", idx, (long long)i);
     const int64_t nnz = p->row_ptr[n];
     if (nnz >= (int64_t(1) << 31)) return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: nnz >= 2^31", idx);
-    if (nnz > 0 && (!p->col || !p->J))
-        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: col and J are required when nnz > 0", idx);
+    if (nnz > 0 && (!p->col || (!p->J && !p->J_tensor)))
+        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: col and J (or J_tensor) are required when nnz > 0", idx);
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) {
             const int32_t j = p->col[k];
             if (j < 0 || j >= n)
                 return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: col[%lld] = %d out of range", idx, (long long)k, j);
             if (j == i) return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: self bond at row %lld", idx, (long long)i);
-            if (!std::isfinite(p->J[k]))
+            if (p->J_tensor) {
+                for (int c = 0; c < 9; ++c)
+                    if (!std::isfinite(p->J_tensor[9 * k + c]))
+                        return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: J_tensor[%lld] not finite", idx,
+                                    (long long)k);
+            } else if (!std::isfinite(p->J[k])) {
                 return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: J[%lld] not finite", idx, (long long)k);
+            }
         }
         if (!(p->mu_s[i] > 0.0) || !std::isfinite(p->mu_s[i]))
             return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: mu_s[%lld] must be finite and > 0", idx, (long long)i);
         if (!std::isfinite(p->k_u[i]))
             return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: k_u[%lld] not finite", idx, (long long)i);
+        if (p->k_c && !std::isfinite(p->k_c[i]))
+            return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: k_c[%lld] not finite", idx, (long long)i);
         if (p->easy_axis) {
             const double *e = p->easy_axis + 3 * i;
             if (!finite3(e) || e[0] * e[0] + e[1] * e[1] + e[2] * e[2] == 0.0)
@@ -266,7 +276,25 @@ ss_status validate(const ss_params *p, int idx) {
     if (!(p->T >= 0.0) || !std::isfinite(p->T))
         return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: T must be finite and >= 0", idx);
     if (!finite3(p->H_app)) return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: H_app not finite", idx);
-    if (p->flags & SS_FLAG_CHECK_SYMMETRY) {
+    if ((p->flags & SS_FLAG_CHECK_SYMMETRY) && p->J_tensor) {
+        // each bond's tensor must be the transpose of its reverse bond's
+        std::unordered_map<uint64_t, int64_t> where;
+        where.reserve((size_t)nnz);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k)
+                where[((uint64_t)i << 32) | (uint32_t)p->col[k]] = k;
+        for (const auto &b : where) {
+            const uint64_t rev = ((b.first & 0xffffffffull) << 32) | (b.first >> 32);
+            auto it = where.find(rev);
+            bool ok = it != where.end();
+            for (int r = 0; ok && r < 3; ++r)
+                for (int c = 0; ok && c < 3; ++c)
+                    ok = p->J_tensor[9 * b.second + 3 * r + c] == p->J_tensor[9 * it->second + 3 * c + r];
+            if (!ok)
+                return fail(nullptr, SS_ERR_INVALID_ARG, "system %d: exchange tensors not transposed at (%llu, %llu)",
+                            idx, (unsigned long long)(b.first >> 32), (unsigned long long)(b.first & 0xffffffffull));
+        }
+    } else if (p->flags & SS_FLAG_CHECK_SYMMETRY) {
         std::unordered_map<uint64_t, double> bonds;
         bonds.reserve((size_t)nnz);
         for (int64_t i = 0; i < n; ++i)
@@ -298,6 +326,8 @@ KArgs<R> make_args(const ss_system *h) {
     a.J = static_cast<const R *>(h->J);
     a.J_value = (R)h->J_value;
     a.J_uniform = h->J_uniform ? 1 : 0;
+    a.Jt = static_cast<const R *>(h->Jt);
+    a.J_tensor = h->J_tensor ? 1 : 0;
     a.demag = h->demag_on ? 1 : 0;
     a.mc_of = h->d_cell_of;
     a.hdx = static_cast<const R *>(h->d_hd[0]);
@@ -575,8 +605,11 @@ void fill_material(MatDesc<R> &m, const MatKey &k, const ss_params *p) {
     m.sig = (R)std::sqrt(2.0 * lam * kBoltzmann / (gamma * mu * p->dt));
     m.mu = (R)mu;
     m.ku = (R)ku;
+    m.kc = (R)k.v[11];
+    m.kcf = (R)(-2.0 * k.v[11] / mu);
     m.sys = k.sys;
     m.has_neel = k.has_neel;
+    m.has_cubic = k.v[11] != 0.0 ? 1 : 0;
 }
 
 template <typename R>
@@ -585,6 +618,9 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     // CSR with global indices
     std::vector<int32_t> rp((size_t)n + 1), col((size_t)std::max<int64_t>(nnz, 1));
     std::vector<R> J((size_t)std::max<int64_t>(nnz, 1));
+    bool tensor = false;
+    for (int s = 0; s < h->nsys; ++s) tensor = tensor || hs[s].p->J_tensor != nullptr;
+    std::vector<R> Jt(tensor ? 9 * (size_t)std::max<int64_t>(nnz, 1) : 0);
     std::vector<int32_t> mat((size_t)n);
     std::vector<MatDesc<R>> mats;
     std::unordered_map<MatKey, int32_t, MatKeyHash> mat_id;
@@ -596,7 +632,12 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
         for (int64_t i = 0; i < p->n; ++i)
             for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) {
                 col[noff + k] = (int32_t)(off + p->col[k]);
-                J[noff + k] = (R)(p->J[k] / p->mu_s[i]);
+                J[noff + k] = p->J ? (R)(p->J[k] / p->mu_s[i]) : (R)0;
+                if (tensor)  // tensors (or J times the identity) divided by the row's moment
+                    for (int c = 0; c < 9; ++c)
+                        Jt[9 * (size_t)(noff + k) + c] =
+                            p->J_tensor ? (R)(p->J_tensor[9 * k + c] / p->mu_s[i])
+                                        : (c % 4 == 0 ? (R)(p->J[k] / p->mu_s[i]) : (R)0);
             }
         MatKey last{};
         int32_t last_id = -1;
@@ -622,6 +663,7 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
                 }
                 key.has_neel = any ? 1 : 0;
             }
+            key.v[11] = p->k_c ? p->k_c[i] : 0.0;
             int32_t id;
             if (last_id >= 0 && key == last) {
                 id = last_id;
@@ -645,7 +687,12 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     rp[n] = (int32_t)nnz;
     h->nmat = (int32_t)mats.size();
     // Homogeneous exchange (one J_ij / mu_s,i for every bond): the kernels skip the J loads.
-    h->J_uniform = nnz > 0;
+    h->J_tensor = tensor;
+    if (tensor) {
+        SS_CUDA(h, dalloc(h, &h->Jt, Jt.size() * sizeof(R)));
+        SS_CUDA(h, cudaMemcpyAsync(h->Jt, Jt.data(), Jt.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
+    }
+    h->J_uniform = nnz > 0 && !tensor;
     for (int64_t k = 1; k < nnz && h->J_uniform; ++k) h->J_uniform = std::memcmp(&J[k], &J[0], sizeof(R)) == 0;
     h->J_value = nnz > 0 ? (double)J[0] : 0.0;
     const size_t rs = sizeof(R);

@@ -55,8 +55,12 @@ struct MatDesc {
     R mu;         // mu_s
     R ku;         // k_u
     R K[6];       // Neel tensor (energy)
+    R kc;         // cubic anisotropy k_c (energy (k_c/2) sum S^4)
+    R kcf;        // -2 k_c / mu_s (field factor of S^3)
     int32_t sys;
     int32_t has_neel;
+    int32_t has_cubic;
+    int32_t pad;
 };
 
 // A contiguous range of spins of one system, processed by one block per pass.
@@ -75,6 +79,8 @@ struct KArgs {
     const R *J;               // [nnz] J_ij / mu_s,i (the exchange field per unit spin, T)
     R J_value;                // the common value when every entry of J is the same
     int J_uniform;            // 1: J is not read, every bond has J_value
+    const R *Jt;              // [9 nnz] exchange tensors / mu_s,i, row by row (J_tensor = 1)
+    int J_tensor;             // 1: the exchange sum uses Jt instead of J
     const int32_t *mc_of;     // [n] macrocell of each spin (demagnetising field)
     const R *hdx, *hdy, *hdz; // [ncell] demagnetising field of each macrocell (T)
     int demag;                // 1: add the macrocell field to every spin's field

@@ -81,6 +81,20 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
     const int32_t b = __ldg(a.row_ptr + i);
     const int32_t e = __ldg(a.row_ptr + i + 1);
     R x = sys_H(sd, 0, R()), y = sys_H(sd, 1, R()), z = sys_H(sd, 2, R());
+    if (a.J_tensor) {  // Eq. HJijSMS: the tensor of bond k applied to S_j
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t j = __ldg(a.col + k);
+            const R *t = a.Jt + 9 * (int64_t)k;
+            const R sx = ld<Coherent>(X + j), sy = ld<Coherent>(Y + j), sz = ld<Coherent>(Z + j);
+            x = fma(__ldg(t + 0), sx, fma(__ldg(t + 1), sy, fma(__ldg(t + 2), sz, x)));
+            y = fma(__ldg(t + 3), sx, fma(__ldg(t + 4), sy, fma(__ldg(t + 5), sz, y)));
+            z = fma(__ldg(t + 6), sx, fma(__ldg(t + 7), sy, fma(__ldg(t + 8), sz, z)));
+        }
+        e0 = x;
+        e1 = y;
+        e2 = z;
+        return;
+    }
     for (int32_t k = b; k < e; ++k) {
         const int32_t j = __ldg(a.col + k);
         const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + k);
@@ -103,6 +117,11 @@ __device__ __forceinline__ R det_field(const MatDesc<R> &m, R s0, R s1, R s2, R 
     H0 = fma(an, m.e[0], e0);
     H1 = fma(an, m.e[1], e1);
     H2 = fma(an, m.e[2], e2);
+    if (m.has_cubic) {  // -(2 k_c / mu_s) S^3
+        H0 = fma(m.kcf * s0 * s0, s0, H0);
+        H1 = fma(m.kcf * s1 * s1, s1, H1);
+        H2 = fma(m.kcf * s2 * s2, s2, H2);
+    }
     if (m.has_neel) {
         H0 += m.kf[0] * s0 + m.kf[3] * s1 + m.kf[4] * s2;
         H1 += m.kf[3] * s0 + m.kf[1] * s1 + m.kf[5] * s2;
@@ -148,6 +167,10 @@ __device__ __forceinline__ void spin_terms(const MatDesc<R> &m, R s0, R s1, R s2
     v[2] = widen(mu * s2);
     v[3] = widen((R)-0.5 * mu * (s0 * e0 + s1 * e1 + s2 * e2));
     R ea = -m.ku * sde * sde;
+    if (m.has_cubic) {
+        const R x2 = s0 * s0, y2 = s1 * s1, z2 = s2 * s2;
+        ea += (R)0.5 * m.kc * (x2 * x2 + y2 * y2 + z2 * z2);
+    }
     if (m.has_neel) {
         ea -= m.K[0] * s0 * s0 + m.K[1] * s1 * s1 + m.K[2] * s2 * s2
             + (R)2 * (m.K[3] * s0 * s1 + m.K[4] * s0 * s2 + m.K[5] * s1 * s2);
@@ -789,6 +812,10 @@ __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs
         const R de = d0 * mt.e[0] + d1 * mt.e[1] + d2 * mt.e[2];
         const R pe = p0 * mt.e[0] + p1 * mt.e[1] + p2 * mt.e[2];
         R dE = -mt.mu * (d0 * h0 + d1 * h1 + d2 * h2) - mt.ku * (de * pe);
+        if (mt.has_cubic) {  // (k_c/2) sum (n^4 - s^4), n^4 - s^4 = (n - s)(n + s)(n^2 + s^2)
+            dE += (R)0.5 * mt.kc * (d0 * p0 * (n0 * n0 + s0 * s0) + d1 * p1 * (n1 * n1 + s1 * s1)
+                                    + d2 * p2 * (n2 * n2 + s2 * s2));
+        }
         if (mt.has_neel) {
             const R k0 = mt.K[0] * p0 + mt.K[3] * p1 + mt.K[4] * p2;
             const R k1 = mt.K[3] * p0 + mt.K[1] * p1 + mt.K[5] * p2;

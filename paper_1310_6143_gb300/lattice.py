@@ -40,6 +40,8 @@ class SpinLattice:
     K_neel: np.ndarray | None = None   # float64 [n, 6] (xx, yy, zz, xy, xz, yz) or None
     pos: np.ndarray | None = None      # float64 [n, 3], m
     meta: dict = field(default_factory=dict)
+    J_tensor: np.ndarray | None = None  # float64 [nnz, 3, 3] exchange tensors (J then unused), or None
+    k_c: np.ndarray | None = None       # float64 [n] cubic anisotropy, J/atom, or None
 
     @property
     def n(self) -> int:
@@ -206,7 +208,9 @@ def subset(lat: SpinLattice, sites: np.ndarray) -> SpinLattice:
     np.cumsum(np.bincount(r, minlength=sites.size), out=row_ptr[1:])
     return SpinLattice(row_ptr, c[order].astype(np.int32), j[order], lat.mu_s[sites], lat.k_u[sites],
                        lat.easy_axis[sites], None if lat.K_neel is None else lat.K_neel[sites],
-                       None if lat.pos is None else lat.pos[sites], meta=dict(lat.meta, subset=True))
+                       None if lat.pos is None else lat.pos[sites], meta=dict(lat.meta, subset=True),
+                       J_tensor=None if lat.J_tensor is None else lat.J_tensor[keep][order],
+                       k_c=None if lat.k_c is None else lat.k_c[sites])
 
 
 def prolate_ellipsoid(diameter=10e-9, height=20e-9, a=3.54e-10, mu_s=1.5 * MU_B, H_a=1.0, J=11.2e-21) -> SpinLattice:

@@ -78,6 +78,8 @@ class SpinSystem:
                 "K_neel": None if lat.K_neel is None else np.ascontiguousarray(lat.K_neel, dtype=np.float64),
                 "pos": None if lat.pos is None else np.ascontiguousarray(lat.pos, dtype=np.float64),
                 "S0": None if S0s[s] is None else np.ascontiguousarray(S0s[s], dtype=np.float64),
+                "J_tensor": None if lat.J_tensor is None else np.ascontiguousarray(lat.J_tensor, dtype=np.float64),
+                "k_c": None if lat.k_c is None else np.ascontiguousarray(lat.k_c, dtype=np.float64),
             }
             keep.append(arrs)
             p = params[s]
