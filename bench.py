@@ -230,6 +230,13 @@ def workload_table(stream, rank):
     rows["sc10_x1024_sweep_fp32"] = dict(spins=sc.n * 1024, systems=1024, **time_workload(
         sweep, dict(alpha=0.1, dt=1e-16, T=[float(t) for t in range(1024)], seed=1 + rank,
                     sys_id=list(range(1024))), "fp32", 500, stream))
+    # tensorial exchange: the fcc crystal with an interface-type DM term (|D| = 0.1 J) and
+    # cubic anisotropy, 9 exchange values per bond
+    dm = L.with_dm(L.fcc(64, 64, 64, J=11.2e-21, k_u=6.69e-24, with_pos=True), D=1.12e-21)
+    dm.k_c = np.full(dm.n, 5e-24)
+    kw = dict(alpha=0.05, dt=1e-16, T=300.0, seed=4 + rank, init_random=True)
+    for prec, k in (("fp32", 200), ("fp64", 50)):
+        rows[f"fcc64_dm_cubic_{prec}"] = dict(spins=dm.n, **time_workload(dm, kw, prec, k, stream))
     cs = L.core_shell_sphere()
     kw = dict(alpha=0.1, dt=1e-16, T=10.0, H=(1.0, 0.0, 0.0), seed=3 + rank)
     for prec, k in (("fp32", 400), ("fp64", 100)):

@@ -91,8 +91,9 @@ struct ss_system {
     int pre_slot = 1 << 30;
     int ahead_q = 6;       // eighths of each tile drawn ahead by the corrector
     bool J_uniform = false;  // every bond has the same J_ij / mu_s,i (J_value)
-    bool J_tensor = false;   // bonds carry exchange tensors (Jt)
+    bool J_tensor = false;   // bonds carry exchange tensors (Jt dictionary, Jtidx per bond)
     void *Jt = nullptr;
+    int32_t *Jtidx = nullptr;
     double J_value = 0.0;
     bool zero_T = true;    // some temperature in force could be zero (the corrector then
                            // skips drawing those spins ahead)
@@ -327,6 +328,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.J_value = (R)h->J_value;
     a.J_uniform = h->J_uniform ? 1 : 0;
     a.Jt = static_cast<const R *>(h->Jt);
+    a.Jtidx = h->Jtidx;
     a.J_tensor = h->J_tensor ? 1 : 0;
     a.demag = h->demag_on ? 1 : 0;
     a.mc_of = h->d_cell_of;
@@ -620,7 +622,9 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     std::vector<R> J((size_t)std::max<int64_t>(nnz, 1));
     bool tensor = false;
     for (int s = 0; s < h->nsys; ++s) tensor = tensor || hs[s].p->J_tensor != nullptr;
-    std::vector<R> Jt(tensor ? 9 * (size_t)std::max<int64_t>(nnz, 1) : 0);
+    std::vector<R> Jt;                                   // distinct tensors, 9 values each
+    std::vector<int32_t> Jtidx(tensor ? (size_t)std::max<int64_t>(nnz, 1) : 0);
+    std::unordered_map<std::string, int32_t> Jt_id;      // tensor bits -> dictionary entry
     std::vector<int32_t> mat((size_t)n);
     std::vector<MatDesc<R>> mats;
     std::unordered_map<MatKey, int32_t, MatKeyHash> mat_id;
@@ -633,11 +637,24 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
             for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) {
                 col[noff + k] = (int32_t)(off + p->col[k]);
                 J[noff + k] = p->J ? (R)(p->J[k] / p->mu_s[i]) : (R)0;
-                if (tensor)  // tensors (or J times the identity) divided by the row's moment
+                if (tensor) {  // tensors (or J times the identity) divided by the row's moment,
+                               // stored once per distinct value
+                    R t[9];
                     for (int c = 0; c < 9; ++c)
-                        Jt[9 * (size_t)(noff + k) + c] =
-                            p->J_tensor ? (R)(p->J_tensor[9 * k + c] / p->mu_s[i])
-                                        : (c % 4 == 0 ? (R)(p->J[k] / p->mu_s[i]) : (R)0);
+                        t[c] = p->J_tensor ? (R)(p->J_tensor[9 * k + c] / p->mu_s[i])
+                                           : (c % 4 == 0 ? (R)(p->J[k] / p->mu_s[i]) : (R)0);
+                    const std::string key(reinterpret_cast<const char *>(t), sizeof(t));
+                    auto it = Jt_id.find(key);
+                    int32_t id;
+                    if (it == Jt_id.end()) {
+                        id = (int32_t)(Jt.size() / 9);
+                        Jt_id.emplace(key, id);
+                        Jt.insert(Jt.end(), t, t + 9);
+                    } else {
+                        id = it->second;
+                    }
+                    Jtidx[(size_t)(noff + k)] = id;
+                }
             }
         MatKey last{};
         int32_t last_id = -1;
@@ -689,8 +706,13 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     // Homogeneous exchange (one J_ij / mu_s,i for every bond): the kernels skip the J loads.
     h->J_tensor = tensor;
     if (tensor) {
+        if (Jt.empty()) Jt.assign(9, (R)0);
         SS_CUDA(h, dalloc(h, &h->Jt, Jt.size() * sizeof(R)));
         SS_CUDA(h, cudaMemcpyAsync(h->Jt, Jt.data(), Jt.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
+        SS_CUDA(h, dalloc(h, (void **)&h->Jtidx, Jtidx.size() * sizeof(int32_t)));
+        SS_CUDA(h, cudaMemcpyAsync(h->Jtidx, Jtidx.data(), Jtidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   h->stream));
+        SS_CUDA(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
     }
     h->J_uniform = nnz > 0 && !tensor;
     for (int64_t k = 1; k < nnz && h->J_uniform; ++k) h->J_uniform = std::memcmp(&J[k], &J[0], sizeof(R)) == 0;

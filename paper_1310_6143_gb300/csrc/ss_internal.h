@@ -79,8 +79,9 @@ struct KArgs {
     const R *J;               // [nnz] J_ij / mu_s,i (the exchange field per unit spin, T)
     R J_value;                // the common value when every entry of J is the same
     int J_uniform;            // 1: J is not read, every bond has J_value
-    const R *Jt;              // [9 nnz] exchange tensors / mu_s,i, row by row (J_tensor = 1)
-    int J_tensor;             // 1: the exchange sum uses Jt instead of J
+    const R *Jt;              // [9 ndict] distinct exchange tensors / mu_s,i, row by row
+    const int32_t *Jtidx;     // [nnz] tensor of each bond (J_tensor = 1)
+    int J_tensor;             // 1: the exchange sum uses Jt[Jtidx[k]] instead of J
     const int32_t *mc_of;     // [n] macrocell of each spin (demagnetising field)
     const R *hdx, *hdy, *hdz; // [ncell] demagnetising field of each macrocell (T)
     int demag;                // 1: add the macrocell field to every spin's field

@@ -84,7 +84,7 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
     if (a.J_tensor) {  // Eq. HJijSMS: the tensor of bond k applied to S_j
         for (int32_t k = b; k < e; ++k) {
             const int32_t j = __ldg(a.col + k);
-            const R *t = a.Jt + 9 * (int64_t)k;
+            const R *t = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + k);
             const R sx = ld<Coherent>(X + j), sy = ld<Coherent>(Y + j), sz = ld<Coherent>(Z + j);
             x = fma(__ldg(t + 0), sx, fma(__ldg(t + 1), sy, fma(__ldg(t + 2), sz, x)));
             y = fma(__ldg(t + 3), sx, fma(__ldg(t + 4), sy, fma(__ldg(t + 5), sz, y)));

@@ -164,7 +164,9 @@ def fcc(nx: int, ny: int, nz: int, periodic=(True, True, True), J=11.2e-21, mu_s
     mu, ku, ax_ = _homogeneous(n, mu_s, k_u, easy_axis)
     pos = X.astype(np.float64) * (a / 2) if with_pos else None
     return SpinLattice(row_ptr, col, Jv, mu, ku, ax_, None, pos,
-                       meta={"kind": "fcc", "cells": (nx, ny, nz), "periodic": tuple(periodic), "a": a})
+                       meta={"kind": "fcc", "cells": (nx, ny, nz), "periodic": tuple(periodic), "a": a,
+                             "box": tuple(np.array([nx, ny, nz], dtype=np.float64) * a * np.array(periodic)
+                                          + np.array([0 if p else np.inf for p in periodic]))})
 
 
 def film(nx=1024, ny=1024, nz=16, J=6.0e-21, mu_s=1.5 * MU_B, k_u=1.0e-24) -> SpinLattice:
@@ -226,6 +228,34 @@ def prolate_ellipsoid(diameter=10e-9, height=20e-9, a=3.54e-10, mu_s=1.5 * MU_B,
     keep = (c[:, 0] / (diameter / 2)) ** 2 + (c[:, 1] / (diameter / 2)) ** 2 + (c[:, 2] / (height / 2)) ** 2 <= 1.0
     lat = subset(big, np.nonzero(keep)[0])
     lat.meta.update(kind="prolate_ellipsoid", atom_volume=a ** 3 / 4, a=a)
+    return lat
+
+
+def with_dm(lat: SpinLattice, D: float, normal=(0.0, 0.0, 1.0)) -> SpinLattice:
+    """Exchange tensors J_ij I + [D_ij]x with an interface-type Dzyaloshinskii-Moriya vector
+    D_ij = D (r_ij x n) / |r_ij| (r_ij from site i to its neighbour j, n the interface normal),
+    so that the energy gains D_ij . (S_i x S_j) (Eqs. HJijM, HJijSMS); the reverse bond carries
+    the transpose (D_ji = -D_ij).  Needs positions; periodic neighbours take the shortest image
+    of the lattice box (meta "box")."""
+    if lat.pos is None:
+        raise ValueError("with_dm needs positions")
+    rows = np.repeat(np.arange(lat.n), np.diff(lat.row_ptr))
+    r = lat.pos[lat.col] - lat.pos[rows]
+    box = lat.meta.get("box")
+    if box is not None:
+        box = np.asarray(box, dtype=np.float64)
+        r -= box * np.round(r / box)
+    u = r / np.linalg.norm(r, axis=1, keepdims=True)
+    Dv = D * np.cross(u, np.asarray(normal, dtype=np.float64))
+    Jt = lat.J[:, None, None] * np.eye(3)[None].repeat(lat.nnz, 0)
+    # [d]x with [d]x v = d x v, so that S_i . [d]x S_j = d . (S_j x S_i) and -S_i.[d]x S_j = d . (S_i x S_j)
+    Jt[:, 0, 1] -= Dv[:, 2]
+    Jt[:, 0, 2] += Dv[:, 1]
+    Jt[:, 1, 0] += Dv[:, 2]
+    Jt[:, 1, 2] -= Dv[:, 0]
+    Jt[:, 2, 0] -= Dv[:, 1]
+    Jt[:, 2, 1] += Dv[:, 0]
+    lat.J_tensor = Jt
     return lat
 
 
