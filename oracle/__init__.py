@@ -17,6 +17,7 @@ from .oracle import (  # noqa: F401
     fields,
     moment_energy,
     heun_run,
+    midpoint_run,
     set_threads,
     max_threads,
     colour_greedy,

@@ -96,6 +96,17 @@
  *       sign of k_c picks the easy axes) in the lattice frame, with the field
  *       -(2 k_c/mu_s)(Sx^3, Sy^3, Sz^3); it is part of the anisotropy energy.
  *
+ * Midpoint integrator (the midpoint rule the paper's time-integration section cites,
+ * d'Aquino et al. 2005), readings:
+ *   I1  S_{n+1} = S_n + dt f(m), m = (S_n + S_{n+1})/2, f the right-hand side of Eq. LLG with
+ *       the deterministic field of m and the thermal field of R4 (drawn once per step from
+ *       the same Philox counters, held over the step).  f(m) is perpendicular to m, so the
+ *       rule keeps |S| without renormalisation.
+ *   I2  The implicit equation is solved by K fixed-point iterations from the Euler predictor
+ *       S^(0) = S_n + dt f(S_n): S^(k+1) = S_n + dt f((S_n + S^(k))/2), k = 0 .. K-1, and
+ *       S_{n+1} = S^(K); nothing is renormalised.
+ *   I3  The record holds the state at the start of each step (R7).
+ *
  * Layout: spins and vectors are array-of-structures, 3 doubles per site (x, y, z).
  * Neel tensors are 6 doubles per site in the order xx, yy, zz, xy, xz, yz.
  *
@@ -447,6 +458,22 @@ int64_t orc_demag_fields(const orc_system *s, const double *S, double *Hd, doubl
     return nc;
 }
 
+/* Thermal field of every site for step `step` at temperature Tn (the thermal-field
+ * equation; readings R3, R4, R6): sqrt(2 lambda kB T / (gamma mu_s dt)) times the Gaussian
+ * triple of the site. */
+static void orc_thermal_field(const orc_system *s, uint32_t step, double Tn, double gamma, double lambda,
+                              double *Hth) {
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+    for (int64_t i = 0; i < s->n; ++i) {
+        double g[3];
+        orc_thermal_gaussians(s->seed, s->sys, s->ids ? s->ids[i] : (uint32_t)i, step, g);
+        double sigma = sqrt(2.0 * lambda * ORC_KB * Tn / (gamma * s->mu_s[i] * s->dt));
+        Hth[3 * i + 0] = sigma * g[0];
+        Hth[3 * i + 1] = sigma * g[1];
+        Hth[3 * i + 2] = sigma * g[2];
+    }
+}
+
 /*
  * Advance nsteps Heun steps from step index step0.  S [3n] is updated in place.
  * T[k] is the temperature of step step0+k (K).  If rec is not NULL it receives
@@ -478,15 +505,7 @@ int orc_heun_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, 
             }
         }
         /* thermal field, drawn once per step (R4) */
-#pragma omp parallel for schedule(static) num_threads(g_threads)
-        for (int64_t i = 0; i < n; ++i) {
-            double g[3];
-            orc_thermal_gaussians(s->seed, s->sys, s->ids ? s->ids[i] : (uint32_t)i, step, g);
-            double sigma = sqrt(2.0 * lambda * ORC_KB * Tn / (gamma * s->mu_s[i] * s->dt));
-            Hth[3 * i + 0] = sigma * g[0];
-            Hth[3 * i + 1] = sigma * g[1];
-            Hth[3 * i + 2] = sigma * g[2];
-        }
+        orc_thermal_field(s, step, Tn, gamma, lambda, Hth);
         /* predictor on every spin */
 #pragma omp parallel for schedule(static) num_threads(g_threads)
         for (int64_t i = 0; i < n; ++i) {
@@ -536,6 +555,58 @@ int orc_heun_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, 
         }
     }
     free(Hth); free(dS); free(Sp); free(Hd);
+    return 0;
+}
+
+/*
+ * Advance nsteps midpoint steps (I1-I3) with K = iters fixed-point iterations each, from
+ * step index step0; arguments as orc_heun_run.  Returns 0, or -1 on allocation failure.
+ */
+int orc_midpoint_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, const double *T, int iters,
+                     double *rec) {
+    int64_t n = s->n;
+    size_t sz = sizeof(double) * 3 * (size_t)(n > 0 ? n : 1);
+    double *Hth = (double *)malloc(sz), *X = (double *)malloc(sz), *Y = (double *)malloc(sz);
+    double *M = (double *)malloc(sz);
+    if (!Hth || !X || !Y || !M) {
+        free(Hth); free(X); free(Y); free(M);
+        return -1;
+    }
+    double gamma = s->gamma > 0.0 ? s->gamma : ORC_GAMMA;
+    double lambda = s->alpha;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        uint32_t step = (uint32_t)(step0 + k);
+        double Tn = T[k];
+        if (rec) orc_moment_energy(s, S, rec + 8 * k);
+        orc_thermal_field(s, step, Tn, gamma, lambda, Hth);
+        /* Euler predictor S^(0) = S_n + dt f(S_n) (I2), into X */
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+        for (int64_t i = 0; i < n; ++i) {
+            double hex[3], H[3], d[3];
+            orc_site_field(s, S, i, hex, H);
+            for (int c = 0; c < 3; ++c) H[c] += Hth[3 * i + c];
+            orc_llg(gamma, lambda, S + 3 * i, H, d);
+            for (int c = 0; c < 3; ++c) X[3 * i + c] = S[3 * i + c] + d[c] * s->dt;
+        }
+        /* fixed-point iterations on the midpoint m = (S_n + S^(k))/2 */
+        for (int it = 0; it < iters; ++it) {
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+            for (int64_t i = 0; i < 3 * n; ++i) M[i] = 0.5 * (S[i] + X[i]);
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+            for (int64_t i = 0; i < n; ++i) {
+                double hex[3], H[3], d[3];
+                orc_site_field(s, M, i, hex, H);
+                for (int c = 0; c < 3; ++c) H[c] += Hth[3 * i + c];
+                orc_llg(gamma, lambda, M + 3 * i, H, d);
+                for (int c = 0; c < 3; ++c) Y[3 * i + c] = S[3 * i + c] + d[c] * s->dt;
+            }
+            double *t = X;
+            X = Y;
+            Y = t;
+        }
+        memcpy(S, X, sz);
+    }
+    free(Hth); free(X); free(Y); free(M);
     return 0;
 }
 

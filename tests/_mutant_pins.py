@@ -331,9 +331,27 @@ def pin_mc_cubic():
     return abs(got - ref) < 0.006
 
 
+def pin_midpoint():
+    """Midpoint rule: undamped precession is the Cayley rotation (2 atan(w dt/2) a step), and
+    the length error falls with the fixed-point iterations."""
+    H = 10.0
+    dt = 0.1 / (GAMMA * H)
+    s = O.OracleSystem(np.zeros(2, dtype=np.int64), np.zeros(0, np.int32), np.zeros(0), [MU], 0.0, (0, 0, 1),
+                       alpha=0.0, dt=dt, H_app=(0.0, 0.0, H))
+    S, _ = O.midpoint_run(s, np.array([[0.6, 0.0, 0.8]]), 100, 0.0, iters=40)
+    d = np.angle(np.exp(1j * (np.arctan2(S[0, 1], S[0, 0]) - 200 * np.arctan(0.05))))
+    if abs(d) > 1e-10:
+        return False
+    lat = L.simple_cubic(4, 4, 4, J=6e-21, k_u=1e-23)
+    sl = O.OracleSystem(lat.row_ptr, lat.col, lat.J, lat.mu_s, lat.k_u, lat.easy_axis, alpha=0.1, dt=1e-16, seed=2)
+    S0 = L.random_state(lat.n, 1)
+    e = [np.abs(np.linalg.norm(O.midpoint_run(sl, S0, 30, 300.0, iters=K)[0], axis=1) - 1).max() for K in (2, 8)]
+    return e[1] < 1e-11 and e[0] > 1e3 * e[1]
+
+
 PINS = [pin_field_gradient, pin_single_spin_analytic, pin_unit_length, pin_gaussians, pin_philox_against_torch,
         pin_boltzmann, pin_curie, pin_mc_boltzmann, pin_mc_langevin, pin_mc_dimer, pin_mc_moves, pin_mc_sigma,
-        pin_mc_zero_T, pin_colouring, pin_demag, pin_tensor_cubic, pin_mc_cubic]
+        pin_mc_zero_T, pin_colouring, pin_demag, pin_tensor_cubic, pin_mc_cubic, pin_midpoint]
 
 if __name__ == "__main__":
     for p in PINS:

@@ -79,6 +79,9 @@ MUTANTS = [
      "            ea -= 0.5 * s->k_c[i] * (x2 * x2 + y2 * y2 + z2 * z2);"),
     ("cubic term missing from the Monte Carlo energy", "        e += 0.5 * s->k_c[i] * (x2 * x2 + y2 * y2 + z2 * z2);",
      "        e += 0.0;"),
+    # midpoint integrator
+    ("midpoint iteration on S^(k) instead of the midpoint", "M[i] = 0.5 * (S[i] + X[i]);", "M[i] = X[i];"),
+    ("midpoint iterations skipped", "        for (int it = 0; it < iters; ++it) {", "        for (int it = 0; it < 0; ++it) {"),
 ]
 
 
