@@ -320,6 +320,36 @@ def demag_table(stream, rank):
     return rows
 
 
+def midpoint_table(stream, rank, steps=40):
+    """The midpoint rule (fixed-point iterations from the Euler predictor) against Heun on the
+    film at 300 K: spin-steps/s for K = 3 and 4 iterations per step."""
+    import torch
+    from paper_1310_6143_gb300.system import SpinSystem
+
+    from paper_1310_6143_gb300 import lattice as L
+
+    film = L.film(1024, 1024, 16)
+    rows = {}
+    for prec in ("fp32", "fp64"):
+        for K in (3, 4):
+            with SpinSystem(film, alpha=0.02, dt=1e-16, T=300.0, seed=5 + rank, precision=prec,
+                            stream=stream) as s:
+                s.midpoint_step(3, iterations=K)
+                s.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.midpoint_step(steps, iterations=K)
+                e1.record(stream)
+                e1.synchronize()
+                s.sync()
+                ms = e0.elapsed_time(e1) / steps
+                dev = float(np.abs(np.linalg.norm(s.spins(), axis=1) - 1).max())
+            rows[f"film_{prec}_K{K}"] = {"spins": film.n, "iterations": K, "ms_per_step": ms,
+                                         "value": film.n / (ms * 1e-3), "unit": "spin-steps/s",
+                                         "max_length_error": dev}
+    return rows
+
+
 def run_reference(args):
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
@@ -353,6 +383,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU legs")
     ap.add_argument("--demag-only", action="store_true",
                     help="run only the demagnetising-field leg on the paper's ellipsoid and print it")
+    ap.add_argument("--midpoint-only", action="store_true",
+                    help="run only the midpoint-rule leg on the film and print it")
     ap.add_argument("--mc-only", action="store_true",
                     help="run only a short Monte Carlo leg on the film (for profiling) and print it")
     ap.add_argument("--no-autotune", action="store_true", help="no autotuning in the batched and workload legs")
@@ -394,6 +426,10 @@ def main():
     if args.demag_only:
         if rank == 0:
             print(json.dumps({"demag": demag_table(stream, rank)}))
+        return
+    if args.midpoint_only:
+        if rank == 0:
+            print(json.dumps({"midpoint": midpoint_table(stream, rank)}))
         return
     if args.mc_only:
         film = dict(spins=lat.n, **time_mc(lat, dict(T=300.0, seed=7 + rank), args.precision, args.steps, stream,
@@ -523,6 +559,7 @@ def main():
         out["workloads"] = workload_table(stream, rank)
         out["mc"] = mc_table(stream, rank)
         out["demag"] = demag_table(stream, rank)
+        out["midpoint"] = midpoint_table(stream, rank)
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(lat, T)
     if rank == 0:

@@ -222,6 +222,18 @@ ss_status get_demag_field(ss_system *h, double *out3n);
  * trial moves, out[1] attempted trial moves (synchronous). */
 ss_status get_mc_stats(ss_system *h, int32_t sys, int64_t out[2]);
 
+/* Advance every system by n >= 0 steps of the midpoint rule instead of Heun (asynchronous;
+ * the alternative integrator the paper's time-integration section cites):
+ * S_{n+1} = S_n + dt f(m), m = (S_n + S_{n+1})/2, f the right-hand side of Eq. LLG with the
+ * field of the midpoint spins and the step's thermal field (drawn once per step from the same
+ * Philox counters as llg_heun_step, held over the step).  Solved by `iterations` (1..1000)
+ * fixed-point iterations from the Euler predictor; nothing is renormalised (the rule keeps
+ * |S| when converged; the residual of the iteration shows in |S| - 1).  Shares the step
+ * counter, record ring and temperatures with llg_heun_step; runs iterations + 5 launches
+ * per step.  SS_ERR_INVALID_ARG for n < 0, iterations out of range, or the demagnetising
+ * field switched on (set_demag), which this rule does not include. */
+ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations);
+
 /* Copy all spins (concatenated over systems) to out3n [3n], AoS, FP64 (synchronous). */
 ss_status get_spins(ss_system *h, double *out3n);
 

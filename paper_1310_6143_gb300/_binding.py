@@ -28,7 +28,7 @@ EXPORTS = (
     "get_spins_device", "get_magnetisation", "get_energy", "get_record", "set_spins", "set_step", "get_step",
     "spin_system_set_exec", "spin_system_set_launch", "spin_system_autotune", "spin_system_info",
     "spin_system_set_barrier_test", "spin_system_sync", "spin_system_time_kernels", "ss_debug_philox", "ss_debug_gaussians",
-    "llg_heun_step_noalloc", "spin_system_set_draw_ahead", "ss_debug_fp64_rate", "mc_step", "get_mc_stats", "set_demag",
+    "llg_heun_step_noalloc", "spin_system_set_draw_ahead", "ss_debug_fp64_rate", "mc_step", "get_mc_stats", "set_demag", "llg_midpoint_step",
     "get_demag_field",
     "ss_last_error", "ss_status_string",
 )
@@ -114,6 +114,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "set_temperature_schedule": [P, P, I64, I64],
         "llg_heun_step": [P, I64],
         "mc_step": [P, I64],
+        "llg_midpoint_step": [P, I64, I32],
         "get_mc_stats": [P, I32, P],
         "set_demag": [P, D, D, I32],
         "get_demag_field": [P, P],

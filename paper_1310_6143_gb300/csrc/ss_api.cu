@@ -1393,6 +1393,36 @@ static ss_status advance_steps(ss_system *h, int64_t n) {
     return SS_OK;
 }
 
+ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (n < 0) return fail(h, SS_ERR_INVALID_ARG, "n must be >= 0");
+    if (iterations < 1 || iterations > 1000) return fail(h, SS_ERR_INVALID_ARG, "iterations must be 1..1000");
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sm_count * 8));
+    const int gmeas = step_grid(h);
+    if (h->demag_on) return fail(h, SS_ERR_INVALID_ARG, "the midpoint rule runs without the demagnetising field");
+    for (int64_t k = 0; k < n; ++k) {
+        double *dst = h->rec + (h->step % h->rec_cap) * (int64_t)h->nsys * kRecComps;
+        cudaError_t e;
+        if (h->precision == SS_FP32_MIXED) {
+            const KArgs<float> a = make_args<float>(h);
+            e = launch_measure<float>(a, h->block, gmeas, h->stream);
+            if (e == cudaSuccess) e = launch_finalize(h->sys, h->sys_tiles, h->nsys, h->partials, dst, h->stream);
+            if (e == cudaSuccess) e = launch_midpoint<float>(a, iterations, grid, h->stream);
+            if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
+        } else {
+            const KArgs<double> a = make_args<double>(h);
+            e = launch_measure<double>(a, h->block, gmeas, h->stream);
+            if (e == cudaSuccess) e = launch_finalize(h->sys, h->sys_tiles, h->nsys, h->partials, dst, h->stream);
+            if (e == cudaSuccess) e = launch_midpoint<double>(a, iterations, grid, h->stream);
+            if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "midpoint step");
+        h->step += 1;
+    }
+    return SS_OK;
+}
+
 ss_status set_demag(ss_system *h, double cell_size, double atom_volume, int32_t every) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;

@@ -166,6 +166,9 @@ template <typename R> cudaError_t launch_mc_colour(const KArgs<R> &a, const McAr
 template <typename R> int mc_blocks_per_sm(int block);
 cudaError_t launch_advance_step(unsigned long long *step, cudaStream_t s);
 template <typename R> cudaError_t launch_demag(const KArgs<R> &a, const DemagArgs &d, cudaStream_t s);
+// One midpoint step's launches after its record: Euler predictor, `iters` fixed-point
+// iterations, copy back (the step counter is advanced separately).
+template <typename R> cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t s);
 cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
                             double *dst, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long long count, uint32_t *out,

@@ -653,6 +653,115 @@ __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long lon
 }
 
 // ----------------------------------------------------------------------------------
+// Midpoint rule (the alternative integrator the paper's time-integration section cites):
+// S_{n+1} = S_n + dt f(m), m = (S_n + S_{n+1})/2, solved by fixed-point iterations from the
+// Euler predictor; the thermal field is drawn once per step (counters as the Heun step) and
+// held; nothing is renormalised (f(m) is perpendicular to m).
+// ----------------------------------------------------------------------------------
+
+// sum_j (J_ij / mu_s,i) X_j over row i (scalar or tensor bonds), without the applied field.
+template <typename R>
+__device__ __forceinline__ void exchange_bare(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int64_t i,
+                                              R &e0, R &e1, R &e2) {
+    const int32_t b = __ldg(a.row_ptr + i);
+    const int32_t e = __ldg(a.row_ptr + i + 1);
+    R x = 0, y = 0, z = 0;
+#pragma unroll 2
+    for (int32_t k = b; k < e; ++k) {
+        const int32_t j = __ldg(a.col + k);
+        const R m0 = X[j], m1 = Y[j], m2 = Z[j];
+        if (a.J_tensor) {
+            const R *t = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + k);
+            x = fma(__ldg(t + 0), m0, fma(__ldg(t + 1), m1, fma(__ldg(t + 2), m2, x)));
+            y = fma(__ldg(t + 3), m0, fma(__ldg(t + 4), m1, fma(__ldg(t + 5), m2, y)));
+            z = fma(__ldg(t + 6), m0, fma(__ldg(t + 7), m1, fma(__ldg(t + 8), m2, z)));
+        } else {
+            const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + k);
+            x = fma(Jk, m0, x);
+            y = fma(Jk, m1, y);
+            z = fma(Jk, m2, z);
+        }
+    }
+    e0 = x;
+    e1 = y;
+    e2 = z;
+}
+
+// First pass: the Euler predictor X = S + dt f(S) written to (px, py, pz), and the part of
+// the midpoint field that stays fixed over the step, C = H_app + H_th + (1/2) sum_j J_ij S_j
+// (the exchange field is linear, so the field of m = (S + X)/2 is C + (1/2) sum_j J_ij X_j
+// plus the on-site terms of m), stored in (hx, hy, hz).
+template <typename R>
+__global__ void k_mid_euler(const KArgs<R> a) {
+    __shared__ SmemTables tab;
+    stage_tables(a, tab);
+    __syncthreads();
+    const uint64_t step = *a.step;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+        const SysDesc &sd = a.sys[m.sys];
+        const R sqrtT = sqrtT_of_step(a, step, sd);
+        R t0 = 0, t1 = 0, t2 = 0;
+        if (sqrtT > (R)0) {
+            const R sig = m.sig * sqrtT;
+            const Philox4 w = philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
+            double g0, g1, g2;
+            box_muller3(w, tab, g0, g1, g2);
+            t0 = sig * narrow<R>(g0);
+            t1 = sig * narrow<R>(g1);
+            t2 = sig * narrow<R>(g2);
+        }
+        const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
+        R x0, x1, x2;
+        exchange_bare(a, a.sx, a.sy, a.sz, i, x0, x1, x2);
+        const R c0 = sys_H(sd, 0, R()) + t0, c1 = sys_H(sd, 1, R()) + t1, c2 = sys_H(sd, 2, R()) + t2;
+        a.hx[i] = fma((R)0.5, x0, c0);
+        a.hy[i] = fma((R)0.5, x1, c1);
+        a.hz[i] = fma((R)0.5, x2, c2);
+        R H0, H1, H2;
+        det_field(m, s0, s1, s2, x0 + c0, x1 + c1, x2 + c2, H0, H1, H2);
+        R d0, d1, d2;
+        llg_rhs(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, d0, d1, d2);
+        a.px[i] = fma(m.dt, d0, s0);
+        a.py[i] = fma(m.dt, d1, s1);
+        a.pz[i] = fma(m.dt, d2, s2);
+    }
+}
+
+// One fixed-point iteration: Y = S + dt f(m), m = (S + X)/2, with the field C + (1/2) sum_j J_ij X_j
+// plus the on-site terms of m.
+template <typename R>
+__global__ void k_mid_iter(const KArgs<R> a, const R *xx, const R *xy, const R *xz, R *yx, R *yy, R *yz) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+        const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
+        const R m0 = (R)0.5 * (s0 + xx[i]), m1 = (R)0.5 * (s1 + xy[i]), m2 = (R)0.5 * (s2 + xz[i]);
+        R x0, x1, x2;
+        exchange_bare(a, xx, xy, xz, i, x0, x1, x2);
+        R H0, H1, H2;
+        det_field(m, m0, m1, m2, fma((R)0.5, x0, a.hx[i]), fma((R)0.5, x1, a.hy[i]), fma((R)0.5, x2, a.hz[i]), H0,
+                  H1, H2);
+        R d0, d1, d2;
+        llg_rhs(m.gp, m.lambda, m0, m1, m2, H0, H1, H2, d0, d1, d2);
+        yx[i] = fma(m.dt, d0, s0);
+        yy[i] = fma(m.dt, d1, s1);
+        yz[i] = fma(m.dt, d2, s2);
+    }
+}
+
+// S <- X (the last iterate), flagging non-finite spins.
+template <typename R>
+__global__ void k_mid_copy(const KArgs<R> a, const R *xx, const R *xy, const R *xz) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R v0 = xx[i], v1 = xy[i], v2 = xz[i];
+        if (bad_inv(v0 * v0 + v1 * v1 + v2 * v2)) atomicOr(a.err, kErrNonFinite);
+        a.sx[i] = v0;
+        a.sy[i] = v1;
+        a.sz[i] = v2;
+    }
+}
+
+// ----------------------------------------------------------------------------------
 // Macrocell demagnetising field (Section "Demagnetising fields")
 // ----------------------------------------------------------------------------------
 

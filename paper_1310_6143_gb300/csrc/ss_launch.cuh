@@ -110,6 +110,27 @@ cudaError_t launch_demag(const KArgs<R> &a, const DemagArgs &d, cudaStream_t s) 
 }
 
 template <typename R>
+cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t s) {
+    k_mid_euler<R><<<grid, 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    R *x[3] = {a.px, a.py, a.pz}, *y[3] = {a.qx, a.qy, a.qz};
+    for (int k = 0; k < iters && e == cudaSuccess; ++k) {
+        k_mid_iter<R><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], y[0], y[1], y[2]);
+        e = cudaGetLastError();
+        for (int c = 0; c < 3; ++c) {
+            R *t = x[c];
+            x[c] = y[c];
+            y[c] = t;
+        }
+    }
+    if (e == cudaSuccess) {
+        k_mid_copy<R><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2]);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <typename R>
 int mc_blocks_per_sm(int block) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
@@ -149,5 +170,6 @@ template int corrector_blocks_per_sm<SS_REAL>(int, bool);
 template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
 template int mc_blocks_per_sm<SS_REAL>(int);
 template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
+template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 
 }  // namespace ss

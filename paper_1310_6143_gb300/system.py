@@ -196,6 +196,10 @@ class SpinSystem:
         self._check(self._lib.get_demag_field(self._h, B.ptr(out)))
         return out
 
+    def midpoint_step(self, n: int = 1, iterations: int = 4):
+        """n steps of the midpoint rule (fixed-point iterations per step), instead of Heun."""
+        self._check(self._lib.llg_midpoint_step(self._h, int(n), int(iterations)))
+
     def mc_step(self, n: int = 1):
         """n Hinzke-Nowak Monte Carlo steps (one trial move per spin each)."""
         self._check(self._lib.mc_step(self._h, int(n)))
