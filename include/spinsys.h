@@ -142,7 +142,8 @@ typedef struct {
     int64_t device_bytes; /* device memory held by the handle                         */
     int32_t draw_ahead;   /* eighths of each tile's spins whose next-step Gaussians the
                              corrector draws (FP32-mixed form; see spin_system_set_draw_ahead) */
-    int32_t pad;
+    int32_t exchange_rows;/* 1: a thread per exchange row; 2: a warp per row; 3: a warp per
+                             row reading packed bonds (see spin_system_set_exchange_rows)  */
 } ss_info;
 
 /* Create one system.  Validates and copies every array (SS_ERR_INVALID_ARG on bad
@@ -267,6 +268,21 @@ ss_status spin_system_set_exec(ss_system *h, ss_exec mode);
 /* Threads per block (64..1024, multiple of 32) and spins per tile (a multiple of the
  * block size, at most 16 blocks' worth) of the step kernels; rebuilds the tile list. */
 ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
+
+/* How the exchange sum of Eq. HJij is split over threads: mode 0 automatic (the default: a
+ * warp per row when the rows average 64 or more bonds, as with exchange beyond the nearest
+ * neighbours -- over 1,000 neighbours per atom for the long-ranged exchange the paper's
+ * scaling section runs), 1 a thread per row (the step kernels sum their own rows), 2 a warp
+ * per row.  With a warp per row, each Heun pass is preceded by a pass in which each warp sums
+ * 32 consecutive rows, its lanes striding over a row's bonds, into a field buffer of 3n
+ * values; for scalar J with at most 256 distinct J_ij / mu_s,i and fewer than 2^24 spins the
+ * bonds are read as packed 32-bit words (neighbour index and dictionary entry, 4 bytes per
+ * bond), built at creation when the automatic rule picks a warp per row.  Only the
+ * summation order differs between the modes.  Monte Carlo and midpoint steps sum a thread
+ * per row in every mode.  A warp per row runs with graph or plain launches:
+ * spin_system_set_exec refuses the persistent and system-block modes (SS_ERR_UNSUPPORTED),
+ * and turning it on resets those to SS_EXEC_AUTO.  SS_ERR_INVALID_ARG for another mode. */
+ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode);
 
 /* FP32-mixed form: the corrector of step n draws the thermal Gaussians of step n+1 for
  * `eighths`/8 of each tile's spins (rounded down to whole blocks), so that their FP64

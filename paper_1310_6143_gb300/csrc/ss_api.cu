@@ -131,6 +131,15 @@ struct ss_system {
     double *d_cpos = nullptr, *d_cvol = nullptr, *d_cm = nullptr, *d_cH = nullptr;
     void *d_hd[3] = {};
 
+    // Long exchange rows: the exchange field summed by a warp per row (k_rows_field) before
+    // each step pass, when rows average kRowsAuto or more bonds (or on request)
+    int rows_req = 0;            // 0 automatic, 1 a thread per row, 2 a warp per row
+    bool rows = false;           // a warp per row in force
+    uint32_t *bw = nullptr;      // packed bonds col << 8 | dictionary entry (scalar J, <= 256 values)
+    void *Jd = nullptr;          // the dictionary of J_ij / mu_s,i
+    int nJd = 0;
+    void *E[3] = {};             // field of the spins a pass reads
+
     // launch state
     int nfin = 1;
     cudaGraphExec_t graph = nullptr;
@@ -330,6 +339,10 @@ KArgs<R> make_args(const ss_system *h) {
     a.Jt = static_cast<const R *>(h->Jt);
     a.Jtidx = h->Jtidx;
     a.J_tensor = h->J_tensor ? 1 : 0;
+    a.ex = a.ey = a.ez = nullptr;
+    a.bw = h->bw;
+    a.Jd = static_cast<const R *>(h->Jd);
+    a.nJd = h->nJd;
     a.demag = h->demag_on ? 1 : 0;
     a.mc_of = h->d_cell_of;
     a.hdx = static_cast<const R *>(h->d_hd[0]);
@@ -370,6 +383,21 @@ KArgs<R> make_args(const ss_system *h) {
     a.bar_extra = h->bar_extra;
     a.bar_timeout_ns = h->bar_timeout_ns;
     return a;
+}
+
+// The step passes read the exchange field that k_rows_field sums beforehand (long rows).
+template <typename R>
+void use_rows(const ss_system *h, KArgs<R> &a) {
+    if (!h->rows) return;
+    a.ex = static_cast<R *>(h->E[0]);
+    a.ey = static_cast<R *>(h->E[1]);
+    a.ez = static_cast<R *>(h->E[2]);
+}
+
+int rows_grid(const ss_system *h) {
+    const int per_sm = h->precision == SS_FP32_MIXED ? rows_blocks_per_sm<float>() : rows_blocks_per_sm<double>();
+    const int64_t g = (int64_t)h->sm_count * std::max(per_sm, 1);
+    return (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, g));
 }
 
 // Forget Gaussians drawn ahead: needed when the tile shape changes (the drawn slots depend
@@ -414,12 +442,15 @@ int persistent_grid(const ss_system *h) {
 
 template <typename R>
 cudaError_t enqueue_steps_kernels(ss_system *h, int64_t n) {
-    const KArgs<R> a = make_args<R>(h);
-    const int gp = step_grid(h), gc = corrector_grid(h);
+    KArgs<R> a = make_args<R>(h);
+    use_rows(h, a);
+    const int gp = step_grid(h), gc = corrector_grid(h), gr = h->rows ? rows_grid(h) : 0;
     for (int64_t k = 0; k < n; ++k) {
-        cudaError_t e = launch_predictor<R>(a, h->block, gp, h->stream);
+        cudaError_t e = h->rows ? launch_rows_field<R>(a, a.sx, a.sy, a.sz, gr, h->stream) : cudaSuccess;
+        if (e == cudaSuccess) e = launch_predictor<R>(a, h->block, gp, h->stream);
         if (e != cudaSuccess) return e;
-        e = launch_corrector<R>(a, h->block, gc, h->nfin, h->stream);
+        if (h->rows) e = launch_rows_field<R>(a, a.px, a.py, a.pz, gr, h->stream);
+        if (e == cudaSuccess) e = launch_corrector<R>(a, h->block, gc, h->nfin, h->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -614,6 +645,9 @@ void fill_material(MatDesc<R> &m, const MatKey &k, const ss_params *p) {
     m.has_cubic = k.v[11] != 0.0 ? 1 : 0;
 }
 
+// Rows averaging this many bonds or more get a warp each for the exchange sum.
+constexpr int64_t kRowsAuto = 64;
+
 template <typename R>
 ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     const int64_t n = h->n, nnz = h->nnz;
@@ -714,6 +748,42 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
                                    h->stream));
         SS_CUDA(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
     }
+    // Packed bonds for rows long enough to go a warp per row: col (< 2^24) and one byte
+    // naming the bond's J_ij / mu_s,i in a dictionary of at most 256 values.
+    if (!tensor && nnz >= kRowsAuto * n && n < (int64_t(1) << 24)) {
+        using Bits = typename std::conditional<sizeof(R) == 8, uint64_t, uint32_t>::type;
+        constexpr int kSlots = 1024;
+        std::vector<Bits> key(kSlots);
+        std::vector<int> id(kSlots, -1);
+        std::vector<R> dict;
+        std::vector<uint32_t> bw((size_t)nnz);
+        bool ok = true;
+        for (int64_t k = 0; k < nnz && ok; ++k) {
+            Bits b;
+            std::memcpy(&b, &J[k], sizeof(R));
+            uint32_t hsh = (uint32_t)(((uint64_t)b * 0x9E3779B97F4A7C15ull) >> 54);  // 10 bits
+            while (id[hsh] >= 0 && key[hsh] != b) hsh = (hsh + 1) & (kSlots - 1);
+            if (id[hsh] < 0) {
+                if (dict.size() == 256) {
+                    ok = false;
+                    break;
+                }
+                key[hsh] = b;
+                id[hsh] = (int)dict.size();
+                dict.push_back(J[k]);
+            }
+            bw[(size_t)k] = ((uint32_t)col[k] << 8) | (uint32_t)id[hsh];
+        }
+        if (ok) {
+            SS_CUDA(h, dalloc(h, &h->Jd, dict.size() * sizeof(R)));
+            SS_CUDA(h, dalloc(h, (void **)&h->bw, bw.size() * sizeof(uint32_t)));
+            SS_CUDA(h, cudaMemcpyAsync(h->Jd, dict.data(), dict.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
+            SS_CUDA(h, cudaMemcpyAsync(h->bw, bw.data(), bw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                       h->stream));
+            SS_CUDA(h, cudaStreamSynchronize(h->stream));
+            h->nJd = (int)dict.size();
+        }
+    }
     h->J_uniform = nnz > 0 && !tensor;
     for (int64_t k = 1; k < nnz && h->J_uniform; ++k) h->J_uniform = std::memcmp(&J[k], &J[0], sizeof(R)) == 0;
     h->J_value = nnz > 0 ? (double)J[0] : 0.0;
@@ -773,6 +843,21 @@ ss_status init_random(ss_system *h, const std::vector<HostSys> &hs) {
                                        (size_t)x.p->n * rs, cudaMemcpyHostToDevice, h->stream));
     }
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SS_OK;
+}
+
+// A warp per row for the exchange sums (mode 2), a thread per row (1), or the automatic
+// choice (0: a warp per row when rows average kRowsAuto bonds or more).
+ss_status set_rows(ss_system *h, int32_t mode) {
+    const bool on = mode == 2 || (mode == 0 && h->nnz >= kRowsAuto * h->n && h->n > 0);
+    if (on && !h->E[0]) {
+        const size_t rs = real_size(h);
+        for (int c = 0; c < 3; ++c) SS_CUDA(h, dalloc(h, &h->E[c], (size_t)h->n * rs));
+    }
+    h->rows_req = mode;
+    if (on != h->rows) drop_graph(h);
+    h->rows = on;
+    if (on && (h->exec == SS_EXEC_PERSISTENT || h->exec == SS_EXEC_SYSTEM_BLOCKS)) h->exec = SS_EXEC_AUTO;
     return SS_OK;
 }
 
@@ -891,6 +976,7 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         h->ahead_q = slots >= 8 ? 4 : 6;  // the faster split on GB300 for each case
     }
     st = build_tiles(h);
+    if (st == SS_OK) st = set_rows(h, 0);
     if (st != SS_OK) return cleanup(st);
     st = h->precision == SS_FP32_MIXED ? init_random<float>(h, hs) : init_random<double>(h, hs);
     if (st != SS_OK) return cleanup(st);
@@ -906,7 +992,9 @@ ss_status usable(ss_system *h) {
 
 template <typename R>
 ss_status measure(ss_system *h) {
-    const KArgs<R> a = make_args<R>(h);
+    KArgs<R> a = make_args<R>(h);
+    use_rows(h, a);
+    if (h->rows) SS_CUDA(h, launch_rows_field<R>(a, a.sx, a.sy, a.sz, rows_grid(h), h->stream));
     SS_CUDA(h, launch_measure<R>(a, h->block, step_grid(h), h->stream));
     SS_CUDA(h, launch_finalize(h->sys, h->sys_tiles, h->nsys, h->partials, h->cur, h->stream));
     return SS_OK;
@@ -925,14 +1013,17 @@ ss_status current_record(ss_system *h, int32_t sys, double rec[kRecComps]) {
 
 template <typename R>
 ss_status time_kernels_impl(ss_system *h, int32_t nsteps, double out_ms[3]) {
-    const KArgs<R> a = make_args<R>(h);
-    const int gp = step_grid(h), gc = corrector_grid(h);
+    KArgs<R> a = make_args<R>(h);
+    use_rows(h, a);
+    const int gp = step_grid(h), gc = corrector_grid(h), gr = h->rows ? rows_grid(h) : 0;
     std::vector<cudaEvent_t> ev(2 * (size_t)nsteps + 1);
     for (auto &e : ev) SS_CUDA(h, cudaEventCreate(&e));
     SS_CUDA(h, cudaEventRecord(ev[0], h->stream));
     for (int32_t k = 0; k < nsteps; ++k) {
+        if (h->rows) SS_CUDA(h, launch_rows_field<R>(a, a.sx, a.sy, a.sz, gr, h->stream));
         SS_CUDA(h, launch_predictor<R>(a, h->block, gp, h->stream));
         SS_CUDA(h, cudaEventRecord(ev[2 * k + 1], h->stream));
+        if (h->rows) SS_CUDA(h, launch_rows_field<R>(a, a.px, a.py, a.pz, gr, h->stream));
         SS_CUDA(h, launch_corrector<R>(a, h->block, gc, h->nfin, h->stream));
         SS_CUDA(h, cudaEventRecord(ev[2 * k + 2], h->stream));
     }
@@ -1646,6 +1737,8 @@ ss_status spin_system_set_exec(ss_system *h, ss_exec mode) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
     if (mode < SS_EXEC_AUTO || mode > SS_EXEC_SYSTEM_BLOCKS) return fail(h, SS_ERR_INVALID_ARG, "unknown exec mode");
+    if ((mode == SS_EXEC_PERSISTENT || mode == SS_EXEC_SYSTEM_BLOCKS) && h->rows)
+        return fail(h, SS_ERR_UNSUPPORTED, "long exchange rows (a warp per row) run as graph or plain launches");
     if (mode == SS_EXEC_PERSISTENT && persistent_grid(h) < 1)
         return fail(h, SS_ERR_UNSUPPORTED, "persistent kernel cannot be made co-resident with block %d", h->block);
     h->exec = mode;
@@ -1663,6 +1756,14 @@ ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile) {
     h->block = block;
     h->tile = tile;
     return build_tiles(h);
+}
+
+ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (mode < 0 || mode > 2) return fail(h, SS_ERR_INVALID_ARG, "mode must be 0 (automatic), 1 or 2");
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    return set_rows(h, mode);
 }
 
 ss_status spin_system_set_draw_ahead(ss_system *h, int32_t eighths) {
@@ -1689,7 +1790,7 @@ ss_status spin_system_info(ss_system *h, ss_info *o) {
     o->record_capacity = h->rec_cap;
     o->device_bytes = (int64_t)h->device_bytes;
     o->draw_ahead = h->ahead_q;
-    o->pad = 0;
+    o->exchange_rows = h->rows ? (h->bw ? 3 : 2) : 1;
     return SS_OK;
 }
 

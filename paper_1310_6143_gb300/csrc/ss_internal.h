@@ -82,6 +82,11 @@ struct KArgs {
     const R *Jt;              // [9 ndict] distinct exchange tensors / mu_s,i, row by row
     const int32_t *Jtidx;     // [nnz] tensor of each bond (J_tensor = 1)
     int J_tensor;             // 1: the exchange sum uses Jt[Jtidx[k]] instead of J
+    R *ex, *ey, *ez;          // [n] exchange + applied field of the spins being updated, computed
+                              // beforehand by k_rows_field (a warp per row), or nullptr
+    const uint32_t *bw;       // [nnz] packed bonds col << 8 | entry of Jd (rows of a warp), or nullptr
+    const R *Jd;              // [nJd <= 256] distinct J_ij / mu_s,i of the packed bonds
+    int nJd;
     const int32_t *mc_of;     // [n] macrocell of each spin (demagnetising field)
     const R *hdx, *hdy, *hdz; // [ncell] demagnetising field of each macrocell (T)
     int demag;                // 1: add the macrocell field to every spin's field
@@ -169,6 +174,10 @@ template <typename R> cudaError_t launch_demag(const KArgs<R> &a, const DemagArg
 // One midpoint step's launches after its record: Euler predictor, `iters` fixed-point
 // iterations, copy back (the step counter is advanced separately).
 template <typename R> cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t s);
+// Exchange + applied field of (X, Y, Z) into (a.ex, a.ey, a.ez), a warp per row (long rows).
+template <typename R>
+cudaError_t launch_rows_field(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int grid, cudaStream_t s);
+template <typename R> int rows_blocks_per_sm();
 cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
                             double *dst, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long long count, uint32_t *out,

@@ -78,6 +78,12 @@ __device__ __forceinline__ void stage_tables(const KArgs<R> &a, SmemTables &t) {
 template <typename R, bool Coherent>
 __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &sd, const R *X, const R *Y,
                                              const R *Z, int64_t i, R &e0, R &e1, R &e2) {
+    if (a.ex) {  // long rows: summed by k_rows_field for the spins this pass reads
+        e0 = ld<Coherent>(a.ex + i);
+        e1 = ld<Coherent>(a.ey + i);
+        e2 = ld<Coherent>(a.ez + i);
+        return;
+    }
     const int32_t b = __ldg(a.row_ptr + i);
     const int32_t e = __ldg(a.row_ptr + i + 1);
     R x = sys_H(sd, 0, R()), y = sys_H(sd, 1, R()), z = sys_H(sd, 2, R());
@@ -648,6 +654,82 @@ __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long lon
             *a.ticket = 0u;
             *a.step = step0 + (uint64_t)nsteps;
             __threadfence();
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// Long exchange rows (hundreds to thousands of neighbours, Eq. HJij): a warp per row.
+// The warp takes 32 consecutive rows; for each, its lanes stride over the row's bonds
+// (coalesced bond loads), gather the neighbours' spins and sum; a butterfly gives every lane
+// the row's total and lane q keeps row q's.  Each lane then writes its row's field
+// H_app + sum_j (J_ij / mu_s,i) X_j (coalesced).  Mode 0: packed bonds (col << 8 | entry of
+// the Jd dictionary, staged in shared memory); 1: col + J (or the uniform J); 2: tensors.
+// ----------------------------------------------------------------------------------
+template <typename R, int Mode>
+__global__ void __launch_bounds__(256) k_rows_field(const KArgs<R> a, const R *X, const R *Y, const R *Z) {
+    __shared__ R jd[256];
+    if (Mode == 0) {
+        for (int t = threadIdx.x; t < a.nJd; t += blockDim.x) jd[t] = a.Jd[t];
+        __syncthreads();
+    }
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = warp * 32; r0 < a.n; r0 += nwarps * 32) {
+        const int64_t row = r0 + lane;
+        int32_t rb = 0, re = 0;
+        if (row < a.n) {
+            rb = __ldg(a.row_ptr + row);
+            re = __ldg(a.row_ptr + row + 1);
+        }
+        const int nr = a.n - r0 < 32 ? (int)(a.n - r0) : 32;
+        R mx = 0, my = 0, mz = 0;
+        for (int q = 0; q < nr; ++q) {
+            const int32_t b = __shfl_sync(FULL, rb, q), e = __shfl_sync(FULL, re, q);
+            R x = 0, y = 0, z = 0;
+#pragma unroll 4
+            for (int32_t k = b + lane; k < e; k += 32) {
+                if (Mode == 0) {
+                    const uint32_t w = __ldg(a.bw + k);
+                    const int32_t j = (int32_t)(w >> 8);
+                    const R Jk = jd[w & 255u];
+                    x = fma(Jk, X[j], x);
+                    y = fma(Jk, Y[j], y);
+                    z = fma(Jk, Z[j], z);
+                } else if (Mode == 1) {
+                    const int32_t j = __ldg(a.col + k);
+                    const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + k);
+                    x = fma(Jk, X[j], x);
+                    y = fma(Jk, Y[j], y);
+                    z = fma(Jk, Z[j], z);
+                } else {
+                    const int32_t j = __ldg(a.col + k);
+                    const R *t = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + k);
+                    const R s0 = X[j], s1 = Y[j], s2 = Z[j];
+                    x = fma(__ldg(t + 0), s0, fma(__ldg(t + 1), s1, fma(__ldg(t + 2), s2, x)));
+                    y = fma(__ldg(t + 3), s0, fma(__ldg(t + 4), s1, fma(__ldg(t + 5), s2, y)));
+                    z = fma(__ldg(t + 6), s0, fma(__ldg(t + 7), s1, fma(__ldg(t + 8), s2, z)));
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_xor_sync(FULL, x, o);
+                y += __shfl_xor_sync(FULL, y, o);
+                z += __shfl_xor_sync(FULL, z, o);
+            }
+            if (lane == q) {
+                mx = x;
+                my = y;
+                mz = z;
+            }
+        }
+        if (row < a.n) {
+            const SysDesc &sd = a.sys[a.mats[__ldg(a.mat + row)].sys];
+            a.ex[row] = sys_H(sd, 0, R()) + mx;
+            a.ey[row] = sys_H(sd, 1, R()) + my;
+            a.ez[row] = sys_H(sd, 2, R()) + mz;
         }
     }
 }

@@ -131,6 +131,27 @@ cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t
 }
 
 template <typename R>
+cudaError_t launch_rows_field(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int grid, cudaStream_t s) {
+    if (a.bw)
+        k_rows_field<R, 0><<<grid, 256, 0, s>>>(a, X, Y, Z);
+    else if (a.J_tensor)
+        k_rows_field<R, 2><<<grid, 256, 0, s>>>(a, X, Y, Z);
+    else
+        k_rows_field<R, 1><<<grid, 256, 0, s>>>(a, X, Y, Z);
+    return cudaGetLastError();
+}
+
+template <typename R>
+int rows_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rows_field<R, 0>, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb;
+}
+
+template <typename R>
 int mc_blocks_per_sm(int block) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
@@ -171,5 +192,8 @@ template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McA
 template int mc_blocks_per_sm<SS_REAL>(int);
 template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
 template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
+template cudaError_t launch_rows_field<SS_REAL>(const KArgs<SS_REAL> &, const SS_REAL *, const SS_REAL *,
+                                                const SS_REAL *, int, cudaStream_t);
+template int rows_blocks_per_sm<SS_REAL>();
 
 }  // namespace ss

@@ -157,6 +157,10 @@ class SpinSystem:
     def set_launch(self, block: int, tile: int):
         self._check(self._lib.spin_system_set_launch(self._h, int(block), int(tile)))
 
+    def set_exchange_rows(self, mode: str):
+        """'auto', 'thread' (a thread per exchange row) or 'warp' (a warp per row)."""
+        self._check(self._lib.spin_system_set_exchange_rows(self._h, {"auto": 0, "thread": 1, "warp": 2}[mode]))
+
     def set_draw_ahead(self, eighths: int):
         self._check(self._lib.spin_system_set_draw_ahead(self._h, int(eighths)))
 
