@@ -320,6 +320,50 @@ def demag_table(stream, rank):
     return rows
 
 
+def long_range_table(stream, rank, cells=64, steps=20, hbm_peak=6800.0):
+    """Long exchange rows: fcc with exchange to 4a (1,060 neighbours per atom, 30 shells), the
+    shape of the paper's long-ranged exchange runs (over 1,000 neighbours, ~1.6e6 atoms),
+    at 300 K.  Heun throughput with a warp per row (packed bond words) and with a thread per
+    row, and the warp-per-row exchange pass alone against the DRAM roofline (its algorithmic
+    bytes: the 4-byte bond words, row pointers, material indices, the spins once and the field
+    written) and, in FP64, against the FP64 pipe (three FMAs per bond)."""
+    import torch
+    from paper_1310_6143_gb300.system import SpinSystem
+
+    from paper_1310_6143_gb300 import lattice as L
+
+    lat = L.fcc_long_range(cells, cells, cells, r_cut=4.0)
+    n, nnz = lat.n, lat.nnz
+    rows = {}
+    for prec, k in (("fp32", steps), ("fp64", max(4, steps // 4))):
+        rs = 4 if prec == "fp32" else 8
+        for mode in ("warp", "thread"):
+            with SpinSystem(lat, alpha=0.1, dt=1e-16, T=300.0, seed=11 + rank, precision=prec,
+                            stream=stream) as s:
+                s.set_exchange_rows("auto" if mode == "warp" else "thread")
+                info = s.info()
+                s.step(3)
+                s.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.step(k)
+                e1.record(stream)
+                e1.synchronize()
+                s.sync()
+                ms = e0.elapsed_time(e1) / k
+                row = {"spins": n, "bonds": nnz, "exchange_rows": info["exchange_rows"], "ms_per_step": ms,
+                       "value": n / (ms * 1e-3), "unit": "spin-steps/s"}
+                if mode == "warp":
+                    t = s.time_rows(10)
+                    alg = nnz * 4 + (n + 1) * 4 + n * 4 + 2 * 3 * n * rs
+                    row.update(rows_pass_ms=t, rows_pass_bytes=alg, rows_pass_gbs=alg / (t * 1e-3) / 1e9,
+                               rows_pass_hbm_frac=alg / (t * 1e-3) / 1e9 / hbm_peak,
+                               rows_pass_fma_per_s=3 * nnz / (t * 1e-3),
+                               rows_share_of_step=2 * t / ms)
+            rows[f"fcc{cells}_lr_{prec}_{mode}"] = row
+    return rows
+
+
 def midpoint_table(stream, rank, steps=40):
     """The midpoint rule (fixed-point iterations from the Euler predictor) against Heun on the
     film at 300 K: spin-steps/s for K = 3 and 4 iterations per step."""
@@ -383,6 +427,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU legs")
     ap.add_argument("--demag-only", action="store_true",
                     help="run only the demagnetising-field leg on the paper's ellipsoid and print it")
+    ap.add_argument("--long-range-only", action="store_true",
+                    help="run only the long-exchange-row leg (fcc, 1,060 neighbours per atom) and print it")
+    ap.add_argument("--lr-cells", type=int, default=64,
+                    help="cubic cells per axis of the long-exchange-row leg's fcc crystal (default 64: 1.05 M atoms)")
     ap.add_argument("--midpoint-only", action="store_true",
                     help="run only the midpoint-rule leg on the film and print it")
     ap.add_argument("--mc-only", action="store_true",
@@ -426,6 +474,10 @@ def main():
     if args.demag_only:
         if rank == 0:
             print(json.dumps({"demag": demag_table(stream, rank)}))
+        return
+    if args.long_range_only:
+        if rank == 0:
+            print(json.dumps({"long_range": long_range_table(stream, rank, cells=args.lr_cells, hbm_peak=hbm_peak)}))
         return
     if args.midpoint_only:
         if rank == 0:
@@ -560,6 +612,7 @@ def main():
         out["mc"] = mc_table(stream, rank)
         out["demag"] = demag_table(stream, rank)
         out["midpoint"] = midpoint_table(stream, rank)
+        out["long_range"] = long_range_table(stream, rank, hbm_peak=hbm_peak)
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(lat, T)
     if rank == 0:

@@ -273,13 +273,17 @@ ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
  * warp per row when the rows average 64 or more bonds, as with exchange beyond the nearest
  * neighbours -- over 1,000 neighbours per atom for the long-ranged exchange the paper's
  * scaling section runs), 1 a thread per row (the step kernels sum their own rows), 2 a warp
- * per row.  With a warp per row, each Heun pass is preceded by a pass in which each warp sums
- * 32 consecutive rows, its lanes striding over a row's bonds, into a field buffer of 3n
- * values; for scalar J with at most 256 distinct J_ij / mu_s,i and fewer than 2^24 spins the
- * bonds are read as packed 32-bit words (neighbour index and dictionary entry, 4 bytes per
- * bond), built at creation when the automatic rule picks a warp per row.  Only the
- * summation order differs between the modes.  Monte Carlo and midpoint steps sum a thread
- * per row in every mode.  A warp per row runs with graph or plain launches:
+ * per row.  With a warp per row, each Heun pass is preceded by a pass that sums the exchange
+ * field of every spin into a buffer of 3n values.  For scalar J with at most 255 distinct
+ * J_ij / mu_s,i and fewer than 2^24 spins (checked at creation, when the automatic rule picks
+ * a warp per row) the bonds are stored as packed 32-bit words (neighbour index and dictionary
+ * entry, 4 bytes per bond) in slices of 32 consecutive rows, bond k of the slice's rows
+ * interleaved and each slice padded to its longest row with zero bonds; lane l of a warp
+ * sums row l of its slice in CSR order from H_app, exactly as a thread per row does, so the
+ * results are identical to mode 1 (ss_info.exchange_rows = 3).  Otherwise (tensors, more
+ * values) each warp sums 32 consecutive rows one by one, its lanes striding over the row's
+ * bonds (exchange_rows = 2): only the summation order differs.  Monte Carlo and midpoint
+ * steps sum a thread per row in every mode.  A warp per row runs with graph or plain launches:
  * spin_system_set_exec refuses the persistent and system-block modes (SS_ERR_UNSUPPORTED),
  * and turning it on resets those to SS_EXEC_AUTO.  SS_ERR_INVALID_ARG for another mode. */
 ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode);
@@ -300,9 +304,16 @@ ss_status spin_system_info(ss_system *h, ss_info *out);
 
 /* Advance `nsteps` steps with one predictor and one corrector launch each, timing every
  * launch with CUDA events on the handle's stream.  out_ms receives the mean duration of
- * (predictor, corrector) launches and the mean wall time of one step, in milliseconds.
- * The steps are real steps: the state and the step counter advance. */
+ * (predictor, corrector) launches and the mean wall time of one step, in milliseconds; with
+ * a warp per exchange row each includes the exchange pass before it.  The steps are real
+ * steps: the state and the step counter advance. */
 ss_status spin_system_time_kernels(ss_system *h, int32_t nsteps, double out_ms[3]);
+
+/* Time `launches` (>= 1) passes of the warp-per-row exchange sum over the current spins
+ * (spin_system_set_exchange_rows), CUDA events on the handle's stream; *out_ms receives the
+ * mean duration of one pass.  The spins and step counter do not change.  SS_ERR_STATE when
+ * the handle sums a thread per row. */
+ss_status spin_system_time_rows(ss_system *h, int32_t launches, double *out_ms);
 
 /* Test hook for the bounded grid barrier: when nonzero, the next persistent launches
  * wait for `extra` blocks that do not exist and give up after `timeout_ns`; the step then

@@ -29,7 +29,7 @@ EXPORTS = (
     "spin_system_set_exec", "spin_system_set_launch", "spin_system_autotune", "spin_system_info",
     "spin_system_set_barrier_test", "spin_system_sync", "spin_system_time_kernels", "ss_debug_philox", "ss_debug_gaussians",
     "llg_heun_step_noalloc", "spin_system_set_draw_ahead", "ss_debug_fp64_rate", "mc_step", "get_mc_stats", "set_demag", "llg_midpoint_step",
-    "spin_system_set_exchange_rows",
+    "spin_system_set_exchange_rows", "spin_system_time_rows",
     "get_demag_field",
     "ss_last_error", "ss_status_string",
 )
@@ -131,6 +131,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "spin_system_set_launch": [P, I32, I32],
         "spin_system_set_draw_ahead": [P, I32],
         "spin_system_set_exchange_rows": [P, I32],
+        "spin_system_time_rows": [P, I32, P],
         "spin_system_autotune": [P, I32, P],
         "spin_system_info": [P, P],
         "spin_system_set_barrier_test": [P, I32, I64],

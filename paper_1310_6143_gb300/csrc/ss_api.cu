@@ -135,9 +135,12 @@ struct ss_system {
     // each step pass, when rows average kRowsAuto or more bonds (or on request)
     int rows_req = 0;            // 0 automatic, 1 a thread per row, 2 a warp per row
     bool rows = false;           // a warp per row in force
-    uint32_t *bw = nullptr;      // packed bonds col << 8 | dictionary entry (scalar J, <= 256 values)
-    void *Jd = nullptr;          // the dictionary of J_ij / mu_s,i
+    uint32_t *sell = nullptr;    // packed bonds col << 8 | dictionary entry, slices of 32 rows
+    int64_t *sell_off = nullptr; // [nslice + 1] word offset of each slice
+    int64_t nslice = 0;
+    void *Jd = nullptr;          // the dictionary of J_ij / mu_s,i (with 0 for the padding)
     int nJd = 0;
+    void *x4 = nullptr;          // (x, y, z, 0) copy of the spins the sliced pass reads
     void *E[3] = {};             // field of the spins a pass reads
 
     // launch state
@@ -340,7 +343,10 @@ KArgs<R> make_args(const ss_system *h) {
     a.Jtidx = h->Jtidx;
     a.J_tensor = h->J_tensor ? 1 : 0;
     a.ex = a.ey = a.ez = nullptr;
-    a.bw = h->bw;
+    a.sell = h->sell;
+    a.sell_off = h->sell_off;
+    a.nslice = h->nslice;
+    a.x4 = static_cast<R *>(h->x4);
     a.Jd = static_cast<const R *>(h->Jd);
     a.nJd = h->nJd;
     a.demag = h->demag_on ? 1 : 0;
@@ -748,40 +754,71 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
                                    h->stream));
         SS_CUDA(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
     }
-    // Packed bonds for rows long enough to go a warp per row: col (< 2^24) and one byte
-    // naming the bond's J_ij / mu_s,i in a dictionary of at most 256 values.
+    // Packed bonds for rows long enough to go a warp per row: col (< 2^24) and one byte naming
+    // the bond's J_ij / mu_s,i in a dictionary of at most 255 values plus 0, stored in slices
+    // of 32 rows (bond k of the slice's row l at 32 k + l), each padded to its longest row with
+    // J = 0 bonds.
     if (!tensor && nnz >= kRowsAuto * n && n < (int64_t(1) << 24)) {
         using Bits = typename std::conditional<sizeof(R) == 8, uint64_t, uint32_t>::type;
         constexpr int kSlots = 1024;
         std::vector<Bits> key(kSlots);
         std::vector<int> id(kSlots, -1);
         std::vector<R> dict;
-        std::vector<uint32_t> bw((size_t)nnz);
+        std::vector<uint8_t> bid((size_t)nnz);
         bool ok = true;
+        int zero = -1;
         for (int64_t k = 0; k < nnz && ok; ++k) {
             Bits b;
             std::memcpy(&b, &J[k], sizeof(R));
             uint32_t hsh = (uint32_t)(((uint64_t)b * 0x9E3779B97F4A7C15ull) >> 54);  // 10 bits
             while (id[hsh] >= 0 && key[hsh] != b) hsh = (hsh + 1) & (kSlots - 1);
             if (id[hsh] < 0) {
-                if (dict.size() == 256) {
+                if (dict.size() == 255) {
                     ok = false;
                     break;
                 }
                 key[hsh] = b;
                 id[hsh] = (int)dict.size();
+                if (b == 0) zero = id[hsh];
                 dict.push_back(J[k]);
             }
-            bw[(size_t)k] = ((uint32_t)col[k] << 8) | (uint32_t)id[hsh];
+            bid[(size_t)k] = (uint8_t)id[hsh];
         }
         if (ok) {
+            if (zero < 0) {
+                zero = (int)dict.size();
+                dict.push_back((R)0);
+            }
+            const int64_t nsl = (n + 31) / 32;
+            std::vector<int64_t> off((size_t)nsl + 1, 0);
+            for (int64_t s = 0; s < nsl; ++s) {
+                int32_t w = 0;
+                for (int64_t i = 32 * s; i < std::min<int64_t>(n, 32 * s + 32); ++i) w = std::max(w, rp[i + 1] - rp[i]);
+                off[(size_t)s + 1] = off[(size_t)s] + 32 * (int64_t)w;
+            }
+            std::vector<uint32_t> sell((size_t)std::max<int64_t>(off[(size_t)nsl], 1));
+            for (int64_t s = 0; s < nsl; ++s) {
+                const int64_t w = (off[(size_t)s + 1] - off[(size_t)s]) / 32;
+                for (int l = 0; l < 32; ++l) {
+                    const int64_t i = 32 * s + l;
+                    const int64_t len = i < n ? rp[i + 1] - rp[i] : 0;
+                    const uint32_t pad = ((uint32_t)(i < n ? i : 0) << 8) | (uint32_t)zero;
+                    for (int64_t k = 0; k < w; ++k)
+                        sell[(size_t)(off[(size_t)s] + 32 * k + l)] =
+                            k < len ? ((uint32_t)col[rp[i] + k] << 8) | bid[(size_t)(rp[i] + k)] : pad;
+                }
+            }
             SS_CUDA(h, dalloc(h, &h->Jd, dict.size() * sizeof(R)));
-            SS_CUDA(h, dalloc(h, (void **)&h->bw, bw.size() * sizeof(uint32_t)));
+            SS_CUDA(h, dalloc(h, (void **)&h->sell, sell.size() * sizeof(uint32_t)));
+            SS_CUDA(h, dalloc(h, (void **)&h->sell_off, off.size() * sizeof(int64_t)));
             SS_CUDA(h, cudaMemcpyAsync(h->Jd, dict.data(), dict.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
-            SS_CUDA(h, cudaMemcpyAsync(h->bw, bw.data(), bw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+            SS_CUDA(h, cudaMemcpyAsync(h->sell, sell.data(), sell.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                       h->stream));
+            SS_CUDA(h, cudaMemcpyAsync(h->sell_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                                        h->stream));
             SS_CUDA(h, cudaStreamSynchronize(h->stream));
             h->nJd = (int)dict.size();
+            h->nslice = nsl;
         }
     }
     h->J_uniform = nnz > 0 && !tensor;
@@ -853,6 +890,7 @@ ss_status set_rows(ss_system *h, int32_t mode) {
     if (on && !h->E[0]) {
         const size_t rs = real_size(h);
         for (int c = 0; c < 3; ++c) SS_CUDA(h, dalloc(h, &h->E[c], (size_t)h->n * rs));
+        if (h->sell) SS_CUDA(h, dalloc(h, &h->x4, 4 * (size_t)h->n * rs));
     }
     h->rows_req = mode;
     if (on != h->rows) drop_graph(h);
@@ -1790,7 +1828,7 @@ ss_status spin_system_info(ss_system *h, ss_info *o) {
     o->record_capacity = h->rec_cap;
     o->device_bytes = (int64_t)h->device_bytes;
     o->draw_ahead = h->ahead_q;
-    o->exchange_rows = h->rows ? (h->bw ? 3 : 2) : 1;
+    o->exchange_rows = h->rows ? (h->sell ? 3 : 2) : 1;
     return SS_OK;
 }
 
@@ -1800,6 +1838,38 @@ ss_status spin_system_time_kernels(ss_system *h, int32_t nsteps, double out_ms[3
     if (nsteps < 1 || !out_ms) return fail(h, SS_ERR_INVALID_ARG, "nsteps >= 1 and out_ms needed");
     return h->precision == SS_FP32_MIXED ? time_kernels_impl<float>(h, nsteps, out_ms)
                                          : time_kernels_impl<double>(h, nsteps, out_ms);
+}
+
+ss_status spin_system_time_rows(ss_system *h, int32_t launches, double *out_ms) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (launches < 1 || !out_ms) return fail(h, SS_ERR_INVALID_ARG, "launches >= 1 and out_ms needed");
+    if (!h->rows) return fail(h, SS_ERR_STATE, "the handle sums a thread per exchange row");
+    cudaEvent_t e0, e1;
+    SS_CUDA(h, cudaEventCreate(&e0));
+    SS_CUDA(h, cudaEventCreate(&e1));
+    const int gr = rows_grid(h);
+    cudaError_t e = cudaEventRecord(e0, h->stream);
+    for (int32_t k = 0; k < launches && e == cudaSuccess; ++k) {
+        if (h->precision == SS_FP32_MIXED) {
+            KArgs<float> a = make_args<float>(h);
+            use_rows(h, a);
+            e = launch_rows_field<float>(a, a.sx, a.sy, a.sz, gr, h->stream);
+        } else {
+            KArgs<double> a = make_args<double>(h);
+            use_rows(h, a);
+            e = launch_rows_field<double>(a, a.sx, a.sy, a.sz, gr, h->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "exchange pass timing");
+    *out_ms = ms / launches;
+    return SS_OK;
 }
 
 ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_info) {

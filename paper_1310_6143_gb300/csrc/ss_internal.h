@@ -84,8 +84,13 @@ struct KArgs {
     int J_tensor;             // 1: the exchange sum uses Jt[Jtidx[k]] instead of J
     R *ex, *ey, *ez;          // [n] exchange + applied field of the spins being updated, computed
                               // beforehand by k_rows_field (a warp per row), or nullptr
-    const uint32_t *bw;       // [nnz] packed bonds col << 8 | entry of Jd (rows of a warp), or nullptr
-    const R *Jd;              // [nJd <= 256] distinct J_ij / mu_s,i of the packed bonds
+    const uint32_t *sell;     // packed bonds col << 8 | entry of Jd in slices of 32 rows: bond k of
+                              // row 32 s + l at sell[sell_off[s] + 32 k + l], padded with J = 0;
+                              // or nullptr
+    const int64_t *sell_off;  // [nslice + 1]
+    int64_t nslice;
+    R *x4;                    // [4n] the spins read by the sliced pass, (x, y, z, 0) per spin
+    const R *Jd;              // [nJd <= 256] distinct J_ij / mu_s,i of the packed bonds (and 0)
     int nJd;
     const int32_t *mc_of;     // [n] macrocell of each spin (demagnetising field)
     const R *hdx, *hdy, *hdz; // [ncell] demagnetising field of each macrocell (T)

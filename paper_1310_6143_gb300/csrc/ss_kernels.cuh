@@ -663,16 +663,86 @@ __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long lon
 // The warp takes 32 consecutive rows; for each, its lanes stride over the row's bonds
 // (coalesced bond loads), gather the neighbours' spins and sum; a butterfly gives every lane
 // the row's total and lane q keeps row q's.  Each lane then writes its row's field
-// H_app + sum_j (J_ij / mu_s,i) X_j (coalesced).  Mode 0: packed bonds (col << 8 | entry of
-// the Jd dictionary, staged in shared memory); 1: col + J (or the uniform J); 2: tensors.
+// H_app + sum_j (J_ij / mu_s,i) X_j (coalesced).  Mode 1: col + J (or the uniform J);
+// 2: tensors.  (Packed scalar bonds go through k_rows_sell below.)
 // ----------------------------------------------------------------------------------
+// Packed bonds in slices (the scalar-J case with at most 255 distinct J_ij / mu_s,i): lane l
+// of the warp owning slice s sums row 32 s + l, all lanes stepping through bond k together,
+// so the bond words load coalesced and the neighbours' spins come as one 16-byte (FP32) or
+// 32-byte (FP64) gather from the (x, y, z, 0) copy.  Consecutive rows keep the slice's
+// neighbourhood compact (on a lattice numbered cell by cell, a few cells), which is what
+// L1 reuse of the gathered spins depends on.  Each row is summed in its CSR order from
+// H_app, like the thread-per-row sum (padding adds 0 * S exactly).
+template <typename R>
+__global__ void k_pack4(const KArgs<R> a, const R *X, const R *Y, const R *Z) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (sizeof(R) == 4) {
+            reinterpret_cast<float4 *>(a.x4)[i] = make_float4(X[i], Y[i], Z[i], 0.f);
+        } else {
+            double2 *d = reinterpret_cast<double2 *>(a.x4) + 2 * i;
+            d[0] = make_double2(X[i], Y[i]);
+            d[1] = make_double2(Z[i], 0.0);
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_spin4(const R *x4, int32_t j, R &s0, R &s1, R &s2) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(x4) + j);
+        s0 = v.x;
+        s1 = v.y;
+        s2 = v.z;
+    } else {
+        const double2 *d = reinterpret_cast<const double2 *>(x4) + 2 * (int64_t)j;
+        const double2 u = __ldg(d), v = __ldg(d + 1);
+        s0 = u.x;
+        s1 = u.y;
+        s2 = v.x;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_rows_sell(const KArgs<R> a) {
+    __shared__ R jd[256];
+    for (int t = threadIdx.x; t < a.nJd; t += blockDim.x) jd[t] = a.Jd[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = warp; s < a.nslice; s += nwarps) {
+        const int64_t row = s * 32 + lane;
+        const int64_t o = __ldg(a.sell_off + s);
+        const int w = (int)((__ldg(a.sell_off + s + 1) - o) >> 5);
+        const uint32_t *p = a.sell + o + lane;
+        R x = 0, y = 0, z = 0;
+        const SysDesc *sd = nullptr;
+        if (row < a.n) {
+            sd = &a.sys[a.mats[__ldg(a.mat + row)].sys];
+            x = sys_H(*sd, 0, R());
+            y = sys_H(*sd, 1, R());
+            z = sys_H(*sd, 2, R());
+        }
+#pragma unroll 8
+        for (int k = 0; k < w; ++k) {
+            const uint32_t b = __ldg(p + 32 * (int64_t)k);
+            const R Jk = jd[b & 255u];
+            R s0, s1, s2;
+            load_spin4(a.x4, (int32_t)(b >> 8), s0, s1, s2);
+            x = fma(Jk, s0, x);
+            y = fma(Jk, s1, y);
+            z = fma(Jk, s2, z);
+        }
+        if (row < a.n) {
+            a.ex[row] = x;
+            a.ey[row] = y;
+            a.ez[row] = z;
+        }
+    }
+}
+
 template <typename R, int Mode>
 __global__ void __launch_bounds__(256) k_rows_field(const KArgs<R> a, const R *X, const R *Y, const R *Z) {
-    __shared__ R jd[256];
-    if (Mode == 0) {
-        for (int t = threadIdx.x; t < a.nJd; t += blockDim.x) jd[t] = a.Jd[t];
-        __syncthreads();
-    }
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -691,14 +761,7 @@ __global__ void __launch_bounds__(256) k_rows_field(const KArgs<R> a, const R *X
             R x = 0, y = 0, z = 0;
 #pragma unroll 4
             for (int32_t k = b + lane; k < e; k += 32) {
-                if (Mode == 0) {
-                    const uint32_t w = __ldg(a.bw + k);
-                    const int32_t j = (int32_t)(w >> 8);
-                    const R Jk = jd[w & 255u];
-                    x = fma(Jk, X[j], x);
-                    y = fma(Jk, Y[j], y);
-                    z = fma(Jk, Z[j], z);
-                } else if (Mode == 1) {
+                if (Mode == 1) {
                     const int32_t j = __ldg(a.col + k);
                     const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + k);
                     x = fma(Jk, X[j], x);

@@ -132,9 +132,13 @@ cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t
 
 template <typename R>
 cudaError_t launch_rows_field(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int grid, cudaStream_t s) {
-    if (a.bw)
-        k_rows_field<R, 0><<<grid, 256, 0, s>>>(a, X, Y, Z);
-    else if (a.J_tensor)
+    if (a.sell) {
+        const int64_t pb = (a.n + 255) / 256;
+        k_pack4<R><<<(int)(pb < 4 * (int64_t)grid ? pb : 4 * (int64_t)grid), 256, 0, s>>>(a, X, Y, Z);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_rows_sell<R><<<grid, 256, 0, s>>>(a);
+    } else if (a.J_tensor)
         k_rows_field<R, 2><<<grid, 256, 0, s>>>(a, X, Y, Z);
     else
         k_rows_field<R, 1><<<grid, 256, 0, s>>>(a, X, Y, Z);
@@ -144,7 +148,7 @@ cudaError_t launch_rows_field(const KArgs<R> &a, const R *X, const R *Y, const R
 template <typename R>
 int rows_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rows_field<R, 0>, 256, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rows_field<R, 1>, 256, 0) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }

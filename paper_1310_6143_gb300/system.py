@@ -181,6 +181,12 @@ class SpinSystem:
         self._check(self._lib.spin_system_time_kernels(self._h, int(nsteps), B.ptr(out)))
         return {"predictor_ms": out[0], "corrector_ms": out[1], "step_ms": out[2]}
 
+    def time_rows(self, launches: int = 10) -> float:
+        """Mean duration (ms) of one warp-per-row exchange pass over the current spins."""
+        out = np.zeros(1)
+        self._check(self._lib.spin_system_time_rows(self._h, int(launches), B.ptr(out)))
+        return float(out[0])
+
     def set_barrier_test(self, extra: int, timeout_ns: int):
         self._check(self._lib.spin_system_set_barrier_test(self._h, int(extra), int(timeout_ns)))
 
