@@ -75,10 +75,10 @@ __device__ __forceinline__ void stage_tables(const KArgs<R> &a, SmemTables &t) {
 
 // H_app + sum_j (J_ij / mu_s,i) X_j over row i (CSR order, one FMA per term and
 // component): the exchange plus applied field, in tesla.
-template <typename R, bool Coherent>
+template <typename R, bool Coherent, bool Rows = false>
 __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &sd, const R *X, const R *Y,
                                              const R *Z, int64_t i, R &e0, R &e1, R &e2) {
-    if (a.ex) {  // long rows: summed by k_rows_field for the spins this pass reads
+    if constexpr (Rows) {  // long rows: summed beforehand by k_rows_sell / k_rows_field
         e0 = ld<Coherent>(a.ex + i);
         e1 = ld<Coherent>(a.ey + i);
         e2 = ld<Coherent>(a.ez + i);
@@ -272,7 +272,7 @@ __device__ __forceinline__ void flush_partials(const double *red, int nq, double
 
 // Predictor over one tile.  Writes S', Q and H_th; acc receives this thread's sums of the
 // per-spin reduction terms.
-template <typename R, int BS, bool Coherent>
+template <typename R, int BS, bool Coherent, bool Rows = false>
 __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
                                                const SmemTables &tab, int pre_slot, double (&acc)[8]) {
     const SysDesc &sd = a.sys[td.sys];
@@ -288,7 +288,7 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = ld<Coherent>(a.sx + i), s1 = ld<Coherent>(a.sy + i), s2 = ld<Coherent>(a.sz + i);
         R e0, e1, e2;
-        exchange_sum<R, Coherent>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
+        exchange_sum<R, Coherent, Rows>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
         R H0, H1, H2;
         const R sde = det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         if (a.demag) add_demag(a, i, H0, H1, H2);
@@ -340,7 +340,7 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
     }
 }
 
-template <typename R, int BS, bool Coherent>
+template <typename R, int BS, bool Coherent, bool Rows = false>
 __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
                                                const SmemTables *tab) {
     const SysDesc &sd = a.sys[td.sys];
@@ -353,7 +353,7 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = ld<Coherent>(a.px + i), s1 = ld<Coherent>(a.py + i), s2 = ld<Coherent>(a.pz + i);
         R e0, e1, e2;
-        exchange_sum<R, Coherent>(a, sd, a.px, a.py, a.pz, i, e0, e1, e2);
+        exchange_sum<R, Coherent, Rows>(a, sd, a.px, a.py, a.pz, i, e0, e1, e2);
         R H0, H1, H2;
         det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         if (a.demag) add_demag(a, i, H0, H1, H2);
@@ -427,7 +427,7 @@ __device__ __forceinline__ void finalize_system(const SysDesc *sys, const int32_
 
 // Predictor passes over the block's tiles t = blockIdx.x + j gridDim.x, in chunks of
 // kTileChunk tiles whose partials are summed after one barrier.
-template <typename R, int BS, bool Coherent>
+template <typename R, int BS, bool Coherent, bool Rows = false>
 __device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step, const SmemTables &tab,
                                                int pre_slot, double *red) {
     const int64_t stride = gridDim.x;
@@ -437,7 +437,7 @@ __device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step,
             const int64_t t = t0 + nq * stride;
             if (t >= a.ntiles) break;
             double acc[8];
-            predictor_tile<R, BS, Coherent>(a, a.tiles[t], step, tab, pre_slot, acc);
+            predictor_tile<R, BS, Coherent, Rows>(a, a.tiles[t], step, tab, pre_slot, acc);
             warp_partials<BS>(acc, red, nq);
         }
         __syncthreads();
@@ -446,7 +446,7 @@ __device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step,
     }
 }
 
-template <typename R, int BS>
+template <typename R, int BS, bool Rows = false>
 __global__ void __launch_bounds__(BS) k_predictor(const KArgs<R> a) {
     __shared__ SmemTables tab;
     __shared__ double red[kTileChunk * (BS / 32) * 8];
@@ -455,12 +455,12 @@ __global__ void __launch_bounds__(BS) k_predictor(const KArgs<R> a) {
     const uint64_t step = *a.step;
     // Gaussians drawn ahead are valid only if the previous corrector ran for this step.
     const int pre_slot = (a.g_step != nullptr && *a.g_step == step) ? a.pre_slot : 1 << 30;
-    predictor_pass<R, BS, false>(a, step, tab, pre_slot, red);
+    predictor_pass<R, BS, false, Rows>(a, step, tab, pre_slot, red);
 }
 
 // Blocks [0, nfin) sum the predictor's tile partials into the record ring; the rest run
 // the corrector over the tiles.  The last block to finish advances the step counter.
-template <typename R, int BS, bool DrawAhead>
+template <typename R, int BS, bool DrawAhead, bool Rows = false>
 __global__ void __launch_bounds__(BS) k_corrector(const KArgs<R> a, int nfin) {
     __shared__ double red[(BS / 32) * 8];
     const uint64_t step = *a.step;
@@ -474,11 +474,12 @@ __global__ void __launch_bounds__(BS) k_corrector(const KArgs<R> a, int nfin) {
         stage_tables(a, tab);
         __syncthreads();
         const int64_t nb = gridDim.x - nfin;
-        for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb) corrector_tile<R, BS, false>(a, a.tiles[t], step, &tab);
+        for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb)
+            corrector_tile<R, BS, false, Rows>(a, a.tiles[t], step, &tab);
     } else {
         const int64_t nb = gridDim.x - nfin;
         for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb)
-            corrector_tile<R, BS, false>(a, a.tiles[t], step, nullptr);
+            corrector_tile<R, BS, false, Rows>(a, a.tiles[t], step, nullptr);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -506,7 +507,10 @@ __global__ void __launch_bounds__(BS) k_measure(const KArgs<R> a) {
             const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
             const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
             R e0, e1, e2;
-            exchange_sum<R, false>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
+            if (a.ex)
+                exchange_sum<R, false, true>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
+            else
+                exchange_sum<R, false>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
             R H0, H1, H2;
             const R sde = det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
             double v[5];

@@ -16,13 +16,21 @@ namespace ss {
 
 template <typename R>
 cudaError_t launch_predictor(const KArgs<R> &a, int block, int grid, cudaStream_t s) {
-    SS_BLOCK_SWITCH(block, k_predictor<R, BS><<<grid, BS, 0, s>>>(a));
+    if (a.ex) {
+        SS_BLOCK_SWITCH(block, k_predictor<R, BS, true><<<grid, BS, 0, s>>>(a));
+    } else {
+        SS_BLOCK_SWITCH(block, k_predictor<R, BS><<<grid, BS, 0, s>>>(a));
+    }
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s) {
-    if (a.g_step != nullptr) {
+    if (a.ex && a.g_step != nullptr) {
+        SS_BLOCK_SWITCH(block, k_corrector<R, BS, true, true><<<grid + nfin, BS, 0, s>>>(a, nfin));
+    } else if (a.ex) {
+        SS_BLOCK_SWITCH(block, k_corrector<R, BS, false, true><<<grid + nfin, BS, 0, s>>>(a, nfin));
+    } else if (a.g_step != nullptr) {
         SS_BLOCK_SWITCH(block, k_corrector<R, BS, true><<<grid + nfin, BS, 0, s>>>(a, nfin));
     } else {
         SS_BLOCK_SWITCH(block, k_corrector<R, BS, false><<<grid + nfin, BS, 0, s>>>(a, nfin));
