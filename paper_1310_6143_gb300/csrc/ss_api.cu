@@ -146,6 +146,9 @@ struct ss_system {
     // launch state
     int nfin = 1;
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t mcgraph = nullptr;  // captured Monte Carlo steps
+    int mcgraph_steps = 0;
+    bool mcgraph_failed = false;
     int graph_steps = 0;
     cudaGraphExec_t pgraph = nullptr;  // captured persistent launch (barrier reset + kernel)
     long long pgraph_steps = 0;
@@ -415,6 +418,9 @@ cudaError_t invalidate_ahead(ss_system *h) {
 }
 
 void drop_graph(ss_system *h) {
+    if (h->mcgraph) cudaGraphExecDestroy(h->mcgraph);
+    h->mcgraph = nullptr;
+    h->mcgraph_steps = 0;
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     h->graph_steps = 0;
@@ -1275,6 +1281,7 @@ ss_status mc_upload_params(ss_system *h) {
     if (h->sched_len > 0) {
         if (h->sched_len > h->mc_sched_cap) {
             SS_CUDA(h, cudaStreamSynchronize(h->stream));
+            drop_graph(h);  // captured launches hold the old table's address
             if (h->mc_sched) dfree(h, h->mc_sched);
             h->mc_sched = nullptr;
             h->mc_sched_cap = 0;
@@ -1307,10 +1314,9 @@ cudaError_t enqueue_mc(ss_system *h, int64_t nsteps) {
     const int ncol = (int)h->mc_cstart.size() - 1;
     cudaError_t e = cudaSuccess;
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-        const int64_t step = h->step + k;
-        double *dst = h->rec + (step % h->rec_cap) * (int64_t)h->nsys * kRecComps;
         e = launch_measure<R>(a, h->block, gmeas, h->stream);
-        if (e == cudaSuccess) e = launch_finalize(h->sys, h->sys_tiles, h->nsys, h->partials, dst, h->stream);
+        if (e == cudaSuccess)
+            e = launch_finalize_ring(h->sys, h->sys_tiles, h->nsys, h->partials, h->rec, h->rec_cap, a.step, h->stream);
         for (int c = 0; c < ncol && e == cudaSuccess; ++c) {
             m.c0 = h->mc_cstart[c];
             m.c1 = h->mc_cstart[c + 1];
@@ -1606,7 +1612,38 @@ ss_status mc_step(ss_system *h, int64_t nsteps) {
     if (st != SS_OK) return st;
     st = mc_upload_params(h);
     if (st != SS_OK) return st;
-    const cudaError_t e = h->precision == SS_FP32_MIXED ? enqueue_mc<float>(h, nsteps) : enqueue_mc<double>(h, nsteps);
+    cudaError_t e = cudaSuccess;
+    int64_t left = nsteps;
+    // Captured steps (the launches hold no host-side step): replayed while whole graphs fit
+    const int g = graph_len(h);
+    if (left >= g && !h->mcgraph_failed && h->exec != SS_EXEC_KERNELS) {
+        if (!h->mcgraph) {
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t ek =
+                    h->precision == SS_FP32_MIXED ? enqueue_mc<float>(h, g) : enqueue_mc<double>(h, g);
+                e = cudaStreamEndCapture(h->stream, &graph);
+                if (ek != cudaSuccess) e = ek;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->mcgraph, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                h->mcgraph = nullptr;
+                h->mcgraph_failed = true;  // capture refused: launch directly from now on
+                e = cudaSuccess;
+            } else {
+                h->mcgraph_steps = g;
+            }
+        }
+        while (h->mcgraph && left >= h->mcgraph_steps && e == cudaSuccess) {
+            e = cudaGraphLaunch(h->mcgraph, h->stream);
+            left -= h->mcgraph_steps;
+        }
+    }
+    if (e == cudaSuccess && left > 0)
+        e = h->precision == SS_FP32_MIXED ? enqueue_mc<float>(h, left) : enqueue_mc<double>(h, left);
     if (e != cudaSuccess) return cuda_fail(h, e, "Monte Carlo launch");
     h->step += nsteps;
     for (int s = 0; s < h->nsys; ++s) h->mc_tried[s] += h->sys_n[s] * nsteps;

@@ -21,6 +21,13 @@ cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int ns
     return cudaGetLastError();
 }
 
+cudaError_t launch_finalize_ring(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
+                                 double *rec, int64_t rec_cap, const unsigned long long *step, cudaStream_t s) {
+    const int grid = nsys < 1024 ? nsys : 1024;
+    k_finalize_ring<256><<<grid > 0 ? grid : 1, 256, 0, s>>>(sys, sys_tiles, nsys, partials, rec, rec_cap, step);
+    return cudaGetLastError();
+}
+
 __global__ void k_debug_philox(uint4 ctr0, uint2 key, long long count, uint32_t *out) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
          k += (long long)gridDim.x * blockDim.x) {

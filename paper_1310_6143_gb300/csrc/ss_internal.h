@@ -183,6 +183,9 @@ template <typename R> cudaError_t launch_midpoint(const KArgs<R> &a, int iters, 
 template <typename R>
 cudaError_t launch_rows_field(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int grid, cudaStream_t s);
 template <typename R> int rows_blocks_per_sm();
+// The record of the current device step (ring entry step % rec_cap).
+cudaError_t launch_finalize_ring(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
+                                 double *rec, int64_t rec_cap, const unsigned long long *step, cudaStream_t s);
 cudaError_t launch_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys, const double *partials,
                             double *dst, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long long count, uint32_t *out,

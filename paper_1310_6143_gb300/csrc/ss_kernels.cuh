@@ -523,6 +523,18 @@ __global__ void __launch_bounds__(BS) k_measure(const KArgs<R> a) {
     }
 }
 
+// As k_finalize, into the record ring's entry of the current device step (so that the
+// launch holds no host-side step and can be captured once and replayed).
+template <int BS>
+__global__ void __launch_bounds__(BS) k_finalize_ring(const SysDesc *sys, const int32_t *sys_tiles, int nsys,
+                                                      const double *partials, double *rec, int64_t rec_cap,
+                                                      const unsigned long long *step) {
+    __shared__ double red[(BS / 32) * 8];
+    double *dst = rec + (int64_t)(*step % (unsigned long long)rec_cap) * nsys * kRecComps;
+    for (int s = blockIdx.x; s < nsys; s += gridDim.x)
+        finalize_system<BS, false>(sys, sys_tiles, partials, s, dst + (int64_t)s * kRecComps, red);
+}
+
 template <int BS>
 __global__ void __launch_bounds__(BS) k_finalize(const SysDesc *sys, const int32_t *sys_tiles, int nsys,
                                                  const double *partials, double *dst) {

@@ -158,3 +158,25 @@ def test_fp32_mixed_boltzmann_single_spin(SS):
     Z = integrate.quad(lambda x: np.exp(K * x * x), 0, 1)[0]
     ref = integrate.quad(lambda x: x * x * np.exp(K * x * x), 0, 1)[0] / Z
     assert abs(np.concatenate(vals).mean() - ref) < 0.005
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_captured_steps_equal_plain_launches(SS, precision):
+    """Monte Carlo steps replayed from a captured graph (records written at the device's step)
+    equal plain launches bitwise, with a temperature schedule and across graph boundaries."""
+    lat = L.simple_cubic(12, 12, 12, J=6.0e-21, k_u=1e-23)
+    S0 = L.random_state(lat.n, 4)
+    T = np.linspace(900.0, 100.0, 150)
+    out = {}
+    for mode in ("kernels", "auto"):
+        with SS(lat, alpha=0.1, dt=1e-16, T=300.0, S0=S0, seed=8, precision=precision) as s:
+            s.set_exec(mode)
+            s.mc_step(5)
+            s.set_temperature_schedule(T, step0=5)
+            s.mc_step(130)
+            s.step(3)
+            s.mc_step(70)
+            out[mode] = (s.spins(), s.record(0, 208), s.mc_stats(0))
+    assert np.array_equal(out["kernels"][0], out["auto"][0])
+    assert np.array_equal(out["kernels"][1], out["auto"][1])
+    assert out["kernels"][2] == out["auto"][2]
