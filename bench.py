@@ -22,6 +22,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -500,8 +501,8 @@ def main():
             torch.cuda.synchronize()
             barrier(world)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_{precision}.csv") if os.path.isdir(
-                    os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{precision}.csv") as ck:
+            with Clocks(os.path.join(os.environ.get("SPINSYS_CLOCKS_DIR", tempfile.gettempdir()),
+                                     f"clocks_{precision}.csv")) as ck:
                 e0.record(stream)
                 s.step(steps)
                 e1.record(stream)

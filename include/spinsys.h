@@ -63,7 +63,7 @@ typedef enum {
     SS_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out                 */
     SS_ERR_NONFINITE = 5,   /* a spin became NaN or infinite                      */
     SS_ERR_STATE = 6,       /* the handle is unusable after an earlier failure    */
-    SS_ERR_UNSUPPORTED = 7  /* a valid request this build cannot serve            */
+    SS_ERR_UNSUPPORTED = 7  /* a valid request the library cannot serve here     */
 } ss_status;
 
 typedef enum {
