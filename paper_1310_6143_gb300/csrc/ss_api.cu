@@ -146,6 +146,9 @@ struct ss_system {
     // launch state
     int nfin = 1;
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t midgraph = nullptr; // captured midpoint steps (midgraph_iters iterations each)
+    int midgraph_steps = 0, midgraph_iters = 0;
+    bool midgraph_failed = false;
     cudaGraphExec_t mcgraph = nullptr;  // captured Monte Carlo steps
     int mcgraph_steps = 0;
     bool mcgraph_failed = false;
@@ -418,6 +421,9 @@ cudaError_t invalidate_ahead(ss_system *h) {
 }
 
 void drop_graph(ss_system *h) {
+    if (h->midgraph) cudaGraphExecDestroy(h->midgraph);
+    h->midgraph = nullptr;
+    h->midgraph_steps = 0;
     if (h->mcgraph) cudaGraphExecDestroy(h->mcgraph);
     h->mcgraph = nullptr;
     h->mcgraph_steps = 0;
@@ -1298,6 +1304,24 @@ ss_status mc_upload_params(ss_system *h) {
     return SS_OK;
 }
 
+// Midpoint steps: per step the record of the state at the start of the step (measure and
+// finalise into the ring at the device's step), the midpoint launches, the step counter.
+template <typename R>
+cudaError_t enqueue_midpoint(ss_system *h, int64_t nsteps, int iterations) {
+    const KArgs<R> a = make_args<R>(h);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sm_count * 8));
+    const int gmeas = step_grid(h);
+    cudaError_t e = cudaSuccess;
+    for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        e = launch_measure<R>(a, h->block, gmeas, h->stream);
+        if (e == cudaSuccess)
+            e = launch_finalize_ring(h->sys, h->sys_tiles, h->nsys, h->partials, h->rec, h->rec_cap, a.step, h->stream);
+        if (e == cudaSuccess) e = launch_midpoint<R>(a, iterations, grid, h->stream);
+        if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
+    }
+    return e;
+}
+
 // Per Monte Carlo step: the record of the state at the start of the step (measure and
 // finalise into the ring), one launch per colour class, then the step counter advances.
 template <typename R>
@@ -1533,28 +1557,48 @@ ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations) {
     if (st != SS_OK) return st;
     if (n < 0) return fail(h, SS_ERR_INVALID_ARG, "n must be >= 0");
     if (iterations < 1 || iterations > 1000) return fail(h, SS_ERR_INVALID_ARG, "iterations must be 1..1000");
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sm_count * 8));
-    const int gmeas = step_grid(h);
     if (h->demag_on) return fail(h, SS_ERR_INVALID_ARG, "the midpoint rule runs without the demagnetising field");
-    for (int64_t k = 0; k < n; ++k) {
-        double *dst = h->rec + (h->step % h->rec_cap) * (int64_t)h->nsys * kRecComps;
-        cudaError_t e;
-        if (h->precision == SS_FP32_MIXED) {
-            const KArgs<float> a = make_args<float>(h);
-            e = launch_measure<float>(a, h->block, gmeas, h->stream);
-            if (e == cudaSuccess) e = launch_finalize(h->sys, h->sys_tiles, h->nsys, h->partials, dst, h->stream);
-            if (e == cudaSuccess) e = launch_midpoint<float>(a, iterations, grid, h->stream);
-            if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
-        } else {
-            const KArgs<double> a = make_args<double>(h);
-            e = launch_measure<double>(a, h->block, gmeas, h->stream);
-            if (e == cudaSuccess) e = launch_finalize(h->sys, h->sys_tiles, h->nsys, h->partials, dst, h->stream);
-            if (e == cudaSuccess) e = launch_midpoint<double>(a, iterations, grid, h->stream);
-            if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
+    auto enqueue = [h, iterations](int64_t k) {
+        return h->precision == SS_FP32_MIXED ? enqueue_midpoint<float>(h, k, iterations)
+                                             : enqueue_midpoint<double>(h, k, iterations);
+    };
+    cudaError_t e = cudaSuccess;
+    int64_t left = n;
+    // Captured steps (no launch holds a host-side step), replayed while whole graphs fit
+    const int g = graph_len(h);
+    if (left >= g && !h->midgraph_failed && h->exec != SS_EXEC_KERNELS) {
+        if (h->midgraph && h->midgraph_iters != iterations) {
+            cudaGraphExecDestroy(h->midgraph);
+            h->midgraph = nullptr;
         }
-        if (e != cudaSuccess) return cuda_fail(h, e, "midpoint step");
-        h->step += 1;
+        if (!h->midgraph) {
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t ek = enqueue(g);
+                e = cudaStreamEndCapture(h->stream, &graph);
+                if (ek != cudaSuccess) e = ek;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->midgraph, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                h->midgraph = nullptr;
+                h->midgraph_failed = true;  // capture refused: launch directly from now on
+                e = cudaSuccess;
+            } else {
+                h->midgraph_steps = g;
+                h->midgraph_iters = iterations;
+            }
+        }
+        while (h->midgraph && left >= h->midgraph_steps && e == cudaSuccess) {
+            e = cudaGraphLaunch(h->midgraph, h->stream);
+            left -= h->midgraph_steps;
+        }
     }
+    if (e == cudaSuccess && left > 0) e = enqueue(left);
+    if (e != cudaSuccess) return cuda_fail(h, e, "midpoint step");
+    h->step += n;
     return SS_OK;
 }
 

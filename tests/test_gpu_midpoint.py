@@ -137,3 +137,22 @@ def test_invalid_arguments(SS):
         s.set_demag(0.0, 0.0)
         s.midpoint_step(2)
         assert s.step_index == 2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_captured_steps_equal_plain_launches(SS, precision):
+    """Midpoint steps replayed from captured graphs (a new capture when K changes) equal plain
+    launches bitwise, records included."""
+    lat = L.simple_cubic(10, 10, 10, J=6e-21, k_u=1e-23)
+    S0 = L.random_state(lat.n, 12)
+    out = {}
+    for mode in ("kernels", "auto"):
+        with SS(lat, alpha=0.1, dt=1e-16, T=300.0, S0=S0, seed=6, precision=precision) as s:
+            s.set_exec(mode)
+            s.midpoint_step(70, iterations=3)
+            s.midpoint_step(65, iterations=4)
+            s.step(2)
+            s.midpoint_step(64, iterations=3)
+            out[mode] = (s.spins(), s.record(0, 201))
+    assert np.array_equal(out["kernels"][0], out["auto"][0])
+    assert np.array_equal(out["kernels"][1], out["auto"][1])
