@@ -230,7 +230,7 @@ ss_status get_mc_stats(ss_system *h, int32_t sys, int64_t out[2]);
  * Philox counters as llg_heun_step, held over the step).  Solved by `iterations` (1..1000)
  * fixed-point iterations from the Euler predictor; nothing is renormalised (the rule keeps
  * |S| when converged; the residual of the iteration shows in |S| - 1).  Shares the step
- * counter, record ring and temperatures with llg_heun_step; runs iterations + 5 launches
+ * counter, record ring and temperatures with llg_heun_step; runs iterations + 4 launches
  * per step.  SS_ERR_INVALID_ARG for n < 0, iterations out of range, or the demagnetising
  * field switched on (set_demag), which this rule does not include. */
 ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations);

@@ -890,8 +890,9 @@ __global__ void k_mid_euler(const KArgs<R> a) {
 }
 
 // One fixed-point iteration: Y = S + dt f(m), m = (S + X)/2, with the field C + (1/2) sum_j J_ij X_j
-// plus the on-site terms of m.
-template <typename R>
+// plus the on-site terms of m.  A thread reads S only at its own spin, so the last iteration
+// writes Y over S (Last: and flags non-finite spins).
+template <typename R, bool Last>
 __global__ void k_mid_iter(const KArgs<R> a, const R *xx, const R *xy, const R *xz, R *yx, R *yy, R *yz) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
@@ -904,21 +905,11 @@ __global__ void k_mid_iter(const KArgs<R> a, const R *xx, const R *xy, const R *
                   H1, H2);
         R d0, d1, d2;
         llg_rhs(m.gp, m.lambda, m0, m1, m2, H0, H1, H2, d0, d1, d2);
-        yx[i] = fma(m.dt, d0, s0);
-        yy[i] = fma(m.dt, d1, s1);
-        yz[i] = fma(m.dt, d2, s2);
-    }
-}
-
-// S <- X (the last iterate), flagging non-finite spins.
-template <typename R>
-__global__ void k_mid_copy(const KArgs<R> a, const R *xx, const R *xy, const R *xz) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R v0 = xx[i], v1 = xy[i], v2 = xz[i];
-        if (bad_inv(v0 * v0 + v1 * v1 + v2 * v2)) atomicOr(a.err, kErrNonFinite);
-        a.sx[i] = v0;
-        a.sy[i] = v1;
-        a.sz[i] = v2;
+        const R v0 = fma(m.dt, d0, s0), v1 = fma(m.dt, d1, s1), v2 = fma(m.dt, d2, s2);
+        if (Last && bad_inv(v0 * v0 + v1 * v1 + v2 * v2)) atomicOr(a.err, kErrNonFinite);
+        yx[i] = v0;
+        yy[i] = v1;
+        yz[i] = v2;
     }
 }
 

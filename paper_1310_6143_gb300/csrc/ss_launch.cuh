@@ -122,8 +122,8 @@ cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t
     k_mid_euler<R><<<grid, 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     R *x[3] = {a.px, a.py, a.pz}, *y[3] = {a.qx, a.qy, a.qz};
-    for (int k = 0; k < iters && e == cudaSuccess; ++k) {
-        k_mid_iter<R><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], y[0], y[1], y[2]);
+    for (int k = 0; k + 1 < iters && e == cudaSuccess; ++k) {
+        k_mid_iter<R, false><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], y[0], y[1], y[2]);
         e = cudaGetLastError();
         for (int c = 0; c < 3; ++c) {
             R *t = x[c];
@@ -131,8 +131,8 @@ cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t
             y[c] = t;
         }
     }
-    if (e == cudaSuccess) {
-        k_mid_copy<R><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2]);
+    if (e == cudaSuccess) {  // the last iterate goes straight to S
+        k_mid_iter<R, true><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], a.sx, a.sy, a.sz);
         e = cudaGetLastError();
     }
     return e;
