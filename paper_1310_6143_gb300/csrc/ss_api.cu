@@ -92,6 +92,7 @@ struct ss_system {
     int ahead_q = 6;       // eighths of each tile drawn ahead by the corrector
     bool J_uniform = false;  // every bond has the same J_ij / mu_s,i (J_value)
     bool J_tensor = false;   // bonds carry exchange tensors (Jt dictionary, Jtidx per bond)
+    bool any_cubic = false;  // some material has cubic anisotropy
     void *Jt = nullptr;
     int32_t *Jtidx = nullptr;
     double J_value = 0.0;
@@ -348,6 +349,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.Jt = static_cast<const R *>(h->Jt);
     a.Jtidx = h->Jtidx;
     a.J_tensor = h->J_tensor ? 1 : 0;
+    a.any_cubic = h->any_cubic ? 1 : 0;
     a.ex = a.ey = a.ez = nullptr;
     a.sell = h->sell;
     a.sell_off = h->sell_off;
@@ -435,9 +437,13 @@ void drop_graph(ss_system *h) {
     h->pgraph_steps = 0;
 }
 
+// The step-kernel variant the launchers pick for this handle (0 plain, 1 general, 2 rows).
+int step_mode(const ss_system *h) { return h->rows ? 2 : (h->J_tensor || h->any_cubic) ? 1 : 0; }
+
 int step_grid(const ss_system *h) {
-    const int per_sm = h->precision == SS_FP32_MIXED ? step_blocks_per_sm<float>(h->block)
-                                                     : step_blocks_per_sm<double>(h->block);
+    const int mode = step_mode(h);
+    const int per_sm = h->precision == SS_FP32_MIXED ? step_blocks_per_sm<float>(h->block, mode)
+                                                     : step_blocks_per_sm<double>(h->block, mode);
     const int64_t g = (int64_t)h->sm_count * std::max(per_sm, 1);
     return (int)std::max<int64_t>(1, std::min<int64_t>(h->ntiles, g));
 }
@@ -445,8 +451,9 @@ int step_grid(const ss_system *h) {
 // One wave of resident corrector blocks (the finalisation blocks come on top).
 int corrector_grid(const ss_system *h) {
     const bool ahead = h->ahead[0] != nullptr;
-    const int per_sm = h->precision == SS_FP32_MIXED ? corrector_blocks_per_sm<float>(h->block, ahead)
-                                                     : corrector_blocks_per_sm<double>(h->block, ahead);
+    const int mode = step_mode(h);
+    const int per_sm = h->precision == SS_FP32_MIXED ? corrector_blocks_per_sm<float>(h->block, ahead, mode)
+                                                     : corrector_blocks_per_sm<double>(h->block, ahead, mode);
     const int64_t g = (int64_t)h->sm_count * std::max(per_sm, 1);
     return (int)std::max<int64_t>(1, std::min<int64_t>(h->ntiles, g));
 }
@@ -498,7 +505,7 @@ cudaError_t enqueue_kernels(ss_system *h, int64_t n) {
 template <typename R>
 cudaError_t enqueue_system_blocks(ss_system *h, int64_t n) {
     const KArgs<R> a = make_args<R>(h);
-    const int per_sm = std::max(1, step_blocks_per_sm<R>(h->block));
+    const int per_sm = std::max(1, step_blocks_per_sm<R>(h->block, 1));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->nsys, (int64_t)h->sm_count * per_sm));
     while (n > 0) {
         const long long k = std::min<long long>(n, 1ll << 20);
@@ -755,6 +762,8 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     }
     rp[n] = (int32_t)nnz;
     h->nmat = (int32_t)mats.size();
+    h->any_cubic = false;
+    for (const MatDesc<R> &m : mats) h->any_cubic = h->any_cubic || m.has_cubic;
     // Homogeneous exchange (one J_ij / mu_s,i for every bond): the kernels skip the J loads.
     h->J_tensor = tensor;
     if (tensor) {

@@ -82,6 +82,7 @@ struct KArgs {
     const R *Jt;              // [9 ndict] distinct exchange tensors / mu_s,i, row by row
     const int32_t *Jtidx;     // [nnz] tensor of each bond (J_tensor = 1)
     int J_tensor;             // 1: the exchange sum uses Jt[Jtidx[k]] instead of J
+    int any_cubic;            // 1: some material has cubic anisotropy
     R *ex, *ey, *ez;          // [n] exchange + applied field of the spins being updated, computed
                               // beforehand by k_rows_field (a warp per row), or nullptr
     const uint32_t *sell;     // packed bonds col << 8 | entry of Jd in slices of 32 rows: bond k of
@@ -169,8 +170,9 @@ template <typename R> cudaError_t launch_persistent(const KArgs<R> &a, int block
 template <typename R> cudaError_t launch_system_blocks(const KArgs<R> &a, int block, int grid, long long nsteps,
                                                        cudaStream_t s);
 template <typename R> int persistent_blocks_per_sm(int block);
-template <typename R> int step_blocks_per_sm(int block);
-template <typename R> int corrector_blocks_per_sm(int block, bool draw_ahead);
+// mode: the step-kernel variant (0 plain, 1 general, 2 rows; kPlain / kGeneral / kRows)
+template <typename R> int step_blocks_per_sm(int block, int mode);
+template <typename R> int corrector_blocks_per_sm(int block, bool draw_ahead, int mode);
 template <typename R> cudaError_t launch_mc_colour(const KArgs<R> &a, const McArgs &m, int block, int grid,
                                                    cudaStream_t s);
 template <typename R> int mc_blocks_per_sm(int block);

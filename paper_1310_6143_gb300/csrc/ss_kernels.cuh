@@ -75,10 +75,16 @@ __device__ __forceinline__ void stage_tables(const KArgs<R> &a, SmemTables &t) {
 
 // H_app + sum_j (J_ij / mu_s,i) X_j over row i (CSR order, one FMA per term and
 // component): the exchange plus applied field, in tesla.
-template <typename R, bool Coherent, bool Rows = false>
+// Variants of the step kernels, fixed at compile time so that a plain lattice's kernels carry
+// no code for the other cases: kPlain (scalar J, no cubic anisotropy), kGeneral (tensor bonds
+// and cubic anisotropy decided per launch / material), kRows (the exchange field summed
+// beforehand by k_rows_sell / k_rows_field; cubic per material).
+constexpr int kPlain = 0, kGeneral = 1, kRows = 2;
+
+template <typename R, bool Coherent, int Mode = kGeneral>
 __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &sd, const R *X, const R *Y,
                                              const R *Z, int64_t i, R &e0, R &e1, R &e2) {
-    if constexpr (Rows) {  // long rows: summed beforehand by k_rows_sell / k_rows_field
+    if constexpr (Mode == kRows) {  // long rows: summed beforehand by k_rows_sell / k_rows_field
         e0 = ld<Coherent>(a.ex + i);
         e1 = ld<Coherent>(a.ey + i);
         e2 = ld<Coherent>(a.ez + i);
@@ -87,7 +93,7 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
     const int32_t b = __ldg(a.row_ptr + i);
     const int32_t e = __ldg(a.row_ptr + i + 1);
     R x = sys_H(sd, 0, R()), y = sys_H(sd, 1, R()), z = sys_H(sd, 2, R());
-    if (a.J_tensor) {  // Eq. HJijSMS: the tensor of bond k applied to S_j
+    if (Mode == kGeneral && a.J_tensor) {  // Eq. HJijSMS: the tensor of bond k applied to S_j
         for (int32_t k = b; k < e; ++k) {
             const int32_t j = __ldg(a.col + k);
             const R *t = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + k);
@@ -115,7 +121,7 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
 
 // Deterministic field (tesla): the exchange + applied field h from exchange_sum, then
 // the anisotropy and Neel terms.  Returns S.e for the anisotropy energy.
-template <typename R>
+template <typename R, bool Cubic = true>
 __device__ __forceinline__ R det_field(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R &H0, R &H1,
                                        R &H2) {
     const R sde = s0 * m.e[0] + s1 * m.e[1] + s2 * m.e[2];
@@ -123,7 +129,7 @@ __device__ __forceinline__ R det_field(const MatDesc<R> &m, R s0, R s1, R s2, R 
     H0 = fma(an, m.e[0], e0);
     H1 = fma(an, m.e[1], e1);
     H2 = fma(an, m.e[2], e2);
-    if (m.has_cubic) {  // -(2 k_c / mu_s) S^3
+    if (Cubic && m.has_cubic) {  // -(2 k_c / mu_s) S^3
         H0 = fma(m.kcf * s0 * s0, s0, H0);
         H1 = fma(m.kcf * s1 * s1, s1, H1);
         H2 = fma(m.kcf * s2 * s2, s2, H2);
@@ -164,7 +170,7 @@ __device__ __forceinline__ void llg_rhs(R gp, R lam, R s0, R s1, R s2, R H0, R H
 // exchange + applied field, and the anisotropy energy.  The applied-field energy is
 // -H.M (H is uniform within a system) and the exchange energy sum(-mu S.h/2) + H.M/2;
 // both are formed from the FP64 sums when a system's record is finalised.
-template <typename R>
+template <typename R, bool Cubic = true>
 __device__ __forceinline__ void spin_terms(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R sde,
                                            double v[5]) {
     const R mu = m.mu;
@@ -173,7 +179,7 @@ __device__ __forceinline__ void spin_terms(const MatDesc<R> &m, R s0, R s1, R s2
     v[2] = widen(mu * s2);
     v[3] = widen((R)-0.5 * mu * (s0 * e0 + s1 * e1 + s2 * e2));
     R ea = -m.ku * sde * sde;
-    if (m.has_cubic) {
+    if (Cubic && m.has_cubic) {
         const R x2 = s0 * s0, y2 = s1 * s1, z2 = s2 * s2;
         ea += (R)0.5 * m.kc * (x2 * x2 + y2 * y2 + z2 * z2);
     }
@@ -272,7 +278,7 @@ __device__ __forceinline__ void flush_partials(const double *red, int nq, double
 
 // Predictor over one tile.  Writes S', Q and H_th; acc receives this thread's sums of the
 // per-spin reduction terms.
-template <typename R, int BS, bool Coherent, bool Rows = false>
+template <typename R, int BS, bool Coherent, int Mode = kGeneral>
 __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
                                                const SmemTables &tab, int pre_slot, double (&acc)[8]) {
     const SysDesc &sd = a.sys[td.sys];
@@ -288,9 +294,9 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = ld<Coherent>(a.sx + i), s1 = ld<Coherent>(a.sy + i), s2 = ld<Coherent>(a.sz + i);
         R e0, e1, e2;
-        exchange_sum<R, Coherent, Rows>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
+        exchange_sum<R, Coherent, Mode>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
         R H0, H1, H2;
-        const R sde = det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+        const R sde = det_field<R, Mode != kPlain>(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         if (a.demag) add_demag(a, i, H0, H1, H2);
         R t0 = 0, t1 = 0, t2 = 0;
         if (sqrtT > (R)0) {
@@ -328,7 +334,7 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
         a.qy[i] = fma(hdt, d1, s1);
         a.qz[i] = fma(hdt, d2, s2);
         double v[5];
-        spin_terms(m, s0, s1, s2, e0, e1, e2, sde, v);
+        spin_terms<R, Mode != kPlain>(m, s0, s1, s2, e0, e1, e2, sde, v);
         if (first) {
 #pragma unroll
             for (int c = 0; c < 5; ++c) acc[c] = v[c];
@@ -340,7 +346,7 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
     }
 }
 
-template <typename R, int BS, bool Coherent, bool Rows = false>
+template <typename R, int BS, bool Coherent, int Mode = kGeneral>
 __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
                                                const SmemTables *tab) {
     const SysDesc &sd = a.sys[td.sys];
@@ -353,9 +359,9 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = ld<Coherent>(a.px + i), s1 = ld<Coherent>(a.py + i), s2 = ld<Coherent>(a.pz + i);
         R e0, e1, e2;
-        exchange_sum<R, Coherent, Rows>(a, sd, a.px, a.py, a.pz, i, e0, e1, e2);
+        exchange_sum<R, Coherent, Mode>(a, sd, a.px, a.py, a.pz, i, e0, e1, e2);
         R H0, H1, H2;
-        det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+        det_field<R, Mode != kPlain>(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         if (a.demag) add_demag(a, i, H0, H1, H2);
         H0 += ld<Coherent>(a.hx + i);
         H1 += ld<Coherent>(a.hy + i);
@@ -427,7 +433,7 @@ __device__ __forceinline__ void finalize_system(const SysDesc *sys, const int32_
 
 // Predictor passes over the block's tiles t = blockIdx.x + j gridDim.x, in chunks of
 // kTileChunk tiles whose partials are summed after one barrier.
-template <typename R, int BS, bool Coherent, bool Rows = false>
+template <typename R, int BS, bool Coherent, int Mode = kGeneral>
 __device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step, const SmemTables &tab,
                                                int pre_slot, double *red) {
     const int64_t stride = gridDim.x;
@@ -437,7 +443,7 @@ __device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step,
             const int64_t t = t0 + nq * stride;
             if (t >= a.ntiles) break;
             double acc[8];
-            predictor_tile<R, BS, Coherent, Rows>(a, a.tiles[t], step, tab, pre_slot, acc);
+            predictor_tile<R, BS, Coherent, Mode>(a, a.tiles[t], step, tab, pre_slot, acc);
             warp_partials<BS>(acc, red, nq);
         }
         __syncthreads();
@@ -446,8 +452,10 @@ __device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step,
     }
 }
 
-template <typename R, int BS, bool Rows = false>
-__global__ void __launch_bounds__(BS) k_predictor(const KArgs<R> a) {
+// FP64: one resident block per SM is enough for the FP64 pipe, and the minimum-blocks bound
+// lets the compiler keep the transform in registers (without it the FP64 form spills at 64).
+template <typename R, int BS, int Mode = kGeneral>
+__global__ void __launch_bounds__(BS, sizeof(R) == 8 ? 1 : 0) k_predictor(const KArgs<R> a) {
     __shared__ SmemTables tab;
     __shared__ double red[kTileChunk * (BS / 32) * 8];
     stage_tables(a, tab);
@@ -455,12 +463,12 @@ __global__ void __launch_bounds__(BS) k_predictor(const KArgs<R> a) {
     const uint64_t step = *a.step;
     // Gaussians drawn ahead are valid only if the previous corrector ran for this step.
     const int pre_slot = (a.g_step != nullptr && *a.g_step == step) ? a.pre_slot : 1 << 30;
-    predictor_pass<R, BS, false, Rows>(a, step, tab, pre_slot, red);
+    predictor_pass<R, BS, false, Mode>(a, step, tab, pre_slot, red);
 }
 
 // Blocks [0, nfin) sum the predictor's tile partials into the record ring; the rest run
 // the corrector over the tiles.  The last block to finish advances the step counter.
-template <typename R, int BS, bool DrawAhead, bool Rows = false>
+template <typename R, int BS, bool DrawAhead, int Mode = kGeneral>
 __global__ void __launch_bounds__(BS) k_corrector(const KArgs<R> a, int nfin) {
     __shared__ double red[(BS / 32) * 8];
     const uint64_t step = *a.step;
@@ -475,11 +483,11 @@ __global__ void __launch_bounds__(BS) k_corrector(const KArgs<R> a, int nfin) {
         __syncthreads();
         const int64_t nb = gridDim.x - nfin;
         for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb)
-            corrector_tile<R, BS, false, Rows>(a, a.tiles[t], step, &tab);
+            corrector_tile<R, BS, false, Mode>(a, a.tiles[t], step, &tab);
     } else {
         const int64_t nb = gridDim.x - nfin;
         for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb)
-            corrector_tile<R, BS, false, Rows>(a, a.tiles[t], step, nullptr);
+            corrector_tile<R, BS, false, Mode>(a, a.tiles[t], step, nullptr);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -508,7 +516,7 @@ __global__ void __launch_bounds__(BS) k_measure(const KArgs<R> a) {
             const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
             R e0, e1, e2;
             if (a.ex)
-                exchange_sum<R, false, true>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
+                exchange_sum<R, false, kRows>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
             else
                 exchange_sum<R, false>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
             R H0, H1, H2;

@@ -17,24 +17,28 @@ namespace ss {
 template <typename R>
 cudaError_t launch_predictor(const KArgs<R> &a, int block, int grid, cudaStream_t s) {
     if (a.ex) {
-        SS_BLOCK_SWITCH(block, k_predictor<R, BS, true><<<grid, BS, 0, s>>>(a));
+        SS_BLOCK_SWITCH(block, k_predictor<R, BS, kRows><<<grid, BS, 0, s>>>(a));
+    } else if (a.J_tensor || a.any_cubic) {
+        SS_BLOCK_SWITCH(block, k_predictor<R, BS, kGeneral><<<grid, BS, 0, s>>>(a));
     } else {
-        SS_BLOCK_SWITCH(block, k_predictor<R, BS><<<grid, BS, 0, s>>>(a));
+        SS_BLOCK_SWITCH(block, k_predictor<R, BS, kPlain><<<grid, BS, 0, s>>>(a));
     }
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s) {
-    if (a.ex && a.g_step != nullptr) {
-        SS_BLOCK_SWITCH(block, k_corrector<R, BS, true, true><<<grid + nfin, BS, 0, s>>>(a, nfin));
-    } else if (a.ex) {
-        SS_BLOCK_SWITCH(block, k_corrector<R, BS, false, true><<<grid + nfin, BS, 0, s>>>(a, nfin));
-    } else if (a.g_step != nullptr) {
-        SS_BLOCK_SWITCH(block, k_corrector<R, BS, true><<<grid + nfin, BS, 0, s>>>(a, nfin));
+    const int mode = a.ex ? kRows : (a.J_tensor || a.any_cubic) ? kGeneral : kPlain;
+    const bool ahead = a.g_step != nullptr;
+#define SS_CORRECTOR(DA, MODE) SS_BLOCK_SWITCH(block, k_corrector<R, BS, DA, MODE><<<grid + nfin, BS, 0, s>>>(a, nfin))
+    if (mode == kRows) {
+        if (ahead) { SS_CORRECTOR(true, kRows); } else { SS_CORRECTOR(false, kRows); }
+    } else if (mode == kGeneral) {
+        if (ahead) { SS_CORRECTOR(true, kGeneral); } else { SS_CORRECTOR(false, kGeneral); }
     } else {
-        SS_BLOCK_SWITCH(block, k_corrector<R, BS, false><<<grid + nfin, BS, 0, s>>>(a, nfin));
+        if (ahead) { SS_CORRECTOR(true, kPlain); } else { SS_CORRECTOR(false, kPlain); }
     }
+#undef SS_CORRECTOR
     return cudaGetLastError();
 }
 
@@ -64,39 +68,38 @@ int persistent_blocks_per_sm(int block) {
     return e == cudaSuccess ? nb : 0;
 }
 
+// Resident blocks per SM of the predictor variant (kPlain / kGeneral / kRows) launched.
 template <typename R>
-int step_blocks_per_sm(int block) {
+int step_blocks_per_sm(int block, int mode) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
-    switch (block) {
-        case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_predictor<R, 128>, 128, 0); break;
-        case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_predictor<R, 256>, 256, 0); break;
-        case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_predictor<R, 512>, 512, 0); break;
-        default: break;
+#define SS_OCC(MODE) SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_predictor<R, BS, MODE>, BS, 0))
+    if (mode == kRows) {
+        SS_OCC(kRows);
+    } else if (mode == kGeneral) {
+        SS_OCC(kGeneral);
+    } else {
+        SS_OCC(kPlain);
     }
+#undef SS_OCC
     return e == cudaSuccess ? nb : 0;
 }
 
 // Resident blocks per SM of the corrector variant the handle launches.
 template <typename R>
-int corrector_blocks_per_sm(int block, bool draw_ahead) {
+int corrector_blocks_per_sm(int block, bool draw_ahead, int mode) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
-    switch (block) {
-        case 128:
-            e = draw_ahead ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 128, true>, 128, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 128, false>, 128, 0);
-            break;
-        case 256:
-            e = draw_ahead ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 256, true>, 256, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 256, false>, 256, 0);
-            break;
-        case 512:
-            e = draw_ahead ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 512, true>, 512, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, 512, false>, 512, 0);
-            break;
-        default: break;
+#define SS_OCC(DA, MODE) \
+    SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector<R, BS, DA, MODE>, BS, 0))
+    if (mode == kRows) {
+        if (draw_ahead) { SS_OCC(true, kRows); } else { SS_OCC(false, kRows); }
+    } else if (mode == kGeneral) {
+        if (draw_ahead) { SS_OCC(true, kGeneral); } else { SS_OCC(false, kGeneral); }
+    } else {
+        if (draw_ahead) { SS_OCC(true, kPlain); } else { SS_OCC(false, kPlain); }
     }
+#undef SS_OCC
     return e == cudaSuccess ? nb : 0;
 }
 
@@ -198,8 +201,8 @@ template cudaError_t launch_measure<SS_REAL>(const KArgs<SS_REAL> &, int, int, c
 template cudaError_t launch_init_sphere<SS_REAL>(const KArgs<SS_REAL> &, cudaStream_t);
 template cudaError_t launch_persistent<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, long long, cudaStream_t);
 template int persistent_blocks_per_sm<SS_REAL>(int);
-template int step_blocks_per_sm<SS_REAL>(int);
-template int corrector_blocks_per_sm<SS_REAL>(int, bool);
+template int step_blocks_per_sm<SS_REAL>(int, int);
+template int corrector_blocks_per_sm<SS_REAL>(int, bool, int);
 template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
 template int mc_blocks_per_sm<SS_REAL>(int);
 template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);

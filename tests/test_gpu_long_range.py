@@ -149,3 +149,29 @@ def test_exec_modes_and_graphs(SS, lr9):
             s.set_exchange_rows("warp")
             assert s.info()["exec"] == 0
     assert np.array_equal(out["kernels"], out["graph"])
+
+
+def test_edge_cases_empty_rows_and_single_spins(SS, lr9):
+    """A batch mixing long rows with bond-free spins and a one-spin system: the slices holding
+    empty rows are padded, the free spins precess in the applied field alone; FP64 parity."""
+    free = L.SpinLattice(np.zeros(6, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0),
+                         np.full(5, 2 * 9.274e-24), np.full(5, 1e-23), np.tile([0.0, 0.0, 1.0], (5, 1)))
+    one = L.SpinLattice(np.zeros(2, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0),
+                        np.full(1, 2 * 9.274e-24), np.zeros(1), np.tile([0.0, 0.0, 1.0], (1, 1)))
+    lats = [free, lr9, one]
+    S0s = [L.random_state(l.n, 30 + k) for k, l in enumerate(lats)]
+    temps = [50.0, 300.0, 0.0]
+    H = [(0.0, 0.0, 1.0), (0.2, 0.0, 0.0), (1.0, 0.0, 0.0)]
+    with SS(lats, alpha=0.1, dt=1e-16, T=temps, H=H, seed=[4, 5, 6], sys_id=[0, 1, 2], S0=S0s,
+            precision="fp64") as b:
+        assert b.info()["exchange_rows"] == 3
+        b.step(30)
+        S_b = b.spins()
+        rec = b.record(0, 30)
+    off = 0
+    for k, lat in enumerate(lats):
+        ref = oracle_system(lat, H=H[k], seed=k + 4, sys_id=k)
+        S_ref, rec_ref = O.heun_run(ref, S0s[k], 30, temps[k], record=True)
+        assert np.abs(S_b[off:off + lat.n] - S_ref).max() <= 1e-12
+        assert np.abs(rec[:, k, 7] - rec_ref[:, 7]).max() <= 1e-12 * max(np.abs(rec_ref[:, 7]).max(), 1e-30)
+        off += lat.n
