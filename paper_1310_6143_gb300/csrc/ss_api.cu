@@ -459,8 +459,9 @@ int corrector_grid(const ss_system *h) {
 }
 
 int persistent_grid(const ss_system *h) {
-    const int per_sm = h->precision == SS_FP32_MIXED ? persistent_blocks_per_sm<float>(h->block)
-                                                     : persistent_blocks_per_sm<double>(h->block);
+    const int mode = std::min(step_mode(h), 1);  // never the rows variant
+    const int per_sm = h->precision == SS_FP32_MIXED ? persistent_blocks_per_sm<float>(h->block, mode)
+                                                     : persistent_blocks_per_sm<double>(h->block, mode);
     const int64_t g = (int64_t)h->sm_count * per_sm;
     return (int)std::max<int64_t>(0, std::min<int64_t>(h->ntiles, g));
 }
@@ -505,7 +506,7 @@ cudaError_t enqueue_kernels(ss_system *h, int64_t n) {
 template <typename R>
 cudaError_t enqueue_system_blocks(ss_system *h, int64_t n) {
     const KArgs<R> a = make_args<R>(h);
-    const int per_sm = std::max(1, step_blocks_per_sm<R>(h->block, 1));
+    const int per_sm = std::max(1, step_blocks_per_sm<R>(h->block, std::min(step_mode(h), 1)));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->nsys, (int64_t)h->sm_count * per_sm));
     while (n > 0) {
         const long long k = std::min<long long>(n, 1ll << 20);

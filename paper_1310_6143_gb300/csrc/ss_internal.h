@@ -169,7 +169,7 @@ template <typename R> cudaError_t launch_persistent(const KArgs<R> &a, int block
                                                     long long nsteps, cudaStream_t s);
 template <typename R> cudaError_t launch_system_blocks(const KArgs<R> &a, int block, int grid, long long nsteps,
                                                        cudaStream_t s);
-template <typename R> int persistent_blocks_per_sm(int block);
+template <typename R> int persistent_blocks_per_sm(int block, int mode);
 // mode: the step-kernel variant (0 plain, 1 general, 2 rows; kPlain / kGeneral / kRows)
 template <typename R> int step_blocks_per_sm(int block, int mode);
 template <typename R> int corrector_blocks_per_sm(int block, bool draw_ahead, int mode);

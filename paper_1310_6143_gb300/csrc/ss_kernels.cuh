@@ -612,7 +612,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int *
 // Many steps in one cooperative launch: predictor phase, barrier, corrector phase (with
 // the record of the step summed by blocks [0, nfin), and in the FP32-mixed form the back
 // half of the next step's Gaussians drawn ahead), barrier.
-template <typename R, int BS>
+template <typename R, int BS, int Mode = kGeneral>
 __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, long long nsteps) {
     __shared__ SmemTables tab;
     __shared__ double red[kTileChunk * (BS / 32) * 8];
@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
     for (long long k = 0; k < nsteps; ++k) {
         const uint64_t step = step0 + (uint64_t)k;
         const int pre_slot = k == 0 ? pre_first : (ahead ? a.pre_slot : 1 << 30);
-        predictor_pass<R, BS, true>(a, step, tab, pre_slot, red);
+        predictor_pass<R, BS, true, Mode>(a, step, tab, pre_slot, red);
         if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
         if ((int)blockIdx.x < nfin) {
             for (int s = blockIdx.x; s < a.nsys; s += nfin) {
@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
             }
         }
         for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x)
-            corrector_tile<R, BS, true>(a, a.tiles[t], step, ahead ? &tab : nullptr);
+            corrector_tile<R, BS, true, Mode>(a, a.tiles[t], step, ahead ? &tab : nullptr);
         if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
 // systems are independent).  Every spin a block reads was written by the same block, after
 // a block barrier; loads bypass the non-coherent L1.  Each step's record is summed in the
 // block directly.  The last block to finish advances the step counter.
-template <typename R, int BS>
+template <typename R, int BS, int Mode = kGeneral>
 __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long long nsteps) {
     __shared__ SmemTables tab;
     __shared__ double red[(BS / 32) * 8];
@@ -664,10 +664,10 @@ __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long lon
         for (long long k = 0; k < nsteps; ++k) {
             const uint64_t step = step0 + (uint64_t)k;
             double acc[8];
-            predictor_tile<R, BS, true>(a, whole, step, tab, 1 << 30, acc);
+            predictor_tile<R, BS, true, Mode>(a, whole, step, tab, 1 << 30, acc);
             const double r = block_sum8<BS>(acc, red);
             write_record(sd, r, a.rec + ((int64_t)(step % (uint64_t)a.rec_cap) * a.nsys + s) * kRecComps);
-            corrector_tile<R, BS, true>(a, whole, step, nullptr);
+            corrector_tile<R, BS, true, Mode>(a, whole, step, nullptr);
             __syncthreads();
         }
     }

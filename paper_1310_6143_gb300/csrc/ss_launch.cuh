@@ -55,15 +55,15 @@ cudaError_t launch_init_sphere(const KArgs<R> &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// (the persistent and system-block kernels come as kPlain and kGeneral variants only)
 template <typename R>
-int persistent_blocks_per_sm(int block) {
+int persistent_blocks_per_sm(int block, int mode) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
-    switch (block) {
-        case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, 128>, 128, 0); break;
-        case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, 256>, 256, 0); break;
-        case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, 512>, 512, 0); break;
-        default: break;
+    if (mode == kPlain) {
+        SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, BS, kPlain>, BS, 0));
+    } else {
+        SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, BS, kGeneral>, BS, 0));
     }
     return e == cudaSuccess ? nb : 0;
 }
@@ -183,14 +183,23 @@ template <typename R>
 cudaError_t launch_persistent(const KArgs<R> &a, int block, int grid, int nfin, long long nsteps, cudaStream_t s) {
     KArgs<R> args = a;
     void *params[] = {(void *)&args, (void *)&nfin, (void *)&nsteps};
-    SS_BLOCK_SWITCH(block, return cudaLaunchCooperativeKernel((const void *)k_persistent<R, BS>, dim3(grid),
-                                                              dim3(BS), params, 0, s));
+    if (a.J_tensor || a.any_cubic) {
+        SS_BLOCK_SWITCH(block, return cudaLaunchCooperativeKernel((const void *)k_persistent<R, BS, kGeneral>, dim3(grid),
+                                                                  dim3(BS), params, 0, s));
+    } else {
+        SS_BLOCK_SWITCH(block, return cudaLaunchCooperativeKernel((const void *)k_persistent<R, BS, kPlain>, dim3(grid),
+                                                                  dim3(BS), params, 0, s));
+    }
     return cudaSuccess;
 }
 
 template <typename R>
 cudaError_t launch_system_blocks(const KArgs<R> &a, int block, int grid, long long nsteps, cudaStream_t s) {
-    SS_BLOCK_SWITCH(block, k_system_blocks<R, BS><<<grid, BS, 0, s>>>(a, nsteps));
+    if (a.J_tensor || a.any_cubic) {
+        SS_BLOCK_SWITCH(block, k_system_blocks<R, BS, kGeneral><<<grid, BS, 0, s>>>(a, nsteps));
+    } else {
+        SS_BLOCK_SWITCH(block, k_system_blocks<R, BS, kPlain><<<grid, BS, 0, s>>>(a, nsteps));
+    }
     return cudaGetLastError();
 }
 
@@ -200,7 +209,7 @@ template cudaError_t launch_corrector<SS_REAL>(const KArgs<SS_REAL> &, int, int,
 template cudaError_t launch_measure<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_init_sphere<SS_REAL>(const KArgs<SS_REAL> &, cudaStream_t);
 template cudaError_t launch_persistent<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, long long, cudaStream_t);
-template int persistent_blocks_per_sm<SS_REAL>(int);
+template int persistent_blocks_per_sm<SS_REAL>(int, int);
 template int step_blocks_per_sm<SS_REAL>(int, int);
 template int corrector_blocks_per_sm<SS_REAL>(int, bool, int);
 template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
