@@ -828,27 +828,38 @@ __global__ void __launch_bounds__(256) k_rows_field(const KArgs<R> a, const R *X
 // held; nothing is renormalised (f(m) is perpendicular to m).
 // ----------------------------------------------------------------------------------
 
-// sum_j (J_ij / mu_s,i) X_j over row i (scalar or tensor bonds), without the applied field.
-template <typename R>
+// sum_j (J_ij / mu_s,i) X_j over row i (scalar or tensor bonds, kPlain: scalar only), without
+// the applied field; one FMA per bond and component in CSR order.
+template <typename R, int Mode>
 __device__ __forceinline__ void exchange_bare(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int64_t i,
                                               R &e0, R &e1, R &e2) {
     const int32_t b = __ldg(a.row_ptr + i);
     const int32_t e = __ldg(a.row_ptr + i + 1);
     R x = 0, y = 0, z = 0;
-#pragma unroll 2
-    for (int32_t k = b; k < e; ++k) {
-        const int32_t j = __ldg(a.col + k);
-        const R m0 = X[j], m1 = Y[j], m2 = Z[j];
-        if (a.J_tensor) {
+    if (Mode != kPlain && a.J_tensor) {
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t j = __ldg(a.col + k);
+            const R m0 = X[j], m1 = Y[j], m2 = Z[j];
             const R *t = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + k);
             x = fma(__ldg(t + 0), m0, fma(__ldg(t + 1), m1, fma(__ldg(t + 2), m2, x)));
             y = fma(__ldg(t + 3), m0, fma(__ldg(t + 4), m1, fma(__ldg(t + 5), m2, y)));
             z = fma(__ldg(t + 6), m0, fma(__ldg(t + 7), m1, fma(__ldg(t + 8), m2, z)));
-        } else {
-            const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + k);
-            x = fma(Jk, m0, x);
-            y = fma(Jk, m1, y);
-            z = fma(Jk, m2, z);
+        }
+    } else if (a.J_uniform) {
+        const R Jk = a.J_value;
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t j = __ldg(a.col + k);
+            x = fma(Jk, X[j], x);
+            y = fma(Jk, Y[j], y);
+            z = fma(Jk, Z[j], z);
+        }
+    } else {
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t j = __ldg(a.col + k);
+            const R Jk = __ldg(a.J + k);
+            x = fma(Jk, X[j], x);
+            y = fma(Jk, Y[j], y);
+            z = fma(Jk, Z[j], z);
         }
     }
     e0 = x;
@@ -860,7 +871,7 @@ __device__ __forceinline__ void exchange_bare(const KArgs<R> &a, const R *X, con
 // the midpoint field that stays fixed over the step, C = H_app + H_th + (1/2) sum_j J_ij S_j
 // (the exchange field is linear, so the field of m = (S + X)/2 is C + (1/2) sum_j J_ij X_j
 // plus the on-site terms of m), stored in (hx, hy, hz).
-template <typename R>
+template <typename R, int Mode>
 __global__ void k_mid_euler(const KArgs<R> a) {
     __shared__ SmemTables tab;
     stage_tables(a, tab);
@@ -882,13 +893,13 @@ __global__ void k_mid_euler(const KArgs<R> a) {
         }
         const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
         R x0, x1, x2;
-        exchange_bare(a, a.sx, a.sy, a.sz, i, x0, x1, x2);
+        exchange_bare<R, Mode>(a, a.sx, a.sy, a.sz, i, x0, x1, x2);
         const R c0 = sys_H(sd, 0, R()) + t0, c1 = sys_H(sd, 1, R()) + t1, c2 = sys_H(sd, 2, R()) + t2;
         a.hx[i] = fma((R)0.5, x0, c0);
         a.hy[i] = fma((R)0.5, x1, c1);
         a.hz[i] = fma((R)0.5, x2, c2);
         R H0, H1, H2;
-        det_field(m, s0, s1, s2, x0 + c0, x1 + c1, x2 + c2, H0, H1, H2);
+        det_field<R, Mode != kPlain>(m, s0, s1, s2, x0 + c0, x1 + c1, x2 + c2, H0, H1, H2);
         R d0, d1, d2;
         llg_rhs(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, d0, d1, d2);
         a.px[i] = fma(m.dt, d0, s0);
@@ -900,16 +911,16 @@ __global__ void k_mid_euler(const KArgs<R> a) {
 // One fixed-point iteration: Y = S + dt f(m), m = (S + X)/2, with the field C + (1/2) sum_j J_ij X_j
 // plus the on-site terms of m.  A thread reads S only at its own spin, so the last iteration
 // writes Y over S (Last: and flags non-finite spins).
-template <typename R, bool Last>
+template <typename R, int Mode, bool Last>
 __global__ void k_mid_iter(const KArgs<R> a, const R *xx, const R *xy, const R *xz, R *yx, R *yy, R *yz) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
         const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
         const R m0 = (R)0.5 * (s0 + xx[i]), m1 = (R)0.5 * (s1 + xy[i]), m2 = (R)0.5 * (s2 + xz[i]);
         R x0, x1, x2;
-        exchange_bare(a, xx, xy, xz, i, x0, x1, x2);
+        exchange_bare<R, Mode>(a, xx, xy, xz, i, x0, x1, x2);
         R H0, H1, H2;
-        det_field(m, m0, m1, m2, fma((R)0.5, x0, a.hx[i]), fma((R)0.5, x1, a.hy[i]), fma((R)0.5, x2, a.hz[i]), H0,
+        det_field<R, Mode != kPlain>(m, m0, m1, m2, fma((R)0.5, x0, a.hx[i]), fma((R)0.5, x1, a.hy[i]), fma((R)0.5, x2, a.hz[i]), H0,
                   H1, H2);
         R d0, d1, d2;
         llg_rhs(m.gp, m.lambda, m0, m1, m2, H0, H1, H2, d0, d1, d2);

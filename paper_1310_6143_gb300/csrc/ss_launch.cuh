@@ -120,13 +120,13 @@ cudaError_t launch_demag(const KArgs<R> &a, const DemagArgs &d, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t s) {
-    k_mid_euler<R><<<grid, 256, 0, s>>>(a);
+template <typename R, int Mode>
+cudaError_t launch_midpoint_mode(const KArgs<R> &a, int iters, int grid, cudaStream_t s) {
+    k_mid_euler<R, Mode><<<grid, 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     R *x[3] = {a.px, a.py, a.pz}, *y[3] = {a.qx, a.qy, a.qz};
     for (int k = 0; k + 1 < iters && e == cudaSuccess; ++k) {
-        k_mid_iter<R, false><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], y[0], y[1], y[2]);
+        k_mid_iter<R, Mode, false><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], y[0], y[1], y[2]);
         e = cudaGetLastError();
         for (int c = 0; c < 3; ++c) {
             R *t = x[c];
@@ -135,10 +135,16 @@ cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t
         }
     }
     if (e == cudaSuccess) {  // the last iterate goes straight to S
-        k_mid_iter<R, true><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], a.sx, a.sy, a.sz);
+        k_mid_iter<R, Mode, true><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], a.sx, a.sy, a.sz);
         e = cudaGetLastError();
     }
     return e;
+}
+
+template <typename R>
+cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t s) {
+    return (a.J_tensor || a.any_cubic) ? launch_midpoint_mode<R, kGeneral>(a, iters, grid, s)
+                                       : launch_midpoint_mode<R, kPlain>(a, iters, grid, s);
 }
 
 template <typename R>
