@@ -439,6 +439,8 @@ void drop_graph(ss_system *h) {
 
 // The step-kernel variant the launchers pick for this handle (0 plain, 1 general, 2 rows).
 int step_mode(const ss_system *h) { return h->rows ? 2 : (h->J_tensor || h->any_cubic) ? 1 : 0; }
+// The variant of the kernels that sum their own rows (Monte Carlo, persistent, system blocks).
+int own_rows_mode(const ss_system *h) { return (h->J_tensor || h->any_cubic) ? 1 : 0; }
 
 int step_grid(const ss_system *h) {
     const int mode = step_mode(h);
@@ -459,7 +461,7 @@ int corrector_grid(const ss_system *h) {
 }
 
 int persistent_grid(const ss_system *h) {
-    const int mode = std::min(step_mode(h), 1);  // never the rows variant
+    const int mode = own_rows_mode(h);
     const int per_sm = h->precision == SS_FP32_MIXED ? persistent_blocks_per_sm<float>(h->block, mode)
                                                      : persistent_blocks_per_sm<double>(h->block, mode);
     const int64_t g = (int64_t)h->sm_count * per_sm;
@@ -506,7 +508,7 @@ cudaError_t enqueue_kernels(ss_system *h, int64_t n) {
 template <typename R>
 cudaError_t enqueue_system_blocks(ss_system *h, int64_t n) {
     const KArgs<R> a = make_args<R>(h);
-    const int per_sm = std::max(1, step_blocks_per_sm<R>(h->block, std::min(step_mode(h), 1)));
+    const int per_sm = std::max(1, step_blocks_per_sm<R>(h->block, own_rows_mode(h)));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->nsys, (int64_t)h->sm_count * per_sm));
     while (n > 0) {
         const long long k = std::min<long long>(n, 1ll << 20);
@@ -1343,7 +1345,7 @@ cudaError_t enqueue_mc(ss_system *h, int64_t nsteps) {
     m.par_sched = h->mc_sched;
     m.acc = h->mc_acc;
     const int block = 256;
-    const int64_t resident = (int64_t)h->sm_count * std::max(1, mc_blocks_per_sm<R>(block));
+    const int64_t resident = (int64_t)h->sm_count * std::max(1, mc_blocks_per_sm<R>(block, own_rows_mode(h)));
     const int gmeas = step_grid(h);
     const int ncol = (int)h->mc_cstart.size() - 1;
     cudaError_t e = cudaSuccess;

@@ -175,7 +175,7 @@ template <typename R> int step_blocks_per_sm(int block, int mode);
 template <typename R> int corrector_blocks_per_sm(int block, bool draw_ahead, int mode);
 template <typename R> cudaError_t launch_mc_colour(const KArgs<R> &a, const McArgs &m, int block, int grid,
                                                    cudaStream_t s);
-template <typename R> int mc_blocks_per_sm(int block);
+template <typename R> int mc_blocks_per_sm(int block, int mode);  // mode: kPlain or kGeneral
 cudaError_t launch_advance_step(unsigned long long *step, cudaStream_t s);
 template <typename R> cudaError_t launch_demag(const KArgs<R> &a, const DemagArgs &d, cudaStream_t s);
 // One midpoint step's launches after its record: Euler predictor, `iters` fixed-point

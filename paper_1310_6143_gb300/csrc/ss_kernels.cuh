@@ -1026,7 +1026,7 @@ __global__ void k_demag_field(const KArgs<R> a, const DemagArgs d) {
 // Spins of one colour share no bond, so each trial reads only spins of other colours.
 // dE is the change of site i's Hamiltonian terms: exchange and applied field through the
 // field h = H_app + sum_j (J_ij / mu_s,i) S_j, then anisotropy and the Neel term.
-template <typename R, int BS>
+template <typename R, int BS, int Mode = kGeneral>
 __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs m) {
     __shared__ SmemTables tab;
     stage_tables(a, tab);
@@ -1084,7 +1084,7 @@ __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs
             n2 *= inv;
         }
         R h0, h1, h2;
-        exchange_sum<R, false>(a, sd, a.sx, a.sy, a.sz, i, h0, h1, h2);
+        exchange_sum<R, false, Mode>(a, sd, a.sx, a.sy, a.sz, i, h0, h1, h2);
         // quadratic terms as (n - s).(A (n + s)): exactly zero when the spin is unchanged or
         // flipped, whatever the contraction of products into FMAs
         const R d0 = n0 - s0, d1 = n1 - s1, d2 = n2 - s2;
@@ -1092,7 +1092,7 @@ __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs
         const R de = d0 * mt.e[0] + d1 * mt.e[1] + d2 * mt.e[2];
         const R pe = p0 * mt.e[0] + p1 * mt.e[1] + p2 * mt.e[2];
         R dE = -mt.mu * (d0 * h0 + d1 * h1 + d2 * h2) - mt.ku * (de * pe);
-        if (mt.has_cubic) {  // (k_c/2) sum (n^4 - s^4), n^4 - s^4 = (n - s)(n + s)(n^2 + s^2)
+        if (Mode != kPlain && mt.has_cubic) {  // (k_c/2) sum (n^4 - s^4), n^4 - s^4 = (n - s)(n + s)(n^2 + s^2)
             dE += (R)0.5 * mt.kc * (d0 * p0 * (n0 * n0 + s0 * s0) + d1 * p1 * (n1 * n1 + s1 * s1)
                                     + d2 * p2 * (n2 * n2 + s2 * s2));
         }

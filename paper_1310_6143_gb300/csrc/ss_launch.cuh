@@ -105,7 +105,11 @@ int corrector_blocks_per_sm(int block, bool draw_ahead, int mode) {
 
 template <typename R>
 cudaError_t launch_mc_colour(const KArgs<R> &a, const McArgs &m, int block, int grid, cudaStream_t s) {
-    SS_BLOCK_SWITCH(block, k_mc_colour<R, BS><<<grid, BS, 0, s>>>(a, m));
+    if (a.J_tensor || a.any_cubic) {
+        SS_BLOCK_SWITCH(block, k_mc_colour<R, BS, kGeneral><<<grid, BS, 0, s>>>(a, m));
+    } else {
+        SS_BLOCK_SWITCH(block, k_mc_colour<R, BS, kPlain><<<grid, BS, 0, s>>>(a, m));
+    }
     return cudaGetLastError();
 }
 
@@ -173,14 +177,13 @@ int rows_blocks_per_sm() {
 }
 
 template <typename R>
-int mc_blocks_per_sm(int block) {
+int mc_blocks_per_sm(int block, int mode) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
-    switch (block) {
-        case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc_colour<R, 128>, 128, 0); break;
-        case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc_colour<R, 256>, 256, 0); break;
-        case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc_colour<R, 512>, 512, 0); break;
-        default: break;
+    if (mode == kPlain) {
+        SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc_colour<R, BS, kPlain>, BS, 0));
+    } else {
+        SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mc_colour<R, BS, kGeneral>, BS, 0));
     }
     return e == cudaSuccess ? nb : 0;
 }
@@ -219,7 +222,7 @@ template int persistent_blocks_per_sm<SS_REAL>(int, int);
 template int step_blocks_per_sm<SS_REAL>(int, int);
 template int corrector_blocks_per_sm<SS_REAL>(int, bool, int);
 template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
-template int mc_blocks_per_sm<SS_REAL>(int);
+template int mc_blocks_per_sm<SS_REAL>(int, int);
 template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
 template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_rows_field<SS_REAL>(const KArgs<SS_REAL> &, const SS_REAL *, const SS_REAL *,
