@@ -18,6 +18,7 @@ from .oracle import (  # noqa: F401
     moment_energy,
     heun_run,
     midpoint_run,
+    sib_run,
     set_threads,
     max_threads,
     colour_greedy,

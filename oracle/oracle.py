@@ -96,6 +96,8 @@ def _load():
             lib.orc_midpoint_run.argtypes = [ctypes.POINTER(_CSys), P, ctypes.c_int64, ctypes.c_int64, P,
                                              ctypes.c_int, P]
             lib.orc_midpoint_run.restype = ctypes.c_int
+            lib.orc_sib_run.argtypes = [ctypes.POINTER(_CSys), P, ctypes.c_int64, ctypes.c_int64, P, P]
+            lib.orc_sib_run.restype = ctypes.c_int
             lib.orc_macrocells.argtypes = [ctypes.POINTER(_CSys), P]
             lib.orc_macrocells.restype = ctypes.c_int64
             lib.orc_demag_fields.argtypes = [ctypes.POINTER(_CSys), P, P, P]
@@ -273,6 +275,19 @@ def midpoint_run(system: OracleSystem, S: np.ndarray, nsteps: int, T, iters: int
     c = system._c()
     rc = _load().orc_midpoint_run(ctypes.byref(c), _ptr(S), int(step0), int(nsteps), _ptr(Tarr), int(iters),
                                   _ptr(rec))
+    if rc != 0:
+        raise MemoryError("oracle: allocation failed")
+    return S, rec
+
+
+def sib_run(system: OracleSystem, S: np.ndarray, nsteps: int, T, step0: int = 0, record: bool = False):
+    """Advance ``nsteps`` semi-implicit predictor-corrector steps (Mentink et al.'s scheme B);
+    returns (S_new, rec or None) as heun_run."""
+    S = np.array(S, dtype=np.float64, copy=True).reshape(system.n, 3)
+    Tarr = np.ascontiguousarray(np.broadcast_to(np.asarray(T, dtype=np.float64), (nsteps,)))
+    rec = np.zeros((nsteps, 8)) if record else None
+    c = system._c()
+    rc = _load().orc_sib_run(ctypes.byref(c), _ptr(S), int(step0), int(nsteps), _ptr(Tarr), _ptr(rec))
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
     return S, rec

@@ -107,6 +107,19 @@
  *       S_{n+1} = S^(K); nothing is renormalised.
  *   I3  The record holds the state at the start of each step (R7).
  *
+ * Semi-implicit predictor-corrector (the modified predictor-corrector midpoint scheme the
+ * paper cites, Mentink et al. 2010, their scheme B), readings:
+ *   P1  Eq. LLG written as dS/dt = S x A(S), A(S) = -gamma/(1+lambda^2) (H + lambda S x H),
+ *       H the deterministic field of S plus the thermal field of R4 (drawn once per step from
+ *       the same Philox counters, held over the step).
+ *   P2  Predictor: S' = S_n + (dt/2) (S_n + S') x A(S_n); corrector: S_{n+1} = S_n +
+ *       (dt/2) (S_n + S_{n+1}) x A(Sb), Sb = (S_n + S')/2 (the field and the damping term
+ *       both at Sb, which is not renormalised).  Each is a 3x3 linear equation in the new
+ *       spin, solved in closed form: with b = (dt/2) A and c = S_n + S_n x b, the new spin is
+ *       (c - b x c + (b.c) b)/(1 + |b|^2), a rotation of S_n, so |S| is kept without
+ *       renormalisation.
+ *   P3  The record holds the state at the start of each step (R7).
+ *
  * Layout: spins and vectors are array-of-structures, 3 doubles per site (x, y, z).
  * Neel tensors are 6 doubles per site in the order xx, yy, zz, xy, xz, yz.
  *
@@ -607,6 +620,74 @@ int orc_midpoint_run(const orc_system *s, double *S, int64_t step0, int64_t nste
         memcpy(S, X, sz);
     }
     free(Hth); free(X); free(Y); free(M);
+    return 0;
+}
+
+/* A(S) of P1 at spin S with field H, and the solution X of X = S_n + (dt/2)(S_n + X) x A (P2). */
+static void orc_sib_a(double gamma, double lambda, const double S[3], const double H[3], double A[3]) {
+    double g = -gamma / (1.0 + lambda * lambda);
+    double sxh0 = S[1] * H[2] - S[2] * H[1];
+    double sxh1 = S[2] * H[0] - S[0] * H[2];
+    double sxh2 = S[0] * H[1] - S[1] * H[0];
+    A[0] = g * (H[0] + lambda * sxh0);
+    A[1] = g * (H[1] + lambda * sxh1);
+    A[2] = g * (H[2] + lambda * sxh2);
+}
+
+static void orc_sib_solve(double dt, const double Sn[3], const double A[3], double X[3]) {
+    double b[3] = {0.5 * dt * A[0], 0.5 * dt * A[1], 0.5 * dt * A[2]};
+    /* c = S_n + S_n x b */
+    double c[3] = {Sn[0] + (Sn[1] * b[2] - Sn[2] * b[1]), Sn[1] + (Sn[2] * b[0] - Sn[0] * b[2]),
+                   Sn[2] + (Sn[0] * b[1] - Sn[1] * b[0])};
+    double bc = b[0] * c[0] + b[1] * c[1] + b[2] * c[2];
+    double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    double bxc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+    for (int k = 0; k < 3; ++k) X[k] = (c[k] - bxc[k] + bc * b[k]) / (1.0 + bb);
+}
+
+/*
+ * Advance nsteps semi-implicit predictor-corrector steps (P1-P3) from step index step0; S [3n]
+ * is updated in place, T and rec as orc_heun_run.  Returns 0, or -1 if memory could not be
+ * allocated.
+ */
+int orc_sib_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, const double *T, double *rec) {
+    int64_t n = s->n;
+    size_t sz = sizeof(double) * 3 * (size_t)(n > 0 ? n : 1);
+    double *Hth = (double *)malloc(sz), *P = (double *)malloc(sz), *M = (double *)malloc(sz);
+    double *X = (double *)malloc(sz);
+    if (!Hth || !P || !M || !X) {
+        free(Hth); free(P); free(M); free(X);
+        return -1;
+    }
+    double gamma = s->gamma > 0.0 ? s->gamma : ORC_GAMMA;
+    double lambda = s->alpha;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        uint32_t step = (uint32_t)(step0 + k);
+        if (rec) orc_moment_energy(s, S, rec + 8 * k);
+        orc_thermal_field(s, step, T[k], gamma, lambda, Hth);
+        /* predictor with A(S_n) */
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+        for (int64_t i = 0; i < n; ++i) {
+            double hex[3], H[3], A[3];
+            orc_site_field(s, S, i, hex, H);
+            for (int c = 0; c < 3; ++c) H[c] += Hth[3 * i + c];
+            orc_sib_a(gamma, lambda, S + 3 * i, H, A);
+            orc_sib_solve(s->dt, S + 3 * i, A, P + 3 * i);
+        }
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+        for (int64_t i = 0; i < 3 * n; ++i) M[i] = 0.5 * (S[i] + P[i]);
+        /* corrector with A(Sb), Sb = (S_n + S')/2 */
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+        for (int64_t i = 0; i < n; ++i) {
+            double hex[3], H[3], A[3];
+            orc_site_field(s, M, i, hex, H);
+            for (int c = 0; c < 3; ++c) H[c] += Hth[3 * i + c];
+            orc_sib_a(gamma, lambda, M + 3 * i, H, A);
+            orc_sib_solve(s->dt, S + 3 * i, A, X + 3 * i);
+        }
+        memcpy(S, X, sz);
+    }
+    free(Hth); free(P); free(M); free(X);
     return 0;
 }
 

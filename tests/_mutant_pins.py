@@ -349,9 +349,50 @@ def pin_midpoint():
     return e[1] < 1e-11 and e[0] > 1e3 * e[1]
 
 
+def pin_sib():
+    """Semi-implicit predictor-corrector: undamped precession is the Cayley rotation, the
+    damped single spin converges at second order, and a spin with anisotropy follows the
+    scheme's two linear equations solved independently."""
+    H = 10.0
+    w = GAMMA * H
+    one = lambda lam, dt, ku=0.0, Happ=(0.0, 0.0, H), axis=(0, 0, 1): O.OracleSystem(  # noqa: E731
+        np.zeros(2, dtype=np.int64), np.zeros(0, np.int32), np.zeros(0), [MU], ku, axis, alpha=lam, dt=dt,
+        H_app=Happ)
+    S, _ = O.sib_run(one(0.0, 0.1 / w), np.array([[0.6, 0.0, 0.8]]), 100, 0.0)
+    if abs(np.angle(np.exp(1j * (np.arctan2(S[0, 1], S[0, 0]) - 200 * np.arctan(0.05))))) > 1e-10:
+        return False
+    errs = []
+    for dt in (4e-15, 2e-15):
+        S, _ = O.sib_run(one(0.1, dt), np.array([[1.0, 0.0, 0.0]]), int(round(20e-12 / dt)), 0.0)
+        a_, w_ = 0.1 * w / 1.01 * 20e-12, w / 1.01 * 20e-12
+        errs.append(np.abs(S[0] - [np.cos(w_) / np.cosh(a_), np.sin(w_) / np.cosh(a_), np.tanh(a_)]).max())
+    if not 3.5 < errs[0] / errs[1] < 4.5:
+        return False
+    lam, ku, dt = 0.3, 2e-23, 2e-15
+    e = np.array([0.3, -0.2, 0.9]) / np.linalg.norm([0.3, -0.2, 0.9])
+    Happ = np.array([0.4, 1.1, -0.7])
+
+    def A(v):
+        Hf = Happ + 2 * ku / MU * (v @ e) * e
+        return -GAMMA / (1 + lam ** 2) * (Hf + lam * np.cross(v, Hf))
+
+    def half(Sn, a):
+        K = np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+        return np.linalg.solve(np.eye(3) + (dt / 2) * K, Sn - (dt / 2) * np.cross(a, Sn))
+
+    ref = np.array([0.48, 0.6, 0.64])
+    S0 = ref.copy()
+    for _ in range(10):
+        P = half(ref, A(ref))
+        ref = half(ref, A(0.5 * (ref + P)))
+    got, _ = O.sib_run(one(lam, dt, ku, tuple(Happ), tuple(e)), S0[None], 10, 0.0)
+    return np.abs(got[0] - ref).max() <= 1e-13
+
+
 PINS = [pin_field_gradient, pin_single_spin_analytic, pin_unit_length, pin_gaussians, pin_philox_against_torch,
         pin_boltzmann, pin_curie, pin_mc_boltzmann, pin_mc_langevin, pin_mc_dimer, pin_mc_moves, pin_mc_sigma,
-        pin_mc_zero_T, pin_colouring, pin_demag, pin_tensor_cubic, pin_mc_cubic, pin_midpoint]
+        pin_mc_zero_T, pin_colouring, pin_demag, pin_tensor_cubic, pin_mc_cubic, pin_midpoint,
+        pin_sib]
 
 if __name__ == "__main__":
     for p in PINS:

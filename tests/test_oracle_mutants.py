@@ -82,6 +82,13 @@ MUTANTS = [
     # midpoint integrator
     ("midpoint iteration on S^(k) instead of the midpoint", "M[i] = 0.5 * (S[i] + X[i]);", "M[i] = X[i];"),
     ("midpoint iterations skipped", "        for (int it = 0; it < iters; ++it) {", "        for (int it = 0; it < 0; ++it) {"),
+    # semi-implicit predictor-corrector
+    ("semi-implicit corrector with the field at S_n", "            orc_site_field(s, M, i, hex, H);\n            for (int c = 0; c < 3; ++c) H[c] += Hth[3 * i + c];\n            orc_sib_a(gamma, lambda, M + 3 * i, H, A);",
+     "            orc_site_field(s, S, i, hex, H);\n            for (int c = 0; c < 3; ++c) H[c] += Hth[3 * i + c];\n            orc_sib_a(gamma, lambda, M + 3 * i, H, A);"),
+    ("semi-implicit damping term at S_n in the corrector", "            orc_sib_a(gamma, lambda, M + 3 * i, H, A);",
+     "            orc_sib_a(gamma, lambda, S + 3 * i, H, A);"),
+    ("semi-implicit solve with b x c added", "X[k] = (c[k] - bxc[k] + bc * b[k]) / (1.0 + bb);",
+     "X[k] = (c[k] + bxc[k] + bc * b[k]) / (1.0 + bb);"),
 ]
 
 
