@@ -235,6 +235,18 @@ ss_status get_mc_stats(ss_system *h, int32_t sys, int64_t out[2]);
  * field switched on (set_demag), which this rule does not include. */
 ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations);
 
+/* Advance every system by n >= 0 steps of the semi-implicit predictor-corrector scheme
+ * (asynchronous; the modified predictor-corrector midpoint scheme of Mentink et al. that the
+ * paper's time-integration section cites).  With Eq. LLG written as dS/dt = S x A(S),
+ * A = -gamma/(1+alpha^2) (H + alpha S x H), the predictor solves
+ * S' = S_n + (dt/2)(S_n + S') x A(S_n) and the corrector S_{n+1} = S_n + (dt/2)(S_n + S_{n+1})
+ * x A(Sb), Sb = (S_n + S')/2, each in closed form (a rotation of S_n: |S| is kept without
+ * renormalisation); H includes the step's thermal field, drawn once per step from the same
+ * Philox counters as llg_heun_step and held over the step.  Shares the step counter, record
+ * ring and temperatures with llg_heun_step; 5 launches per step, captured in CUDA graphs for
+ * runs of whole graphs.  SS_ERR_INVALID_ARG for n < 0 or with the demagnetising field on. */
+ss_status llg_semi_implicit_step(ss_system *h, int64_t n);
+
 /* Copy all spins (concatenated over systems) to out3n [3n], AoS, FP64 (synchronous). */
 ss_status get_spins(ss_system *h, double *out3n);
 

@@ -29,7 +29,7 @@ EXPORTS = (
     "spin_system_set_exec", "spin_system_set_launch", "spin_system_autotune", "spin_system_info",
     "spin_system_set_barrier_test", "spin_system_sync", "spin_system_time_kernels", "ss_debug_philox", "ss_debug_gaussians",
     "llg_heun_step_noalloc", "spin_system_set_draw_ahead", "ss_debug_fp64_rate", "mc_step", "get_mc_stats", "set_demag", "llg_midpoint_step",
-    "spin_system_set_exchange_rows", "spin_system_time_rows",
+    "spin_system_set_exchange_rows", "spin_system_time_rows", "llg_semi_implicit_step",
     "get_demag_field",
     "ss_last_error", "ss_status_string",
 )
@@ -116,6 +116,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "llg_heun_step": [P, I64],
         "mc_step": [P, I64],
         "llg_midpoint_step": [P, I64, I32],
+        "llg_semi_implicit_step": [P, I64],
         "get_mc_stats": [P, I32, P],
         "set_demag": [P, D, D, I32],
         "get_demag_field": [P, P],

@@ -147,7 +147,8 @@ struct ss_system {
     // launch state
     int nfin = 1;
     cudaGraphExec_t graph = nullptr;
-    cudaGraphExec_t midgraph = nullptr; // captured midpoint steps (midgraph_iters iterations each)
+    cudaGraphExec_t midgraph = nullptr; // captured midpoint (midgraph_iters iterations each) or
+                                        // semi-implicit (midgraph_iters = -1) steps
     int midgraph_steps = 0, midgraph_iters = 0;
     bool midgraph_failed = false;
     cudaGraphExec_t mcgraph = nullptr;  // captured Monte Carlo steps
@@ -1334,6 +1335,67 @@ cudaError_t enqueue_midpoint(ss_system *h, int64_t nsteps, int iterations) {
     return e;
 }
 
+// Steps of an alternative integrator, enqueued by `enqueue` (k steps per call): runs of whole
+// graphs are captured once (per integrator variant `key`) and replayed; the launches hold no
+// host-side step.
+template <typename F>
+ss_status integrate_captured(ss_system *h, int64_t n, int key, F enqueue, const char *what) {
+    cudaError_t e = cudaSuccess;
+    int64_t left = n;
+    const int g = graph_len(h);
+    if (left >= g && !h->midgraph_failed && h->exec != SS_EXEC_KERNELS) {
+        if (h->midgraph && h->midgraph_iters != key) {
+            cudaGraphExecDestroy(h->midgraph);
+            h->midgraph = nullptr;
+        }
+        if (!h->midgraph) {
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t ek = enqueue(g);
+                e = cudaStreamEndCapture(h->stream, &graph);
+                if (ek != cudaSuccess) e = ek;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->midgraph, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                h->midgraph = nullptr;
+                h->midgraph_failed = true;  // capture refused: launch directly from now on
+                e = cudaSuccess;
+            } else {
+                h->midgraph_steps = g;
+                h->midgraph_iters = key;
+            }
+        }
+        while (h->midgraph && left >= h->midgraph_steps && e == cudaSuccess) {
+            e = cudaGraphLaunch(h->midgraph, h->stream);
+            left -= h->midgraph_steps;
+        }
+    }
+    if (e == cudaSuccess && left > 0) e = enqueue(left);
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    h->step += n;
+    return SS_OK;
+}
+
+// Semi-implicit predictor-corrector steps: record, predictor, corrector, step counter.
+template <typename R>
+cudaError_t enqueue_sib(ss_system *h, int64_t nsteps) {
+    const KArgs<R> a = make_args<R>(h);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sm_count * 8));
+    const int gmeas = step_grid(h);
+    cudaError_t e = cudaSuccess;
+    for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        e = launch_measure<R>(a, h->block, gmeas, h->stream);
+        if (e == cudaSuccess)
+            e = launch_finalize_ring(h->sys, h->sys_tiles, h->nsys, h->partials, h->rec, h->rec_cap, a.step, h->stream);
+        if (e == cudaSuccess) e = launch_sib<R>(a, grid, h->stream);
+        if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
+    }
+    return e;
+}
+
 // Per Monte Carlo step: the record of the state at the start of the step (measure and
 // finalise into the ring), one launch per colour class, then the step counter advances.
 template <typename R>
@@ -1574,44 +1636,19 @@ ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations) {
         return h->precision == SS_FP32_MIXED ? enqueue_midpoint<float>(h, k, iterations)
                                              : enqueue_midpoint<double>(h, k, iterations);
     };
-    cudaError_t e = cudaSuccess;
-    int64_t left = n;
-    // Captured steps (no launch holds a host-side step), replayed while whole graphs fit
-    const int g = graph_len(h);
-    if (left >= g && !h->midgraph_failed && h->exec != SS_EXEC_KERNELS) {
-        if (h->midgraph && h->midgraph_iters != iterations) {
-            cudaGraphExecDestroy(h->midgraph);
-            h->midgraph = nullptr;
-        }
-        if (!h->midgraph) {
-            cudaGraph_t graph = nullptr;
-            e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                const cudaError_t ek = enqueue(g);
-                e = cudaStreamEndCapture(h->stream, &graph);
-                if (ek != cudaSuccess) e = ek;
-            }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->midgraph, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                h->midgraph = nullptr;
-                h->midgraph_failed = true;  // capture refused: launch directly from now on
-                e = cudaSuccess;
-            } else {
-                h->midgraph_steps = g;
-                h->midgraph_iters = iterations;
-            }
-        }
-        while (h->midgraph && left >= h->midgraph_steps && e == cudaSuccess) {
-            e = cudaGraphLaunch(h->midgraph, h->stream);
-            left -= h->midgraph_steps;
-        }
-    }
-    if (e == cudaSuccess && left > 0) e = enqueue(left);
-    if (e != cudaSuccess) return cuda_fail(h, e, "midpoint step");
-    h->step += n;
-    return SS_OK;
+    return integrate_captured(h, n, iterations, enqueue, "midpoint step");
+}
+
+ss_status llg_semi_implicit_step(ss_system *h, int64_t n) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (n < 0) return fail(h, SS_ERR_INVALID_ARG, "n must be >= 0");
+    if (h->demag_on)
+        return fail(h, SS_ERR_INVALID_ARG, "the semi-implicit scheme runs without the demagnetising field");
+    auto enqueue = [h](int64_t k) {
+        return h->precision == SS_FP32_MIXED ? enqueue_sib<float>(h, k) : enqueue_sib<double>(h, k);
+    };
+    return integrate_captured(h, n, -1, enqueue, "semi-implicit step");
 }
 
 ss_status set_demag(ss_system *h, double cell_size, double atom_volume, int32_t every) {

@@ -181,6 +181,9 @@ template <typename R> cudaError_t launch_demag(const KArgs<R> &a, const DemagArg
 // One midpoint step's launches after its record: Euler predictor, `iters` fixed-point
 // iterations, copy back (the step counter is advanced separately).
 template <typename R> cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t s);
+// One semi-implicit predictor-corrector step's launches after its record (predictor, corrector;
+// the step counter is advanced separately).
+template <typename R> cudaError_t launch_sib(const KArgs<R> &a, int grid, cudaStream_t s);
 // Exchange + applied field of (X, Y, Z) into (a.ex, a.ey, a.ez), a warp per row (long rows).
 template <typename R>
 cudaError_t launch_rows_field(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int grid, cudaStream_t s);

@@ -933,6 +933,100 @@ __global__ void k_mid_iter(const KArgs<R> a, const R *xx, const R *xy, const R *
 }
 
 // ----------------------------------------------------------------------------------
+// Semi-implicit predictor-corrector (the modified predictor-corrector midpoint scheme of
+// Mentink et al. that the paper's time-integration section cites): with Eq. LLG written as
+// dS/dt = S x A(S), A = -gamma/(1+lambda^2) (H + lambda S x H), each half-step solves
+// X = S_n + (dt/2)(S_n + X) x A in closed form, a rotation of S_n.  The predictor takes A at
+// S_n, the corrector at Sb = (S_n + S')/2; the thermal field is drawn once per step and held.
+// ----------------------------------------------------------------------------------
+
+// X = (c - b x c + (b.c) b)/(1 + |b|^2), b = (dt/2) A, c = S + S x b.
+template <typename R>
+__device__ __forceinline__ void sib_solve(R hdt, R s0, R s1, R s2, R a0, R a1, R a2, R &x0, R &x1, R &x2) {
+    const R b0 = hdt * a0, b1 = hdt * a1, b2 = hdt * a2;
+    const R c0 = s0 + (s1 * b2 - s2 * b1), c1 = s1 + (s2 * b0 - s0 * b2), c2 = s2 + (s0 * b1 - s1 * b0);
+    const R bc = b0 * c0 + b1 * c1 + b2 * c2;
+    const R den = (R)1 + (b0 * b0 + b1 * b1 + b2 * b2);
+    x0 = (c0 - (b1 * c2 - b2 * c1) + bc * b0) / den;
+    x1 = (c1 - (b2 * c0 - b0 * c2) + bc * b1) / den;
+    x2 = (c2 - (b0 * c1 - b1 * c0) + bc * b2) / den;
+}
+
+// A = -gp (H + lambda v x H).
+template <typename R>
+__device__ __forceinline__ void sib_a(R gp, R lam, R v0, R v1, R v2, R H0, R H1, R H2, R &a0, R &a1, R &a2) {
+    a0 = -gp * fma(lam, v1 * H2 - v2 * H1, H0);
+    a1 = -gp * fma(lam, v2 * H0 - v0 * H2, H1);
+    a2 = -gp * fma(lam, v0 * H1 - v1 * H0, H2);
+}
+
+// Predictor: the step's thermal field (counters as the Heun step), S' into (px, py, pz), and
+// the part of the corrector's field that is fixed over the step, C = H_app + H_th +
+// (1/2) sum_j J_ij S_j, into (hx, hy, hz).
+template <typename R, int Mode>
+__global__ void k_sib_pred(const KArgs<R> a) {
+    __shared__ SmemTables tab;
+    stage_tables(a, tab);
+    __syncthreads();
+    const uint64_t step = *a.step;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+        const SysDesc &sd = a.sys[m.sys];
+        const R sqrtT = sqrtT_of_step(a, step, sd);
+        R t0 = 0, t1 = 0, t2 = 0;
+        if (sqrtT > (R)0) {
+            const R sig = m.sig * sqrtT;
+            const Philox4 w = philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
+            double g0, g1, g2;
+            box_muller3(w, tab, g0, g1, g2);
+            t0 = sig * narrow<R>(g0);
+            t1 = sig * narrow<R>(g1);
+            t2 = sig * narrow<R>(g2);
+        }
+        const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
+        R x0, x1, x2;
+        exchange_bare<R, Mode>(a, a.sx, a.sy, a.sz, i, x0, x1, x2);
+        const R c0 = sys_H(sd, 0, R()) + t0, c1 = sys_H(sd, 1, R()) + t1, c2 = sys_H(sd, 2, R()) + t2;
+        a.hx[i] = fma((R)0.5, x0, c0);
+        a.hy[i] = fma((R)0.5, x1, c1);
+        a.hz[i] = fma((R)0.5, x2, c2);
+        R H0, H1, H2;
+        det_field<R, Mode != kPlain>(m, s0, s1, s2, x0 + c0, x1 + c1, x2 + c2, H0, H1, H2);
+        R a0, a1, a2;
+        sib_a(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, a0, a1, a2);
+        R p0, p1, p2;
+        sib_solve((R)0.5 * m.dt, s0, s1, s2, a0, a1, a2, p0, p1, p2);
+        a.px[i] = p0;
+        a.py[i] = p1;
+        a.pz[i] = p2;
+    }
+}
+
+// Corrector: A at Sb = (S + S')/2 with the field C + (1/2) sum_j J_ij S'_j plus the on-site
+// terms of Sb; the new spin overwrites S (a thread reads S only at its own spin).
+template <typename R, int Mode>
+__global__ void k_sib_corr(const KArgs<R> a) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+        const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
+        const R m0 = (R)0.5 * (s0 + a.px[i]), m1 = (R)0.5 * (s1 + a.py[i]), m2 = (R)0.5 * (s2 + a.pz[i]);
+        R x0, x1, x2;
+        exchange_bare<R, Mode>(a, a.px, a.py, a.pz, i, x0, x1, x2);
+        R H0, H1, H2;
+        det_field<R, Mode != kPlain>(m, m0, m1, m2, fma((R)0.5, x0, a.hx[i]), fma((R)0.5, x1, a.hy[i]),
+                                     fma((R)0.5, x2, a.hz[i]), H0, H1, H2);
+        R a0, a1, a2;
+        sib_a(m.gp, m.lambda, m0, m1, m2, H0, H1, H2, a0, a1, a2);
+        R v0, v1, v2;
+        sib_solve((R)0.5 * m.dt, s0, s1, s2, a0, a1, a2, v0, v1, v2);
+        if (bad_inv(v0 * v0 + v1 * v1 + v2 * v2)) atomicOr(a.err, kErrNonFinite);
+        a.sx[i] = v0;
+        a.sy[i] = v1;
+        a.sz[i] = v2;
+    }
+}
+
+// ----------------------------------------------------------------------------------
 // Macrocell demagnetising field (Section "Demagnetising fields")
 // ----------------------------------------------------------------------------------
 

@@ -152,6 +152,18 @@ cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t
 }
 
 template <typename R>
+cudaError_t launch_sib(const KArgs<R> &a, int grid, cudaStream_t s) {
+    if (a.J_tensor || a.any_cubic) {
+        k_sib_pred<R, kGeneral><<<grid, 256, 0, s>>>(a);
+        k_sib_corr<R, kGeneral><<<grid, 256, 0, s>>>(a);
+    } else {
+        k_sib_pred<R, kPlain><<<grid, 256, 0, s>>>(a);
+        k_sib_corr<R, kPlain><<<grid, 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_rows_field(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int grid, cudaStream_t s) {
     if (a.sell) {
         const int64_t pb = (a.n + 255) / 256;
@@ -225,6 +237,7 @@ template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McA
 template int mc_blocks_per_sm<SS_REAL>(int, int);
 template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
 template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
+template cudaError_t launch_sib<SS_REAL>(const KArgs<SS_REAL> &, int, cudaStream_t);
 template cudaError_t launch_rows_field<SS_REAL>(const KArgs<SS_REAL> &, const SS_REAL *, const SS_REAL *,
                                                 const SS_REAL *, int, cudaStream_t);
 template int rows_blocks_per_sm<SS_REAL>();

@@ -210,6 +210,10 @@ class SpinSystem:
         """n steps of the midpoint rule (fixed-point iterations per step), instead of Heun."""
         self._check(self._lib.llg_midpoint_step(self._h, int(n), int(iterations)))
 
+    def semi_implicit_step(self, n: int = 1):
+        """n steps of the semi-implicit predictor-corrector scheme (Mentink et al.), instead of Heun."""
+        self._check(self._lib.llg_semi_implicit_step(self._h, int(n)))
+
     def mc_step(self, n: int = 1):
         """n Hinzke-Nowak Monte Carlo steps (one trial move per spin each)."""
         self._check(self._lib.mc_step(self._h, int(n)))
