@@ -1317,19 +1317,16 @@ ss_status mc_upload_params(ss_system *h) {
     return SS_OK;
 }
 
-// Midpoint steps: per step the record of the state at the start of the step (measure and
-// finalise into the ring at the device's step), the midpoint launches, the step counter.
+// Midpoint steps: per step the midpoint launches (the first of which leaves the tile partials
+// of the record of the state at the start of the step, finalised into the ring at the
+// device's step) and the step counter.
 template <typename R>
 cudaError_t enqueue_midpoint(ss_system *h, int64_t nsteps, int iterations) {
     const KArgs<R> a = make_args<R>(h);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sm_count * 8));
-    const int gmeas = step_grid(h);
     cudaError_t e = cudaSuccess;
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-        e = launch_measure<R>(a, h->block, gmeas, h->stream);
-        if (e == cudaSuccess)
-            e = launch_finalize_ring(h->sys, h->sys_tiles, h->nsys, h->partials, h->rec, h->rec_cap, a.step, h->stream);
-        if (e == cudaSuccess) e = launch_midpoint<R>(a, iterations, grid, h->stream);
+        e = launch_midpoint<R>(a, iterations, grid, h->stream);
         if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
     }
     return e;
@@ -1379,18 +1376,15 @@ ss_status integrate_captured(ss_system *h, int64_t n, int key, F enqueue, const 
     return SS_OK;
 }
 
-// Semi-implicit predictor-corrector steps: record, predictor, corrector, step counter.
+// Semi-implicit predictor-corrector steps: predictor (with the record's tile partials),
+// record, corrector, step counter.
 template <typename R>
 cudaError_t enqueue_sib(ss_system *h, int64_t nsteps) {
     const KArgs<R> a = make_args<R>(h);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sm_count * 8));
-    const int gmeas = step_grid(h);
     cudaError_t e = cudaSuccess;
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-        e = launch_measure<R>(a, h->block, gmeas, h->stream);
-        if (e == cudaSuccess)
-            e = launch_finalize_ring(h->sys, h->sys_tiles, h->nsys, h->partials, h->rec, h->rec_cap, a.step, h->stream);
-        if (e == cudaSuccess) e = launch_sib<R>(a, grid, h->stream);
+        e = launch_sib<R>(a, grid, h->stream);
         if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
     }
     return e;

@@ -867,71 +867,6 @@ __device__ __forceinline__ void exchange_bare(const KArgs<R> &a, const R *X, con
     e2 = z;
 }
 
-// First pass: the Euler predictor X = S + dt f(S) written to (px, py, pz), and the part of
-// the midpoint field that stays fixed over the step, C = H_app + H_th + (1/2) sum_j J_ij S_j
-// (the exchange field is linear, so the field of m = (S + X)/2 is C + (1/2) sum_j J_ij X_j
-// plus the on-site terms of m), stored in (hx, hy, hz).
-template <typename R, int Mode>
-__global__ void k_mid_euler(const KArgs<R> a) {
-    __shared__ SmemTables tab;
-    stage_tables(a, tab);
-    __syncthreads();
-    const uint64_t step = *a.step;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
-        const SysDesc &sd = a.sys[m.sys];
-        const R sqrtT = sqrtT_of_step(a, step, sd);
-        R t0 = 0, t1 = 0, t2 = 0;
-        if (sqrtT > (R)0) {
-            const R sig = m.sig * sqrtT;
-            const Philox4 w = philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
-            double g0, g1, g2;
-            box_muller3(w, tab, g0, g1, g2);
-            t0 = sig * narrow<R>(g0);
-            t1 = sig * narrow<R>(g1);
-            t2 = sig * narrow<R>(g2);
-        }
-        const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
-        R x0, x1, x2;
-        exchange_bare<R, Mode>(a, a.sx, a.sy, a.sz, i, x0, x1, x2);
-        const R c0 = sys_H(sd, 0, R()) + t0, c1 = sys_H(sd, 1, R()) + t1, c2 = sys_H(sd, 2, R()) + t2;
-        a.hx[i] = fma((R)0.5, x0, c0);
-        a.hy[i] = fma((R)0.5, x1, c1);
-        a.hz[i] = fma((R)0.5, x2, c2);
-        R H0, H1, H2;
-        det_field<R, Mode != kPlain>(m, s0, s1, s2, x0 + c0, x1 + c1, x2 + c2, H0, H1, H2);
-        R d0, d1, d2;
-        llg_rhs(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, d0, d1, d2);
-        a.px[i] = fma(m.dt, d0, s0);
-        a.py[i] = fma(m.dt, d1, s1);
-        a.pz[i] = fma(m.dt, d2, s2);
-    }
-}
-
-// One fixed-point iteration: Y = S + dt f(m), m = (S + X)/2, with the field C + (1/2) sum_j J_ij X_j
-// plus the on-site terms of m.  A thread reads S only at its own spin, so the last iteration
-// writes Y over S (Last: and flags non-finite spins).
-template <typename R, int Mode, bool Last>
-__global__ void k_mid_iter(const KArgs<R> a, const R *xx, const R *xy, const R *xz, R *yx, R *yy, R *yz) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
-        const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
-        const R m0 = (R)0.5 * (s0 + xx[i]), m1 = (R)0.5 * (s1 + xy[i]), m2 = (R)0.5 * (s2 + xz[i]);
-        R x0, x1, x2;
-        exchange_bare<R, Mode>(a, xx, xy, xz, i, x0, x1, x2);
-        R H0, H1, H2;
-        det_field<R, Mode != kPlain>(m, m0, m1, m2, fma((R)0.5, x0, a.hx[i]), fma((R)0.5, x1, a.hy[i]), fma((R)0.5, x2, a.hz[i]), H0,
-                  H1, H2);
-        R d0, d1, d2;
-        llg_rhs(m.gp, m.lambda, m0, m1, m2, H0, H1, H2, d0, d1, d2);
-        const R v0 = fma(m.dt, d0, s0), v1 = fma(m.dt, d1, s1), v2 = fma(m.dt, d2, s2);
-        if (Last && bad_inv(v0 * v0 + v1 * v1 + v2 * v2)) atomicOr(a.err, kErrNonFinite);
-        yx[i] = v0;
-        yy[i] = v1;
-        yz[i] = v2;
-    }
-}
-
 // ----------------------------------------------------------------------------------
 // Semi-implicit predictor-corrector (the modified predictor-corrector midpoint scheme of
 // Mentink et al. that the paper's time-integration section cites): with Eq. LLG written as
@@ -960,46 +895,114 @@ __device__ __forceinline__ void sib_a(R gp, R lam, R v0, R v1, R v2, R H0, R H1,
     a2 = -gp * fma(lam, v0 * H1 - v1 * H0, H2);
 }
 
-// Predictor: the step's thermal field (counters as the Heun step), S' into (px, py, pz), and
-// the part of the corrector's field that is fixed over the step, C = H_app + H_th +
-// (1/2) sum_j J_ij S_j, into (hx, hy, hz).
+// Threads per block of the first pass of the alternative integrators.
+constexpr int kAltBlock = 256;
+
+// First pass of the alternative integrators, tile by tile: the step's thermal field (counters
+// as the Heun step), the part of the second pass's field that is fixed over the step,
+// C = H_app + H_th + (1/2) sum_j J_ij S_j (the exchange field is linear, so the field of
+// (S + X)/2 is C + (1/2) sum_j J_ij X_j plus the on-site terms), into (hx, hy, hz); the first new
+// spin into (px, py, pz): the semi-implicit predictor (Sib) or the Euler predictor of the
+// midpoint rule; and the tile partials of the record of S, the state at the start of the step.
+template <typename R, int Mode, bool Sib>
+__device__ __forceinline__ void alt_first_pass(const KArgs<R> &a, const SmemTables &tab, double *red) {
+    const uint64_t step = *a.step;
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const TileDesc td = a.tiles[t];
+        const SysDesc &sd = a.sys[td.sys];
+        const R sqrtT = sqrtT_of_step(a, step, sd);
+        const R ha0 = sys_H(sd, 0, R()), ha1 = sys_H(sd, 1, R()), ha2 = sys_H(sd, 2, R());
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = threadIdx.x; k < td.count; k += kAltBlock) {
+            const int64_t i = td.start + k;
+            const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+            R t0 = 0, t1 = 0, t2 = 0;
+            if (sqrtT > (R)0) {
+                const R sig = m.sig * sqrtT;
+                const Philox4 w =
+                    philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
+                double g0, g1, g2;
+                box_muller3(w, tab, g0, g1, g2);
+                t0 = sig * narrow<R>(g0);
+                t1 = sig * narrow<R>(g1);
+                t2 = sig * narrow<R>(g2);
+            }
+            const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
+            R x0, x1, x2;
+            exchange_bare<R, Mode>(a, a.sx, a.sy, a.sz, i, x0, x1, x2);
+            const R c0 = ha0 + t0, c1 = ha1 + t1, c2 = ha2 + t2;
+            a.hx[i] = fma((R)0.5, x0, c0);
+            a.hy[i] = fma((R)0.5, x1, c1);
+            a.hz[i] = fma((R)0.5, x2, c2);
+            R H0, H1, H2;
+            const R sde = det_field<R, Mode != kPlain>(m, s0, s1, s2, x0 + c0, x1 + c1, x2 + c2, H0, H1, H2);
+            double v[5];
+            spin_terms<R, Mode != kPlain>(m, s0, s1, s2, x0 + ha0, x1 + ha1, x2 + ha2, sde, v);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) acc[c] += v[c];
+            R p0, p1, p2;
+            if constexpr (Sib) {
+                R a0, a1, a2;
+                sib_a(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, a0, a1, a2);
+                sib_solve((R)0.5 * m.dt, s0, s1, s2, a0, a1, a2, p0, p1, p2);
+            } else {
+                R d0, d1, d2;
+                llg_rhs(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, d0, d1, d2);
+                p0 = fma(m.dt, d0, s0);
+                p1 = fma(m.dt, d1, s1);
+                p2 = fma(m.dt, d2, s2);
+            }
+            a.px[i] = p0;
+            a.py[i] = p1;
+            a.pz[i] = p2;
+        }
+        const double r = block_sum8<kAltBlock>(acc, red);
+        if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
+    }
+}
+
+// Midpoint rule, first pass: the Euler predictor X = S + dt f(S).
 template <typename R, int Mode>
-__global__ void k_sib_pred(const KArgs<R> a) {
+__global__ void __launch_bounds__(kAltBlock) k_mid_euler(const KArgs<R> a) {
     __shared__ SmemTables tab;
+    __shared__ double red[(kAltBlock / 32) * 8];
     stage_tables(a, tab);
     __syncthreads();
-    const uint64_t step = *a.step;
+    alt_first_pass<R, Mode, false>(a, tab, red);
+}
+
+// One fixed-point iteration: Y = S + dt f(m), m = (S + X)/2, with the field C + (1/2) sum_j J_ij X_j
+// plus the on-site terms of m.  A thread reads S only at its own spin, so the last iteration
+// writes Y over S (Last: and flags non-finite spins).
+template <typename R, int Mode, bool Last>
+__global__ void k_mid_iter(const KArgs<R> a, const R *xx, const R *xy, const R *xz, R *yx, R *yy, R *yz) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
         const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
-        const SysDesc &sd = a.sys[m.sys];
-        const R sqrtT = sqrtT_of_step(a, step, sd);
-        R t0 = 0, t1 = 0, t2 = 0;
-        if (sqrtT > (R)0) {
-            const R sig = m.sig * sqrtT;
-            const Philox4 w = philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
-            double g0, g1, g2;
-            box_muller3(w, tab, g0, g1, g2);
-            t0 = sig * narrow<R>(g0);
-            t1 = sig * narrow<R>(g1);
-            t2 = sig * narrow<R>(g2);
-        }
         const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
+        const R m0 = (R)0.5 * (s0 + xx[i]), m1 = (R)0.5 * (s1 + xy[i]), m2 = (R)0.5 * (s2 + xz[i]);
         R x0, x1, x2;
-        exchange_bare<R, Mode>(a, a.sx, a.sy, a.sz, i, x0, x1, x2);
-        const R c0 = sys_H(sd, 0, R()) + t0, c1 = sys_H(sd, 1, R()) + t1, c2 = sys_H(sd, 2, R()) + t2;
-        a.hx[i] = fma((R)0.5, x0, c0);
-        a.hy[i] = fma((R)0.5, x1, c1);
-        a.hz[i] = fma((R)0.5, x2, c2);
+        exchange_bare<R, Mode>(a, xx, xy, xz, i, x0, x1, x2);
         R H0, H1, H2;
-        det_field<R, Mode != kPlain>(m, s0, s1, s2, x0 + c0, x1 + c1, x2 + c2, H0, H1, H2);
-        R a0, a1, a2;
-        sib_a(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, a0, a1, a2);
-        R p0, p1, p2;
-        sib_solve((R)0.5 * m.dt, s0, s1, s2, a0, a1, a2, p0, p1, p2);
-        a.px[i] = p0;
-        a.py[i] = p1;
-        a.pz[i] = p2;
+        det_field<R, Mode != kPlain>(m, m0, m1, m2, fma((R)0.5, x0, a.hx[i]), fma((R)0.5, x1, a.hy[i]),
+                                     fma((R)0.5, x2, a.hz[i]), H0, H1, H2);
+        R d0, d1, d2;
+        llg_rhs(m.gp, m.lambda, m0, m1, m2, H0, H1, H2, d0, d1, d2);
+        const R v0 = fma(m.dt, d0, s0), v1 = fma(m.dt, d1, s1), v2 = fma(m.dt, d2, s2);
+        if (Last && bad_inv(v0 * v0 + v1 * v1 + v2 * v2)) atomicOr(a.err, kErrNonFinite);
+        yx[i] = v0;
+        yy[i] = v1;
+        yz[i] = v2;
     }
+}
+
+// Semi-implicit predictor: S' = S_n + (dt/2)(S_n + S') x A(S_n), with the first-pass outputs above.
+template <typename R, int Mode>
+__global__ void __launch_bounds__(kAltBlock) k_sib_pred(const KArgs<R> a) {
+    __shared__ SmemTables tab;
+    __shared__ double red[(kAltBlock / 32) * 8];
+    stage_tables(a, tab);
+    __syncthreads();
+    alt_first_pass<R, Mode, true>(a, tab, red);
 }
 
 // Corrector: A at Sb = (S + S')/2 with the field C + (1/2) sum_j J_ij S'_j plus the on-site

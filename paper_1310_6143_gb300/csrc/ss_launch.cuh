@@ -124,10 +124,19 @@ cudaError_t launch_demag(const KArgs<R> &a, const DemagArgs &d, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+// The first pass of the alternative integrators over the tiles, then the record of the state
+// at the start of the step from its tile partials.
+template <typename R>
+int alt_first_grid(const KArgs<R> &a, int grid) {
+    return (int)(a.ntiles < (int64_t)grid ? (a.ntiles > 0 ? a.ntiles : 1) : grid);
+}
+
 template <typename R, int Mode>
 cudaError_t launch_midpoint_mode(const KArgs<R> &a, int iters, int grid, cudaStream_t s) {
-    k_mid_euler<R, Mode><<<grid, 256, 0, s>>>(a);
+    k_mid_euler<R, Mode><<<alt_first_grid(a, grid), kAltBlock, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_finalize_ring(a.sys, a.sys_tiles, a.nsys, a.partials, a.rec, a.rec_cap, a.step, s);
     R *x[3] = {a.px, a.py, a.pz}, *y[3] = {a.qx, a.qy, a.qz};
     for (int k = 0; k + 1 < iters && e == cudaSuccess; ++k) {
         k_mid_iter<R, Mode, false><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], y[0], y[1], y[2]);
@@ -153,13 +162,19 @@ cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t
 
 template <typename R>
 cudaError_t launch_sib(const KArgs<R> &a, int grid, cudaStream_t s) {
-    if (a.J_tensor || a.any_cubic) {
-        k_sib_pred<R, kGeneral><<<grid, 256, 0, s>>>(a);
+    const bool general = a.J_tensor || a.any_cubic;
+    if (general)
+        k_sib_pred<R, kGeneral><<<alt_first_grid(a, grid), kAltBlock, 0, s>>>(a);
+    else
+        k_sib_pred<R, kPlain><<<alt_first_grid(a, grid), kAltBlock, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_finalize_ring(a.sys, a.sys_tiles, a.nsys, a.partials, a.rec, a.rec_cap, a.step, s);
+    if (e != cudaSuccess) return e;
+    if (general)
         k_sib_corr<R, kGeneral><<<grid, 256, 0, s>>>(a);
-    } else {
-        k_sib_pred<R, kPlain><<<grid, 256, 0, s>>>(a);
+    else
         k_sib_corr<R, kPlain><<<grid, 256, 0, s>>>(a);
-    }
     return cudaGetLastError();
 }
 
