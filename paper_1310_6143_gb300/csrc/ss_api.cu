@@ -119,6 +119,14 @@ struct ss_system {
     int64_t mc_sched_cap = 0;
     bool mc_par_dirty = true;
     unsigned long long *mc_acc = nullptr;    // accepted trial moves per system (device)
+    // record summed in the colour passes (at most two colour classes): per class its tiles
+    // (runs of mc_order within one system) and their partial slots, slots system by system
+    bool mc_rec = false;
+    TileDesc *mc_tiles[2] = {};
+    int32_t *mc_slot[2] = {};
+    int64_t mc_ntiles[2] = {};
+    int32_t *mc_sys_slots = nullptr;         // [nsys + 1] first slot of each system
+    double *mc_partials = nullptr;
     std::vector<int64_t> mc_tried;           // trial moves per system (host count)
 
     // Macrocell demagnetising field (set_demag)
@@ -1276,6 +1284,51 @@ ss_status mc_prepare(ss_system *h) {
     SS_CUDA(h, dalloc(h, (void **)&dorder, order.size() * sizeof(int32_t)));
     SS_CUDA(h, cudaMemcpyAsync(dorder, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                                h->stream));
+    if (ncol <= 2 && n > 0) {
+        // tiles of at most `tile` trials within one system, per colour class (1,024, or 256 when
+        // a class would give fewer than four tiles per SM); partial slots system by system
+        // (class 0's tiles of the system, then class 1's)
+        const int64_t kMcTile = h->mc_cstart[1] >= (int64_t)h->sm_count * 4 * 1024 ? 1024 : 256;
+        std::vector<TileDesc> tl[2];
+        std::vector<int32_t> sl[2];
+        std::vector<int32_t> sys_slots((size_t)h->nsys + 1, 0);
+        int32_t next = 0;
+        for (int s = 0; s < h->nsys; ++s) {
+            sys_slots[(size_t)s] = next;
+            for (int c = 0; c < ncol; ++c) {
+                // the spins of system s in class c: a contiguous run of order[] (sorted by index)
+                const int64_t lo = h->sys_offset[s], hi = lo + h->sys_n[s];
+                const int32_t *b0 = order.data() + h->mc_cstart[c], *b1 = order.data() + h->mc_cstart[c + 1];
+                const int64_t r0 = std::lower_bound(b0, b1, (int32_t)lo) - order.data();
+                const int64_t r1 = std::lower_bound(b0, b1, (int32_t)std::min<int64_t>(hi, INT32_MAX)) - order.data();
+                for (int64_t q = r0; q < r1; q += kMcTile) {
+                    TileDesc t;
+                    t.start = q;
+                    t.count = (int32_t)std::min<int64_t>(kMcTile, r1 - q);
+                    t.sys = s;
+                    tl[c].push_back(t);
+                    sl[c].push_back(next++);
+                }
+            }
+        }
+        sys_slots[(size_t)h->nsys] = next;
+        for (int c = 0; c < ncol; ++c) {
+            h->mc_ntiles[c] = (int64_t)tl[c].size();
+            if (tl[c].empty()) continue;
+            SS_CUDA(h, dalloc(h, (void **)&h->mc_tiles[c], tl[c].size() * sizeof(TileDesc)));
+            SS_CUDA(h, dalloc(h, (void **)&h->mc_slot[c], sl[c].size() * sizeof(int32_t)));
+            SS_CUDA(h, cudaMemcpyAsync(h->mc_tiles[c], tl[c].data(), tl[c].size() * sizeof(TileDesc),
+                                       cudaMemcpyHostToDevice, h->stream));
+            SS_CUDA(h, cudaMemcpyAsync(h->mc_slot[c], sl[c].data(), sl[c].size() * sizeof(int32_t),
+                                       cudaMemcpyHostToDevice, h->stream));
+        }
+        SS_CUDA(h, dalloc(h, (void **)&h->mc_sys_slots, sys_slots.size() * sizeof(int32_t)));
+        SS_CUDA(h, cudaMemcpyAsync(h->mc_sys_slots, sys_slots.data(), sys_slots.size() * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, h->stream));
+        SS_CUDA(h, dalloc(h, (void **)&h->mc_partials, (size_t)std::max(next, 1) * kPartComps * sizeof(double)));
+        SS_CUDA(h, cudaStreamSynchronize(h->stream));
+        h->mc_rec = true;
+    }
     SS_CUDA(h, dalloc(h, (void **)&h->mc_acc, (size_t)h->nsys * sizeof(unsigned long long)));
     SS_CUDA(h, cudaMemsetAsync(h->mc_acc, 0, (size_t)h->nsys * sizeof(unsigned long long), h->stream));
     SS_CUDA(h, dalloc(h, (void **)&h->mc_par, (size_t)h->nsys * sizeof(double2)));
@@ -1405,6 +1458,27 @@ cudaError_t enqueue_mc(ss_system *h, int64_t nsteps) {
     const int gmeas = step_grid(h);
     const int ncol = (int)h->mc_cstart.size() - 1;
     cudaError_t e = cudaSuccess;
+    if (h->mc_rec) {  // the record summed in the colour passes
+        m.partials = h->mc_partials;
+        for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+            for (int c = 0; c < ncol && e == cudaSuccess; ++c) {
+                m.c0 = h->mc_cstart[c];
+                m.c1 = h->mc_cstart[c + 1];
+                m.tiles = h->mc_tiles[c];
+                m.slot = h->mc_slot[c];
+                m.ntiles = h->mc_ntiles[c];
+                m.first = c == 0 ? 1 : 0;
+                if (m.ntiles == 0) continue;
+                const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(m.ntiles, resident));
+                e = launch_mc_colour_rec<R>(a, m, grid, h->stream);
+            }
+            if (e == cudaSuccess)
+                e = launch_finalize_ring(h->sys, h->mc_sys_slots, h->nsys, h->mc_partials, h->rec, h->rec_cap, a.step,
+                                         h->stream);
+            if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
+        }
+        return e;
+    }
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
         e = launch_measure<R>(a, h->block, gmeas, h->stream);
         if (e == cudaSuccess)

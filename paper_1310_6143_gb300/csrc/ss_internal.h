@@ -139,6 +139,14 @@ struct McArgs {
     const double2 *par_sys;   // per system (-kB T, sigma_g) when no schedule is set
     const double2 *par_sched; // per schedule step (-kB T_k, sigma_g(T_k))
     unsigned long long *acc;  // accepted trial moves per system
+    // Record of the state at the start of the step summed in the colour passes (lattices with
+    // at most two colour classes): the class's tiles, each a run of order[] within one system
+    // whose record terms go to partials[slot]; slots run system by system.
+    const TileDesc *tiles;    // tiles of this colour class (start and count in order[])
+    const int32_t *slot;      // partial slot of each tile
+    int64_t ntiles;
+    double *partials;         // [slots * kPartComps]
+    int first;                // 1: the first class (its rows' bonds are summed, both ends unchanged)
 };
 
 // Macrocell demagnetising field (Section "Demagnetising fields").
@@ -173,6 +181,8 @@ template <typename R> int persistent_blocks_per_sm(int block, int mode);
 // mode: the step-kernel variant (0 plain, 1 general, 2 rows; kPlain / kGeneral / kRows)
 template <typename R> int step_blocks_per_sm(int block, int mode);
 template <typename R> int corrector_blocks_per_sm(int block, bool draw_ahead, int mode);
+// One colour pass over the tiles of m that also sums the record terms of the pre-step state.
+template <typename R> cudaError_t launch_mc_colour_rec(const KArgs<R> &a, const McArgs &m, int grid, cudaStream_t s);
 template <typename R> cudaError_t launch_mc_colour(const KArgs<R> &a, const McArgs &m, int block, int grid,
                                                    cudaStream_t s);
 template <typename R> int mc_blocks_per_sm(int block, int mode);  // mode: kPlain or kGeneral

@@ -1123,6 +1123,118 @@ __global__ void k_demag_field(const KArgs<R> a, const DemagArgs d) {
 // Spins of one colour share no bond, so each trial reads only spins of other colours.
 // dE is the change of site i's Hamiltonian terms: exchange and applied field through the
 // field h = H_app + sum_j (J_ij / mu_s,i) S_j, then anisotropy and the Neel term.
+// One Hinzke-Nowak trial move of spin i (Section "Monte Carlo Methods"): spin flip, Gaussian
+// or random move by a Philox draw, accepted by Eq. AMCP.  Returns whether it was accepted;
+// sysid receives the spin's system.  Rec (0: none) also gives the spin's record terms of the
+// pre-step state in v: mu S (3), the exchange term (1: -mu S.(h - H_app) - mu S.H_app/2 for
+// the first colour class, whose bonds all end on unchanged spins; 2: -mu S.H_app/2), and
+// the anisotropy energy.
+template <typename R, int Mode, int Rec>
+__device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int64_t i, uint64_t step,
+                                         const SmemTables &tab, int &sysid, double v[5]) {
+    bool accept;
+    const MatDesc<R> &mt = a.mats[__ldg(a.mat + i)];
+    const SysDesc &sd = a.sys[mt.sys];
+    double2 par;
+    if (a.sched_len > 0) {
+        int64_t q = (int64_t)step - a.sched_step0;
+        q = q < 0 ? 0 : (q >= a.sched_len ? a.sched_len - 1 : q);
+        par = m.par_sched[q];
+    } else {
+        par = m.par_sys[mt.sys];
+    }
+    const uint32_t spin = (uint32_t)(i - sd.offset);
+    const Philox4 wa = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 2u, sd.key0, sd.key1);
+    const Philox4 wb = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 3u, sd.key0, sd.key1);
+    const int move = (int)(((uint64_t)wb.w0 * 3u) >> 32);
+    const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
+    R n0, n1, n2;
+    if (move == 0) {  // spin flip
+        n0 = -s0;
+        n1 = -s1;
+        n2 = -s2;
+    } else if (move == 1 && par.y == 0.0) {  // T = 0: a Gaussian cone of width 0
+        n0 = s0;
+        n1 = s1;
+        n2 = s2;
+    } else {
+        double g0, g1, g2;
+        box_muller3(wa, tab, g0, g1, g2);
+        if (move == 1) {  // Gaussian move: S + sigma_g Gamma, normalised
+            const double sg = par.y;
+            if constexpr (sizeof(R) == 8) {
+                n0 = fma(sg, g0, (double)s0);
+                n1 = fma(sg, g1, (double)s1);
+                n2 = fma(sg, g2, (double)s2);
+            } else {
+                const float sgf = narrow<float>(sg);
+                n0 = fmaf(sgf, narrow<float>(g0), (float)s0);
+                n1 = fmaf(sgf, narrow<float>(g1), (float)s1);
+                n2 = fmaf(sgf, narrow<float>(g2), (float)s2);
+            }
+        } else {  // random move: Gamma normalised
+            n0 = narrow<R>(g0);
+            n1 = narrow<R>(g1);
+            n2 = narrow<R>(g2);
+        }
+        const R inv = rsqrt_r(n0 * n0 + n1 * n1 + n2 * n2);
+        n0 *= inv;
+        n1 *= inv;
+        n2 *= inv;
+    }
+    R h0, h1, h2;
+    exchange_sum<R, false, Mode>(a, sd, a.sx, a.sy, a.sz, i, h0, h1, h2);
+    // quadratic terms as (n - s).(A (n + s)): exactly zero when the spin is unchanged or
+    // flipped, whatever the contraction of products into FMAs
+    const R d0 = n0 - s0, d1 = n1 - s1, d2 = n2 - s2;
+    const R p0 = n0 + s0, p1 = n1 + s1, p2 = n2 + s2;
+    const R de = d0 * mt.e[0] + d1 * mt.e[1] + d2 * mt.e[2];
+    const R pe = p0 * mt.e[0] + p1 * mt.e[1] + p2 * mt.e[2];
+    R dE = -mt.mu * (d0 * h0 + d1 * h1 + d2 * h2) - mt.ku * (de * pe);
+    if (Mode != kPlain && mt.has_cubic) {  // (k_c/2) sum (n^4 - s^4), n^4 - s^4 = (n - s)(n + s)(n^2 + s^2)
+        dE += (R)0.5 * mt.kc * (d0 * p0 * (n0 * n0 + s0 * s0) + d1 * p1 * (n1 * n1 + s1 * s1)
+                                + d2 * p2 * (n2 * n2 + s2 * s2));
+    }
+    if (mt.has_neel) {
+        const R k0 = mt.K[0] * p0 + mt.K[3] * p1 + mt.K[4] * p2;
+        const R k1 = mt.K[3] * p0 + mt.K[1] * p1 + mt.K[5] * p2;
+        const R k2 = mt.K[4] * p0 + mt.K[5] * p1 + mt.K[2] * p2;
+        dE -= d0 * k0 + d1 * k1 + d2 * k2;
+    }
+    // accept when dE <= -kB T ln u = (-kB T)(-1/2)(-2 ln u); at T = 0 when dE <= 0
+    const double dEd = widen(dE);
+    accept = par.x < 0.0 ? dEd <= par.x * (-0.5 * neg2log_u(wb.w1, tab)) : dEd <= 0.0;
+    if (accept) {
+        a.sx[i] = n0;
+        a.sy[i] = n1;
+        a.sz[i] = n2;
+    }
+    if constexpr (Rec != 0) {  // terms in the working type, summed in FP64 (as spin_terms)
+        const R mu = mt.mu;
+        v[0] = widen(mu * s0);
+        v[1] = widen(mu * s1);
+        v[2] = widen(mu * s2);
+        const R sh = s0 * sys_H(sd, 0, R()) + s1 * sys_H(sd, 1, R()) + s2 * sys_H(sd, 2, R());  // S.H_app
+        if (Rec == 1)
+            v[3] = widen(-mu * (s0 * h0 + s1 * h1 + s2 * h2) + (R)0.5 * mu * sh);
+        else
+            v[3] = widen((R)-0.5 * mu * sh);
+        const R se = s0 * mt.e[0] + s1 * mt.e[1] + s2 * mt.e[2];
+        R ea = -mt.ku * se * se;
+        if (Mode != kPlain && mt.has_cubic) {
+            const R x2 = s0 * s0, y2 = s1 * s1, z2 = s2 * s2;
+            ea += (R)0.5 * mt.kc * (x2 * x2 + y2 * y2 + z2 * z2);
+        }
+        if (mt.has_neel) {
+            ea -= mt.K[0] * s0 * s0 + mt.K[1] * s1 * s1 + mt.K[2] * s2 * s2
+                + (R)2 * (mt.K[3] * s0 * s1 + mt.K[4] * s0 * s2 + mt.K[5] * s1 * s2);
+        }
+        v[4] = widen(ea);
+    }
+    sysid = mt.sys;
+    return accept;
+}
+
 template <typename R, int BS, int Mode = kGeneral>
 __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs m) {
     __shared__ SmemTables tab;
@@ -1130,89 +1242,44 @@ __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs
     __syncthreads();
     const uint64_t step = *a.step;
     for (int64_t k = m.c0 + (int64_t)blockIdx.x * BS + threadIdx.x; k < m.c1; k += (int64_t)gridDim.x * BS) {
-        const int64_t i = __ldg(m.order + k);
-        const MatDesc<R> &mt = a.mats[__ldg(a.mat + i)];
-        const SysDesc &sd = a.sys[mt.sys];
-        double2 par;
-        if (a.sched_len > 0) {
-            int64_t q = (int64_t)step - a.sched_step0;
-            q = q < 0 ? 0 : (q >= a.sched_len ? a.sched_len - 1 : q);
-            par = m.par_sched[q];
-        } else {
-            par = m.par_sys[mt.sys];
-        }
-        const uint32_t spin = (uint32_t)(i - sd.offset);
-        const Philox4 wa = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 2u, sd.key0, sd.key1);
-        const Philox4 wb = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 3u, sd.key0, sd.key1);
-        const int move = (int)(((uint64_t)wb.w0 * 3u) >> 32);
-        const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
-        R n0, n1, n2;
-        if (move == 0) {  // spin flip
-            n0 = -s0;
-            n1 = -s1;
-            n2 = -s2;
-        } else if (move == 1 && par.y == 0.0) {  // T = 0: a Gaussian cone of width 0
-            n0 = s0;
-            n1 = s1;
-            n2 = s2;
-        } else {
-            double g0, g1, g2;
-            box_muller3(wa, tab, g0, g1, g2);
-            if (move == 1) {  // Gaussian move: S + sigma_g Gamma, normalised
-                const double sg = par.y;
-                if constexpr (sizeof(R) == 8) {
-                    n0 = fma(sg, g0, (double)s0);
-                    n1 = fma(sg, g1, (double)s1);
-                    n2 = fma(sg, g2, (double)s2);
-                } else {
-                    const float sgf = narrow<float>(sg);
-                    n0 = fmaf(sgf, narrow<float>(g0), (float)s0);
-                    n1 = fmaf(sgf, narrow<float>(g1), (float)s1);
-                    n2 = fmaf(sgf, narrow<float>(g2), (float)s2);
-                }
-            } else {  // random move: Gamma normalised
-                n0 = narrow<R>(g0);
-                n1 = narrow<R>(g1);
-                n2 = narrow<R>(g2);
-            }
-            const R inv = rsqrt_r(n0 * n0 + n1 * n1 + n2 * n2);
-            n0 *= inv;
-            n1 *= inv;
-            n2 *= inv;
-        }
-        R h0, h1, h2;
-        exchange_sum<R, false, Mode>(a, sd, a.sx, a.sy, a.sz, i, h0, h1, h2);
-        // quadratic terms as (n - s).(A (n + s)): exactly zero when the spin is unchanged or
-        // flipped, whatever the contraction of products into FMAs
-        const R d0 = n0 - s0, d1 = n1 - s1, d2 = n2 - s2;
-        const R p0 = n0 + s0, p1 = n1 + s1, p2 = n2 + s2;
-        const R de = d0 * mt.e[0] + d1 * mt.e[1] + d2 * mt.e[2];
-        const R pe = p0 * mt.e[0] + p1 * mt.e[1] + p2 * mt.e[2];
-        R dE = -mt.mu * (d0 * h0 + d1 * h1 + d2 * h2) - mt.ku * (de * pe);
-        if (Mode != kPlain && mt.has_cubic) {  // (k_c/2) sum (n^4 - s^4), n^4 - s^4 = (n - s)(n + s)(n^2 + s^2)
-            dE += (R)0.5 * mt.kc * (d0 * p0 * (n0 * n0 + s0 * s0) + d1 * p1 * (n1 * n1 + s1 * s1)
-                                    + d2 * p2 * (n2 * n2 + s2 * s2));
-        }
-        if (mt.has_neel) {
-            const R k0 = mt.K[0] * p0 + mt.K[3] * p1 + mt.K[4] * p2;
-            const R k1 = mt.K[3] * p0 + mt.K[1] * p1 + mt.K[5] * p2;
-            const R k2 = mt.K[4] * p0 + mt.K[5] * p1 + mt.K[2] * p2;
-            dE -= d0 * k0 + d1 * k1 + d2 * k2;
-        }
-        // accept when dE <= -kB T ln u = (-kB T)(-1/2)(-2 ln u); at T = 0 when dE <= 0
-        const double dEd = widen(dE);
-        const bool accept = par.x < 0.0 ? dEd <= par.x * (-0.5 * neg2log_u(wb.w1, tab)) : dEd <= 0.0;
-        if (accept) {
-            a.sx[i] = n0;
-            a.sy[i] = n1;
-            a.sz[i] = n2;
-        }
+        int sysid;
+        double v[5];
+        const bool accept = mc_trial<R, Mode, 0>(a, m, __ldg(m.order + k), step, tab, sysid, v);
         // accepted moves per system, one atomic per (warp, system)
         const unsigned act = __activemask();
-        const unsigned same = __match_any_sync(act, mt.sys);
+        const unsigned same = __match_any_sync(act, sysid);
         const unsigned yes = __ballot_sync(act, accept);
         if ((int)(threadIdx.x & 31) == __ffs(same) - 1)
-            atomicAdd(m.acc + mt.sys, (unsigned long long)__popc(yes & same));
+            atomicAdd(m.acc + sysid, (unsigned long long)__popc(yes & same));
+    }
+}
+
+// A colour pass tile by tile that also sums the record terms of the pre-step state of its
+// spins (tile partials in the block's fixed order), for lattices of at most two classes.
+template <typename R, int BS, int Mode, bool First>
+__global__ void __launch_bounds__(BS) k_mc_colour_rec(const KArgs<R> a, const McArgs m) {
+    __shared__ SmemTables tab;
+    __shared__ double red[(BS / 32) * 8];
+    stage_tables(a, tab);
+    __syncthreads();
+    const uint64_t step = *a.step;
+    for (int64_t t = blockIdx.x; t < m.ntiles; t += gridDim.x) {
+        const TileDesc td = m.tiles[t];
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = threadIdx.x; k < td.count; k += BS) {
+            int sysid;
+            double v[5];
+            const bool accept = mc_trial<R, Mode, First ? 1 : 2>(a, m, __ldg(m.order + td.start + k), step, tab,
+                                                                 sysid, v);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) acc[c] += v[c];
+            // a tile lies in one system: one atomic per warp
+            const unsigned act = __activemask();
+            const unsigned yes = __ballot_sync(act, accept);
+            if ((int)(threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(m.acc + sysid, (unsigned long long)__popc(yes));
+        }
+        const double r = block_sum8<BS>(acc, red);
+        if (threadIdx.x < kPartComps) m.partials[(int64_t)m.slot[t] * kPartComps + threadIdx.x] = r;
     }
 }
 

@@ -104,6 +104,24 @@ int corrector_blocks_per_sm(int block, bool draw_ahead, int mode) {
 }
 
 template <typename R>
+cudaError_t launch_mc_colour_rec(const KArgs<R> &a, const McArgs &m, int grid, cudaStream_t s) {
+    constexpr int BS = 256;
+    const bool general = a.J_tensor || a.any_cubic;
+    if (m.first) {
+        if (general)
+            k_mc_colour_rec<R, BS, kGeneral, true><<<grid, BS, 0, s>>>(a, m);
+        else
+            k_mc_colour_rec<R, BS, kPlain, true><<<grid, BS, 0, s>>>(a, m);
+    } else {
+        if (general)
+            k_mc_colour_rec<R, BS, kGeneral, false><<<grid, BS, 0, s>>>(a, m);
+        else
+            k_mc_colour_rec<R, BS, kPlain, false><<<grid, BS, 0, s>>>(a, m);
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_mc_colour(const KArgs<R> &a, const McArgs &m, int block, int grid, cudaStream_t s) {
     if (a.J_tensor || a.any_cubic) {
         SS_BLOCK_SWITCH(block, k_mc_colour<R, BS, kGeneral><<<grid, BS, 0, s>>>(a, m));
@@ -249,6 +267,7 @@ template int persistent_blocks_per_sm<SS_REAL>(int, int);
 template int step_blocks_per_sm<SS_REAL>(int, int);
 template int corrector_blocks_per_sm<SS_REAL>(int, bool, int);
 template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
+template cudaError_t launch_mc_colour_rec<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);
 template int mc_blocks_per_sm<SS_REAL>(int, int);
 template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
 template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
