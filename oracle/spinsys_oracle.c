@@ -105,7 +105,8 @@
  *   I2  The implicit equation is solved by K fixed-point iterations from the Euler predictor
  *       S^(0) = S_n + dt f(S_n): S^(k+1) = S_n + dt f((S_n + S^(k))/2), k = 0 .. K-1, and
  *       S_{n+1} = S^(K); nothing is renormalised.
- *   I3  The record holds the state at the start of each step (R7).
+ *   I3  The record holds the state at the start of each step (R7); the demagnetising field,
+ *       when on, is updated as for Heun (D4) and held, like the thermal field, over the step.
  *
  * Semi-implicit predictor-corrector (the modified predictor-corrector midpoint scheme the
  * paper cites, Mentink et al. 2010, their scheme B), readings:
@@ -118,7 +119,7 @@
  *       spin, solved in closed form: with b = (dt/2) A and c = S_n + S_n x b, the new spin is
  *       (c - b x c + (b.c) b)/(1 + |b|^2), a rotation of S_n, so |S| is kept without
  *       renormalisation.
- *   P3  The record holds the state at the start of each step (R7).
+ *   P3  The record holds the state at the start of each step (R7); the demagnetising field as I3.
  *
  * Layout: spins and vectors are array-of-structures, 3 doubles per site (x, y, z).
  * Neel tensors are 6 doubles per site in the order xx, yy, zz, xy, xz, yz.
@@ -581,8 +582,11 @@ int orc_midpoint_run(const orc_system *s, double *S, int64_t step0, int64_t nste
     size_t sz = sizeof(double) * 3 * (size_t)(n > 0 ? n : 1);
     double *Hth = (double *)malloc(sz), *X = (double *)malloc(sz), *Y = (double *)malloc(sz);
     double *M = (double *)malloc(sz);
-    if (!Hth || !X || !Y || !M) {
-        free(Hth); free(X); free(Y); free(M);
+    int demag = s->demag_cell > 0.0;
+    int64_t every = s->demag_every > 0 ? s->demag_every : 1;
+    double *Hd = demag ? (double *)calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double)) : NULL;
+    if (!Hth || !X || !Y || !M || (demag && !Hd)) {
+        free(Hth); free(X); free(Y); free(M); free(Hd);
         return -1;
     }
     double gamma = s->gamma > 0.0 ? s->gamma : ORC_GAMMA;
@@ -592,6 +596,15 @@ int orc_midpoint_run(const orc_system *s, double *S, int64_t step0, int64_t nste
         double Tn = T[k];
         if (rec) orc_moment_energy(s, S, rec + 8 * k);
         orc_thermal_field(s, step, Tn, gamma, lambda, Hth);
+        /* demagnetising field from the state at the start of the step, held (D4) */
+        if (demag && (k == 0 || (step0 + k) % every == 0)) {
+            if (orc_demag_fields(s, S, Hd, NULL) < 0) {
+                free(Hth); free(X); free(Y); free(M); free(Hd);
+                return -1;
+            }
+        }
+        if (demag)
+            for (int64_t q = 0; q < 3 * n; ++q) Hth[q] += Hd[q];  /* both are held over the step */
         /* Euler predictor S^(0) = S_n + dt f(S_n) (I2), into X */
 #pragma omp parallel for schedule(static) num_threads(g_threads)
         for (int64_t i = 0; i < n; ++i) {
@@ -619,7 +632,7 @@ int orc_midpoint_run(const orc_system *s, double *S, int64_t step0, int64_t nste
         }
         memcpy(S, X, sz);
     }
-    free(Hth); free(X); free(Y); free(M);
+    free(Hth); free(X); free(Y); free(M); free(Hd);
     return 0;
 }
 
@@ -655,8 +668,11 @@ int orc_sib_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, c
     size_t sz = sizeof(double) * 3 * (size_t)(n > 0 ? n : 1);
     double *Hth = (double *)malloc(sz), *P = (double *)malloc(sz), *M = (double *)malloc(sz);
     double *X = (double *)malloc(sz);
-    if (!Hth || !P || !M || !X) {
-        free(Hth); free(P); free(M); free(X);
+    int demag = s->demag_cell > 0.0;
+    int64_t every = s->demag_every > 0 ? s->demag_every : 1;
+    double *Hd = demag ? (double *)calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double)) : NULL;
+    if (!Hth || !P || !M || !X || (demag && !Hd)) {
+        free(Hth); free(P); free(M); free(X); free(Hd);
         return -1;
     }
     double gamma = s->gamma > 0.0 ? s->gamma : ORC_GAMMA;
@@ -665,6 +681,15 @@ int orc_sib_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, c
         uint32_t step = (uint32_t)(step0 + k);
         if (rec) orc_moment_energy(s, S, rec + 8 * k);
         orc_thermal_field(s, step, T[k], gamma, lambda, Hth);
+        /* demagnetising field from the state at the start of the step, held (D4) */
+        if (demag && (k == 0 || (step0 + k) % every == 0)) {
+            if (orc_demag_fields(s, S, Hd, NULL) < 0) {
+                free(Hth); free(P); free(M); free(X); free(Hd);
+                return -1;
+            }
+        }
+        if (demag)
+            for (int64_t q = 0; q < 3 * n; ++q) Hth[q] += Hd[q];  /* both are held over the step */
         /* predictor with A(S_n) */
 #pragma omp parallel for schedule(static) num_threads(g_threads)
         for (int64_t i = 0; i < n; ++i) {
@@ -687,7 +712,7 @@ int orc_sib_run(const orc_system *s, double *S, int64_t step0, int64_t nsteps, c
         }
         memcpy(S, X, sz);
     }
-    free(Hth); free(P); free(M); free(X);
+    free(Hth); free(P); free(M); free(X); free(Hd);
     return 0;
 }
 

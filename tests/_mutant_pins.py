@@ -389,10 +389,26 @@ def pin_sib():
     return np.abs(got[0] - ref).max() <= 1e-13
 
 
+def pin_alt_demag():
+    """The alternative integrators with the demagnetising field as the only field converge
+    to the Heun trajectory at second order."""
+    lat = L.simple_cubic(6, 6, 2, periodic=(False, False, False), J=0.0, k_u=0.0, with_pos=True)
+    mk = lambda dt: O.OracleSystem(  # noqa: E731
+        lat.row_ptr, lat.col, lat.J, lat.mu_s, lat.k_u, lat.easy_axis, alpha=0.5, dt=dt, seed=5, pos=lat.pos,
+        demag_cell=6e-10, demag_vatom=(3e-10) ** 3, demag_every=1)
+    S0 = L.random_state(lat.n, 1)
+    for run in (lambda s, n: O.midpoint_run(s, S0, n, 0.0, iters=30)[0], lambda s, n: O.sib_run(s, S0, n, 0.0)[0]):
+        d = [np.abs(run(mk(dt), int(round(4e-11 / dt))) - O.heun_run(mk(dt), S0, int(round(4e-11 / dt)), 0.0)[0]).max()
+             for dt in (2e-13, 1e-13)]
+        if not 3.5 < d[0] / d[1] < 4.5:
+            return False
+    return True
+
+
 PINS = [pin_field_gradient, pin_single_spin_analytic, pin_unit_length, pin_gaussians, pin_philox_against_torch,
         pin_boltzmann, pin_curie, pin_mc_boltzmann, pin_mc_langevin, pin_mc_dimer, pin_mc_moves, pin_mc_sigma,
         pin_mc_zero_T, pin_colouring, pin_demag, pin_tensor_cubic, pin_mc_cubic, pin_midpoint,
-        pin_sib]
+        pin_sib, pin_alt_demag]
 
 if __name__ == "__main__":
     for p in PINS:

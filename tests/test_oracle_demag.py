@@ -146,3 +146,33 @@ def test_update_interval_holds_the_field_between_updates():
                          seed=5)
     none, _ = O.heun_run(off, S0, 10, 50.0)
     assert np.abs(none - one).max() > 1e-6
+
+
+@pytest.mark.parametrize("scheme", ["midpoint", "semi_implicit"])
+def test_alternative_integrators_hold_the_field_and_agree_with_heun(scheme):
+    """The midpoint rule and the semi-implicit scheme take the held field as the Heun step
+    does (reading D4): one run of 10 steps equals two of 5 with updates every 5, and with the
+    field updated every step their difference from the Heun trajectory falls as dt^2 (a field
+    left out or taken at another state would leave an O(1) difference)."""
+    lat = L.simple_cubic(8, 8, 2, periodic=(False, False, False), J=6e-21, k_u=0.0, with_pos=True)
+    mk = lambda every, dt, J=1.0: O.OracleSystem(  # noqa: E731
+        lat.row_ptr, lat.col, J * lat.J, lat.mu_s, lat.k_u, lat.easy_axis, alpha=0.5, dt=dt, seed=5, pos=lat.pos,
+        demag_cell=6e-10, demag_vatom=(3e-10) ** 3, demag_every=every)
+    if scheme == "midpoint":
+        run = lambda s, S, n, st=0: O.midpoint_run(s, S, n, 0.0, iters=30, step0=st)  # noqa: E731
+    else:
+        run = lambda s, S, n, st=0: O.sib_run(s, S, n, 0.0, step0=st)  # noqa: E731
+    S0 = L.random_state(lat.n, 1)
+    one, _ = run(mk(5, 1e-15), S0, 10)
+    half, _ = run(mk(5, 1e-15), S0, 5)
+    two, _ = run(mk(5, 1e-15), half, 5, 5)
+    assert np.array_equal(one, two)
+    # with exchange (20 fs), and with the demagnetising field as the only field (40 ps)
+    for J, dts, t_end in ((1.0, (4e-16, 2e-16, 1e-16), 2e-14), (0.0, (2e-13, 1e-13, 5e-14), 4e-11)):
+        d = []
+        for dt in dts:
+            nst = int(round(t_end / dt))
+            a, _ = run(mk(1, dt, J), S0, nst)
+            b, _ = O.heun_run(mk(1, dt, J), S0, nst, 0.0)
+            d.append(np.abs(a - b).max())
+        assert 3.5 < d[0] / d[1] < 4.5 and 3.5 < d[1] / d[2] < 4.5

@@ -87,6 +87,8 @@ MUTANTS = [
      "            orc_site_field(s, S, i, hex, H);\n            for (int c = 0; c < 3; ++c) H[c] += Hth[3 * i + c];\n            orc_sib_a(gamma, lambda, M + 3 * i, H, A);"),
     ("semi-implicit damping term at S_n in the corrector", "            orc_sib_a(gamma, lambda, M + 3 * i, H, A);",
      "            orc_sib_a(gamma, lambda, S + 3 * i, H, A);"),
+    ("midpoint without the demagnetising field", "            for (int64_t q = 0; q < 3 * n; ++q) Hth[q] += Hd[q];  /* both are held over the step */\n        /* Euler predictor",
+     "            (void)0;\n        /* Euler predictor"),
     ("semi-implicit solve with b x c added", "X[k] = (c[k] - bxc[k] + bc * b[k]) / (1.0 + bb);",
      "X[k] = (c[k] + bxc[k] + bc * b[k]) / (1.0 + bb);"),
 ]
