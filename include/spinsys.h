@@ -230,9 +230,10 @@ ss_status get_mc_stats(ss_system *h, int32_t sys, int64_t out[2]);
  * Philox counters as llg_heun_step, held over the step).  Solved by `iterations` (1..1000)
  * fixed-point iterations from the Euler predictor; nothing is renormalised (the rule keeps
  * |S| when converged; the residual of the iteration shows in |S| - 1).  Shares the step
- * counter, record ring and temperatures with llg_heun_step; runs iterations + 3 launches
- * per step (the first also sums the step's record).  SS_ERR_INVALID_ARG for n < 0, iterations out of range, or the demagnetising
- * field switched on (set_demag), which this rule does not include. */
+ * counter, record ring, temperatures and demagnetising field (set_demag: updated at the same
+ * steps, held over each step) with llg_heun_step; runs iterations + 3 launches per step (the
+ * first also sums the step's record).  SS_ERR_INVALID_ARG for n < 0 or iterations out of
+ * range. */
 ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations);
 
 /* Advance every system by n >= 0 steps of the semi-implicit predictor-corrector scheme
@@ -243,8 +244,9 @@ ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations);
  * x A(Sb), Sb = (S_n + S')/2, each in closed form (a rotation of S_n: |S| is kept without
  * renormalisation); H includes the step's thermal field, drawn once per step from the same
  * Philox counters as llg_heun_step and held over the step.  Shares the step counter, record
- * ring and temperatures with llg_heun_step; 4 launches per step (the predictor also sums the
- * step's record), captured in CUDA graphs for runs of whole graphs.  SS_ERR_INVALID_ARG for n < 0 or with the demagnetising field on. */
+ * ring, temperatures and demagnetising field (as llg_midpoint_step) with llg_heun_step; 4
+ * launches per step (the predictor also sums the step's record), captured in CUDA graphs for
+ * runs of whole graphs.  SS_ERR_INVALID_ARG for n < 0. */
 ss_status llg_semi_implicit_step(ss_system *h, int64_t n);
 
 /* Copy all spins (concatenated over systems) to out3n [3n], AoS, FP64 (synchronous). */

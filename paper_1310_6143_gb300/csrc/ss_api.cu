@@ -1429,6 +1429,25 @@ ss_status integrate_captured(ss_system *h, int64_t n, int key, F enqueue, const 
     return SS_OK;
 }
 
+// As integrate_captured, with the demagnetising field (when on) recomputed at multiples of its
+// interval (and when stale) and held in between: the steps between two updates run as one chunk.
+template <typename F>
+ss_status integrate_with_demag(ss_system *h, int64_t n, int key, F enqueue, const char *what) {
+    if (!h->demag_on) return integrate_captured(h, n, key, enqueue, what);
+    while (n > 0) {
+        const int64_t r = h->step % h->demag_every;
+        if (r == 0 || h->demag_stale) {
+            const cudaError_t e = demag_update(h);
+            if (e != cudaSuccess) return cuda_fail(h, e, "demagnetising field");
+        }
+        const int64_t chunk = std::min<int64_t>(n, h->demag_every - r);
+        const ss_status st = integrate_captured(h, chunk, key, enqueue, what);
+        if (st != SS_OK) return st;
+        n -= chunk;
+    }
+    return SS_OK;
+}
+
 // Semi-implicit predictor-corrector steps: predictor (with the record's tile partials),
 // record, corrector, step counter.
 template <typename R>
@@ -1699,24 +1718,21 @@ ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations) {
     if (st != SS_OK) return st;
     if (n < 0) return fail(h, SS_ERR_INVALID_ARG, "n must be >= 0");
     if (iterations < 1 || iterations > 1000) return fail(h, SS_ERR_INVALID_ARG, "iterations must be 1..1000");
-    if (h->demag_on) return fail(h, SS_ERR_INVALID_ARG, "the midpoint rule runs without the demagnetising field");
     auto enqueue = [h, iterations](int64_t k) {
         return h->precision == SS_FP32_MIXED ? enqueue_midpoint<float>(h, k, iterations)
                                              : enqueue_midpoint<double>(h, k, iterations);
     };
-    return integrate_captured(h, n, iterations, enqueue, "midpoint step");
+    return integrate_with_demag(h, n, iterations, enqueue, "midpoint step");
 }
 
 ss_status llg_semi_implicit_step(ss_system *h, int64_t n) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
     if (n < 0) return fail(h, SS_ERR_INVALID_ARG, "n must be >= 0");
-    if (h->demag_on)
-        return fail(h, SS_ERR_INVALID_ARG, "the semi-implicit scheme runs without the demagnetising field");
     auto enqueue = [h](int64_t k) {
         return h->precision == SS_FP32_MIXED ? enqueue_sib<float>(h, k) : enqueue_sib<double>(h, k);
     };
-    return integrate_captured(h, n, -1, enqueue, "semi-implicit step");
+    return integrate_with_demag(h, n, -1, enqueue, "semi-implicit step");
 }
 
 ss_status set_demag(ss_system *h, double cell_size, double atom_volume, int32_t every) {

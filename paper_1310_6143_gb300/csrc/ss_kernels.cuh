@@ -936,6 +936,7 @@ __device__ __forceinline__ void alt_first_pass(const KArgs<R> &a, const SmemTabl
             a.hz[i] = fma((R)0.5, x2, c2);
             R H0, H1, H2;
             const R sde = det_field<R, Mode != kPlain>(m, s0, s1, s2, x0 + c0, x1 + c1, x2 + c2, H0, H1, H2);
+            if (a.demag) add_demag(a, i, H0, H1, H2);
             double v[5];
             spin_terms<R, Mode != kPlain>(m, s0, s1, s2, x0 + ha0, x1 + ha1, x2 + ha2, sde, v);
 #pragma unroll
@@ -985,6 +986,7 @@ __global__ void k_mid_iter(const KArgs<R> a, const R *xx, const R *xy, const R *
         R H0, H1, H2;
         det_field<R, Mode != kPlain>(m, m0, m1, m2, fma((R)0.5, x0, a.hx[i]), fma((R)0.5, x1, a.hy[i]),
                                      fma((R)0.5, x2, a.hz[i]), H0, H1, H2);
+        if (a.demag) add_demag(a, i, H0, H1, H2);
         R d0, d1, d2;
         llg_rhs(m.gp, m.lambda, m0, m1, m2, H0, H1, H2, d0, d1, d2);
         const R v0 = fma(m.dt, d0, s0), v1 = fma(m.dt, d1, s1), v2 = fma(m.dt, d2, s2);
@@ -1018,6 +1020,7 @@ __global__ void k_sib_corr(const KArgs<R> a) {
         R H0, H1, H2;
         det_field<R, Mode != kPlain>(m, m0, m1, m2, fma((R)0.5, x0, a.hx[i]), fma((R)0.5, x1, a.hy[i]),
                                      fma((R)0.5, x2, a.hz[i]), H0, H1, H2);
+        if (a.demag) add_demag(a, i, H0, H1, H2);
         R a0, a1, a2;
         sib_a(m.gp, m.lambda, m0, m1, m2, H0, H1, H2, a0, a1, a2);
         R v0, v1, v2;

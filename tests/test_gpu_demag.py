@@ -163,3 +163,34 @@ def test_paper_platelet_and_ellipsoid_through_the_library(SS):
         Hx = s.demag_field()
     shift = Hz[:, 2].mean() - Hx[:, 0].mean()  # (N_x - N_z) mu0 M, since H_k = -N_k mu0 M
     assert shift == pytest.approx(0.33, rel=0.08)
+
+
+@pytest.mark.parametrize("scheme", ["midpoint", "semi_implicit"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_alternative_integrators_with_the_field_match_oracle(SS, scheme, precision, tol):
+    """The midpoint rule and the semi-implicit scheme with the field updated every 5 steps,
+    then Heun steps from a multiple of the interval (the oracle recomputes the field at the
+    first step of each run, the library at multiples of the interval), against the oracle."""
+    a = 3e-10
+    lat = _lat(10, 10, 3, a)
+    S0 = L.random_state(lat.n, 9)
+    kw = dict(alpha=0.3, dt=2e-16, seed=6)
+    with SS(lat, T=100.0, S0=S0, precision=precision, **kw) as s:
+        s.set_demag(2 * a, a ** 3, every=5)
+        if scheme == "midpoint":
+            s.midpoint_step(20, iterations=3)
+        else:
+            s.semi_implicit_step(20)
+        s.step(5)
+        S_gpu = s.spins()
+        rec = s.record(0, 25)
+    ref = _oracle(lat, 2 * a, a ** 3, every=5, **kw)
+    if scheme == "midpoint":
+        S_ref, r1 = O.midpoint_run(ref, S0, 20, 100.0, iters=3, record=True)
+    else:
+        S_ref, r1 = O.sib_run(ref, S0, 20, 100.0, record=True)
+    S_ref, r2 = O.heun_run(ref, S_ref, 5, 100.0, step0=20, record=True)
+    assert np.abs(S_gpu - S_ref).max() <= tol
+    if precision == "fp64":
+        rr = np.concatenate([r1, r2])
+        assert np.abs(rec[:, 0, 7] - rr[:, 7]).max() <= 1e-12 * np.abs(rr[:, 7]).max()

@@ -131,10 +131,6 @@ def test_invalid_arguments(SS):
                 s.midpoint_step(1, iterations=bad)
         with pytest.raises(Exception, match=">= 0"):
             s.midpoint_step(-1)
-        s.set_demag(6e-10, 2.7e-29)
-        with pytest.raises(Exception, match="demagnetising"):
-            s.midpoint_step(1)
-        s.set_demag(0.0, 0.0)
         s.midpoint_step(2)
         assert s.step_index == 2
 

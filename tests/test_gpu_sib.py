@@ -125,9 +125,5 @@ def test_invalid_arguments(SS):
     with SS(lat, T=0.0) as s:
         with pytest.raises(Exception, match=">= 0"):
             s.semi_implicit_step(-1)
-        s.set_demag(6e-10, 2.7e-29)
-        with pytest.raises(Exception, match="demagnetising"):
-            s.semi_implicit_step(1)
-        s.set_demag(0.0, 0.0)
         s.semi_implicit_step(2)
         assert s.step_index == 2
