@@ -353,6 +353,15 @@ ss_status ss_debug_gaussians(uint64_t seed, uint32_t sys_id, uint32_t step, int6
  * rate.  Synchronous; allocates and frees a small device buffer. */
 ss_status ss_debug_fp64_rate(int32_t mode, double *inst_per_s);
 
+/* Test hooks for failure handling (process-wide, thread-safe).  ss_debug_fail_allocations:
+ * after `after` (>= 0) more successful device allocations by the handles of this process,
+ * every device allocation fails as if the device were out of memory, so the calls that
+ * allocate (create, set_demag, the first mc_step, ...) return SS_ERR_OOM; a negative value
+ * switches the injection off.  ss_debug_live_bytes: the device bytes currently held by all
+ * handles of this process (a failed create holds none). */
+ss_status ss_debug_fail_allocations(int64_t after);
+int64_t ss_debug_live_bytes(void);
+
 /* ---------------------------------------------------------------------------------
  * Allocation-free stepping.  The paper has no counterpart of this entry point.
  *

@@ -30,6 +30,7 @@ EXPORTS = (
     "spin_system_set_barrier_test", "spin_system_sync", "spin_system_time_kernels", "ss_debug_philox", "ss_debug_gaussians",
     "llg_heun_step_noalloc", "spin_system_set_draw_ahead", "ss_debug_fp64_rate", "mc_step", "get_mc_stats", "set_demag", "llg_midpoint_step",
     "spin_system_set_exchange_rows", "spin_system_time_rows", "llg_semi_implicit_step",
+    "ss_debug_fail_allocations", "ss_debug_live_bytes",
     "get_demag_field",
     "ss_last_error", "ss_status_string",
 )
@@ -117,6 +118,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "mc_step": [P, I64],
         "llg_midpoint_step": [P, I64, I32],
         "llg_semi_implicit_step": [P, I64],
+        "ss_debug_fail_allocations": [I64],
         "get_mc_stats": [P, I32, P],
         "set_demag": [P, D, D, I32],
         "get_demag_field": [P, P],
@@ -146,6 +148,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.ss_debug_live_bytes.argtypes = []
+    lib.ss_debug_live_bytes.restype = ctypes.c_int64
     lib.ss_last_error.argtypes = [P]
     lib.ss_last_error.restype = ctypes.c_char_p
     lib.ss_status_string.argtypes = [ctypes.c_int]

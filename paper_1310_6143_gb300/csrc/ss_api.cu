@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -199,13 +200,24 @@ ss_status cuda_fail(ss_system *h, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
     } while (0)
 
+// Allocation-failure injection (ss_debug_fail_allocations): < 0 off, else the successful
+// allocations left before every allocation fails; and the bytes held by all handles.
+std::atomic<int64_t> g_fail_after{-1};
+std::atomic<int64_t> g_live_bytes{0};
+
 cudaError_t dalloc(ss_system *h, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    int64_t left = g_fail_after.load();
+    while (left >= 0) {
+        if (left == 0) return cudaErrorMemoryAllocation;
+        if (g_fail_after.compare_exchange_weak(left, left - 1)) break;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) return e;
     h->bufs.push_back({*p, bytes});
     h->device_bytes += bytes;
+    g_live_bytes += (int64_t)bytes;
     return cudaSuccess;
 }
 
@@ -214,6 +226,7 @@ void dfree(ss_system *h, void *p) {
         if (h->bufs[i].p == p) {
             cudaFree(p);
             h->device_bytes -= h->bufs[i].bytes;
+            g_live_bytes -= (int64_t)h->bufs[i].bytes;
             h->bufs.erase(h->bufs.begin() + (long)i);
             return;
         }
@@ -1528,7 +1541,10 @@ ss_status spin_system_destroy(ss_system *h) {
     if (!h) return SS_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graph(h);
-    for (auto &b : h->bufs) cudaFree(b.p);
+    for (auto &b : h->bufs) {
+        cudaFree(b.p);
+        g_live_bytes -= (int64_t)b.bytes;
+    }
     h->bufs.clear();
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -2160,6 +2176,13 @@ ss_status spin_system_set_barrier_test(ss_system *h, int32_t extra, int64_t time
     drop_graph(h);
     return SS_OK;
 }
+
+ss_status ss_debug_fail_allocations(int64_t after) {
+    g_fail_after.store(after < 0 ? -1 : after);
+    return SS_OK;
+}
+
+int64_t ss_debug_live_bytes(void) { return g_live_bytes.load(); }
 
 ss_status ss_debug_philox(const uint32_t ctr0[4], const uint32_t key[2], int64_t count, uint32_t *out) {
     if (!ctr0 || !key || !out || count < 0) return fail(nullptr, SS_ERR_INVALID_ARG, "bad arguments");

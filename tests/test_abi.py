@@ -23,7 +23,7 @@ def lib():
 def _declared():
     txt = open(os.path.join(ROOT, "include", "spinsys.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return set(re.findall(r"^\s*(?:ss_status|const char \*)\s*(\w+)\s*\(", txt, flags=re.M))
+    return set(re.findall(r"^\s*(?:ss_status|const char \*|int64_t)\s*(\w+)\s*\(", txt, flags=re.M))
 
 
 def test_header_declares_the_boundary():
