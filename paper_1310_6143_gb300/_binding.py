@@ -98,7 +98,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    path = path or os.environ.get("SPINSYS_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"libspinsys.so not found at {path}: build it with "
                           "`python -c 'import __graft_entry__ as g; g.build()'` (CUDA path is mandatory)")

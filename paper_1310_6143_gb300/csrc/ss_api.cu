@@ -380,6 +380,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.Jd = static_cast<const R *>(h->Jd);
     a.nJd = h->nJd;
     a.demag = h->demag_on ? 1 : 0;
+    a.ncell = h->ncell;
     a.mc_of = h->d_cell_of;
     a.hdx = static_cast<const R *>(h->d_hd[0]);
     a.hdy = static_cast<const R *>(h->d_hd[1]);
@@ -620,6 +621,9 @@ ss_status check_device_flags(ss_system *h) {
         const unsigned long long zero[3] = {ctl[0], 0ull, 0ull};
         SS_CUDA(h, cudaMemcpyAsync(h->ctl, zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream));
         SS_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (err & kErrBounds)
+            return fail(h, SS_ERR_STATE, "a kernel met an index out of its range (checked build); step counter at %lld",
+                        (long long)h->step);
         if (err & kErrTimeout) {
             SS_CUDA(h, invalidate_ahead(h));  // an aborted launch may have drawn part of a step
             SS_CUDA(h, cudaStreamSynchronize(h->stream));

@@ -96,6 +96,7 @@ struct KArgs {
     const int32_t *mc_of;     // [n] macrocell of each spin (demagnetising field)
     const R *hdx, *hdy, *hdz; // [ncell] demagnetising field of each macrocell (T)
     int demag;                // 1: add the macrocell field to every spin's field
+    int64_t ncell;            // macrocells (index bound of mc_of)
     const int32_t *mat;       // [n] material index
     const MatDesc<R> *mats;
     const SysDesc *sys;
@@ -164,6 +165,7 @@ struct DemagArgs {
 
 constexpr unsigned int kErrNonFinite = 1u;
 constexpr unsigned int kErrTimeout = 2u;
+constexpr unsigned int kErrBounds = 4u;   // checked builds: an index out of its range was met
 
 // Host helper (ss_api.cu): sets the message returned by ss_last_error(NULL).
 void set_global_error(const char *msg);

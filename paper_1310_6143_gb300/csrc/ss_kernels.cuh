@@ -81,6 +81,22 @@ __device__ __forceinline__ void stage_tables(const KArgs<R> &a, SmemTables &t) {
 // beforehand by k_rows_sell / k_rows_field; cubic per material).
 constexpr int kPlain = 0, kGeneral = 1, kRows = 2;
 
+// Checked builds (SS_CHECKED): an index about to be gathered with is checked against [0, n);
+// a bad one sets kErrBounds in the error word and is replaced by 0, so nothing outside the
+// arrays is read.  Other builds return it unchanged.
+__device__ __forceinline__ int32_t chk(int64_t j, int64_t n, unsigned int *err) {
+#ifdef SS_CHECKED
+    if (j < 0 || j >= n) {
+        atomicOr(err, kErrBounds);
+        return 0;
+    }
+#else
+    (void)n;
+    (void)err;
+#endif
+    return (int32_t)j;
+}
+
 template <typename R, bool Coherent, int Mode = kGeneral>
 __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &sd, const R *X, const R *Y,
                                              const R *Z, int64_t i, R &e0, R &e1, R &e2) {
@@ -95,7 +111,7 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
     R x = sys_H(sd, 0, R()), y = sys_H(sd, 1, R()), z = sys_H(sd, 2, R());
     if (Mode == kGeneral && a.J_tensor) {  // Eq. HJijSMS: the tensor of bond k applied to S_j
         for (int32_t k = b; k < e; ++k) {
-            const int32_t j = __ldg(a.col + k);
+            const int32_t j = chk(__ldg(a.col + k), a.n, a.err);
             const R *t = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + k);
             const R sx = ld<Coherent>(X + j), sy = ld<Coherent>(Y + j), sz = ld<Coherent>(Z + j);
             x = fma(__ldg(t + 0), sx, fma(__ldg(t + 1), sy, fma(__ldg(t + 2), sz, x)));
@@ -108,7 +124,7 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
         return;
     }
     for (int32_t k = b; k < e; ++k) {
-        const int32_t j = __ldg(a.col + k);
+        const int32_t j = chk(__ldg(a.col + k), a.n, a.err);
         const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + k);
         x = fma(Jk, ld<Coherent>(X + j), x);
         y = fma(Jk, ld<Coherent>(Y + j), y);
@@ -146,7 +162,7 @@ __device__ __forceinline__ R det_field(const MatDesc<R> &m, R s0, R s1, R s2, R 
 // field is held between updates, so it is read like a parameter).
 template <typename R>
 __device__ __forceinline__ void add_demag(const KArgs<R> &a, int64_t i, R &H0, R &H1, R &H2) {
-    const int32_t c = __ldg(a.mc_of + i);
+    const int32_t c = chk(__ldg(a.mc_of + i), a.ncell, a.err);
     H0 += __ldg(a.hdx + c);
     H1 += __ldg(a.hdy + c);
     H2 += __ldg(a.hdz + c);
@@ -750,9 +766,9 @@ __global__ void __launch_bounds__(256) k_rows_sell(const KArgs<R> a) {
 #pragma unroll 8
         for (int k = 0; k < w; ++k) {
             const uint32_t b = __ldg(p + 32 * (int64_t)k);
-            const R Jk = jd[b & 255u];
+            const R Jk = jd[chk(b & 255u, a.nJd, a.err)];
             R s0, s1, s2;
-            load_spin4(a.x4, (int32_t)(b >> 8), s0, s1, s2);
+            load_spin4(a.x4, chk(b >> 8, a.n, a.err), s0, s1, s2);
             x = fma(Jk, s0, x);
             y = fma(Jk, s1, y);
             z = fma(Jk, s2, z);
@@ -786,13 +802,13 @@ __global__ void __launch_bounds__(256) k_rows_field(const KArgs<R> a, const R *X
 #pragma unroll 4
             for (int32_t k = b + lane; k < e; k += 32) {
                 if (Mode == 1) {
-                    const int32_t j = __ldg(a.col + k);
+                    const int32_t j = chk(__ldg(a.col + k), a.n, a.err);
                     const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + k);
                     x = fma(Jk, X[j], x);
                     y = fma(Jk, Y[j], y);
                     z = fma(Jk, Z[j], z);
                 } else {
-                    const int32_t j = __ldg(a.col + k);
+                    const int32_t j = chk(__ldg(a.col + k), a.n, a.err);
                     const R *t = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + k);
                     const R s0 = X[j], s1 = Y[j], s2 = Z[j];
                     x = fma(__ldg(t + 0), s0, fma(__ldg(t + 1), s1, fma(__ldg(t + 2), s2, x)));
@@ -838,7 +854,7 @@ __device__ __forceinline__ void exchange_bare(const KArgs<R> &a, const R *X, con
     R x = 0, y = 0, z = 0;
     if (Mode != kPlain && a.J_tensor) {
         for (int32_t k = b; k < e; ++k) {
-            const int32_t j = __ldg(a.col + k);
+            const int32_t j = chk(__ldg(a.col + k), a.n, a.err);
             const R m0 = X[j], m1 = Y[j], m2 = Z[j];
             const R *t = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + k);
             x = fma(__ldg(t + 0), m0, fma(__ldg(t + 1), m1, fma(__ldg(t + 2), m2, x)));
@@ -848,14 +864,14 @@ __device__ __forceinline__ void exchange_bare(const KArgs<R> &a, const R *X, con
     } else if (a.J_uniform) {
         const R Jk = a.J_value;
         for (int32_t k = b; k < e; ++k) {
-            const int32_t j = __ldg(a.col + k);
+            const int32_t j = chk(__ldg(a.col + k), a.n, a.err);
             x = fma(Jk, X[j], x);
             y = fma(Jk, Y[j], y);
             z = fma(Jk, Z[j], z);
         }
     } else {
         for (int32_t k = b; k < e; ++k) {
-            const int32_t j = __ldg(a.col + k);
+            const int32_t j = chk(__ldg(a.col + k), a.n, a.err);
             const R Jk = __ldg(a.J + k);
             x = fma(Jk, X[j], x);
             y = fma(Jk, Y[j], y);
@@ -1247,7 +1263,7 @@ __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs
     for (int64_t k = m.c0 + (int64_t)blockIdx.x * BS + threadIdx.x; k < m.c1; k += (int64_t)gridDim.x * BS) {
         int sysid;
         double v[5];
-        const bool accept = mc_trial<R, Mode, 0>(a, m, __ldg(m.order + k), step, tab, sysid, v);
+        const bool accept = mc_trial<R, Mode, 0>(a, m, chk(__ldg(m.order + k), a.n, a.err), step, tab, sysid, v);
         // accepted moves per system, one atomic per (warp, system)
         const unsigned act = __activemask();
         const unsigned same = __match_any_sync(act, sysid);
@@ -1272,8 +1288,8 @@ __global__ void __launch_bounds__(BS) k_mc_colour_rec(const KArgs<R> a, const Mc
         for (int k = threadIdx.x; k < td.count; k += BS) {
             int sysid;
             double v[5];
-            const bool accept = mc_trial<R, Mode, First ? 1 : 2>(a, m, __ldg(m.order + td.start + k), step, tab,
-                                                                 sysid, v);
+            const bool accept = mc_trial<R, Mode, First ? 1 : 2>(a, m, chk(__ldg(m.order + td.start + k), a.n, a.err),
+                                                                 step, tab, sysid, v);
 #pragma unroll
             for (int c = 0; c < 5; ++c) acc[c] += v[c];
             // a tile lies in one system: one atomic per warp
