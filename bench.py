@@ -185,9 +185,36 @@ def cpu_baseline(lat, T, seconds=15.0):
         S, _ = O.heun_run(ref, S, extra, T[1:1 + extra], step0=1, record=True)
         one = (one + time.perf_counter() - t1)
         steps += extra
+    # one more step on a single thread
+    O.set_threads(1)
+    t2 = time.perf_counter()
+    S, _ = O.heun_run(ref, S, 1, T[steps:steps + 1], step0=steps, record=True)
+    single = time.perf_counter() - t2
+    O.set_threads(threads)
     return {"value": lat.n * steps / one, "unit": "spin-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"{steps} Heun step(s) of the full 1024x1024x16 film (FP64, with per-step moment/energy "
-                      f"record), {one:.1f} s"}
+                      f"record), {one:.1f} s",
+            "single_thread_value": lat.n / single, "cpu_model": cpu_model()}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.machine()
 
 
 def time_workload(lats, kw, precision, steps, stream, warmup=5, autotune=True):
@@ -603,6 +630,7 @@ def main():
         out["fp64"] = {"value": world * lat.n * k64 / (ms64 * 1e-3), "unit": "spin-steps/s", "steps": k64,
                        "kernels_ms": kt64, "clocks": clk64,
                        "hbm_frac": step_bytes_per_spin(8, nnz_per) * lat.n / (ms64 / k64 * 1e-3) / 1e9 / hbm_peak}
+        out["fp32_vs_fp64"] = out["value"] / out["fp64"]["value"]  # FP32-mixed speed-up on the same GPU
         # the batched form: 256 independent columnar grains (2,000-40,000 spins each, T
         # uniform in 0-800 K) in one handle, launch shape chosen by the autotuner
         grains, temps = L.grain_ensemble(count=256, seed=12345)
