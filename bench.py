@@ -389,6 +389,19 @@ def long_range_table(stream, rank, cells=64, steps=20, hbm_peak=6800.0):
                                rows_pass_fma_per_s=3 * nnz / (t * 1e-3),
                                rows_share_of_step=2 * t / ms)
             rows[f"fcc{cells}_lr_{prec}_{mode}"] = row
+        # the semi-implicit scheme on the same rows (row passes before its predictor and corrector)
+        with SpinSystem(lat, alpha=0.1, dt=1e-16, T=300.0, seed=11 + rank, precision=prec, stream=stream) as s:
+            s.semi_implicit_step(3)
+            s.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.semi_implicit_step(k)
+            e1.record(stream)
+            e1.synchronize()
+            s.sync()
+            ms = e0.elapsed_time(e1) / k
+        rows[f"fcc{cells}_lr_{prec}_semi_implicit"] = {"spins": n, "bonds": nnz, "ms_per_step": ms,
+                                                        "value": n / (ms * 1e-3), "unit": "spin-steps/s"}
     return rows
 
 

@@ -296,8 +296,9 @@ ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
  * sums row l of its slice in CSR order from H_app, exactly as a thread per row does, so the
  * results are identical to mode 1 (ss_info.exchange_rows = 3).  Otherwise (tensors, more
  * values) each warp sums 32 consecutive rows one by one, its lanes striding over the row's
- * bonds (exchange_rows = 2): only the summation order differs.  Monte Carlo and midpoint
- * steps sum a thread per row in every mode.  A warp per row runs with graph or plain launches:
+ * bonds (exchange_rows = 2): only the summation order differs.  The midpoint and
+ * semi-implicit steps use the same passes (sums without H_app) before each of their passes;
+ * Monte Carlo steps sum a thread per row in every mode.  A warp per row runs with graph or plain launches:
  * spin_system_set_exec refuses the persistent and system-block modes (SS_ERR_UNSUPPORTED),
  * and turning it on resets those to SS_EXEC_AUTO.  SS_ERR_INVALID_ARG for another mode. */
 ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode);

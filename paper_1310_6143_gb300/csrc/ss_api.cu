@@ -373,6 +373,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.J_tensor = h->J_tensor ? 1 : 0;
     a.any_cubic = h->any_cubic ? 1 : 0;
     a.ex = a.ey = a.ez = nullptr;
+    a.rows_bare = 0;
     a.sell = h->sell;
     a.sell_off = h->sell_off;
     a.nslice = h->nslice;
@@ -1392,11 +1393,14 @@ ss_status mc_upload_params(ss_system *h) {
 // device's step) and the step counter.
 template <typename R>
 cudaError_t enqueue_midpoint(ss_system *h, int64_t nsteps, int iterations) {
-    const KArgs<R> a = make_args<R>(h);
+    KArgs<R> a = make_args<R>(h);
+    use_rows(h, a);  // long rows: bare exchange sums from the row passes
+    a.rows_bare = 1;
+    const int rgrid = h->rows ? rows_grid(h) : 0;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sm_count * 8));
     cudaError_t e = cudaSuccess;
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-        e = launch_midpoint<R>(a, iterations, grid, h->stream);
+        e = launch_midpoint<R>(a, iterations, grid, rgrid, h->stream);
         if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
     }
     return e;
@@ -1469,11 +1473,14 @@ ss_status integrate_with_demag(ss_system *h, int64_t n, int key, F enqueue, cons
 // record, corrector, step counter.
 template <typename R>
 cudaError_t enqueue_sib(ss_system *h, int64_t nsteps) {
-    const KArgs<R> a = make_args<R>(h);
+    KArgs<R> a = make_args<R>(h);
+    use_rows(h, a);  // long rows: bare exchange sums from the row passes
+    a.rows_bare = 1;
+    const int rgrid = h->rows ? rows_grid(h) : 0;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sm_count * 8));
     cudaError_t e = cudaSuccess;
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-        e = launch_sib<R>(a, grid, h->stream);
+        e = launch_sib<R>(a, grid, rgrid, h->stream);
         if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
     }
     return e;

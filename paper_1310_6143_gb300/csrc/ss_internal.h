@@ -83,6 +83,7 @@ struct KArgs {
     const int32_t *Jtidx;     // [nnz] tensor of each bond (J_tensor = 1)
     int J_tensor;             // 1: the exchange sum uses Jt[Jtidx[k]] instead of J
     int any_cubic;            // 1: some material has cubic anisotropy
+    int rows_bare;            // 1: the long-row passes write sum_j J_ij X_j alone (no H_app)
     R *ex, *ey, *ez;          // [n] exchange + applied field of the spins being updated, computed
                               // beforehand by k_rows_field (a warp per row), or nullptr
     const uint32_t *sell;     // packed bonds col << 8 | entry of Jd in slices of 32 rows: bond k of
@@ -192,10 +193,11 @@ cudaError_t launch_advance_step(unsigned long long *step, cudaStream_t s);
 template <typename R> cudaError_t launch_demag(const KArgs<R> &a, const DemagArgs &d, cudaStream_t s);
 // One midpoint step's launches after its record: Euler predictor, `iters` fixed-point
 // iterations, copy back (the step counter is advanced separately).
-template <typename R> cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t s);
+// (rgrid: grid of the long-row passes, used when a.ex is set)
+template <typename R> cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, int rgrid, cudaStream_t s);
 // One semi-implicit predictor-corrector step's launches after its record (predictor, corrector;
 // the step counter is advanced separately).
-template <typename R> cudaError_t launch_sib(const KArgs<R> &a, int grid, cudaStream_t s);
+template <typename R> cudaError_t launch_sib(const KArgs<R> &a, int grid, int rgrid, cudaStream_t s);
 // Exchange + applied field of (X, Y, Z) into (a.ex, a.ey, a.ez), a warp per row (long rows).
 template <typename R>
 cudaError_t launch_rows_field(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int grid, cudaStream_t s);

@@ -757,7 +757,7 @@ __global__ void __launch_bounds__(256) k_rows_sell(const KArgs<R> a) {
         const uint32_t *p = a.sell + o + lane;
         R x = 0, y = 0, z = 0;
         const SysDesc *sd = nullptr;
-        if (row < a.n) {
+        if (row < a.n && !a.rows_bare) {
             sd = &a.sys[a.mats[__ldg(a.mat + row)].sys];
             x = sys_H(*sd, 0, R());
             y = sys_H(*sd, 1, R());
@@ -829,10 +829,16 @@ __global__ void __launch_bounds__(256) k_rows_field(const KArgs<R> a, const R *X
             }
         }
         if (row < a.n) {
-            const SysDesc &sd = a.sys[a.mats[__ldg(a.mat + row)].sys];
-            a.ex[row] = sys_H(sd, 0, R()) + mx;
-            a.ey[row] = sys_H(sd, 1, R()) + my;
-            a.ez[row] = sys_H(sd, 2, R()) + mz;
+            if (a.rows_bare) {
+                a.ex[row] = mx;
+                a.ey[row] = my;
+                a.ez[row] = mz;
+            } else {
+                const SysDesc &sd = a.sys[a.mats[__ldg(a.mat + row)].sys];
+                a.ex[row] = sys_H(sd, 0, R()) + mx;
+                a.ey[row] = sys_H(sd, 1, R()) + my;
+                a.ez[row] = sys_H(sd, 2, R()) + mz;
+            }
         }
     }
 }
@@ -849,6 +855,12 @@ __global__ void __launch_bounds__(256) k_rows_field(const KArgs<R> a, const R *X
 template <typename R, int Mode>
 __device__ __forceinline__ void exchange_bare(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int64_t i,
                                               R &e0, R &e1, R &e2) {
+    if constexpr (Mode == kRows) {  // long rows: summed beforehand (without H_app) by the row passes
+        e0 = a.ex[i];
+        e1 = a.ey[i];
+        e2 = a.ez[i];
+        return;
+    }
     const int32_t b = __ldg(a.row_ptr + i);
     const int32_t e = __ldg(a.row_ptr + i + 1);
     R x = 0, y = 0, z = 0;

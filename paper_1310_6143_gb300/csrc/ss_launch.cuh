@@ -150,13 +150,16 @@ int alt_first_grid(const KArgs<R> &a, int grid) {
 }
 
 template <typename R, int Mode>
-cudaError_t launch_midpoint_mode(const KArgs<R> &a, int iters, int grid, cudaStream_t s) {
+cudaError_t launch_midpoint_mode(const KArgs<R> &a, int iters, int grid, int rgrid, cudaStream_t s) {
+    cudaError_t e = Mode == kRows ? launch_rows_field<R>(a, a.sx, a.sy, a.sz, rgrid, s) : cudaSuccess;
+    if (e != cudaSuccess) return e;
     k_mid_euler<R, Mode><<<alt_first_grid(a, grid), kAltBlock, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e == cudaSuccess)
         e = launch_finalize_ring(a.sys, a.sys_tiles, a.nsys, a.partials, a.rec, a.rec_cap, a.step, s);
     R *x[3] = {a.px, a.py, a.pz}, *y[3] = {a.qx, a.qy, a.qz};
     for (int k = 0; k + 1 < iters && e == cudaSuccess; ++k) {
+        if (Mode == kRows && (e = launch_rows_field<R>(a, x[0], x[1], x[2], rgrid, s)) != cudaSuccess) break;
         k_mid_iter<R, Mode, false><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], y[0], y[1], y[2]);
         e = cudaGetLastError();
         for (int c = 0; c < 3; ++c) {
@@ -165,6 +168,7 @@ cudaError_t launch_midpoint_mode(const KArgs<R> &a, int iters, int grid, cudaStr
             y[c] = t;
         }
     }
+    if (e == cudaSuccess && Mode == kRows) e = launch_rows_field<R>(a, x[0], x[1], x[2], rgrid, s);
     if (e == cudaSuccess) {  // the last iterate goes straight to S
         k_mid_iter<R, Mode, true><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], a.sx, a.sy, a.sz);
         e = cudaGetLastError();
@@ -173,23 +177,31 @@ cudaError_t launch_midpoint_mode(const KArgs<R> &a, int iters, int grid, cudaStr
 }
 
 template <typename R>
-cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, cudaStream_t s) {
-    return (a.J_tensor || a.any_cubic) ? launch_midpoint_mode<R, kGeneral>(a, iters, grid, s)
-                                       : launch_midpoint_mode<R, kPlain>(a, iters, grid, s);
+cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, int rgrid, cudaStream_t s) {
+    if (a.ex) return launch_midpoint_mode<R, kRows>(a, iters, grid, rgrid, s);
+    return (a.J_tensor || a.any_cubic) ? launch_midpoint_mode<R, kGeneral>(a, iters, grid, rgrid, s)
+                                       : launch_midpoint_mode<R, kPlain>(a, iters, grid, rgrid, s);
 }
 
 template <typename R>
-cudaError_t launch_sib(const KArgs<R> &a, int grid, cudaStream_t s) {
-    const bool general = a.J_tensor || a.any_cubic;
-    if (general)
+cudaError_t launch_sib(const KArgs<R> &a, int grid, int rgrid, cudaStream_t s) {
+    const int mode = a.ex ? kRows : (a.J_tensor || a.any_cubic) ? kGeneral : kPlain;
+    cudaError_t e = mode == kRows ? launch_rows_field<R>(a, a.sx, a.sy, a.sz, rgrid, s) : cudaSuccess;
+    if (e != cudaSuccess) return e;
+    if (mode == kRows)
+        k_sib_pred<R, kRows><<<alt_first_grid(a, grid), kAltBlock, 0, s>>>(a);
+    else if (mode == kGeneral)
         k_sib_pred<R, kGeneral><<<alt_first_grid(a, grid), kAltBlock, 0, s>>>(a);
     else
         k_sib_pred<R, kPlain><<<alt_first_grid(a, grid), kAltBlock, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e == cudaSuccess)
         e = launch_finalize_ring(a.sys, a.sys_tiles, a.nsys, a.partials, a.rec, a.rec_cap, a.step, s);
+    if (e == cudaSuccess && mode == kRows) e = launch_rows_field<R>(a, a.px, a.py, a.pz, rgrid, s);
     if (e != cudaSuccess) return e;
-    if (general)
+    if (mode == kRows)
+        k_sib_corr<R, kRows><<<grid, 256, 0, s>>>(a);
+    else if (mode == kGeneral)
         k_sib_corr<R, kGeneral><<<grid, 256, 0, s>>>(a);
     else
         k_sib_corr<R, kPlain><<<grid, 256, 0, s>>>(a);
@@ -270,8 +282,8 @@ template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McA
 template cudaError_t launch_mc_colour_rec<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);
 template int mc_blocks_per_sm<SS_REAL>(int, int);
 template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
-template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
-template cudaError_t launch_sib<SS_REAL>(const KArgs<SS_REAL> &, int, cudaStream_t);
+template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
+template cudaError_t launch_sib<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_rows_field<SS_REAL>(const KArgs<SS_REAL> &, const SS_REAL *, const SS_REAL *,
                                                 const SS_REAL *, int, cudaStream_t);
 template int rows_blocks_per_sm<SS_REAL>();

@@ -175,3 +175,35 @@ def test_edge_cases_empty_rows_and_single_spins(SS, lr9):
         assert np.abs(S_b[off:off + lat.n] - S_ref).max() <= 1e-12
         assert np.abs(rec[:, k, 7] - rec_ref[:, 7]).max() <= 1e-12 * max(np.abs(rec_ref[:, 7]).max(), 1e-30)
         off += lat.n
+
+
+@pytest.mark.parametrize("scheme", ["midpoint", "semi_implicit"])
+def test_alternative_integrators_on_long_rows(SS, scheme):
+    """The midpoint rule and the semi-implicit scheme read their exchange sums from the row
+    passes: FP64 parity with the oracle, and bitwise the thread-per-row result with packed
+    slices (same summation order)."""
+    lat = L.fcc_long_range(9, 9, 9, r_cut=3.0)
+    S0 = L.random_state(lat.n, 13)
+
+    def run(mode, precision="fp64"):
+        with SS(lat, alpha=0.1, dt=1e-16, T=300.0, S0=S0, seed=3, precision=precision) as s:
+            if mode != "auto":
+                s.set_exchange_rows(mode)
+            if scheme == "midpoint":
+                s.midpoint_step(30, iterations=3)
+            else:
+                s.semi_implicit_step(30)
+            return s.spins(), s.record(0, 30), s.info()["exchange_rows"]
+
+    Sw, rw, mw = run("auto")
+    St, rt, mt = run("thread")
+    assert mw == 3 and mt == 1
+    assert np.array_equal(Sw, St) and np.array_equal(rw, rt)
+    ref = oracle_system(lat, seed=3)
+    if scheme == "midpoint":
+        S_ref, _ = O.midpoint_run(ref, S0, 30, 300.0, iters=3)
+    else:
+        S_ref, _ = O.sib_run(ref, S0, 30, 300.0)
+    assert np.abs(Sw - S_ref).max() <= 1e-12
+    S32, _, _ = run("auto", "fp32")
+    assert np.abs(S32 - S_ref).max() <= 1e-4
