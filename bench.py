@@ -272,13 +272,15 @@ def workload_table(stream, rank):
     return rows
 
 
-def time_mc(lat, kw, precision, steps, stream, warmup=3):
+def time_mc(lat, kw, precision, steps, stream, warmup=3, rows="auto"):
     """Hinzke-Nowak Monte Carlo steps (one trial move per spin each, with the per-step
     moment/energy record), timed with CUDA events on the handle's stream."""
     import torch
     from paper_1310_6143_gb300.system import SpinSystem
 
     with SpinSystem(lat, precision=precision, stream=stream, **kw) as s:
+        if rows != "auto":
+            s.set_exchange_rows(rows)
         s.mc_step(warmup)
         s.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -402,6 +404,10 @@ def long_range_table(stream, rank, cells=64, steps=20, hbm_peak=6800.0):
             ms = e0.elapsed_time(e1) / k
         rows[f"fcc{cells}_lr_{prec}_semi_implicit"] = {"spins": n, "bonds": nnz, "ms_per_step": ms,
                                                         "value": n / (ms * 1e-3), "unit": "spin-steps/s"}
+    # Monte Carlo on the same rows: a warp per 32 trials against a thread per trial (FP32-mixed)
+    for mode in ("auto", "thread"):
+        r = time_mc(lat, dict(T=300.0, seed=13 + rank), "fp32", 4, stream, warmup=1, rows=mode)
+        rows[f"fcc{cells}_lr_fp32_mc_{'warp' if mode == 'auto' else 'thread'}"] = dict(spins=n, bonds=nnz, **r)
     return rows
 
 

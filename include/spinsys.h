@@ -298,7 +298,8 @@ ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
  * values) each warp sums 32 consecutive rows one by one, its lanes striding over the row's
  * bonds (exchange_rows = 2): only the summation order differs.  The midpoint and
  * semi-implicit steps use the same passes (sums without H_app) before each of their passes;
- * Monte Carlo steps sum a thread per row in every mode.  A warp per row runs with graph or plain launches:
+ * Monte Carlo steps sum each trial's row across a warp (32 trials a warp, or one when a
+ * colour class is small).  A warp per row runs with graph or plain launches:
  * spin_system_set_exec refuses the persistent and system-block modes (SS_ERR_UNSUPPORTED),
  * and turning it on resets those to SS_EXEC_AUTO.  SS_ERR_INVALID_ARG for another mode. */
 ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode);

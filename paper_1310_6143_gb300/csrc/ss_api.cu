@@ -1501,7 +1501,7 @@ cudaError_t enqueue_mc(ss_system *h, int64_t nsteps) {
     const int gmeas = step_grid(h);
     const int ncol = (int)h->mc_cstart.size() - 1;
     cudaError_t e = cudaSuccess;
-    if (h->mc_rec) {  // the record summed in the colour passes
+    if (h->mc_rec && !h->rows) {  // the record summed in the colour passes
         m.partials = h->mc_partials;
         for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
             for (int c = 0; c < ncol && e == cudaSuccess; ++c) {
@@ -1522,8 +1522,12 @@ cudaError_t enqueue_mc(ss_system *h, int64_t nsteps) {
         }
         return e;
     }
+    KArgs<R> ar = a;  // the record's measurement reads the row passes' field on long rows
+    use_rows(h, ar);
+    const int rgrid = h->rows ? rows_grid(h) : 0;
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-        e = launch_measure<R>(a, h->block, gmeas, h->stream);
+        if (h->rows) e = launch_rows_field<R>(ar, ar.sx, ar.sy, ar.sz, rgrid, h->stream);
+        if (e == cudaSuccess) e = launch_measure<R>(ar, h->block, gmeas, h->stream);
         if (e == cudaSuccess)
             e = launch_finalize_ring(h->sys, h->sys_tiles, h->nsys, h->partials, h->rec, h->rec_cap, a.step, h->stream);
         for (int c = 0; c < ncol && e == cudaSuccess; ++c) {
@@ -1531,7 +1535,8 @@ cudaError_t enqueue_mc(ss_system *h, int64_t nsteps) {
             m.c1 = h->mc_cstart[c + 1];
             const int64_t need = (m.c1 - m.c0 + block - 1) / block;
             const int grid = (int)std::max<int64_t>(1, std::min(need, resident));
-            e = launch_mc_colour<R>(a, m, block, grid, h->stream);
+            e = h->rows ? launch_mc_colour_warp<R>(a, m, grid, h->stream)  // long rows: a warp per 32 trials
+                        : launch_mc_colour<R>(a, m, block, grid, h->stream);
         }
         if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
     }

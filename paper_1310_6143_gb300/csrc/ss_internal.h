@@ -184,6 +184,8 @@ template <typename R> int persistent_blocks_per_sm(int block, int mode);
 // mode: the step-kernel variant (0 plain, 1 general, 2 rows; kPlain / kGeneral / kRows)
 template <typename R> int step_blocks_per_sm(int block, int mode);
 template <typename R> int corrector_blocks_per_sm(int block, bool draw_ahead, int mode);
+// One colour pass for long exchange rows: a warp sums the rows of 32 trials cooperatively.
+template <typename R> cudaError_t launch_mc_colour_warp(const KArgs<R> &a, const McArgs &m, int grid, cudaStream_t s);
 // One colour pass over the tiles of m that also sums the record terms of the pre-step state.
 template <typename R> cudaError_t launch_mc_colour_rec(const KArgs<R> &a, const McArgs &m, int grid, cudaStream_t s);
 template <typename R> cudaError_t launch_mc_colour(const KArgs<R> &a, const McArgs &m, int block, int grid,

@@ -1160,9 +1160,10 @@ __global__ void k_demag_field(const KArgs<R> a, const DemagArgs d) {
 // pre-step state in v: mu S (3), the exchange term (1: -mu S.(h - H_app) - mu S.H_app/2 for
 // the first colour class, whose bonds all end on unchanged spins; 2: -mu S.H_app/2), and
 // the anisotropy energy.
-template <typename R, int Mode, int Rec>
+template <typename R, int Mode, int Rec, bool GivenH = false>
 __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int64_t i, uint64_t step,
-                                         const SmemTables &tab, int &sysid, double v[5]) {
+                                         const SmemTables &tab, int &sysid, double v[5], R gh0 = 0, R gh1 = 0,
+                                         R gh2 = 0) {
     bool accept;
     const MatDesc<R> &mt = a.mats[__ldg(a.mat + i)];
     const SysDesc &sd = a.sys[mt.sys];
@@ -1213,8 +1214,8 @@ __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int
         n1 *= inv;
         n2 *= inv;
     }
-    R h0, h1, h2;
-    exchange_sum<R, false, Mode>(a, sd, a.sx, a.sy, a.sz, i, h0, h1, h2);
+    R h0 = gh0, h1 = gh1, h2 = gh2;  // GivenH: H_app + sum_j (J_ij/mu_s,i) S_j summed by the caller
+    if constexpr (!GivenH) exchange_sum<R, false, Mode>(a, sd, a.sx, a.sy, a.sz, i, h0, h1, h2);
     // quadratic terms as (n - s).(A (n + s)): exactly zero when the spin is unchanged or
     // flipped, whatever the contraction of products into FMAs
     const R d0 = n0 - s0, d1 = n1 - s1, d2 = n2 - s2;
@@ -1282,6 +1283,124 @@ __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs
         const unsigned yes = __ballot_sync(act, accept);
         if ((int)(threadIdx.x & 31) == __ffs(same) - 1)
             atomicAdd(m.acc + sysid, (unsigned long long)__popc(yes & same));
+    }
+}
+
+// A colour pass for long exchange rows: each warp takes 32 trials of the class, sums their
+// rows one by one with its lanes striding over the row's bonds (col + J, or tensors) and a
+// butterfly, and each lane then runs its own trial with its row's field (the neighbours of a
+// class are of other classes, unchanged during the pass).
+template <typename R, int BS, int Mode>
+__global__ void __launch_bounds__(BS) k_mc_colour_warp(const KArgs<R> a, const McArgs m) {
+    __shared__ SmemTables tab;
+    stage_tables(a, tab);
+    __syncthreads();
+    const uint64_t step = *a.step;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * BS + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * BS) >> 5;
+    for (int64_t k0 = m.c0 + warp * 32; k0 < m.c1; k0 += nwarps * 32) {
+        const int64_t k = k0 + lane;
+        const int64_t i = k < m.c1 ? (int64_t)chk(__ldg(m.order + k), a.n, a.err) : -1;
+        int32_t rb = 0, re = 0;
+        if (i >= 0) {
+            rb = __ldg(a.row_ptr + i);
+            re = __ldg(a.row_ptr + i + 1);
+        }
+        const int nr = m.c1 - k0 < 32 ? (int)(m.c1 - k0) : 32;
+        R mx = 0, my = 0, mz = 0;
+        for (int q = 0; q < nr; ++q) {
+            const int32_t b = __shfl_sync(FULL, rb, q), e = __shfl_sync(FULL, re, q);
+            R x = 0, y = 0, z = 0;
+#pragma unroll 4
+            for (int32_t t = b + lane; t < e; t += 32) {
+                const int32_t j = chk(__ldg(a.col + t), a.n, a.err);
+                const R s0 = a.sx[j], s1 = a.sy[j], s2 = a.sz[j];
+                if (Mode != kPlain && a.J_tensor) {
+                    const R *tt = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + t);
+                    x = fma(__ldg(tt + 0), s0, fma(__ldg(tt + 1), s1, fma(__ldg(tt + 2), s2, x)));
+                    y = fma(__ldg(tt + 3), s0, fma(__ldg(tt + 4), s1, fma(__ldg(tt + 5), s2, y)));
+                    z = fma(__ldg(tt + 6), s0, fma(__ldg(tt + 7), s1, fma(__ldg(tt + 8), s2, z)));
+                } else {
+                    const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + t);
+                    x = fma(Jk, s0, x);
+                    y = fma(Jk, s1, y);
+                    z = fma(Jk, s2, z);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_xor_sync(FULL, x, o);
+                y += __shfl_xor_sync(FULL, y, o);
+                z += __shfl_xor_sync(FULL, z, o);
+            }
+            if (lane == q) {
+                mx = x;
+                my = y;
+                mz = z;
+            }
+        }
+        bool accept = false;
+        int sysid = -1;
+        if (i >= 0) {
+            const SysDesc &sd = a.sys[a.mats[__ldg(a.mat + i)].sys];
+            double v[5];
+            accept = mc_trial<R, Mode, 0, true>(a, m, i, step, tab, sysid, v, sys_H(sd, 0, R()) + mx,
+                                                 sys_H(sd, 1, R()) + my, sys_H(sd, 2, R()) + mz);
+        }
+        const unsigned same = __match_any_sync(FULL, sysid);
+        const unsigned yes = __ballot_sync(FULL, accept);
+        if (sysid >= 0 && lane == __ffs(same) - 1) atomicAdd(m.acc + sysid, (unsigned long long)__popc(yes & same));
+    }
+}
+
+// As k_mc_colour_warp for colour classes too small to fill the GPU 32 trials to a warp: each
+// warp takes one trial, sums its row across the lanes, and lane 0 runs the trial.
+template <typename R, int BS, int Mode>
+__global__ void __launch_bounds__(BS) k_mc_colour_warp1(const KArgs<R> a, const McArgs m) {
+    __shared__ SmemTables tab;
+    stage_tables(a, tab);
+    __syncthreads();
+    const uint64_t step = *a.step;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * BS + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * BS) >> 5;
+    for (int64_t k = m.c0 + warp; k < m.c1; k += nwarps) {
+        const int64_t i = chk(__ldg(m.order + k), a.n, a.err);
+        const int32_t b = __ldg(a.row_ptr + i), e = __ldg(a.row_ptr + i + 1);
+        R x = 0, y = 0, z = 0;
+#pragma unroll 4
+        for (int32_t t = b + lane; t < e; t += 32) {
+            const int32_t j = chk(__ldg(a.col + t), a.n, a.err);
+            const R s0 = a.sx[j], s1 = a.sy[j], s2 = a.sz[j];
+            if (Mode != kPlain && a.J_tensor) {
+                const R *tt = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + t);
+                x = fma(__ldg(tt + 0), s0, fma(__ldg(tt + 1), s1, fma(__ldg(tt + 2), s2, x)));
+                y = fma(__ldg(tt + 3), s0, fma(__ldg(tt + 4), s1, fma(__ldg(tt + 5), s2, y)));
+                z = fma(__ldg(tt + 6), s0, fma(__ldg(tt + 7), s1, fma(__ldg(tt + 8), s2, z)));
+            } else {
+                const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + t);
+                x = fma(Jk, s0, x);
+                y = fma(Jk, s1, y);
+                z = fma(Jk, s2, z);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(FULL, x, o);
+            y += __shfl_xor_sync(FULL, y, o);
+            z += __shfl_xor_sync(FULL, z, o);
+        }
+        if (lane == 0) {
+            const SysDesc &sd = a.sys[a.mats[__ldg(a.mat + i)].sys];
+            int sysid;
+            double v[5];
+            const bool accept = mc_trial<R, Mode, 0, true>(a, m, i, step, tab, sysid, v, sys_H(sd, 0, R()) + x,
+                                                           sys_H(sd, 1, R()) + y, sys_H(sd, 2, R()) + z);
+            if (accept) atomicAdd(m.acc + sysid, 1ull);
+        }
     }
 }
 

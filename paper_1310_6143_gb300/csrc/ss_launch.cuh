@@ -104,6 +104,27 @@ int corrector_blocks_per_sm(int block, bool draw_ahead, int mode) {
 }
 
 template <typename R>
+cudaError_t launch_mc_colour_warp(const KArgs<R> &a, const McArgs &m, int grid, cudaStream_t s) {
+    constexpr int BS = 256;
+    const bool general = a.J_tensor || a.any_cubic;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (m.c1 - m.c0 < (int64_t)sms * 64 * 32) {  // a warp per trial: enough warps to fill the SMs
+        const int64_t blocks = (m.c1 - m.c0 + BS / 32 - 1) / (BS / 32);
+        const int g = (int)(blocks < (int64_t)sms * 8 ? (blocks > 0 ? blocks : 1) : (int64_t)sms * 8);
+        if (general)
+            k_mc_colour_warp1<R, BS, kGeneral><<<g, BS, 0, s>>>(a, m);
+        else
+            k_mc_colour_warp1<R, BS, kPlain><<<g, BS, 0, s>>>(a, m);
+    } else if (general) {
+        k_mc_colour_warp<R, BS, kGeneral><<<grid, BS, 0, s>>>(a, m);
+    } else {
+        k_mc_colour_warp<R, BS, kPlain><<<grid, BS, 0, s>>>(a, m);
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_mc_colour_rec(const KArgs<R> &a, const McArgs &m, int grid, cudaStream_t s) {
     constexpr int BS = 256;
     const bool general = a.J_tensor || a.any_cubic;
@@ -280,6 +301,7 @@ template int step_blocks_per_sm<SS_REAL>(int, int);
 template int corrector_blocks_per_sm<SS_REAL>(int, bool, int);
 template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
 template cudaError_t launch_mc_colour_rec<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);
+template cudaError_t launch_mc_colour_warp<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);
 template int mc_blocks_per_sm<SS_REAL>(int, int);
 template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
 template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);

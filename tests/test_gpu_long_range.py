@@ -207,3 +207,32 @@ def test_alternative_integrators_on_long_rows(SS, scheme):
     assert np.abs(Sw - S_ref).max() <= 1e-12
     S32, _, _ = run("auto", "fp32")
     assert np.abs(S32 - S_ref).max() <= 1e-4
+
+
+@pytest.mark.parametrize("kind", ["long_range", "forced_warp_sc"])
+def test_monte_carlo_on_long_rows(SS, kind):
+    """Monte Carlo with a warp summing the rows of 32 trials: FP64 per-step accepted counts
+    equal to the oracle's and spins within 1e-12 (the row sums differ only in order)."""
+    if kind == "long_range":
+        lat = L.fcc_long_range(9, 9, 9, r_cut=3.0)
+        mode, steps, T = "auto", 8, 900.0
+    else:
+        lat = L.simple_cubic(8, 8, 8, J=6e-21, k_u=1e-23)
+        mode, steps, T = "warp", 20, 400.0
+    S0 = L.random_state(lat.n, 21)
+    with SS(lat, alpha=0.1, dt=1e-16, T=T, S0=S0, seed=5, sys_id=1, precision="fp64") as s:
+        if mode != "auto":
+            s.set_exchange_rows(mode)
+        assert s.info()["exchange_rows"] >= 2
+        accs, prev = [], 0
+        for _ in range(steps):
+            s.mc_step(1)
+            acc, _ = s.mc_stats(0)
+            accs.append(acc - prev)
+            prev = acc
+        S = s.spins()
+        rec = s.record(0, steps)
+    S_ref, rec_ref, acc_ref = O.mc_run(oracle_system(lat, seed=5, sys_id=1), S0, steps, T, record=True)
+    assert np.array_equal(np.array(accs), acc_ref)
+    assert np.abs(S - S_ref).max() <= 1e-12
+    assert np.abs(rec[:, 0, 7] - rec_ref[:, 7]).max() <= 1e-12 * np.abs(rec_ref[:, 7]).max()
