@@ -430,14 +430,33 @@ __device__ __forceinline__ void write_record(const SysDesc &sd, double r, double
 }
 
 // Sum the tile partials of system s in tile order and write one record (8 doubles).
-template <int BS, bool Coherent>
+template <int BS, bool Coherent, bool Chains4 = false>
 __device__ __forceinline__ void finalize_system(const SysDesc *sys, const int32_t *sys_tiles, const double *partials,
                                                 int s, double *dst, double *red) {
     const int32_t t0 = sys_tiles[s], t1 = sys_tiles[s + 1];
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int32_t t = t0 + threadIdx.x; t < t1; t += BS) {
+    if constexpr (Chains4) {
+        // four independent chains per thread (tiles t, t + BS, t + 2 BS, t + 3 BS of each
+        // round), joined in a fixed order: deterministic, and the loads overlap (the
+        // stand-alone finalisation kernels; inside the step kernels the registers cost more)
+        double a4[4][5] = {};
+        for (int32_t t = t0 + threadIdx.x; t < t1; t += 4 * BS) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) acc[c] += ld<Coherent>(partials + (int64_t)t * kPartComps + c);
+            for (int q = 0; q < 4; ++q) {
+                const int32_t u = t + q * BS;
+                if (u < t1) {
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) a4[q][c] += ld<Coherent>(partials + (int64_t)u * kPartComps + c);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) acc[c] = (a4[0][c] + a4[1][c]) + (a4[2][c] + a4[3][c]);
+    } else {
+        for (int32_t t = t0 + threadIdx.x; t < t1; t += BS) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) acc[c] += ld<Coherent>(partials + (int64_t)t * kPartComps + c);
+        }
     }
     const double r = block_sum8<BS>(acc, red);
     write_record(sys[s], r, dst);
@@ -556,7 +575,7 @@ __global__ void __launch_bounds__(BS) k_finalize_ring(const SysDesc *sys, const 
     __shared__ double red[(BS / 32) * 8];
     double *dst = rec + (int64_t)(*step % (unsigned long long)rec_cap) * nsys * kRecComps;
     for (int s = blockIdx.x; s < nsys; s += gridDim.x)
-        finalize_system<BS, false>(sys, sys_tiles, partials, s, dst + (int64_t)s * kRecComps, red);
+        finalize_system<BS, false, true>(sys, sys_tiles, partials, s, dst + (int64_t)s * kRecComps, red);
 }
 
 template <int BS>
@@ -564,7 +583,7 @@ __global__ void __launch_bounds__(BS) k_finalize(const SysDesc *sys, const int32
                                                  const double *partials, double *dst) {
     __shared__ double red[(BS / 32) * 8];
     for (int s = blockIdx.x; s < nsys; s += gridDim.x)
-        finalize_system<BS, false>(sys, sys_tiles, partials, s, dst + (int64_t)s * kRecComps, red);
+        finalize_system<BS, false, true>(sys, sys_tiles, partials, s, dst + (int64_t)s * kRecComps, red);
 }
 
 // Random unit spins from the reserved stream: counter (i, 0xFFFFFFFF, system, 1).
