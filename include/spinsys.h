@@ -313,7 +313,10 @@ ss_status spin_system_set_draw_ahead(ss_system *h, int32_t eighths);
 
 /* Time the candidate (exec, block, tile, draw-ahead) choices on this handle over `trial_steps`
  * steps each, keep the fastest, and write it to *out_info.  The spins and the step
- * counter are restored afterwards, so the trajectory is unchanged. */
+ * counter are restored afterwards, so the trajectory is unchanged.  With the environment
+ * variable SPINSYS_AUTOTUNE_CACHE naming a file, a workload tuned before on the same device
+ * (same precision, spins, bonds, systems, largest system, exchange-row mode and kernel
+ * variant) takes its stored choice without trial runs, and a new result is appended. */
 ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_info);
 
 ss_status spin_system_info(ss_system *h, ss_info *out);

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -2118,12 +2119,53 @@ ss_status spin_system_time_rows(ss_system *h, int32_t launches, double *out_ms) 
     return SS_OK;
 }
 
+// The autotune cache (SPINSYS_AUTOTUNE_CACHE): one line per tuned workload, "key<TAB>exec block
+// tile draw-ahead", the key naming the device and what the launch shape depends on.
+static std::string autotune_key(const ss_system *h) {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) cudaGetLastError();
+    int64_t nmax = 0;
+    for (int64_t v : h->sys_n) nmax = std::max(nmax, v);
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "v1|%s|%d|%lld|%lld|%d|%lld|%d|%d", prop.name, h->precision, (long long)h->n,
+                  (long long)h->nnz, h->nsys, (long long)nmax, h->rows ? (h->sell ? 3 : 2) : 1, step_mode(h));
+    for (char *c = buf; *c; ++c)
+        if (*c == '\t' || *c == '\n') *c = ' ';
+    return buf;
+}
+
+static bool autotune_lookup(const std::string &path, const std::string &key, int v[4]) {
+    FILE *f = std::fopen(path.c_str(), "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        char *tab = std::strchr(line, '\t');
+        if (!tab || std::string(line, (size_t)(tab - line)) != key) continue;
+        found = std::sscanf(tab + 1, "%d %d %d %d", &v[0], &v[1], &v[2], &v[3]) == 4;  // the last entry wins
+    }
+    std::fclose(f);
+    return found;
+}
+
 ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_info) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
     if (trial_steps < 1) return fail(h, SS_ERR_INVALID_ARG, "trial_steps must be >= 1");
     st = check_device_flags(h);
     if (st != SS_OK) return st;
+    const char *cache = std::getenv("SPINSYS_AUTOTUNE_CACHE");
+    const std::string key = cache && *cache ? autotune_key(h) : std::string();
+    if (!key.empty()) {
+        int v[4];
+        if (autotune_lookup(cache, key, v) && v[3] >= 0 && v[3] <= 8) {
+            h->ahead_q = v[3];
+            st = spin_system_set_launch(h, v[1], v[2]);
+            if (st == SS_OK) st = spin_system_set_exec(h, (ss_exec)v[0]);
+            if (st == SS_OK) return out_info ? spin_system_info(h, out_info) : SS_OK;
+            h->bad = false;  // a stale entry: tune afresh
+        }
+    }
     const size_t rs = real_size(h);
     const int64_t n = h->n;
     const int64_t step0 = h->step;
@@ -2178,6 +2220,12 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
     dfree(h, save);
     if (st == SS_OK) st = set_step(h, step0);
+    if (st == SS_OK && !key.empty()) {
+        if (FILE *f = std::fopen(cache, "a")) {
+            std::fprintf(f, "%s\t%d %d %d %d\n", key.c_str(), h->exec, h->block, h->tile, h->ahead_q);
+            std::fclose(f);
+        }
+    }
     if (st == SS_OK && out_info) st = spin_system_info(h, out_info);
     return st;
 }
