@@ -1,8 +1,10 @@
 """Closed-form physics checks of the CUDA path itself (the oracle's dynamics and statistics pins,
 run through the C ABI): the Larmor period, second-order convergence of Heun at T = 0 to the
 closed form Eq. analytic_LLG, energy and total-spin conservation without damping, Stoner-
-Wohlfarth switching (angular variation of the coercivity, easy-axis coercivity 2 k_u/mu_s), and
-the Langevin function <cos theta> = coth x - 1/x reached by the stochastic LLG at finite T."""
+Wohlfarth switching (angular variation of the coercivity, easy-axis coercivity 2 k_u/mu_s), the
+Langevin function <cos theta> = coth x - 1/x and the Boltzmann distribution (Eq. boltz) reached by
+the stochastic LLG at finite T, and the LLG equilibrium magnetisation of the paper's sc 28^3
+system against its fitted m(T) (Fig. MCLLG)."""
 import json
 import os
 
@@ -134,3 +136,46 @@ def test_langevin_function_from_the_stochastic_llg(SS, precision):
             s.step(300)
             c.append(s.spins()[:, 2])
     assert abs(np.concatenate(c).mean() - _langevin(x)) < 0.01
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_boltzmann_distribution_from_the_stochastic_llg(SS, precision):
+    """Eq. boltz: free spins with uniaxial anisotropy, k_u/(kB T) = 3, sample cos theta with
+    density proportional to exp(3 cos^2 theta); the histogram of 20 bins matches it."""
+    n, kappa, lam = 20000, 3.0, 1.0
+    mu = 1.5 * L.MU_B
+    ku = 1e-22
+    T = ku / (kappa * KB)
+    dt = 0.005 * mu / (2 * lam * KB * T * GAMMA)
+    lat = L.SpinLattice(np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0), np.full(n, mu),
+                        np.full(n, ku), np.tile([0.0, 0.0, 1.0], (n, 1)))
+    with SS(lat, alpha=lam, dt=dt, T=T, seed=23, precision=precision) as s:
+        s.step(2000)
+        c = []
+        for _ in range(60):
+            s.step(300)
+            c.append(s.spins()[:, 2])
+    c = np.concatenate(c)
+    edges = np.linspace(-1.0, 1.0, 21)
+    hist = np.histogram(c, bins=edges)[0] / c.size
+    from scipy import integrate
+
+    Z = integrate.quad(lambda u: np.exp(kappa * u * u), -1, 1)[0]
+    expect = np.array([integrate.quad(lambda u: np.exp(kappa * u * u), a, b)[0] for a, b in zip(edges[:-1], edges[1:])])
+    expect /= Z
+    assert np.abs(hist - expect).max() < 0.006, np.abs(hist - expect).max()
+
+
+@pytest.mark.parametrize("precision,T,tol", [("fp64", 300.0, 0.03), ("fp32", 450.0, 0.04)])
+def test_llg_equilibrium_matches_the_papers_fitted_curve(SS, precision, T, tol):
+    """Fig. MCLLG: the LLG equilibrium magnetisation of the sc 28^3 system (J = 6.0e-21 J/link,
+    periodic) follows the paper's fit m(T) = (1 - T/Tc)^beta, Tc = 631.82 K, beta = 0.334297, as
+    its Monte Carlo does."""
+    lat = L.simple_cubic(28, 28, 28, J=6.0e-21, k_u=0.0)
+    with SS(lat, alpha=1.0, dt=5e-16, T=T, seed=41, precision=precision) as s:
+        s.step(6000)
+        first = s.step_index
+        s.step(4000)
+        rec = s.record(first, 4000)
+    m = np.linalg.norm(rec[:, 0, :3], axis=1) / rec[:, 0, 3]
+    assert abs(m.mean() - (1 - T / 631.82) ** 0.334297) < tol
