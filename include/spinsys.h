@@ -284,13 +284,13 @@ ss_status spin_system_set_exec(ss_system *h, ss_exec mode);
 ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
 
 /* How the exchange sum of Eq. HJij is split over threads: mode 0 automatic (the default: a
- * warp per row when the rows average 64 or more bonds, as with exchange beyond the nearest
- * neighbours -- over 1,000 neighbours per atom for the long-ranged exchange the paper's
- * scaling section runs), 1 a thread per row (the step kernels sum their own rows), 2 a warp
- * per row.  With a warp per row, each Heun pass is preceded by a pass that sums the exchange
+ * warp per row when the rows average at least 24 bonds in the FP32-mixed form or 128 in the
+ * FP64 form with packed bonds, 64 or 256 without -- exchange beyond the nearest neighbours,
+ * up to the over 1,000 neighbours per atom of the long-ranged exchange the paper's scaling
+ * section runs), 1 a thread per row (the step kernels sum their own rows), 2 a warp per row.  With a warp per row, each Heun pass is preceded by a pass that sums the exchange
  * field of every spin into a buffer of 3n values.  For scalar J with at most 255 distinct
- * J_ij / mu_s,i and fewer than 2^24 spins (checked at creation, when the automatic rule picks
- * a warp per row) the bonds are stored as packed 32-bit words (neighbour index and dictionary
+ * J_ij / mu_s,i and fewer than 2^24 spins (checked at creation, when the rows average 16 or
+ * more bonds) the bonds are stored as packed 32-bit words (neighbour index and dictionary
  * entry, 4 bytes per bond) in slices of 32 consecutive rows, bond k of the slice's rows
  * interleaved and each slice padded to its longest row with zero bonds; lane l of a warp
  * sums row l of its slice in CSR order from H_app, exactly as a thread per row does, so the

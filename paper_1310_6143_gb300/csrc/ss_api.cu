@@ -701,8 +701,11 @@ void fill_material(MatDesc<R> &m, const MatKey &k, const ss_params *p) {
     m.has_cubic = k.v[11] != 0.0 ? 1 : 0;
 }
 
-// Rows averaging this many bonds or more get a warp each for the exchange sum.
+// Rows averaging this many bonds or more get a warp each for the exchange sum (FP32-mixed,
+// without packed slices; see set_rows).
 constexpr int64_t kRowsAuto = 64;
+// Packed slices are built for rows averaging this many bonds or more.
+constexpr int64_t kSellMin = 16;
 
 template <typename R>
 ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
@@ -810,7 +813,7 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     // the bond's J_ij / mu_s,i in a dictionary of at most 255 values plus 0, stored in slices
     // of 32 rows (bond k of the slice's row l at 32 k + l), each padded to its longest row with
     // J = 0 bonds.
-    if (!tensor && nnz >= kRowsAuto * n && n < (int64_t(1) << 24)) {
+    if (!tensor && nnz >= kSellMin * n && n < (int64_t(1) << 24)) {
         using Bits = typename std::conditional<sizeof(R) == 8, uint64_t, uint32_t>::type;
         constexpr int kSlots = 1024;
         std::vector<Bits> key(kSlots);
@@ -936,9 +939,12 @@ ss_status init_random(ss_system *h, const std::vector<HostSys> &hs) {
 }
 
 // A warp per row for the exchange sums (mode 2), a thread per row (1), or the automatic
-// choice (0: a warp per row when rows average kRowsAuto bonds or more).
+// choice (0): a warp per row when rows average at least 24 bonds (FP32-mixed) or 128 (FP64)
+// with packed slices, 64 or 256 without (measured crossovers on GB300).
 ss_status set_rows(ss_system *h, int32_t mode) {
-    const bool on = mode == 2 || (mode == 0 && h->nnz >= kRowsAuto * h->n && h->n > 0);
+    const bool packed = h->sell != nullptr;
+    const int64_t thr = h->precision == SS_FP32_MIXED ? (packed ? 24 : kRowsAuto) : (packed ? 128 : 256);
+    const bool on = mode == 2 || (mode == 0 && h->n > 0 && h->nnz >= thr * h->n);
     if (on && !h->E[0]) {
         const size_t rs = real_size(h);
         for (int c = 0; c < 3; ++c) SS_CUDA(h, dalloc(h, &h->E[c], (size_t)h->n * rs));
