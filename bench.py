@@ -18,6 +18,7 @@ rank advances its own replica of the film (statistical parallelism, no collectiv
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import subprocess
@@ -89,6 +90,14 @@ EXEC_NAMES = {0: "auto", 1: "kernels", 2: "graph", 3: "persistent", 4: "system_b
 FP64_SLOTS_PER_SM_CYCLE = 2
 
 
+def _smi_time(stamp):
+    """nvidia-smi's timestamp ('2026/12/03 10:00:00.123') as host epoch seconds; -1 if unreadable."""
+    try:
+        return datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+    except ValueError:
+        return -1.0
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -99,14 +108,20 @@ class Clocks:
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
+        self.window = None
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # the sampler is producing rows before the timed region starts
         except Exception:
             self.proc = None
         return self
+
+    def mark(self, t0, t1):
+        """Host wall-clock bounds of the timed region: only the samples inside it are summarised."""
+        self.window = (t0, t1)
 
     def __exit__(self, *exc):
         if self.proc:
@@ -122,7 +137,10 @@ class Clocks:
             rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
         except Exception:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(device_index)]
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 10 and r[0].strip() == str(device_index)]
+        if self.window:
+            inside = [r for r in rows if self.window[0] <= _smi_time(r[9]) <= self.window[1]]
+            rows = inside or rows
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -483,7 +501,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, batched and CPU legs")
@@ -564,10 +582,12 @@ def main():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with Clocks(os.path.join(os.environ.get("SPINSYS_CLOCKS_DIR", tempfile.gettempdir()),
                                      f"clocks_{precision}.csv")) as ck:
+                h0 = time.time()
                 e0.record(stream)
                 s.step(steps)
                 e1.record(stream)
                 e1.synchronize()
+                ck.mark(h0, time.time())
             s.sync()
             torch.cuda.synchronize()
             barrier(world)
