@@ -5,7 +5,8 @@ surfaces, the first and last sites, tile boundaries) are recomputed by the oracl
 their exact two-bond neighbourhood (the predictor values of the neighbours need their
 own neighbours), with the Philox spin word mapped to the global index.  Properties that
 hold at any size are checked on every spin: |S| = 1, and the step's record of the
-initial state equals the oracle's FP64 moment and energy of that state.
+initial state equals the oracle's FP64 moment and energy of that state.  The film is also
+compared whole: all 16,777,216 spins after eight steps against the oracle run over the film.
 """
 import numpy as np
 import pytest
@@ -22,6 +23,11 @@ def SS():
     from paper_1310_6143_gb300.system import SpinSystem
 
     return SpinSystem
+
+
+@pytest.fixture(scope="module")
+def film():
+    return L.film(1024, 1024, 16)
 
 
 def _samples(n, tile, rng, extra=()):
@@ -58,11 +64,38 @@ def _check_one_step(SS, lat, precision, tol, alpha, dt, T, H=(0.0, 0.0, 0.0), se
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 2e-6), ("fp64", 1e-14)])
-def test_film_1024x1024x16(SS, precision, tol):
-    lat = L.film(1024, 1024, 16)
+def test_film_1024x1024x16(SS, film, precision, tol):
+    lat = film
     nz = 16
     surface = [3 * nz, 3 * nz + nz - 1, lat.n - 1 - nz * 1024]  # bottom / top layer sites
     _check_one_step(SS, lat, precision, tol, alpha=0.02, dt=1e-16, T=1200.0, extra=surface)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-12)])
+def test_film_whole_state_eight_steps_as_benchmarked(SS, film, precision, tol):
+    """Every spin of the film after eight steps in the benchmark's execution mode (one launch
+    of the captured eight-step graph that the library chooses for a system of this size,
+    default launch shape, the corrector drawing part of the next step's thermal field) under a
+    temperature pulse, against the oracle run over the whole film; the eight in-loop records of
+    the pre-step states against the oracle's."""
+    lat = film
+    T = np.array([300.0, 450.0, 700.0, 1000.0, 1200.0, 1000.0, 700.0, 450.0])
+    S0 = L.random_state(lat.n, 31)
+    with SS(lat, alpha=0.02, dt=1e-16, T=0.0, seed=5, S0=S0, precision=precision) as s:
+        s.set_temperature_schedule(T)
+        start = s.spins()
+        assert s.info()["exec"] == 0  # automatic: eight or more steps of a system this size run as a graph
+        s.step(8)
+        S = s.spins()
+        rec = s.record(0, 8)[:, 0, :]
+    ref = oracle_system(lat, alpha=0.02, dt=1e-16, seed=5)
+    S_ref, rec_ref = O.heun_run(ref, start, 8, T, record=True)
+    assert np.abs(S - S_ref).max() <= tol
+    rtol = 1e-5 if precision == "fp32" else 1e-12
+    ms = rec_ref[0, 3]
+    assert np.abs(rec[:, 3] - rec_ref[:, 3]).max() <= 1e-14 * ms
+    assert np.abs(rec[:, :3] - rec_ref[:, :3]).max() <= rtol * ms
+    assert np.abs(rec[:, 4:] - rec_ref[:, 4:]).max() <= rtol * np.abs(rec_ref[:, 4:7]).sum(1).max()
 
 
 def test_fcc_64_cubed(SS):
