@@ -138,3 +138,69 @@ def test_grain_ensemble_256(SS):
             out, _ = O.heun_run(sref, start[o + sites], 1, temps[gidx])
             k = int(np.searchsorted(sites, c))
             assert np.abs(out[k] - S1[o + c]).max() <= 2e-6
+
+
+def _whole_state(SS, lats, precision, steps, tol, oracles, T, **kw):
+    """Autotune as the benchmark does (the state is restored), take `steps` steps, and compare
+    every spin and every system's records with the oracle runs over the whole systems."""
+    with SS(lats, precision=precision, T=T, **kw) as s:
+        s.autotune(8)
+        start = s.spins()
+        s.step(steps)
+        S = s.spins()
+        rec = s.record(0, steps)
+    temps = T if isinstance(T, list) else [T]
+    rtol = 1e-5 if precision == "fp32" else 1e-12
+    off = 0
+    for k, (ref, n) in enumerate(oracles):
+        S_ref, rec_ref = O.heun_run(ref, start[off:off + n], steps, temps[k], record=True)
+        assert np.abs(S[off:off + n] - S_ref).max() <= tol, k
+        ms = rec_ref[0, 3]
+        assert np.abs(rec[:, k, 3] - rec_ref[:, 3]).max() <= 1e-14 * ms
+        assert np.abs(rec[:, k, :3] - rec_ref[:, :3]).max() <= rtol * ms
+        assert np.abs(rec[:, k, 4:] - rec_ref[:, 4:]).max() <= rtol * np.abs(rec_ref[:, 4:7]).sum(1).max()
+        off += n
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-12)])
+def test_fcc64_whole_state_as_benchmarked(SS, precision, tol):
+    """The fcc 64^3 crystal of the temperature sweep (random start from the library's reserved
+    stream, 1,000 K), 64 steps (one captured graph) in the autotuned launch shape."""
+    lat = L.fcc(64, 64, 64, J=11.2e-21, k_u=6.69e-24)
+    ref = oracle_system(lat, alpha=0.05, dt=1e-16, seed=2)
+    _whole_state(SS, lat, precision, 64, tol, [(ref, lat.n)], 1000.0, alpha=0.05, dt=1e-16, seed=2,
+                 init_random=True)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-12)])
+def test_fcc64_dm_cubic_whole_state_as_benchmarked(SS, precision, tol):
+    """fcc 64^3 with a DM term (|D| = 0.1 J, nine exchange values per bond) and cubic anisotropy
+    at 300 K, 64 steps in the autotuned launch shape."""
+    lat = L.with_dm(L.fcc(64, 64, 64, J=11.2e-21, k_u=6.69e-24, with_pos=True), D=1.12e-21)
+    lat.k_c = np.full(lat.n, 5e-24)
+    ref = O.OracleSystem(lat.row_ptr, lat.col, lat.J, lat.mu_s, lat.k_u, lat.easy_axis, lat.K_neel, alpha=0.05,
+                         dt=1e-16, seed=4, J_tensor=lat.J_tensor, k_c=lat.k_c)
+    _whole_state(SS, lat, precision, 64, tol, [(ref, lat.n)], 300.0, alpha=0.05, dt=1e-16, seed=4,
+                 init_random=True)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-12)])
+def test_core_shell_whole_state_as_benchmarked(SS, precision, tol):
+    """The 20 nm core-shell sphere (Neel surface anisotropy, 1 T along x, 10 K), 64 steps in the
+    autotuned launch shape."""
+    lat = L.core_shell_sphere()
+    S0 = L.random_state(lat.n, 33)
+    ref = oracle_system(lat, alpha=0.1, dt=1e-16, H=(1.0, 0.0, 0.0), seed=3)
+    _whole_state(SS, lat, precision, 64, tol, [(ref, lat.n)], 10.0, alpha=0.1, dt=1e-16, H=(1.0, 0.0, 0.0),
+                 seed=3, S0=S0)
+
+
+def test_grain_ensemble_whole_state_as_benchmarked(SS):
+    """All 256 grains (5.4 M spins) of the batched form, FP32-mixed, 16 steps in the autotuned
+    launch shape, every spin and every grain's records against one oracle run per grain."""
+    grains, temps = L.grain_ensemble(count=256, seed=12345)
+    seeds = [4000 + k for k in range(256)]
+    S0 = [L.random_state(g.n, 50 + k) for k, g in enumerate(grains)]
+    refs = [(oracle_system(g, alpha=0.1, dt=1e-16, seed=seeds[k], sys_id=k), g.n) for k, g in enumerate(grains)]
+    _whole_state(SS, grains, "fp32", 16, 1e-4, refs, [float(t) for t in temps], alpha=0.1, dt=1e-16, seed=seeds,
+                 sys_id=list(range(256)), S0=S0)
