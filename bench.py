@@ -513,6 +513,8 @@ def main():
                     help="cubic cells per axis of the long-exchange-row leg's fcc crystal (default 64: 1.05 M atoms)")
     ap.add_argument("--midpoint-only", action="store_true",
                     help="run only the midpoint-rule leg on the film and print it")
+    ap.add_argument("--alt-steps", type=int, default=40,
+                    help="timed steps of each alternative-integrator run with --midpoint-only")
     ap.add_argument("--mc-only", action="store_true",
                     help="run only a short Monte Carlo leg on the film (for profiling) and print it")
     ap.add_argument("--no-autotune", action="store_true", help="no autotuning in the batched and workload legs")
@@ -561,7 +563,7 @@ def main():
         return
     if args.midpoint_only:
         if rank == 0:
-            print(json.dumps({"midpoint": midpoint_table(stream, rank)}))
+            print(json.dumps({"midpoint": midpoint_table(stream, rank, steps=args.alt_steps)}))
         return
     if args.mc_only:
         film = dict(spins=lat.n, **time_mc(lat, dict(T=300.0, seed=7 + rank), args.precision, args.steps, stream,
