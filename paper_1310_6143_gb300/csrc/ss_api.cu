@@ -1395,6 +1395,19 @@ ss_status mc_upload_params(ss_system *h) {
     return SS_OK;
 }
 
+// The kernel variant the alternative integrators launch for these arguments.
+template <typename R>
+int alt_mode(const KArgs<R> &a) {
+    return a.ex ? 2 : (a.J_tensor || a.any_cubic) ? 1 : 0;  // rows, general, plain (as step_mode)
+}
+
+// A grid-stride grid capped at one wave of `per_sm` resident blocks on every SM: more blocks
+// than fit would leave a partial second wave running at low occupancy.
+int one_wave(const ss_system *h, int grid, int per_sm) {
+    const int64_t wave = (int64_t)per_sm * h->sm_count;
+    return per_sm > 0 && wave < grid ? (int)wave : grid;
+}
+
 // Midpoint steps: per step the midpoint launches (the first of which leaves the tile partials
 // of the record of the state at the start of the step, finalised into the ring at the
 // device's step) and the step counter.
@@ -1405,9 +1418,10 @@ cudaError_t enqueue_midpoint(ss_system *h, int64_t nsteps, int iterations) {
     a.rows_bare = 1;
     const int rgrid = h->rows ? rows_grid(h) : 0;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sm_count * 8));
+    const int igrid = one_wave(h, grid, alt_pass_blocks_per_sm<R>(0, alt_mode(a)));
     cudaError_t e = cudaSuccess;
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-        e = launch_midpoint<R>(a, iterations, grid, rgrid, h->stream);
+        e = launch_midpoint<R>(a, iterations, grid, igrid, rgrid, h->stream);
         if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
     }
     return e;
@@ -1485,9 +1499,10 @@ cudaError_t enqueue_sib(ss_system *h, int64_t nsteps) {
     a.rows_bare = 1;
     const int rgrid = h->rows ? rows_grid(h) : 0;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + 255) / 256, (int64_t)h->sm_count * 8));
+    const int cgrid = one_wave(h, grid, alt_pass_blocks_per_sm<R>(1, alt_mode(a)));
     cudaError_t e = cudaSuccess;
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-        e = launch_sib<R>(a, grid, rgrid, h->stream);
+        e = launch_sib<R>(a, grid, cgrid, rgrid, h->stream);
         if (e == cudaSuccess) e = launch_advance_step(a.step, h->stream);
     }
     return e;

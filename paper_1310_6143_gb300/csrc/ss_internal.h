@@ -196,10 +196,16 @@ template <typename R> cudaError_t launch_demag(const KArgs<R> &a, const DemagArg
 // One midpoint step's launches after its record: Euler predictor, `iters` fixed-point
 // iterations, copy back (the step counter is advanced separately).
 // (rgrid: grid of the long-row passes, used when a.ex is set)
-template <typename R> cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, int rgrid, cudaStream_t s);
+// (igrid: grid of the fixed-point iterations, at most one resident wave)
+template <typename R> cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, int igrid, int rgrid,
+                                                  cudaStream_t s);
 // One semi-implicit predictor-corrector step's launches after its record (predictor, corrector;
 // the step counter is advanced separately).
-template <typename R> cudaError_t launch_sib(const KArgs<R> &a, int grid, int rgrid, cudaStream_t s);
+// (cgrid: grid of the corrector, at most one resident wave)
+template <typename R> cudaError_t launch_sib(const KArgs<R> &a, int grid, int cgrid, int rgrid, cudaStream_t s);
+// Resident 256-thread blocks per SM of the midpoint iterations (which = 0) or of the
+// semi-implicit corrector (which = 1) in the kernel variant `mode`.
+template <typename R> int alt_pass_blocks_per_sm(int which, int mode);
 // Exchange + applied field of (X, Y, Z) into (a.ex, a.ey, a.ez), a warp per row (long rows).
 template <typename R>
 cudaError_t launch_rows_field(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int grid, cudaStream_t s);

@@ -171,7 +171,7 @@ int alt_first_grid(const KArgs<R> &a, int grid) {
 }
 
 template <typename R, int Mode>
-cudaError_t launch_midpoint_mode(const KArgs<R> &a, int iters, int grid, int rgrid, cudaStream_t s) {
+cudaError_t launch_midpoint_mode(const KArgs<R> &a, int iters, int grid, int igrid, int rgrid, cudaStream_t s) {
     cudaError_t e = Mode == kRows ? launch_rows_field<R>(a, a.sx, a.sy, a.sz, rgrid, s) : cudaSuccess;
     if (e != cudaSuccess) return e;
     k_mid_euler<R, Mode><<<alt_first_grid(a, grid), kAltBlock, 0, s>>>(a);
@@ -181,7 +181,7 @@ cudaError_t launch_midpoint_mode(const KArgs<R> &a, int iters, int grid, int rgr
     R *x[3] = {a.px, a.py, a.pz}, *y[3] = {a.qx, a.qy, a.qz};
     for (int k = 0; k + 1 < iters && e == cudaSuccess; ++k) {
         if (Mode == kRows && (e = launch_rows_field<R>(a, x[0], x[1], x[2], rgrid, s)) != cudaSuccess) break;
-        k_mid_iter<R, Mode, false><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], y[0], y[1], y[2]);
+        k_mid_iter<R, Mode, false><<<igrid, 256, 0, s>>>(a, x[0], x[1], x[2], y[0], y[1], y[2]);
         e = cudaGetLastError();
         for (int c = 0; c < 3; ++c) {
             R *t = x[c];
@@ -191,21 +191,48 @@ cudaError_t launch_midpoint_mode(const KArgs<R> &a, int iters, int grid, int rgr
     }
     if (e == cudaSuccess && Mode == kRows) e = launch_rows_field<R>(a, x[0], x[1], x[2], rgrid, s);
     if (e == cudaSuccess) {  // the last iterate goes straight to S
-        k_mid_iter<R, Mode, true><<<grid, 256, 0, s>>>(a, x[0], x[1], x[2], a.sx, a.sy, a.sz);
+        k_mid_iter<R, Mode, true><<<igrid, 256, 0, s>>>(a, x[0], x[1], x[2], a.sx, a.sy, a.sz);
         e = cudaGetLastError();
     }
     return e;
 }
 
 template <typename R>
-cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, int rgrid, cudaStream_t s) {
-    if (a.ex) return launch_midpoint_mode<R, kRows>(a, iters, grid, rgrid, s);
-    return (a.J_tensor || a.any_cubic) ? launch_midpoint_mode<R, kGeneral>(a, iters, grid, rgrid, s)
-                                       : launch_midpoint_mode<R, kPlain>(a, iters, grid, rgrid, s);
+cudaError_t launch_midpoint(const KArgs<R> &a, int iters, int grid, int igrid, int rgrid, cudaStream_t s) {
+    if (a.ex) return launch_midpoint_mode<R, kRows>(a, iters, grid, igrid, rgrid, s);
+    return (a.J_tensor || a.any_cubic) ? launch_midpoint_mode<R, kGeneral>(a, iters, grid, igrid, rgrid, s)
+                                       : launch_midpoint_mode<R, kPlain>(a, iters, grid, igrid, rgrid, s);
+}
+
+// Resident 256-thread blocks per SM of the second-pass kernels of the alternative integrators
+// (which = 0: the midpoint iterations, the smaller of their two variants; 1: the semi-implicit
+// corrector) in the variant `mode` (kPlain, kGeneral or kRows); 0 if the query fails.
+template <typename R>
+int alt_pass_blocks_per_sm(int which, int mode) {
+    int n0 = 0, n1 = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define SS_OCC(MODE)                                                                              \
+    if (which == 0) {                                                                             \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_mid_iter<R, MODE, false>, 256, 0); \
+        if (e == cudaSuccess)                                                                     \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_mid_iter<R, MODE, true>, 256, 0); \
+        n0 = n1 < n0 ? n1 : n0;                                                                   \
+    } else {                                                                                      \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_sib_corr<R, MODE>, 256, 0);      \
+    }
+    if (mode == kRows) {
+        SS_OCC(kRows)
+    } else if (mode == kGeneral) {
+        SS_OCC(kGeneral)
+    } else {
+        SS_OCC(kPlain)
+    }
+#undef SS_OCC
+    return e == cudaSuccess ? n0 : 0;
 }
 
 template <typename R>
-cudaError_t launch_sib(const KArgs<R> &a, int grid, int rgrid, cudaStream_t s) {
+cudaError_t launch_sib(const KArgs<R> &a, int grid, int cgrid, int rgrid, cudaStream_t s) {
     const int mode = a.ex ? kRows : (a.J_tensor || a.any_cubic) ? kGeneral : kPlain;
     cudaError_t e = mode == kRows ? launch_rows_field<R>(a, a.sx, a.sy, a.sz, rgrid, s) : cudaSuccess;
     if (e != cudaSuccess) return e;
@@ -221,11 +248,11 @@ cudaError_t launch_sib(const KArgs<R> &a, int grid, int rgrid, cudaStream_t s) {
     if (e == cudaSuccess && mode == kRows) e = launch_rows_field<R>(a, a.px, a.py, a.pz, rgrid, s);
     if (e != cudaSuccess) return e;
     if (mode == kRows)
-        k_sib_corr<R, kRows><<<grid, 256, 0, s>>>(a);
+        k_sib_corr<R, kRows><<<cgrid, 256, 0, s>>>(a);
     else if (mode == kGeneral)
-        k_sib_corr<R, kGeneral><<<grid, 256, 0, s>>>(a);
+        k_sib_corr<R, kGeneral><<<cgrid, 256, 0, s>>>(a);
     else
-        k_sib_corr<R, kPlain><<<grid, 256, 0, s>>>(a);
+        k_sib_corr<R, kPlain><<<cgrid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -304,8 +331,9 @@ template cudaError_t launch_mc_colour_rec<SS_REAL>(const KArgs<SS_REAL> &, const
 template cudaError_t launch_mc_colour_warp<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);
 template int mc_blocks_per_sm<SS_REAL>(int, int);
 template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
-template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
-template cudaError_t launch_sib<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
+template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, int, cudaStream_t);
+template cudaError_t launch_sib<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
+template int alt_pass_blocks_per_sm<SS_REAL>(int, int);
 template cudaError_t launch_rows_field<SS_REAL>(const KArgs<SS_REAL> &, const SS_REAL *, const SS_REAL *,
                                                 const SS_REAL *, int, cudaStream_t);
 template int rows_blocks_per_sm<SS_REAL>();
