@@ -2197,10 +2197,14 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     struct Cand { int exec, block, tile, ahead; };
     std::vector<Cand> cands;
     const bool mixed = h->precision == SS_FP32_MIXED;
-    for (int b : {256, 512})
+    // 128-thread blocks only where 256-thread tiles would leave most SMs idle: a small system
+    // spread over twice the SMs has twice the FP64 lanes for its thermal draws
+    const bool small = n <= (int64_t)h->sm_count * 256;
+    for (int b : {128, 256, 512})
         for (int m : {1, 2, 4, 8})
             for (int q : {4, 5, 6}) {
                 if (!mixed && q != 6) continue;  // no draw-ahead in the FP64 form
+                if (b == 128 && (!small || m > 2)) continue;
                 cands.push_back({SS_EXEC_GRAPH, b, b * m, q});
                 cands.push_back({SS_EXEC_PERSISTENT, b, b * m, q});
             }
