@@ -62,7 +62,9 @@ class SpinSystem:
         Hs = _per_system(H, count, "H")
         seeds = _per_system(seed, count, "seed")
         ids = list(range(count)) if sys_id is None else _per_system(sys_id, count, "sys_id")
-        S0s = [None] * count if S0 is None else (S0 if count > 1 else [S0])
+        S0s = [None] * count if S0 is None else (list(S0) if count > 1 else [S0])
+        if len(S0s) != count:
+            raise ValueError(f"S0: need one initial state per system ({count})")
         if precision not in _PREC:
             raise ValueError(f"precision must be one of {sorted(_PREC)}")
         keep = []
@@ -135,6 +137,7 @@ class SpinSystem:
         """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (own stream)."""
         raw = getattr(stream, "cuda_stream", stream)
         self._check(self._lib.spin_system_set_stream(self._h, ctypes.c_void_p(raw) if raw else None))
+        self._stream = stream  # the handle launches on it: keep the owner alive as long as the handle
 
     def set_field(self, H, sys: int = -1):
         arr = np.ascontiguousarray(H, dtype=np.float64).reshape(3)

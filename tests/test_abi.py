@@ -89,3 +89,17 @@ def test_host_validation_without_gpu(lib):
         st, msg = create(**over)
         assert st == 1, (over, st, msg)  # SS_ERR_INVALID_ARG
         assert text in msg, (over, msg)
+
+
+def test_binding_rejects_mismatched_per_system_arguments(lib):
+    """The Python front end checks per-system argument counts before it calls the library."""
+    from paper_1310_6143_gb300 import lattice as L
+    from paper_1310_6143_gb300.system import SpinSystem
+
+    lats = [L.simple_cubic(3, 3, 3)] * 2
+    with pytest.raises(ValueError, match="S0"):
+        SpinSystem(lats, S0=[L.random_state(27, 1)])
+    with pytest.raises(ValueError, match="T"):
+        SpinSystem(lats, T=[1.0, 2.0, 3.0])
+    with pytest.raises(ValueError, match="precision"):
+        SpinSystem(lats[0], precision="bf16")
