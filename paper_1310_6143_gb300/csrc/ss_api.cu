@@ -143,7 +143,7 @@ struct ss_system {
     void *d_hd[3] = {};
 
     // Long exchange rows: the exchange field summed by a warp per row (k_rows_field) before
-    // each step pass, when rows average kRowsAuto or more bonds (or on request)
+    // each step pass, when the rows are long enough (set_rows) or on request
     int rows_req = 0;            // 0 automatic, 1 a thread per row, 2 a warp per row
     bool rows = false;           // a warp per row in force
     uint32_t *sell = nullptr;    // packed bonds col << 8 | dictionary entry, slices of 32 rows
