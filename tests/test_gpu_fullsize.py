@@ -196,7 +196,7 @@ def test_core_shell_whole_state_as_benchmarked(SS, precision, tol):
 
 
 def test_grain_ensemble_whole_state_as_benchmarked(SS):
-    """All 256 grains (5.4 M spins) of the batched form, FP32-mixed, 16 steps in the autotuned
+    """All 256 grains (5.2 M spins) of the batched form, FP32-mixed, 16 steps in the autotuned
     launch shape, every spin and every grain's records against one oracle run per grain."""
     grains, temps = L.grain_ensemble(count=256, seed=12345)
     seeds = [4000 + k for k in range(256)]
