@@ -319,6 +319,9 @@ ss_status spin_system_set_draw_ahead(ss_system *h, int32_t eighths);
  * variant) takes its stored choice without trial runs, and a new result is appended. */
 ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_info);
 
+/* The handle's sizes and current launch settings into *out (caller-owned).  `exec` is the mode
+ * selected (SS_EXEC_AUTO stays AUTO: the library picks graphs or plain launches per call).
+ * Host-only, no synchronisation; SS_ERR_INVALID_ARG for a NULL out. */
 ss_status spin_system_info(ss_system *h, ss_info *out);
 
 /* Advance `nsteps` steps with one predictor and one corrector launch each, timing every
