@@ -24,7 +24,7 @@ LIB = os.path.join(OUT_DIR, "libspinsys.so")
 CHECKED_DIR = os.path.join(HERE, "_build_checked")
 CHECKED_LIB = os.path.join(CHECKED_DIR, "libspinsys.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-Wall,-Wextra"]
 
 
 def nvcc() -> str:
