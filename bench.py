@@ -691,7 +691,9 @@ def main():
         "gpu_launches": (-(-args.steps // 64)) if info32["exec"] == 3 else 2 * args.steps,
         "final_m": [float(x) for x in mag32],
     }
-    if not args.no_extras:
+    # the FP64, batched, workload, Monte Carlo, demagnetising, alternative-integrator, long-row and
+    # CPU-baseline legs are single-GPU diagnostics: at N > 1 the line carries the headline only
+    if not args.no_extras and world == 1:
         k64 = max(20, args.steps // 4)
         ms64, kt64, _, clk64, _, _ = timed_run("fp64", k64, args.warmup, 5)
         out["fp64"] = {"value": world * lat.n * k64 / (ms64 * 1e-3), "unit": "spin-steps/s", "steps": k64,
@@ -724,8 +726,7 @@ def main():
         out["demag"] = demag_table(stream, rank)
         out["midpoint"] = midpoint_table(stream, rank)
         out["long_range"] = long_range_table(stream, rank, hbm_peak=hbm_peak)
-        if rank == 0:
-            out["cpu_baseline"] = cpu_baseline(lat, T)
+        out["cpu_baseline"] = cpu_baseline(lat, T)
     if rank == 0:
         print(json.dumps(out))
 
