@@ -637,6 +637,7 @@ def main():
         return ms, kt, e2e_s / e2e_steps, ck.summary(local), mag, info
 
     ms32, kt32, e2e32, clk32, mag32, info32 = timed_run(args.precision, args.steps, args.warmup, 5)
+    e2e32 = max_over_ranks(world, e2e32)  # the job's end-to-end step time: its slowest rank
     value = world * lat.n * args.steps / (ms32 * 1e-3)
     sm_ghz = (clk32.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))) / 1e3
     fp64_peak = SMS * FP64_SLOTS_PER_SM_CYCLE * 2 * sm_ghz / 1e3  # TFLOP/s (FMA-slot flops)
