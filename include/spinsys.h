@@ -349,8 +349,11 @@ ss_status spin_system_sync(ss_system *h);
 /* Diagnostics (synchronous, default device, no handle).  ss_debug_philox writes the
  * Philox4x32-10 blocks of counters (ctr0[0]+k, ctr0[1], ctr0[2], ctr0[3]), k < count,
  * to out[4*count].  ss_debug_gaussians writes the thermal Gaussian triples of spins
- * 0..n-1 at one (seed, system id, step) to out[3n]; mode 0 uses the step kernels'
- * table-driven FP64 transform, mode 1 CUDA's own log/sqrt/sincospi. */
+ * 0..n-1 at one (seed, system id, step) to out[3n]; mode 0 uses the FP64 form's
+ * table-driven FP64 transform, mode 1 CUDA's own log/sqrt/sincospi; modes 2-4 the FP32-mixed
+ * form's transform: 2 the float Gaussians its step kernels use (the FP64 transform's values
+ * rounded to float), 3 the double-float values before that rounding, 4 a flag (1.0 in the
+ * first slot) for draws whose rounding the double-float evaluation could not certify. */
 ss_status ss_debug_philox(const uint32_t ctr0[4], const uint32_t key[2], int64_t count, uint32_t *out);
 ss_status ss_debug_gaussians(uint64_t seed, uint32_t sys_id, uint32_t step, int64_t n, int32_t mode, double *out);
 

@@ -106,7 +106,10 @@ struct ss_system {
     float *sched_f = nullptr;
     int64_t rec_cap = 0, sched_len = 0, sched_step0 = 0, sched_cap = 0;
     unsigned long long *ctl = nullptr;  // [0] step, [1] err|ticket, [2] barrier count|gen
-    double2 *tab = nullptr;             // Box-Muller tables (build_bm_tables)
+    double2 *tab = nullptr;             // Box-Muller tables (build_bm_tables), then the
+                                        // double-float tables (build_ff_tables)
+    int32_t max_row = 0;                // longest CSR row
+    alignas(16) unsigned char mat0[sizeof(MatDesc<double>)] = {};  // MatDesc<R> of material 0
 
     std::vector<SysDesc> hsys;
     std::vector<int64_t> sys_offset, sys_n;
@@ -354,10 +357,13 @@ ss_status validate(const ss_params *p, int idx) {
     return SS_OK;
 }
 
-// Function tables of the table-driven FP64 Box-Muller transform.
+// Function tables of the table-driven FP64 Box-Muller transform, followed by the double-float
+// tables of the FP32-mixed transform (16-byte slots both).
 void build_tables(std::vector<double2> &t) {
-    t.resize(kTabCount);
+    static_assert(sizeof(float4) == sizeof(double2), "table slots");
+    t.resize(kTabCount + kFFTabFloat4);
     build_bm_tables(t.data());
+    build_ff_tables(reinterpret_cast<float4 *>(t.data() + kTabCount));
 }
 
 template <typename R>
@@ -369,6 +375,9 @@ KArgs<R> make_args(const ss_system *h) {
     a.J = static_cast<const R *>(h->J);
     a.J_value = (R)h->J_value;
     a.J_uniform = h->J_uniform ? 1 : 0;
+    a.short_rows = h->max_row <= kShortRow ? 1 : 0;
+    a.mat_uniform = h->nmat == 1 ? 1 : 0;
+    std::memcpy(&a.mat0, h->mat0, sizeof(MatDesc<R>));
     a.Jt = static_cast<const R *>(h->Jt);
     a.Jtidx = h->Jtidx;
     a.J_tensor = h->J_tensor ? 1 : 0;
@@ -419,6 +428,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.bar_count = reinterpret_cast<unsigned int *>(h->ctl + 2);
     a.bar_gen = reinterpret_cast<unsigned int *>(h->ctl + 2) + 1;
     a.tab = h->tab;
+    a.fftab = reinterpret_cast<const float4 *>(h->tab + kTabCount);
     a.bar_extra = h->bar_extra;
     a.bar_timeout_ns = h->bar_timeout_ns;
     return a;
@@ -462,8 +472,11 @@ void drop_graph(ss_system *h) {
     h->pgraph_steps = 0;
 }
 
-// The step-kernel variant the launchers pick for this handle (0 plain, 1 general, 2 rows).
-int step_mode(const ss_system *h) { return h->rows ? 2 : (h->J_tensor || h->any_cubic) ? 1 : 0; }
+// The Heun step-kernel variant the launchers pick for this handle (0 plain, 1 general, 2 rows,
+// 3 plain with a single material).
+int step_mode(const ss_system *h) {
+    return h->rows ? 2 : (h->J_tensor || h->any_cubic) ? 1 : (h->nmat == 1 ? 3 : 0);
+}
 // The variant of the kernels that sum their own rows (Monte Carlo, persistent, system blocks).
 int own_rows_mode(const ss_system *h) { return (h->J_tensor || h->any_cubic) ? 1 : 0; }
 
@@ -486,7 +499,7 @@ int corrector_grid(const ss_system *h) {
 }
 
 int persistent_grid(const ss_system *h) {
-    const int mode = own_rows_mode(h);
+    const int mode = own_rows_mode(h) == 0 && h->nmat == 1 ? 3 : own_rows_mode(h);
     const int per_sm = h->precision == SS_FP32_MIXED ? persistent_blocks_per_sm<float>(h->block, mode)
                                                      : persistent_blocks_per_sm<double>(h->block, mode);
     const int64_t g = (int64_t)h->sm_count * per_sm;
@@ -796,6 +809,9 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     }
     rp[n] = (int32_t)nnz;
     h->nmat = (int32_t)mats.size();
+    if (!mats.empty()) std::memcpy(h->mat0, &mats[0], sizeof(MatDesc<R>));
+    h->max_row = 0;
+    for (int64_t i = 0; i < n; ++i) h->max_row = std::max<int32_t>(h->max_row, rp[i + 1] - rp[i]);
     h->any_cubic = false;
     for (const MatDesc<R> &m : mats) h->any_cubic = h->any_cubic || m.has_cubic;
     // Homogeneous exchange (one J_ij / mu_s,i for every bond): the kernels skip the J loads.
@@ -2284,7 +2300,7 @@ ss_status ss_debug_philox(const uint32_t ctr0[4], const uint32_t key[2], int64_t
 }
 
 ss_status ss_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, int64_t n, int32_t mode, double *out) {
-    if (!out || n < 0 || (mode != 0 && mode != 1)) return fail(nullptr, SS_ERR_INVALID_ARG, "bad arguments");
+    if (!out || n < 0 || mode < 0 || mode > 4) return fail(nullptr, SS_ERR_INVALID_ARG, "bad arguments");
     std::vector<double2> tab;
     build_tables(tab);
     double2 *dt = nullptr;

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "ss_ff.cuh"
 #include "ss_kernels.cuh"
 
 namespace ss {
@@ -47,7 +48,7 @@ cudaError_t launch_debug_philox(const uint32_t *ctr0, const uint32_t *key, long 
     return cudaGetLastError();
 }
 
-// mode 0: the step kernels' table-driven transform; mode 1: CUDA's log/sqrt/sincospi.
+// mode 0: the FP64 form's table-driven transform; mode 1: CUDA's log/sqrt/sincospi.
 __global__ void k_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
                                   const double2 *tabs, double *out) {
     __shared__ SmemTables tab;
@@ -67,9 +68,65 @@ __global__ void k_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, lo
     }
 }
 
+// The FP32-mixed form's transform.  mode 2: the Gaussians the step kernels use (rounded to
+// float, uncertain roundings resolved by the FP64 transform); mode 3: the double-float values
+// hi + lo before rounding; mode 4: 1 where a rounding of the draw was uncertain, else 0 (in
+// the first of the three slots).
+__global__ void k_debug_gaussians_ff(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
+                                     const double2 *tabs, double *out) {
+    __shared__ FFTables tab;
+    stage_ff_tables(reinterpret_cast<const float4 *>(tabs + kTabCount), tab);
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const Philox4 w = philox4x32_10((uint32_t)i, step, sys, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+        double v[3] = {0.0, 0.0, 0.0};
+        if (mode == 2) {
+            float g0, g1, g2;
+            gaussians_f32(w, tab, tabs, g0, g1, g2);
+            v[0] = g0;
+            v[1] = g1;
+            v[2] = g2;
+        } else {
+            const FF R1 = ff_sqrt(ff_neg2log(w.w0, tab));
+            const FF R2 = ff_sqrt(ff_neg2log(w.w2, tab));
+            float g[3];
+            const bool ok = box_muller3_ff(w, tab, g[0], g[1], g[2]);
+            if (mode == 4) {
+                v[0] = ok ? 0.0 : 1.0;
+            } else {
+                // the unrounded double-float products, as box_muller3_ff forms them
+                const FFTurn a = ff_turn(w.w1, tab);
+                const FF sb = ff_rot(a.tv.x, a.tv.y, a.tv.z, a.tv.w, a);
+                const FF cb = ff_rot(a.tv.z, a.tv.w, -a.tv.x, -a.tv.y, a);
+                const bool swap = ((a.o + 1u) >> 1) & 1u;
+                FF S = swap ? cb : sb, Co = swap ? sb : cb;
+                if (a.o & 4u) S = ff_neg(S);
+                if ((a.o + 2u) & 4u) Co = ff_neg(Co);
+                const FFTurn b = ff_turn(w.w3, tab);
+                const bool swap2 = ((b.o + 1u) >> 1) & 1u;
+                FF C2 = swap2 ? ff_rot(b.tv.x, b.tv.y, b.tv.z, b.tv.w, b)
+                              : ff_rot(b.tv.z, b.tv.w, -b.tv.x, -b.tv.y, b);
+                if ((b.o + 2u) & 4u) C2 = ff_neg(C2);
+                const FF R[3] = {R1, R1, R2}, V[3] = {Co, S, C2};
+                for (int c = 0; c < 3; ++c) {
+                    const float gh = __fmul_rn(R[c].hi, V[c].hi);
+                    const float ge = __fadd_rn(fmaf(R[c].hi, V[c].hi, -gh), fmaf(R[c].hi, V[c].lo, __fmul_rn(R[c].lo, V[c].hi)));
+                    v[c] = (double)gh + (double)ge;
+                }
+            }
+        }
+        out[3 * i + 0] = v[0];
+        out[3 * i + 1] = v[1];
+        out[3 * i + 2] = v[2];
+    }
+}
+
 cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
                                    const double2 *tab, double *out, cudaStream_t s) {
-    k_debug_gaussians<<<256, 256, 0, s>>>(seed, sys, step, n, mode, tab, out);
+    if (mode <= 1)
+        k_debug_gaussians<<<256, 256, 0, s>>>(seed, sys, step, n, mode, tab, out);
+    else
+        k_debug_gaussians_ff<<<256, 256, 0, s>>>(seed, sys, step, n, mode, tab, out);
     return cudaGetLastError();
 }
 
@@ -106,6 +163,31 @@ void build_bm_tables(double2 *t) {
         const long double a = twopi * (long double)j / 4096.0L;  // first octant of 4096 points
         t[kLogTab + kLn2Tab + j] = make_double2((double)sinl(a), (double)cosl(a));
     }
+}
+
+// Double-float tables of the FP32-mixed transform (layout in FFTables), evaluated in long
+// double and split as hi = the value rounded to float, lo = the remainder rounded to float.
+void build_ff_tables(float4 *t) {
+    auto split = [](long double v, float &hi, float &lo) {
+        hi = (float)v;
+        lo = (float)(v - (long double)hi);
+    };
+    for (int i = 0; i < kLogTab; ++i) {
+        const long double c = (long double)(kLogFirst + i) / (long double)kLogScale;
+        split(1.0L / c, t[i].x, t[i].y);
+        split(-2.0L * logl(c), t[i].z, t[i].w);
+    }
+    const long double twopi = 6.283185307179586476925286766559005768L;
+    for (int m = 0; m < kTrigTab; ++m) {
+        const long double a = twopi * (long double)m / 4096.0L;  // first octant of 4096 points
+        float4 &e = t[kLogTab + m];
+        split(sinl(a), e.x, e.y);
+        split(cosl(a), e.z, e.w);
+    }
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    float *l2 = reinterpret_cast<float *>(t + kLogTab + kTrigTab);
+    for (int i = 0; i < 4 * ((kLn2Tab + 1) / 2); ++i) l2[i] = 0.0f;
+    for (int n = 0; n < kLn2Tab; ++n) split(2.0L * (long double)n * ln2, l2[2 * n], l2[2 * n + 1]);
 }
 
 // FP64 instruction throughput probe: eight independent chains per thread.  mode 0: DFMA

@@ -21,6 +21,10 @@ constexpr int kTrigTab = 513;  // (sin, cos) of pi m / 2048, m = 0..512: one oct
 constexpr int kLogLo = (kLogTab + 3) / 4;  // double2 slots holding the kLogTab float remainders
 // One table buffer of double2: log | ln2 | trig | log remainders (floats, packed four per slot).
 constexpr int kTabCount = kLogTab + kLn2Tab + kTrigTab + kLogLo;
+// The double-float tables of the FP32-mixed transform (build_ff_tables), in float4 slots after
+// the kTabCount double2 slots of the same buffer: log | trig | 2 n ln 2 (two per slot).
+constexpr int kFFTabFloat4 = kLogTab + kTrigTab + (kLn2Tab + 1) / 2;
+constexpr int kShortRow = 6;   // rows of at most this many bonds take the unrolled exchange sum
 constexpr int kRecComps = 8;   // record: sum mu S (3), sum mu, E_exc, E_ani, E_app, E_total
 constexpr int kPartComps = 8;  // tile partials: sum mu S (3), sum -mu S.h/2, E_ani, 0, 0, 0
 
@@ -79,6 +83,9 @@ struct KArgs {
     const R *J;               // [nnz] J_ij / mu_s,i (the exchange field per unit spin, T)
     R J_value;                // the common value when every entry of J is the same
     int J_uniform;            // 1: J is not read, every bond has J_value
+    int short_rows;           // 1: no row has more than kShortRow bonds
+    MatDesc<R> mat0;          // the only material when mat_uniform is set
+    int mat_uniform;          // 1: every spin has material 0 (mat is not read)
     const R *Jt;              // [9 ndict] distinct exchange tensors / mu_s,i, row by row
     const int32_t *Jtidx;     // [nnz] tensor of each bond (J_tensor = 1)
     int J_tensor;             // 1: the exchange sum uses Jt[Jtidx[k]] instead of J
@@ -127,6 +134,7 @@ struct KArgs {
     unsigned int *err;        // bit 0: non-finite spin, bit 1: barrier timeout
     unsigned int *ticket;     // completion counter of the corrector launch
     const double2 *tab;       // Box-Muller tables, kTabCount entries (build_bm_tables)
+    const float4 *fftab;      // double-float tables, kFFTabFloat4 entries (build_ff_tables)
     unsigned int *bar_count;  // grid barrier of the persistent kernel
     unsigned int *bar_gen;
     unsigned int bar_extra;   // test hook: phantom blocks the barrier waits for
@@ -223,5 +231,7 @@ cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, l
 
 // Host (ss_common.cu): fills the kTabCount entries of the Box-Muller tables.
 void build_bm_tables(double2 *t);
+// Host (ss_common.cu): fills the kFFTabFloat4 entries of the double-float tables.
+void build_ff_tables(float4 *t);
 
 }  // namespace ss

@@ -25,6 +25,7 @@
 #include <stdint.h>
 
 #include "ss_internal.h"
+#include "ss_ff.cuh"
 #include "ss_math.cuh"
 
 namespace ss {
@@ -73,6 +74,27 @@ __device__ __forceinline__ void stage_tables(const KArgs<R> &a, SmemTables &t) {
     stage_bm_tables(a.tab, t);
 }
 
+// Tables of the Heun step kernels' thermal transform: the FP64 tables for the FP64 form, the
+// double-float tables for the FP32-mixed form (whose rare uncertain roundings read the FP64
+// tables from global memory).
+template <typename R> struct StepTab { using type = SmemTables; };
+template <> struct StepTab<float> { using type = FFTables; };
+template <typename R> using StepTabT = typename StepTab<R>::type;
+
+__device__ __forceinline__ void stage_step_tables(const KArgs<double> &a, SmemTables &t) { stage_bm_tables(a.tab, t); }
+__device__ __forceinline__ void stage_step_tables(const KArgs<float> &a, FFTables &t) { stage_ff_tables(a.fftab, t); }
+
+// Three standard Gaussians of one Philox block in the working type: the FP64 transform, and
+// in the FP32-mixed form its values rounded to float (bit for bit, see ss_ff.cuh).
+__device__ __forceinline__ void thermal_gaussians(const KArgs<double> &, const SmemTables &tab, const Philox4 &w,
+                                                  double &g0, double &g1, double &g2) {
+    box_muller3(w, tab, g0, g1, g2);
+}
+__device__ __forceinline__ void thermal_gaussians(const KArgs<float> &a, const FFTables &tab, const Philox4 &w,
+                                                  float &g0, float &g1, float &g2) {
+    gaussians_f32(w, tab, a.tab, g0, g1, g2);
+}
+
 // H_app + sum_j (J_ij / mu_s,i) X_j over row i (CSR order, one FMA per term and
 // component): the exchange plus applied field, in tesla.
 // Variants of the step kernels, fixed at compile time so that a plain lattice's kernels carry
@@ -80,6 +102,20 @@ __device__ __forceinline__ void stage_tables(const KArgs<R> &a, SmemTables &t) {
 // and cubic anisotropy decided per launch / material), kRows (the exchange field summed
 // beforehand by k_rows_sell / k_rows_field; cubic per material).
 constexpr int kPlain = 0, kGeneral = 1, kRows = 2;
+// kUniform: kPlain with a single material, read from the kernel arguments (the Heun step
+// kernels only; everything else treats it as kPlain).
+constexpr int kUniform = 3;
+__host__ __device__ constexpr int base_mode(int mode) { return mode == kUniform ? kPlain : mode; }
+
+template <int Mode, typename R>
+__device__ __forceinline__ const MatDesc<R> &mat_at(const KArgs<R> &a, int64_t i) {
+    if constexpr (Mode == kUniform) {
+        (void)i;
+        return a.mat0;
+    } else {
+        return a.mats[__ldg(a.mat + i)];
+    }
+}
 
 // Checked builds (SS_CHECKED): an index about to be gathered with is checked against [0, n);
 // a bad one sets kErrBounds in the error word and is replaced by 0, so nothing outside the
@@ -123,12 +159,25 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
         e2 = z;
         return;
     }
-    for (int32_t k = b; k < e; ++k) {
-        const int32_t j = chk(__ldg(a.col + k), a.n, a.err);
-        const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + k);
-        x = fma(Jk, ld<Coherent>(X + j), x);
-        y = fma(Jk, ld<Coherent>(Y + j), y);
-        z = fma(Jk, ld<Coherent>(Z + j), z);
+    if (a.short_rows) {  // at most kShortRow bonds: unrolled, so the row's loads issue together
+#pragma unroll
+        for (int q = 0; q < kShortRow; ++q) {
+            if (b + q < e) {
+                const int32_t j = chk(__ldg(a.col + b + q), a.n, a.err);
+                const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + b + q);
+                x = fma(Jk, ld<Coherent>(X + j), x);
+                y = fma(Jk, ld<Coherent>(Y + j), y);
+                z = fma(Jk, ld<Coherent>(Z + j), z);
+            }
+        }
+    } else {
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t j = chk(__ldg(a.col + k), a.n, a.err);
+            const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + k);
+            x = fma(Jk, ld<Coherent>(X + j), x);
+            y = fma(Jk, ld<Coherent>(Y + j), y);
+            z = fma(Jk, ld<Coherent>(Z + j), z);
+        }
     }
     e0 = x;
     e1 = y;
@@ -187,13 +236,13 @@ __device__ __forceinline__ void llg_rhs(R gp, R lam, R s0, R s1, R s2, R H0, R H
 // -H.M (H is uniform within a system) and the exchange energy sum(-mu S.h/2) + H.M/2;
 // both are formed from the FP64 sums when a system's record is finalised.
 template <typename R, bool Cubic = true>
-__device__ __forceinline__ void spin_terms(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R sde,
-                                           double v[5]) {
+__device__ __forceinline__ void spin_terms_r(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R sde,
+                                             R v[5]) {
     const R mu = m.mu;
-    v[0] = widen(mu * s0);
-    v[1] = widen(mu * s1);
-    v[2] = widen(mu * s2);
-    v[3] = widen((R)-0.5 * mu * (s0 * e0 + s1 * e1 + s2 * e2));
+    v[0] = mu * s0;
+    v[1] = mu * s1;
+    v[2] = mu * s2;
+    v[3] = (R)-0.5 * mu * (s0 * e0 + s1 * e1 + s2 * e2);
     R ea = -m.ku * sde * sde;
     if (Cubic && m.has_cubic) {
         const R x2 = s0 * s0, y2 = s1 * s1, z2 = s2 * s2;
@@ -203,8 +252,65 @@ __device__ __forceinline__ void spin_terms(const MatDesc<R> &m, R s0, R s1, R s2
         ea -= m.K[0] * s0 * s0 + m.K[1] * s1 * s1 + m.K[2] * s2 * s2
             + (R)2 * (m.K[3] * s0 * s1 + m.K[4] * s0 * s2 + m.K[5] * s1 * s2);
     }
-    v[4] = widen(ea);
+    v[4] = ea;
 }
+
+template <typename R, bool Cubic = true>
+__device__ __forceinline__ void spin_terms(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R sde,
+                                           double v[5]) {
+    R t[5];
+    spin_terms_r<R, Cubic>(m, s0, s1, s2, e0, e1, e2, sde, t);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v[c] = widen(t[c]);
+}
+
+// A thread's sums of the five record terms over its spins of a tile.  FP64 form: FP64 sums.
+// FP32-mixed form: each float term is added by TwoSum, the running sum hi keeping the float
+// sum and lo the sum of TwoSum's exact rounding errors, so that hi + lo is the exact sum up
+// to lo's own rounding (a relative 2^-48 of the sum); hi and lo are widened to FP64 once per
+// tile, and every later stage sums in FP64.  The FP64 pipe then runs no per-spin work.
+template <typename R>
+struct TermAcc;
+
+template <>
+struct TermAcc<double> {
+    double s[5];
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) s[c] = 0.0;
+    }
+    __device__ __forceinline__ void add(const double v[5]) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) s[c] += v[c];
+    }
+    __device__ __forceinline__ void out(double (&acc)[8]) const {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) acc[c] = s[c];
+        acc[5] = acc[6] = acc[7] = 0.0;
+    }
+};
+
+template <>
+struct TermAcc<float> {
+    float h[5], l[5];
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) h[c] = l[c] = 0.0f;
+    }
+    __device__ __forceinline__ void add(const float v[5]) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const FF t = ff_two_sum(h[c], v[c]);
+            h[c] = t.hi;
+            l[c] = __fadd_rn(l[c], t.lo);
+        }
+    }
+    __device__ __forceinline__ void out(double (&acc)[8]) const {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) acc[c] = f2d_bits(h[c]) + f2d_bits(l[c]);
+        acc[5] = acc[6] = acc[7] = 0.0;
+    }
+};
 
 // Sum of eight FP64 values over a warp by a transposing butterfly: 9 additions per lane
 // instead of 40.  Afterwards lane L holds component ((L>>4)&1)*4 + ((L>>3)&1)*2 + ((L>>2)&1).
@@ -296,23 +402,25 @@ __device__ __forceinline__ void flush_partials(const double *red, int nq, double
 // per-spin reduction terms.
 template <typename R, int BS, bool Coherent, int Mode = kGeneral>
 __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
-                                               const SmemTables &tab, int pre_slot, double (&acc)[8]) {
+                                               const StepTabT<R> &tab, int pre_slot, double (&acc)[8]) {
+    constexpr int BM = base_mode(Mode);
     const SysDesc &sd = a.sys[td.sys];
     const R sqrtT = sqrtT_of_step(a, step, sd);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = 0.0;
-    bool first = true;
+    const uint32_t key0 = sd.key0, key1 = sd.key1, ctr2 = sd.ctr2;
+    const int64_t off = sd.offset;
+    TermAcc<R> ta;
+    ta.reset();
     // The slot index is rotated by the warp index, so that the warps of a block reach their
-    // FP64-heavy slots (the Gaussians not drawn ahead) at different times.
+    // transform-heavy slots (the Gaussians not drawn ahead) at different times.
     int rot = (threadIdx.x >> 5) % a.slots;
     for (int k = threadIdx.x; k < td.count; k += BS, rot = rot + 1 == a.slots ? 0 : rot + 1) {
         const int64_t i = td.start + k;
-        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+        const MatDesc<R> &m = mat_at<Mode>(a, i);
         const R s0 = ld<Coherent>(a.sx + i), s1 = ld<Coherent>(a.sy + i), s2 = ld<Coherent>(a.sz + i);
         R e0, e1, e2;
-        exchange_sum<R, Coherent, Mode>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
+        exchange_sum<R, Coherent, BM>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
         R H0, H1, H2;
-        const R sde = det_field<R, Mode != kPlain>(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+        const R sde = det_field<R, BM != kPlain>(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         if (a.demag) add_demag(a, i, H0, H1, H2);
         R t0 = 0, t1 = 0, t2 = 0;
         if (sqrtT > (R)0) {
@@ -322,13 +430,12 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
                 t1 = sig * ld<Coherent>(a.gy + i);
                 t2 = sig * ld<Coherent>(a.gz + i);
             } else {
-                const Philox4 w =
-                    philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
-                double g0, g1, g2;
-                box_muller3(w, tab, g0, g1, g2);
-                t0 = sig * narrow<R>(g0);
-                t1 = sig * narrow<R>(g1);
-                t2 = sig * narrow<R>(g2);
+                const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)step, ctr2, 0u, key0, key1);
+                R g0, g1, g2;
+                thermal_gaussians(a, tab, w, g0, g1, g2);
+                t0 = sig * g0;
+                t1 = sig * g1;
+                t2 = sig * g2;
             }
         }
         a.hx[i] = t0;
@@ -349,35 +456,38 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
         a.qx[i] = fma(hdt, d0, s0);
         a.qy[i] = fma(hdt, d1, s1);
         a.qz[i] = fma(hdt, d2, s2);
-        double v[5];
-        spin_terms<R, Mode != kPlain>(m, s0, s1, s2, e0, e1, e2, sde, v);
-        if (first) {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) acc[c] = v[c];
-            first = false;
+        if constexpr (sizeof(R) == 4) {
+            R v[5];
+            spin_terms_r<R, BM != kPlain>(m, s0, s1, s2, e0, e1, e2, sde, v);
+            ta.add(v);
         } else {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) acc[c] += v[c];
+            double v[5];
+            spin_terms<R, BM != kPlain>(m, s0, s1, s2, e0, e1, e2, sde, v);
+            ta.add(v);
         }
     }
+    ta.out(acc);
 }
 
 template <typename R, int BS, bool Coherent, int Mode = kGeneral>
 __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
-                                               const SmemTables *tab) {
+                                               const StepTabT<R> *tab) {
+    constexpr int BM = base_mode(Mode);
     const SysDesc &sd = a.sys[td.sys];
     // Gaussians of step + 1 for the slots the next predictor will not draw (FP32-mixed):
-    // this puts FP64 transform work next to the corrector's memory traffic.
+    // this puts transform work next to the corrector's memory traffic.
     const R sqrtT_next = tab ? sqrtT_of_step(a, step + 1, sd) : (R)0;
+    const uint32_t key0 = sd.key0, key1 = sd.key1, ctr2 = sd.ctr2;
+    const int64_t off = sd.offset;
     int rot = (threadIdx.x >> 5) % a.slots;  // the predictor's rotated slot index
     for (int k = threadIdx.x; k < td.count; k += BS, rot = rot + 1 == a.slots ? 0 : rot + 1) {
         const int64_t i = td.start + k;
-        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+        const MatDesc<R> &m = mat_at<Mode>(a, i);
         const R s0 = ld<Coherent>(a.px + i), s1 = ld<Coherent>(a.py + i), s2 = ld<Coherent>(a.pz + i);
         R e0, e1, e2;
-        exchange_sum<R, Coherent, Mode>(a, sd, a.px, a.py, a.pz, i, e0, e1, e2);
+        exchange_sum<R, Coherent, BM>(a, sd, a.px, a.py, a.pz, i, e0, e1, e2);
         R H0, H1, H2;
-        det_field<R, Mode != kPlain>(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
+        det_field<R, BM != kPlain>(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         if (a.demag) add_demag(a, i, H0, H1, H2);
         H0 += ld<Coherent>(a.hx + i);
         H1 += ld<Coherent>(a.hy + i);
@@ -394,13 +504,12 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
         a.sy[i] = v1 * inv;
         a.sz[i] = v2 * inv;
         if (rot >= a.pre_slot && sqrtT_next > (R)0) {
-            const Philox4 w =
-                philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)(step + 1), sd.ctr2, 0u, sd.key0, sd.key1);
-            double g0, g1, g2;
-            box_muller3(w, *tab, g0, g1, g2);
-            a.gx[i] = narrow<R>(g0);
-            a.gy[i] = narrow<R>(g1);
-            a.gz[i] = narrow<R>(g2);
+            const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)(step + 1), ctr2, 0u, key0, key1);
+            R g0, g1, g2;
+            thermal_gaussians(a, *tab, w, g0, g1, g2);
+            a.gx[i] = g0;
+            a.gy[i] = g1;
+            a.gz[i] = g2;
         }
     }
 }
@@ -469,7 +578,7 @@ __device__ __forceinline__ void finalize_system(const SysDesc *sys, const int32_
 // Predictor passes over the block's tiles t = blockIdx.x + j gridDim.x, in chunks of
 // kTileChunk tiles whose partials are summed after one barrier.
 template <typename R, int BS, bool Coherent, int Mode = kGeneral>
-__device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step, const SmemTables &tab,
+__device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step, const StepTabT<R> &tab,
                                                int pre_slot, double *red) {
     const int64_t stride = gridDim.x;
     for (int64_t t0 = blockIdx.x; t0 < a.ntiles; t0 += (int64_t)kTileChunk * stride) {
@@ -490,10 +599,16 @@ __device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step,
 // FP64: one resident block per SM is enough for the FP64 pipe, and the minimum-blocks bound
 // lets the compiler keep the transform in registers (without it the FP64 form spills at 64).
 template <typename R, int BS, int Mode = kGeneral>
-__global__ void __launch_bounds__(BS, sizeof(R) == 8 ? 1 : 0) k_predictor(const KArgs<R> a) {
-    __shared__ SmemTables tab;
+#ifndef SS_PRED_WARPS
+#define SS_PRED_WARPS 32
+#endif
+#ifndef SS_CORR_WARPS
+#define SS_CORR_WARPS 32
+#endif
+__global__ void __launch_bounds__(BS, sizeof(R) == 8 ? 1 : SS_PRED_WARPS * 32 / BS) k_predictor(const KArgs<R> a) {
+    __shared__ StepTabT<R> tab;
     __shared__ double red[kTileChunk * (BS / 32) * 8];
-    stage_tables(a, tab);
+    stage_step_tables(a, tab);
     __syncthreads();
     const uint64_t step = *a.step;
     // Gaussians drawn ahead are valid only if the previous corrector ran for this step.
@@ -504,7 +619,7 @@ __global__ void __launch_bounds__(BS, sizeof(R) == 8 ? 1 : 0) k_predictor(const 
 // Blocks [0, nfin) sum the predictor's tile partials into the record ring; the rest run
 // the corrector over the tiles.  The last block to finish advances the step counter.
 template <typename R, int BS, bool DrawAhead, int Mode = kGeneral>
-__global__ void __launch_bounds__(BS) k_corrector(const KArgs<R> a, int nfin) {
+__global__ void __launch_bounds__(BS, sizeof(R) == 8 ? 0 : SS_CORR_WARPS * 32 / BS) k_corrector(const KArgs<R> a, int nfin) {
     __shared__ double red[(BS / 32) * 8];
     const uint64_t step = *a.step;
     if ((int)blockIdx.x < nfin) {
@@ -513,8 +628,8 @@ __global__ void __launch_bounds__(BS) k_corrector(const KArgs<R> a, int nfin) {
             finalize_system<BS, false>(a.sys, a.sys_tiles, a.partials, s, dst, red);
         }
     } else if constexpr (DrawAhead) {
-        __shared__ SmemTables tab;
-        stage_tables(a, tab);
+        __shared__ StepTabT<R> tab;
+        stage_step_tables(a, tab);
         __syncthreads();
         const int64_t nb = gridDim.x - nfin;
         for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb)
@@ -544,7 +659,8 @@ __global__ void __launch_bounds__(BS) k_measure(const KArgs<R> a) {
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDesc td = a.tiles[t];
         const SysDesc &sd = a.sys[td.sys];
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // summed in the order of the step kernels
+        TermAcc<R> ta;  // summed as in the step kernels
+        ta.reset();
         for (int k = threadIdx.x; k < td.count; k += BS) {
             const int64_t i = td.start + k;
             const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
@@ -556,11 +672,18 @@ __global__ void __launch_bounds__(BS) k_measure(const KArgs<R> a) {
                 exchange_sum<R, false>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
             R H0, H1, H2;
             const R sde = det_field(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
-            double v[5];
-            spin_terms(m, s0, s1, s2, e0, e1, e2, sde, v);
-#pragma unroll
-            for (int c = 0; c < 5; ++c) acc[c] += v[c];
+            if constexpr (sizeof(R) == 4) {
+                R v[5];
+                spin_terms_r(m, s0, s1, s2, e0, e1, e2, sde, v);
+                ta.add(v);
+            } else {
+                double v[5];
+                spin_terms(m, s0, s1, s2, e0, e1, e2, sde, v);
+                ta.add(v);
+            }
         }
+        double acc[8];
+        ta.out(acc);
         const double r = block_sum8<BS>(acc, red);
         if (threadIdx.x < kPartComps) a.partials[t * kPartComps + threadIdx.x] = r;
     }
@@ -649,9 +772,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int *
 // half of the next step's Gaussians drawn ahead), barrier.
 template <typename R, int BS, int Mode = kGeneral>
 __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, long long nsteps) {
-    __shared__ SmemTables tab;
+    __shared__ StepTabT<R> tab;
     __shared__ double red[kTileChunk * (BS / 32) * 8];
-    stage_tables(a, tab);
+    stage_step_tables(a, tab);
     __syncthreads();
     const uint64_t step0 = __ldcg(a.step);
     const bool ahead = a.g_step != nullptr;
@@ -685,9 +808,9 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
 // block directly.  The last block to finish advances the step counter.
 template <typename R, int BS, int Mode = kGeneral>
 __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long long nsteps) {
-    __shared__ SmemTables tab;
+    __shared__ StepTabT<R> tab;
     __shared__ double red[(BS / 32) * 8];
-    stage_tables(a, tab);
+    stage_step_tables(a, tab);
     __syncthreads();
     const uint64_t step0 = __ldcg(a.step);
     for (int s = blockIdx.x; s < a.nsys; s += gridDim.x) {

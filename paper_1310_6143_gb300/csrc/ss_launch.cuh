@@ -14,27 +14,37 @@ namespace ss {
         default: return cudaErrorInvalidValue;           \
     }
 
+// The Heun step-kernel variant for these arguments: kRows, kGeneral, kUniform (plain lattice,
+// one material) or kPlain.
+template <typename R>
+int heun_mode(const KArgs<R> &a) {
+    if (a.ex) return kRows;
+    if (a.J_tensor || a.any_cubic) return kGeneral;
+    return a.mat_uniform ? kUniform : kPlain;
+}
+
 template <typename R>
 cudaError_t launch_predictor(const KArgs<R> &a, int block, int grid, cudaStream_t s) {
-    if (a.ex) {
-        SS_BLOCK_SWITCH(block, k_predictor<R, BS, kRows><<<grid, BS, 0, s>>>(a));
-    } else if (a.J_tensor || a.any_cubic) {
-        SS_BLOCK_SWITCH(block, k_predictor<R, BS, kGeneral><<<grid, BS, 0, s>>>(a));
-    } else {
-        SS_BLOCK_SWITCH(block, k_predictor<R, BS, kPlain><<<grid, BS, 0, s>>>(a));
+    switch (heun_mode(a)) {
+        case kRows: SS_BLOCK_SWITCH(block, k_predictor<R, BS, kRows><<<grid, BS, 0, s>>>(a)); break;
+        case kGeneral: SS_BLOCK_SWITCH(block, k_predictor<R, BS, kGeneral><<<grid, BS, 0, s>>>(a)); break;
+        case kUniform: SS_BLOCK_SWITCH(block, k_predictor<R, BS, kUniform><<<grid, BS, 0, s>>>(a)); break;
+        default: SS_BLOCK_SWITCH(block, k_predictor<R, BS, kPlain><<<grid, BS, 0, s>>>(a)); break;
     }
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s) {
-    const int mode = a.ex ? kRows : (a.J_tensor || a.any_cubic) ? kGeneral : kPlain;
+    const int mode = heun_mode(a);
     const bool ahead = a.g_step != nullptr;
 #define SS_CORRECTOR(DA, MODE) SS_BLOCK_SWITCH(block, k_corrector<R, BS, DA, MODE><<<grid + nfin, BS, 0, s>>>(a, nfin))
     if (mode == kRows) {
         if (ahead) { SS_CORRECTOR(true, kRows); } else { SS_CORRECTOR(false, kRows); }
     } else if (mode == kGeneral) {
         if (ahead) { SS_CORRECTOR(true, kGeneral); } else { SS_CORRECTOR(false, kGeneral); }
+    } else if (mode == kUniform) {
+        if (ahead) { SS_CORRECTOR(true, kUniform); } else { SS_CORRECTOR(false, kUniform); }
     } else {
         if (ahead) { SS_CORRECTOR(true, kPlain); } else { SS_CORRECTOR(false, kPlain); }
     }
@@ -55,13 +65,15 @@ cudaError_t launch_init_sphere(const KArgs<R> &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// (the persistent and system-block kernels come as kPlain and kGeneral variants only)
+// (the persistent and system-block kernels come as kPlain, kUniform and kGeneral variants)
 template <typename R>
 int persistent_blocks_per_sm(int block, int mode) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
     if (mode == kPlain) {
         SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, BS, kPlain>, BS, 0));
+    } else if (mode == kUniform) {
+        SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, BS, kUniform>, BS, 0));
     } else {
         SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<R, BS, kGeneral>, BS, 0));
     }
@@ -78,6 +90,8 @@ int step_blocks_per_sm(int block, int mode) {
         SS_OCC(kRows);
     } else if (mode == kGeneral) {
         SS_OCC(kGeneral);
+    } else if (mode == kUniform) {
+        SS_OCC(kUniform);
     } else {
         SS_OCC(kPlain);
     }
@@ -96,6 +110,8 @@ int corrector_blocks_per_sm(int block, bool draw_ahead, int mode) {
         if (draw_ahead) { SS_OCC(true, kRows); } else { SS_OCC(false, kRows); }
     } else if (mode == kGeneral) {
         if (draw_ahead) { SS_OCC(true, kGeneral); } else { SS_OCC(false, kGeneral); }
+    } else if (mode == kUniform) {
+        if (draw_ahead) { SS_OCC(true, kUniform); } else { SS_OCC(false, kUniform); }
     } else {
         if (draw_ahead) { SS_OCC(true, kPlain); } else { SS_OCC(false, kPlain); }
     }
@@ -299,6 +315,9 @@ cudaError_t launch_persistent(const KArgs<R> &a, int block, int grid, int nfin, 
     void *params[] = {(void *)&args, (void *)&nfin, (void *)&nsteps};
     if (a.J_tensor || a.any_cubic) {
         SS_BLOCK_SWITCH(block, return cudaLaunchCooperativeKernel((const void *)k_persistent<R, BS, kGeneral>, dim3(grid),
+                                                                  dim3(BS), params, 0, s));
+    } else if (a.mat_uniform) {
+        SS_BLOCK_SWITCH(block, return cudaLaunchCooperativeKernel((const void *)k_persistent<R, BS, kUniform>, dim3(grid),
                                                                   dim3(BS), params, 0, s));
     } else {
         SS_BLOCK_SWITCH(block, return cudaLaunchCooperativeKernel((const void *)k_persistent<R, BS, kPlain>, dim3(grid),

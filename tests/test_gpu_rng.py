@@ -53,3 +53,38 @@ def test_extreme_uniforms_keep_relative_accuracy(ss):
     small = r_ref < 1e-2
     assert small.any()
     assert (np.abs(r_gpu[small] - r_ref[small]) / r_ref[small]).max() < 1e-13
+
+
+def _radii(seed, sys_id, step, n):
+    """Box-Muller radii sqrt(-2 ln u0), sqrt(-2 ln u2) of each draw, from the oracle's Philox."""
+    w = O.philox_bulk([0, step, sys_id, 0], [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], n).astype(np.float64)
+    r1 = np.sqrt(-2.0 * np.log((w[:, 0] + 0.5) * 2.0 ** -32))
+    r2 = np.sqrt(-2.0 * np.log((w[:, 2] + 0.5) * 2.0 ** -32))
+    return np.stack([r1, r1, r2], axis=1)
+
+
+def test_fp32_transform_is_fp64_transform_rounded(ss):
+    """The FP32-mixed form's Gaussians (double-float evaluation, certified rounding) are the FP64
+    transform's values rounded to nearest float, bit for bit, including the draws whose rounding
+    falls back to the FP64 transform."""
+    for seed, sys_id, step in ((1, 0, 0), (5, 3, 12345), ((7 << 32) | 9, 255, 0xFFFFFFFF), (2, 1, 77)):
+        n = 4_000_000
+        g32 = ss.debug_gaussians(seed, sys_id, step, n, mode=2)
+        g64 = ss.debug_gaussians(seed, sys_id, step, n, mode=0)
+        np.testing.assert_array_equal(g32, g64.astype(np.float32).astype(np.float64))
+        flags = ss.debug_gaussians(seed, sys_id, step, n, mode=4)[:, 0]
+        frac = flags.mean()
+        assert flags.sum() > 0 and frac < 1e-3, frac  # the fallback path runs, and rarely
+
+
+def test_double_float_values_within_certified_bound(ss):
+    """Before rounding, the double-float Gaussians lie within a sixteenth of the bound the
+    rounding check assumes (2^-41 |g| + 2^-43 R) of the oracle's FP64 libm values."""
+    for seed, sys_id, step in ((3, 0, 7), (11, 2, 99)):
+        n = 2_000_000
+        gd = ss.debug_gaussians(seed, sys_id, step, n, mode=3)
+        ref = O.gaussians_bulk(seed, sys_id, step, n)
+        R = _radii(seed, sys_id, step, n)
+        bound = 2.0 ** -41 * np.abs(ref) + 2.0 ** -43 * R
+        ratio = np.abs(gd - ref) / bound
+        assert ratio.max() < 1.0 / 16.0, ratio.max()
