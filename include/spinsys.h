@@ -144,6 +144,8 @@ typedef struct {
                              corrector draws (FP32-mixed form; see spin_system_set_draw_ahead) */
     int32_t exchange_rows;/* 1: a thread per exchange row; 2: a warp per row; 3: a warp per
                              row reading packed bonds (see spin_system_set_exchange_rows)  */
+    int32_t row_patterns; /* row forms the thread-per-row exchange sums read instead of the
+                             CSR (see spin_system_set_row_patterns); 0: the CSR is read    */
 } ss_info;
 
 /* Create one system.  Validates and copies every array (SS_ERR_INVALID_ARG on bad
@@ -303,6 +305,18 @@ ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
  * spin_system_set_exec refuses the persistent and system-block modes (SS_ERR_UNSUPPORTED),
  * and turning it on resets those to SS_EXEC_AUTO.  SS_ERR_INVALID_ARG for another mode. */
 ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode);
+
+/* Neighbour-list storage read by the thread-per-row exchange sums (Eq. HJij) of the Heun
+ * steps, the on-demand measurement and Monte Carlo.  At creation, when the rows take at most
+ * 256 distinct forms -- a form being a row's length (at most 12) and its (column - row,
+ * J_ij/mu_s,i) pairs in CSR order, as on a lattice whose interior rows all look alike and
+ * whose boundary rows come in a few kinds (the film: 27 forms) -- each spin stores a one-byte
+ * form index and the forms are kept in small tables; the sums then read one byte per spin
+ * instead of the row's offsets and columns, and add the same terms in the same order, so the
+ * results are identical.  on = 1 (the default) uses the forms when they were built, 0 reads
+ * the CSR; ss_info.row_patterns gives the number of forms in use (0: CSR).  Tensor bonds
+ * always read the CSR.  SS_ERR_INVALID_ARG for another value. */
+ss_status spin_system_set_row_patterns(ss_system *h, int32_t on);
 
 /* FP32-mixed form: the corrector of step n draws the thermal Gaussians of step n+1 for
  * `eighths`/8 of each tile's spins (rounded down to whole blocks), so that their FP64

@@ -109,6 +109,12 @@ struct ss_system {
     double2 *tab = nullptr;             // Box-Muller tables (build_bm_tables), then the
                                         // double-float tables (build_ff_tables)
     int32_t max_row = 0;                // longest CSR row
+    // Row patterns (the CSR stored as one byte per row, see build_patterns)
+    uint8_t *pat = nullptr;
+    int32_t *pat_len = nullptr, *pat_off = nullptr;
+    void *pat_J = nullptr;
+    int32_t npat = 0;                   // 0: no patterns (more than kMaxPatterns, rows too long)
+    bool use_pat = true;                // spin_system_set_row_patterns
     alignas(16) unsigned char mat0[sizeof(MatDesc<double>)] = {};  // MatDesc<R> of material 0
 
     std::vector<SysDesc> hsys;
@@ -366,6 +372,72 @@ void build_tables(std::vector<double2> &t) {
     build_ff_tables(reinterpret_cast<float4 *>(t.data() + kTabCount));
 }
 
+// Row patterns: when the rows take at most kMaxPatterns distinct forms -- a form being the
+// row's length and its (column - row, J_ij / mu_s,i) pairs in CSR order, as on a lattice whose
+// interior rows all look alike and whose boundary rows come in a few kinds -- each spin stores
+// the one-byte index of its row's form and the forms are kept in small tables, so a pass reads
+// one byte per spin instead of the row's offsets and columns (27.5 bytes on the film).  The
+// exchange sum is then the CSR sum term for term.  Rows longer than kPatRow, or more forms,
+// keep the CSR (npat = 0).
+template <typename R>
+ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std::vector<int32_t> &col,
+                         const std::vector<R> &J) {
+    h->npat = 0;
+    if (h->nnz <= 0 || h->max_row > kPatRow || h->J_tensor) return SS_OK;
+    const int64_t n = h->n;
+    std::vector<uint8_t> pat((size_t)n);
+    std::vector<int32_t> plen, poff;
+    std::vector<R> pJ;
+    std::unordered_map<uint64_t, int32_t> id_of;  // row hash -> pattern (contents verified)
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t b = rp[i], len = rp[i + 1] - rp[i];
+        uint64_t hsh = 0x9E3779B97F4A7C15ull ^ (uint64_t)len;
+        for (int32_t q = 0; q < len; ++q) {
+            uint64_t jb = 0;
+            std::memcpy(&jb, &J[(size_t)(b + q)], sizeof(R));
+            const uint64_t v = (uint64_t)(uint32_t)(col[(size_t)(b + q)] - (int32_t)i) * 0xBF58476D1CE4E5B9ull ^ jb;
+            hsh = (hsh ^ v) * 0x94D049BB133111EBull;
+            hsh ^= hsh >> 31;
+        }
+        auto it = id_of.find(hsh);
+        int32_t id;
+        if (it == id_of.end()) {
+            if ((int32_t)plen.size() == kMaxPatterns) return SS_OK;  // too many forms: keep the CSR
+            id = (int32_t)plen.size();
+            id_of.emplace(hsh, id);
+            plen.push_back(len);
+            poff.resize(poff.size() + kPatRow, 0);
+            pJ.resize(pJ.size() + kPatRow, (R)0);
+            for (int32_t q = 0; q < len; ++q) {
+                poff[(size_t)id * kPatRow + q] = col[(size_t)(b + q)] - (int32_t)i;
+                pJ[(size_t)id * kPatRow + q] = J[(size_t)(b + q)];
+            }
+        } else {
+            id = it->second;
+            bool same = plen[(size_t)id] == len;
+            for (int32_t q = 0; q < len && same; ++q)
+                same = poff[(size_t)id * kPatRow + q] == col[(size_t)(b + q)] - (int32_t)i &&
+                       std::memcmp(&pJ[(size_t)id * kPatRow + q], &J[(size_t)(b + q)], sizeof(R)) == 0;
+            if (!same) return SS_OK;  // a hash collision: keep the CSR
+        }
+        pat[(size_t)i] = (uint8_t)id;
+    }
+    const int32_t np = (int32_t)plen.size();
+    SS_CUDA(h, dalloc(h, (void **)&h->pat, pat.size()));
+    SS_CUDA(h, dalloc(h, (void **)&h->pat_len, (size_t)np * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, (void **)&h->pat_off, poff.size() * sizeof(int32_t)));
+    SS_CUDA(h, dalloc(h, &h->pat_J, pJ.size() * sizeof(R)));
+    SS_CUDA(h, cudaMemcpyAsync(h->pat, pat.data(), pat.size(), cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->pat_len, plen.data(), plen.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->pat_off, poff.data(), poff.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->pat_J, pJ.data(), pJ.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
+    h->npat = np;
+    return SS_OK;
+}
+
 template <typename R>
 KArgs<R> make_args(const ss_system *h) {
     KArgs<R> a{};
@@ -376,6 +448,11 @@ KArgs<R> make_args(const ss_system *h) {
     a.J_value = (R)h->J_value;
     a.J_uniform = h->J_uniform ? 1 : 0;
     a.short_rows = h->max_row <= kShortRow ? 1 : 0;
+    const bool pat = h->npat > 0 && h->use_pat;
+    a.pat = pat ? h->pat : nullptr;
+    a.pat_len = pat ? h->pat_len : nullptr;
+    a.pat_off = pat ? h->pat_off : nullptr;
+    a.pat_J = pat ? static_cast<const R *>(h->pat_J) : nullptr;
     a.mat_uniform = h->nmat == 1 ? 1 : 0;
     std::memcpy(&a.mat0, h->mat0, sizeof(MatDesc<R>));
     a.Jt = static_cast<const R *>(h->Jt);
@@ -907,6 +984,10 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     SS_CUDA(h, cudaMemcpyAsync(h->mat, mat.data(), mat.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->mats, mats.data(), mats.size() * sizeof(MatDesc<R>), cudaMemcpyHostToDevice,
                                h->stream));
+    {
+        const ss_status ps = build_patterns<R>(h, rp, col, J);
+        if (ps != SS_OK) return ps;
+    }
     for (int b = 0; b < 12; ++b) SS_CUDA(h, dalloc(h, &h->state[b], (size_t)n * rs));
     if (h->precision == SS_FP32_MIXED)
         for (int b = 0; b < 3; ++b) SS_CUDA(h, dalloc(h, &h->ahead[b], (size_t)n * rs));
@@ -2088,6 +2169,16 @@ ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode) {
     return set_rows(h, mode);
 }
 
+ss_status spin_system_set_row_patterns(ss_system *h, int32_t on) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (on != 0 && on != 1) return fail(h, SS_ERR_INVALID_ARG, "on must be 0 or 1");
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->use_pat = on != 0;
+    drop_graph(h);  // captured launches hold the old arguments
+    return SS_OK;
+}
+
 ss_status spin_system_set_draw_ahead(ss_system *h, int32_t eighths) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
@@ -2113,6 +2204,7 @@ ss_status spin_system_info(ss_system *h, ss_info *o) {
     o->device_bytes = (int64_t)h->device_bytes;
     o->draw_ahead = h->ahead_q;
     o->exchange_rows = h->rows ? (h->sell ? 3 : 2) : 1;
+    o->row_patterns = h->use_pat ? h->npat : 0;
     return SS_OK;
 }
 

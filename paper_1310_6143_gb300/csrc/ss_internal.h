@@ -25,6 +25,8 @@ constexpr int kTabCount = kLogTab + kLn2Tab + kTrigTab + kLogLo;
 // the kTabCount double2 slots of the same buffer: log | trig | 2 n ln 2 (two per slot).
 constexpr int kFFTabFloat4 = kLogTab + kTrigTab + (kLn2Tab + 1) / 2;
 constexpr int kShortRow = 6;   // rows of at most this many bonds take the unrolled exchange sum
+constexpr int kPatRow = 12;    // longest row a row pattern holds
+constexpr int kMaxPatterns = 256;  // row patterns addressable by the one-byte pattern index
 constexpr int kRecComps = 8;   // record: sum mu S (3), sum mu, E_exc, E_ani, E_app, E_total
 constexpr int kPartComps = 8;  // tile partials: sum mu S (3), sum -mu S.h/2, E_ani, 0, 0, 0
 
@@ -84,6 +86,10 @@ struct KArgs {
     R J_value;                // the common value when every entry of J is the same
     int J_uniform;            // 1: J is not read, every bond has J_value
     int short_rows;           // 1: no row has more than kShortRow bonds
+    const uint8_t *pat;       // [n] row pattern of each spin, or nullptr (the CSR is read)
+    const int32_t *pat_len;   // [npat] bonds of each pattern
+    const int32_t *pat_off;   // [npat][kPatRow] column - row of each bond, in CSR order
+    const R *pat_J;           // [npat][kPatRow] J_ij / mu_s,i of each bond (nullptr if J_uniform)
     MatDesc<R> mat0;          // the only material when mat_uniform is set
     int mat_uniform;          // 1: every spin has material 0 (mat is not read)
     const R *Jt;              // [9 ndict] distinct exchange tensors / mu_s,i, row by row

@@ -142,9 +142,39 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
         e2 = ld<Coherent>(a.ez + i);
         return;
     }
+    R x = sys_H(sd, 0, R()), y = sys_H(sd, 1, R()), z = sys_H(sd, 2, R());
+    if (a.pat && !(Mode == kGeneral && a.J_tensor)) {
+        // Row patterns: the row's bonds are the pattern's (column - row, J) pairs in CSR order,
+        // so the sum is the CSR sum term for term; one byte per row is read instead of the
+        // row's offsets and columns.
+        const int p = __ldg(a.pat + i);
+        const int len = __ldg(a.pat_len + p);
+        const int32_t *po = a.pat_off + p * kPatRow;
+        const R *pj = a.pat_J + p * kPatRow;
+#pragma unroll
+        for (int q = 0; q < kShortRow; ++q) {
+            if (q < len) {
+                const int32_t j = chk(i + __ldg(po + q), a.n, a.err);
+                const R Jk = a.J_uniform ? a.J_value : __ldg(pj + q);
+                x = fma(Jk, ld<Coherent>(X + j), x);
+                y = fma(Jk, ld<Coherent>(Y + j), y);
+                z = fma(Jk, ld<Coherent>(Z + j), z);
+            }
+        }
+        for (int q = kShortRow; q < len; ++q) {
+            const int32_t j = chk(i + __ldg(po + q), a.n, a.err);
+            const R Jk = a.J_uniform ? a.J_value : __ldg(pj + q);
+            x = fma(Jk, ld<Coherent>(X + j), x);
+            y = fma(Jk, ld<Coherent>(Y + j), y);
+            z = fma(Jk, ld<Coherent>(Z + j), z);
+        }
+        e0 = x;
+        e1 = y;
+        e2 = z;
+        return;
+    }
     const int32_t b = __ldg(a.row_ptr + i);
     const int32_t e = __ldg(a.row_ptr + i + 1);
-    R x = sys_H(sd, 0, R()), y = sys_H(sd, 1, R()), z = sys_H(sd, 2, R());
     if (Mode == kGeneral && a.J_tensor) {  // Eq. HJijSMS: the tensor of bond k applied to S_j
         for (int32_t k = b; k < e; ++k) {
             const int32_t j = chk(__ldg(a.col + k), a.n, a.err);

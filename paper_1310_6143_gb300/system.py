@@ -164,6 +164,10 @@ class SpinSystem:
         """'auto', 'thread' (a thread per exchange row) or 'warp' (a warp per row)."""
         self._check(self._lib.spin_system_set_exchange_rows(self._h, {"auto": 0, "thread": 1, "warp": 2}[mode]))
 
+    def set_row_patterns(self, on: bool):
+        """Read the one-byte row forms (True, the default when they were built) or the CSR."""
+        self._check(self._lib.spin_system_set_row_patterns(self._h, 1 if on else 0))
+
     def set_draw_ahead(self, eighths: int):
         self._check(self._lib.spin_system_set_draw_ahead(self._h, int(eighths)))
 
