@@ -146,6 +146,8 @@ typedef struct {
                              row reading packed bonds (see spin_system_set_exchange_rows)  */
     int32_t row_patterns; /* row forms the thread-per-row exchange sums read instead of the
                              CSR (see spin_system_set_row_patterns); 0: the CSR is read    */
+    int32_t gaussian_pass;/* 1: graph and plain-launch steps run the Gaussian pass before
+                             the Heun passes (see spin_system_set_gaussian_pass)          */
 } ss_info;
 
 /* Create one system.  Validates and copies every array (SS_ERR_INVALID_ARG on bad
@@ -318,6 +320,18 @@ ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode);
  * always read the CSR.  SS_ERR_INVALID_ARG for another value. */
 ss_status spin_system_set_row_patterns(ss_system *h, int32_t on);
 
+/* FP32-mixed form, thread-per-row exchange, graph and plain-launch execution: on = 1 (the
+ * default) runs each step as three launches -- a pass that writes the step's thermal
+ * Gaussians (the transform of ss_debug_gaussians mode 2) for every spin at a non-zero
+ * temperature, then the predictor and the corrector, both forming the thermal field
+ * sigma_i sqrt(T_n) g from them (so the field is the same in both passes, and the same as
+ * with on = 0) -- instead of drawing the Gaussians inside the Heun passes (on = 0, which the
+ * persistent and system-block modes always do).  The transform is pure arithmetic and the
+ * Heun passes are memory-bound: kept apart, the passes need fewer registers and keep more
+ * warps in flight.  Results do not depend on the setting.  SS_ERR_INVALID_ARG for another
+ * value. */
+ss_status spin_system_set_gaussian_pass(ss_system *h, int32_t on);
+
 /* FP32-mixed form: the corrector of step n draws the thermal Gaussians of step n+1 for
  * `eighths`/8 of each tile's spins (rounded down to whole blocks), so that their FP64
  * transform overlaps the corrector's memory traffic; the predictor draws the rest.
@@ -344,6 +358,11 @@ ss_status spin_system_info(ss_system *h, ss_info *out);
  * a warp per exchange row each includes the exchange pass before it.  The steps are real
  * steps: the state and the step counter advance. */
 ss_status spin_system_time_kernels(ss_system *h, int32_t nsteps, double out_ms[3]);
+
+/* As spin_system_time_kernels, with the Gaussian pass of the split FP32-mixed step timed on
+ * its own: out_ms receives the mean duration of (Gaussian pass, predictor, corrector) launches
+ * and the mean wall time of one step (the first is 0 without a Gaussian pass). */
+ss_status spin_system_time_passes(ss_system *h, int32_t nsteps, double out_ms[4]);
 
 /* Time `launches` (>= 1) passes of the warp-per-row exchange sum over the current spins
  * (spin_system_set_exchange_rows), CUDA events on the handle's stream; *out_ms receives the

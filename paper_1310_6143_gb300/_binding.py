@@ -28,7 +28,7 @@ EXPORTS = (
     "get_spins_device", "get_magnetisation", "get_energy", "get_record", "set_spins", "set_step", "get_step",
     "spin_system_set_exec", "spin_system_set_launch", "spin_system_autotune", "spin_system_info",
     "spin_system_set_barrier_test", "spin_system_sync", "spin_system_time_kernels", "ss_debug_philox", "ss_debug_gaussians",
-    "llg_heun_step_noalloc", "spin_system_set_draw_ahead", "spin_system_set_row_patterns", "ss_debug_fp64_rate", "mc_step", "get_mc_stats", "set_demag", "llg_midpoint_step",
+    "llg_heun_step_noalloc", "spin_system_set_draw_ahead", "spin_system_set_row_patterns", "spin_system_set_gaussian_pass", "spin_system_time_passes", "ss_debug_fp64_rate", "mc_step", "get_mc_stats", "set_demag", "llg_midpoint_step",
     "spin_system_set_exchange_rows", "spin_system_time_rows", "llg_semi_implicit_step",
     "ss_debug_fail_allocations", "ss_debug_live_bytes",
     "get_demag_field",
@@ -85,6 +85,7 @@ class SSInfo(ctypes.Structure):
         ("draw_ahead", ctypes.c_int32),
         ("exchange_rows", ctypes.c_int32),
         ("row_patterns", ctypes.c_int32),
+        ("gaussian_pass", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -135,6 +136,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "spin_system_set_launch": [P, I32, I32],
         "spin_system_set_draw_ahead": [P, I32],
         "spin_system_set_row_patterns": [P, I32],
+        "spin_system_set_gaussian_pass": [P, I32],
+        "spin_system_time_passes": [P, I32, P],
         "spin_system_set_exchange_rows": [P, I32],
         "spin_system_time_rows": [P, I32, P],
         "spin_system_autotune": [P, I32, P],

@@ -111,10 +111,12 @@ struct ss_system {
     int32_t max_row = 0;                // longest CSR row
     // Row patterns (the CSR stored as one byte per row, see build_patterns)
     uint8_t *pat = nullptr;
-    int32_t *pat_len = nullptr, *pat_off = nullptr;
+    int32_t *pat_off = nullptr;
     void *pat_J = nullptr;
     int32_t npat = 0;                   // 0: no patterns (more than kMaxPatterns, rows too long)
+    int32_t pat_w = 8;                  // slots of a pattern row (8 or 16, see KArgs)
     bool use_pat = true;                // spin_system_set_row_patterns
+    bool gauss_pass = true;             // spin_system_set_gaussian_pass
     alignas(16) unsigned char mat0[sizeof(MatDesc<double>)] = {};  // MatDesc<R> of material 0
 
     std::vector<SysDesc> hsys;
@@ -384,9 +386,11 @@ ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std
                          const std::vector<R> &J) {
     h->npat = 0;
     if (h->nnz <= 0 || h->max_row > kPatRow || h->J_tensor) return SS_OK;
+    const int NS = h->max_row <= kShortRow ? kShortRow : kPatRow;  // offset slots, then the length
+    const int W = NS == kShortRow ? 8 : 16;
     const int64_t n = h->n;
     std::vector<uint8_t> pat((size_t)n);
-    std::vector<int32_t> plen, poff;
+    std::vector<int32_t> poff;
     std::vector<R> pJ;
     std::unordered_map<uint64_t, int32_t> id_of;  // row hash -> pattern (contents verified)
     for (int64_t i = 0; i < n; ++i) {
@@ -402,39 +406,36 @@ ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std
         auto it = id_of.find(hsh);
         int32_t id;
         if (it == id_of.end()) {
-            if ((int32_t)plen.size() == kMaxPatterns) return SS_OK;  // too many forms: keep the CSR
-            id = (int32_t)plen.size();
+            if ((int32_t)(poff.size() / W) == kMaxPatterns) return SS_OK;  // too many forms: keep the CSR
+            id = (int32_t)(poff.size() / W);
             id_of.emplace(hsh, id);
-            plen.push_back(len);
-            poff.resize(poff.size() + kPatRow, 0);
-            pJ.resize(pJ.size() + kPatRow, (R)0);
+            poff.resize(poff.size() + W, 0);
+            pJ.resize(pJ.size() + W, (R)0);
             for (int32_t q = 0; q < len; ++q) {
-                poff[(size_t)id * kPatRow + q] = col[(size_t)(b + q)] - (int32_t)i;
-                pJ[(size_t)id * kPatRow + q] = J[(size_t)(b + q)];
+                poff[(size_t)id * W + q] = col[(size_t)(b + q)] - (int32_t)i;
+                pJ[(size_t)id * W + q] = J[(size_t)(b + q)];
             }
+            poff[(size_t)id * W + NS] = len;
         } else {
             id = it->second;
-            bool same = plen[(size_t)id] == len;
+            bool same = poff[(size_t)id * W + NS] == len;
             for (int32_t q = 0; q < len && same; ++q)
-                same = poff[(size_t)id * kPatRow + q] == col[(size_t)(b + q)] - (int32_t)i &&
-                       std::memcmp(&pJ[(size_t)id * kPatRow + q], &J[(size_t)(b + q)], sizeof(R)) == 0;
+                same = poff[(size_t)id * W + q] == col[(size_t)(b + q)] - (int32_t)i &&
+                       std::memcmp(&pJ[(size_t)id * W + q], &J[(size_t)(b + q)], sizeof(R)) == 0;
             if (!same) return SS_OK;  // a hash collision: keep the CSR
         }
         pat[(size_t)i] = (uint8_t)id;
     }
-    const int32_t np = (int32_t)plen.size();
     SS_CUDA(h, dalloc(h, (void **)&h->pat, pat.size()));
-    SS_CUDA(h, dalloc(h, (void **)&h->pat_len, (size_t)np * sizeof(int32_t)));
     SS_CUDA(h, dalloc(h, (void **)&h->pat_off, poff.size() * sizeof(int32_t)));
     SS_CUDA(h, dalloc(h, &h->pat_J, pJ.size() * sizeof(R)));
     SS_CUDA(h, cudaMemcpyAsync(h->pat, pat.data(), pat.size(), cudaMemcpyHostToDevice, h->stream));
-    SS_CUDA(h, cudaMemcpyAsync(h->pat_len, plen.data(), plen.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                               h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->pat_off, poff.data(), poff.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                                h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->pat_J, pJ.data(), pJ.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
     SS_CUDA(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
-    h->npat = np;
+    h->npat = (int32_t)(poff.size() / W);
+    h->pat_w = W;
     return SS_OK;
 }
 
@@ -450,9 +451,9 @@ KArgs<R> make_args(const ss_system *h) {
     a.short_rows = h->max_row <= kShortRow ? 1 : 0;
     const bool pat = h->npat > 0 && h->use_pat;
     a.pat = pat ? h->pat : nullptr;
-    a.pat_len = pat ? h->pat_len : nullptr;
     a.pat_off = pat ? h->pat_off : nullptr;
     a.pat_J = pat ? static_cast<const R *>(h->pat_J) : nullptr;
+    a.pat_w = h->pat_w;
     a.mat_uniform = h->nmat == 1 ? 1 : 0;
     std::memcpy(&a.mat0, h->mat0, sizeof(MatDesc<R>));
     a.Jt = static_cast<const R *>(h->Jt);
@@ -575,6 +576,18 @@ int corrector_grid(const ss_system *h) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(h->ntiles, g));
 }
 
+// The split FP32-mixed step (a Gaussian pass before the Heun passes) is used by the graph and
+// plain-launch modes of FP32-mixed handles that sum a thread per exchange row.
+bool split_step(const ss_system *h) { return h->gauss_pass && h->precision == SS_FP32_MIXED && !h->rows; }
+
+// One wave of resident blocks of the split step's kernel `which` (0 Gaussian pass, 1 predictor,
+// 2 corrector; the corrector's finalisation blocks come on top).
+int split_grid(const ss_system *h, int which) {
+    const int per_sm = split_blocks_per_sm<float>(h->block, step_mode(h), which);
+    const int64_t g = (int64_t)h->sm_count * std::max(per_sm, 1);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(h->ntiles, g));
+}
+
 int persistent_grid(const ss_system *h) {
     const int mode = own_rows_mode(h) == 0 && h->nmat == 1 ? 3 : own_rows_mode(h);
     const int per_sm = h->precision == SS_FP32_MIXED ? persistent_blocks_per_sm<float>(h->block, mode)
@@ -587,6 +600,16 @@ template <typename R>
 cudaError_t enqueue_steps_kernels(ss_system *h, int64_t n) {
     KArgs<R> a = make_args<R>(h);
     use_rows(h, a);
+    if (split_step(h)) {
+        const int gg = split_grid(h, 0), gp = split_grid(h, 1), gc = split_grid(h, 2);
+        for (int64_t k = 0; k < n; ++k) {
+            cudaError_t e = launch_gauss<R>(a, h->block, gg, h->stream);
+            if (e == cudaSuccess) e = launch_predictor_split<R>(a, h->block, gp, h->stream);
+            if (e == cudaSuccess) e = launch_corrector_split<R>(a, h->block, gc, h->nfin, h->stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const int gp = step_grid(h), gc = corrector_grid(h), gr = h->rows ? rows_grid(h) : 0;
     for (int64_t k = 0; k < n; ++k) {
         cudaError_t e = h->rows ? launch_rows_field<R>(a, a.sx, a.sy, a.sz, gr, h->stream) : cudaSuccess;
@@ -1158,9 +1181,10 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         return cleanup(cuda_fail(h, e, "cudaMalloc"));
     st = h->precision == SS_FP32_MIXED ? upload_system<float>(h, hs) : upload_system<double>(h, hs);
     if (st != SS_OK) return cleanup(st);
-    // Launch shape: 512-thread blocks for large systems; spins per thread (a power of two,
-    // at most 8) chosen so that there are about eight tiles per resident block.
-    h->block = n >= (int64_t(1) << 22) ? 512 : 256;
+    // Launch shape: 512-thread blocks for large FP64 systems, else 256 (the FP32-mixed split
+    // step's lean passes keep more warps in flight with 256-thread blocks); spins per thread (a
+    // power of two, at most 8) chosen so that there are about eight tiles per resident block.
+    h->block = n >= (int64_t(1) << 22) && h->precision == SS_FP64 ? 512 : 256;
     {
         int64_t spt = n / ((int64_t)std::max(h->sm_count, 1) * 8 * h->block);
         int slots = 1;
@@ -1205,27 +1229,40 @@ ss_status current_record(ss_system *h, int32_t sys, double rec[kRecComps]) {
 }
 
 template <typename R>
-ss_status time_kernels_impl(ss_system *h, int32_t nsteps, double out_ms[3]) {
+ss_status time_kernels_impl(ss_system *h, int32_t nsteps, double out_ms[4]) {
     KArgs<R> a = make_args<R>(h);
     use_rows(h, a);
-    const int gp = step_grid(h), gc = corrector_grid(h), gr = h->rows ? rows_grid(h) : 0;
-    std::vector<cudaEvent_t> ev(2 * (size_t)nsteps + 1);
+    const bool split = split_step(h);
+    const int gp = split ? split_grid(h, 1) : step_grid(h), gc = split ? split_grid(h, 2) : corrector_grid(h);
+    const int gg = split ? split_grid(h, 0) : 0, gr = h->rows ? rows_grid(h) : 0;
+    // per step: [Gaussian pass] ev[3k+1] predictor ev[3k+2] corrector ev[3k+3]
+    std::vector<cudaEvent_t> ev(3 * (size_t)nsteps + 1);
     for (auto &e : ev) SS_CUDA(h, cudaEventCreate(&e));
     SS_CUDA(h, cudaEventRecord(ev[0], h->stream));
     for (int32_t k = 0; k < nsteps; ++k) {
+        if (split) SS_CUDA(h, launch_gauss<R>(a, h->block, gg, h->stream));
+        SS_CUDA(h, cudaEventRecord(ev[3 * k + 1], h->stream));
         if (h->rows) SS_CUDA(h, launch_rows_field<R>(a, a.sx, a.sy, a.sz, gr, h->stream));
-        SS_CUDA(h, launch_predictor<R>(a, h->block, gp, h->stream));
-        SS_CUDA(h, cudaEventRecord(ev[2 * k + 1], h->stream));
+        if (split)
+            SS_CUDA(h, launch_predictor_split<R>(a, h->block, gp, h->stream));
+        else
+            SS_CUDA(h, launch_predictor<R>(a, h->block, gp, h->stream));
+        SS_CUDA(h, cudaEventRecord(ev[3 * k + 2], h->stream));
         if (h->rows) SS_CUDA(h, launch_rows_field<R>(a, a.px, a.py, a.pz, gr, h->stream));
-        SS_CUDA(h, launch_corrector<R>(a, h->block, gc, h->nfin, h->stream));
-        SS_CUDA(h, cudaEventRecord(ev[2 * k + 2], h->stream));
+        if (split)
+            SS_CUDA(h, launch_corrector_split<R>(a, h->block, gc, h->nfin, h->stream));
+        else
+            SS_CUDA(h, launch_corrector<R>(a, h->block, gc, h->nfin, h->stream));
+        SS_CUDA(h, cudaEventRecord(ev[3 * k + 3], h->stream));
     }
     SS_CUDA(h, cudaEventSynchronize(ev.back()));
-    double tp = 0.0, tc = 0.0;
+    double tg = 0.0, tp = 0.0, tc = 0.0;
     for (int32_t k = 0; k < nsteps; ++k) {
-        float a1 = 0.f, a2 = 0.f;
-        cudaEventElapsedTime(&a1, ev[2 * k], ev[2 * k + 1]);
-        cudaEventElapsedTime(&a2, ev[2 * k + 1], ev[2 * k + 2]);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        cudaEventElapsedTime(&a0, ev[3 * k], ev[3 * k + 1]);
+        cudaEventElapsedTime(&a1, ev[3 * k + 1], ev[3 * k + 2]);
+        cudaEventElapsedTime(&a2, ev[3 * k + 2], ev[3 * k + 3]);
+        tg += a0;
         tp += a1;
         tc += a2;
     }
@@ -1233,9 +1270,10 @@ ss_status time_kernels_impl(ss_system *h, int32_t nsteps, double out_ms[3]) {
     cudaEventElapsedTime(&all, ev[0], ev.back());
     for (auto &e : ev) cudaEventDestroy(e);
     h->step += nsteps;
-    out_ms[0] = tp / nsteps;
-    out_ms[1] = tc / nsteps;
-    out_ms[2] = all / nsteps;
+    out_ms[0] = tg / nsteps;
+    out_ms[1] = tp / nsteps;
+    out_ms[2] = tc / nsteps;
+    out_ms[3] = all / nsteps;
     return check_device_flags(h);
 }
 
@@ -2169,6 +2207,17 @@ ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode) {
     return set_rows(h, mode);
 }
 
+ss_status spin_system_set_gaussian_pass(ss_system *h, int32_t on) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (on != 0 && on != 1) return fail(h, SS_ERR_INVALID_ARG, "on must be 0 or 1");
+    SS_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->gauss_pass = on != 0;
+    drop_graph(h);  // captured launches hold the other step's kernels
+    SS_CUDA(h, invalidate_ahead(h));
+    return SS_OK;
+}
+
 ss_status spin_system_set_row_patterns(ss_system *h, int32_t on) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
@@ -2205,10 +2254,23 @@ ss_status spin_system_info(ss_system *h, ss_info *o) {
     o->draw_ahead = h->ahead_q;
     o->exchange_rows = h->rows ? (h->sell ? 3 : 2) : 1;
     o->row_patterns = h->use_pat ? h->npat : 0;
+    o->gaussian_pass = split_step(h) ? 1 : 0;
     return SS_OK;
 }
 
 ss_status spin_system_time_kernels(ss_system *h, int32_t nsteps, double out_ms[3]) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (nsteps < 1 || !out_ms) return fail(h, SS_ERR_INVALID_ARG, "nsteps >= 1 and out_ms needed");
+    double t[4];
+    st = h->precision == SS_FP32_MIXED ? time_kernels_impl<float>(h, nsteps, t) : time_kernels_impl<double>(h, nsteps, t);
+    out_ms[0] = t[0] + t[1];  // the Gaussian pass (split step) counted with the predictor
+    out_ms[1] = t[2];
+    out_ms[2] = t[3];
+    return st;
+}
+
+ss_status spin_system_time_passes(ss_system *h, int32_t nsteps, double out_ms[4]) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
     if (nsteps < 1 || !out_ms) return fail(h, SS_ERR_INVALID_ARG, "nsteps >= 1 and out_ms needed");

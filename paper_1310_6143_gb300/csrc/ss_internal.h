@@ -87,9 +87,11 @@ struct KArgs {
     int J_uniform;            // 1: J is not read, every bond has J_value
     int short_rows;           // 1: no row has more than kShortRow bonds
     const uint8_t *pat;       // [n] row pattern of each spin, or nullptr (the CSR is read)
-    const int32_t *pat_len;   // [npat] bonds of each pattern
-    const int32_t *pat_off;   // [npat][kPatRow] column - row of each bond, in CSR order
-    const R *pat_J;           // [npat][kPatRow] J_ij / mu_s,i of each bond (nullptr if J_uniform)
+    const int32_t *pat_off;   // [npat][pat_w] column - row of each bond in CSR order, 0 past the
+                              // row's end, then the row length at slot pat_w - 2 (short) or
+                              // pat_w - 4 (long); 32- or 64-byte aligned rows
+    const R *pat_J;           // [npat][pat_w] J_ij / mu_s,i of each bond, 0 past the row's end
+    int pat_w;                // 8: rows of at most kShortRow bonds; 16: at most kPatRow
     MatDesc<R> mat0;          // the only material when mat_uniform is set
     int mat_uniform;          // 1: every spin has material 0 (mat is not read)
     const R *Jt;              // [9 ndict] distinct exchange tensors / mu_s,i, row by row
@@ -189,6 +191,14 @@ void set_global_error(const char *msg);
 template <typename R> cudaError_t launch_predictor(const KArgs<R> &a, int block, int grid, cudaStream_t s);
 template <typename R> cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s);
 template <typename R> cudaError_t launch_measure(const KArgs<R> &a, int block, int grid, cudaStream_t s);
+// The split FP32-mixed step: the Gaussian pass, then the Heun passes reading it (FP32 only).
+template <typename R> cudaError_t launch_gauss(const KArgs<R> &a, int block, int grid, cudaStream_t s);
+template <typename R> cudaError_t launch_predictor_split(const KArgs<R> &a, int block, int grid, cudaStream_t s);
+template <typename R>
+cudaError_t launch_corrector_split(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s);
+// Resident blocks per SM of the split step's kernels (which: 0 Gaussian pass, 1 predictor,
+// 2 corrector; mode: the kernel variant).
+template <typename R> int split_blocks_per_sm(int block, int mode, int which);
 template <typename R> cudaError_t launch_init_sphere(const KArgs<R> &a, cudaStream_t s);
 template <typename R> cudaError_t launch_persistent(const KArgs<R> &a, int block, int grid, int nfin,
                                                     long long nsteps, cudaStream_t s);

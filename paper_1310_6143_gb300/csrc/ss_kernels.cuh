@@ -65,6 +65,11 @@ __device__ __forceinline__ double rsqrt_r<double>(double x) {
     return rsqrt_pos(x);
 }
 
+// a b rounded, never fused into a following add: the thermal field sigma g is formed this way
+// wherever it is used, so that the predictor's and the corrector's fields are the same value.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // True when the reciprocal length of a renormalised spin is NaN or infinite.
 __device__ __forceinline__ bool bad_inv(float v) { return !(v < 3.0e38f); }
 __device__ __forceinline__ bool bad_inv(double v) { return ((__double2hiint(v) >> 20) & 0x7FF) == 0x7FF; }
@@ -134,40 +139,71 @@ __device__ __forceinline__ int32_t chk(int64_t j, int64_t n, unsigned int *err) 
 }
 
 template <typename R, bool Coherent, int Mode = kGeneral>
+__device__ __forceinline__ void exchange_sum_h(const KArgs<R> &a, R hx, R hy, R hz, const R *X, const R *Y,
+                                               const R *Z, int64_t i, R &e0, R &e1, R &e2);
+
+// The exchange sum of a row stored as a row pattern (NS slots: kShortRow or kPatRow): the
+// pattern's offsets and length come as vector loads, every slot is summed, and the slots past
+// the row's end carry the spin's own index and J = 0, adding exact zeros after the row's CSR
+// terms (so the sum is the CSR sum).
+template <typename R, bool Coherent, int NS>
+__device__ __forceinline__ void pattern_sum(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int64_t i, R &x,
+                                            R &y, R &z) {
+    constexpr int W = NS == kShortRow ? 8 : 16;
+    const int p = __ldg(a.pat + i);
+    int32_t off[W];
+    const int4 *row = reinterpret_cast<const int4 *>(a.pat_off) + (int64_t)p * (W / 4);
+#pragma unroll
+    for (int v = 0; v < W / 4; ++v) {
+        const int4 t = __ldg(row + v);
+        off[4 * v] = t.x;
+        off[4 * v + 1] = t.y;
+        off[4 * v + 2] = t.z;
+        off[4 * v + 3] = t.w;
+    }
+    const int len = off[NS];
+    R Jr[NS];
+    if (a.J_uniform) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) Jr[q] = q < len ? a.J_value : (R)0;
+    } else {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) Jr[q] = __ldg(a.pat_J + (int64_t)p * W + q);
+    }
+    const int32_t ii = (int32_t)i;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        const int32_t j = chk((int64_t)ii + off[q], a.n, a.err);
+        x = fma(Jr[q], ld<Coherent>(X + j), x);
+        y = fma(Jr[q], ld<Coherent>(Y + j), y);
+        z = fma(Jr[q], ld<Coherent>(Z + j), z);
+    }
+}
+
+template <typename R, bool Coherent, int Mode = kGeneral>
 __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &sd, const R *X, const R *Y,
                                              const R *Z, int64_t i, R &e0, R &e1, R &e2) {
+    exchange_sum_h<R, Coherent, Mode>(a, sys_H(sd, 0, R()), sys_H(sd, 1, R()), sys_H(sd, 2, R()), X, Y, Z, i, e0,
+                                      e1, e2);
+}
+
+// The sum started at the system's applied field (hx, hy, hz), passed in by callers that hold
+// it in registers for a whole tile.
+template <typename R, bool Coherent, int Mode>
+__device__ __forceinline__ void exchange_sum_h(const KArgs<R> &a, R hx, R hy, R hz, const R *X, const R *Y,
+                                               const R *Z, int64_t i, R &e0, R &e1, R &e2) {
     if constexpr (Mode == kRows) {  // long rows: summed beforehand by k_rows_sell / k_rows_field
         e0 = ld<Coherent>(a.ex + i);
         e1 = ld<Coherent>(a.ey + i);
         e2 = ld<Coherent>(a.ez + i);
         return;
     }
-    R x = sys_H(sd, 0, R()), y = sys_H(sd, 1, R()), z = sys_H(sd, 2, R());
+    R x = hx, y = hy, z = hz;
     if (a.pat && !(Mode == kGeneral && a.J_tensor)) {
-        // Row patterns: the row's bonds are the pattern's (column - row, J) pairs in CSR order,
-        // so the sum is the CSR sum term for term; one byte per row is read instead of the
-        // row's offsets and columns.
-        const int p = __ldg(a.pat + i);
-        const int len = __ldg(a.pat_len + p);
-        const int32_t *po = a.pat_off + p * kPatRow;
-        const R *pj = a.pat_J + p * kPatRow;
-#pragma unroll
-        for (int q = 0; q < kShortRow; ++q) {
-            if (q < len) {
-                const int32_t j = chk(i + __ldg(po + q), a.n, a.err);
-                const R Jk = a.J_uniform ? a.J_value : __ldg(pj + q);
-                x = fma(Jk, ld<Coherent>(X + j), x);
-                y = fma(Jk, ld<Coherent>(Y + j), y);
-                z = fma(Jk, ld<Coherent>(Z + j), z);
-            }
-        }
-        for (int q = kShortRow; q < len; ++q) {
-            const int32_t j = chk(i + __ldg(po + q), a.n, a.err);
-            const R Jk = a.J_uniform ? a.J_value : __ldg(pj + q);
-            x = fma(Jk, ld<Coherent>(X + j), x);
-            y = fma(Jk, ld<Coherent>(Y + j), y);
-            z = fma(Jk, ld<Coherent>(Z + j), z);
-        }
+        if (a.pat_w == 8)
+            pattern_sum<R, Coherent, kShortRow>(a, X, Y, Z, i, x, y, z);
+        else
+            pattern_sum<R, Coherent, kPatRow>(a, X, Y, Z, i, x, y, z);
         e0 = x;
         e1 = y;
         e2 = z;
@@ -215,24 +251,27 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
 }
 
 // Deterministic field (tesla): the exchange + applied field h from exchange_sum, then
-// the anisotropy and Neel terms.  Returns S.e for the anisotropy energy.
+// the anisotropy and Neel terms.  Returns S.e for the anisotropy energy.  Here and in llg_rhs
+// and spin_terms_r every product and sum is spelled out (fma, products rounded on their own),
+// so that no kernel variant that inlines them contracts them differently: the step kernels'
+// variants (split or fused, any launch mode) give bitwise the same states and records.
 template <typename R, bool Cubic = true>
 __device__ __forceinline__ R det_field(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R &H0, R &H1,
                                        R &H2) {
-    const R sde = s0 * m.e[0] + s1 * m.e[1] + s2 * m.e[2];
-    const R an = m.ani * sde;
+    const R sde = fma(s2, m.e[2], fma(s1, m.e[1], mul_rn(s0, m.e[0])));
+    const R an = mul_rn(m.ani, sde);
     H0 = fma(an, m.e[0], e0);
     H1 = fma(an, m.e[1], e1);
     H2 = fma(an, m.e[2], e2);
     if (Cubic && m.has_cubic) {  // -(2 k_c / mu_s) S^3
-        H0 = fma(m.kcf * s0 * s0, s0, H0);
-        H1 = fma(m.kcf * s1 * s1, s1, H1);
-        H2 = fma(m.kcf * s2 * s2, s2, H2);
+        H0 = fma(mul_rn(mul_rn(m.kcf, s0), s0), s0, H0);
+        H1 = fma(mul_rn(mul_rn(m.kcf, s1), s1), s1, H1);
+        H2 = fma(mul_rn(mul_rn(m.kcf, s2), s2), s2, H2);
     }
     if (m.has_neel) {
-        H0 += m.kf[0] * s0 + m.kf[3] * s1 + m.kf[4] * s2;
-        H1 += m.kf[3] * s0 + m.kf[1] * s1 + m.kf[5] * s2;
-        H2 += m.kf[4] * s0 + m.kf[5] * s1 + m.kf[2] * s2;
+        H0 = H0 + fma(m.kf[4], s2, fma(m.kf[3], s1, mul_rn(m.kf[0], s0)));
+        H1 = H1 + fma(m.kf[5], s2, fma(m.kf[1], s1, mul_rn(m.kf[3], s0)));
+        H2 = H2 + fma(m.kf[2], s2, fma(m.kf[5], s1, mul_rn(m.kf[4], s0)));
     }
     return sde;
 }
@@ -250,15 +289,15 @@ __device__ __forceinline__ void add_demag(const KArgs<R> &a, int64_t i, R &H0, R
 // dS = -gamma/(1+lambda^2) [S x H + lambda S x (S x H)]  (Eq. LLG)
 template <typename R>
 __device__ __forceinline__ void llg_rhs(R gp, R lam, R s0, R s1, R s2, R H0, R H1, R H2, R &d0, R &d1, R &d2) {
-    const R c0 = s1 * H2 - s2 * H1;
-    const R c1 = s2 * H0 - s0 * H2;
-    const R c2 = s0 * H1 - s1 * H0;
-    const R x0 = s1 * c2 - s2 * c1;
-    const R x1 = s2 * c0 - s0 * c2;
-    const R x2 = s0 * c1 - s1 * c0;
-    d0 = -gp * fma(lam, x0, c0);
-    d1 = -gp * fma(lam, x1, c1);
-    d2 = -gp * fma(lam, x2, c2);
+    const R c0 = fma(s1, H2, -mul_rn(s2, H1));
+    const R c1 = fma(s2, H0, -mul_rn(s0, H2));
+    const R c2 = fma(s0, H1, -mul_rn(s1, H0));
+    const R x0 = fma(s1, c2, -mul_rn(s2, c1));
+    const R x1 = fma(s2, c0, -mul_rn(s0, c2));
+    const R x2 = fma(s0, c1, -mul_rn(s1, c0));
+    d0 = mul_rn(-gp, fma(lam, x0, c0));
+    d1 = mul_rn(-gp, fma(lam, x1, c1));
+    d2 = mul_rn(-gp, fma(lam, x2, c2));
 }
 
 // Per-spin contributions to the reductions of the state S: mu S (3), -mu S.h/2 with h the
@@ -269,18 +308,19 @@ template <typename R, bool Cubic = true>
 __device__ __forceinline__ void spin_terms_r(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R sde,
                                              R v[5]) {
     const R mu = m.mu;
-    v[0] = mu * s0;
-    v[1] = mu * s1;
-    v[2] = mu * s2;
-    v[3] = (R)-0.5 * mu * (s0 * e0 + s1 * e1 + s2 * e2);
-    R ea = -m.ku * sde * sde;
+    v[0] = mul_rn(mu, s0);
+    v[1] = mul_rn(mu, s1);
+    v[2] = mul_rn(mu, s2);
+    v[3] = mul_rn((R)-0.5 * mu, fma(s2, e2, fma(s1, e1, mul_rn(s0, e0))));
+    R ea = mul_rn(-m.ku, mul_rn(sde, sde));
     if (Cubic && m.has_cubic) {
-        const R x2 = s0 * s0, y2 = s1 * s1, z2 = s2 * s2;
-        ea += (R)0.5 * m.kc * (x2 * x2 + y2 * y2 + z2 * z2);
+        const R x2 = mul_rn(s0, s0), y2 = mul_rn(s1, s1), z2 = mul_rn(s2, s2);
+        ea = fma((R)0.5 * m.kc, fma(z2, z2, fma(y2, y2, mul_rn(x2, x2))), ea);
     }
     if (m.has_neel) {
-        ea -= m.K[0] * s0 * s0 + m.K[1] * s1 * s1 + m.K[2] * s2 * s2
-            + (R)2 * (m.K[3] * s0 * s1 + m.K[4] * s0 * s2 + m.K[5] * s1 * s2);
+        const R d = fma(mul_rn(m.K[2], s2), s2, fma(mul_rn(m.K[1], s1), s1, mul_rn(mul_rn(m.K[0], s0), s0)));
+        const R o = fma(mul_rn(m.K[5], s1), s2, fma(mul_rn(m.K[4], s0), s2, mul_rn(mul_rn(m.K[3], s0), s1)));
+        ea = ea - fma((R)2, o, d);
     }
     v[4] = ea;
 }
@@ -337,7 +377,7 @@ struct TermAcc<float> {
     }
     __device__ __forceinline__ void out(double (&acc)[8]) const {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) acc[c] = f2d_bits(h[c]) + f2d_bits(l[c]);
+        for (int c = 0; c < 5; ++c) acc[c] = (double)h[c] + (double)l[c];  // once per tile
         acc[5] = acc[6] = acc[7] = 0.0;
     }
 };
@@ -429,15 +469,18 @@ __device__ __forceinline__ void flush_partials(const double *red, int nq, double
 }
 
 // Predictor over one tile.  Writes S', Q and H_th; acc receives this thread's sums of the
-// per-spin reduction terms.
-template <typename R, int BS, bool Coherent, int Mode = kGeneral>
+// per-spin reduction terms.  Split: the step's Gaussians were written beforehand by k_gauss
+// (every spin reads them, nothing is drawn here) and H_th is not stored (the corrector forms
+// the same product again).
+template <typename R, int BS, bool Coherent, int Mode = kGeneral, bool Split = false>
 __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
-                                               const StepTabT<R> &tab, int pre_slot, double (&acc)[8]) {
+                                               const StepTabT<R> *tab, int pre_slot, double (&acc)[8]) {
     constexpr int BM = base_mode(Mode);
     const SysDesc &sd = a.sys[td.sys];
     const R sqrtT = sqrtT_of_step(a, step, sd);
     const uint32_t key0 = sd.key0, key1 = sd.key1, ctr2 = sd.ctr2;
     const int64_t off = sd.offset;
+    const R ha0 = sys_H(sd, 0, R()), ha1 = sys_H(sd, 1, R()), ha2 = sys_H(sd, 2, R());
     TermAcc<R> ta;
     ta.reset();
     // The slot index is rotated by the warp index, so that the warps of a block reach their
@@ -448,29 +491,31 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
         const MatDesc<R> &m = mat_at<Mode>(a, i);
         const R s0 = ld<Coherent>(a.sx + i), s1 = ld<Coherent>(a.sy + i), s2 = ld<Coherent>(a.sz + i);
         R e0, e1, e2;
-        exchange_sum<R, Coherent, BM>(a, sd, a.sx, a.sy, a.sz, i, e0, e1, e2);
+        exchange_sum_h<R, Coherent, BM>(a, ha0, ha1, ha2, a.sx, a.sy, a.sz, i, e0, e1, e2);
         R H0, H1, H2;
         const R sde = det_field<R, BM != kPlain>(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         if (a.demag) add_demag(a, i, H0, H1, H2);
         R t0 = 0, t1 = 0, t2 = 0;
         if (sqrtT > (R)0) {
             const R sig = m.sig * sqrtT;
-            if (rot >= pre_slot) {  // drawn ahead by the previous corrector
-                t0 = sig * ld<Coherent>(a.gx + i);
-                t1 = sig * ld<Coherent>(a.gy + i);
-                t2 = sig * ld<Coherent>(a.gz + i);
-            } else {
+            if (Split || rot >= pre_slot) {  // drawn beforehand (k_gauss, or the previous corrector)
+                t0 = mul_rn(sig, ld<Coherent>(a.gx + i));
+                t1 = mul_rn(sig, ld<Coherent>(a.gy + i));
+                t2 = mul_rn(sig, ld<Coherent>(a.gz + i));
+            } else if constexpr (!Split) {
                 const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)step, ctr2, 0u, key0, key1);
                 R g0, g1, g2;
-                thermal_gaussians(a, tab, w, g0, g1, g2);
-                t0 = sig * g0;
-                t1 = sig * g1;
-                t2 = sig * g2;
+                thermal_gaussians(a, *tab, w, g0, g1, g2);
+                t0 = mul_rn(sig, g0);
+                t1 = mul_rn(sig, g1);
+                t2 = mul_rn(sig, g2);
             }
         }
-        a.hx[i] = t0;
-        a.hy[i] = t1;
-        a.hz[i] = t2;
+        if constexpr (!Split) {
+            a.hx[i] = t0;
+            a.hy[i] = t1;
+            a.hz[i] = t2;
+        }
         H0 += t0;
         H1 += t1;
         H2 += t2;
@@ -478,10 +523,10 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
         llg_rhs(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, d0, d1, d2);
         const R dt = m.dt;
         const R v0 = fma(dt, d0, s0), v1 = fma(dt, d1, s1), v2 = fma(dt, d2, s2);
-        const R inv = rsqrt_r(v0 * v0 + v1 * v1 + v2 * v2);
-        a.px[i] = v0 * inv;
-        a.py[i] = v1 * inv;
-        a.pz[i] = v2 * inv;
+        const R inv = rsqrt_r(fma(v2, v2, fma(v1, v1, mul_rn(v0, v0))));
+        a.px[i] = mul_rn(v0, inv);
+        a.py[i] = mul_rn(v1, inv);
+        a.pz[i] = mul_rn(v2, inv);
         const R hdt = (R)0.5 * dt;
         a.qx[i] = fma(hdt, d0, s0);
         a.qy[i] = fma(hdt, d1, s1);
@@ -499,41 +544,52 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
     ta.out(acc);
 }
 
-template <typename R, int BS, bool Coherent, int Mode = kGeneral>
+template <typename R, int BS, bool Coherent, int Mode = kGeneral, bool Split = false>
 __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
                                                const StepTabT<R> *tab) {
     constexpr int BM = base_mode(Mode);
     const SysDesc &sd = a.sys[td.sys];
+    const R sqrtT = Split ? sqrtT_of_step(a, step, sd) : (R)0;  // the thermal field from the Gaussians
     // Gaussians of step + 1 for the slots the next predictor will not draw (FP32-mixed):
     // this puts transform work next to the corrector's memory traffic.
     const R sqrtT_next = tab ? sqrtT_of_step(a, step + 1, sd) : (R)0;
     const uint32_t key0 = sd.key0, key1 = sd.key1, ctr2 = sd.ctr2;
     const int64_t off = sd.offset;
+    const R ha0 = sys_H(sd, 0, R()), ha1 = sys_H(sd, 1, R()), ha2 = sys_H(sd, 2, R());
     int rot = (threadIdx.x >> 5) % a.slots;  // the predictor's rotated slot index
     for (int k = threadIdx.x; k < td.count; k += BS, rot = rot + 1 == a.slots ? 0 : rot + 1) {
         const int64_t i = td.start + k;
         const MatDesc<R> &m = mat_at<Mode>(a, i);
         const R s0 = ld<Coherent>(a.px + i), s1 = ld<Coherent>(a.py + i), s2 = ld<Coherent>(a.pz + i);
         R e0, e1, e2;
-        exchange_sum<R, Coherent, BM>(a, sd, a.px, a.py, a.pz, i, e0, e1, e2);
+        exchange_sum_h<R, Coherent, BM>(a, ha0, ha1, ha2, a.px, a.py, a.pz, i, e0, e1, e2);
         R H0, H1, H2;
         det_field<R, BM != kPlain>(m, s0, s1, s2, e0, e1, e2, H0, H1, H2);
         if (a.demag) add_demag(a, i, H0, H1, H2);
-        H0 += ld<Coherent>(a.hx + i);
-        H1 += ld<Coherent>(a.hy + i);
-        H2 += ld<Coherent>(a.hz + i);
+        if constexpr (Split) {  // the predictor's H_th, formed the same way
+            if (sqrtT > (R)0) {
+                const R sig = m.sig * sqrtT;
+                H0 += mul_rn(sig, ld<Coherent>(a.gx + i));
+                H1 += mul_rn(sig, ld<Coherent>(a.gy + i));
+                H2 += mul_rn(sig, ld<Coherent>(a.gz + i));
+            }
+        } else {
+            H0 += ld<Coherent>(a.hx + i);
+            H1 += ld<Coherent>(a.hy + i);
+            H2 += ld<Coherent>(a.hz + i);
+        }
         R d0, d1, d2;
         llg_rhs(m.gp, m.lambda, s0, s1, s2, H0, H1, H2, d0, d1, d2);
         const R hdt = (R)0.5 * m.dt;
         const R v0 = fma(hdt, d0, ld<Coherent>(a.qx + i));
         const R v1 = fma(hdt, d1, ld<Coherent>(a.qy + i));
         const R v2 = fma(hdt, d2, ld<Coherent>(a.qz + i));
-        const R inv = rsqrt_r(v0 * v0 + v1 * v1 + v2 * v2);
+        const R inv = rsqrt_r(fma(v2, v2, fma(v1, v1, mul_rn(v0, v0))));
         if (bad_inv(inv)) atomicOr(a.err, kErrNonFinite);  // NaN or infinite length
-        a.sx[i] = v0 * inv;
-        a.sy[i] = v1 * inv;
-        a.sz[i] = v2 * inv;
-        if (rot >= a.pre_slot && sqrtT_next > (R)0) {
+        a.sx[i] = mul_rn(v0, inv);
+        a.sy[i] = mul_rn(v1, inv);
+        a.sz[i] = mul_rn(v2, inv);
+        if (!Split && rot >= a.pre_slot && sqrtT_next > (R)0) {
             const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)(step + 1), ctr2, 0u, key0, key1);
             R g0, g1, g2;
             thermal_gaussians(a, *tab, w, g0, g1, g2);
@@ -607,8 +663,8 @@ __device__ __forceinline__ void finalize_system(const SysDesc *sys, const int32_
 
 // Predictor passes over the block's tiles t = blockIdx.x + j gridDim.x, in chunks of
 // kTileChunk tiles whose partials are summed after one barrier.
-template <typename R, int BS, bool Coherent, int Mode = kGeneral>
-__device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step, const StepTabT<R> &tab,
+template <typename R, int BS, bool Coherent, int Mode = kGeneral, bool Split = false>
+__device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step, const StepTabT<R> *tab,
                                                int pre_slot, double *red) {
     const int64_t stride = gridDim.x;
     for (int64_t t0 = blockIdx.x; t0 < a.ntiles; t0 += (int64_t)kTileChunk * stride) {
@@ -617,7 +673,7 @@ __device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step,
             const int64_t t = t0 + nq * stride;
             if (t >= a.ntiles) break;
             double acc[8];
-            predictor_tile<R, BS, Coherent, Mode>(a, a.tiles[t], step, tab, pre_slot, acc);
+            predictor_tile<R, BS, Coherent, Mode, Split>(a, a.tiles[t], step, tab, pre_slot, acc);
             warp_partials<BS>(acc, red, nq);
         }
         __syncthreads();
@@ -643,7 +699,7 @@ __global__ void __launch_bounds__(BS, sizeof(R) == 8 ? 1 : SS_PRED_WARPS * 32 / 
     const uint64_t step = *a.step;
     // Gaussians drawn ahead are valid only if the previous corrector ran for this step.
     const int pre_slot = (a.g_step != nullptr && *a.g_step == step) ? a.pre_slot : 1 << 30;
-    predictor_pass<R, BS, false, Mode>(a, step, tab, pre_slot, red);
+    predictor_pass<R, BS, false, Mode>(a, step, &tab, pre_slot, red);
 }
 
 // Blocks [0, nfin) sum the predictor's tile partials into the record ring; the rest run
@@ -676,6 +732,71 @@ __global__ void __launch_bounds__(BS, sizeof(R) == 8 ? 0 : SS_CORR_WARPS * 32 / 
         if (done == gridDim.x - 1) {
             *a.ticket = 0u;
             if (DrawAhead) *a.g_step = step + 1ull;
+            *a.step = step + 1ull;
+            __threadfence();
+        }
+    }
+}
+
+// The split FP32-mixed step: k_gauss writes the step's Gaussians for every spin, then the
+// predictor and the corrector read them.  The transform is pure arithmetic and the two Heun
+// passes are memory-bound; apart, the passes carry no transform code, hold fewer registers and
+// keep more warps in flight.  The Gaussians move 12 bytes per spin out and 24 back per step,
+// what the stored thermal field and the drawn-ahead Gaussians of the fused step moved.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_gauss(const KArgs<float> a) {
+    __shared__ FFTables tab;
+    stage_ff_tables(a.fftab, tab);
+    __syncthreads();
+    const uint64_t step = *a.step;
+    // the buffer no longer holds Gaussians drawn ahead by a fused corrector
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.g_step) *a.g_step = ~0ull;
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const TileDesc td = a.tiles[t];
+        const SysDesc &sd = a.sys[td.sys];
+        if (!(sqrtT_of_step(a, step, sd) > 0.0f)) continue;  // no thermal field: nothing reads them
+        const uint32_t key0 = sd.key0, key1 = sd.key1, ctr2 = sd.ctr2;
+        const int64_t off = sd.offset;
+        for (int k = threadIdx.x; k < td.count; k += BS) {
+            const int64_t i = td.start + k;
+            const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)step, ctr2, 0u, key0, key1);
+            float g0, g1, g2;
+            gaussians_f32(w, tab, a.tab, g0, g1, g2);
+            a.gx[i] = g0;
+            a.gy[i] = g1;
+            a.gz[i] = g2;
+        }
+    }
+}
+
+template <typename R, int BS, int Mode = kGeneral>
+__global__ void __launch_bounds__(BS) k_predictor_split(const KArgs<R> a) {
+    __shared__ double red[kTileChunk * (BS / 32) * 8];
+    const uint64_t step = *a.step;
+    // (no tables: nothing is drawn in this pass)
+    predictor_pass<R, BS, false, Mode, true>(a, step, nullptr, 0, red);
+}
+
+template <typename R, int BS, int Mode = kGeneral>
+__global__ void __launch_bounds__(BS) k_corrector_split(const KArgs<R> a, int nfin) {
+    __shared__ double red[(BS / 32) * 8];
+    const uint64_t step = *a.step;
+    if ((int)blockIdx.x < nfin) {
+        for (int s = blockIdx.x; s < a.nsys; s += nfin) {
+            double *dst = a.rec + ((int64_t)(step % (uint64_t)a.rec_cap) * a.nsys + s) * kRecComps;
+            finalize_system<BS, false>(a.sys, a.sys_tiles, a.partials, s, dst, red);
+        }
+    } else {
+        const int64_t nb = gridDim.x - nfin;
+        for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb)
+            corrector_tile<R, BS, false, Mode, true>(a, a.tiles[t], step, nullptr);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int done = atomicAdd(a.ticket, 1u);
+        if (done == gridDim.x - 1) {
+            *a.ticket = 0u;
             *a.step = step + 1ull;
             __threadfence();
         }
@@ -813,7 +934,7 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
     for (long long k = 0; k < nsteps; ++k) {
         const uint64_t step = step0 + (uint64_t)k;
         const int pre_slot = k == 0 ? pre_first : (ahead ? a.pre_slot : 1 << 30);
-        predictor_pass<R, BS, true, Mode>(a, step, tab, pre_slot, red);
+        predictor_pass<R, BS, true, Mode>(a, step, &tab, pre_slot, red);
         if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
         if ((int)blockIdx.x < nfin) {
             for (int s = blockIdx.x; s < a.nsys; s += nfin) {
@@ -852,7 +973,7 @@ __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long lon
         for (long long k = 0; k < nsteps; ++k) {
             const uint64_t step = step0 + (uint64_t)k;
             double acc[8];
-            predictor_tile<R, BS, true, Mode>(a, whole, step, tab, 1 << 30, acc);
+            predictor_tile<R, BS, true, Mode>(a, whole, step, &tab, 1 << 30, acc);
             const double r = block_sum8<BS>(acc, red);
             write_record(sd, r, a.rec + ((int64_t)(step % (uint64_t)a.rec_cap) * a.nsys + s) * kRecComps);
             corrector_tile<R, BS, true, Mode>(a, whole, step, nullptr);

@@ -52,6 +52,83 @@ cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, c
     return cudaGetLastError();
 }
 
+// The split FP32-mixed step (a Gaussian pass, then the two Heun passes reading it): variants
+// kUniform, kPlain and kGeneral of the thread-per-row exchange sum.
+template <typename R>
+cudaError_t launch_gauss(const KArgs<R> &a, int block, int grid, cudaStream_t s) {
+    if constexpr (sizeof(R) == 4) {
+        SS_BLOCK_SWITCH(block, k_gauss<BS><<<grid, BS, 0, s>>>(a));
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+template <typename R>
+cudaError_t launch_predictor_split(const KArgs<R> &a, int block, int grid, cudaStream_t s) {
+    if constexpr (sizeof(R) == 4) {
+        switch (heun_mode(a)) {
+            case kGeneral: SS_BLOCK_SWITCH(block, k_predictor_split<R, BS, kGeneral><<<grid, BS, 0, s>>>(a)); break;
+            case kUniform: SS_BLOCK_SWITCH(block, k_predictor_split<R, BS, kUniform><<<grid, BS, 0, s>>>(a)); break;
+            case kPlain: SS_BLOCK_SWITCH(block, k_predictor_split<R, BS, kPlain><<<grid, BS, 0, s>>>(a)); break;
+            default: return cudaErrorNotSupported;
+        }
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+template <typename R>
+cudaError_t launch_corrector_split(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s) {
+    if constexpr (sizeof(R) == 4) {
+        switch (heun_mode(a)) {
+            case kGeneral:
+                SS_BLOCK_SWITCH(block, k_corrector_split<R, BS, kGeneral><<<grid + nfin, BS, 0, s>>>(a, nfin));
+                break;
+            case kUniform:
+                SS_BLOCK_SWITCH(block, k_corrector_split<R, BS, kUniform><<<grid + nfin, BS, 0, s>>>(a, nfin));
+                break;
+            case kPlain:
+                SS_BLOCK_SWITCH(block, k_corrector_split<R, BS, kPlain><<<grid + nfin, BS, 0, s>>>(a, nfin));
+                break;
+            default: return cudaErrorNotSupported;
+        }
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+// Resident blocks per SM of the split step's kernels: which = 0 the Gaussian pass, 1 the
+// predictor, 2 the corrector, in the variant `mode` (1 general, 3 uniform, else plain).
+template <typename R>
+int split_blocks_per_sm(int block, int mode, int which) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if constexpr (sizeof(R) == 4) {
+#define SS_OCC(MODE)                                                                                                  \
+    if (which == 0) {                                                                                                 \
+        SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gauss<BS>, BS, 0));           \
+    } else if (which == 1) {                                                                                          \
+        SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_predictor_split<R, BS, MODE>, \
+                                                                                 BS, 0));                             \
+    } else {                                                                                                          \
+        SS_BLOCK_SWITCH(block, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_corrector_split<R, BS, MODE>, \
+                                                                                 BS, 0));                             \
+    }
+        if (mode == kGeneral) {
+            SS_OCC(kGeneral)
+        } else if (mode == kUniform) {
+            SS_OCC(kUniform)
+        } else {
+            SS_OCC(kPlain)
+        }
+#undef SS_OCC
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
 template <typename R>
 cudaError_t launch_measure(const KArgs<R> &a, int block, int grid, cudaStream_t s) {
     SS_BLOCK_SWITCH(block, k_measure<R, BS><<<grid, BS, 0, s>>>(a));
@@ -339,6 +416,10 @@ cudaError_t launch_system_blocks(const KArgs<R> &a, int block, int grid, long lo
 template cudaError_t launch_system_blocks<SS_REAL>(const KArgs<SS_REAL> &, int, int, long long, cudaStream_t);
 template cudaError_t launch_predictor<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_corrector<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
+template cudaError_t launch_gauss<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
+template cudaError_t launch_predictor_split<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
+template cudaError_t launch_corrector_split<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
+template int split_blocks_per_sm<SS_REAL>(int, int, int);
 template cudaError_t launch_measure<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_init_sphere<SS_REAL>(const KArgs<SS_REAL> &, cudaStream_t);
 template cudaError_t launch_persistent<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, long long, cudaStream_t);

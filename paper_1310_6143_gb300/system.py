@@ -164,6 +164,18 @@ class SpinSystem:
         """'auto', 'thread' (a thread per exchange row) or 'warp' (a warp per row)."""
         self._check(self._lib.spin_system_set_exchange_rows(self._h, {"auto": 0, "thread": 1, "warp": 2}[mode]))
 
+    def set_gaussian_pass(self, on: bool):
+        """FP32-mixed: a separate pass writes each step's Gaussians (True, the default) or the
+        Heun passes draw them (False)."""
+        self._check(self._lib.spin_system_set_gaussian_pass(self._h, 1 if on else 0))
+
+    def time_passes(self, nsteps: int) -> dict:
+        """Real steps with CUDA events around every launch: mean Gaussian-pass, predictor and
+        corrector launch times and mean step time, in ms."""
+        out = np.zeros(4)
+        self._check(self._lib.spin_system_time_passes(self._h, int(nsteps), B.ptr(out)))
+        return {"gauss_ms": out[0], "predictor_ms": out[1], "corrector_ms": out[2], "step_ms": out[3]}
+
     def set_row_patterns(self, on: bool):
         """Read the one-byte row forms (True, the default when they were built) or the CSR."""
         self._check(self._lib.spin_system_set_row_patterns(self._h, 1 if on else 0))
