@@ -43,51 +43,50 @@ def pulse_T(nsteps, dt=1e-16, base=300.0, peak=1200.0, t0=1e-12, fwhm=100e-15):
     return base + (peak - base) * np.exp(-((t - t0) ** 2) / (2 * s * s))
 
 
-# Algorithmic HBM bytes per spin-step of the two-pass Heun step with the CSR as stored
-# (read S, write S' and the half step, read them back, write S: 18 words; the CSR read
-# once per pass): 18 p + 2 (z (4 + p) + 4).  For the film (mean z = 5.875) this is 174 B
-# in FP32 and 293 B in FP64.
+# Algorithmic HBM bytes per spin of one Heun pass with the CSR as stored: the pass reads one
+# spin vector and writes two (predictor: S -> S', P) or reads two and writes one (corrector:
+# S', P -> S), 9 words, and reads the CSR row once (z columns and values, one row offset):
+# 9 p + z (4 + p) + 4.  The step is two passes: 18 p + 2 (z (4 + p) + 4), for the film (mean
+# z = 5.875) 87 B per pass and 174 B per step in FP32, 146.5 and 293 B in FP64.
+def pass_bytes_per_spin(real_bytes, nnz_per_spin):
+    return 9 * real_bytes + nnz_per_spin * (4 + real_bytes) + 4
+
+
 def step_bytes_per_spin(real_bytes, nnz_per_spin):
-    return 18 * real_bytes + 2 * (nnz_per_spin * (4 + real_bytes) + 4)
+    return 2 * pass_bytes_per_spin(real_bytes, nnz_per_spin)
 
 
 # Bytes the implemented layout moves per spin-step: S, S', the half step Q and the stored
 # thermal field (24 words), the Gaussians drawn ahead (written and read back for a fraction
-# f of the spins), the CSR columns and row offsets once per pass, J once per pass unless
-# every bond has the same J_ij/mu_s,i, and the material index once per pass.
-def layout_bytes_per_spin(real_bytes, nnz_per_spin, f_ahead, j_uniform):
-    return (24 * real_bytes + 6 * real_bytes * f_ahead + 2 * (nnz_per_spin * 4 + 4)
-            + (0 if j_uniform else 2 * nnz_per_spin * real_bytes) + 8)
+# f of the spins), the neighbour rows once per pass -- one byte per spin with row patterns,
+# else the CSR columns and row offset (and J unless every bond has the same J_ij/mu_s,i) --
+# and the material index once per pass unless the handle has a single material.
+def layout_bytes_per_spin(real_bytes, nnz_per_spin, f_ahead, j_uniform, patterns=False, one_material=False):
+    rows = 2.0 if patterns else 2 * (nnz_per_spin * 4 + 4) + (0 if j_uniform else 2 * nnz_per_spin * real_bytes)
+    return 24 * real_bytes + 6 * real_bytes * f_ahead + rows + (0 if one_material else 8)
 
 
-# FP64 pipe instructions per spin of the FP32-mixed step kernels.  One thermal draw (the
-# table-driven FP64 Box-Muller) costs 19 FP64 instructions; the corrector draws a fraction
-# f of them for the next step, the predictor the rest.  The FP64 moment/energy sums cost
-# 5 DADD per spin accumulated per thread over `spt` spins plus a 9-add warp butterfly.
-# For the default film shape (block 512, 8 spins per thread, f = 4/8) this gives 15.0
-# and 9.5, the values ncu counts (profiles/k_predictor_film1024x1024x16_fp32.md,
-# profiles/k_corrector_film1024x1024x16_fp32.md).  Each FP64 instruction (DADD, DMUL or
-# DFMA) takes one FMA slot of the pipe (2 slots per cycle per SM), so it counts as 2
-# flop-equivalents, the convention of the chip's FP64 rating.
-FP64_PER_DRAW = 19.0
+# The FP64 form's step kernels run every operation on the FP64 pipe (2 instructions per cycle
+# per SM on GB300): FP64 instructions per spin counted by ncu (sass_thread_inst_executed_op_
+# dadd/dmul/dfma) on the film's predictor, profiles/k_predictor_film1024x1024x16_fp64.md.
+# Each counts as 2 flop-equivalents, the convention of the chip's FP64 rating.
+FP64_FORM_PREDICTOR_FP64_PER_SPIN = 101.0
 
-
-def fp64_inst_per_spin(kernel, block, tile, draw_ahead_eighths):
-    spt = tile // block
-    f = ((draw_ahead_eighths * spt) // 8) / spt
-    if kernel == "k_corrector":
-        return FP64_PER_DRAW * f
-    return FP64_PER_DRAW * (1 - f) + 5.0 * (spt - 1) / spt + 9.0 / spt
-
-
-# DRAM bytes per launch of the default film shape (block, tile, draw-ahead eighths), from
-# the same ncu captures.
+# DRAM bytes per launch of the default film shape (block, tile, draw-ahead eighths), read from
+# one ncu capture of the FP32-mixed kernels (profiles/k_predictor_film1024x1024x16_fp32.md,
+# profiles/k_corrector_film1024x1024x16_fp32.md), not measured in this run.
 DEFAULT_FILM_SHAPE = (512, 4096, 4)
-KERNEL_DRAM_BYTES = {"k_predictor": 0.842e9 + 0.568e9, "k_corrector": 1.150e9 + 0.286e9}
+KERNEL_DRAM_BYTES = {"k_predictor": 0.883e9, "k_corrector": 0.899e9}
 SMS = 152
 NO_AUTOTUNE = False
 EXEC_NAMES = {0: "auto", 1: "kernels", 2: "graph", 3: "persistent", 4: "system_blocks"}
 FP64_SLOTS_PER_SM_CYCLE = 2
+PULSE_PEAK_STEP = 10_000  # the temperature pulse peaks at t0 = 1 ps = step 10,000 at dt = 1e-16 s
+
+
+def timed_window(steps, warmup):
+    """First step of the warm-up so that the timed steps are centred on the pulse peak."""
+    return max(0, PULSE_PEAK_STEP - steps // 2 - warmup)
 
 
 def _smi_time(stamp):
@@ -212,7 +211,52 @@ def cpu_baseline(lat, T, seconds=15.0):
     return {"value": lat.n * steps / one, "unit": "spin-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"{steps} Heun step(s) of the full 1024x1024x16 film (FP64, with per-step moment/energy "
                       f"record), {one:.1f} s",
-            "single_thread_value": lat.n / single, "cpu_model": cpu_model()}
+            "single_thread_value": lat.n / single, "cpu_model": cpu_model(), "build": "gcc " + " ".join(O.FLAGS)}
+
+
+def fp32_error(stream):
+    """The FP32-mixed form's trajectory error against the FP64 oracle, as numbers: every spin of
+    the film after eight benchmarked steps (a pulse-shaped schedule, random start), and the sc
+    10^3 workload after 100 steps (the stated 1e-4 tolerance is for 100 steps), with the FP64
+    form beside each (1e-12 after 1000 steps for sc 10^3)."""
+    import oracle as O
+    from paper_1310_6143_gb300 import lattice as L
+    from paper_1310_6143_gb300.system import SpinSystem
+
+    O.build()
+    O.set_threads(O.max_threads())
+
+    def run(lat, precision, steps, T, S0, alpha, seed):
+        with SpinSystem(lat, alpha=alpha, dt=1e-16, T=0.0, seed=seed, S0=S0, precision=precision,
+                        stream=stream) as s:
+            s.set_temperature_schedule(T)
+            start = s.spins()
+            s.step(steps)
+            return start, s.spins(), s.record(0, steps)[:, 0, :]
+
+    def oracle_run(lat, start, steps, T, alpha, seed):
+        ref = O.OracleSystem(lat.row_ptr, lat.col, lat.J, lat.mu_s, lat.k_u, lat.easy_axis, alpha=alpha, dt=1e-16,
+                             seed=seed)
+        return O.heun_run(ref, start, steps, T, record=True)
+
+    out = {}
+    film = L.film(1024, 1024, 16)
+    T8 = np.array([300.0, 450.0, 700.0, 1000.0, 1200.0, 1000.0, 700.0, 450.0])
+    S0 = L.random_state(film.n, 31)
+    for prec in ("fp32", "fp64"):
+        start, S, rec = run(film, prec, 8, T8, S0, 0.02, 5)
+        S_ref, rec_ref = oracle_run(film, start, 8, T8, 0.02, 5)
+        out[f"film_8_steps_{prec}"] = {"max_abs_dS": float(np.abs(S - S_ref).max()),
+                                       "max_rel_dM": float(np.abs(rec[:, :3] - rec_ref[:, :3]).max() / rec_ref[0, 3])}
+    sc = L.simple_cubic(10, 10, 10, J=6.0e-21, k_u=1.0e-24)
+    for prec, steps in (("fp32", 100), ("fp64", 1000)):
+        start, S, rec = run(sc, prec, steps, np.full(steps, 300.0), L.uniform_state(sc.n), 0.1, 1)
+        S_ref, rec_ref = oracle_run(sc, start, steps, np.full(steps, 300.0), 0.1, 1)
+        out[f"sc10_{steps}_steps_{prec}"] = {"max_abs_dS": float(np.abs(S - S_ref).max()),
+                                              "max_rel_dM": float(np.abs(rec[:, :3] - rec_ref[:, :3]).max()
+                                                                  / rec_ref[0, 3])}
+    out["tolerances"] = {"fp32_100_steps": 1e-4, "fp64_1000_steps": 1e-12}
+    return out
 
 
 def cpu_model():
@@ -513,7 +557,7 @@ def run_reference(args):
     cb = {"value": v, "unit": "spin-steps/s", "cores": threads, "kind": "oracle",
           "sample": f"{K} Heun steps (after {W} untimed) of a 1024x{ny}x16 film of the workload's construction "
                     f"({lat.n} spins; FP64, with per-step moment/energy record), {secs:.1f} s",
-          "cpu_model": cpu_model()}
+          "cpu_model": cpu_model(), "build": "gcc " + " ".join(O.FLAGS)}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "spin-steps/s", "n_gpus": 1,
             "steps": K, "warmup": W, "ms_per_step": 1e3 * secs / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -575,7 +619,9 @@ def main():
 
     lat = L.film(1024, 1024, 16)
     nnz_per = lat.nnz / lat.n
-    total_steps = args.warmup + args.steps + 64
+    # the timed steps are centred on the pulse peak (step 10,000): the schedule covers them
+    step0 = timed_window(args.steps, args.warmup)
+    total_steps = step0 + args.warmup + args.steps + 64
     T = pulse_T(total_steps + 16)
     stream = torch.cuda.Stream()
     res = {}
@@ -603,8 +649,10 @@ def main():
                         stream=stream) as s:
             s.set_temperature_schedule(T)
             info = s.autotune(6) if args.autotune_film else s.info()
+            s.step_index = timed_window(steps, warmup)
             s.step(warmup)
             s.sync()
+            first = s.step_index
             torch.cuda.synchronize()
             barrier(world)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -621,107 +669,137 @@ def main():
             barrier(world)
             ms = e0.elapsed_time(e1)
             ms = max_over_ranks(world, ms)
-            kt = s.time_kernels(5)
+            kt = s.time_passes(5)
             # end to end through the public API: per step the temperature goes host->device,
             # the step runs, and the step's moment/energy record comes back device->host
             e2e_steps = max(5, min(steps, 50))
             s.set_exec("kernels")
             t0 = time.perf_counter()
-            first = s.step_index
+            e2e_first = s.step_index
             for k in range(e2e_steps):
-                s.set_temperature(float(T[(first + k) % len(T)]))
+                s.set_temperature(float(T[(e2e_first + k) % len(T)]))
                 s.step(1)
-                s.record(first + k, 1)
+                s.record(e2e_first + k, 1)
             e2e_s = time.perf_counter() - t0
             mag = s.magnetisation()
-        return ms, kt, e2e_s / e2e_steps, ck.summary(local), mag, info
+        window = {"first_step": int(first), "steps": int(steps),
+                  "T_min_K": float(T[first:first + steps].min()), "T_max_K": float(T[first:first + steps].max())}
+        return ms, kt, e2e_s / e2e_steps, ck.summary(local), mag, info, window
 
-    ms32, kt32, e2e32, clk32, mag32, info32 = timed_run(args.precision, args.steps, args.warmup, 5)
+    ms32, kt32, e2e32, clk32, mag32, info32, win32 = timed_run(args.precision, args.steps, args.warmup, 5)
     e2e32 = max_over_ranks(world, e2e32)  # the job's end-to-end step time: its slowest rank
     value = world * lat.n * args.steps / (ms32 * 1e-3)
-    sm_ghz = (clk32.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))) / 1e3
-    fp64_peak = SMS * FP64_SLOTS_PER_SM_CYCLE * 2 * sm_ghz / 1e3  # TFLOP/s (FMA-slot flops)
-    # the dominant kernel of the step, by live CUDA-event time
+    rb = 4 if args.precision == "fp32" else 8
+    pass_b = pass_bytes_per_spin(rb, nnz_per)
+    step_b = step_bytes_per_spin(rb, nnz_per)
+    # the dominant kernel of the step, by live CUDA-event time on the handle's stream
     dom = "k_predictor" if kt32["predictor_ms"] >= kt32["corrector_ms"] else "k_corrector"
     dom_ms = kt32["predictor_ms"] if dom == "k_predictor" else kt32["corrector_ms"]
-    inst = fp64_inst_per_spin(dom, info32["block"], info32["tile"], info32["draw_ahead"]) \
-        if args.precision == "fp32" else None
-    achieved = 2 * inst * lat.n / (dom_ms * 1e-3) / 1e12 if inst else None
-    default_shape = (info32["block"], info32["tile"], info32["draw_ahead"]) == DEFAULT_FILM_SHAPE
-    step_b = step_bytes_per_spin(4 if args.precision == "fp32" else 8, nnz_per)
-    from paper_1310_6143_gb300.system import debug_fp64_rate
-
-    fp64_meas = None if args.no_extras else {
-        f"{name}_inst_per_sm_cycle": debug_fp64_rate(m) / SMS / (sm_ghz * 1e9)
-        for m, name in ((0, "dfma_shared_operands"), (1, "dfma_distinct_operands"), (2, "dadd"))}
-    hbm_achieved = step_b * lat.n / (ms32 / args.steps * 1e-3) / 1e9
+    kernel_gbs = pass_b * lat.n / (dom_ms * 1e-3) / 1e9
+    step_gbs = step_b * lat.n / (ms32 / args.steps * 1e-3) / 1e9
     spt = info32["tile"] // info32["block"]
     f_ahead = ((info32["draw_ahead"] * spt) // 8) / spt if args.precision == "fp32" else 0.0
     j_rows = lat.J / np.repeat(lat.mu_s, np.diff(lat.row_ptr))
-    lay_b = layout_bytes_per_spin(4 if args.precision == "fp32" else 8, nnz_per, f_ahead,
-                                  bool(np.all(j_rows == j_rows[0])))
+    lay_b = layout_bytes_per_spin(rb, nnz_per, f_ahead, bool(np.all(j_rows == j_rows[0])),
+                                  patterns=info32.get("row_patterns", 0) > 0, one_material=info32["num_materials"] == 1)
+    default_shape = (info32["block"], info32["tile"], info32["draw_ahead"]) == DEFAULT_FILM_SHAPE
+    sm_ghz = (clk32.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))) / 1e3
     out = {
         "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": "film 1024x1024x16 sc (16,777,216 spins), in-plane periodic, J 6.0e-21, "
-                               "k_u 1.0e-24 || z, alpha 0.02, dt 1e-16 s, T pulse 300->1200 K (100 fs FWHM)",
-                   "precision": "fp32-mixed (FP64 Box-Muller and reductions)" if args.precision == "fp32" else "fp64",
-                   "spins": lat.n, "nnz": lat.nnz,
+                               "k_u 1.0e-24 || z, alpha 0.02, dt 1e-16 s, T pulse 300->1200 K (100 fs FWHM, peak at "
+                               f"step {PULSE_PEAK_STEP}); timed steps {win32['first_step']}..."
+                               f"{win32['first_step'] + win32['steps'] - 1} of the schedule, centred on the pulse "
+                               f"(T {win32['T_min_K']:.0f}-{win32['T_max_K']:.0f} K), entered from the warm-up state",
+                   "precision": "fp32-mixed (FP64-exact thermal transform and FP64 reductions)"
+                   if args.precision == "fp32" else "fp64",
+                   "spins": lat.n, "nnz": lat.nnz, "timed_window": win32,
                    "exec": EXEC_NAMES[info32["exec"]] if info32["exec"] else "auto (captured graphs of step launches)",
                    "block": info32["block"], "tile": info32["tile"], "draw_ahead_eighths": info32["draw_ahead"],
+                   "gaussian_pass": info32.get("gaussian_pass", 0), "row_patterns": info32.get("row_patterns", 0),
                    "launch_shape": "spin_system_autotune" if args.autotune_film else "library default",
                    "l2": "state 0.8 GB >> 126 MB L2, no flush needed", "replicas": world},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak if achieved else None,
+        "roofline": {"bound": "hbm", "achieved": kernel_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": kernel_gbs / hbm_peak,
                      "traffic": KERNEL_DRAM_BYTES[dom] if (default_shape and args.precision == "fp32") else None,
+                     "traffic_source": "one ncu capture (profiles/), not measured in this run",
                      "kernel": dom, "kernel_ms": dom_ms,
-                     "pipe": "fp64", "per_unit": f"{inst:.2f} FP64 instructions per spin, 2 flop-equivalents each"
-                     if inst else None,
-                     "peak_source": f"152 SMs x 2 FP64 slots/cycle x 2 x {sm_ghz:.3f} GHz (measured clock)",
-                     "measured_fp64_rate": fp64_meas},
-        "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
-                         "layout_bytes_per_spin_step": lay_b,
-                         "layout_frac": lay_b * lat.n / (ms32 / args.steps * 1e-3) / 1e9 / hbm_peak,
-                         "per_unit": f"{step_b:.1f} B per spin-step (whole step)", "peak_source": peak_src},
+                     "per_unit": f"{pass_b:.1f} B per spin per Heun pass (the survey's two-pass model with the CSR "
+                                 f"as stored), {lat.n} spins per launch",
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                     "step_achieved": step_gbs, "step_frac": step_gbs / hbm_peak,
+                     "step_per_unit": f"{step_b:.1f} B per spin-step",
+                     "layout_bytes_per_spin_step": lay_b,
+                     "layout_frac": lay_b * lat.n / (ms32 / args.steps * 1e-3) / 1e9 / hbm_peak},
         "kernels_ms": kt32, "clocks": clk32,
         "e2e": {"value": world * lat.n / e2e32, "unit": "spin-steps/s", "h2d_bytes_per_step": 8,
                 "d2h_bytes_per_step": 64},
-        # step kernels launched in the timed region: a predictor and a corrector per step, or
-        # one cooperative launch per 64 steps in the persistent form
-        "gpu_launches": (-(-args.steps // 64)) if info32["exec"] == 3 else 2 * args.steps,
+        # step kernels launched in the timed region: a predictor and a corrector per step (and a
+        # Gaussian pass with the split step), or one cooperative launch per 64 steps persistent
+        "gpu_launches": (-(-args.steps // 64)) if info32["exec"] == 3 else
+                        (3 if info32.get("gaussian_pass", 0) else 2) * args.steps,
         "final_m": [float(x) for x in mag32],
     }
     # the FP64, batched, workload, Monte Carlo, demagnetising, alternative-integrator, long-row and
     # CPU-baseline legs are single-GPU diagnostics: at N > 1 the line carries the headline only
     if not args.no_extras and world == 1:
         k64 = max(20, args.steps // 4)
-        ms64, kt64, _, clk64, _, _ = timed_run("fp64", k64, args.warmup, 5)
+        ms64, kt64, _, clk64, _, _, win64 = timed_run("fp64", k64, args.warmup, 5)
+        fp64_peak = SMS * FP64_SLOTS_PER_SM_CYCLE * 2 * sm_ghz / 1e3  # TFLOP/s (FMA-slot flops)
+        fp64_ach = 2 * FP64_FORM_PREDICTOR_FP64_PER_SPIN * lat.n / (kt64["predictor_ms"] * 1e-3) / 1e12
         out["fp64"] = {"value": world * lat.n * k64 / (ms64 * 1e-3), "unit": "spin-steps/s", "steps": k64,
                        "kernels_ms": kt64, "clocks": clk64,
-                       "hbm_frac": step_bytes_per_spin(8, nnz_per) * lat.n / (ms64 / k64 * 1e-3) / 1e9 / hbm_peak}
+                       "hbm_frac": step_bytes_per_spin(8, nnz_per) * lat.n / (ms64 / k64 * 1e-3) / 1e9 / hbm_peak,
+                       "fp64_pipe": {"bound": "alu", "kernel": "k_predictor", "achieved": fp64_ach,
+                                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": fp64_ach / fp64_peak,
+                                     "per_unit": f"{FP64_FORM_PREDICTOR_FP64_PER_SPIN:.0f} FP64 instructions per "
+                                                 "spin (ncu, profiles/), 2 flop-equivalents each",
+                                     "peak_source": f"152 SMs x 2 FP64 slots/cycle x 2 x {sm_ghz:.3f} GHz "
+                                                    "(measured clock)"}}
         out["fp32_vs_fp64"] = out["value"] / out["fp64"]["value"]  # FP32-mixed speed-up on the same GPU
+        out["fp32_error"] = fp32_error(stream)
+        from paper_1310_6143_gb300.system import debug_fp64_rate
+        out["fp64_rate_probe"] = {f"{name}_inst_per_sm_cycle": debug_fp64_rate(m) / SMS / (sm_ghz * 1e9)
+                                  for m, name in ((0, "dfma_shared_operands"), (1, "dfma_distinct_operands"),
+                                                  (2, "dadd"))}
         # the batched form: 256 independent columnar grains (2,000-40,000 spins each, T
         # uniform in 0-800 K) in one handle, launch shape chosen by the autotuner
         grains, temps = L.grain_ensemble(count=256, seed=12345)
         ng = sum(g.n for g in grains)
-        with SpinSystem(grains, alpha=0.1, dt=1e-16, T=list(temps), seed=[4000 + k for k in range(256)],
-                        sys_id=list(range(256)), precision="fp32", stream=stream) as b:
-            tuned = b.info() if args.no_autotune else b.autotune(10)
+        nnz_g = sum(g.nnz for g in grains)
+        kb = max(50, args.steps // 2)
+
+        def batch_ms(b, steps):
             b.step(args.warmup)
             b.sync()
-            kb = max(50, args.steps // 2)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            b.step(kb)
+            b.step(steps)
             e1.record(stream)
             e1.synchronize()
             b.sync()
-            msb = e0.elapsed_time(e1)
-        out["batched"] = {"value": world * ng * kb / (msb * 1e-3), "unit": "spin-steps/s", "steps": kb,
-                          "systems": 256, "spins": ng, "ms_per_step": msb / kb,
-                          "exec": EXEC_NAMES[tuned["exec"]],
-                          "block": tuned["block"], "tile": tuned["tile"]}
+            return e0.elapsed_time(e1) / steps
+
+        with SpinSystem(grains, alpha=0.1, dt=1e-16, T=list(temps), seed=[4000 + k for k in range(256)],
+                        sys_id=list(range(256)), precision="fp32", stream=stream) as b:
+            tuned = b.info() if args.no_autotune else b.autotune(10)
+            msb = batch_ms(b, kb)
+            # the two launch forms side by side in the tuned shape: per-step captured graphs, and
+            # one persistent cooperative launch per 64 steps (captured)
+            forms = {}
+            for mode in ("graph", "persistent"):
+                b.set_exec(mode)
+                forms[f"{mode}_ms"] = batch_ms(b, kb)
+        gb = step_bytes_per_spin(4, nnz_g / ng)
+        out["batched"] = {"value": world * ng / (msb * 1e-3), "unit": "spin-steps/s", "steps": kb,
+                          "systems": 256, "spins": ng, "ms_per_step": msb,
+                          "exec": EXEC_NAMES[tuned["exec"]], "block": tuned["block"], "tile": tuned["tile"],
+                          "gaussian_pass": tuned.get("gaussian_pass", 0), "row_patterns": tuned.get("row_patterns", 0),
+                          **forms,
+                          "hbm_frac": gb * ng / (msb * 1e-3) / 1e9 / hbm_peak,
+                          "hbm_per_unit": f"{gb:.1f} B per spin-step (two-pass model, mean row {nnz_g / ng:.3f})"}
         out["workloads"] = workload_table(stream, rank)
         out["mc"] = mc_table(stream, rank)
         out["demag"] = demag_table(stream, rank)

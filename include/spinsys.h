@@ -146,8 +146,9 @@ typedef struct {
                              row reading packed bonds (see spin_system_set_exchange_rows)  */
     int32_t row_patterns; /* row forms the thread-per-row exchange sums read instead of the
                              CSR (see spin_system_set_row_patterns); 0: the CSR is read    */
-    int32_t gaussian_pass;/* 1: graph and plain-launch steps run the Gaussian pass before
-                             the Heun passes (see spin_system_set_gaussian_pass)          */
+    int32_t gaussian_pass;/* graph and plain-launch steps: 0 Gaussians drawn in the Heun
+                             passes, 1 a Gaussian pass before them, 2 that pass overlapping
+                             the previous step (see spin_system_set_gaussian_pass)        */
 } ss_info;
 
 /* Create one system.  Validates and copies every array (SS_ERR_INVALID_ARG on bad
@@ -320,17 +321,19 @@ ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode);
  * always read the CSR.  SS_ERR_INVALID_ARG for another value. */
 ss_status spin_system_set_row_patterns(ss_system *h, int32_t on);
 
-/* FP32-mixed form, thread-per-row exchange, graph and plain-launch execution: on = 1 (the
- * default) runs each step as three launches -- a pass that writes the step's thermal
+/* FP32-mixed form, thread-per-row exchange, graph and plain-launch execution.  mode 0 (the
+ * default; the persistent and system-block modes always work this way): the Heun passes draw
+ * the thermal Gaussians themselves.  mode 1: each step runs a pass that writes the step's
  * Gaussians (the transform of ss_debug_gaussians mode 2) for every spin at a non-zero
  * temperature, then the predictor and the corrector, both forming the thermal field
- * sigma_i sqrt(T_n) g from them (so the field is the same in both passes, and the same as
- * with on = 0) -- instead of drawing the Gaussians inside the Heun passes (on = 0, which the
- * persistent and system-block modes always do).  The transform is pure arithmetic and the
- * Heun passes are memory-bound: kept apart, the passes need fewer registers and keep more
- * warps in flight.  Results do not depend on the setting.  SS_ERR_INVALID_ARG for another
- * value. */
-ss_status spin_system_set_gaussian_pass(ss_system *h, int32_t on);
+ * sigma_i sqrt(T_n) g from them -- so the field is the same in both passes and the same as in
+ * mode 0.  mode 2: as mode 1, with the Gaussian pass of step n+1 running on a second,
+ * low-priority stream beside the Heun passes of step n (Gaussians of even and odd steps in two
+ * buffers, the pass's step held in its own device counter; the Heun passes then take one block
+ * per SM less, leaving room for it).  The transform is pure arithmetic and the Heun passes are
+ * memory-bound.  Results do not depend on the mode.  Modes 1 and 2 allocate a second Gaussian
+ * buffer (12 bytes per spin) on first use.  SS_ERR_INVALID_ARG for another value. */
+ss_status spin_system_set_gaussian_pass(ss_system *h, int32_t mode);
 
 /* FP32-mixed form: the corrector of step n draws the thermal Gaussians of step n+1 for
  * `eighths`/8 of each tile's spins (rounded down to whole blocks), so that their FP64
@@ -339,7 +342,7 @@ ss_status spin_system_set_gaussian_pass(ss_system *h, int32_t on);
  * Results do not depend on it (the same Gaussians are drawn). */
 ss_status spin_system_set_draw_ahead(ss_system *h, int32_t eighths);
 
-/* Time the candidate (exec, block, tile, draw-ahead) choices on this handle over `trial_steps`
+/* Time the candidate (exec, block, tile, draw-ahead, Gaussian pass) choices on this handle over `trial_steps`
  * steps each, keep the fastest, and write it to *out_info.  The spins and the step
  * counter are restored afterwards, so the trajectory is unchanged.  With the environment
  * variable SPINSYS_AUTOTUNE_CACHE naming a file, a workload tuned before on the same device

@@ -6,6 +6,7 @@ may import this package.  The product package never imports it, and the oracle s
 no code with the CUDA path.
 """
 from .oracle import (  # noqa: F401
+    FLAGS,
     OracleSystem,
     build,
     lib_path,

@@ -116,7 +116,12 @@ struct ss_system {
     int32_t npat = 0;                   // 0: no patterns (more than kMaxPatterns, rows too long)
     int32_t pat_w = 8;                  // slots of a pattern row (8 or 16, see KArgs)
     bool use_pat = true;                // spin_system_set_row_patterns
-    bool gauss_pass = true;             // spin_system_set_gaussian_pass
+    int gauss_mode = 0;                 // spin_system_set_gaussian_pass: 0 fused, 1 split, 2 split
+                                        // with the next step's Gaussian pass running concurrently
+    void *ahead2[3] = {};               // the split step's Gaussians of odd steps (allocated on use)
+    cudaStream_t side = nullptr;        // the concurrent Gaussian passes' stream
+    int side_priority = 0;              // their launch priority (the device's lowest)
+    cudaEvent_t ev_fork = nullptr, ev_gauss = nullptr, ev_corr = nullptr;
     alignas(16) unsigned char mat0[sizeof(MatDesc<double>)] = {};  // MatDesc<R> of material 0
 
     std::vector<SysDesc> hsys;
@@ -490,6 +495,11 @@ KArgs<R> make_args(const ss_system *h) {
     a.gy = static_cast<R *>(h->ahead[1]);
     a.gz = static_cast<R *>(h->ahead[2]);
     a.g_step = h->ahead[0] ? h->ctl + 3 : nullptr;
+    a.g2x = static_cast<R *>(h->ahead2[0]);
+    a.g2y = static_cast<R *>(h->ahead2[1]);
+    a.g2z = static_cast<R *>(h->ahead2[2]);
+    a.gstep = h->ctl + 4;
+    a.gticket = reinterpret_cast<unsigned int *>(h->ctl + 5);
     a.pre_slot = h->pre_slot;
     a.slots = std::max(1, h->tile / h->block);
     a.partials = h->partials;
@@ -578,13 +588,18 @@ int corrector_grid(const ss_system *h) {
 
 // The split FP32-mixed step (a Gaussian pass before the Heun passes) is used by the graph and
 // plain-launch modes of FP32-mixed handles that sum a thread per exchange row.
-bool split_step(const ss_system *h) { return h->gauss_pass && h->precision == SS_FP32_MIXED && !h->rows; }
+bool split_step(const ss_system *h) {
+    return h->gauss_mode > 0 && h->ahead2[0] && h->precision == SS_FP32_MIXED && !h->rows;
+}
 
 // One wave of resident blocks of the split step's kernel `which` (0 Gaussian pass, 1 predictor,
-// 2 corrector; the corrector's finalisation blocks come on top).
+// 2 corrector; the corrector's finalisation blocks come on top).  With the Gaussian pass running
+// concurrently (mode 2) the Heun passes take one block per SM less, leaving room for one block
+// of the Gaussian pass on every SM.
 int split_grid(const ss_system *h, int which) {
-    const int per_sm = split_blocks_per_sm<float>(h->block, step_mode(h), which);
-    const int64_t g = (int64_t)h->sm_count * std::max(per_sm, 1);
+    int per_sm = std::max(1, split_blocks_per_sm<float>(h->block, step_mode(h), which));
+    if (h->gauss_mode == 2) per_sm = which == 0 ? 1 : std::max(1, per_sm - 1);
+    const int64_t g = (int64_t)h->sm_count * per_sm;
     return (int)std::max<int64_t>(1, std::min<int64_t>(h->ntiles, g));
 }
 
@@ -602,13 +617,42 @@ cudaError_t enqueue_steps_kernels(ss_system *h, int64_t n) {
     use_rows(h, a);
     if (split_step(h)) {
         const int gg = split_grid(h, 0), gp = split_grid(h, 1), gc = split_grid(h, 2);
-        for (int64_t k = 0; k < n; ++k) {
-            cudaError_t e = launch_gauss<R>(a, h->block, gg, h->stream);
+        if (n <= 0) return cudaSuccess;
+        cudaError_t e = launch_gstep_sync<R>(a, h->stream);
+        if (h->gauss_mode == 1) {  // Gaussian pass, predictor, corrector, in order
+            for (int64_t k = 0; k < n && e == cudaSuccess; ++k) {
+                e = launch_gauss<R>(a, h->block, gg, h->stream, 0);
+                if (e == cudaSuccess) e = launch_predictor_split<R>(a, h->block, gp, h->stream);
+                if (e == cudaSuccess) e = launch_corrector_split<R>(a, h->block, gc, h->nfin, h->stream);
+            }
+            return e;
+        }
+        // Concurrent: the first step's Gaussians on the handle's stream; then the pass of step
+        // s + 1 runs on the side stream beside step s's Heun passes, once the corrector of step
+        // s - 1 (the last reader of its buffer) is done; the predictor of step s + 1 waits for it.
+        {
+            const int full = (int)std::max<int64_t>(  // the first pass has the GPU to itself
+                1, std::min<int64_t>(h->ntiles, (int64_t)h->sm_count *
+                                                    std::max(1, split_blocks_per_sm<float>(h->block, step_mode(h), 0))));
+            if (e == cudaSuccess) e = launch_gauss<R>(a, h->block, full, h->stream, 0);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+        for (int64_t k = 0; k < n && e == cudaSuccess; ++k) {
+            if (k + 1 < n) {
+                if (k >= 1) e = cudaStreamWaitEvent(h->side, h->ev_corr, 0);
+                if (e == cudaSuccess) e = launch_gauss<R>(a, h->block, gg, h->side, h->side_priority);
+                if (e == cudaSuccess) e = cudaEventRecord(h->ev_gauss, h->side);
+            }
+            if (e == cudaSuccess && k >= 1) e = cudaStreamWaitEvent(h->stream, h->ev_gauss, 0);
             if (e == cudaSuccess) e = launch_predictor_split<R>(a, h->block, gp, h->stream);
             if (e == cudaSuccess) e = launch_corrector_split<R>(a, h->block, gc, h->nfin, h->stream);
-            if (e != cudaSuccess) return e;
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_corr, h->stream);
         }
-        return cudaSuccess;
+        // join the side stream (needed when it ran nothing after the fork)
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, h->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_fork, 0);
+        return e;
     }
     const int gp = step_grid(h), gc = corrector_grid(h), gr = h->rows ? rows_grid(h) : 0;
     for (int64_t k = 0; k < n; ++k) {
@@ -1160,9 +1204,9 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
                              h->stream)) != cudaSuccess)
         return cleanup(cuda_fail(h, e, "cudaMemcpyAsync"));
     // control words, tables, record ring, current measurement
-    if ((e = dalloc(h, (void **)&h->ctl, 4 * sizeof(unsigned long long))) != cudaSuccess)
+    if ((e = dalloc(h, (void **)&h->ctl, 6 * sizeof(unsigned long long))) != cudaSuccess)
         return cleanup(cuda_fail(h, e, "cudaMalloc"));
-    if ((e = cudaMemsetAsync(h->ctl, 0, 4 * sizeof(unsigned long long), h->stream)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(h->ctl, 0, 6 * sizeof(unsigned long long), h->stream)) != cudaSuccess)
         return cleanup(cuda_fail(h, e, "cudaMemsetAsync"));
     std::vector<double2> tab;
     build_tables(tab);
@@ -1181,10 +1225,9 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         return cleanup(cuda_fail(h, e, "cudaMalloc"));
     st = h->precision == SS_FP32_MIXED ? upload_system<float>(h, hs) : upload_system<double>(h, hs);
     if (st != SS_OK) return cleanup(st);
-    // Launch shape: 512-thread blocks for large FP64 systems, else 256 (the FP32-mixed split
-    // step's lean passes keep more warps in flight with 256-thread blocks); spins per thread (a
-    // power of two, at most 8) chosen so that there are about eight tiles per resident block.
-    h->block = n >= (int64_t(1) << 22) && h->precision == SS_FP64 ? 512 : 256;
+    // Launch shape: 512-thread blocks for large systems; spins per thread (a power of two,
+    // at most 8) chosen so that there are about eight tiles per resident block.
+    h->block = n >= (int64_t(1) << 22) ? 512 : 256;
     {
         int64_t spt = n / ((int64_t)std::max(h->sm_count, 1) * 8 * h->block);
         int slots = 1;
@@ -1240,7 +1283,8 @@ ss_status time_kernels_impl(ss_system *h, int32_t nsteps, double out_ms[4]) {
     for (auto &e : ev) SS_CUDA(h, cudaEventCreate(&e));
     SS_CUDA(h, cudaEventRecord(ev[0], h->stream));
     for (int32_t k = 0; k < nsteps; ++k) {
-        if (split) SS_CUDA(h, launch_gauss<R>(a, h->block, gg, h->stream));
+        if (split && k == 0) SS_CUDA(h, launch_gstep_sync<R>(a, h->stream));
+        if (split) SS_CUDA(h, launch_gauss<R>(a, h->block, gg, h->stream, 0));
         SS_CUDA(h, cudaEventRecord(ev[3 * k + 1], h->stream));
         if (h->rows) SS_CUDA(h, launch_rows_field<R>(a, a.sx, a.sy, a.sz, gr, h->stream));
         if (split)
@@ -1719,6 +1763,12 @@ ss_status spin_system_destroy(ss_system *h) {
         g_live_bytes -= (int64_t)b.bytes;
     }
     h->bufs.clear();
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    for (cudaEvent_t ev : {h->ev_fork, h->ev_gauss, h->ev_corr})
+        if (ev) cudaEventDestroy(ev);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
     return SS_OK;
@@ -2207,12 +2257,23 @@ ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode) {
     return set_rows(h, mode);
 }
 
-ss_status spin_system_set_gaussian_pass(ss_system *h, int32_t on) {
+ss_status spin_system_set_gaussian_pass(ss_system *h, int32_t mode) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
-    if (on != 0 && on != 1) return fail(h, SS_ERR_INVALID_ARG, "on must be 0 or 1");
+    if (mode < 0 || mode > 2) return fail(h, SS_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
-    h->gauss_pass = on != 0;
+    if (mode > 0 && h->precision == SS_FP32_MIXED && !h->ahead2[0])
+        for (int b = 0; b < 3; ++b) SS_CUDA(h, dalloc(h, &h->ahead2[b], (size_t)h->n * sizeof(float)));
+    if (mode == 2 && !h->side) {
+        int least = 0, greatest = 0;
+        SS_CUDA(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        h->side_priority = least;
+        SS_CUDA(h, cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, least));
+        SS_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        SS_CUDA(h, cudaEventCreateWithFlags(&h->ev_gauss, cudaEventDisableTiming));
+        SS_CUDA(h, cudaEventCreateWithFlags(&h->ev_corr, cudaEventDisableTiming));
+    }
+    h->gauss_mode = mode;
     drop_graph(h);  // captured launches hold the other step's kernels
     SS_CUDA(h, invalidate_ahead(h));
     return SS_OK;
@@ -2254,7 +2315,7 @@ ss_status spin_system_info(ss_system *h, ss_info *o) {
     o->draw_ahead = h->ahead_q;
     o->exchange_rows = h->rows ? (h->sell ? 3 : 2) : 1;
     o->row_patterns = h->use_pat ? h->npat : 0;
-    o->gaussian_pass = split_step(h) ? 1 : 0;
+    o->gaussian_pass = split_step(h) ? h->gauss_mode : 0;
     return SS_OK;
 }
 
@@ -2318,14 +2379,14 @@ static std::string autotune_key(const ss_system *h) {
     int64_t nmax = 0;
     for (int64_t v : h->sys_n) nmax = std::max(nmax, v);
     char buf[512];
-    std::snprintf(buf, sizeof(buf), "v1|%s|%d|%lld|%lld|%d|%lld|%d|%d", prop.name, h->precision, (long long)h->n,
+    std::snprintf(buf, sizeof(buf), "v2|%s|%d|%lld|%lld|%d|%lld|%d|%d", prop.name, h->precision, (long long)h->n,
                   (long long)h->nnz, h->nsys, (long long)nmax, h->rows ? (h->sell ? 3 : 2) : 1, step_mode(h));
     for (char *c = buf; *c; ++c)
         if (*c == '\t' || *c == '\n') *c = ' ';
     return buf;
 }
 
-static bool autotune_lookup(const std::string &path, const std::string &key, int v[4]) {
+static bool autotune_lookup(const std::string &path, const std::string &key, int v[5]) {
     FILE *f = std::fopen(path.c_str(), "r");
     if (!f) return false;
     char line[1024];
@@ -2333,7 +2394,7 @@ static bool autotune_lookup(const std::string &path, const std::string &key, int
     while (std::fgets(line, sizeof(line), f)) {
         char *tab = std::strchr(line, '\t');
         if (!tab || std::string(line, (size_t)(tab - line)) != key) continue;
-        found = std::sscanf(tab + 1, "%d %d %d %d", &v[0], &v[1], &v[2], &v[3]) == 4;  // the last entry wins
+        found = std::sscanf(tab + 1, "%d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4]) == 5;  // the last entry wins
     }
     std::fclose(f);
     return found;
@@ -2348,10 +2409,11 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     const char *cache = std::getenv("SPINSYS_AUTOTUNE_CACHE");
     const std::string key = cache && *cache ? autotune_key(h) : std::string();
     if (!key.empty()) {
-        int v[4];
-        if (autotune_lookup(cache, key, v) && v[3] >= 0 && v[3] <= 8) {
+        int v[5];
+        if (autotune_lookup(cache, key, v) && v[3] >= 0 && v[3] <= 8 && v[4] >= 0 && v[4] <= 2) {
             h->ahead_q = v[3];
-            st = spin_system_set_launch(h, v[1], v[2]);
+            st = spin_system_set_gaussian_pass(h, v[4]);
+            if (st == SS_OK) st = spin_system_set_launch(h, v[1], v[2]);
             if (st == SS_OK) st = spin_system_set_exec(h, (ss_exec)v[0]);
             if (st == SS_OK) return out_info ? spin_system_info(h, out_info) : SS_OK;
             h->bad = false;  // a stale entry: tune afresh
@@ -2364,7 +2426,7 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     SS_CUDA(h, dalloc(h, &save, 3 * (size_t)n * rs));
     for (int c = 0; c < 3; ++c)
         SS_CUDA(h, cudaMemcpyAsync((char *)save + c * n * rs, h->state[c], n * rs, cudaMemcpyDeviceToDevice, h->stream));
-    struct Cand { int exec, block, tile, ahead; };
+    struct Cand { int exec, block, tile, ahead, gauss; };
     std::vector<Cand> cands;
     const bool mixed = h->precision == SS_FP32_MIXED;
     // 128-thread blocks only where 256-thread tiles would leave most SMs idle: a small system
@@ -2375,21 +2437,26 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
             for (int q : {4, 5, 6}) {
                 if (!mixed && q != 6) continue;  // no draw-ahead in the FP64 form
                 if (b == 128 && (!small || m > 2)) continue;
-                cands.push_back({SS_EXEC_GRAPH, b, b * m, q});
-                cands.push_back({SS_EXEC_PERSISTENT, b, b * m, q});
+                cands.push_back({SS_EXEC_GRAPH, b, b * m, q, 0});
+                cands.push_back({SS_EXEC_PERSISTENT, b, b * m, q, 0});
             }
+    // the split step (a Gaussian pass, then the lean Heun passes)
+    if (mixed && !h->rows)
+        for (int b : {256, 512})
+            for (int m : {4, 8}) cands.push_back({SS_EXEC_GRAPH, b, b * m, h->ahead_q, 1});
     // whole systems per block pays when every system fits a few blocks' worth of threads
     int64_t biggest = 0;
     for (int64_t v : h->sys_n) biggest = std::max(biggest, v);
     if (biggest <= 16384)
-        for (int b : {128, 256, 512}) cands.push_back({SS_EXEC_SYSTEM_BLOCKS, b, b, h->ahead_q});
+        for (int b : {128, 256, 512}) cands.push_back({SS_EXEC_SYSTEM_BLOCKS, b, b, h->ahead_q, 0});
     cudaEvent_t e0, e1;
     SS_CUDA(h, cudaEventCreate(&e0));
     SS_CUDA(h, cudaEventCreate(&e1));
     float best = 1e30f;
-    Cand bestc{h->exec, h->block, h->tile, h->ahead_q};
+    Cand bestc{h->exec, h->block, h->tile, h->ahead_q, h->gauss_mode};
     for (const Cand &c : cands) {
         h->ahead_q = c.ahead;
+        if (spin_system_set_gaussian_pass(h, c.gauss) != SS_OK) { h->bad = false; continue; }
         if (spin_system_set_launch(h, c.block, c.tile) != SS_OK) continue;
         if (spin_system_set_exec(h, (ss_exec)c.exec) != SS_OK) continue;
         if (llg_heun_step(h, std::min(trial_steps, 4)) != SS_OK) { h->bad = false; continue; }
@@ -2408,7 +2475,8 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->ahead_q = bestc.ahead;
-    st = spin_system_set_launch(h, bestc.block, bestc.tile);
+    st = spin_system_set_gaussian_pass(h, bestc.gauss);
+    if (st == SS_OK) st = spin_system_set_launch(h, bestc.block, bestc.tile);
     if (st == SS_OK) st = spin_system_set_exec(h, (ss_exec)bestc.exec);
     for (int c = 0; c < 3; ++c)
         SS_CUDA(h, cudaMemcpyAsync(h->state[c], (char *)save + c * n * rs, n * rs, cudaMemcpyDeviceToDevice, h->stream));
@@ -2417,7 +2485,8 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     if (st == SS_OK) st = set_step(h, step0);
     if (st == SS_OK && !key.empty()) {
         if (FILE *f = std::fopen(cache, "a")) {
-            std::fprintf(f, "%s\t%d %d %d %d\n", key.c_str(), h->exec, h->block, h->tile, h->ahead_q);
+            std::fprintf(f, "%s\t%d %d %d %d %d\n", key.c_str(), h->exec, h->block, h->tile, h->ahead_q,
+                         h->gauss_mode);
             std::fclose(f);
         }
     }

@@ -124,7 +124,11 @@ struct KArgs {
     R *px, *py, *pz;          // S' (predictor, renormalised)
     R *qx, *qy, *qz;          // S + dt/2 dS (predictor half step)
     R *hx, *hy, *hz;          // thermal field of the current step
-    R *gx, *gy, *gz;          // Gaussians of the next step drawn by the corrector (FP32-mixed)
+    R *gx, *gy, *gz;          // Gaussians of the next step drawn by the corrector (FP32-mixed);
+                              // the split step's Gaussians of even steps
+    R *g2x, *g2y, *g2z;       // the split step's Gaussians of odd steps (FP32-mixed)
+    unsigned long long *gstep;  // step whose Gaussians the next Gaussian pass writes
+    unsigned int *gticket;    // completion counter of the Gaussian pass
     unsigned long long *g_step; // step whose Gaussians gx..gz hold (tile slots >= pre_slot)
     int pre_slot;             // Gaussians of a tile slot (spin k of a tile: slot k / block) are
                               // drawn ahead by the corrector when its rotated index
@@ -192,7 +196,8 @@ template <typename R> cudaError_t launch_predictor(const KArgs<R> &a, int block,
 template <typename R> cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s);
 template <typename R> cudaError_t launch_measure(const KArgs<R> &a, int block, int grid, cudaStream_t s);
 // The split FP32-mixed step: the Gaussian pass, then the Heun passes reading it (FP32 only).
-template <typename R> cudaError_t launch_gauss(const KArgs<R> &a, int block, int grid, cudaStream_t s);
+template <typename R> cudaError_t launch_gauss(const KArgs<R> &a, int block, int grid, cudaStream_t s, int priority);
+template <typename R> cudaError_t launch_gstep_sync(const KArgs<R> &a, cudaStream_t s);
 template <typename R> cudaError_t launch_predictor_split(const KArgs<R> &a, int block, int grid, cudaStream_t s);
 template <typename R>
 cudaError_t launch_corrector_split(const KArgs<R> &a, int block, int grid, int nfin, cudaStream_t s);

@@ -474,7 +474,8 @@ __device__ __forceinline__ void flush_partials(const double *red, int nq, double
 // the same product again).
 template <typename R, int BS, bool Coherent, int Mode = kGeneral, bool Split = false>
 __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
-                                               const StepTabT<R> *tab, int pre_slot, double (&acc)[8]) {
+                                               const StepTabT<R> *tab, int pre_slot, double (&acc)[8],
+                                               const R *Gx, const R *Gy, const R *Gz) {
     constexpr int BM = base_mode(Mode);
     const SysDesc &sd = a.sys[td.sys];
     const R sqrtT = sqrtT_of_step(a, step, sd);
@@ -499,9 +500,9 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
         if (sqrtT > (R)0) {
             const R sig = m.sig * sqrtT;
             if (Split || rot >= pre_slot) {  // drawn beforehand (k_gauss, or the previous corrector)
-                t0 = mul_rn(sig, ld<Coherent>(a.gx + i));
-                t1 = mul_rn(sig, ld<Coherent>(a.gy + i));
-                t2 = mul_rn(sig, ld<Coherent>(a.gz + i));
+                t0 = mul_rn(sig, ld<Coherent>(Gx + i));
+                t1 = mul_rn(sig, ld<Coherent>(Gy + i));
+                t2 = mul_rn(sig, ld<Coherent>(Gz + i));
             } else if constexpr (!Split) {
                 const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)step, ctr2, 0u, key0, key1);
                 R g0, g1, g2;
@@ -546,7 +547,8 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
 
 template <typename R, int BS, bool Coherent, int Mode = kGeneral, bool Split = false>
 __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc &td, uint64_t step,
-                                               const StepTabT<R> *tab) {
+                                               const StepTabT<R> *tab, const R *Gx = nullptr,
+                                               const R *Gy = nullptr, const R *Gz = nullptr) {
     constexpr int BM = base_mode(Mode);
     const SysDesc &sd = a.sys[td.sys];
     const R sqrtT = Split ? sqrtT_of_step(a, step, sd) : (R)0;  // the thermal field from the Gaussians
@@ -569,9 +571,9 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
         if constexpr (Split) {  // the predictor's H_th, formed the same way
             if (sqrtT > (R)0) {
                 const R sig = m.sig * sqrtT;
-                H0 += mul_rn(sig, ld<Coherent>(a.gx + i));
-                H1 += mul_rn(sig, ld<Coherent>(a.gy + i));
-                H2 += mul_rn(sig, ld<Coherent>(a.gz + i));
+                H0 += mul_rn(sig, ld<Coherent>(Gx + i));
+                H1 += mul_rn(sig, ld<Coherent>(Gy + i));
+                H2 += mul_rn(sig, ld<Coherent>(Gz + i));
             }
         } else {
             H0 += ld<Coherent>(a.hx + i);
@@ -665,7 +667,8 @@ __device__ __forceinline__ void finalize_system(const SysDesc *sys, const int32_
 // kTileChunk tiles whose partials are summed after one barrier.
 template <typename R, int BS, bool Coherent, int Mode = kGeneral, bool Split = false>
 __device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step, const StepTabT<R> *tab,
-                                               int pre_slot, double *red) {
+                                               int pre_slot, double *red, const R *Gx, const R *Gy,
+                                               const R *Gz) {
     const int64_t stride = gridDim.x;
     for (int64_t t0 = blockIdx.x; t0 < a.ntiles; t0 += (int64_t)kTileChunk * stride) {
         int nq = 0;
@@ -673,7 +676,7 @@ __device__ __forceinline__ void predictor_pass(const KArgs<R> &a, uint64_t step,
             const int64_t t = t0 + nq * stride;
             if (t >= a.ntiles) break;
             double acc[8];
-            predictor_tile<R, BS, Coherent, Mode, Split>(a, a.tiles[t], step, tab, pre_slot, acc);
+            predictor_tile<R, BS, Coherent, Mode, Split>(a, a.tiles[t], step, tab, pre_slot, acc, Gx, Gy, Gz);
             warp_partials<BS>(acc, red, nq);
         }
         __syncthreads();
@@ -699,7 +702,7 @@ __global__ void __launch_bounds__(BS, sizeof(R) == 8 ? 1 : SS_PRED_WARPS * 32 / 
     const uint64_t step = *a.step;
     // Gaussians drawn ahead are valid only if the previous corrector ran for this step.
     const int pre_slot = (a.g_step != nullptr && *a.g_step == step) ? a.pre_slot : 1 << 30;
-    predictor_pass<R, BS, false, Mode>(a, step, &tab, pre_slot, red);
+    predictor_pass<R, BS, false, Mode>(a, step, &tab, pre_slot, red, a.gx, a.gy, a.gz);
 }
 
 // Blocks [0, nfin) sum the predictor's tile partials into the record ring; the rest run
@@ -748,8 +751,11 @@ __global__ void __launch_bounds__(BS) k_gauss(const KArgs<float> a) {
     __shared__ FFTables tab;
     stage_ff_tables(a.fftab, tab);
     __syncthreads();
-    const uint64_t step = *a.step;
-    // the buffer no longer holds Gaussians drawn ahead by a fused corrector
+    // The step comes from the Gaussian pass's own counter: the pass may run while the previous
+    // step's Heun passes (which advance the step counter) are still running.
+    const uint64_t step = *a.gstep;
+    float *Gx = (step & 1) ? a.g2x : a.gx, *Gy = (step & 1) ? a.g2y : a.gy, *Gz = (step & 1) ? a.g2z : a.gz;
+    // the buffers no longer hold Gaussians drawn ahead by a fused corrector
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.g_step) *a.g_step = ~0ull;
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDesc td = a.tiles[t];
@@ -762,19 +768,34 @@ __global__ void __launch_bounds__(BS) k_gauss(const KArgs<float> a) {
             const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)step, ctr2, 0u, key0, key1);
             float g0, g1, g2;
             gaussians_f32(w, tab, a.tab, g0, g1, g2);
-            a.gx[i] = g0;
-            a.gy[i] = g1;
-            a.gz[i] = g2;
+            Gx[i] = g0;
+            Gy[i] = g1;
+            Gz[i] = g2;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // the last block to finish moves the counter to the next step
+        __threadfence();
+        const unsigned int done = atomicAdd(a.gticket, 1u);
+        if (done == gridDim.x - 1) {
+            *a.gticket = 0u;
+            *a.gstep = step + 1ull;
+            __threadfence();
         }
     }
 }
+
+// Start of a run of split steps: the Gaussian pass's counter joins the step counter.
+static __global__ void k_gstep_sync(unsigned long long *gstep, const unsigned long long *step) { *gstep = *step; }
 
 template <typename R, int BS, int Mode = kGeneral>
 __global__ void __launch_bounds__(BS) k_predictor_split(const KArgs<R> a) {
     __shared__ double red[kTileChunk * (BS / 32) * 8];
     const uint64_t step = *a.step;
     // (no tables: nothing is drawn in this pass)
-    predictor_pass<R, BS, false, Mode, true>(a, step, nullptr, 0, red);
+    const bool odd = step & 1;
+    predictor_pass<R, BS, false, Mode, true>(a, step, nullptr, 0, red, odd ? a.g2x : a.gx, odd ? a.g2y : a.gy,
+                                             odd ? a.g2z : a.gz);
 }
 
 template <typename R, int BS, int Mode = kGeneral>
@@ -788,8 +809,10 @@ __global__ void __launch_bounds__(BS) k_corrector_split(const KArgs<R> a, int nf
         }
     } else {
         const int64_t nb = gridDim.x - nfin;
+        const bool odd = step & 1;
         for (int64_t t = blockIdx.x - nfin; t < a.ntiles; t += nb)
-            corrector_tile<R, BS, false, Mode, true>(a, a.tiles[t], step, nullptr);
+            corrector_tile<R, BS, false, Mode, true>(a, a.tiles[t], step, nullptr, odd ? a.g2x : a.gx,
+                                                     odd ? a.g2y : a.gy, odd ? a.g2z : a.gz);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -934,7 +957,7 @@ __global__ void __launch_bounds__(BS) k_persistent(const KArgs<R> a, int nfin, l
     for (long long k = 0; k < nsteps; ++k) {
         const uint64_t step = step0 + (uint64_t)k;
         const int pre_slot = k == 0 ? pre_first : (ahead ? a.pre_slot : 1 << 30);
-        predictor_pass<R, BS, true, Mode>(a, step, &tab, pre_slot, red);
+        predictor_pass<R, BS, true, Mode>(a, step, &tab, pre_slot, red, a.gx, a.gy, a.gz);
         if (!grid_barrier(a.bar_count, a.bar_gen, expected, a.bar_timeout_ns, a.err)) return;
         if ((int)blockIdx.x < nfin) {
             for (int s = blockIdx.x; s < a.nsys; s += nfin) {
@@ -973,7 +996,7 @@ __global__ void __launch_bounds__(BS) k_system_blocks(const KArgs<R> a, long lon
         for (long long k = 0; k < nsteps; ++k) {
             const uint64_t step = step0 + (uint64_t)k;
             double acc[8];
-            predictor_tile<R, BS, true, Mode>(a, whole, step, &tab, 1 << 30, acc);
+            predictor_tile<R, BS, true, Mode>(a, whole, step, &tab, 1 << 30, acc, a.gx, a.gy, a.gz);
             const double r = block_sum8<BS>(acc, red);
             write_record(sd, r, a.rec + ((int64_t)(step % (uint64_t)a.rec_cap) * a.nsys + s) * kRecComps);
             corrector_tile<R, BS, true, Mode>(a, whole, step, nullptr);

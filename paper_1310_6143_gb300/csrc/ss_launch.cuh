@@ -54,14 +54,33 @@ cudaError_t launch_corrector(const KArgs<R> &a, int block, int grid, int nfin, c
 
 // The split FP32-mixed step (a Gaussian pass, then the two Heun passes reading it): variants
 // kUniform, kPlain and kGeneral of the thread-per-row exchange sum.
+// priority: the launch's scheduling priority (cudaLaunchAttributePriority; 0 = the stream's)
 template <typename R>
-cudaError_t launch_gauss(const KArgs<R> &a, int block, int grid, cudaStream_t s) {
+cudaError_t launch_gauss(const KArgs<R> &a, int block, int grid, cudaStream_t s, int priority) {
     if constexpr (sizeof(R) == 4) {
-        SS_BLOCK_SWITCH(block, k_gauss<BS><<<grid, BS, 0, s>>>(a));
-        return cudaGetLastError();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributePriority;
+        attr[0].val.priority = priority;
+        cfg.attrs = attr;
+        cfg.numAttrs = priority ? 1 : 0;
+        switch (block) {
+            case 128: cfg.blockDim = dim3(128); return cudaLaunchKernelEx(&cfg, k_gauss<128>, a);
+            case 256: cfg.blockDim = dim3(256); return cudaLaunchKernelEx(&cfg, k_gauss<256>, a);
+            case 512: cfg.blockDim = dim3(512); return cudaLaunchKernelEx(&cfg, k_gauss<512>, a);
+            default: return cudaErrorInvalidValue;
+        }
     } else {
         return cudaErrorNotSupported;
     }
+}
+
+template <typename R>
+cudaError_t launch_gstep_sync(const KArgs<R> &a, cudaStream_t s) {
+    k_gstep_sync<<<1, 1, 0, s>>>(a.gstep, a.step);
+    return cudaGetLastError();
 }
 
 template <typename R>
@@ -416,7 +435,8 @@ cudaError_t launch_system_blocks(const KArgs<R> &a, int block, int grid, long lo
 template cudaError_t launch_system_blocks<SS_REAL>(const KArgs<SS_REAL> &, int, int, long long, cudaStream_t);
 template cudaError_t launch_predictor<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_corrector<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
-template cudaError_t launch_gauss<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
+template cudaError_t launch_gauss<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t, int);
+template cudaError_t launch_gstep_sync<SS_REAL>(const KArgs<SS_REAL> &, cudaStream_t);
 template cudaError_t launch_predictor_split<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_corrector_split<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
 template int split_blocks_per_sm<SS_REAL>(int, int, int);

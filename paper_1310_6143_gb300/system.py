@@ -164,10 +164,11 @@ class SpinSystem:
         """'auto', 'thread' (a thread per exchange row) or 'warp' (a warp per row)."""
         self._check(self._lib.spin_system_set_exchange_rows(self._h, {"auto": 0, "thread": 1, "warp": 2}[mode]))
 
-    def set_gaussian_pass(self, on: bool):
-        """FP32-mixed: a separate pass writes each step's Gaussians (True, the default) or the
-        Heun passes draw them (False)."""
-        self._check(self._lib.spin_system_set_gaussian_pass(self._h, 1 if on else 0))
+    def set_gaussian_pass(self, mode):
+        """FP32-mixed: 0/False the Heun passes draw the Gaussians (the default), 1/True a
+        separate pass writes each step's Gaussians first, 2 that pass runs concurrently with
+        the previous step."""
+        self._check(self._lib.spin_system_set_gaussian_pass(self._h, int(mode)))
 
     def time_passes(self, nsteps: int) -> dict:
         """Real steps with CUDA events around every launch: mean Gaussian-pass, predictor and

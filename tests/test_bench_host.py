@@ -1,6 +1,7 @@
-"""Host-side arithmetic of bench.py (no GPU): the algorithmic bytes per spin-step of the
-two-pass Heun step, the FP64 instruction count behind the roofline, the temperature pulse,
-and the clock-record summary (samples kept only inside the timed window, throttle reasons)."""
+"""Host-side arithmetic of bench.py (no GPU): the algorithmic bytes per Heun pass and per
+spin-step, the bytes of the implemented layout, the timed window around the temperature
+pulse, and the clock-record summary (samples kept only inside the timed window, throttle
+reasons)."""
 import datetime
 import os
 import sys
@@ -21,15 +22,24 @@ def test_step_bytes_per_spin(z, p, expect):
     assert bench.step_bytes_per_spin(p, z) == pytest.approx(6 * 3 * p + 2 * (z * (4 + p) + 4))
 
 
-def test_fp64_instructions_per_spin_default_shape():
-    # block 512, 8 spins per thread, half the draws in the corrector: 9.5 + 5 * 7/8 + 9/8
-    assert bench.fp64_inst_per_spin("k_predictor", 512, 4096, 4) == pytest.approx(15.0)
-    assert bench.fp64_inst_per_spin("k_corrector", 512, 4096, 4) == pytest.approx(9.5)
-    # no draw-ahead: the whole transform in the predictor
-    assert bench.fp64_inst_per_spin("k_corrector", 512, 4096, 0) == 0.0
-    assert bench.fp64_inst_per_spin("k_predictor", 512, 4096, 0) == pytest.approx(19.0 + 5.5)
-    # draw-ahead rounds down to whole spins per thread: 4 spins per thread, 3/8 -> 1/4
-    assert bench.fp64_inst_per_spin("k_corrector", 256, 1024, 3) == pytest.approx(19.0 / 4)
+def test_pass_and_layout_bytes():
+    # one Heun pass of the film: 9 words and the CSR row; the step is two passes
+    assert bench.pass_bytes_per_spin(4, 5.875) == pytest.approx(87.0)
+    assert bench.step_bytes_per_spin(4, 5.875) == pytest.approx(2 * bench.pass_bytes_per_spin(4, 5.875))
+    # the implemented layout: 24 words of state, half the Gaussians drawn ahead (written and
+    # read back), one pattern byte per pass, a single material (no index)
+    assert bench.layout_bytes_per_spin(4, 5.875, 0.5, True, patterns=True, one_material=True) == pytest.approx(
+        96 + 12 + 2)
+    # the CSR and the material index instead
+    assert bench.layout_bytes_per_spin(4, 5.875, 0.5, True) == pytest.approx(96 + 12 + 2 * (5.875 * 4 + 4) + 8)
+    assert bench.layout_bytes_per_spin(8, 6, 0.0, False) == pytest.approx(192 + 2 * (6 * 4 + 4) + 2 * 6 * 8 + 8)
+
+
+def test_timed_window_is_centred_on_the_pulse():
+    for steps, warmup in ((1000, 10), (20, 5), (3, 3)):
+        first = bench.timed_window(steps, warmup) + warmup
+        assert first <= bench.PULSE_PEAK_STEP < first + steps
+    assert bench.timed_window(30000, 10) == 0
 
 
 def test_pulse_peak_and_width():

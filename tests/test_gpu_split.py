@@ -46,12 +46,15 @@ def test_split_step_bitwise_equal_to_fused(SS, name):
         g, temps = L.grain_ensemble(count=5, n_min=300, n_max=700, layers=3, seed=3)
         lats = g
         kw.update(T=[float(t) for t in temps], seed=[21 + k for k in range(5)])
-    fused = _run(SS, lats, kw, [(False, "kernels", 20)])
-    split = _run(SS, lats, kw, [(True, "kernels", 7), (True, "graph", 13)])
-    mixed = _run(SS, lats, kw, [(False, "kernels", 3), (True, "kernels", 4), (False, "graph", 5), (True, "kernels", 8)])
-    for a, b, c in zip(fused, split, mixed):
+    fused = _run(SS, lats, kw, [(0, "kernels", 20)])
+    split = _run(SS, lats, kw, [(1, "kernels", 7), (1, "graph", 13)])
+    conc = _run(SS, lats, kw, [(2, "kernels", 1), (2, "kernels", 6), (2, "graph", 13)])
+    mixed = _run(SS, lats, kw, [(0, "kernels", 3), (2, "kernels", 4), (0, "graph", 5), (1, "kernels", 3),
+                                (2, "graph", 5)])
+    for a, b, c, d in zip(fused, split, conc, mixed):
         np.testing.assert_array_equal(a, b)
         np.testing.assert_array_equal(a, c)
+        np.testing.assert_array_equal(a, d)
 
 
 def test_split_step_under_schedule_and_zero_temperature(SS):
@@ -60,15 +63,16 @@ def test_split_step_under_schedule_and_zero_temperature(SS):
     lat = L.film(24, 20, 8)
     T = np.concatenate([np.full(5, 400.0), np.zeros(6), np.linspace(10.0, 900.0, 30)])
     kw = dict(alpha=0.1, dt=1e-16, T=0.0, seed=4)
-    fused = _run(SS, lat, kw, [(False, "kernels", 30)], sched=T)
-    split = _run(SS, lat, kw, [(True, "kernels", 9), (True, "persistent", 7), (True, "graph", 14)], sched=T)
+    fused = _run(SS, lat, kw, [(0, "kernels", 30)], sched=T)
+    split = _run(SS, lat, kw, [(1, "kernels", 9), (1, "persistent", 7), (2, "graph", 14)], sched=T)
     for a, b in zip(fused, split):
         np.testing.assert_array_equal(a, b)
 
 
 def test_time_passes_reports_the_gaussian_pass(SS):
     with SS(L.film(64, 64, 16), precision="fp32", T=300.0) as s:
+        s.set_gaussian_pass(1)
         t = s.time_passes(3)
         assert t["gauss_ms"] > 0 and t["predictor_ms"] > 0 and t["corrector_ms"] > 0
-        s.set_gaussian_pass(False)
+        s.set_gaussian_pass(0)
         assert s.time_passes(2)["gauss_ms"] < t["gauss_ms"]

@@ -98,8 +98,9 @@ def _build(name, text, tmp):
     path = os.path.join(tmp, f"lib_{abs(hash(name))}.so")
     csrc = path.replace(".so", ".c")
     open(csrc, "w").write(text)
-    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC", "-std=c11",
-                    "-o", path, csrc, "-lm"], check=True)
+    import oracle
+
+    subprocess.run(["gcc", *oracle.FLAGS, "-o", path, csrc, "-lm"], check=True)
     return path
 
 
