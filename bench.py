@@ -70,7 +70,7 @@ def layout_bytes_per_spin(real_bytes, nnz_per_spin, f_ahead, j_uniform, patterns
 # per SM on GB300): FP64 instructions per spin counted by ncu (sass_thread_inst_executed_op_
 # dadd/dmul/dfma) on the film's predictor, profiles/k_predictor_film1024x1024x16_fp64.md.
 # Each counts as 2 flop-equivalents, the convention of the chip's FP64 rating.
-FP64_FORM_PREDICTOR_FP64_PER_SPIN = 101.0
+FP64_FORM_PREDICTOR_FP64_PER_SPIN = 102.0
 
 # DRAM bytes per launch of the default film shape (block, tile, draw-ahead eighths), read from
 # one ncu capture of the FP32-mixed kernels (profiles/k_predictor_film1024x1024x16_fp32.md,
