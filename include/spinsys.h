@@ -22,8 +22,11 @@
  * (Salmon et al., SC'11) with counter (spin index within its system, step, system id, 0)
  * and key (seed low word, seed high word), followed by an FP64 Box-Muller transform:
  * u_k = (w_k + 1/2) 2^-32, gx = sqrt(-2 ln u0) cos(2 pi u1), gy = sqrt(-2 ln u0)
- * sin(2 pi u1), gz = sqrt(-2 ln u2) cos(2 pi u3).  Steps are counted modulo 2^32 in the
- * counter.  Constants are those of Table I: gamma = 1.76e11 1/(T s), kB = 1.3807e-23 J/K.
+ * sin(2 pi u1), gz = sqrt(-2 ln u2) cos(2 pi u3).  The FP32-mixed form uses exactly that
+ * transform's values rounded to float (evaluated in double-float arithmetic with a
+ * certified rounding, the rare uncertain roundings by the FP64 transform itself).  Steps
+ * are counted modulo 2^32 in the counter.  Constants are those of Table I:
+ * gamma = 1.76e11 1/(T s), kB = 1.3807e-23 J/K.
  *
  * Units: SI throughout -- moments J/T, energies J, fields T, temperatures K, time s.
  * Layouts: vectors are array-of-structures on the host (x, y, z per site); Neel tensors
@@ -170,10 +173,17 @@ ss_status spin_system_destroy(ss_system *h);
  * stream).  The handle synchronises its previous stream first. */
 ss_status spin_system_set_stream(ss_system *h, void *cuda_stream);
 
-/* Applied field (T) of system `sys`, or of every system when sys < 0. */
+/* Applied field (T) of system `sys`, or of every system when sys < 0: the H_app of the
+ * Zeeman term -sum_i mu_s S_i.H_app of Eq. spinhamiltonian, entering every spin's effective
+ * field (Eq. Heff) unchanged.  Asynchronous; SS_ERR_INVALID_ARG for sys >= number of systems
+ * or a non-finite component. */
 ss_status set_field(ss_system *h, int32_t sys, const double H_app[3]);
 
-/* Temperature (K) of every system; removes any temperature schedule. */
+/* Temperature (K) of every system; removes any temperature schedule.  T sets the variance
+ * 2 lambda kB T / (gamma mu_s dt) of the thermal field of the Langevin-dynamics section
+ * (the paper's thermal-field equation, each component a zero-mean Gaussian, drawn once per
+ * step and held over both Heun passes).  Asynchronous; SS_ERR_INVALID_ARG for a negative or
+ * non-finite T. */
 ss_status set_temperature(ss_system *h, double T);
 
 /* Temperatures of systems 0..count-1 (count = number of systems). */
@@ -184,8 +194,14 @@ ss_status set_temperature_batch(ss_system *h, const double *T, int32_t count);
  * The temperature of a step is taken at its start, t_n = n dt. */
 ss_status set_temperature_schedule(ss_system *h, const double *T_per_step, int64_t nsteps, int64_t step0);
 
-/* Advance every system by n >= 0 Heun steps (asynchronous).  Each step records the
- * moment and energy of the state at its start into the per-step record ring. */
+/* Advance every system by n >= 0 Heun steps (asynchronous): the stochastic LLG equation
+ * (Eq. LLG with the effective field of Eq. Heff plus the thermal field) integrated by the
+ * Heun predictor-corrector scheme of the section "Time Integration of the LLG Equation" --
+ * predictor S' = norm(S + dt dS(S, H)) over every spin, then corrector
+ * S <- norm(S + dt/2 (dS(S, H) + dS(S', H'))) with the same thermal field in H and H'.
+ * Each step records the moment and energy of the state at its start (Eq. spinhamiltonian)
+ * into the per-step record ring.  SS_ERR_INVALID_ARG for n < 0; a non-finite spin raised
+ * on the device is reported as SS_ERR_NONFINITE by the next synchronising call. */
 ss_status llg_heun_step(ss_system *h, int64_t n);
 
 /* Advance every system by n >= 0 Monte Carlo steps (asynchronous; Section "Monte Carlo
@@ -254,18 +270,26 @@ ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations);
  * runs of whole graphs.  SS_ERR_INVALID_ARG for n < 0. */
 ss_status llg_semi_implicit_step(ss_system *h, int64_t n);
 
-/* Copy all spins (concatenated over systems) to out3n [3n], AoS, FP64 (synchronous). */
+/* Copy all spins (concatenated over systems) to out3n [3n], AoS, FP64 (synchronous): the
+ * unit vectors S_i of the classical Heisenberg model (Eq. spinhamiltonian), |S_i| = 1 after
+ * every Heun step (renormalised as the time-integration section prescribes).
+ * out3n is caller-owned; SS_ERR_INVALID_ARG for NULL. */
 ss_status get_spins(ss_system *h, double *out3n);
 
 /* Device pointers of the x, y, z spin arrays (SoA, float or double as the precision). */
 ss_status get_spins_device(ss_system *h, const void **sx, const void **sy, const void **sz);
 
 /* Magnetisation of the current state of system `sys`: out = (mx, my, mz, |m|) with
- * m = sum_i mu_s,i S_i / sum_i mu_s,i (FP64 sums; synchronous). */
+ * m = sum_i mu_s,i S_i / sum_i mu_s,i (FP64 sums; synchronous) -- the reduced magnetisation
+ * whose time average the paper's m(T) curves (Monte Carlo vs LLG, the Curie-temperature
+ * fit) report.  SS_ERR_INVALID_ARG for sys out of range or NULL out. */
 ss_status get_magnetisation(ss_system *h, int32_t sys, double out[4]);
 
 /* Energy of the current state of system `sys` (J, FP64 sums, thermal field excluded):
- * out = (total, exchange, anisotropy incl. Neel, applied-field). */
+ * out = (total, exchange, anisotropy incl. Neel, applied-field) -- the terms of the
+ * Hamiltonian Eq. spinhamiltonian: exchange -1/2 sum_i sum_j J_ij S_i.S_j (Eq. HJij, each
+ * bond of the symmetric list once), uniaxial anisotropy -sum_i k_u (S_i.e_i)^2, applied
+ * field -sum_i mu_s S_i.H_app.  SS_ERR_INVALID_ARG for sys out of range or NULL out. */
 ss_status get_energy(ss_system *h, int32_t sys, double out[4]);
 
 /* Per-step record of steps first_step .. first_step+count-1 (all still in the ring):
@@ -284,8 +308,11 @@ ss_status get_step(ss_system *h, int64_t *step);
 /* Select how llg_heun_step launches its work (see ss_exec). */
 ss_status spin_system_set_exec(ss_system *h, ss_exec mode);
 
-/* Threads per block (64..1024, multiple of 32) and spins per tile (a multiple of the
- * block size, at most 16 blocks' worth) of the step kernels; rebuilds the tile list. */
+/* Threads per block (32, 64, 128, 256 or 512) and spins per tile (a multiple of the
+ * block size, at most 16 blocks' worth) of the step kernels; rebuilds the tile list.
+ * SS_ERR_INVALID_ARG for other values.  Single-warp blocks spread a small system's spins
+ * over more SMs (the FP64 pipe issues a warp's instruction in the same time whatever the
+ * number of active lanes). */
 ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
 
 /* How the exchange sum of Eq. HJij is split over threads: mode 0 automatic (the default: a
@@ -426,13 +453,24 @@ int64_t ss_debug_live_bytes(void);
  *  - n <= SS_NOALLOC_MAX_SPINS (131072); larger systems are rejected with
  *    SS_ERR_INVALID_ARG before any device work.  The static array holds 9.5 MB on every
  *    GPU that loads the library, until the process exits.
- *  - The first call on a device (the current device) finds the array's device address
- *    and uploads the function tables with synchronous copies; make that first call
- *    before any stream capture.  Later calls are asynchronous on `cuda_stream`.
- *  - All calls share the one array, which keeps the last call's contents; each call
- *    clears what must start at zero.  Calls whose work overlaps on the GPU (on
- *    different streams or devices sharing no order) race on the array and give wrong
- *    results: order them on one stream.
+ *  - Every call looks up the array's device address on the current device
+ *    (cudaGetSymbolAddress, which allocates nothing).  The first call on a device, and any
+ *    call that finds the address changed, uploads the function tables with a synchronous
+ *    copy; make that first call before any stream capture.  Other calls are asynchronous
+ *    on `cuda_stream`.  After cudaDeviceReset (or a torn-down and recreated context) the
+ *    array comes back zeroed; if it comes back at the same address the tables are not
+ *    uploaded again and the results are wrong: do not use the entry point after a reset in
+ *    the same process.
+ *  - All calls share the one array, which keeps the last call's contents.  Nothing in it
+ *    needs clearing: every word a step reads (predictor spins, half steps, thermal field,
+ *    reduction partials) is written earlier in the same step.  Calls whose work overlaps on
+ *    the GPU (on different streams or devices sharing no order) race on the array and give
+ *    wrong results: order them on one stream.
+ *  - step0 + nsteps <= 2^32 - 1: the step index is the 32-bit Philox counter word (larger
+ *    values are rejected with SS_ERR_INVALID_ARG).
+ *  - Launch failures are checked after the first step's launches and after the last; an
+ *    error left pending by earlier, unrelated work in the process is reported (and cleared)
+ *    by this call as SS_ERR_CUDA.
  *  - The result equals llg_heun_step on a handle created from the same arrays with
  *    precision SS_FP64 (same Philox stream, same Heun step, same reductions).
  *  - Non-finite spins are not reported by this call; inspect the spins or the record.

@@ -2239,8 +2239,8 @@ ss_status spin_system_set_exec(ss_system *h, ss_exec mode) {
 ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
-    if (block != 128 && block != 256 && block != 512)
-        return fail(h, SS_ERR_INVALID_ARG, "block must be 128, 256 or 512");
+    if (block != 32 && block != 64 && block != 128 && block != 256 && block != 512)
+        return fail(h, SS_ERR_INVALID_ARG, "block must be 32, 64, 128, 256 or 512");
     if (tile < block || tile % block != 0 || tile > 16 * block)
         return fail(h, SS_ERR_INVALID_ARG, "tile must be a multiple of block, at most 16 blocks");
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -2432,11 +2432,14 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     // 128-thread blocks only where 256-thread tiles would leave most SMs idle: a small system
     // spread over twice the SMs has twice the FP64 lanes for its thermal draws
     const bool small = n <= (int64_t)h->sm_count * 256;
-    for (int b : {128, 256, 512})
+    // single- and two-warp blocks for systems of at most 64 spins per SM: one warp per SM
+    const bool tiny = n <= (int64_t)h->sm_count * 64;
+    for (int b : {32, 64, 128, 256, 512})
         for (int m : {1, 2, 4, 8})
             for (int q : {4, 5, 6}) {
                 if (!mixed && q != 6) continue;  // no draw-ahead in the FP64 form
                 if (b == 128 && (!small || m > 2)) continue;
+                if (b <= 64 && (!tiny || m > 2)) continue;
                 cands.push_back({SS_EXEC_GRAPH, b, b * m, q, 0});
                 cands.push_back({SS_EXEC_PERSISTENT, b, b * m, q, 0});
             }

@@ -459,8 +459,8 @@ __device__ __forceinline__ void warp_partials(const double v[8], double *red, in
 template <int BS>
 __device__ __forceinline__ void flush_partials(const double *red, int nq, double *partials, int64_t t0,
                                                int64_t stride) {
-    if ((int)threadIdx.x < nq * 8) {
-        const int q = threadIdx.x >> 3, c = threadIdx.x & 7;
+    for (int idx = threadIdx.x; idx < nq * 8; idx += BS) {  // (blocks of fewer than 64 threads loop)
+        const int q = idx >> 3, c = idx & 7;
         double r = 0.0;
 #pragma unroll 4
         for (int w = 0; w < BS / 32; ++w) r += red[(q * (BS / 32) + w) * 8 + c];

@@ -1,0 +1,4 @@
+// FP64 instantiation, part 3: Monte Carlo and the alternative integrators.
+#define SS_REAL double
+#define SS_PART 3
+#include "ss_launch.cuh"

@@ -1,0 +1,5 @@
+// FP64 instantiation, part 2: the persistent and system-block kernels, the demagnetising
+// field.
+#define SS_REAL double
+#define SS_PART 2
+#include "ss_launch.cuh"

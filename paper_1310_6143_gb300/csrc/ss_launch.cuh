@@ -8,6 +8,8 @@ namespace ss {
 
 #define SS_BLOCK_SWITCH(block, ...)                      \
     switch (block) {                                     \
+        case 32: { constexpr int BS = 32; __VA_ARGS__; } break; \
+        case 64: { constexpr int BS = 64; __VA_ARGS__; } break; \
         case 128: { constexpr int BS = 128; __VA_ARGS__; } break; \
         case 256: { constexpr int BS = 256; __VA_ARGS__; } break; \
         case 512: { constexpr int BS = 512; __VA_ARGS__; } break; \
@@ -67,6 +69,8 @@ cudaError_t launch_gauss(const KArgs<R> &a, int block, int grid, cudaStream_t s,
         cfg.attrs = attr;
         cfg.numAttrs = priority ? 1 : 0;
         switch (block) {
+            case 32: cfg.blockDim = dim3(32); return cudaLaunchKernelEx(&cfg, k_gauss<32>, a);
+            case 64: cfg.blockDim = dim3(64); return cudaLaunchKernelEx(&cfg, k_gauss<64>, a);
             case 128: cfg.blockDim = dim3(128); return cudaLaunchKernelEx(&cfg, k_gauss<128>, a);
             case 256: cfg.blockDim = dim3(256); return cudaLaunchKernelEx(&cfg, k_gauss<256>, a);
             case 512: cfg.blockDim = dim3(512); return cudaLaunchKernelEx(&cfg, k_gauss<512>, a);
@@ -432,7 +436,9 @@ cudaError_t launch_system_blocks(const KArgs<R> &a, int block, int grid, long lo
     return cudaGetLastError();
 }
 
-template cudaError_t launch_system_blocks<SS_REAL>(const KArgs<SS_REAL> &, int, int, long long, cudaStream_t);
+// Explicit instantiations, split over three translation units per precision (SS_PART) so
+// that the build compiles them in parallel.
+#if SS_PART == 1  // the Heun passes, the split step, the measurement, the long-row passes
 template cudaError_t launch_predictor<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_corrector<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
 template cudaError_t launch_gauss<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t, int);
@@ -442,20 +448,24 @@ template cudaError_t launch_corrector_split<SS_REAL>(const KArgs<SS_REAL> &, int
 template int split_blocks_per_sm<SS_REAL>(int, int, int);
 template cudaError_t launch_measure<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_init_sphere<SS_REAL>(const KArgs<SS_REAL> &, cudaStream_t);
-template cudaError_t launch_persistent<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, long long, cudaStream_t);
-template int persistent_blocks_per_sm<SS_REAL>(int, int);
 template int step_blocks_per_sm<SS_REAL>(int, int);
 template int corrector_blocks_per_sm<SS_REAL>(int, bool, int);
+template cudaError_t launch_rows_field<SS_REAL>(const KArgs<SS_REAL> &, const SS_REAL *, const SS_REAL *,
+                                                const SS_REAL *, int, cudaStream_t);
+template int rows_blocks_per_sm<SS_REAL>();
+#elif SS_PART == 2  // many steps per launch, the demagnetising field
+template cudaError_t launch_system_blocks<SS_REAL>(const KArgs<SS_REAL> &, int, int, long long, cudaStream_t);
+template cudaError_t launch_persistent<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, long long, cudaStream_t);
+template int persistent_blocks_per_sm<SS_REAL>(int, int);
+template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
+#else  // Monte Carlo and the alternative integrators
 template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
 template cudaError_t launch_mc_colour_rec<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);
 template cudaError_t launch_mc_colour_warp<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);
 template int mc_blocks_per_sm<SS_REAL>(int, int);
-template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
 template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, int, cudaStream_t);
 template cudaError_t launch_sib<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
 template int alt_pass_blocks_per_sm<SS_REAL>(int, int);
-template cudaError_t launch_rows_field<SS_REAL>(const KArgs<SS_REAL> &, const SS_REAL *, const SS_REAL *,
-                                                const SS_REAL *, int, cudaStream_t);
-template int rows_blocks_per_sm<SS_REAL>();
+#endif
 
 }  // namespace ss

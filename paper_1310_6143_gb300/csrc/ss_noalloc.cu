@@ -10,7 +10,8 @@
 // live in `g_noalloc_scratch`.
 //
 // In host code the name g_noalloc_scratch is only a host-side stand-in for the device
-// array; its device address is obtained once per device with cudaGetSymbolAddress and
+// array; its device address is obtained with cudaGetSymbolAddress on every call (the tables
+// are uploaded again whenever the address differs from the last one seen on the device) and
 // passed to the kernels.  Calls share the array; calls that overlap on the GPU race.
 #include <cuda_runtime.h>
 
@@ -38,7 +39,7 @@ constexpr size_t kNaBytes = kNaStateOff + 9 * (size_t)kNaMax * sizeof(double);  
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
-// Device address of g_noalloc_scratch per device ordinal, found at the first call.
+// Device address of g_noalloc_scratch per device ordinal at the last table upload.
 std::mutex g_na_mutex;
 unsigned char *g_na_base[128] = {};
 
@@ -196,18 +197,19 @@ ss_status na_error(ss_status s, const char *msg) {
     return s;
 }
 
-// Device address of the static array on the current device; the first call per device
-// looks it up and uploads the tables (synchronous copy, no allocation).
+// Device address of the static array on the current device, looked up on every call (no
+// allocation); the tables are uploaded (synchronous copy) at the first call on the device and
+// again whenever the address has changed since.
 ss_status na_base(unsigned char **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_error(SS_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= 128) return na_error(SS_ERR_UNSUPPORTED, "device ordinal out of range");
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return na_error(SS_ERR_CUDA, "cudaGetSymbolAddress(g_noalloc_scratch) failed");
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_base[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return na_error(SS_ERR_CUDA, "cudaGetSymbolAddress(g_noalloc_scratch) failed");
+    if (g_na_base[dev] != (unsigned char *)p) {
         static double2 tab[kNaTabCount];
         build_bm_tables(tab);
         e = cudaMemcpy((unsigned char *)p + kNaTabOff, tab, sizeof(tab), cudaMemcpyHostToDevice);
@@ -240,6 +242,9 @@ extern "C" ss_status llg_heun_step_noalloc(const ss_noalloc_step *p, int64_t nst
         !finite_d(p->H_app[1]) || !finite_d(p->H_app[2]))
         return na_error(SS_ERR_INVALID_ARG, "llg_heun_step_noalloc: alpha, dt, gamma, T or H_app out of range");
     if (p->step0 < 0) return na_error(SS_ERR_INVALID_ARG, "llg_heun_step_noalloc: step0 < 0");
+    // the step index is the 32-bit Philox counter word: every step of the call must fit it
+    if (p->step0 > 0xFFFFFFFFll || nsteps > 0xFFFFFFFFll - p->step0)
+        return na_error(SS_ERR_INVALID_ARG, "llg_heun_step_noalloc: step0 + nsteps exceeds 2^32 - 1");
     if (nsteps == 0) return SS_OK;
     unsigned char *base = nullptr;
     ss_status st = na_base(&base);
@@ -283,8 +288,10 @@ extern "C" ss_status llg_heun_step_noalloc(const ss_noalloc_step *p, int64_t nst
         a.record = p->record ? p->record + 8 * k : nullptr;
         k_na_predictor<<<grid, kNaBlock, 0, s>>>(a);
         k_na_corrector<<<grid + 1, kNaBlock, 0, s>>>(a);
+        if (k == 0 || k + 1 == nsteps) {  // a launch failure stops the call at the first step
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return na_error(SS_ERR_CUDA, cudaGetErrorString(e));
+        }
     }
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return na_error(SS_ERR_CUDA, cudaGetErrorString(e));
     return SS_OK;
 }

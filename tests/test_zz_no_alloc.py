@@ -7,7 +7,9 @@ such a caller: it holds the system's arrays in device memory (allocated here, by
 test, with torch), calls the new entry point twice in a row through the C ABI, and
 compares spins and per-step records with a handle created by spin_system_create and
 advanced by llg_heun_step, within the FP64 parity tolerance of the other tests (1e-12).
-It also checks that a system larger than SS_NOALLOC_MAX_SPINS is refused.
+Around the second call the device's free memory does not change (an allocation of the
+working buffers, 9.5 MB, would show).  It also checks that a system larger than
+SS_NOALLOC_MAX_SPINS, and steps past the 32-bit counter, are refused.
 """
 import ctypes
 
@@ -115,8 +117,10 @@ def test_noalloc_matches_handle_two_calls(lib):
     # second call continues from the first call's output: steps k1 .. k1+k2-1
     p.step0 = k1
     p.record = rec.data_ptr() + k1 * 8 * 8
+    free_before = torch.cuda.mem_get_info()[0]
     assert lib.llg_heun_step_noalloc(ctypes.byref(p), k2, ctypes.c_void_p(stream)) == 0
     torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before  # nothing allocated on the device
     got2 = torch.stack(S, 1).cpu().numpy()
     assert np.abs(got2 - ref2).max() <= TOL
     r = rec.cpu().numpy()
@@ -135,3 +139,12 @@ def test_noalloc_rejects_oversized_system(lib):
     st = lib.llg_heun_step_noalloc(ctypes.byref(p), 1, None)
     assert st == 1  # SS_ERR_INVALID_ARG
     assert "SS_NOALLOC_MAX_SPINS" in B.load().ss_last_error(None).decode()
+
+
+def test_noalloc_rejects_steps_past_the_counter(lib):
+    p = NoAllocStep()
+    p.n = 8
+    p.dt = 1e-16
+    p.row_ptr = p.col = p.J = p.mu_s = p.k_u = p.easy_axis = p.sx = p.sy = p.sz = 1  # never dereferenced
+    p.step0 = 2**32 - 3
+    assert lib.llg_heun_step_noalloc(ctypes.byref(p), 3, None) == 1  # SS_ERR_INVALID_ARG: step 2^32 - 1
