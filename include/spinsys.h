@@ -498,6 +498,56 @@ typedef struct {
 
 ss_status llg_heun_step_noalloc(const ss_noalloc_step *p, int64_t nsteps, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------------
+ * Slab decomposition of one system (the paper's parallelisation, Appendix C: each
+ * processor owns a geometric slab of the system, sorted into core spins, boundary spins
+ * and halo copies of its neighbours' boundary spins, and the halo is passed between
+ * processors twice per time step -- after the predictor, before the corrector, and after
+ * the corrector, before the next predictor -- while core spins hide the transfer).
+ *
+ * spin_slab_create makes the handle of slab `slab` (0 <= slab < nslabs) of the system `p`:
+ * it owns the contiguous global index range [lo, hi), lo = n slab / nslabs, hi = n (slab+1)
+ * / nslabs -- a slab along the slowest index of a lattice numbered plane by plane, as the
+ * workloads' lattices are.  Its arrays hold the owned spins first (local index g - lo), then
+ * halo copies of every other spin an owned row names, in global order; the owned rows are
+ * kept in CSR order with renumbered columns, the halo copies have no rows.  Every owned spin
+ * draws its thermal field from the Philox counter of its GLOBAL index, so a decomposed run
+ * gives, spin for spin and bit for bit, the states of the undecomposed run once the halos are
+ * refreshed as above.  Scalar exchange only (SS_ERR_UNSUPPORTED for tensors); llg_heun_step,
+ * Monte Carlo, the alternative integrators, the demagnetising field, warp-per-row exchange,
+ * the kernel timers and the autotuner are refused on a slab (SS_ERR_UNSUPPORTED): a slab
+ * sums a row per thread and advances by spin_system_heun_pass.
+ * Tiles hold owned spins only, those with a halo neighbour (boundary tiles) first.
+ * --------------------------------------------------------------------------------- */
+typedef struct {
+    int64_t lo, hi;          /* owned global index range                               */
+    int64_t n_halo;          /* halo copies (local indices hi - lo .. hi - lo + n_halo - 1) */
+    int64_t num_runs;        /* maximal runs of consecutive global indices in the halo  */
+    int64_t boundary_tiles;  /* tiles 0 .. boundary_tiles-1 hold spins with halo neighbours */
+    int64_t num_tiles;
+    int32_t nslabs, slab;
+} ss_slab_info;
+
+ss_status spin_slab_create(const ss_params *p, int32_t nslabs, int32_t slab, ss_system **out);
+ss_status spin_slab_info(ss_system *h, ss_slab_info *out);
+
+/* The halo runs of a slab into out3[3 * num_runs] (cap >= num_runs): (first global index,
+ * length, first local index) per run, in global order. */
+ss_status spin_slab_halo_runs(ss_system *h, int64_t *out3, int64_t cap);
+
+/* Device pointers of the x, y, z arrays of the state S (which = 0) or of the predictor
+ * spins S' (which = 1), SoA in the working precision; valid until spin_system_destroy. */
+ss_status get_state_device(ss_system *h, int32_t which, const void **x, const void **y, const void **z);
+
+/* One pass of the Heun step over tiles [tile0, tile0 + ntiles) (asynchronous): pass 0 the
+ * predictor, 1 the corrector (S' of the halo must be current), 2 the end of the step (the
+ * record of the step's state from every tile's predictor sums, then the step counter
+ * advances).  A step is pass 0 over all tiles, a halo refresh of S', pass 1 over all tiles,
+ * pass 2, a halo refresh of S -- with the boundary tiles' passes first, so that the halo
+ * transfer overlaps the core tiles' passes.  Thread-per-row exchange only; SS_ERR_INVALID_ARG
+ * for a bad pass or tile range. */
+ss_status spin_system_heun_pass(ss_system *h, int32_t pass, int64_t tile0, int64_t ntiles);
+
 /* Human-readable message of the last failure on this handle ("" if none). */
 const char *ss_last_error(ss_system *h);
 const char *ss_status_string(ss_status s);

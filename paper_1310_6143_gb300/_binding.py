@@ -32,6 +32,7 @@ EXPORTS = (
     "spin_system_set_exchange_rows", "spin_system_time_rows", "llg_semi_implicit_step",
     "ss_debug_fail_allocations", "ss_debug_live_bytes",
     "get_demag_field",
+    "spin_slab_create", "spin_slab_info", "spin_slab_halo_runs", "get_state_device", "spin_system_heun_pass",
     "ss_last_error", "ss_status_string",
 )
 
@@ -86,6 +87,22 @@ class SSInfo(ctypes.Structure):
         ("exchange_rows", ctypes.c_int32),
         ("row_patterns", ctypes.c_int32),
         ("gaussian_pass", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SSSlabInfo(ctypes.Structure):
+    _fields_ = [
+        ("lo", ctypes.c_int64),
+        ("hi", ctypes.c_int64),
+        ("n_halo", ctypes.c_int64),
+        ("num_runs", ctypes.c_int64),
+        ("boundary_tiles", ctypes.c_int64),
+        ("num_tiles", ctypes.c_int64),
+        ("nslabs", ctypes.c_int32),
+        ("slab", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -148,6 +165,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "ss_debug_philox": [P, P, I64, P],
         "ss_debug_gaussians": [U64, U32, U32, I64, I32, P],
         "ss_debug_fp64_rate": [I32, P],
+        "spin_slab_create": [P, I32, I32, P],
+        "spin_slab_info": [P, P],
+        "spin_slab_halo_runs": [P, P, I64],
+        "get_state_device": [P, I32, P, P, P],
+        "spin_system_heun_pass": [P, I32, I64, I64],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)

@@ -116,6 +116,14 @@ struct ss_system {
     int32_t npat = 0;                   // 0: no patterns (more than kMaxPatterns, rows too long)
     int32_t pat_w = 8;                  // slots of a pattern row (8 or 16, see KArgs)
     bool use_pat = true;                // spin_system_set_row_patterns
+    // Slab of a decomposed system (spin_slab_create): the owned spins are the first slab_own
+    // of the arrays, the halo copies follow; tiles cover the owned spins, boundary tiles first
+    int64_t slab_own = -1;              // -1: not a slab
+    int64_t slab_lo = 0, slab_hi = 0;   // owned global index range
+    int32_t nslabs = 0, slab_index = 0;
+    int64_t slab_boundary_tiles = 0;
+    std::vector<int64_t> slab_runs;     // halo runs: (global start, length, local start)
+    std::vector<uint8_t> slab_edge;     // owned spin with a neighbour in the halo
     int gauss_mode = 0;                 // spin_system_set_gaussian_pass: 0 fused, 1 split, 2 split
                                         // with the next step's Gaussian pass running concurrently
     void *ahead2[3] = {};               // the split step's Gaussians of odd steps (allocated on use)
@@ -513,6 +521,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.sched_step0 = h->sched_step0;
     a.err = reinterpret_cast<unsigned int *>(h->ctl + 1);
     a.ticket = reinterpret_cast<unsigned int *>(h->ctl + 1) + 1;
+    a.advance = 1;
     a.bar_count = reinterpret_cast<unsigned int *>(h->ctl + 2);
     a.bar_gen = reinterpret_cast<unsigned int *>(h->ctl + 2) + 1;
     a.tab = h->tab;
@@ -806,6 +815,17 @@ ss_status build_tiles(ss_system *h) {
             t.sys = s;
             tiles.push_back(t);
         }
+    }
+    if (h->slab_own >= 0) {  // a slab: the tiles holding spins with halo neighbours first
+        std::vector<TileDesc> edge, inner;
+        for (const TileDesc &t : tiles) {
+            bool e = false;
+            for (int32_t k = 0; k < t.count && !e; ++k) e = h->slab_edge[(size_t)(t.start + k)] != 0;
+            (e ? edge : inner).push_back(t);
+        }
+        h->slab_boundary_tiles = (int64_t)edge.size();
+        tiles = edge;
+        tiles.insert(tiles.end(), inner.begin(), inner.end());
     }
     st[h->nsys] = (int32_t)tiles.size();
     if (h->tiles) dfree(h, h->tiles);
@@ -1121,7 +1141,14 @@ ss_status set_rows(ss_system *h, int32_t mode) {
     return SS_OK;
 }
 
-ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) {
+// A slab's owned range and Philox base, passed from spin_slab_create to create_impl.
+struct SlabInit {
+    int64_t n_own;                   // owned spins (the first n_own of the local arrays)
+    int64_t pbase;                   // global index of the first owned spin
+    const std::vector<uint8_t> *edge;  // [n_own] owned spins with a halo neighbour
+};
+
+ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out, const SlabInit *slab = nullptr) {
     if (!out) return fail(nullptr, SS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!systems || count < 1) return fail(nullptr, SS_ERR_INVALID_ARG, "need at least one system");
@@ -1160,8 +1187,12 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
     bool all_pos = true;
     for (int s = 0; s < count; ++s) {
         h->sys_offset.push_back(hs[s].offset);
-        h->sys_n.push_back(systems[s].n);
+        h->sys_n.push_back(slab ? slab->n_own : systems[s].n);  // a slab integrates its owned spins
         all_pos = all_pos && systems[s].pos != nullptr;
+    }
+    if (slab) {
+        h->slab_own = slab->n_own;
+        h->slab_edge = *slab->edge;
     }
     if (all_pos) {  // kept for the macrocell demagnetising field
         for (int s = 0; s < count; ++s) {
@@ -1176,7 +1207,8 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         SysDesc &d = h->hsys[s];
         std::memset(&d, 0, sizeof(d));
         d.offset = hs[s].offset;
-        d.n = p->n;
+        d.n = slab ? slab->n_own : p->n;
+        d.pbase = slab ? slab->pbase : 0;
         d.key0 = (uint32_t)(p->seed & 0xffffffffull);
         d.key1 = (uint32_t)(p->seed >> 32);
         d.ctr2 = p->sys_id;
@@ -1188,7 +1220,7 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         d.sqrtTf = (float)d.sqrtT;
         h->Tsys.push_back(p->T);
         double ms = 0.0;
-        for (int64_t i = 0; i < p->n; ++i) ms += p->mu_s[i];
+        for (int64_t i = 0; i < d.n; ++i) ms += p->mu_s[i];
         d.msum = ms;
     }
     auto cleanup = [&](ss_status st) {
@@ -1234,9 +1266,10 @@ ss_status create_impl(const ss_params *systems, int32_t count, ss_system **out) 
         while (slots < 8 && 2 * slots <= spt) slots *= 2;
         h->tile = slots * h->block;
         h->ahead_q = slots >= 8 ? 4 : 6;  // the faster split on GB300 for each case
+        if (slab) h->ahead_q = 0;         // a slab's passes draw their own Gaussians
     }
     st = build_tiles(h);
-    if (st == SS_OK) st = set_rows(h, 0);
+    if (st == SS_OK) st = set_rows(h, slab ? 1 : 0);  // a slab's passes sum a row per thread
     if (st != SS_OK) return cleanup(st);
     st = h->precision == SS_FP32_MIXED ? init_random<float>(h, hs) : init_random<double>(h, hs);
     if (st != SS_OK) return cleanup(st);
@@ -1319,6 +1352,31 @@ ss_status time_kernels_impl(ss_system *h, int32_t nsteps, double out_ms[4]) {
     out_ms[2] = tc / nsteps;
     out_ms[3] = all / nsteps;
     return check_device_flags(h);
+}
+
+template <typename R>
+ss_status heun_pass_impl(ss_system *h, int32_t pass, int64_t tile0, int64_t ntiles) {
+    KArgs<R> a = make_args<R>(h);
+    if (pass == 2) {  // the step's record from every tile's partials, then the next step
+        SS_CUDA(h, launch_finalize_ring(h->sys, h->sys_tiles, h->nsys, h->partials, h->rec, h->rec_cap, h->ctl,
+                                        h->stream));
+        SS_CUDA(h, launch_advance_step(h->ctl, h->stream));
+        h->step += 1;
+        return SS_OK;
+    }
+    if (ntiles == 0) return SS_OK;
+    a.tiles = h->tiles + tile0;
+    a.ntiles = ntiles;
+    a.partials = h->partials + tile0 * kPartComps;
+    a.advance = 0;
+    if (pass == 0) {
+        const int g = (int)std::min<int64_t>(ntiles, step_grid(h));
+        SS_CUDA(h, launch_predictor<R>(a, h->block, g, h->stream));
+    } else {
+        const int g = (int)std::min<int64_t>(ntiles, corrector_grid(h));
+        SS_CUDA(h, launch_corrector<R>(a, h->block, g, 0, h->stream));
+    }
+    return SS_OK;
 }
 
 // ----------------------------------------------------------------------------------
@@ -1885,6 +1943,8 @@ static ss_status advance_steps(ss_system *h, int64_t n);
 ss_status llg_heun_step(ss_system *h, int64_t n) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
+    if (h->slab_own >= 0)
+        return fail(h, SS_ERR_UNSUPPORTED, "a slab advances by spin_system_heun_pass with halo exchanges");
     if (n < 0) return fail(h, SS_ERR_INVALID_ARG, "n must be >= 0");
     if (n == 0) return SS_OK;
     if (!h->demag_on) return advance_steps(h, n);
@@ -1955,6 +2015,7 @@ static ss_status advance_steps(ss_system *h, int64_t n) {
 ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
+    if (h->slab_own >= 0) return fail(h, SS_ERR_UNSUPPORTED, "not available on a slab handle");
     if (n < 0) return fail(h, SS_ERR_INVALID_ARG, "n must be >= 0");
     if (iterations < 1 || iterations > 1000) return fail(h, SS_ERR_INVALID_ARG, "iterations must be 1..1000");
     auto enqueue = [h, iterations](int64_t k) {
@@ -1967,6 +2028,7 @@ ss_status llg_midpoint_step(ss_system *h, int64_t n, int32_t iterations) {
 ss_status llg_semi_implicit_step(ss_system *h, int64_t n) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
+    if (h->slab_own >= 0) return fail(h, SS_ERR_UNSUPPORTED, "not available on a slab handle");
     if (n < 0) return fail(h, SS_ERR_INVALID_ARG, "n must be >= 0");
     auto enqueue = [h](int64_t k) {
         return h->precision == SS_FP32_MIXED ? enqueue_sib<float>(h, k) : enqueue_sib<double>(h, k);
@@ -1977,6 +2039,7 @@ ss_status llg_semi_implicit_step(ss_system *h, int64_t n) {
 ss_status set_demag(ss_system *h, double cell_size, double atom_volume, int32_t every) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
+    if (h->slab_own >= 0) return fail(h, SS_ERR_UNSUPPORTED, "not available on a slab handle");
     if (!std::isfinite(cell_size)) return fail(h, SS_ERR_INVALID_ARG, "cell_size must be finite");
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
     drop_graph(h);  // captured launches hold the previous arguments
@@ -2022,6 +2085,7 @@ ss_status get_demag_field(ss_system *h, double *out3n) {
 ss_status mc_step(ss_system *h, int64_t nsteps) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
+    if (h->slab_own >= 0) return fail(h, SS_ERR_UNSUPPORTED, "not available on a slab handle");
     if (nsteps < 0) return fail(h, SS_ERR_INVALID_ARG, "nsteps must be >= 0");
     if (nsteps == 0) return SS_OK;
     st = mc_prepare(h);
@@ -2252,6 +2316,7 @@ ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile) {
 ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
+    if (h->slab_own >= 0) return fail(h, SS_ERR_UNSUPPORTED, "not available on a slab handle");
     if (mode < 0 || mode > 2) return fail(h, SS_ERR_INVALID_ARG, "mode must be 0 (automatic), 1 or 2");
     SS_CUDA(h, cudaStreamSynchronize(h->stream));
     return set_rows(h, mode);
@@ -2298,6 +2363,147 @@ ss_status spin_system_set_draw_ahead(ss_system *h, int32_t eighths) {
     return build_tiles(h);
 }
 
+// ----------------------------------------------------------------------------------
+// Slab decomposition of one system (Appendix C: geometric decomposition with core, boundary
+// and halo spins, the halo passed between processors twice per time step)
+// ----------------------------------------------------------------------------------
+
+ss_status spin_slab_create(const ss_params *p, int32_t nslabs, int32_t slab, ss_system **out) {
+    if (!out) return fail(nullptr, SS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, SS_ERR_INVALID_ARG, "params is NULL");
+    ss_status st = validate(p, 0);
+    if (st != SS_OK) return st;
+    if (nslabs < 1 || slab < 0 || slab >= nslabs || nslabs > p->n)
+        return fail(nullptr, SS_ERR_INVALID_ARG, "need 1 <= nslabs <= n and 0 <= slab < nslabs");
+    if (p->J_tensor) return fail(nullptr, SS_ERR_UNSUPPORTED, "slabs take scalar exchange");
+    const int64_t n = p->n;
+    const int64_t lo = n * slab / nslabs, hi = n * (slab + 1) / nslabs, own = hi - lo;
+    // halo: every neighbour of an owned spin outside [lo, hi), sorted
+    std::vector<int64_t> halo;
+    std::vector<uint8_t> edge((size_t)own, 0);
+    for (int64_t i = lo; i < hi; ++i)
+        for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) {
+            const int64_t j = p->col[k];
+            if (j < lo || j >= hi) {
+                halo.push_back(j);
+                edge[(size_t)(i - lo)] = 1;
+            }
+        }
+    std::sort(halo.begin(), halo.end());
+    halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+    const int64_t nh = (int64_t)halo.size(), nt = own + nh;
+    auto local = [&](int64_t g) -> int64_t {
+        if (g >= lo && g < hi) return g - lo;
+        return own + (int64_t)(std::lower_bound(halo.begin(), halo.end(), g) - halo.begin());
+    };
+    // local arrays: the owned rows (columns renumbered), empty rows for the halo copies
+    std::vector<int64_t> rp((size_t)nt + 1, 0);
+    std::vector<int32_t> col;
+    std::vector<double> J, mu((size_t)nt), ku((size_t)nt), ea, kn, kc, S0, pos;
+    col.reserve((size_t)(p->row_ptr[hi] - p->row_ptr[lo]));
+    for (int64_t i = lo; i < hi; ++i) {
+        for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) {
+            col.push_back((int32_t)local(p->col[k]));
+            J.push_back(p->J[k]);
+        }
+        rp[(size_t)(i - lo) + 1] = (int64_t)col.size();
+    }
+    for (int64_t i = own; i < nt; ++i) rp[(size_t)i + 1] = (int64_t)col.size();
+    auto global = [&](int64_t l) { return l < own ? lo + l : halo[(size_t)(l - own)]; };
+    auto take = [&](const double *src, int w, std::vector<double> &dst) {
+        if (!src) return;
+        dst.resize((size_t)nt * w);
+        for (int64_t l = 0; l < nt; ++l)
+            for (int c = 0; c < w; ++c) dst[(size_t)l * w + c] = src[global(l) * w + c];
+    };
+    for (int64_t l = 0; l < nt; ++l) {
+        mu[(size_t)l] = p->mu_s[global(l)];
+        ku[(size_t)l] = p->k_u[global(l)];
+    }
+    take(p->easy_axis, 3, ea);
+    take(p->K_neel, 6, kn);
+    take(p->k_c, 1, kc);
+    take(p->S0, 3, S0);
+    take(p->pos, 3, pos);
+    ss_params q = *p;
+    q.n = nt;
+    q.row_ptr = rp.data();
+    q.col = col.data();
+    q.J = J.data();
+    q.mu_s = mu.data();
+    q.k_u = ku.data();
+    q.easy_axis = p->easy_axis ? ea.data() : nullptr;
+    q.K_neel = p->K_neel ? kn.data() : nullptr;
+    q.k_c = p->k_c ? kc.data() : nullptr;
+    q.S0 = p->S0 ? S0.data() : nullptr;
+    q.pos = p->pos ? pos.data() : nullptr;
+    q.flags &= ~(uint32_t)SS_FLAG_CHECK_SYMMETRY;  // the local list is one-sided at the halo
+    const SlabInit init{own, lo, &edge};
+    ss_system *h = nullptr;
+    st = create_impl(&q, 1, &h, &init);
+    if (st != SS_OK) return st;
+    h->slab_lo = lo;
+    h->slab_hi = hi;
+    h->nslabs = nslabs;
+    h->slab_index = slab;
+    for (size_t r = 0; r < halo.size();) {  // maximal runs of consecutive global indices
+        size_t e = r + 1;
+        while (e < halo.size() && halo[e] == halo[e - 1] + 1) ++e;
+        h->slab_runs.push_back(halo[r]);
+        h->slab_runs.push_back((int64_t)(e - r));
+        h->slab_runs.push_back(own + (int64_t)r);
+        r = e;
+    }
+    *out = h;
+    return SS_OK;
+}
+
+ss_status spin_slab_info(ss_system *h, ss_slab_info *o) {
+    if (!h || !o) return fail(h, SS_ERR_INVALID_ARG, "NULL argument");
+    if (h->slab_own < 0) return fail(h, SS_ERR_INVALID_ARG, "not a slab handle");
+    o->lo = h->slab_lo;
+    o->hi = h->slab_hi;
+    o->n_halo = h->n - h->slab_own;
+    o->num_runs = (int64_t)h->slab_runs.size() / 3;
+    o->boundary_tiles = h->slab_boundary_tiles;
+    o->num_tiles = h->ntiles;
+    o->nslabs = h->nslabs;
+    o->slab = h->slab_index;
+    return SS_OK;
+}
+
+ss_status spin_slab_halo_runs(ss_system *h, int64_t *out3, int64_t cap) {
+    if (!h || !out3) return fail(h, SS_ERR_INVALID_ARG, "NULL argument");
+    if (h->slab_own < 0) return fail(h, SS_ERR_INVALID_ARG, "not a slab handle");
+    const int64_t nr = (int64_t)h->slab_runs.size() / 3;
+    if (cap < nr) return fail(h, SS_ERR_INVALID_ARG, "cap %lld below the %lld runs", (long long)cap, (long long)nr);
+    std::copy(h->slab_runs.begin(), h->slab_runs.end(), out3);
+    return SS_OK;
+}
+
+ss_status get_state_device(ss_system *h, int32_t which, const void **x, const void **y, const void **z) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (which < 0 || which > 1 || !x || !y || !z) return fail(h, SS_ERR_INVALID_ARG, "which must be 0 or 1");
+    *x = h->state[3 * which];
+    *y = h->state[3 * which + 1];
+    *z = h->state[3 * which + 2];
+    return SS_OK;
+}
+
+ss_status spin_system_heun_pass(ss_system *h, int32_t pass, int64_t tile0, int64_t ntiles) {
+    ss_status st = usable(h);
+    if (st != SS_OK) return st;
+    if (pass < 0 || pass > 2) return fail(h, SS_ERR_INVALID_ARG, "pass must be 0, 1 or 2");
+    if (tile0 < 0 || ntiles < 0 || tile0 + ntiles > h->ntiles)
+        return fail(h, SS_ERR_INVALID_ARG, "tiles [%lld, %lld) outside [0, %lld)", (long long)tile0,
+                    (long long)(tile0 + ntiles), (long long)h->ntiles);
+    if (h->rows || h->demag_on) return fail(h, SS_ERR_UNSUPPORTED, "passes take thread-per-row exchange, no demag");
+    return h->precision == SS_FP32_MIXED ? heun_pass_impl<float>(h, pass, tile0, ntiles)
+                                         : heun_pass_impl<double>(h, pass, tile0, ntiles);
+}
+
 ss_status spin_system_info(ss_system *h, ss_info *o) {
     if (!h || !o) return fail(h, SS_ERR_INVALID_ARG, "NULL argument");
     o->n = h->n;
@@ -2322,6 +2528,7 @@ ss_status spin_system_info(ss_system *h, ss_info *o) {
 ss_status spin_system_time_kernels(ss_system *h, int32_t nsteps, double out_ms[3]) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
+    if (h->slab_own >= 0) return fail(h, SS_ERR_UNSUPPORTED, "not available on a slab handle");
     if (nsteps < 1 || !out_ms) return fail(h, SS_ERR_INVALID_ARG, "nsteps >= 1 and out_ms needed");
     double t[4];
     st = h->precision == SS_FP32_MIXED ? time_kernels_impl<float>(h, nsteps, t) : time_kernels_impl<double>(h, nsteps, t);
@@ -2334,6 +2541,7 @@ ss_status spin_system_time_kernels(ss_system *h, int32_t nsteps, double out_ms[3
 ss_status spin_system_time_passes(ss_system *h, int32_t nsteps, double out_ms[4]) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
+    if (h->slab_own >= 0) return fail(h, SS_ERR_UNSUPPORTED, "not available on a slab handle");
     if (nsteps < 1 || !out_ms) return fail(h, SS_ERR_INVALID_ARG, "nsteps >= 1 and out_ms needed");
     return h->precision == SS_FP32_MIXED ? time_kernels_impl<float>(h, nsteps, out_ms)
                                          : time_kernels_impl<double>(h, nsteps, out_ms);
@@ -2403,6 +2611,7 @@ static bool autotune_lookup(const std::string &path, const std::string &key, int
 ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_info) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
+    if (h->slab_own >= 0) return fail(h, SS_ERR_UNSUPPORTED, "not available on a slab handle");
     if (trial_steps < 1) return fail(h, SS_ERR_INVALID_ARG, "trial_steps must be >= 1");
     st = check_device_flags(h);
     if (st != SS_OK) return st;

@@ -38,6 +38,8 @@ struct SysDesc {
     uint32_t key0, key1; // Philox key = (seed low word, seed high word)
     uint32_t ctr2;       // third counter word (system id)
     uint32_t pad;
+    int64_t pbase;       // Philox spin index of the system's first spin (a slab's first global
+                         // index; 0 otherwise): spin i draws with word i - offset + pbase
     double H[3];         // applied field, T
     double sqrtT;        // square root of the temperature, sqrt(K)
     double msum;         // sum of mu_s over the system, J/T
@@ -145,6 +147,8 @@ struct KArgs {
     int64_t sched_step0;
     unsigned int *err;        // bit 0: non-finite spin, bit 1: barrier timeout
     unsigned int *ticket;     // completion counter of the corrector launch
+    int advance;              // 1: the corrector's last block advances the step counter (0 for a
+                              // corrector pass over part of the tiles)
     const double2 *tab;       // Box-Muller tables, kTabCount entries (build_bm_tables)
     const float4 *fftab;      // double-float tables, kFFTabFloat4 entries (build_ff_tables)
     unsigned int *bar_count;  // grid barrier of the persistent kernel

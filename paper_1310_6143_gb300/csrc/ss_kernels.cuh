@@ -480,7 +480,7 @@ __device__ __forceinline__ void predictor_tile(const KArgs<R> &a, const TileDesc
     const SysDesc &sd = a.sys[td.sys];
     const R sqrtT = sqrtT_of_step(a, step, sd);
     const uint32_t key0 = sd.key0, key1 = sd.key1, ctr2 = sd.ctr2;
-    const int64_t off = sd.offset;
+    const int64_t off = sd.offset - sd.pbase;  // Philox spin index i - off
     const R ha0 = sys_H(sd, 0, R()), ha1 = sys_H(sd, 1, R()), ha2 = sys_H(sd, 2, R());
     TermAcc<R> ta;
     ta.reset();
@@ -556,7 +556,7 @@ __device__ __forceinline__ void corrector_tile(const KArgs<R> &a, const TileDesc
     // this puts transform work next to the corrector's memory traffic.
     const R sqrtT_next = tab ? sqrtT_of_step(a, step + 1, sd) : (R)0;
     const uint32_t key0 = sd.key0, key1 = sd.key1, ctr2 = sd.ctr2;
-    const int64_t off = sd.offset;
+    const int64_t off = sd.offset - sd.pbase;  // Philox spin index i - off
     const R ha0 = sys_H(sd, 0, R()), ha1 = sys_H(sd, 1, R()), ha2 = sys_H(sd, 2, R());
     int rot = (threadIdx.x >> 5) % a.slots;  // the predictor's rotated slot index
     for (int k = threadIdx.x; k < td.count; k += BS, rot = rot + 1 == a.slots ? 0 : rot + 1) {
@@ -734,8 +734,10 @@ __global__ void __launch_bounds__(BS, sizeof(R) == 8 ? 0 : SS_CORR_WARPS * 32 / 
         const unsigned int done = atomicAdd(a.ticket, 1u);
         if (done == gridDim.x - 1) {
             *a.ticket = 0u;
-            if (DrawAhead) *a.g_step = step + 1ull;
-            *a.step = step + 1ull;
+            if (a.advance) {
+                if (DrawAhead) *a.g_step = step + 1ull;
+                *a.step = step + 1ull;
+            }
             __threadfence();
         }
     }
@@ -762,7 +764,7 @@ __global__ void __launch_bounds__(BS) k_gauss(const KArgs<float> a) {
         const SysDesc &sd = a.sys[td.sys];
         if (!(sqrtT_of_step(a, step, sd) > 0.0f)) continue;  // no thermal field: nothing reads them
         const uint32_t key0 = sd.key0, key1 = sd.key1, ctr2 = sd.ctr2;
-        const int64_t off = sd.offset;
+        const int64_t off = sd.offset - sd.pbase;  // Philox spin index i - off
         for (int k = threadIdx.x; k < td.count; k += BS) {
             const int64_t i = td.start + k;
             const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)step, ctr2, 0u, key0, key1);
@@ -894,7 +896,8 @@ __global__ void k_init_sphere(const KArgs<R> a) {
         const SysDesc &sd = a.sys[td.sys];
         for (int k = threadIdx.x; k < td.count; k += blockDim.x) {
             const int64_t i = td.start + k;
-            const Philox4 w = philox4x32_10((uint32_t)(i - sd.offset), 0xFFFFFFFFu, sd.ctr2, 1u, sd.key0, sd.key1);
+            const Philox4 w =
+                philox4x32_10((uint32_t)(i - sd.offset + sd.pbase), 0xFFFFFFFFu, sd.ctr2, 1u, sd.key0, sd.key1);
             double g0, g1, g2;
             box_muller3(w, tab, g0, g1, g2);
             const double inv = 1.0 / sqrt(g0 * g0 + g1 * g1 + g2 * g2);
@@ -1264,7 +1267,7 @@ __device__ __forceinline__ void alt_first_pass(const KArgs<R> &a, const SmemTabl
             if (sqrtT > (R)0) {
                 const R sig = m.sig * sqrtT;
                 const Philox4 w =
-                    philox4x32_10((uint32_t)(i - sd.offset), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
+                    philox4x32_10((uint32_t)(i - sd.offset + sd.pbase), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
                 double g0, g1, g2;
                 box_muller3(w, tab, g0, g1, g2);
                 t0 = sig * narrow<R>(g0);
@@ -1491,7 +1494,7 @@ __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int
     } else {
         par = m.par_sys[mt.sys];
     }
-    const uint32_t spin = (uint32_t)(i - sd.offset);
+    const uint32_t spin = (uint32_t)(i - sd.offset + sd.pbase);
     const Philox4 wa = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 2u, sd.key0, sd.key1);
     const Philox4 wb = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 3u, sd.key0, sd.key1);
     const int move = (int)(((uint64_t)wb.w0 * 3u) >> 32);

@@ -45,11 +45,13 @@ class SpinSystem:
     ``alpha``, ``dt``, ``T``, ``H``, ``seed``, ``sys_id`` and ``S0`` may be given per
     system as sequences.  ``precision`` is "fp64" or "fp32" (FP32 storage and field/LLG
     arithmetic with FP64 thermal transform and FP64 reductions).
+    ``slab=(nslabs, index)`` makes the handle of one slab of a single lattice (the owned
+    global range plus halo copies, advanced by ``heun_pass``; see ``paper_1310_6143_gb300.slab``).
     """
 
     def __init__(self, lattices: SpinLattice | Sequence[SpinLattice], *, alpha=0.1, dt=1e-16, T=0.0,
                  H=(0.0, 0.0, 0.0), seed=1, sys_id=None, precision="fp64", S0=None, init_random=False,
-                 gamma=0.0, check_symmetry=False, stream=None):
+                 gamma=0.0, check_symmetry=False, stream=None, slab=None):
         self._lib = B.load()
         self._h = ctypes.c_void_p()
         lats = [lattices] if isinstance(lattices, SpinLattice) else list(lattices)
@@ -98,12 +100,20 @@ class SpinSystem:
             p.sys_id = int(ids[s]) & 0xFFFFFFFF
             p.precision = _PREC[precision]
             p.flags = (B.SS_FLAG_CHECK_SYMMETRY if check_symmetry else 0) | (B.SS_FLAG_INIT_RANDOM if init_random else 0)
-        if count == 1:
+        if slab is not None:
+            if count != 1:
+                raise ValueError("a slab handle decomposes one lattice")
+            st = self._lib.spin_slab_create(ctypes.byref(params[0]), int(slab[0]), int(slab[1]), ctypes.byref(self._h))
+        elif count == 1:
             st = self._lib.spin_system_create(ctypes.byref(params[0]), ctypes.byref(self._h))
         else:
             st = self._lib.spin_batch_create(params, count, ctypes.byref(self._h))
         B.check(st, None)
         self.n = int(sum(l.n for l in lats))
+        self.slab = None
+        if slab is not None:
+            si = self.slab_info()
+            self.n = int(si["hi"] - si["lo"] + si["n_halo"])  # owned spins, then the halo copies
         self.num_systems = count
         self.sizes = [l.n for l in lats]
         self.offsets = list(np.cumsum([0] + self.sizes[:-1]))
@@ -275,6 +285,36 @@ class SpinSystem:
         self._check(self._lib.get_spins_device(self._h, ctypes.byref(px), ctypes.byref(py), ctypes.byref(pz)))
         ts = "<f4" if self.precision != "fp64" else "<f8"
         return tuple(torch.as_tensor(_DeviceArray(p.value, self.n, ts), device="cuda") for p in (px, py, pz))
+
+    def state_device(self, which: int = 0):
+        """Zero-copy torch views (x, y, z) of the state S (which=0) or the predictor spins S'
+        (which=1); the buffers live as long as the handle."""
+        import torch
+
+        px, py, pz = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        self._check(self._lib.get_state_device(self._h, int(which), ctypes.byref(px), ctypes.byref(py),
+                                               ctypes.byref(pz)))
+        ts = "<f4" if self.precision != "fp64" else "<f8"
+        return tuple(torch.as_tensor(_DeviceArray(p.value, self.n, ts), device="cuda") for p in (px, py, pz))
+
+    def slab_info(self) -> dict:
+        """The slab's ranges and tile split (refreshed: a new launch shape re-tiles)."""
+        si = B.SSSlabInfo()
+        self._check(self._lib.spin_slab_info(self._h, ctypes.byref(si)))
+        self.slab = si.as_dict()
+        return self.slab
+
+    def halo_runs(self) -> np.ndarray:
+        """(num_runs, 3) int64: first global index, length, first local index of each halo run."""
+        nr = int(self.slab["num_runs"]) if self.slab else 0
+        out = np.zeros((max(nr, 1), 3), dtype=np.int64)
+        self._check(self._lib.spin_slab_halo_runs(self._h, B.ptr(out), nr))
+        return out[:nr]
+
+    def heun_pass(self, which: int, tile0: int, ntiles: int):
+        """Enqueue pass ``which`` (0 predictor, 1 corrector, 2 end of step) over tiles
+        [tile0, tile0 + ntiles) on the handle's stream."""
+        self._check(self._lib.spin_system_heun_pass(self._h, int(which), int(tile0), int(ntiles)))
 
     def magnetisation(self, sys: int = 0) -> np.ndarray:
         out = np.zeros(4)
