@@ -126,8 +126,14 @@ typedef enum {
     SS_EXEC_GRAPH = 2,     /* CUDA graphs of captured step launches                 */
     SS_EXEC_PERSISTENT = 3, /* one cooperative launch runs many steps, with a bounded
                               grid barrier between the Heun passes                  */
-    SS_EXEC_SYSTEM_BLOCKS = 4 /* one thread block advances whole systems for many steps
+    SS_EXEC_SYSTEM_BLOCKS = 4, /* one thread block advances whole systems for many steps
                               with block barriers only (batches of small systems)   */
+    SS_EXEC_CLUSTER = 5    /* one small system (at most 2048 spins, rows of at most 12
+                              scalar bonds, no demagnetising field) in one thread-block
+                              cluster holding the spins in shared memory: chunks of 64
+                              steps, their Gaussians drawn beforehand over the whole GPU
+                              and their records summed afterwards; states and records
+                              bitwise those of the other modes                       */
 } ss_exec;
 
 typedef struct {

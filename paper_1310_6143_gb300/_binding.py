@@ -19,7 +19,7 @@ STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID_ARG", 2: "SS_ERR_CUDA", 3: "SS_ERR_OOM"
           5: "SS_ERR_NONFINITE", 6: "SS_ERR_STATE", 7: "SS_ERR_UNSUPPORTED"}
 SS_FP64, SS_FP32_MIXED = 0, 1
 SS_FLAG_CHECK_SYMMETRY, SS_FLAG_INIT_RANDOM = 1, 2
-SS_EXEC_AUTO, SS_EXEC_KERNELS, SS_EXEC_GRAPH, SS_EXEC_PERSISTENT, SS_EXEC_SYSTEM_BLOCKS = 0, 1, 2, 3, 4
+SS_EXEC_AUTO, SS_EXEC_KERNELS, SS_EXEC_GRAPH, SS_EXEC_PERSISTENT, SS_EXEC_SYSTEM_BLOCKS, SS_EXEC_CLUSTER = 0, 1, 2, 3, 4, 5
 
 # Every entry point include/spinsys.h declares.
 EXPORTS = (

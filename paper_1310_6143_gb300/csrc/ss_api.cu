@@ -196,6 +196,12 @@ struct ss_system {
     unsigned int bar_extra = 0;
     long long bar_timeout_ns = 2000000000ll;
     long long persist_chunk = 64;  // steps per persistent launch
+    // The cluster step of a small single system (SS_EXEC_CLUSTER): geometry and the chunk's
+    // Gaussians, record terms and tile partials
+    int cl_ctas = 0, cl_groups = 0;   // 0: not set up
+    void *cl_G = nullptr, *cl_T = nullptr;
+    double *cl_part = nullptr;
+    int64_t cl_ntiles = 0;            // tiles cl_part was sized for
 };
 
 namespace {
@@ -718,6 +724,74 @@ cudaError_t enqueue_persist(ss_system *h, int64_t n) {
     return h->precision == SS_FP32_MIXED ? enqueue_persistent<float>(h, n) : enqueue_persistent<double>(h, n);
 }
 
+// The cluster step (ss_cluster.cuh) for this handle: why it cannot run, or nullptr.  The
+// geometry is the fewest 32-spin groups per CTA whose cluster the device can launch.
+template <typename R>
+const char *cluster_setup(ss_system *h) {
+    if (h->nsys != 1) return "the cluster step takes one system";
+    if (h->slab_own >= 0) return "not available on a slab handle";
+    if (h->rows || h->J_tensor || h->demag_on)
+        return "the cluster step takes a thread-per-row scalar exchange sum and no demagnetising field";
+    if (h->max_row > kPatRow) return "the cluster step takes rows of at most 12 bonds";
+    if (h->cl_groups == 0) {
+        const KArgs<R> a = make_args<R>(h);
+        for (int g = 1; g <= kClusterMaxGroups && h->cl_groups == 0; g *= 2) {
+            const int64_t ctas = (h->n + 32 * g - 1) / (32 * g);
+            if (ctas <= cluster_max_ctas<R>(a, g, h->max_row)) {
+                h->cl_groups = g;
+                h->cl_ctas = (int)ctas;
+            }
+        }
+        if (h->cl_groups == 0) return "the system does not fit one thread-block cluster";
+    }
+    const size_t rs = sizeof(R);
+    if (!h->cl_G) {
+        if (dalloc(h, &h->cl_G, (size_t)kClusterChunk * 3 * h->n * rs) != cudaSuccess ||
+            dalloc(h, &h->cl_T, (size_t)kClusterChunk * 5 * h->n * rs) != cudaSuccess)
+            return "out of device memory";
+    }
+    if (h->cl_ntiles < h->ntiles) {
+        if (h->cl_part) dfree(h, h->cl_part);
+        h->cl_part = nullptr;
+        h->cl_ntiles = 0;
+        if (dalloc(h, (void **)&h->cl_part, (size_t)kClusterChunk * h->ntiles * kPartComps * sizeof(double)) !=
+            cudaSuccess)
+            return "out of device memory";
+        h->cl_ntiles = h->ntiles;
+    }
+    return nullptr;
+}
+
+const char *cluster_ready(ss_system *h) {
+    return h->precision == SS_FP32_MIXED ? cluster_setup<float>(h) : cluster_setup<double>(h);
+}
+
+// Chunks of kClusterChunk steps: the Gaussians, the steps in one cluster, the records.
+template <typename R>
+cudaError_t enqueue_cluster_steps(ss_system *h, int64_t n) {
+    const KArgs<R> a = make_args<R>(h);
+    ClusterArgs<R> c{};
+    c.G = (R *)h->cl_G;
+    c.T = (R *)h->cl_T;
+    c.partials = h->cl_part;
+    c.span = 32 * h->cl_groups;
+    c.groups = h->cl_groups;
+    for (int64_t done = 0; done < n;) {
+        c.step0 = (uint64_t)(h->step + done);
+        c.m = (int)std::min<int64_t>({(int64_t)kClusterChunk, n - done, h->rec_cap});
+        cudaError_t e = launch_cluster_gauss<R>(a, c, h->stream);
+        if (e == cudaSuccess) e = launch_cluster_steps<R>(a, c, h->cl_ctas, h->max_row, h->stream);
+        if (e == cudaSuccess) e = launch_cluster_record<R>(a, c, h->block, h->stream);
+        if (e != cudaSuccess) return e;
+        done += c.m;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_cluster(ss_system *h, int64_t n) {
+    return h->precision == SS_FP32_MIXED ? enqueue_cluster_steps<float>(h, n) : enqueue_cluster_steps<double>(h, n);
+}
+
 // The persistent launch of `persist_chunk` steps (barrier reset + cooperative kernel),
 // captured once into a CUDA graph and replayed.  Returns an error if capture is refused;
 // the caller then launches directly.
@@ -1137,7 +1211,8 @@ ss_status set_rows(ss_system *h, int32_t mode) {
     h->rows_req = mode;
     if (on != h->rows) drop_graph(h);
     h->rows = on;
-    if (on && (h->exec == SS_EXEC_PERSISTENT || h->exec == SS_EXEC_SYSTEM_BLOCKS)) h->exec = SS_EXEC_AUTO;
+    if (on && (h->exec == SS_EXEC_PERSISTENT || h->exec == SS_EXEC_SYSTEM_BLOCKS || h->exec == SS_EXEC_CLUSTER))
+        h->exec = SS_EXEC_AUTO;
     return SS_OK;
 }
 
@@ -1988,6 +2063,10 @@ static ss_status advance_steps(ss_system *h, int64_t n) {
         e = enqueue_kernels(h, left);
     } else if (mode == SS_EXEC_SYSTEM_BLOCKS) {
         e = enqueue_sysblocks(h, n);
+    } else if (mode == SS_EXEC_CLUSTER) {
+        const char *why = cluster_ready(h);
+        if (why) return fail(h, SS_ERR_UNSUPPORTED, "%s", why);
+        e = enqueue_cluster(h, n);
     } else if (mode == SS_EXEC_PERSISTENT) {
         int64_t left = n;
         if (!h->pgraph_failed) {
@@ -2291,7 +2370,11 @@ ss_status get_step(ss_system *h, int64_t *step) {
 ss_status spin_system_set_exec(ss_system *h, ss_exec mode) {
     ss_status st = usable(h);
     if (st != SS_OK) return st;
-    if (mode < SS_EXEC_AUTO || mode > SS_EXEC_SYSTEM_BLOCKS) return fail(h, SS_ERR_INVALID_ARG, "unknown exec mode");
+    if (mode < SS_EXEC_AUTO || mode > SS_EXEC_CLUSTER) return fail(h, SS_ERR_INVALID_ARG, "unknown exec mode");
+    if (mode == SS_EXEC_CLUSTER) {
+        const char *why = cluster_ready(h);
+        if (why) return fail(h, SS_ERR_UNSUPPORTED, "%s", why);
+    }
     if ((mode == SS_EXEC_PERSISTENT || mode == SS_EXEC_SYSTEM_BLOCKS) && h->rows)
         return fail(h, SS_ERR_UNSUPPORTED, "long exchange rows (a warp per row) run as graph or plain launches");
     if (mode == SS_EXEC_PERSISTENT && persistent_grid(h) < 1)

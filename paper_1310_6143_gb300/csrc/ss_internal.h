@@ -254,6 +254,28 @@ cudaError_t fp64_rate(int mode, double *inst_per_s);
 cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, long long n, int mode,
                                    const double2 *tab, double *out, cudaStream_t s);
 
+// The cluster step of one small system (ss_cluster.cuh): a chunk of m steps advanced by one
+// thread-block cluster whose CTAs hold the spins in shared memory.
+template <typename R>
+struct ClusterArgs {
+    R *G;               // [m][3][n] the chunk's Gaussians (k_cluster_gauss)
+    R *T;               // [m][5][n] the per-spin record terms of the chunk's states
+    double *partials;   // [m][ntiles][kPartComps] tile partials of the chunk's records
+    uint64_t step0;     // first step of the chunk
+    int m;              // steps of the chunk
+    int span;           // spins per CTA (32 groups)
+    int groups;         // groups of 32 spins per CTA (four warps each)
+};
+constexpr int kClusterChunk = 64;     // steps per cluster launch
+constexpr int kClusterMaxGroups = 4;  // groups of 32 spins per CTA (512 threads)
+template <typename R> cudaError_t launch_cluster_gauss(const KArgs<R> &a, const ClusterArgs<R> &c, cudaStream_t s);
+template <typename R>
+cudaError_t launch_cluster_steps(const KArgs<R> &a, const ClusterArgs<R> &c, int ctas, int row_slots, cudaStream_t s);
+template <typename R>
+cudaError_t launch_cluster_record(const KArgs<R> &a, const ClusterArgs<R> &c, int block, cudaStream_t s);
+// Largest cluster the step kernel can be launched with for `groups` groups per CTA (0: none).
+template <typename R> int cluster_max_ctas(const KArgs<R> &a, int groups, int row_slots);
+
 // Host (ss_common.cu): fills the kTabCount entries of the Box-Muller tables.
 void build_bm_tables(double2 *t);
 // Host (ss_common.cu): fills the kFFTabFloat4 entries of the double-float tables.

@@ -436,8 +436,8 @@ cudaError_t launch_system_blocks(const KArgs<R> &a, int block, int grid, long lo
     return cudaGetLastError();
 }
 
-// Explicit instantiations, split over three translation units per precision (SS_PART) so
-// that the build compiles them in parallel.
+// Explicit instantiations, split over translation units per precision (SS_PART) so that the
+// build compiles them in parallel (part 4, the cluster step, instantiates in ss_cluster.cuh).
 #if SS_PART == 1  // the Heun passes, the split step, the measurement, the long-row passes
 template cudaError_t launch_predictor<SS_REAL>(const KArgs<SS_REAL> &, int, int, cudaStream_t);
 template cudaError_t launch_corrector<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);
@@ -458,7 +458,7 @@ template cudaError_t launch_system_blocks<SS_REAL>(const KArgs<SS_REAL> &, int, 
 template cudaError_t launch_persistent<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, long long, cudaStream_t);
 template int persistent_blocks_per_sm<SS_REAL>(int, int);
 template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagArgs &, cudaStream_t);
-#else  // Monte Carlo and the alternative integrators
+#elif SS_PART == 3  // Monte Carlo and the alternative integrators
 template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
 template cudaError_t launch_mc_colour_rec<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);
 template cudaError_t launch_mc_colour_warp<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);

@@ -17,7 +17,7 @@ from .lattice import SpinLattice
 
 _PREC = {"fp64": B.SS_FP64, "fp32": B.SS_FP32_MIXED, "fp32_mixed": B.SS_FP32_MIXED}
 _EXEC = {"auto": B.SS_EXEC_AUTO, "kernels": B.SS_EXEC_KERNELS, "graph": B.SS_EXEC_GRAPH,
-         "persistent": B.SS_EXEC_PERSISTENT, "system_blocks": B.SS_EXEC_SYSTEM_BLOCKS}
+         "persistent": B.SS_EXEC_PERSISTENT, "system_blocks": B.SS_EXEC_SYSTEM_BLOCKS, "cluster": B.SS_EXEC_CLUSTER}
 
 
 def _per_system(v, count, name):
