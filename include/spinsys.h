@@ -130,10 +130,10 @@ typedef enum {
                               with block barriers only (batches of small systems)   */
     SS_EXEC_CLUSTER = 5    /* one small system (at most 2048 spins, rows of at most 12
                               scalar bonds, no demagnetising field) in one thread-block
-                              cluster holding the spins in shared memory: chunks of 64
-                              steps, their Gaussians drawn beforehand over the whole GPU
-                              and their records summed afterwards; states and records
-                              bitwise those of the other modes                       */
+                              cluster holding the spins in shared memory: chunks of 256
+                              steps, their thermal fields drawn beforehand and their
+                              records summed afterwards on other SMs, beside the cluster;
+                              states and records bitwise those of the other modes     */
 } ss_exec;
 
 typedef struct {

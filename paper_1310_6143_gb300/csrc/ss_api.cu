@@ -199,9 +199,11 @@ struct ss_system {
     // The cluster step of a small single system (SS_EXEC_CLUSTER): geometry and the chunk's
     // Gaussians, record terms and tile partials
     int cl_ctas = 0, cl_groups = 0;   // 0: not set up
-    void *cl_G = nullptr, *cl_T = nullptr;
+    void *cl_G = nullptr, *cl_T = nullptr;  // two chunks each (double-buffered)
     double *cl_part = nullptr;
     int64_t cl_ntiles = 0;            // tiles cl_part was sized for
+    cudaStream_t cl_side = nullptr;   // the thermal-field and record passes, beside the cluster
+    cudaEvent_t cl_ev[7] = {};        // fields ready (2), chunk done (2), records done (2), start
 };
 
 namespace {
@@ -746,9 +748,14 @@ const char *cluster_setup(ss_system *h) {
     }
     const size_t rs = sizeof(R);
     if (!h->cl_G) {
-        if (dalloc(h, &h->cl_G, (size_t)kClusterChunk * 3 * h->n * rs) != cudaSuccess ||
-            dalloc(h, &h->cl_T, (size_t)kClusterChunk * 5 * h->n * rs) != cudaSuccess)
+        if (dalloc(h, &h->cl_G, (size_t)2 * kClusterChunk * 3 * h->n * rs) != cudaSuccess ||
+            dalloc(h, &h->cl_T, (size_t)2 * kClusterChunk * 5 * h->n * rs) != cudaSuccess)
             return "out of device memory";
+    }
+    if (!h->cl_side) {
+        if (cudaStreamCreateWithFlags(&h->cl_side, cudaStreamNonBlocking) != cudaSuccess) return "no stream";
+        for (cudaEvent_t &ev : h->cl_ev)
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return "no event";
     }
     if (h->cl_ntiles < h->ntiles) {
         if (h->cl_part) dfree(h, h->cl_part);
@@ -766,26 +773,49 @@ const char *cluster_ready(ss_system *h) {
     return h->precision == SS_FP32_MIXED ? cluster_setup<float>(h) : cluster_setup<double>(h);
 }
 
-// Chunks of kClusterChunk steps: the Gaussians, the steps in one cluster, the records.
+// Chunks of kClusterChunk steps.  The cluster advances chunk after chunk on the handle's
+// stream; beside it, on other SMs, a second stream draws the thermal fields of the next chunk
+// and sums the records of the last one (two buffers of each, handed over by events).
 template <typename R>
 cudaError_t enqueue_cluster_steps(ss_system *h, int64_t n) {
     const KArgs<R> a = make_args<R>(h);
-    ClusterArgs<R> c{};
-    c.G = (R *)h->cl_G;
-    c.T = (R *)h->cl_T;
-    c.partials = h->cl_part;
-    c.span = 32 * h->cl_groups;
-    c.groups = h->cl_groups;
-    for (int64_t done = 0; done < n;) {
-        c.step0 = (uint64_t)(h->step + done);
-        c.m = (int)std::min<int64_t>({(int64_t)kClusterChunk, n - done, h->rec_cap});
-        cudaError_t e = launch_cluster_gauss<R>(a, c, h->stream);
-        if (e == cudaSuccess) e = launch_cluster_steps<R>(a, c, h->cl_ctas, h->max_row, h->stream);
-        if (e == cudaSuccess) e = launch_cluster_record<R>(a, c, h->block, h->stream);
-        if (e != cudaSuccess) return e;
-        done += c.m;
+    const int64_t chunk = std::min<int64_t>(kClusterChunk, h->rec_cap);
+    const int64_t nk = (n + chunk - 1) / chunk;
+    auto args = [&](int64_t k) {
+        ClusterArgs<R> c{};
+        c.G = (R *)h->cl_G + (k & 1) * kClusterChunk * 3 * h->n;
+        c.T = (R *)h->cl_T + (k & 1) * kClusterChunk * 5 * h->n;
+        c.partials = h->cl_part;
+        c.span = 32 * h->cl_groups;
+        c.groups = h->cl_groups;
+        c.step0 = (uint64_t)(h->step + k * chunk);
+        c.m = (int)std::min<int64_t>(chunk, n - k * chunk);
+        return c;
+    };
+    cudaEvent_t *eg = h->cl_ev, *ec = h->cl_ev + 2, *er = h->cl_ev + 4;
+    cudaStream_t side = h->cl_side;
+    cudaError_t e = cudaEventRecord(h->cl_ev[6], h->stream);  // parameters and state written before
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, h->cl_ev[6], 0);
+    if (e == cudaSuccess) e = launch_cluster_gauss<R>(a, args(0), side);
+    if (e == cudaSuccess) e = cudaEventRecord(eg[0], side);
+    for (int64_t k = 0; k < nk && e == cudaSuccess; ++k) {
+        const int b = (int)(k & 1), nb = (int)((k + 1) & 1);
+        if (k + 1 < nk) {  // the next chunk's thermal fields, once chunk k - 1 has read that buffer
+            e = cudaStreamWaitEvent(side, ec[nb], 0);
+            if (e == cudaSuccess) e = launch_cluster_gauss<R>(a, args(k + 1), side);
+            if (e == cudaSuccess) e = cudaEventRecord(eg[nb], side);
+        }
+        // chunk k, once its fields are drawn and the records of chunk k - 2 are summed
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, eg[b], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, er[b], 0);
+        if (e == cudaSuccess) e = launch_cluster_steps<R>(a, args(k), h->cl_ctas, h->max_row, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ec[b], h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ec[b], 0);
+        if (e == cudaSuccess) e = launch_cluster_record<R>(a, args(k), h->block, side);
+        if (e == cudaSuccess) e = cudaEventRecord(er[b], side);
     }
-    return cudaSuccess;
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, er[(nk - 1) & 1], 0);  // every record summed
+    return e;
 }
 
 cudaError_t enqueue_cluster(ss_system *h, int64_t n) {
@@ -1901,6 +1931,12 @@ ss_status spin_system_destroy(ss_system *h) {
         cudaStreamDestroy(h->side);
     }
     for (cudaEvent_t ev : {h->ev_fork, h->ev_gauss, h->ev_corr})
+        if (ev) cudaEventDestroy(ev);
+    if (h->cl_side) {
+        cudaStreamSynchronize(h->cl_side);
+        cudaStreamDestroy(h->cl_side);
+    }
+    for (cudaEvent_t ev : h->cl_ev)
         if (ev) cudaEventDestroy(ev);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;

@@ -6,9 +6,9 @@
 // thread, is therefore bound by the FP64 instructions each warp issues per step (the
 // Gaussian transform and the record sums included), not by memory, and spreading the spins
 // thinner over more SMs does not shorten it.  This path takes the per-warp work apart:
-//   * k_cluster_gauss draws the Gaussians of a whole chunk of steps beforehand, over the
-//     whole GPU, with the Philox counters and the transform of the step kernels (so the
-//     values are theirs);
+//   * k_cluster_gauss draws the thermal fields of a whole chunk of steps beforehand, over
+//     the whole GPU, with the Philox counters, the transform and the product sigma g of the
+//     step kernels (so the values are theirs);
 //   * k_cluster_steps runs the chunk in one cluster of up to 16 CTAs.  CTA r holds spins
 //     [r P, r P + P) of S and S' in shared memory; a neighbour in another CTA is read through
 //     distributed shared memory (mapa + ld.shared::cluster), and the two Heun passes of a step
@@ -57,13 +57,21 @@ __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// The four warps of one group of 32 spins (named barrier 1 + group): between two cluster
+// barriers the groups of a CTA touch only their own spins' entries, so they need not wait
+// for one another.
+__device__ __forceinline__ void group_sync(int grp) {
+    asm volatile("bar.sync %0, 128;" ::"r"(grp + 1) : "memory");
+}
+
 template <typename R>
 __device__ __forceinline__ R pick3(int c, R x, R y, R z) {
     return c == 0 ? x : (c == 1 ? y : z);
 }
 
-// The Gaussians of steps step0 .. step0 + m - 1 of every spin (steps at zero temperature are
-// skipped: nothing reads them).
+// The thermal field sigma g of steps step0 .. step0 + m - 1 of every spin: the step kernels'
+// product mul_rn(sig sqrt(T), g) of its Gaussians, or 0 at zero temperature (where the step
+// kernels add 0).
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_cluster_gauss(const KArgs<R> a, const ClusterArgs<R> c) {
     __shared__ StepTabT<R> tab;
@@ -76,25 +84,41 @@ __global__ void __launch_bounds__(BS) k_cluster_gauss(const KArgs<R> a, const Cl
         const int s = (int)(idx / n);
         const int64_t i = idx - (int64_t)s * n;
         const uint64_t step = c.step0 + (uint64_t)s;
-        if (!(sqrtT_of_step(a, step, sd) > (R)0)) continue;
-        const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
-        R g0, g1, g2;
-        thermal_gaussians(a, tab, w, g0, g1, g2);
+        const R sqrtT = sqrtT_of_step(a, step, sd);
+        R t0 = (R)0, t1 = (R)0, t2 = (R)0;
+        if (sqrtT > (R)0) {
+            const R sig = (a.mat_uniform ? a.mat0.sig : a.mats[__ldg(a.mat + i)].sig) * sqrtT;
+            const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
+            R g0, g1, g2;
+            thermal_gaussians(a, tab, w, g0, g1, g2);
+            t0 = mul_rn(sig, g0);
+            t1 = mul_rn(sig, g1);
+            t2 = mul_rn(sig, g2);
+        }
         R *G = c.G + (int64_t)s * 3 * n + i;
-        G[0] = g0;
-        G[n] = g1;
-        G[2 * n] = g2;
+        G[0] = t0;
+        G[n] = t1;
+        G[2 * n] = t2;
     }
 }
 
 // m Heun steps of the single system of `a` in one cluster (gridDim.x CTAs of 128 groups
 // threads).  NR: the row slots (kShortRow or kPatRow, at least the longest row).
+// A pass has five phases, separated by barriers of the group's four warps:
+//   A  exchange sums (components);              S.e (scalars)
+//   B  the field component (det_field + H_th);  record terms mu S, E_ani (scalars, predictor)
+//   C  this component of S x H;                 record term -mu S.h/2 (scalars, predictor)
+//   D  S x (S x H), dS and the update;          --
+//   E  --                                       1/|v| and the renormalised spin (scalars)
+// then a cluster barrier.  Two component warps share one SM sub-partition, a scalar and a
+// component warp each of the others; the scalar warps' record terms fill phases whose
+// critical path is the component warps'.
 template <typename R, int Mode, int NR>
 __global__ void __launch_bounds__(32 * 4 * kClusterMaxGroups) k_cluster_steps(const KArgs<R> a, const ClusterArgs<R> c) {
     extern __shared__ __align__(16) unsigned char cl_smem[];
     R *const sm = reinterpret_cast<R *>(cl_smem);
     const int P = c.span;
-    // S | S' | exchange sums | field | S x H | unnormalised update | an | 1/|v|, per component
+    // S | S' | exchange sums | field | S x H | unnormalised update, per component | an
     R *const S = sm;
     R *const Sp = sm + 3 * P;
     R *const E = sm + 6 * P;
@@ -102,8 +126,11 @@ __global__ void __launch_bounds__(32 * 4 * kClusterMaxGroups) k_cluster_steps(co
     R *const Cs = sm + 12 * P;
     R *const Vs = sm + 15 * P;
     R *const AN = sm + 18 * P;
-    R *const INV = sm + 19 * P;
     constexpr bool Cubic = Mode == kGeneral;
+    // FP32-mixed form: this component's thermal field loaded a step ahead, the record terms
+    // stored in phase C; FP64 form: the load where it is used, the terms stored after the
+    // cluster barrier (the faster arrangement of each, measured on GB300)
+    constexpr bool kAhead = sizeof(R) == 4;
     const uint32_t rank = cluster_ctarank();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = warp >> 2;
     // warp roles rotate with the group, so that the scalar warps sit on different SM
@@ -116,7 +143,6 @@ __global__ void __launch_bounds__(32 * 4 * kClusterMaxGroups) k_cluster_steps(co
     const bool comp = role < 3;
     const SysDesc &sd = a.sys[0];
     const MatDesc<R> &m = mat_at<Mode>(a, act ? i : 0);
-    R *const mine = comp ? pick3(role, a.sx, a.sy, a.sz) : nullptr;
 
     // per-role constants: the component's applied field, easy-axis entry and Neel row
     const int rc = comp ? role : 0;
@@ -125,8 +151,12 @@ __global__ void __launch_bounds__(32 * 4 * kClusterMaxGroups) k_cluster_steps(co
     const R k0 = pick3(rc, m.kf[0], m.kf[3], m.kf[4]);
     const R k1 = pick3(rc, m.kf[3], m.kf[1], m.kf[5]);
     const R k2 = pick3(rc, m.kf[4], m.kf[5], m.kf[2]);
+    // the material's constants in registers for the whole chunk
+    const R ex = m.e[0], ey = m.e[1], ez = m.e[2], ani = m.ani, mgp = -m.gp, lam = m.lambda, dt = m.dt;
+    const R hdt = (R)0.5 * dt, kcf = m.kcf, mu = m.mu;
+    const bool cubic = Cubic && m.has_cubic, neel = m.has_neel != 0;
 
-    if (act && comp) S[role * P + ls] = mine[i];
+    if (act && comp) S[role * P + ls] = pick3(role, a.sx, a.sy, a.sz)[i];
     // the neighbours: cluster-window address of this component of each one's S (S' lies
     // 3 P elements further in every CTA) and J_ij / mu_s,i
     uint32_t nb[NR];
@@ -157,13 +187,29 @@ __global__ void __launch_bounds__(32 * 4 * kClusterMaxGroups) k_cluster_steps(co
             if (q < len) x = fma(Jn[q], ld_cluster(nb[q] + shift, R()), x);
         return x;
     };
+    // the scalar warp's last phase: 1/|v| of the group's update and the renormalised spin
+    auto renormalise = [&](R *dst, bool check) {
+        const R v0 = Vs[ls], v1 = Vs[P + ls], v2 = Vs[2 * P + ls];
+        const R inv = rsqrt_r(fma(v2, v2, fma(v1, v1, mul_rn(v0, v0))));
+        if (check && bad_inv(inv)) atomicOr(a.err, kErrNonFinite);
+        dst[ls] = mul_rn(v0, inv);
+        dst[P + ls] = mul_rn(v1, inv);
+        dst[2 * P + ls] = mul_rn(v2, inv);
+    };
+    auto store_terms = [&](int s, const R (&tv)[5]) {
+        R *T = c.T + (int64_t)s * 5 * n + i;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) T[k * n] = tv[k];
+    };
+    R t_next = (kAhead && act && comp) ? c.G[(int64_t)role * n + i] : (R)0;
     cluster_barrier();  // every CTA's S is in place before the first remote read
 
     for (int s = 0; s < c.m; ++s) {
-        const uint64_t step = c.step0 + (uint64_t)s;
-        const R sqrtT = sqrtT_of_step(a, step, sd);
-        // ---- predictor.  A: exchange sums (components); S.e (scalars)
-        R s0 = (R)0, s1 = (R)0, s2 = (R)0, ec = (R)0, t = (R)0, cc = (R)0, vc = (R)0, qc = (R)0, sde = (R)0;
+        R t = t_next;  // this component's thermal field of the step
+        if (kAhead && act && comp && s + 1 < c.m) t_next = c.G[((int64_t)(s + 1) * 3 + role) * n + i];
+        R s0 = (R)0, s1 = (R)0, s2 = (R)0, ec = (R)0, cc = (R)0, qc = (R)0, sde = (R)0;
+        R tv[5];
+        // ---- predictor.  A
         if (act) {
             s0 = S[ls];
             s1 = S[P + ls];
@@ -172,64 +218,59 @@ __global__ void __launch_bounds__(32 * 4 * kClusterMaxGroups) k_cluster_steps(co
                 ec = xsum(0u);
                 E[role * P + ls] = ec;
             } else {
-                sde = fma(s2, m.e[2], fma(s1, m.e[1], mul_rn(s0, m.e[0])));
-                AN[ls] = mul_rn(m.ani, sde);
+                sde = fma(s2, ez, fma(s1, ey, mul_rn(s0, ex)));
+                AN[ls] = mul_rn(ani, sde);
             }
         }
-        __syncthreads();
-        // B: the field component (det_field, then the thermal field sigma g)
-        if (act && comp) {
-            const R sc = pick3(role, s0, s1, s2);
-            R H = fma(AN[ls], eC, ec);
-            if (Cubic && m.has_cubic) H = fma(mul_rn(mul_rn(m.kcf, sc), sc), sc, H);
-            if (m.has_neel) H = H + fma(k2, s2, fma(k1, s1, mul_rn(k0, s0)));
-            if (sqrtT > (R)0) {
-                const R sig = m.sig * sqrtT;
-                t = mul_rn(sig, c.G[((int64_t)s * 3 + role) * n + i]);
-            }
-            H += t;
-            Hs[role * P + ls] = H;
-        }
-        __syncthreads();
-        // C: this component of S x H
-        if (act && comp) {
-            const R H0 = Hs[ls], H1 = Hs[P + ls], H2 = Hs[2 * P + ls];
-            cc = role == 0 ? fma(s1, H2, -mul_rn(s2, H1))
-                           : (role == 1 ? fma(s2, H0, -mul_rn(s0, H2)) : fma(s0, H1, -mul_rn(s1, H0)));
-            Cs[role * P + ls] = cc;
-        }
-        __syncthreads();
-        // D: S x (S x H), dS, the Euler and half steps (components); the record terms (scalars)
+        group_sync(grp);
+        // B
         if (act) {
             if (comp) {
-                const R c0 = Cs[ls], c1 = Cs[P + ls], c2 = Cs[2 * P + ls];
-                const R xc = role == 0 ? fma(s1, c2, -mul_rn(s2, c1))
-                                       : (role == 1 ? fma(s2, c0, -mul_rn(s0, c2)) : fma(s0, c1, -mul_rn(s1, c0)));
-                const R dc = mul_rn(-m.gp, fma(m.lambda, xc, cc));
                 const R sc = pick3(role, s0, s1, s2);
-                vc = fma(m.dt, dc, sc);
-                qc = fma((R)0.5 * m.dt, dc, sc);
-                Vs[role * P + ls] = vc;
+                R H = fma(AN[ls], eC, ec);
+                if (cubic) H = fma(mul_rn(mul_rn(kcf, sc), sc), sc, H);
+                if (neel) H = H + fma(k2, s2, fma(k1, s1, mul_rn(k0, s0)));
+                if (!kAhead) t = c.G[((int64_t)s * 3 + role) * n + i];
+                H += t;
+                Hs[role * P + ls] = H;
             } else {
-                R v[5];
-                spin_terms_r<R, Cubic>(m, s0, s1, s2, E[ls], E[P + ls], E[2 * P + ls], sde, v);
-                R *T = c.T + (int64_t)s * 5 * n + i;
-#pragma unroll
-                for (int k = 0; k < 5; ++k) T[k * n] = v[k];
+                tv[0] = mul_rn(mu, s0);
+                tv[1] = mul_rn(mu, s1);
+                tv[2] = mul_rn(mu, s2);
+                tv[4] = anisotropy_term<R, Cubic>(m, s0, s1, s2, sde);
             }
         }
-        __syncthreads();
-        // E: 1/|v| (scalars)
-        if (act && !comp) {
-            const R v0 = Vs[ls], v1 = Vs[P + ls], v2 = Vs[2 * P + ls];
-            INV[ls] = rsqrt_r(fma(v2, v2, fma(v1, v1, mul_rn(v0, v0))));
+        group_sync(grp);
+        // C
+        if (act) {
+            if (comp) {
+                const R H0 = Hs[ls], H1 = Hs[P + ls], H2 = Hs[2 * P + ls];
+                cc = role == 0 ? fma(s1, H2, -mul_rn(s2, H1))
+                               : (role == 1 ? fma(s2, H0, -mul_rn(s0, H2)) : fma(s0, H1, -mul_rn(s1, H0)));
+                Cs[role * P + ls] = cc;
+            } else {
+                tv[3] = exchange_term(m, s0, s1, s2, E[ls], E[P + ls], E[2 * P + ls]);
+                if (kAhead) store_terms(s, tv);
+            }
         }
-        __syncthreads();
-        // F: S' = v / |v|
-        if (act && comp) Sp[role * P + ls] = mul_rn(vc, INV[ls]);
+        group_sync(grp);
+        // D
+        if (act && comp) {
+            const R c0 = Cs[ls], c1 = Cs[P + ls], c2 = Cs[2 * P + ls];
+            const R xc = role == 0 ? fma(s1, c2, -mul_rn(s2, c1))
+                                   : (role == 1 ? fma(s2, c0, -mul_rn(s0, c2)) : fma(s0, c1, -mul_rn(s1, c0)));
+            const R dc = mul_rn(mgp, fma(lam, xc, cc));
+            const R sc = pick3(role, s0, s1, s2);
+            qc = fma(hdt, dc, sc);
+            Vs[role * P + ls] = fma(dt, dc, sc);
+        }
+        group_sync(grp);
+        // E: S' = v / |v|
+        if (act && !comp) renormalise(Sp, false);
         cluster_barrier();
+        if (!kAhead && act && !comp) store_terms(s, tv);  // after the barrier: its release waits for no store
 
-        // ---- corrector.  A: exchange sums of S' (components); S'.e (scalars)
+        // ---- corrector (the same phases on S', with the predictor's thermal field).  A
         R p0 = (R)0, p1 = (R)0, p2 = (R)0;
         if (act) {
             p0 = Sp[ls];
@@ -238,50 +279,41 @@ __global__ void __launch_bounds__(32 * 4 * kClusterMaxGroups) k_cluster_steps(co
             if (comp)
                 ec = xsum(sp_off);
             else
-                AN[ls] = mul_rn(m.ani, fma(p2, m.e[2], fma(p1, m.e[1], mul_rn(p0, m.e[0]))));
+                AN[ls] = mul_rn(ani, fma(p2, ez, fma(p1, ey, mul_rn(p0, ex))));
         }
-        __syncthreads();
-        // B: the field component with the predictor's thermal field
+        group_sync(grp);
+        // B
         if (act && comp) {
             const R pc = pick3(role, p0, p1, p2);
             R H = fma(AN[ls], eC, ec);
-            if (Cubic && m.has_cubic) H = fma(mul_rn(mul_rn(m.kcf, pc), pc), pc, H);
-            if (m.has_neel) H = H + fma(k2, p2, fma(k1, p1, mul_rn(k0, p0)));
+            if (cubic) H = fma(mul_rn(mul_rn(kcf, pc), pc), pc, H);
+            if (neel) H = H + fma(k2, p2, fma(k1, p1, mul_rn(k0, p0)));
             H += t;
             Hs[role * P + ls] = H;
         }
-        __syncthreads();
-        // C: S' x H'
+        group_sync(grp);
+        // C
         if (act && comp) {
             const R H0 = Hs[ls], H1 = Hs[P + ls], H2 = Hs[2 * P + ls];
             cc = role == 0 ? fma(p1, H2, -mul_rn(p2, H1))
                            : (role == 1 ? fma(p2, H0, -mul_rn(p0, H2)) : fma(p0, H1, -mul_rn(p1, H0)));
             Cs[role * P + ls] = cc;
         }
-        __syncthreads();
-        // D: S' x (S' x H'), dS', Q + dt/2 dS'
+        group_sync(grp);
+        // D
         if (act && comp) {
             const R c0 = Cs[ls], c1 = Cs[P + ls], c2 = Cs[2 * P + ls];
             const R xc = role == 0 ? fma(p1, c2, -mul_rn(p2, c1))
                                    : (role == 1 ? fma(p2, c0, -mul_rn(p0, c2)) : fma(p0, c1, -mul_rn(p1, c0)));
-            const R dc = mul_rn(-m.gp, fma(m.lambda, xc, cc));
-            vc = fma((R)0.5 * m.dt, dc, qc);
-            Vs[role * P + ls] = vc;
+            const R dc = mul_rn(mgp, fma(lam, xc, cc));
+            Vs[role * P + ls] = fma(hdt, dc, qc);
         }
-        __syncthreads();
-        // E: 1/|v| (scalars), with the non-finite check of the corrector kernel
-        if (act && !comp) {
-            const R v0 = Vs[ls], v1 = Vs[P + ls], v2 = Vs[2 * P + ls];
-            const R inv = rsqrt_r(fma(v2, v2, fma(v1, v1, mul_rn(v0, v0))));
-            if (bad_inv(inv)) atomicOr(a.err, kErrNonFinite);
-            INV[ls] = inv;
-        }
-        __syncthreads();
-        // F: S = v / |v|
-        if (act && comp) S[role * P + ls] = mul_rn(vc, INV[ls]);
+        group_sync(grp);
+        // E: S = v / |v|, with the corrector kernel's non-finite check
+        if (act && !comp) renormalise(S, true);
         cluster_barrier();
     }
-    if (act && comp) mine[i] = S[role * P + ls];
+    if (act && comp) pick3(role, a.sx, a.sy, a.sz)[i] = S[role * P + ls];
     if (rank == 0 && threadIdx.x == 0) *a.step = c.step0 + (uint64_t)c.m;
 }
 
@@ -331,7 +363,7 @@ __global__ void __launch_bounds__(BS) k_cluster_record(const KArgs<R> a, const C
 
 template <typename R>
 size_t cluster_smem(int groups) {
-    return (size_t)20 * 32 * groups * sizeof(R);
+    return (size_t)19 * 32 * groups * sizeof(R);
 }
 
 template <typename R, int Mode, int NR>

@@ -258,7 +258,7 @@ cudaError_t launch_debug_gaussians(uint64_t seed, uint32_t sys, uint32_t step, l
 // thread-block cluster whose CTAs hold the spins in shared memory.
 template <typename R>
 struct ClusterArgs {
-    R *G;               // [m][3][n] the chunk's Gaussians (k_cluster_gauss)
+    R *G;               // [m][3][n] the chunk's thermal fields sigma g (k_cluster_gauss)
     R *T;               // [m][5][n] the per-spin record terms of the chunk's states
     double *partials;   // [m][ntiles][kPartComps] tile partials of the chunk's records
     uint64_t step0;     // first step of the chunk
@@ -266,7 +266,7 @@ struct ClusterArgs {
     int span;           // spins per CTA (32 groups)
     int groups;         // groups of 32 spins per CTA (four warps each)
 };
-constexpr int kClusterChunk = 64;     // steps per cluster launch
+constexpr int kClusterChunk = 256;    // steps per cluster launch
 constexpr int kClusterMaxGroups = 4;  // groups of 32 spins per CTA (512 threads)
 template <typename R> cudaError_t launch_cluster_gauss(const KArgs<R> &a, const ClusterArgs<R> &c, cudaStream_t s);
 template <typename R>

@@ -304,14 +304,15 @@ __device__ __forceinline__ void llg_rhs(R gp, R lam, R s0, R s1, R s2, R H0, R H
 // exchange + applied field, and the anisotropy energy.  The applied-field energy is
 // -H.M (H is uniform within a system) and the exchange energy sum(-mu S.h/2) + H.M/2;
 // both are formed from the FP64 sums when a system's record is finalised.
+// -mu S.h/2 of one spin (h: exchange + applied field).
+template <typename R>
+__device__ __forceinline__ R exchange_term(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2) {
+    return mul_rn((R)-0.5 * m.mu, fma(s2, e2, fma(s1, e1, mul_rn(s0, e0))));
+}
+
+// The anisotropy energy of one spin (uniaxial from S.e, cubic, Neel).
 template <typename R, bool Cubic = true>
-__device__ __forceinline__ void spin_terms_r(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R sde,
-                                             R v[5]) {
-    const R mu = m.mu;
-    v[0] = mul_rn(mu, s0);
-    v[1] = mul_rn(mu, s1);
-    v[2] = mul_rn(mu, s2);
-    v[3] = mul_rn((R)-0.5 * mu, fma(s2, e2, fma(s1, e1, mul_rn(s0, e0))));
+__device__ __forceinline__ R anisotropy_term(const MatDesc<R> &m, R s0, R s1, R s2, R sde) {
     R ea = mul_rn(-m.ku, mul_rn(sde, sde));
     if (Cubic && m.has_cubic) {
         const R x2 = mul_rn(s0, s0), y2 = mul_rn(s1, s1), z2 = mul_rn(s2, s2);
@@ -322,7 +323,18 @@ __device__ __forceinline__ void spin_terms_r(const MatDesc<R> &m, R s0, R s1, R 
         const R o = fma(mul_rn(m.K[5], s1), s2, fma(mul_rn(m.K[4], s0), s2, mul_rn(mul_rn(m.K[3], s0), s1)));
         ea = ea - fma((R)2, o, d);
     }
-    v[4] = ea;
+    return ea;
+}
+
+template <typename R, bool Cubic = true>
+__device__ __forceinline__ void spin_terms_r(const MatDesc<R> &m, R s0, R s1, R s2, R e0, R e1, R e2, R sde,
+                                             R v[5]) {
+    const R mu = m.mu;
+    v[0] = mul_rn(mu, s0);
+    v[1] = mul_rn(mu, s1);
+    v[2] = mul_rn(mu, s2);
+    v[3] = exchange_term(m, s0, s1, s2, e0, e1, e2);
+    v[4] = anisotropy_term<R, Cubic>(m, s0, s1, s2, sde);
 }
 
 template <typename R, bool Cubic = true>

@@ -91,13 +91,13 @@ def test_all_terms_ragged_tiles(SS, precision, tol, steps):
 def test_exec_modes_bitwise_identical(SS):
     lat = L.simple_cubic(9, 7, 5)
     out = {}
-    for mode in ("kernels", "graph", "persistent", "system_blocks"):
+    for mode in ("kernels", "graph", "persistent", "system_blocks", "cluster"):
         with SS(lat, alpha=0.1, dt=1e-16, T=400.0, seed=3, precision="fp64") as s:
             s.set_launch(128, 256)
             s.set_exec(mode)
             s.step(130)
             out[mode] = (s.spins(), s.record(0, 130))
-    for mode in ("graph", "persistent"):
+    for mode in ("graph", "persistent", "cluster"):
         np.testing.assert_array_equal(out[mode][0], out["kernels"][0])
         np.testing.assert_array_equal(out[mode][1], out["kernels"][1])
     # whole systems per block: same spins; the record sums in another order
