@@ -79,7 +79,7 @@ DEFAULT_FILM_SHAPE = (512, 4096, 4)
 KERNEL_DRAM_BYTES = {"k_predictor": 0.883e9, "k_corrector": 0.899e9}
 SMS = 152
 NO_AUTOTUNE = False
-EXEC_NAMES = {0: "auto", 1: "kernels", 2: "graph", 3: "persistent", 4: "system_blocks"}
+EXEC_NAMES = {0: "auto", 1: "kernels", 2: "graph", 3: "persistent", 4: "system_blocks", 5: "cluster"}
 FP64_SLOTS_PER_SM_CYCLE = 2
 PULSE_PEAK_STEP = 10_000  # the temperature pulse peaks at t0 = 1 ps = step 10,000 at dt = 1e-16 s
 

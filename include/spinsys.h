@@ -121,7 +121,8 @@ typedef struct {
 
 /* Execution modes of llg_heun_step (spin_system_set_exec). */
 typedef enum {
-    SS_EXEC_AUTO = 0,      /* graphs for long runs, direct launches for short ones  */
+    SS_EXEC_AUTO = 0,      /* SS_EXEC_CLUSTER for a single system it takes, else
+                              graphs for long runs, direct launches for short ones  */
     SS_EXEC_KERNELS = 1,   /* one predictor and one corrector launch per step       */
     SS_EXEC_GRAPH = 2,     /* CUDA graphs of captured step launches                 */
     SS_EXEC_PERSISTENT = 3, /* one cooperative launch runs many steps, with a bounded
@@ -384,7 +385,8 @@ ss_status spin_system_set_draw_ahead(ss_system *h, int32_t eighths);
 ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_info);
 
 /* The handle's sizes and current launch settings into *out (caller-owned).  `exec` is the mode
- * selected (SS_EXEC_AUTO stays AUTO: the library picks graphs or plain launches per call).
+ * selected (SS_EXEC_AUTO stays AUTO: the library picks the cluster step, graphs or plain
+ * launches per call).
  * Host-only, no synchronisation; SS_ERR_INVALID_ARG for a NULL out. */
 ss_status spin_system_info(ss_system *h, ss_info *out);
 

@@ -2078,6 +2078,10 @@ ss_status llg_heun_step(ss_system *h, int64_t n) {
 static ss_status advance_steps(ss_system *h, int64_t n) {
     cudaError_t e = cudaSuccess;
     int mode = h->exec;
+    // automatic: the cluster step for a small single system that it takes (on GB300 a few
+    // times faster than any per-step launch there), else graphs for long runs
+    if (mode == SS_EXEC_AUTO && h->n <= kClusterAutoMax && h->nsys == 1 && !cluster_ready(h))
+        mode = SS_EXEC_CLUSTER;
     if (mode == SS_EXEC_AUTO) mode = n >= graph_len(h) ? SS_EXEC_GRAPH : SS_EXEC_KERNELS;
     if (mode == SS_EXEC_GRAPH && !h->graph_failed) {
         e = ensure_graph(h);
@@ -2780,6 +2784,8 @@ ss_status spin_system_autotune(ss_system *h, int32_t trial_steps, ss_info *out_i
     for (int64_t v : h->sys_n) biggest = std::max(biggest, v);
     if (biggest <= 16384)
         for (int b : {128, 256, 512}) cands.push_back({SS_EXEC_SYSTEM_BLOCKS, b, b, h->ahead_q, 0});
+    // one small system in one thread-block cluster
+    if (!cluster_ready(h)) cands.push_back({SS_EXEC_CLUSTER, h->block, h->tile, h->ahead_q, 0});
     cudaEvent_t e0, e1;
     SS_CUDA(h, cudaEventCreate(&e0));
     SS_CUDA(h, cudaEventCreate(&e1));

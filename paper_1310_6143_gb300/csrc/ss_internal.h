@@ -268,6 +268,7 @@ struct ClusterArgs {
 };
 constexpr int kClusterChunk = 256;    // steps per cluster launch
 constexpr int kClusterMaxGroups = 4;  // groups of 32 spins per CTA (512 threads)
+constexpr int kClusterAutoMax = 2048; // largest system the automatic launch mode steps in a cluster
 template <typename R> cudaError_t launch_cluster_gauss(const KArgs<R> &a, const ClusterArgs<R> &c, cudaStream_t s);
 template <typename R>
 cudaError_t launch_cluster_steps(const KArgs<R> &a, const ClusterArgs<R> &c, int ctas, int row_slots, cudaStream_t s);
