@@ -109,12 +109,13 @@ struct ss_system {
     double2 *tab = nullptr;             // Box-Muller tables (build_bm_tables), then the
                                         // double-float tables (build_ff_tables)
     int32_t max_row = 0;                // longest CSR row
-    // Row patterns (the CSR stored as one byte per row, see build_patterns)
+    // Row patterns (the CSR stored as one or two bytes per row, see build_patterns)
     uint8_t *pat = nullptr;
     int32_t *pat_off = nullptr;
     void *pat_J = nullptr;
     int32_t npat = 0;                   // 0: no patterns (more than kMaxPatterns, rows too long)
     int32_t pat_w = 8;                  // slots of a pattern row (8 or 16, see KArgs)
+    bool pat_wide = false;              // two-byte pattern indices (more than 256 forms)
     bool use_pat = true;                // spin_system_set_row_patterns
     // Slab of a decomposed system (spin_slab_create): the owned spins are the first slab_own
     // of the arrays, the halo copies follow; tiles cover the owned spins, boundary tiles first
@@ -398,8 +399,9 @@ void build_tables(std::vector<double2> &t) {
 // Row patterns: when the rows take at most kMaxPatterns distinct forms -- a form being the
 // row's length and its (column - row, J_ij / mu_s,i) pairs in CSR order, as on a lattice whose
 // interior rows all look alike and whose boundary rows come in a few kinds -- each spin stores
-// the one-byte index of its row's form and the forms are kept in small tables, so a pass reads
-// one byte per spin instead of the row's offsets and columns (27.5 bytes on the film).  The
+// the index of its row's form (one byte up to 256 forms: the film has 27; two bytes beyond: a
+// batch of 256 grains has 6,846) and the forms are kept in tables, so a pass reads one or two
+// bytes per spin instead of the row's offsets and columns (27.5 bytes on the film).  The
 // exchange sum is then the CSR sum term for term.  Rows longer than kPatRow, or more forms,
 // keep the CSR (npat = 0).
 template <typename R>
@@ -410,7 +412,7 @@ ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std
     const int NS = h->max_row <= kShortRow ? kShortRow : kPatRow;  // offset slots, then the length
     const int W = NS == kShortRow ? 8 : 16;
     const int64_t n = h->n;
-    std::vector<uint8_t> pat((size_t)n);
+    std::vector<uint16_t> pat((size_t)n);
     std::vector<int32_t> poff;
     std::vector<R> pJ;
     std::unordered_map<uint64_t, int32_t> id_of;  // row hash -> pattern (contents verified)
@@ -445,18 +447,24 @@ ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std
                        std::memcmp(&pJ[(size_t)id * W + q], &J[(size_t)(b + q)], sizeof(R)) == 0;
             if (!same) return SS_OK;  // a hash collision: keep the CSR
         }
-        pat[(size_t)i] = (uint8_t)id;
+        pat[(size_t)i] = (uint16_t)id;
     }
-    SS_CUDA(h, dalloc(h, (void **)&h->pat, pat.size()));
+    const bool wide = poff.size() / W > (size_t)kBytePatterns;
+    std::vector<uint8_t> pat8;
+    if (!wide) pat8.assign(pat.begin(), pat.end());
+    const size_t pbytes = (size_t)n * (wide ? 2 : 1);
+    SS_CUDA(h, dalloc(h, (void **)&h->pat, pbytes));
     SS_CUDA(h, dalloc(h, (void **)&h->pat_off, poff.size() * sizeof(int32_t)));
     SS_CUDA(h, dalloc(h, &h->pat_J, pJ.size() * sizeof(R)));
-    SS_CUDA(h, cudaMemcpyAsync(h->pat, pat.data(), pat.size(), cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->pat, wide ? (const void *)pat.data() : (const void *)pat8.data(), pbytes,
+                               cudaMemcpyHostToDevice, h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->pat_off, poff.data(), poff.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                                h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->pat_J, pJ.data(), pJ.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
     SS_CUDA(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
     h->npat = (int32_t)(poff.size() / W);
     h->pat_w = W;
+    h->pat_wide = wide;
     return SS_OK;
 }
 
@@ -475,6 +483,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.pat_off = pat ? h->pat_off : nullptr;
     a.pat_J = pat ? static_cast<const R *>(h->pat_J) : nullptr;
     a.pat_w = h->pat_w;
+    a.pat_wide = h->pat_wide ? 1 : 0;
     a.mat_uniform = h->nmat == 1 ? 1 : 0;
     std::memcpy(&a.mat0, h->mat0, sizeof(MatDesc<R>));
     a.Jt = static_cast<const R *>(h->Jt);

@@ -26,7 +26,8 @@ constexpr int kTabCount = kLogTab + kLn2Tab + kTrigTab + kLogLo;
 constexpr int kFFTabFloat4 = kLogTab + kTrigTab + (kLn2Tab + 1) / 2;
 constexpr int kShortRow = 6;   // rows of at most this many bonds take the unrolled exchange sum
 constexpr int kPatRow = 12;    // longest row a row pattern holds
-constexpr int kMaxPatterns = 256;  // row patterns addressable by the one-byte pattern index
+constexpr int kMaxPatterns = 65536;   // row patterns addressable by the pattern index
+constexpr int kBytePatterns = 256;    // up to this many forms the index is one byte, else two
 constexpr int kRecComps = 8;   // record: sum mu S (3), sum mu, E_exc, E_ani, E_app, E_total
 constexpr int kPartComps = 8;  // tile partials: sum mu S (3), sum -mu S.h/2, E_ani, 0, 0, 0
 
@@ -88,7 +89,9 @@ struct KArgs {
     R J_value;                // the common value when every entry of J is the same
     int J_uniform;            // 1: J is not read, every bond has J_value
     int short_rows;           // 1: no row has more than kShortRow bonds
-    const uint8_t *pat;       // [n] row pattern of each spin, or nullptr (the CSR is read)
+    const uint8_t *pat;       // [n] row pattern of each spin (uint8, or uint16 when pat_wide), or
+                              // nullptr (the CSR is read)
+    int pat_wide;             // 1: pat holds uint16 indices (more than 256 forms)
     const int32_t *pat_off;   // [npat][pat_w] column - row of each bond in CSR order, 0 past the
                               // row's end, then the row length at slot pat_w - 2 (short) or
                               // pat_w - 4 (long); 32- or 64-byte aligned rows

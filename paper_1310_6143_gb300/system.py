@@ -188,7 +188,7 @@ class SpinSystem:
         return {"gauss_ms": out[0], "predictor_ms": out[1], "corrector_ms": out[2], "step_ms": out[3]}
 
     def set_row_patterns(self, on: bool):
-        """Read the one-byte row forms (True, the default when they were built) or the CSR."""
+        """Read the row forms (True, the default when they were built) or the CSR."""
         self._check(self._lib.spin_system_set_row_patterns(self._h, 1 if on else 0))
 
     def set_draw_ahead(self, eighths: int):

@@ -1,5 +1,5 @@
-"""Row patterns (one byte per row instead of the CSR offsets and columns) give exactly the
-CSR results: the exchange sum adds the same terms in the same order.  Checked bit for bit on
+"""Row patterns (a one- or two-byte form index per row instead of the CSR offsets and columns)
+give exactly the CSR results: the exchange sum adds the same terms in the same order.  Checked bit for bit on
 the workload lattices, in both precisions and every step kind that reads rows."""
 import numpy as np
 import pytest
@@ -59,3 +59,17 @@ def test_film_form_count(SS):
     """The film's rows come in 27 forms (bulk, top and bottom surface, times the in-plane wraps)."""
     with SS(L.film(32, 24, 16), precision="fp32") as s:
         assert s.info()["row_patterns"] == 27
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_two_byte_forms_bitwise_equal_to_csr(SS, precision):
+    """A batch whose rows take more than 256 forms (40 grains of ragged shapes) stores two-byte
+    form indices; the results are still the CSR's bit for bit."""
+    g, temps = L.grain_ensemble(count=40, n_min=2000, n_max=6000, layers=5, seed=21)
+    kw = dict(alpha=0.05, dt=1e-16, T=[float(t) for t in temps], seed=[5 + k for k in range(40)],
+              sys_id=list(range(40)))
+    on = _run(SS, g, True, precision, kw, mc=2)
+    off = _run(SS, g, False, precision, kw, mc=2)
+    assert 256 < on[0]["row_patterns"] <= 65536 and off[0]["row_patterns"] == 0
+    for a, b in zip(on[1:], off[1:]):
+        np.testing.assert_array_equal(a, b)
