@@ -1491,9 +1491,17 @@ __global__ void k_demag_field(const KArgs<R> a, const DemagArgs d) {
 // pre-step state in v: mu S (3), the exchange term (1: -mu S.(h - H_app) - mu S.H_app/2 for
 // the first colour class, whose bonds all end on unchanged spins; 2: -mu S.H_app/2), and
 // the anisotropy energy.
+// The FP64 Box-Muller tables of a kernel: its shared-memory copy in the FP64 form; in the
+// FP32-mixed form (whose kernels stage the double-float tables) the global buffer itself, laid
+// out as SmemTables (log | ln2 | trig | log remainders), read through the caches.
+__device__ __forceinline__ const SmemTables &fp64_tables(const KArgs<double> &, const SmemTables &t) { return t; }
+__device__ __forceinline__ const SmemTables &fp64_tables(const KArgs<float> &a, const FFTables &) {
+    return *reinterpret_cast<const SmemTables *>(a.tab);
+}
+
 template <typename R, int Mode, int Rec, bool GivenH = false>
 __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int64_t i, uint64_t step,
-                                         const SmemTables &tab, int &sysid, double v[5], R gh0 = 0, R gh1 = 0,
+                                         const StepTabT<R> &tab, int &sysid, double v[5], R gh0 = 0, R gh1 = 0,
                                          R gh2 = 0) {
     bool accept;
     const MatDesc<R> &mt = a.mats[__ldg(a.mat + i)];
@@ -1521,24 +1529,32 @@ __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int
         n1 = s1;
         n2 = s2;
     } else {
-        double g0, g1, g2;
-        box_muller3(wa, tab, g0, g1, g2);
-        if (move == 1) {  // Gaussian move: S + sigma_g Gamma, normalised
-            const double sg = par.y;
-            if constexpr (sizeof(R) == 8) {
-                n0 = fma(sg, g0, (double)s0);
-                n1 = fma(sg, g1, (double)s1);
-                n2 = fma(sg, g2, (double)s2);
-            } else {
-                const float sgf = narrow<float>(sg);
-                n0 = fmaf(sgf, narrow<float>(g0), (float)s0);
-                n1 = fmaf(sgf, narrow<float>(g1), (float)s1);
-                n2 = fmaf(sgf, narrow<float>(g2), (float)s2);
+        if constexpr (sizeof(R) == 8) {
+            double g0, g1, g2;
+            box_muller3(wa, tab, g0, g1, g2);
+            if (move == 1) {  // Gaussian move: S + sigma_g Gamma, normalised
+                const double sg = par.y;
+                n0 = fma(sg, g0, s0);
+                n1 = fma(sg, g1, s1);
+                n2 = fma(sg, g2, s2);
+            } else {  // random move: Gamma normalised
+                n0 = g0;
+                n1 = g1;
+                n2 = g2;
             }
-        } else {  // random move: Gamma normalised
-            n0 = narrow<R>(g0);
-            n1 = narrow<R>(g1);
-            n2 = narrow<R>(g2);
+        } else {  // the FP64 transform's values rounded to float, from the double-float transform
+            float g0, g1, g2;
+            gaussians_f32(wa, tab, a.tab, g0, g1, g2);
+            if (move == 1) {
+                const float sgf = narrow<float>(par.y);
+                n0 = fmaf(sgf, g0, s0);
+                n1 = fmaf(sgf, g1, s1);
+                n2 = fmaf(sgf, g2, s2);
+            } else {
+                n0 = g0;
+                n1 = g1;
+                n2 = g2;
+            }
         }
         const R inv = rsqrt_r(n0 * n0 + n1 * n1 + n2 * n2);
         n0 *= inv;
@@ -1566,7 +1582,7 @@ __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int
     }
     // accept when dE <= -kB T ln u = (-kB T)(-1/2)(-2 ln u); at T = 0 when dE <= 0
     const double dEd = widen(dE);
-    accept = par.x < 0.0 ? dEd <= par.x * (-0.5 * neg2log_u(wb.w1, tab)) : dEd <= 0.0;
+    accept = par.x < 0.0 ? dEd <= par.x * (-0.5 * neg2log_u(wb.w1, fp64_tables(a, tab))) : dEd <= 0.0;
     if (accept) {
         a.sx[i] = n0;
         a.sy[i] = n1;
@@ -1600,8 +1616,8 @@ __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int
 
 template <typename R, int BS, int Mode = kGeneral>
 __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs m) {
-    __shared__ SmemTables tab;
-    stage_tables(a, tab);
+    __shared__ StepTabT<R> tab;
+    stage_step_tables(a, tab);
     __syncthreads();
     const uint64_t step = *a.step;
     for (int64_t k = m.c0 + (int64_t)blockIdx.x * BS + threadIdx.x; k < m.c1; k += (int64_t)gridDim.x * BS) {
@@ -1623,8 +1639,8 @@ __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs
 // class are of other classes, unchanged during the pass).
 template <typename R, int BS, int Mode>
 __global__ void __launch_bounds__(BS) k_mc_colour_warp(const KArgs<R> a, const McArgs m) {
-    __shared__ SmemTables tab;
-    stage_tables(a, tab);
+    __shared__ StepTabT<R> tab;
+    stage_step_tables(a, tab);
     __syncthreads();
     const uint64_t step = *a.step;
     const unsigned FULL = 0xffffffffu;
@@ -1690,8 +1706,8 @@ __global__ void __launch_bounds__(BS) k_mc_colour_warp(const KArgs<R> a, const M
 // warp takes one trial, sums its row across the lanes, and lane 0 runs the trial.
 template <typename R, int BS, int Mode>
 __global__ void __launch_bounds__(BS) k_mc_colour_warp1(const KArgs<R> a, const McArgs m) {
-    __shared__ SmemTables tab;
-    stage_tables(a, tab);
+    __shared__ StepTabT<R> tab;
+    stage_step_tables(a, tab);
     __syncthreads();
     const uint64_t step = *a.step;
     const unsigned FULL = 0xffffffffu;
@@ -1739,9 +1755,9 @@ __global__ void __launch_bounds__(BS) k_mc_colour_warp1(const KArgs<R> a, const 
 // spins (tile partials in the block's fixed order), for lattices of at most two classes.
 template <typename R, int BS, int Mode, bool First>
 __global__ void __launch_bounds__(BS) k_mc_colour_rec(const KArgs<R> a, const McArgs m) {
-    __shared__ SmemTables tab;
+    __shared__ StepTabT<R> tab;
     __shared__ double red[(BS / 32) * 8];
-    stage_tables(a, tab);
+    stage_step_tables(a, tab);
     __syncthreads();
     const uint64_t step = *a.step;
     for (int64_t t = blockIdx.x; t < m.ntiles; t += gridDim.x) {
