@@ -86,7 +86,9 @@ struct ss_system {
     size_t device_bytes = 0;
 
     // device arrays
-    int32_t *row_ptr = nullptr, *col = nullptr, *mat = nullptr, *sys_tiles = nullptr;
+    int32_t *row_ptr = nullptr, *col = nullptr, *sys_tiles = nullptr;
+    void *mat = nullptr;   // material index per spin, mat_bytes each (1 up to 256 materials, 2 up to 65,536)
+    int mat_bytes = 4;
     void *J = nullptr, *mats = nullptr;
     void *state[12] = {};  // sx sy sz px py pz qx qy qz hx hy hz
     void *ahead[3] = {};   // Gaussians drawn ahead by the corrector (FP32-mixed only)
@@ -505,6 +507,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.hdy = static_cast<const R *>(h->d_hd[1]);
     a.hdz = static_cast<const R *>(h->d_hd[2]);
     a.mat = h->mat;
+    a.mat_bytes = h->mat_bytes;
     a.mats = static_cast<const MatDesc<R> *>(h->mats);
     a.sys = h->sys;
     a.tiles = h->tiles;
@@ -1176,12 +1179,19 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     SS_CUDA(h, dalloc(h, (void **)&h->row_ptr, rp.size() * sizeof(int32_t)));
     SS_CUDA(h, dalloc(h, (void **)&h->col, col.size() * sizeof(int32_t)));
     SS_CUDA(h, dalloc(h, &h->J, J.size() * rs));
-    SS_CUDA(h, dalloc(h, (void **)&h->mat, mat.size() * sizeof(int32_t)));
+    h->mat_bytes = mats.size() <= 256 ? 1 : (mats.size() <= 65536 ? 2 : 4);
+    std::vector<uint8_t> mat_packed(mat.size() * (size_t)h->mat_bytes);
+    for (size_t k = 0; k < mat.size(); ++k) {
+        if (h->mat_bytes == 1) mat_packed[k] = (uint8_t)mat[k];
+        else if (h->mat_bytes == 2) reinterpret_cast<uint16_t *>(mat_packed.data())[k] = (uint16_t)mat[k];
+        else reinterpret_cast<int32_t *>(mat_packed.data())[k] = mat[k];
+    }
+    SS_CUDA(h, dalloc(h, (void **)&h->mat, mat_packed.size()));
     SS_CUDA(h, dalloc(h, &h->mats, mats.size() * sizeof(MatDesc<R>)));
     SS_CUDA(h, cudaMemcpyAsync(h->row_ptr, rp.data(), rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->col, col.data(), col.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->J, J.data(), J.size() * rs, cudaMemcpyHostToDevice, h->stream));
-    SS_CUDA(h, cudaMemcpyAsync(h->mat, mat.data(), mat.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    SS_CUDA(h, cudaMemcpyAsync(h->mat, mat_packed.data(), mat_packed.size(), cudaMemcpyHostToDevice, h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->mats, mats.data(), mats.size() * sizeof(MatDesc<R>), cudaMemcpyHostToDevice,
                                h->stream));
     {

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(BS) k_cluster_gauss(const KArgs<R> a, const Cl
         const R sqrtT = sqrtT_of_step(a, step, sd);
         R t0 = (R)0, t1 = (R)0, t2 = (R)0;
         if (sqrtT > (R)0) {
-            const R sig = (a.mat_uniform ? a.mat0.sig : a.mats[__ldg(a.mat + i)].sig) * sqrtT;
+            const R sig = (a.mat_uniform ? a.mat0.sig : a.mats[mat_of(a, i)].sig) * sqrtT;
             const Philox4 w = philox4x32_10((uint32_t)(i - off), (uint32_t)step, sd.ctr2, 0u, sd.key0, sd.key1);
             R g0, g1, g2;
             thermal_gaussians(a, tab, w, g0, g1, g2);

@@ -118,7 +118,8 @@ struct KArgs {
     const R *hdx, *hdy, *hdz; // [ncell] demagnetising field of each macrocell (T)
     int demag;                // 1: add the macrocell field to every spin's field
     int64_t ncell;            // macrocells (index bound of mc_of)
-    const int32_t *mat;       // [n] material index
+    const void *mat;          // [n] material index: uint8 (mat_bytes 1), uint16 (2) or int32 (4)
+    int mat_bytes;
     const MatDesc<R> *mats;
     const SysDesc *sys;
     const TileDesc *tiles;

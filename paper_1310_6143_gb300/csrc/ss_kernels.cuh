@@ -112,13 +112,21 @@ constexpr int kPlain = 0, kGeneral = 1, kRows = 2;
 constexpr int kUniform = 3;
 __host__ __device__ constexpr int base_mode(int mode) { return mode == kUniform ? kPlain : mode; }
 
+// The material index of spin i (stored in one, two or four bytes by the number of materials).
+template <typename R>
+__device__ __forceinline__ int32_t mat_of(const KArgs<R> &a, int64_t i) {
+    if (a.mat_bytes == 1) return __ldg(static_cast<const uint8_t *>(a.mat) + i);
+    if (a.mat_bytes == 2) return __ldg(static_cast<const uint16_t *>(a.mat) + i);
+    return __ldg(static_cast<const int32_t *>(a.mat) + i);
+}
+
 template <int Mode, typename R>
 __device__ __forceinline__ const MatDesc<R> &mat_at(const KArgs<R> &a, int64_t i) {
     if constexpr (Mode == kUniform) {
         (void)i;
         return a.mat0;
     } else {
-        return a.mats[__ldg(a.mat + i)];
+        return a.mats[mat_of(a, i)];
     }
 }
 
@@ -851,7 +859,7 @@ __global__ void __launch_bounds__(BS) k_measure(const KArgs<R> a) {
         ta.reset();
         for (int k = threadIdx.x; k < td.count; k += BS) {
             const int64_t i = td.start + k;
-            const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+            const MatDesc<R> &m = a.mats[mat_of(a, i)];
             const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
             R e0, e1, e2;
             if (a.ex)
@@ -1089,7 +1097,7 @@ __global__ void __launch_bounds__(256) k_rows_sell(const KArgs<R> a) {
         R x = 0, y = 0, z = 0;
         const SysDesc *sd = nullptr;
         if (row < a.n && !a.rows_bare) {
-            sd = &a.sys[a.mats[__ldg(a.mat + row)].sys];
+            sd = &a.sys[a.mats[mat_of(a, row)].sys];
             x = sys_H(*sd, 0, R());
             y = sys_H(*sd, 1, R());
             z = sys_H(*sd, 2, R());
@@ -1165,7 +1173,7 @@ __global__ void __launch_bounds__(256) k_rows_field(const KArgs<R> a, const R *X
                 a.ey[row] = my;
                 a.ez[row] = mz;
             } else {
-                const SysDesc &sd = a.sys[a.mats[__ldg(a.mat + row)].sys];
+                const SysDesc &sd = a.sys[a.mats[mat_of(a, row)].sys];
                 a.ex[row] = sys_H(sd, 0, R()) + mx;
                 a.ey[row] = sys_H(sd, 1, R()) + my;
                 a.ez[row] = sys_H(sd, 2, R()) + mz;
@@ -1274,7 +1282,7 @@ __device__ __forceinline__ void alt_first_pass(const KArgs<R> &a, const SmemTabl
         double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int k = threadIdx.x; k < td.count; k += kAltBlock) {
             const int64_t i = td.start + k;
-            const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+            const MatDesc<R> &m = a.mats[mat_of(a, i)];
             R t0 = 0, t1 = 0, t2 = 0;
             if (sqrtT > (R)0) {
                 const R sig = m.sig * sqrtT;
@@ -1337,7 +1345,7 @@ __global__ void __launch_bounds__(kAltBlock) k_mid_euler(const KArgs<R> a) {
 template <typename R, int Mode, bool Last>
 __global__ void k_mid_iter(const KArgs<R> a, const R *xx, const R *xy, const R *xz, R *yx, R *yy, R *yz) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+        const MatDesc<R> &m = a.mats[mat_of(a, i)];
         const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
         const R m0 = (R)0.5 * (s0 + xx[i]), m1 = (R)0.5 * (s1 + xy[i]), m2 = (R)0.5 * (s2 + xz[i]);
         R x0, x1, x2;
@@ -1371,7 +1379,7 @@ __global__ void __launch_bounds__(kAltBlock) k_sib_pred(const KArgs<R> a) {
 template <typename R, int Mode>
 __global__ void k_sib_corr(const KArgs<R> a) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const MatDesc<R> &m = a.mats[__ldg(a.mat + i)];
+        const MatDesc<R> &m = a.mats[mat_of(a, i)];
         const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
         const R m0 = (R)0.5 * (s0 + a.px[i]), m1 = (R)0.5 * (s1 + a.py[i]), m2 = (R)0.5 * (s2 + a.pz[i]);
         R x0, x1, x2;
@@ -1406,7 +1414,7 @@ __global__ void k_demag_moments(const KArgs<R> a, const DemagArgs d) {
         double m0 = 0.0, m1 = 0.0, m2 = 0.0;
         for (int32_t k = d.cell_start[c] + lane; k < d.cell_start[c + 1]; k += 32) {
             const int32_t i = d.cell_spins[k];
-            const double mu = widen(a.mats[a.mat[i]].mu);
+            const double mu = widen(a.mats[mat_of(a, i)].mu);
             m0 += mu * widen(a.sx[i]);
             m1 += mu * widen(a.sy[i]);
             m2 += mu * widen(a.sz[i]);
@@ -1504,7 +1512,7 @@ __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int
                                          const StepTabT<R> &tab, int &sysid, double v[5], R gh0 = 0, R gh1 = 0,
                                          R gh2 = 0) {
     bool accept;
-    const MatDesc<R> &mt = a.mats[__ldg(a.mat + i)];
+    const MatDesc<R> &mt = a.mats[mat_of(a, i)];
     const SysDesc &sd = a.sys[mt.sys];
     double2 par;
     if (a.sched_len > 0) {
@@ -1691,7 +1699,7 @@ __global__ void __launch_bounds__(BS) k_mc_colour_warp(const KArgs<R> a, const M
         bool accept = false;
         int sysid = -1;
         if (i >= 0) {
-            const SysDesc &sd = a.sys[a.mats[__ldg(a.mat + i)].sys];
+            const SysDesc &sd = a.sys[a.mats[mat_of(a, i)].sys];
             double v[5];
             accept = mc_trial<R, Mode, 0, true>(a, m, i, step, tab, sysid, v, sys_H(sd, 0, R()) + mx,
                                                  sys_H(sd, 1, R()) + my, sys_H(sd, 2, R()) + mz);
@@ -1741,7 +1749,7 @@ __global__ void __launch_bounds__(BS) k_mc_colour_warp1(const KArgs<R> a, const 
             z += __shfl_xor_sync(FULL, z, o);
         }
         if (lane == 0) {
-            const SysDesc &sd = a.sys[a.mats[__ldg(a.mat + i)].sys];
+            const SysDesc &sd = a.sys[a.mats[mat_of(a, i)].sys];
             int sysid;
             double v[5];
             const bool accept = mc_trial<R, Mode, 0, true>(a, m, i, step, tab, sysid, v, sys_H(sd, 0, R()) + x,
