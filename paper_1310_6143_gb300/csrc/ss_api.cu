@@ -148,6 +148,9 @@ struct ss_system {
     int64_t mc_sched_cap = 0;
     bool mc_par_dirty = true;
     unsigned long long *mc_acc = nullptr;    // accepted trial moves per system (device)
+    uint8_t *mc_pre_move = nullptr;          // the step's trial randoms for the long-row passes
+    void *mc_pre_g = nullptr;                // (k_mc_prep): move type, Gaussians [3][n], acceptance
+    double *mc_pre_acc = nullptr;
     // record summed in the colour passes (at most two colour classes): per class its tiles
     // (runs of mc_order within one system) and their partial slots, slots system by system
     bool mc_rec = false;
@@ -1908,11 +1911,18 @@ cudaError_t enqueue_mc(ss_system *h, int64_t nsteps) {
     KArgs<R> ar = a;  // the record's measurement reads the row passes' field on long rows
     use_rows(h, ar);
     const int rgrid = h->rows ? rows_grid(h) : 0;
+    if (h->rows) {  // the long-row passes read each step's trial randoms, drawn for all spins first
+        if (!h->mc_pre_move) return cudaErrorInvalidValue;  // allocated by mc_step
+        m.pre_move = h->mc_pre_move;
+        m.pre_g = h->mc_pre_g;
+        m.pre_acc = h->mc_pre_acc;
+    }
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
         if (h->rows) e = launch_rows_field<R>(ar, ar.sx, ar.sy, ar.sz, rgrid, h->stream);
         if (e == cudaSuccess) e = launch_measure<R>(ar, h->block, gmeas, h->stream);
         if (e == cudaSuccess)
             e = launch_finalize_ring(h->sys, h->sys_tiles, h->nsys, h->partials, h->rec, h->rec_cap, a.step, h->stream);
+        if (h->rows && e == cudaSuccess) e = launch_mc_prep<R>(a, m, h->stream);
         for (int c = 0; c < ncol && e == cudaSuccess; ++c) {
             m.c0 = h->mc_cstart[c];
             m.c1 = h->mc_cstart[c + 1];
@@ -2230,6 +2240,11 @@ ss_status mc_step(ss_system *h, int64_t nsteps) {
     if (st != SS_OK) return st;
     st = mc_upload_params(h);
     if (st != SS_OK) return st;
+    if (h->rows && !h->mc_pre_move) {  // the long-row passes' trial randoms (before any capture)
+        SS_CUDA(h, dalloc(h, (void **)&h->mc_pre_move, (size_t)h->n));
+        SS_CUDA(h, dalloc(h, &h->mc_pre_g, 3 * (size_t)h->n * real_size(h)));
+        SS_CUDA(h, dalloc(h, (void **)&h->mc_pre_acc, (size_t)h->n * sizeof(double)));
+    }
     cudaError_t e = cudaSuccess;
     int64_t left = nsteps;
     // Captured steps (the launches hold no host-side step): replayed while whole graphs fit

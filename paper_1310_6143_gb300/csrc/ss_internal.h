@@ -169,6 +169,12 @@ struct McArgs {
     const double2 *par_sys;   // per system (-kB T, sigma_g) when no schedule is set
     const double2 *par_sched; // per schedule step (-kB T_k, sigma_g(T_k))
     unsigned long long *acc;  // accepted trial moves per system
+    // The step's trial randoms drawn beforehand for every spin by k_mc_prep (long-row passes),
+    // or nullptr (each trial draws its own): move type, the Gaussian triple in the working type
+    // ([3][n]), and the acceptance factor -ln(u)/... as the trial uses it (-1/2 of -2 ln u).
+    const uint8_t *pre_move;
+    const void *pre_g;
+    const double *pre_acc;
     // Record of the state at the start of the step summed in the colour passes (lattices with
     // at most two colour classes): the class's tiles, each a run of order[] within one system
     // whose record terms go to partials[slot]; slots run system by system.
@@ -223,6 +229,8 @@ template <typename R> int step_blocks_per_sm(int block, int mode);
 template <typename R> int corrector_blocks_per_sm(int block, bool draw_ahead, int mode);
 // One colour pass for long exchange rows: a warp sums the rows of 32 trials cooperatively.
 template <typename R> cudaError_t launch_mc_colour_warp(const KArgs<R> &a, const McArgs &m, int grid, cudaStream_t s);
+// The trial randoms of the device's current step for every spin (McArgs.pre_*).
+template <typename R> cudaError_t launch_mc_prep(const KArgs<R> &a, const McArgs &m, cudaStream_t s);
 // One colour pass over the tiles of m that also sums the record terms of the pre-step state.
 template <typename R> cudaError_t launch_mc_colour_rec(const KArgs<R> &a, const McArgs &m, int grid, cudaStream_t s);
 template <typename R> cudaError_t launch_mc_colour(const KArgs<R> &a, const McArgs &m, int block, int grid,

@@ -1507,9 +1507,31 @@ __device__ __forceinline__ const SmemTables &fp64_tables(const KArgs<float> &a, 
     return *reinterpret_cast<const SmemTables *>(a.tab);
 }
 
-template <typename R, int Mode, int Rec, bool GivenH = false>
+// The random part of spin i's trial at `step`: the move type (0 flip, 1 Gaussian, 2 random),
+// the Gaussian triple (drawn for moves 1 and 2) and the acceptance factor -(-2 ln u)/2.
+template <typename R>
+__device__ __forceinline__ int mc_randoms(const KArgs<R> &a, int64_t i, uint64_t step, const StepTabT<R> &tab,
+                                          R &g0, R &g1, R &g2, double &lnu) {
+    const MatDesc<R> &mt = a.mats[mat_of(a, i)];
+    const SysDesc &sd = a.sys[mt.sys];
+    const uint32_t spin = (uint32_t)(i - sd.offset + sd.pbase);
+    const Philox4 wa = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 2u, sd.key0, sd.key1);
+    const Philox4 wb = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 3u, sd.key0, sd.key1);
+    const int move = (int)(((uint64_t)wb.w0 * 3u) >> 32);
+    if (move != 0) {
+        if constexpr (sizeof(R) == 8) {
+            box_muller3(wa, tab, g0, g1, g2);
+        } else {  // the FP64 transform's values rounded to float, from the double-float transform
+            gaussians_f32(wa, tab, a.tab, g0, g1, g2);
+        }
+    }
+    lnu = -0.5 * neg2log_u(wb.w1, fp64_tables(a, tab));
+    return move;
+}
+
+template <typename R, int Mode, int Rec, bool GivenH = false, bool Pre = false>
 __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int64_t i, uint64_t step,
-                                         const StepTabT<R> &tab, int &sysid, double v[5], R gh0 = 0, R gh1 = 0,
+                                         const StepTabT<R> *tab, int &sysid, double v[5], R gh0 = 0, R gh1 = 0,
                                          R gh2 = 0) {
     bool accept;
     const MatDesc<R> &mt = a.mats[mat_of(a, i)];
@@ -1522,10 +1544,19 @@ __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int
     } else {
         par = m.par_sys[mt.sys];
     }
-    const uint32_t spin = (uint32_t)(i - sd.offset + sd.pbase);
-    const Philox4 wa = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 2u, sd.key0, sd.key1);
-    const Philox4 wb = philox4x32_10(spin, (uint32_t)step, sd.ctr2, 3u, sd.key0, sd.key1);
-    const int move = (int)(((uint64_t)wb.w0 * 3u) >> 32);
+    R g0 = (R)0, g1 = (R)0, g2 = (R)0;
+    double lnu;
+    int move;
+    if constexpr (Pre) {  // drawn beforehand by k_mc_prep
+        move = m.pre_move[i];
+        const R *pg = static_cast<const R *>(m.pre_g);
+        g0 = pg[i];
+        g1 = pg[a.n + i];
+        g2 = pg[2 * a.n + i];
+        lnu = m.pre_acc[i];
+    } else {
+        move = mc_randoms(a, i, step, *tab, g0, g1, g2, lnu);
+    }
     const R s0 = a.sx[i], s1 = a.sy[i], s2 = a.sz[i];
     R n0, n1, n2;
     if (move == 0) {  // spin flip
@@ -1537,32 +1568,22 @@ __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int
         n1 = s1;
         n2 = s2;
     } else {
-        if constexpr (sizeof(R) == 8) {
-            double g0, g1, g2;
-            box_muller3(wa, tab, g0, g1, g2);
-            if (move == 1) {  // Gaussian move: S + sigma_g Gamma, normalised
+        if (move == 1) {  // Gaussian move: S + sigma_g Gamma, normalised
+            if constexpr (sizeof(R) == 8) {
                 const double sg = par.y;
                 n0 = fma(sg, g0, s0);
                 n1 = fma(sg, g1, s1);
                 n2 = fma(sg, g2, s2);
-            } else {  // random move: Gamma normalised
-                n0 = g0;
-                n1 = g1;
-                n2 = g2;
-            }
-        } else {  // the FP64 transform's values rounded to float, from the double-float transform
-            float g0, g1, g2;
-            gaussians_f32(wa, tab, a.tab, g0, g1, g2);
-            if (move == 1) {
+            } else {
                 const float sgf = narrow<float>(par.y);
                 n0 = fmaf(sgf, g0, s0);
                 n1 = fmaf(sgf, g1, s1);
                 n2 = fmaf(sgf, g2, s2);
-            } else {
-                n0 = g0;
-                n1 = g1;
-                n2 = g2;
             }
+        } else {  // random move: Gamma normalised
+            n0 = g0;
+            n1 = g1;
+            n2 = g2;
         }
         const R inv = rsqrt_r(n0 * n0 + n1 * n1 + n2 * n2);
         n0 *= inv;
@@ -1590,7 +1611,7 @@ __device__ __forceinline__ bool mc_trial(const KArgs<R> &a, const McArgs &m, int
     }
     // accept when dE <= -kB T ln u = (-kB T)(-1/2)(-2 ln u); at T = 0 when dE <= 0
     const double dEd = widen(dE);
-    accept = par.x < 0.0 ? dEd <= par.x * (-0.5 * neg2log_u(wb.w1, fp64_tables(a, tab))) : dEd <= 0.0;
+    accept = par.x < 0.0 ? dEd <= par.x * lnu : dEd <= 0.0;
     if (accept) {
         a.sx[i] = n0;
         a.sy[i] = n1;
@@ -1631,7 +1652,7 @@ __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs
     for (int64_t k = m.c0 + (int64_t)blockIdx.x * BS + threadIdx.x; k < m.c1; k += (int64_t)gridDim.x * BS) {
         int sysid;
         double v[5];
-        const bool accept = mc_trial<R, Mode, 0>(a, m, chk(__ldg(m.order + k), a.n, a.err), step, tab, sysid, v);
+        const bool accept = mc_trial<R, Mode, 0>(a, m, chk(__ldg(m.order + k), a.n, a.err), step, &tab, sysid, v);
         // accepted moves per system, one atomic per (warp, system)
         const unsigned act = __activemask();
         const unsigned same = __match_any_sync(act, sysid);
@@ -1645,11 +1666,32 @@ __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs
 // rows one by one with its lanes striding over the row's bonds (col + J, or tensors) and a
 // butterfly, and each lane then runs its own trial with its row's field (the neighbours of a
 // class are of other classes, unchanged during the pass).
-template <typename R, int BS, int Mode>
-__global__ void __launch_bounds__(BS) k_mc_colour_warp(const KArgs<R> a, const McArgs m) {
+// The trial randoms of the device's current step for every spin (move type, Gaussian triple,
+// acceptance factor), for the long-row colour passes: their trials then run without the
+// transform's tables or its serial work (mc_randoms is what mc_trial draws otherwise).
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_mc_prep(const KArgs<R> a, const McArgs m) {
     __shared__ StepTabT<R> tab;
     stage_step_tables(a, tab);
     __syncthreads();
+    const uint64_t step = *a.step;
+    uint8_t *mv = const_cast<uint8_t *>(m.pre_move);
+    R *pg = static_cast<R *>(const_cast<void *>(m.pre_g));
+    double *pa = const_cast<double *>(m.pre_acc);
+    for (int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * BS) {
+        R g0 = (R)0, g1 = (R)0, g2 = (R)0;
+        double lnu;
+        mv[i] = (uint8_t)mc_randoms(a, i, step, tab, g0, g1, g2, lnu);
+        pg[i] = g0;
+        pg[a.n + i] = g1;
+        pg[2 * a.n + i] = g2;
+        pa[i] = lnu;
+    }
+}
+
+template <typename R, int BS, int Mode>
+__global__ void __launch_bounds__(BS) k_mc_colour_warp(const KArgs<R> a, const McArgs m) {
+    // the trial randoms come from k_mc_prep: no tables
     const uint64_t step = *a.step;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1701,7 +1743,7 @@ __global__ void __launch_bounds__(BS) k_mc_colour_warp(const KArgs<R> a, const M
         if (i >= 0) {
             const SysDesc &sd = a.sys[a.mats[mat_of(a, i)].sys];
             double v[5];
-            accept = mc_trial<R, Mode, 0, true>(a, m, i, step, tab, sysid, v, sys_H(sd, 0, R()) + mx,
+            accept = mc_trial<R, Mode, 0, true, true>(a, m, i, step, nullptr, sysid, v, sys_H(sd, 0, R()) + mx,
                                                  sys_H(sd, 1, R()) + my, sys_H(sd, 2, R()) + mz);
         }
         const unsigned same = __match_any_sync(FULL, sysid);
@@ -1714,9 +1756,7 @@ __global__ void __launch_bounds__(BS) k_mc_colour_warp(const KArgs<R> a, const M
 // warp takes one trial, sums its row across the lanes, and lane 0 runs the trial.
 template <typename R, int BS, int Mode>
 __global__ void __launch_bounds__(BS) k_mc_colour_warp1(const KArgs<R> a, const McArgs m) {
-    __shared__ StepTabT<R> tab;
-    stage_step_tables(a, tab);
-    __syncthreads();
+    // the trial randoms come from k_mc_prep: no tables
     const uint64_t step = *a.step;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1752,7 +1792,7 @@ __global__ void __launch_bounds__(BS) k_mc_colour_warp1(const KArgs<R> a, const 
             const SysDesc &sd = a.sys[a.mats[mat_of(a, i)].sys];
             int sysid;
             double v[5];
-            const bool accept = mc_trial<R, Mode, 0, true>(a, m, i, step, tab, sysid, v, sys_H(sd, 0, R()) + x,
+            const bool accept = mc_trial<R, Mode, 0, true, true>(a, m, i, step, nullptr, sysid, v, sys_H(sd, 0, R()) + x,
                                                            sys_H(sd, 1, R()) + y, sys_H(sd, 2, R()) + z);
             if (accept) atomicAdd(m.acc + sysid, 1ull);
         }
@@ -1775,7 +1815,7 @@ __global__ void __launch_bounds__(BS) k_mc_colour_rec(const KArgs<R> a, const Mc
             int sysid;
             double v[5];
             const bool accept = mc_trial<R, Mode, First ? 1 : 2>(a, m, chk(__ldg(m.order + td.start + k), a.n, a.err),
-                                                                 step, tab, sysid, v);
+                                                                 step, &tab, sysid, v);
 #pragma unroll
             for (int c = 0; c < 5; ++c) acc[c] += v[c];
             // a tile lies in one system: one atomic per warp

@@ -241,6 +241,17 @@ cudaError_t launch_mc_colour_warp(const KArgs<R> &a, const McArgs &m, int grid, 
 }
 
 template <typename R>
+cudaError_t launch_mc_prep(const KArgs<R> &a, const McArgs &m, cudaStream_t s) {
+    constexpr int BS = 256;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (a.n + BS - 1) / BS;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 4));
+    k_mc_prep<R, BS><<<g, BS, 0, s>>>(a, m);
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_mc_colour_rec(const KArgs<R> &a, const McArgs &m, int grid, cudaStream_t s) {
     constexpr int BS = 256;
     const bool general = a.J_tensor || a.any_cubic;
@@ -462,6 +473,7 @@ template cudaError_t launch_demag<SS_REAL>(const KArgs<SS_REAL> &, const DemagAr
 template cudaError_t launch_mc_colour<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, int, cudaStream_t);
 template cudaError_t launch_mc_colour_rec<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);
 template cudaError_t launch_mc_colour_warp<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, int, cudaStream_t);
+template cudaError_t launch_mc_prep<SS_REAL>(const KArgs<SS_REAL> &, const McArgs &, cudaStream_t);
 template int mc_blocks_per_sm<SS_REAL>(int, int);
 template cudaError_t launch_midpoint<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, int, cudaStream_t);
 template cudaError_t launch_sib<SS_REAL>(const KArgs<SS_REAL> &, int, int, int, cudaStream_t);

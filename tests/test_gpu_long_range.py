@@ -236,3 +236,21 @@ def test_monte_carlo_on_long_rows(SS, kind):
     assert np.array_equal(np.array(accs), acc_ref)
     assert np.abs(S - S_ref).max() <= 1e-12
     assert np.abs(rec[:, 0, 7] - rec_ref[:, 7]).max() <= 1e-12 * np.abs(rec_ref[:, 7]).max()
+
+
+def test_monte_carlo_long_rows_fp32_warp_and_thread_agree(SS):
+    """FP32-mixed Monte Carlo on long rows: the warp-summed passes (their trial randoms drawn for
+    all spins by a pass of their own) against the thread-per-row passes (each trial drawing its
+    own): the same moves and thresholds, row sums in another order."""
+    lat = L.fcc_long_range(9, 9, 9, r_cut=3.0)
+    S0 = L.random_state(lat.n, 4)
+    out = {}
+    for mode in ("warp", "thread"):
+        with SS(lat, alpha=0.1, dt=1e-16, T=700.0, S0=S0, seed=9, precision="fp32") as s:
+            s.set_exchange_rows(mode)
+            s.mc_step(6)
+            out[mode] = (s.spins(), s.mc_stats(0)[0])
+    acc_w, acc_t = out["warp"][1], out["thread"][1]
+    assert abs(acc_w - acc_t) <= 0.002 * lat.n * 6, (acc_w, acc_t)
+    same = np.all(out["warp"][0] == out["thread"][0], axis=1).mean()
+    assert same > 0.99, same
