@@ -1666,6 +1666,40 @@ __global__ void __launch_bounds__(BS) k_mc_colour(const KArgs<R> a, const McArgs
 // rows one by one with its lanes striding over the row's bonds (col + J, or tensors) and a
 // butterfly, and each lane then runs its own trial with its row's field (the neighbours of a
 // class are of other classes, unchanged during the pass).
+// Lane `lane`'s share of the scalar exchange sum of row [b, e) (bonds b + lane, b + lane + 32,
+// ... in order): eight bonds at a time, their columns first, then their gathers, then the
+// sums in bond order, so that the loads of a lane overlap.
+template <typename R>
+__device__ __forceinline__ void mc_row_sum8(const KArgs<R> &a, int32_t b, int32_t e, int lane, R &x, R &y, R &z) {
+    constexpr int U = 8;
+    for (int32_t t0 = b + lane; t0 < e; t0 += 32 * U) {
+        int32_t jj[U];
+        R Jk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t t = t0 + 32 * u;
+            jj[u] = t < e ? chk(__ldg(a.col + t), a.n, a.err) : -1;
+            Jk[u] = a.J_uniform ? a.J_value : (t < e ? __ldg(a.J + t) : (R)0);
+        }
+        R sx[U], sy[U], sz[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t j = jj[u] >= 0 ? jj[u] : 0;
+            sx[u] = a.sx[j];
+            sy[u] = a.sy[j];
+            sz[u] = a.sz[j];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (jj[u] >= 0) {
+                x = fma(Jk[u], sx[u], x);
+                y = fma(Jk[u], sy[u], y);
+                z = fma(Jk[u], sz[u], z);
+            }
+        }
+    }
+}
+
 // The trial randoms of the device's current step for every spin (move type, Gaussian triple,
 // acceptance factor), for the long-row colour passes: their trials then run without the
 // transform's tables or its serial work (mc_randoms is what mc_trial draws otherwise).
@@ -1710,20 +1744,17 @@ __global__ void __launch_bounds__(BS) k_mc_colour_warp(const KArgs<R> a, const M
         for (int q = 0; q < nr; ++q) {
             const int32_t b = __shfl_sync(FULL, rb, q), e = __shfl_sync(FULL, re, q);
             R x = 0, y = 0, z = 0;
+            if (Mode == kPlain || !a.J_tensor) {
+                mc_row_sum8(a, b, e, lane, x, y, z);
+            } else {
 #pragma unroll 4
-            for (int32_t t = b + lane; t < e; t += 32) {
-                const int32_t j = chk(__ldg(a.col + t), a.n, a.err);
-                const R s0 = a.sx[j], s1 = a.sy[j], s2 = a.sz[j];
-                if (Mode != kPlain && a.J_tensor) {
+                for (int32_t t = b + lane; t < e; t += 32) {
+                    const int32_t j = chk(__ldg(a.col + t), a.n, a.err);
+                    const R s0 = a.sx[j], s1 = a.sy[j], s2 = a.sz[j];
                     const R *tt = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + t);
                     x = fma(__ldg(tt + 0), s0, fma(__ldg(tt + 1), s1, fma(__ldg(tt + 2), s2, x)));
                     y = fma(__ldg(tt + 3), s0, fma(__ldg(tt + 4), s1, fma(__ldg(tt + 5), s2, y)));
                     z = fma(__ldg(tt + 6), s0, fma(__ldg(tt + 7), s1, fma(__ldg(tt + 8), s2, z)));
-                } else {
-                    const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + t);
-                    x = fma(Jk, s0, x);
-                    y = fma(Jk, s1, y);
-                    z = fma(Jk, s2, z);
                 }
             }
 #pragma unroll
@@ -1766,20 +1797,17 @@ __global__ void __launch_bounds__(BS) k_mc_colour_warp1(const KArgs<R> a, const 
         const int64_t i = chk(__ldg(m.order + k), a.n, a.err);
         const int32_t b = __ldg(a.row_ptr + i), e = __ldg(a.row_ptr + i + 1);
         R x = 0, y = 0, z = 0;
+        if (Mode == kPlain || !a.J_tensor) {
+            mc_row_sum8(a, b, e, lane, x, y, z);
+        } else {
 #pragma unroll 4
-        for (int32_t t = b + lane; t < e; t += 32) {
-            const int32_t j = chk(__ldg(a.col + t), a.n, a.err);
-            const R s0 = a.sx[j], s1 = a.sy[j], s2 = a.sz[j];
-            if (Mode != kPlain && a.J_tensor) {
+            for (int32_t t = b + lane; t < e; t += 32) {
+                const int32_t j = chk(__ldg(a.col + t), a.n, a.err);
+                const R s0 = a.sx[j], s1 = a.sy[j], s2 = a.sz[j];
                 const R *tt = a.Jt + 9 * (int64_t)__ldg(a.Jtidx + t);
                 x = fma(__ldg(tt + 0), s0, fma(__ldg(tt + 1), s1, fma(__ldg(tt + 2), s2, x)));
                 y = fma(__ldg(tt + 3), s0, fma(__ldg(tt + 4), s1, fma(__ldg(tt + 5), s2, y)));
                 z = fma(__ldg(tt + 6), s0, fma(__ldg(tt + 7), s1, fma(__ldg(tt + 8), s2, z)));
-            } else {
-                const R Jk = a.J_uniform ? a.J_value : __ldg(a.J + t);
-                x = fma(Jk, s0, x);
-                y = fma(Jk, s1, y);
-                z = fma(Jk, s2, z);
             }
         }
 #pragma unroll
