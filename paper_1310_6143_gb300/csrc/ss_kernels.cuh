@@ -1102,15 +1102,47 @@ __global__ void __launch_bounds__(256) k_rows_sell(const KArgs<R> a) {
             y = sys_H(*sd, 1, R());
             z = sys_H(*sd, 2, R());
         }
+        if constexpr (sizeof(R) == 8) {
+            // FP64: eight bonds at a time, their words, then their gathers, then the sums in
+            // bond order (5.80 against 6.34 ms per pass on fcc 64^3 to 4a; in FP32 the plain
+            // loop below is faster, 1.52 against 1.70 ms)
+            constexpr int U = 8;
+            int k = 0;
+            for (; k + U <= w; k += U) {
+                uint32_t bw[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) bw[u] = __ldg(p + 32 * (int64_t)(k + u));
+                R s0[U], s1[U], s2[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) load_spin4(a.x4, chk(bw[u] >> 8, a.n, a.err), s0[u], s1[u], s2[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const R Jk = jd[chk(bw[u] & 255u, a.nJd, a.err)];
+                    x = fma(Jk, s0[u], x);
+                    y = fma(Jk, s1[u], y);
+                    z = fma(Jk, s2[u], z);
+                }
+            }
+            for (; k < w; ++k) {
+                const uint32_t b = __ldg(p + 32 * (int64_t)k);
+                const R Jk = jd[chk(b & 255u, a.nJd, a.err)];
+                R s0, s1, s2;
+                load_spin4(a.x4, chk(b >> 8, a.n, a.err), s0, s1, s2);
+                x = fma(Jk, s0, x);
+                y = fma(Jk, s1, y);
+                z = fma(Jk, s2, z);
+            }
+        } else {
 #pragma unroll 8
-        for (int k = 0; k < w; ++k) {
-            const uint32_t b = __ldg(p + 32 * (int64_t)k);
-            const R Jk = jd[chk(b & 255u, a.nJd, a.err)];
-            R s0, s1, s2;
-            load_spin4(a.x4, chk(b >> 8, a.n, a.err), s0, s1, s2);
-            x = fma(Jk, s0, x);
-            y = fma(Jk, s1, y);
-            z = fma(Jk, s2, z);
+            for (int k = 0; k < w; ++k) {
+                const uint32_t b = __ldg(p + 32 * (int64_t)k);
+                const R Jk = jd[chk(b & 255u, a.nJd, a.err)];
+                R s0, s1, s2;
+                load_spin4(a.x4, chk(b >> 8, a.n, a.err), s0, s1, s2);
+                x = fma(Jk, s0, x);
+                y = fma(Jk, s1, y);
+                z = fma(Jk, s2, z);
+            }
         }
         if (row < a.n) {
             a.ex[row] = x;
