@@ -309,8 +309,9 @@ def workload_table(stream, rank):
 
     rows = {}
     sc = L.simple_cubic(10, 10, 10, J=6.0e-21, k_u=1.0e-24)
-    rows["sc10_fp64"] = dict(spins=sc.n, **time_workload(sc, dict(alpha=0.1, dt=1e-16, T=300.0, seed=1 + rank),
-                                                          "fp64", 2000, stream))
+    for prec in ("fp64", "fp32"):
+        rows[f"sc10_{prec}"] = dict(spins=sc.n, **time_workload(sc, dict(alpha=0.1, dt=1e-16, T=300.0, seed=1 + rank),
+                                                                 prec, 2000, stream))
     fcc = L.fcc(64, 64, 64, J=11.2e-21, k_u=6.69e-24)
     kw = dict(alpha=0.05, dt=1e-16, T=1000.0, seed=2 + rank, init_random=True)
     for prec, k in (("fp32", 200), ("fp64", 50)):
