@@ -210,7 +210,7 @@ def cpu_baseline(lat, T, seconds=15.0):
     O.set_threads(threads)
     return {"value": lat.n * steps / one, "unit": "spin-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"{steps} Heun step(s) of the full 1024x1024x16 film (FP64, with per-step moment/energy "
-                      f"record), {one:.1f} s",
+                      f"record), {one:.1f} s, oracle built gcc {' '.join(O.FLAGS)}",
             "single_thread_value": lat.n / single, "cpu_model": cpu_model(), "build": "gcc " + " ".join(O.FLAGS)}
 
 
