@@ -557,7 +557,8 @@ def run_reference(args):
     v = lat.n * K / secs
     cb = {"value": v, "unit": "spin-steps/s", "cores": threads, "kind": "oracle",
           "sample": f"{K} Heun steps (after {W} untimed) of a 1024x{ny}x16 film of the workload's construction "
-                    f"({lat.n} spins; FP64, with per-step moment/energy record), {secs:.1f} s",
+                    f"({lat.n} spins; FP64, with per-step moment/energy record), {secs:.1f} s, oracle built gcc "
+                    f"{' '.join(O.FLAGS)}",
           "cpu_model": cpu_model(), "build": "gcc " + " ".join(O.FLAGS)}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "spin-steps/s", "n_gpus": 1,
             "steps": K, "warmup": W, "ms_per_step": 1e3 * secs / K, "higher_is_better": True,
