@@ -396,8 +396,10 @@ struct TermAcc<float> {
         }
     }
     __device__ __forceinline__ void out(double (&acc)[8]) const {
+        // once per tile; the floats widened from their bits (integer instructions, exact for the
+        // normal floats these sums hold) rather than by conversions on the FP64 pipe
 #pragma unroll
-        for (int c = 0; c < 5; ++c) acc[c] = (double)h[c] + (double)l[c];  // once per tile
+        for (int c = 0; c < 5; ++c) acc[c] = f2d_bits(h[c]) + f2d_bits(l[c]);
         acc[5] = acc[6] = acc[7] = 0.0;
     }
 };
