@@ -728,8 +728,8 @@ def main():
                      "traffic": KERNEL_DRAM_BYTES[dom] if (default_shape and args.precision == "fp32") else None,
                      "traffic_source": "one ncu capture (profiles/), not measured in this run",
                      "kernel": dom, "kernel_ms": dom_ms,
-                     "per_unit": f"{pass_b:.1f} B per spin per Heun pass (the survey's two-pass model with the CSR "
-                                 f"as stored), {lat.n} spins per launch",
+                     "per_unit": f"{pass_b:.1f} B per spin per Heun pass (the two-pass byte model: S, S' and Q "
+                                 f"streamed, the CSR row as stored), {lat.n} spins per launch",
                      "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
                      "step_achieved": step_gbs, "step_frac": step_gbs / hbm_peak,
                      "step_per_unit": f"{step_b:.1f} B per spin-step",
