@@ -312,14 +312,20 @@ ss_status set_spins(ss_system *h, const double *in3n);
 ss_status set_step(ss_system *h, int64_t step);
 ss_status get_step(ss_system *h, int64_t *step);
 
-/* Select how llg_heun_step launches its work (see ss_exec). */
+/* Select how llg_heun_step launches its work (see ss_exec).  SS_ERR_INVALID_ARG for an unknown
+ * mode; SS_ERR_UNSUPPORTED for SS_EXEC_PERSISTENT / SS_EXEC_SYSTEM_BLOCKS with warp-per-row
+ * exchange, and for SS_EXEC_CLUSTER when the handle is not one system of at most 2,048 spins
+ * with rows of at most 12 scalar bonds and no demagnetising field (the message says which).
+ * Every mode gives bitwise the same states; the records too, except SS_EXEC_SYSTEM_BLOCKS,
+ * which sums them in another order. */
 ss_status spin_system_set_exec(ss_system *h, ss_exec mode);
 
 /* Threads per block (32, 64, 128, 256 or 512) and spins per tile (a multiple of the
  * block size, at most 16 blocks' worth) of the step kernels; rebuilds the tile list.
- * SS_ERR_INVALID_ARG for other values.  Single-warp blocks spread a small system's spins
- * over more SMs (the FP64 pipe issues a warp's instruction in the same time whatever the
- * number of active lanes). */
+ * SS_ERR_INVALID_ARG for other values.  Single-warp blocks put each warp of a small system
+ * on an SM of its own; a single small system runs faster still in SS_EXEC_CLUSTER (an FP64
+ * warp instruction holds its SM sub-partition's pipe about 64 cycles whatever the number of
+ * active lanes, so what counts is the FP64 work per warp, which that mode splits up). */
 ss_status spin_system_set_launch(ss_system *h, int32_t block, int32_t tile);
 
 /* How the exchange sum of Eq. HJij is split over threads: mode 0 automatic (the default: a
