@@ -1106,8 +1106,9 @@ __global__ void __launch_bounds__(256) k_rows_sell(const KArgs<R> a) {
         }
         if constexpr (sizeof(R) == 8) {
             // FP64: eight bonds at a time, their words, then their gathers, then the sums in
-            // bond order (5.80 against 6.34 ms per pass on fcc 64^3 to 4a; in FP32 the plain
-            // loop below is faster, 1.52 against 1.70 ms)
+            // bond order (5.80 against 6.34 ms per pass on fcc 64^3 to 4a; sixteen at a time
+            // gives 5.83 ms; in FP32 the plain loop below is faster, 1.52 against 1.70 ms with
+            // eight and 1.99 ms with four)
             constexpr int U = 8;
             int k = 0;
             for (; k + U <= w; k += U) {
