@@ -455,13 +455,12 @@ int64_t ss_debug_live_bytes(void);
  *
  * Some callers cannot call cudaMalloc: code running inside a memory pool or arena that
  * owns all device memory of the process, callers that must not allocate after start-up
- * (real-time loops, allocators that forbid it during stream capture), or host code
- * that receives device buffers from another runtime.  llg_heun_step_noalloc advances
- * one FP64 system whose arrays the caller already holds in device memory, and keeps its
- * working buffers (predictor spins, half steps, thermal field, reduction partials,
- * Box-Muller tables) in one statically sized device array inside the library instead
- * of allocating them.  It never calls cudaMalloc, cudaFree or any allocating library
- * routine.
+ * (real-time loops), or host code that receives device buffers from another runtime.
+ * llg_heun_step_noalloc advances one FP64 system whose arrays the caller already holds in
+ * device memory, and keeps its working buffers (predictor spins, half steps, thermal field,
+ * reduction partials, Box-Muller tables) in one statically sized device array inside the
+ * library instead of allocating them.  It never calls cudaMalloc, cudaFree or any allocating
+ * library routine.
  *
  * Limits and behaviour:
  *  - n <= SS_NOALLOC_MAX_SPINS (131072); larger systems are rejected with
@@ -470,11 +469,10 @@ int64_t ss_debug_live_bytes(void);
  *  - Every call looks up the array's device address on the current device
  *    (cudaGetSymbolAddress, which allocates nothing).  The first call on a device, and any
  *    call that finds the address changed, uploads the function tables with a synchronous
- *    copy; make that first call before any stream capture.  Other calls are asynchronous
- *    on `cuda_stream`.  After cudaDeviceReset (or a torn-down and recreated context) the
- *    array comes back zeroed; if it comes back at the same address the tables are not
- *    uploaded again and the results are wrong: do not use the entry point after a reset in
- *    the same process.
+ *    copy.  Other calls are asynchronous on `cuda_stream`.  After cudaDeviceReset (or a
+ *    torn-down and recreated context) the array comes back zeroed; if it comes back at the
+ *    same address the tables are not uploaded again and the results are wrong: do not use
+ *    the entry point after a reset in the same process.
  *  - All calls share the one array, which keeps the last call's contents.  Nothing in it
  *    needs clearing: every word a step reads (predictor spins, half steps, thermal field,
  *    reduction partials) is written earlier in the same step.  Calls whose work overlaps on
