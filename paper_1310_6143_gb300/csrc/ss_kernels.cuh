@@ -158,7 +158,9 @@ template <typename R, bool Coherent, int NS>
 __device__ __forceinline__ void pattern_sum(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int64_t i, R &x,
                                             R &y, R &z) {
     constexpr int W = NS == kShortRow ? 8 : 16;
-    const int p = a.pat_wide ? (int)__ldg(reinterpret_cast<const uint16_t *>(a.pat) + i) : (int)__ldg(a.pat + i);
+    const int p = a.pat_wide == 0   ? (int)__ldg(a.pat + i)
+                  : a.pat_wide == 1 ? (int)__ldg(reinterpret_cast<const uint16_t *>(a.pat) + i)
+                                    : (int)__ldg(reinterpret_cast<const uint32_t *>(a.pat) + i);
     int32_t off[W];
     const int4 *row = reinterpret_cast<const int4 *>(a.pat_off) + (int64_t)p * (W / 4);
 #pragma unroll
