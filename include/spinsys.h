@@ -360,8 +360,9 @@ ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode);
  * the results are identical.  "Few" means at most 2^22 forms and at most one form slot (8 per
  * form for rows of up to 6 bonds, 16 beyond) per two bonds, so that the tables stay well below
  * the CSR's size.  on = 1 (the default) uses the forms when they were built, 0 reads the CSR;
- * ss_info.row_patterns gives the number of forms in use (0: CSR).  Tensor bonds always read
- * the CSR.  SS_ERR_INVALID_ARG for another value. */
+ * ss_info.row_patterns gives the number of forms in use (0: CSR).  With tensor bonds (Eq.
+ * HJijSMS) a form holds each bond's tensor, as an entry of the handle's tensor dictionary, in
+ * place of J_ij/mu_s,i.  SS_ERR_INVALID_ARG for another value. */
 ss_status spin_system_set_row_patterns(ss_system *h, int32_t on);
 
 /* FP32-mixed form, thread-per-row exchange, graph and plain-launch execution.  mode 0 (the

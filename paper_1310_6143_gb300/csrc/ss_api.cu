@@ -116,6 +116,7 @@ struct ss_system {
     uint8_t *pat = nullptr;
     int32_t *pat_off = nullptr;
     void *pat_J = nullptr;
+    int32_t *pat_tidx = nullptr;        // tensor bonds: the forms' Jt entries (else nullptr)
     int32_t npat = 0;                   // 0: no patterns (too many forms, rows too long)
     int32_t pat_w = 8;                  // slots of a pattern row (8 or 16, see KArgs)
     int pat_wide = 0;                   // index bytes: 0 one, 1 two (more than 256 forms), 2 four
@@ -408,20 +409,22 @@ void build_tables(std::vector<double2> &t) {
 // form (one byte up to 256 forms: the film has 27; two bytes up to 65,536: a batch of 256
 // grains has 6,846; four beyond: the core-shell sphere has 76,795) and the forms are kept in
 // tables, so a pass reads one to four bytes per spin instead of the row's offsets and columns
-// (27.5 bytes on the film).  The exchange sum is then the CSR sum term for term.  Rows longer
-// than kPatRow, or more forms than kMaxPatterns or than half the bonds fill (npat W > nnz / 2:
-// the tables would rival the CSR), keep the CSR (npat = 0).
+// (27.5 bytes on the film).  The exchange sum is then the CSR sum term for term.  With tensor
+// bonds a form holds each bond's tensor entry (tidx, the Jt dictionary index) in place of J.
+// Rows longer than kPatRow, or more forms than kMaxPatterns or than half the bonds fill
+// (npat W > nnz / 2: the tables would rival the CSR), keep the CSR (npat = 0).
 template <typename R>
 ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std::vector<int32_t> &col,
-                         const std::vector<R> &J) {
+                         const std::vector<R> &J, const std::vector<int32_t> &tidx) {
     h->npat = 0;
-    if (h->nnz <= 0 || h->max_row > kPatRow || h->J_tensor) return SS_OK;
+    const bool tensor = h->J_tensor;
+    if (h->nnz <= 0 || h->max_row > kPatRow) return SS_OK;
     const int NS = h->max_row <= kShortRow ? kShortRow : kPatRow;  // offset slots, then the length
     const int W = NS == kShortRow ? 8 : 16;
     const int64_t n = h->n;
     std::vector<uint32_t> pat((size_t)n);
     const int64_t max_forms = std::min<int64_t>(kMaxPatterns, h->nnz / (2 * W));
-    std::vector<int32_t> poff;
+    std::vector<int32_t> poff, ptid;
     std::vector<R> pJ;
     std::unordered_map<uint64_t, int32_t> id_of;  // row hash -> pattern (contents verified)
     for (int64_t i = 0; i < n; ++i) {
@@ -429,7 +432,8 @@ ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std
         uint64_t hsh = 0x9E3779B97F4A7C15ull ^ (uint64_t)len;
         for (int32_t q = 0; q < len; ++q) {
             uint64_t jb = 0;
-            std::memcpy(&jb, &J[(size_t)(b + q)], sizeof(R));
+            if (tensor) jb = (uint64_t)(uint32_t)tidx[(size_t)(b + q)];
+            else std::memcpy(&jb, &J[(size_t)(b + q)], sizeof(R));
             const uint64_t v = (uint64_t)(uint32_t)(col[(size_t)(b + q)] - (int32_t)i) * 0xBF58476D1CE4E5B9ull ^ jb;
             hsh = (hsh ^ v) * 0x94D049BB133111EBull;
             hsh ^= hsh >> 31;
@@ -442,9 +446,11 @@ ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std
             id_of.emplace(hsh, id);
             poff.resize(poff.size() + W, 0);
             pJ.resize(pJ.size() + W, (R)0);
+            if (tensor) ptid.resize(ptid.size() + W, 0);
             for (int32_t q = 0; q < len; ++q) {
                 poff[(size_t)id * W + q] = col[(size_t)(b + q)] - (int32_t)i;
-                pJ[(size_t)id * W + q] = J[(size_t)(b + q)];
+                if (tensor) ptid[(size_t)id * W + q] = tidx[(size_t)(b + q)];
+                else pJ[(size_t)id * W + q] = J[(size_t)(b + q)];
             }
             poff[(size_t)id * W + NS] = len;
         } else {
@@ -452,7 +458,8 @@ ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std
             bool same = poff[(size_t)id * W + NS] == len;
             for (int32_t q = 0; q < len && same; ++q)
                 same = poff[(size_t)id * W + q] == col[(size_t)(b + q)] - (int32_t)i &&
-                       std::memcmp(&pJ[(size_t)id * W + q], &J[(size_t)(b + q)], sizeof(R)) == 0;
+                       (tensor ? ptid[(size_t)id * W + q] == tidx[(size_t)(b + q)]
+                               : std::memcmp(&pJ[(size_t)id * W + q], &J[(size_t)(b + q)], sizeof(R)) == 0);
             if (!same) return SS_OK;  // a hash collision: keep the CSR
         }
         pat[(size_t)i] = (uint32_t)id;
@@ -473,6 +480,11 @@ ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std
     SS_CUDA(h, cudaMemcpyAsync(h->pat_off, poff.data(), poff.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                                h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->pat_J, pJ.data(), pJ.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
+    if (tensor) {
+        SS_CUDA(h, dalloc(h, (void **)&h->pat_tidx, ptid.size() * sizeof(int32_t)));
+        SS_CUDA(h, cudaMemcpyAsync(h->pat_tidx, ptid.data(), ptid.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   h->stream));
+    }
     SS_CUDA(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
     h->npat = (int32_t)(poff.size() / W);
     h->pat_w = W;
@@ -494,6 +506,7 @@ KArgs<R> make_args(const ss_system *h) {
     a.pat = pat ? h->pat : nullptr;
     a.pat_off = pat ? h->pat_off : nullptr;
     a.pat_J = pat ? static_cast<const R *>(h->pat_J) : nullptr;
+    a.pat_tidx = pat ? h->pat_tidx : nullptr;
     a.pat_w = h->pat_w;
     a.pat_wide = h->pat_wide;
     a.mat_uniform = h->nmat == 1 ? 1 : 0;
@@ -1205,7 +1218,7 @@ ss_status upload_system(ss_system *h, const std::vector<HostSys> &hs) {
     SS_CUDA(h, cudaMemcpyAsync(h->mats, mats.data(), mats.size() * sizeof(MatDesc<R>), cudaMemcpyHostToDevice,
                                h->stream));
     {
-        const ss_status ps = build_patterns<R>(h, rp, col, J);
+        const ss_status ps = build_patterns<R>(h, rp, col, J, Jtidx);
         if (ps != SS_OK) return ps;
     }
     for (int b = 0; b < 12; ++b) SS_CUDA(h, dalloc(h, &h->state[b], (size_t)n * rs));

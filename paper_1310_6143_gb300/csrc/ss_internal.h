@@ -98,6 +98,8 @@ struct KArgs {
                               // row's end, then the row length at slot pat_w - 2 (short) or
                               // pat_w - 4 (long); 32- or 64-byte aligned rows
     const R *pat_J;           // [npat][pat_w] J_ij / mu_s,i of each bond, 0 past the row's end
+    const int32_t *pat_tidx;  // tensor bonds: [npat][pat_w] Jt entry of each bond (the forms then
+                              // hold these instead of J), else nullptr
     int pat_w;                // 8: rows of at most kShortRow bonds; 16: at most kPatRow
     MatDesc<R> mat0;          // the only material when mat_uniform is set
     int mat_uniform;          // 1: every spin has material 0 (mat is not read)

@@ -197,6 +197,46 @@ __device__ __forceinline__ void exchange_sum(const KArgs<R> &a, const SysDesc &s
                                       e1, e2);
 }
 
+// The exchange sum of a row of tensor bonds stored as a row pattern: the form's offsets, length
+// and tensor entries come as vector loads, and the row's bonds (the slots before its length)
+// are summed as the CSR loop sums them, the tensor of bond k applied to S_j.
+template <typename R, bool Coherent, int NS>
+__device__ __forceinline__ void pattern_sum_tensor(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int64_t i,
+                                                   R &x, R &y, R &z) {
+    constexpr int W = NS == kShortRow ? 8 : 16;
+    const int p = a.pat_wide == 0   ? (int)__ldg(a.pat + i)
+                  : a.pat_wide == 1 ? (int)__ldg(reinterpret_cast<const uint16_t *>(a.pat) + i)
+                                    : (int)__ldg(reinterpret_cast<const uint32_t *>(a.pat) + i);
+    int32_t off[W], tid[W];
+    const int4 *row = reinterpret_cast<const int4 *>(a.pat_off) + (int64_t)p * (W / 4);
+    const int4 *trow = reinterpret_cast<const int4 *>(a.pat_tidx) + (int64_t)p * (W / 4);
+#pragma unroll
+    for (int v = 0; v < W / 4; ++v) {
+        const int4 t = __ldg(row + v), u = __ldg(trow + v);
+        off[4 * v] = t.x;
+        off[4 * v + 1] = t.y;
+        off[4 * v + 2] = t.z;
+        off[4 * v + 3] = t.w;
+        tid[4 * v] = u.x;
+        tid[4 * v + 1] = u.y;
+        tid[4 * v + 2] = u.z;
+        tid[4 * v + 3] = u.w;
+    }
+    const int len = off[NS];
+    const int32_t ii = (int32_t)i;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        if (q < len) {
+            const int32_t j = chk((int64_t)ii + off[q], a.n, a.err);
+            const R *t = a.Jt + 9 * (int64_t)tid[q];
+            const R sx = ld<Coherent>(X + j), sy = ld<Coherent>(Y + j), sz = ld<Coherent>(Z + j);
+            x = fma(__ldg(t + 0), sx, fma(__ldg(t + 1), sy, fma(__ldg(t + 2), sz, x)));
+            y = fma(__ldg(t + 3), sx, fma(__ldg(t + 4), sy, fma(__ldg(t + 5), sz, y)));
+            z = fma(__ldg(t + 6), sx, fma(__ldg(t + 7), sy, fma(__ldg(t + 8), sz, z)));
+        }
+    }
+}
+
 // The sum started at the system's applied field (hx, hy, hz), passed in by callers that hold
 // it in registers for a whole tile.
 template <typename R, bool Coherent, int Mode>
@@ -214,6 +254,16 @@ __device__ __forceinline__ void exchange_sum_h(const KArgs<R> &a, R hx, R hy, R 
             pattern_sum<R, Coherent, kShortRow>(a, X, Y, Z, i, x, y, z);
         else
             pattern_sum<R, Coherent, kPatRow>(a, X, Y, Z, i, x, y, z);
+        e0 = x;
+        e1 = y;
+        e2 = z;
+        return;
+    }
+    if (Mode == kGeneral && a.J_tensor && a.pat) {
+        if (a.pat_w == 8)
+            pattern_sum_tensor<R, Coherent, kShortRow>(a, X, Y, Z, i, x, y, z);
+        else
+            pattern_sum_tensor<R, Coherent, kPatRow>(a, X, Y, Z, i, x, y, z);
         e0 = x;
         e1 = y;
         e2 = z;

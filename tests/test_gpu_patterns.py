@@ -86,3 +86,26 @@ def test_four_byte_forms_bitwise_equal_to_csr(SS, precision):
     assert on[0]["row_patterns"] == 76795 and off[0]["row_patterns"] == 0
     for a, b in zip(on[1:], off[1:]):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("name", ["sc_open", "fcc64"])
+def test_tensor_forms_bitwise_equal_to_csr(SS, name, precision):
+    """Tensor bonds with an interface Dzyaloshinskii-Moriya term and cubic anisotropy: the forms
+    hold each bond's tensor entry in place of J, and the results are the CSR's bit for bit, in
+    the Heun steps, the records and Monte Carlo.  sc with a free axis (rows of up to 6 bonds, 27
+    forms); fcc 64^3 as benchmarked (rows of 12, 17,959 forms: the DM vectors' last bits follow
+    the positions, two-byte indices)."""
+    if name == "sc_open":
+        lat = L.with_dm(L.simple_cubic(9, 7, 11, periodic=(True, False, True), k_u=1e-24, with_pos=True), D=1e-21)
+        steps, mc = 12, 3
+    else:
+        lat = L.with_dm(L.fcc(64, 64, 64, J=11.2e-21, k_u=6.69e-24, with_pos=True), D=1.12e-21)
+        steps, mc = 4, 1
+    lat.k_c = np.full(lat.n, 5e-24)
+    kw = dict(alpha=0.05, dt=1e-16, T=300.0, seed=4, H=(0.1, 0.0, 0.2))
+    on = _run(SS, lat, True, precision, kw, steps=steps, mc=mc)
+    off = _run(SS, lat, False, precision, kw, steps=steps, mc=mc)
+    assert on[0]["row_patterns"] > 0 and off[0]["row_patterns"] == 0
+    for a, b in zip(on[1:], off[1:]):
+        np.testing.assert_array_equal(a, b)
