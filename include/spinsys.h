@@ -353,13 +353,13 @@ ss_status spin_system_set_exchange_rows(ss_system *h, int32_t mode);
  * steps, the on-demand measurement and Monte Carlo.  At creation, when the rows take few
  * distinct forms -- a form being a row's length (at most 12) and its (column - row,
  * J_ij/mu_s,i) pairs in CSR order, as on a lattice whose interior rows all look alike and
- * whose boundary rows come in a few kinds (the film: 27 forms; a batch of 256 grains: 6,846;
- * the 20 nm core-shell sphere: 76,795) -- each spin stores a form index (one byte up to 256
- * forms, two up to 65,536, else four) and the forms are kept in tables; the sums then read the
- * index instead of the row's offsets and columns, and add the same terms in the same order, so
- * the results are identical.  "Few" means at most 2^22 forms and at most one form slot (8 per
- * form for rows of up to 6 bonds, 16 beyond) per two bonds, so that the tables stay well below
- * the CSR's size.  on = 1 (the default) uses the forms when they were built, 0 reads the CSR;
+ * whose boundary rows come in a few kinds (the film: 27 forms; a batch of 256 grains: 6,846) --
+ * each spin stores a form index (one byte up to 256 forms, else two) and the forms are kept in
+ * tables; the sums then read one or two bytes per spin instead of the row's offsets and
+ * columns, and add the same terms in the same order, so the results are identical.  "Few"
+ * means at most 65,536 forms and at most one form slot (8 per form for rows of up to 6 bonds,
+ * 16 beyond) per two bonds, so that the tables stay well below the CSR's size (the 20 nm
+ * core-shell sphere, 76,795 forms, reads the CSR).  on = 1 (the default) uses the forms when they were built, 0 reads the CSR;
  * ss_info.row_patterns gives the number of forms in use (0: CSR).  With tensor bonds (Eq.
  * HJijSMS) a form holds each bond's tensor, as an entry of the handle's tensor dictionary, in
  * place of J_ij/mu_s,i.  SS_ERR_INVALID_ARG for another value. */

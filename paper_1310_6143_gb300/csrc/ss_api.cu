@@ -111,15 +111,13 @@ struct ss_system {
     double2 *tab = nullptr;             // Box-Muller tables (build_bm_tables), then the
                                         // double-float tables (build_ff_tables)
     int32_t max_row = 0;                // longest CSR row
-    // Row patterns (the CSR stored as a one-, two- or four-byte form index per row, see
-    // build_patterns)
+    // Row patterns (the CSR stored as one or two bytes per row, see build_patterns)
     uint8_t *pat = nullptr;
     int32_t *pat_off = nullptr;
-    void *pat_J = nullptr;
-    int32_t *pat_tidx = nullptr;        // tensor bonds: the forms' Jt entries (else nullptr)
+    void *pat_J = nullptr;              // J of the forms' bonds, or their Jt entries (tensor bonds)
     int32_t npat = 0;                   // 0: no patterns (too many forms, rows too long)
     int32_t pat_w = 8;                  // slots of a pattern row (8 or 16, see KArgs)
-    int pat_wide = 0;                   // index bytes: 0 one, 1 two (more than 256 forms), 2 four
+    bool pat_wide = false;              // two-byte pattern indices (more than 256 forms)
     bool use_pat = true;                // spin_system_set_row_patterns
     // Slab of a decomposed system (spin_slab_create): the owned spins are the first slab_own
     // of the arrays, the halo copies follow; tiles cover the owned spins, boundary tiles first
@@ -407,9 +405,8 @@ void build_tables(std::vector<double2> &t) {
 // (column - row, J_ij / mu_s,i) pairs in CSR order, as on a lattice whose interior rows all look
 // alike and whose boundary rows come in a few kinds -- each spin stores the index of its row's
 // form (one byte up to 256 forms: the film has 27; two bytes up to 65,536: a batch of 256
-// grains has 6,846; four beyond: the core-shell sphere has 76,795) and the forms are kept in
-// tables, so a pass reads one to four bytes per spin instead of the row's offsets and columns
-// (27.5 bytes on the film).  The exchange sum is then the CSR sum term for term.  With tensor
+// grains has 6,846) and the forms are kept in tables, so a pass reads one or two bytes per spin
+// instead of the row's offsets and columns (27.5 bytes on the film).  The exchange sum is then the CSR sum term for term.  With tensor
 // bonds a form holds each bond's tensor entry (tidx, the Jt dictionary index) in place of J.
 // Rows longer than kPatRow, or more forms than kMaxPatterns or than half the bonds fill
 // (npat W > nnz / 2: the tables would rival the CSR), keep the CSR (npat = 0).
@@ -422,7 +419,7 @@ ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std
     const int NS = h->max_row <= kShortRow ? kShortRow : kPatRow;  // offset slots, then the length
     const int W = NS == kShortRow ? 8 : 16;
     const int64_t n = h->n;
-    std::vector<uint32_t> pat((size_t)n);
+    std::vector<uint16_t> pat((size_t)n);
     const int64_t max_forms = std::min<int64_t>(kMaxPatterns, h->nnz / (2 * W));
     std::vector<int32_t> poff, ptid;
     std::vector<R> pJ;
@@ -462,29 +459,26 @@ ss_status build_patterns(ss_system *h, const std::vector<int32_t> &rp, const std
                                : std::memcmp(&pJ[(size_t)id * W + q], &J[(size_t)(b + q)], sizeof(R)) == 0);
             if (!same) return SS_OK;  // a hash collision: keep the CSR
         }
-        pat[(size_t)i] = (uint32_t)id;
+        pat[(size_t)i] = (uint16_t)id;
     }
-    const size_t nforms = poff.size() / W;
-    const int wide = nforms > (size_t)kShortPatterns ? 2 : nforms > (size_t)kBytePatterns ? 1 : 0;
+    const bool wide = poff.size() / W > (size_t)kBytePatterns;
     std::vector<uint8_t> pat8;
-    std::vector<uint16_t> pat16;
-    if (wide == 0) pat8.assign(pat.begin(), pat.end());
-    if (wide == 1) pat16.assign(pat.begin(), pat.end());
-    const void *psrc = wide == 0 ? (const void *)pat8.data() : wide == 1 ? (const void *)pat16.data()
-                                                                        : (const void *)pat.data();
-    const size_t pbytes = (size_t)n << wide;
+    if (!wide) pat8.assign(pat.begin(), pat.end());
+    const void *psrc = wide ? (const void *)pat.data() : (const void *)pat8.data();
+    const size_t pbytes = (size_t)n * (wide ? 2 : 1);
     SS_CUDA(h, dalloc(h, (void **)&h->pat, pbytes));
     SS_CUDA(h, dalloc(h, (void **)&h->pat_off, poff.size() * sizeof(int32_t)));
+    // tensor bonds: the forms' Jt entries (int32) take the place of J, W of them per form, at the
+    // start of each form's W * sizeof(R) bytes
+    if (tensor)
+        for (size_t f = 0; f < poff.size() / W; ++f)
+            std::memcpy(reinterpret_cast<char *>(pJ.data()) + f * W * sizeof(R), &ptid[f * W], W * sizeof(int32_t));
     SS_CUDA(h, dalloc(h, &h->pat_J, pJ.size() * sizeof(R)));
     SS_CUDA(h, cudaMemcpyAsync(h->pat, psrc, pbytes, cudaMemcpyHostToDevice, h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->pat_off, poff.data(), poff.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                                h->stream));
     SS_CUDA(h, cudaMemcpyAsync(h->pat_J, pJ.data(), pJ.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
-    if (tensor) {
-        SS_CUDA(h, dalloc(h, (void **)&h->pat_tidx, ptid.size() * sizeof(int32_t)));
-        SS_CUDA(h, cudaMemcpyAsync(h->pat_tidx, ptid.data(), ptid.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                   h->stream));
-    }
+
     SS_CUDA(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
     h->npat = (int32_t)(poff.size() / W);
     h->pat_w = W;
@@ -506,9 +500,8 @@ KArgs<R> make_args(const ss_system *h) {
     a.pat = pat ? h->pat : nullptr;
     a.pat_off = pat ? h->pat_off : nullptr;
     a.pat_J = pat ? static_cast<const R *>(h->pat_J) : nullptr;
-    a.pat_tidx = pat ? h->pat_tidx : nullptr;
     a.pat_w = h->pat_w;
-    a.pat_wide = h->pat_wide;
+    a.pat_wide = h->pat_wide ? 1 : 0;
     a.mat_uniform = h->nmat == 1 ? 1 : 0;
     std::memcpy(&a.mat0, h->mat0, sizeof(MatDesc<R>));
     a.Jt = static_cast<const R *>(h->Jt);

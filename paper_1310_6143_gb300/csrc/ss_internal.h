@@ -26,9 +26,8 @@ constexpr int kTabCount = kLogTab + kLn2Tab + kTrigTab + kLogLo;
 constexpr int kFFTabFloat4 = kLogTab + kTrigTab + (kLn2Tab + 1) / 2;
 constexpr int kShortRow = 6;   // rows of at most this many bonds take the unrolled exchange sum
 constexpr int kPatRow = 12;    // longest row a row pattern holds
-constexpr int kMaxPatterns = 1 << 22;  // most row forms kept (and at most half the bonds' worth)
-constexpr int kBytePatterns = 256;     // up to this many forms the index is one byte,
-constexpr int kShortPatterns = 65536;  // up to this many two bytes, else four
+constexpr int kMaxPatterns = 65536;  // most row forms kept (and at most half the bonds' worth)
+constexpr int kBytePatterns = 256;   // up to this many forms the index is one byte, else two
 constexpr int kRecComps = 8;   // record: sum mu S (3), sum mu, E_exc, E_ani, E_app, E_total
 constexpr int kPartComps = 8;  // tile partials: sum mu S (3), sum -mu S.h/2, E_ani, 0, 0, 0
 
@@ -90,16 +89,14 @@ struct KArgs {
     R J_value;                // the common value when every entry of J is the same
     int J_uniform;            // 1: J is not read, every bond has J_value
     int short_rows;           // 1: no row has more than kShortRow bonds
-    const uint8_t *pat;       // [n] row pattern of each spin (uint8, uint16 or uint32 by pat_wide),
-                              // or nullptr (the CSR is read)
-    int pat_wide;             // 0: uint8 indices, 1: uint16 (more than 256 forms), 2: uint32
-                              // (more than 65,536)
+    const uint8_t *pat;       // [n] row pattern of each spin (uint8, or uint16 when pat_wide), or
+                              // nullptr (the CSR is read)
+    int pat_wide;             // 1: pat holds uint16 indices (more than 256 forms)
     const int32_t *pat_off;   // [npat][pat_w] column - row of each bond in CSR order, 0 past the
                               // row's end, then the row length at slot pat_w - 2 (short) or
                               // pat_w - 4 (long); 32- or 64-byte aligned rows
-    const R *pat_J;           // [npat][pat_w] J_ij / mu_s,i of each bond, 0 past the row's end
-    const int32_t *pat_tidx;  // tensor bonds: [npat][pat_w] Jt entry of each bond (the forms then
-                              // hold these instead of J), else nullptr
+    const R *pat_J;           // [npat][pat_w] J_ij / mu_s,i of each bond, 0 past the row's end;
+                              // with tensor bonds int32 Jt entries instead (J is not read)
     int pat_w;                // 8: rows of at most kShortRow bonds; 16: at most kPatRow
     MatDesc<R> mat0;          // the only material when mat_uniform is set
     int mat_uniform;          // 1: every spin has material 0 (mat is not read)

@@ -158,9 +158,7 @@ template <typename R, bool Coherent, int NS>
 __device__ __forceinline__ void pattern_sum(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int64_t i, R &x,
                                             R &y, R &z) {
     constexpr int W = NS == kShortRow ? 8 : 16;
-    const int p = a.pat_wide == 0   ? (int)__ldg(a.pat + i)
-                  : a.pat_wide == 1 ? (int)__ldg(reinterpret_cast<const uint16_t *>(a.pat) + i)
-                                    : (int)__ldg(reinterpret_cast<const uint32_t *>(a.pat) + i);
+    const int p = a.pat_wide ? (int)__ldg(reinterpret_cast<const uint16_t *>(a.pat) + i) : (int)__ldg(a.pat + i);
     int32_t off[W];
     const int4 *row = reinterpret_cast<const int4 *>(a.pat_off) + (int64_t)p * (W / 4);
 #pragma unroll
@@ -204,12 +202,11 @@ template <typename R, bool Coherent, int NS>
 __device__ __forceinline__ void pattern_sum_tensor(const KArgs<R> &a, const R *X, const R *Y, const R *Z, int64_t i,
                                                    R &x, R &y, R &z) {
     constexpr int W = NS == kShortRow ? 8 : 16;
-    const int p = a.pat_wide == 0   ? (int)__ldg(a.pat + i)
-                  : a.pat_wide == 1 ? (int)__ldg(reinterpret_cast<const uint16_t *>(a.pat) + i)
-                                    : (int)__ldg(reinterpret_cast<const uint32_t *>(a.pat) + i);
+    const int p = a.pat_wide ? (int)__ldg(reinterpret_cast<const uint16_t *>(a.pat) + i) : (int)__ldg(a.pat + i);
     int32_t off[W], tid[W];
     const int4 *row = reinterpret_cast<const int4 *>(a.pat_off) + (int64_t)p * (W / 4);
-    const int4 *trow = reinterpret_cast<const int4 *>(a.pat_tidx) + (int64_t)p * (W / 4);
+    // the form's Jt entries: W int32 at the start of its W * sizeof(R) bytes of pat_J
+    const int4 *trow = reinterpret_cast<const int4 *>(a.pat_J) + (int64_t)p * (W / 4) * ((int)sizeof(R) / 4);
 #pragma unroll
     for (int v = 0; v < W / 4; ++v) {
         const int4 t = __ldg(row + v), u = __ldg(trow + v);
